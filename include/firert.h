@@ -1,0 +1,218 @@
+/* firert.h — C ABI of the B300 (sm_103a) per-pixel wildfire-temperature
+ * retrieval: the forward model of Eq. (fm) = Eq. (solar) + Eq. (thermal),
+ * fitted to every pixel of a VSWIR scene by the two-stage windowed
+ * least-squares inversion of Sec. 2.6 (Eq. loss, Eq. affine), here solved
+ * with a damped Gauss-Newton (Levenberg-Marquardt) iteration.
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only. Every array is caller-owned unless stated; the
+ *    context owns its device tables and workspace.
+ *  - Device pointers are CUDA global-memory pointers on the context's device;
+ *    host pointers are ordinary (ideally pinned) host memory.
+ *  - Calls are asynchronous on the given stream (NULL = legacy default
+ *    stream) unless stated. Per-pixel failures are reported in the per-pixel
+ *    status byte, never in the return code, which only reports argument,
+ *    shape, memory and CUDA errors. No exceptions cross the ABI.
+ *  - A context is not thread-safe: use one per host thread.
+ */
+#ifndef FIRERT_H
+#define FIRERT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fire_stream_t; /* == cudaStream_t */
+
+typedef enum {
+  FIRE_OK = 0,
+  FIRE_ERR_ARG = 1,        /* NULL pointer or out-of-range scalar */
+  FIRE_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  FIRE_ERR_NOMEM = 3,      /* device or pinned allocation failed */
+  FIRE_ERR_SHAPE = 4,      /* sizes outside what the kernels support */
+  FIRE_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+  FIRE_ERR_CHECKPOINT = 6, /* bad or corrupt MLP checkpoint */
+  FIRE_ERR_STATE = 7       /* call not valid in the context's state */
+} fire_status_t;
+
+/* Per-pixel status byte: low 3 bits are the outcome, upper bits are flags. */
+enum {
+  FIRE_PX_CONVERGED = 0,     /* stage 2 met a convergence test */
+  FIRE_PX_MAXITER = 1,       /* stage 2 hit its iteration cap */
+  FIRE_PX_NONFINITE = 2,     /* a radiance value is NaN or Inf: not fitted */
+  FIRE_PX_ALL_MASKED = 3,    /* too few unmasked bands in a window */
+  FIRE_PX_CHOL_FAIL = 4,     /* damped normal matrix never factorised */
+  FIRE_PX_NOT_CANDIDATE = 5, /* below the HFDI gate (Sec. 2.1): not fitted */
+  FIRE_PX_F_FP64 = 8,        /* an ill-conditioned step was solved in FP64 */
+  FIRE_PX_F_NOT_IDENT = 16,  /* Laplace sd(E[T]) or alpha SNR outside limits */
+  FIRE_PX_F_MLP_FALLBACK = 32, /* MLP-initialised fit replaced by plain LM */
+  FIRE_PX_F_S1_MAXITER = 64  /* stage 1 hit its iteration cap */
+};
+
+enum { FIRE_MEM_DEVICE = 0, FIRE_MEM_HOST = 1 };
+enum { FIRE_INIT_DEFAULT = 0, FIRE_INIT_GIVEN = 1, FIRE_INIT_MLP = 2 };
+enum { FIRE_FIT_ALL = 0, FIRE_FIT_HFDI = 1 };
+enum { FIRE_MAX_ENDM = 8, FIRE_MAX_BANDS = 512, FIRE_MAX_TGRID = 128, FIRE_MAX_WV = 256 };
+
+/* Scene tables (Sec. 2.3): HOST pointers, copied into the context by
+ * fire_ctx_create; the caller may free them afterwards.
+ *   wavelength_nm [n_bands]  band centres, strictly increasing (nm)
+ *   solar_irr     [n_bands]  E_sun(lambda), W m^-2 nm^-1 (Eq. solar)
+ *   cos_sza                   cos(theta_s)
+ *   tau_down, tau_up, rho_atm, sph_alb [n_wv][n_bands]: the per-scene LUT
+ *                             evaluated at each quantised water-vapour bin
+ *                             (Sec. 2.5-2.6); rho_atm / sph_alb may be NULL (0)
+ *   endmembers    [n_endm][n_bands] surface reflectance library (Sec. 2.4)
+ *   sat_level     [n_bands] or NULL: a band with L >= sat_level is masked,
+ *                             m(lambda) = 0 in Eq. (loss)
+ *   tgrid_lo/hi, n_tgrid      temperature grid of Eq. (thermal), [350, 2200] K */
+typedef struct {
+  int32_t n_bands, n_wv, n_endm, n_tgrid;
+  const float *wavelength_nm;
+  const float *solar_irr;
+  float cos_sza;
+  const float *tau_down, *tau_up, *rho_atm, *sph_alb;
+  const float *endmembers;
+  const float *sat_level;
+  float tgrid_lo, tgrid_hi;
+} fire_tables_t;
+
+/* Solver constants. Windows follow Sec. 2.3/2.6; the iteration caps read the
+ * paper's 30/100 optimiser steps as caps (50/100); the rest are this
+ * library's stated choices (the paper gives no LM constants). Fill with
+ * fire_default_config and edit. */
+typedef struct {
+  float win1_lo, win1_hi;           /* Omega_1 (nm) */
+  float win2h_lo, win2h_hi;         /* Omega_2^hot */
+  float win2s_lo, win2s_hi;         /* Omega_2^smol; stage 2 fits the union */
+  int32_t max_it1, max_it2;         /* trial steps per stage */
+  float tau0;                       /* initial damping = tau0 * max diag */
+  float tol_g;                      /* |g_i| <= tol_g sqrt(H_ii cost) */
+  float tol_x;                      /* max |step| in z below tol_x */
+  float tol_f;                      /* relative cost decrease below tol_f */
+  float kappa_max;                  /* condition estimate that switches the
+                                       step solve to FP64 */
+  float dfloor;                     /* damping diagonal floor (relative) */
+  float noise_rel, noise_abs;       /* noise model sd^2 = (rel L)^2 + abs^2 */
+  int32_t weighted;                 /* 0: Eq. (loss) as printed; 1: 1/sd^2 */
+  float hfdi_thresh;                /* Sec. 2.1: HFDI >= -0.1 */
+  float hfdi_lambda_hi, hfdi_lambda_lo; /* 2430 nm, 2061 nm */
+  float ident_sd_et;                /* identifiable: Laplace sd(E[T]) <= this */
+  float ident_alpha_snr;            /* ... and alpha >= snr * sd(alpha) */
+} fire_config_t;
+
+/* Priors: bounds of Eq. (affine), a weak diagonal Gaussian prior in z
+ * (precision counted in units of one band's noise variance), the start rule.
+ * Stage-1 layout [x_surf(K), alpha1, T1]; stage-2 layout
+ * [mu_h, sigma_h, mu_s, sigma_s, eta, alpha]. A variable with lo == hi is
+ * held fixed. The surface fractions must all have bounds [0, 1]. */
+typedef struct {
+  float lo1[FIRE_MAX_ENDM + 2], hi1[FIRE_MAX_ENDM + 2];
+  float pm1[FIRE_MAX_ENDM + 2], pp1[FIRE_MAX_ENDM + 2];
+  float lo2[6], hi2[6], pm2[6], pp2[6];
+  float init_alpha1, init_T1, init_sigma, init_mu_h_floor, init_mu_s_ceil;
+  float init_eta_lo, init_eta_hi;
+  int32_t init_mode;                /* FIRE_INIT_* */
+  const float *init_state;          /* [n_pix][n_endm + 8] when GIVEN, same
+                                       memory kind as the scene */
+} fire_priors_t;
+
+/* One scene: BIP radiance [n_pix][n_bands] fp32 (W m^-2 sr^-1 nm^-1) and
+ * the water-vapour bin of each pixel [n_pix] (< n_wv; a pixel whose bin is out
+ * of range is not fitted and gets status FIRE_PX_NONFINITE). mem: FIRE_MEM_DEVICE
+ * or FIRE_MEM_HOST (host buffers are staged through device memory inside
+ * the call, which then synchronises the stream before returning). */
+typedef struct {
+  int64_t n_pix;
+  const float *radiance;
+  const uint16_t *wv_bin;
+  int32_t mem;
+  int32_t gate_mode;                /* FIRE_FIT_ALL or FIRE_FIT_HFDI */
+} fire_scene_t;
+
+/* Per-pixel outputs, same memory kind as the scene; any may be NULL.
+ *   state  [n_pix][n_endm+8]  [x_surf, alpha1, T1, mu_h, s_h, mu_s, s_s, eta, alpha]
+ *   ET, sdT                   moment-matched E[T], sigma[T] (Sec. 2.3), K
+ *   alpha                     stage-2 thermal scaling
+ *   cov    [n_pix][21]        Laplace covariance of the stage-2 state, packed
+ *                             upper triangle, physical units, FP64-computed
+ *   var_ET                    delta-method variance of E[T]
+ *   cost                      final stage-2 cost; rms: unweighted residual rms
+ *   hfdi                      HFDI of the pixel
+ *   status, iters [n_pix][2]  status byte; trial steps of stage 1 and 2 */
+typedef struct {
+  float *state, *ET, *sdT, *alpha, *cov, *var_ET, *cost, *rms, *hfdi;
+  uint8_t *status;
+  uint16_t *iters;
+} fire_outputs_t;
+
+/* Counters of the last retrieve call (read after the stream synchronises). */
+typedef struct {
+  uint64_t n_pixels, sum_it1, sum_it2, n_fp64_pixels;
+  uint64_t band_evals1, band_evals2, node_band_evals2;  /* work units */
+  uint64_t status_counts[8];
+  double flops;                     /* algorithmic flops of the fit */
+  int32_t kernel_launches;
+} fire_stats_t;
+
+typedef struct fire_ctx fire_ctx_t;
+
+/* Fill the documented defaults. */
+void fire_default_config(fire_config_t *cfg);
+void fire_default_priors(fire_priors_t *pri, int32_t n_endm, int32_t n_tgrid,
+                         float tgrid_lo, float tgrid_hi);
+
+/* Create a context on the current CUDA device: validates and uploads the
+ * tables, builds the Planck grid B(lambda_b, T_j) and the per-band constants
+ * on the device (Eq. thermal; synchronous). cfg NULL = defaults.
+ * Errors: FIRE_ERR_ARG (NULL/invalid), FIRE_ERR_SHAPE (n_bands > 512,
+ * n_endm not in 1..8, n_tgrid not in 2..128, empty window), FIRE_ERR_NOMEM,
+ * FIRE_ERR_CUDA. On error *out is NULL. */
+fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tables,
+                              const fire_config_t *cfg);
+void fire_ctx_destroy(fire_ctx_t *ctx);
+
+/* Retrieve every pixel of one scene (Sec. 2.6 stage 1 then stage 2, per
+ * pixel, on the GPU). pri NULL = defaults. n_pix == 0 is a no-op.
+ * Errors: FIRE_ERR_ARG, FIRE_ERR_SHAPE, FIRE_ERR_NOMEM (host staging),
+ * FIRE_ERR_CUDA, FIRE_ERR_TIMEOUT (table staging wait gave up). */
+fire_status_t fire_retrieve(fire_ctx_t *ctx, const fire_scene_t *scene,
+                            const fire_priors_t *pri, const fire_outputs_t *out,
+                            fire_stream_t stream);
+
+/* Forward model Eq. (fm) for n states (device pointers):
+ *   mode 1: state [n][K+2] = [x_surf, alpha1, T1] (single temperature);
+ *   mode 2: state [n][K+6] = [x_surf, mu_h, s_h, mu_s, s_s, eta, alpha]
+ *           (two-component Gaussian p(T) on the grid).
+ * L_out [n][n_bands] fp32. If noise_rel or noise_abs > 0, adds
+ * sd * N(0,1) with sd^2 = (rel L)^2 + abs^2, the normal drawn by Box-Muller
+ * from the counter-based SplitMix64 stream (seed, stream_id, pixel_offset + i,
+ * 2b / 2b+1). A state whose water-vapour bin is out of range gets NaN radiance. */
+fire_status_t fire_forward(fire_ctx_t *ctx, int32_t mode, const float *state,
+                           const uint16_t *wv_bin, int64_t n, float noise_rel,
+                           float noise_abs, uint64_t seed, uint64_t stream_id,
+                           int64_t pixel_offset, float *L_out, fire_stream_t stream);
+
+/* 12x12-style block mean of a BIP cube (Sec. 2.9): src [height][width][n_bands]
+ * -> dst [height/block][width/block][n_bands], edge remainder dropped.
+ * Device pointers. */
+fire_status_t fire_block_mean(const float *src, int32_t width, int32_t height,
+                              int32_t n_bands, int32_t block, float *dst,
+                              fire_stream_t stream);
+
+/* Counters of the last fire_retrieve on this context (synchronises it). */
+fire_status_t fire_get_stats(fire_ctx_t *ctx, fire_stats_t *stats);
+
+/* Band index ranges of the two fitting windows (for tests and reporting). */
+fire_status_t fire_window_bands(fire_ctx_t *ctx, int32_t *b1_lo, int32_t *n1,
+                                int32_t *b2_lo, int32_t *n2);
+
+const char *fire_status_str(fire_status_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIRERT_H */

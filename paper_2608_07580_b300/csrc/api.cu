@@ -1,0 +1,492 @@
+// api.cu — the C ABI (include/firert.h): argument validation, context and
+// device-memory management, host staging and kernel launches. No retrieval
+// arithmetic runs on the host: tables, forward model and fits are kernels.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/firert.h"
+#include "internal.cuh"
+
+using namespace firert;
+
+struct fire_ctx {
+  int device = 0;
+  int num_sms = 0;
+  fire_config_t cfg;
+  KTables t;
+  // device buffers
+  float *d_image = nullptr;
+  float4 *d_wvtab = nullptr;
+  float *d_sat = nullptr;
+  unsigned long long *d_work = nullptr;  // [0] counter, [1..] stats
+  int *d_err = nullptr;
+  // host staging for FIRE_MEM_HOST scenes
+  void *d_stage = nullptr;
+  size_t stage_bytes = 0;
+  int last_launches = 0;
+};
+
+namespace {
+
+fire_status_t cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return FIRE_OK;
+  if (e == cudaErrorMemoryAllocation) return FIRE_ERR_NOMEM;
+  return FIRE_ERR_CUDA;
+}
+
+#define CK(call)                                 \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+// contiguous band range [lo, lo + n) whose centres fall in [wlo, whi]
+// (or in the union of two intervals); n = 0 if none
+void band_range(const float *wl, int nb, float a_lo, float a_hi, float b_lo, float b_hi,
+                int *lo, int *n) {
+  int first = -1, last = -1;
+  for (int b = 0; b < nb; b++) {
+    bool in = (wl[b] >= a_lo && wl[b] <= a_hi) || (wl[b] >= b_lo && wl[b] <= b_hi);
+    if (in) {
+      if (first < 0) first = b;
+      last = b;
+    }
+  }
+  *lo = first < 0 ? 0 : first;
+  *n = first < 0 ? 0 : last - first + 1;
+}
+
+int nearest_band(const float *wl, int nb, float lam) {
+  int best = 0;
+  for (int b = 1; b < nb; b++)
+    if (fabsf(wl[b] - lam) < fabsf(wl[best] - lam)) best = b;
+  return best;
+}
+
+void fill_kconfig(KConfig &k, const fire_config_t &c, const fire_priors_t &p, int K) {
+  memset(&k, 0, sizeof(k));
+  for (int i = 0; i < K + 2; i++) {
+    k.lo1[i] = p.lo1[i];
+    k.hi1[i] = p.hi1[i];
+    k.pm1[i] = p.pm1[i];
+    k.pp1[i] = p.pp1[i];
+  }
+  for (int i = 0; i < 6; i++) {
+    k.lo2[i] = p.lo2[i];
+    k.hi2[i] = p.hi2[i];
+    k.pm2[i] = p.pm2[i];
+    k.pp2[i] = p.pp2[i];
+  }
+  k.init_alpha1 = p.init_alpha1;
+  k.init_T1 = p.init_T1;
+  k.init_sigma = p.init_sigma;
+  k.init_mu_h_floor = p.init_mu_h_floor;
+  k.init_mu_s_ceil = p.init_mu_s_ceil;
+  k.init_eta_lo = p.init_eta_lo;
+  k.init_eta_hi = p.init_eta_hi;
+  k.max_it1 = c.max_it1;
+  k.max_it2 = c.max_it2;
+  k.tau0 = c.tau0;
+  k.tol_g = c.tol_g;
+  k.tol_x = c.tol_x;
+  k.tol_f = c.tol_f;
+  k.kappa_max = c.kappa_max;
+  k.dfloor = c.dfloor;
+  k.noise_rel = c.noise_rel;
+  k.noise_abs = c.noise_abs;
+  k.weighted = c.weighted;
+  k.hfdi_thresh = c.hfdi_thresh;
+  k.ident_sd_et = c.ident_sd_et;
+  k.ident_alpha_snr = c.ident_alpha_snr;
+}
+
+bool priors_valid(const fire_priors_t &p, int K) {
+  for (int i = 0; i < K; i++)
+    if (p.lo1[i] != 0.f || p.hi1[i] != 1.f) return false;  // fractions live on [0, 1]
+  for (int i = 0; i < K + 2; i++)
+    if (!(p.hi1[i] >= p.lo1[i]) || !(p.pp1[i] >= 0.f)) return false;
+  for (int i = 0; i < 6; i++)
+    if (!(p.hi2[i] >= p.lo2[i]) || !(p.pp2[i] >= 0.f)) return false;
+  if (!(p.lo1[K + 1] > 0.f) || !(p.lo2[1] > 0.f) || !(p.lo2[3] > 0.f)) return false;  // T, sigma > 0
+  if (p.init_mode != FIRE_INIT_DEFAULT && p.init_mode != FIRE_INIT_GIVEN) return false;
+  return true;
+}
+
+template <class T>
+fire_status_t dev_alloc(T **p, size_t bytes) {
+  cudaError_t e = cudaMalloc((void **)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? FIRE_ERR_NOMEM : FIRE_ERR_CUDA;
+  }
+  return FIRE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fire_default_config(fire_config_t *c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->win1_lo = 350.f;   // Omega_1 (Sec. 2.6)
+  c->win1_hi = 2500.f;
+  c->win2h_lo = 900.f;  // Omega_2^hot, Omega_2^smol (Sec. 2.3)
+  c->win2h_hi = 1800.f;
+  c->win2s_lo = 1500.f;
+  c->win2s_hi = 2500.f;
+  c->max_it1 = 50;
+  c->max_it2 = 100;
+  c->tau0 = 1e-3f;
+  c->tol_g = 1e-6f;
+  c->tol_x = 1e-7f;
+  c->tol_f = 1e-10f;
+  c->kappa_max = 1e5f;
+  c->dfloor = 1e-12f;
+  c->noise_rel = 0.005f;
+  c->noise_abs = 1e-4f;
+  c->weighted = 0;
+  c->hfdi_thresh = -0.1f;  // Sec. 2.1
+  c->hfdi_lambda_hi = 2430.f;
+  c->hfdi_lambda_lo = 2061.f;
+  c->ident_sd_et = 100.f;
+  c->ident_alpha_snr = 3.f;
+}
+
+void fire_default_priors(fire_priors_t *p, int32_t K, int32_t nt, float tlo, float thi) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  if (K < 1 || K > FIRE_MAX_ENDM || nt < 2) return;
+  float dT = (thi - tlo) / (float)(nt - 1);
+  for (int k = 0; k < K; k++) {
+    p->lo1[k] = 0.f;
+    p->hi1[k] = 1.f;
+  }
+  p->lo1[K] = 0.f;      // alpha1
+  p->hi1[K] = 1.f;
+  p->lo1[K + 1] = tlo;  // T1 on the temperature grid
+  p->hi1[K + 1] = thi;
+  p->pm1[K] = -1.f;     // weak prior: alpha towards 0, T1 towards the grid centre
+  p->pp1[K] = 1.f;
+  p->pm1[K + 1] = 0.f;
+  p->pp1[K + 1] = 1.f;
+  const float lo2[6] = {900.f, dT, tlo, dT, 0.f, 0.f};
+  const float hi2[6] = {thi, 500.f, 1000.f, 500.f, 1.f, 1.f};
+  for (int i = 0; i < 6; i++) {
+    p->lo2[i] = lo2[i];
+    p->hi2[i] = hi2[i];
+    p->pm2[i] = i == 5 ? -1.f : 0.f;
+    p->pp2[i] = 1.f;
+  }
+  p->init_alpha1 = 0.01f;
+  p->init_T1 = 800.f;
+  p->init_sigma = 100.f;
+  p->init_mu_h_floor = 1000.f;
+  p->init_mu_s_ceil = 700.f;
+  p->init_eta_lo = 0.05f;
+  p->init_eta_hi = 0.95f;
+  p->init_mode = FIRE_INIT_DEFAULT;
+  p->init_state = nullptr;
+}
+
+const char *fire_status_str(fire_status_t s) {
+  switch (s) {
+    case FIRE_OK: return "ok";
+    case FIRE_ERR_ARG: return "invalid argument";
+    case FIRE_ERR_CUDA: return "CUDA error";
+    case FIRE_ERR_NOMEM: return "out of memory";
+    case FIRE_ERR_SHAPE: return "unsupported shape";
+    case FIRE_ERR_TIMEOUT: return "device wait timed out";
+    case FIRE_ERR_CHECKPOINT: return "bad checkpoint";
+    case FIRE_ERR_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+void fire_ctx_destroy(fire_ctx_t *ctx) {
+  if (!ctx) return;
+  cudaFree(ctx->d_image);
+  cudaFree(ctx->d_wvtab);
+  cudaFree(ctx->d_sat);
+  cudaFree(ctx->d_work);
+  cudaFree(ctx->d_err);
+  cudaFree(ctx->d_stage);
+  delete ctx;
+}
+
+fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const fire_config_t *cfg) {
+  if (!out) return FIRE_ERR_ARG;
+  *out = nullptr;
+  if (!tb || !tb->wavelength_nm || !tb->solar_irr || !tb->tau_down || !tb->tau_up ||
+      !tb->endmembers)
+    return FIRE_ERR_ARG;
+  const int nb = tb->n_bands, K = tb->n_endm, nt = tb->n_tgrid, nwv = tb->n_wv;
+  if (nb < 8 || nb > FIRE_MAX_BANDS || K < 1 || K > FIRE_MAX_ENDM || nt < 2 ||
+      nt > FIRE_MAX_TGRID || nwv < 1 || nwv > FIRE_MAX_WV)
+    return FIRE_ERR_SHAPE;
+  if (K != 3 && K != 5) return FIRE_ERR_SHAPE;  // compiled kernel variants
+  if (!(tb->tgrid_hi > tb->tgrid_lo) || !(tb->tgrid_lo > 0.f) || !(tb->cos_sza > 0.f))
+    return FIRE_ERR_ARG;
+  for (int b = 1; b < nb; b++)
+    if (!(tb->wavelength_nm[b] > tb->wavelength_nm[b - 1])) return FIRE_ERR_ARG;
+  fire_ctx *c = new (std::nothrow) fire_ctx();
+  if (!c) return FIRE_ERR_NOMEM;
+  if (cfg) c->cfg = *cfg;
+  else fire_default_config(&c->cfg);
+  cudaGetDevice(&c->device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+
+  KTables &t = c->t;
+  memset(&t, 0, sizeof(t));
+  t.nb = nb;
+  t.nwv = nwv;
+  t.K = K;
+  t.nt = nt;
+  t.tglo = tb->tgrid_lo;
+  t.tgstep = (tb->tgrid_hi - tb->tgrid_lo) / (float)(nt - 1);
+  const fire_config_t &cf = c->cfg;
+  band_range(tb->wavelength_nm, nb, cf.win1_lo, cf.win1_hi, cf.win1_lo, cf.win1_hi, &t.b1lo, &t.n1);
+  band_range(tb->wavelength_nm, nb, cf.win2h_lo, cf.win2h_hi, cf.win2s_lo, cf.win2s_hi, &t.b2lo,
+             &t.n2);
+  if (t.n1 < K + 3 || t.n2 < 7 || t.n1 > 512 || t.n2 > 512) {
+    delete c;
+    return FIRE_ERR_SHAPE;
+  }
+  t.bh = nearest_band(tb->wavelength_nm, nb, cf.hfdi_lambda_hi);
+  t.bl = nearest_band(tb->wavelength_nm, nb, cf.hfdi_lambda_lo);
+  ImageLayout &L = t.lay;
+  int o = 0;
+  auto take = [&](int n) { int r = o; o += (n + 3) & ~3; return r; };
+  L.off_c2l = take(nb);
+  L.off_c1l5 = take(nb);
+  L.off_endm = take(K * nb);
+  L.off_win1 = take(nb);
+  L.off_win2 = take(nb);
+  L.n2s = (t.n2 + 31) & ~31;
+  L.off_planck = take(nt * L.n2s);
+  L.total = o;
+  if (lm_smem_bytes(t) > 200 * 1024) {
+    delete c;
+    return FIRE_ERR_SHAPE;
+  }
+
+  // upload raw tables, build the device tables with a kernel
+  fire_status_t st = FIRE_OK;
+  float *raw = nullptr;
+  size_t nraw = (size_t)nb * 2 + (size_t)nwv * nb * 4 + (size_t)K * nb;
+  do {
+    if ((st = dev_alloc(&c->d_image, (size_t)L.total * 4)) != FIRE_OK) break;
+    if ((st = dev_alloc(&c->d_wvtab, (size_t)nwv * nb * sizeof(float4))) != FIRE_OK) break;
+    if ((st = dev_alloc(&c->d_work, (size_t)(1 + ST_COUNT) * 8)) != FIRE_OK) break;
+    if ((st = dev_alloc(&c->d_err, sizeof(int))) != FIRE_OK) break;
+    if ((st = dev_alloc(&raw, nraw * 4)) != FIRE_OK) break;
+    if (tb->sat_level) {
+      if ((st = dev_alloc(&c->d_sat, (size_t)nb * 4)) != FIRE_OK) break;
+      if ((st = cuda_status(cudaMemcpy(c->d_sat, tb->sat_level, nb * 4, cudaMemcpyHostToDevice))) != FIRE_OK) break;
+    }
+    float *d_wl = raw, *d_e0 = raw + nb, *d_td = d_e0 + nb, *d_tu = d_td + (size_t)nwv * nb;
+    float *d_ra = d_tu + (size_t)nwv * nb, *d_sa = d_ra + (size_t)nwv * nb;
+    float *d_en = d_sa + (size_t)nwv * nb;
+    size_t wb = (size_t)nwv * nb * 4;
+    cudaMemcpy(d_wl, tb->wavelength_nm, nb * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_e0, tb->solar_irr, nb * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_td, tb->tau_down, wb, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_tu, tb->tau_up, wb, cudaMemcpyHostToDevice);
+    if (tb->rho_atm) cudaMemcpy(d_ra, tb->rho_atm, wb, cudaMemcpyHostToDevice);
+    else cudaMemset(d_ra, 0, wb);
+    if (tb->sph_alb) cudaMemcpy(d_sa, tb->sph_alb, wb, cudaMemcpyHostToDevice);
+    else cudaMemset(d_sa, 0, wb);
+    cudaMemcpy(d_en, tb->endmembers, (size_t)K * nb * 4, cudaMemcpyHostToDevice);
+    t.image = c->d_image;
+    t.wvtab = c->d_wvtab;
+    t.sat = c->d_sat;
+    const float win[6] = {cf.win1_lo, cf.win1_hi, cf.win2h_lo, cf.win2h_hi, cf.win2s_lo, cf.win2s_hi};
+    if ((st = cuda_status(launch_build_tables(t, d_wl, d_e0, tb->cos_sza, d_td, d_tu, d_ra, d_sa,
+                                              d_en, c->d_image, c->d_wvtab, win, 0))) != FIRE_OK)
+      break;
+    st = cuda_status(cudaDeviceSynchronize());
+  } while (0);
+  if (raw) cudaFree(raw);
+  if (st != FIRE_OK) {
+    fire_ctx_destroy(c);
+    return st;
+  }
+  *out = c;
+  return FIRE_OK;
+}
+
+fire_status_t fire_window_bands(fire_ctx_t *c, int32_t *b1lo, int32_t *n1, int32_t *b2lo,
+                                int32_t *n2) {
+  if (!c) return FIRE_ERR_ARG;
+  if (b1lo) *b1lo = c->t.b1lo;
+  if (n1) *n1 = c->t.n1;
+  if (b2lo) *b2lo = c->t.b2lo;
+  if (n2) *n2 = c->t.n2;
+  return FIRE_OK;
+}
+
+fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_priors_t *pri,
+                            const fire_outputs_t *out, fire_stream_t stream) {
+  if (!c || !sc || !out) return FIRE_ERR_ARG;
+  if (sc->n_pix < 0) return FIRE_ERR_ARG;
+  if (sc->mem != FIRE_MEM_DEVICE && sc->mem != FIRE_MEM_HOST) return FIRE_ERR_ARG;
+  if (sc->gate_mode != FIRE_FIT_ALL && sc->gate_mode != FIRE_FIT_HFDI) return FIRE_ERR_ARG;
+  fire_priors_t pd;
+  if (!pri) {
+    fire_default_priors(&pd, c->t.K, c->t.nt, c->t.tglo, c->t.tglo + c->t.tgstep * (c->t.nt - 1));
+    pri = &pd;
+  }
+  if (!priors_valid(*pri, c->t.K)) return FIRE_ERR_ARG;
+  if (pri->init_mode == FIRE_INIT_GIVEN && !pri->init_state) return FIRE_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(c->d_work, 0, (size_t)(1 + ST_COUNT) * 8, st));
+  c->last_launches = 0;
+  if (sc->n_pix == 0) return FIRE_OK;
+  if (!sc->radiance || !sc->wv_bin) return FIRE_ERR_ARG;
+  const int64_t n = sc->n_pix;
+  const int K = c->t.K, NS = K + 8;
+
+  LMLaunch p;
+  memset(&p, 0, sizeof(p));
+  p.t = c->t;
+  fill_kconfig(p.c, c->cfg, *pri, K);
+  p.s.n_pix = n;
+  p.s.gate = sc->gate_mode == FIRE_FIT_HFDI;
+  p.w.counter = c->d_work;
+  p.w.stats = c->d_work + 1;
+  p.w.err = c->d_err;
+
+  // per-pixel output sizes (bytes), in the order staged for host scenes
+  const size_t szf = (size_t)n * 4;
+  const size_t s_state = szf * NS, s_cov = szf * 21, s_u8 = (size_t)n, s_it = (size_t)n * 4;
+  if (sc->mem == FIRE_MEM_DEVICE) {
+    p.s.rad = sc->radiance;
+    p.s.wv = sc->wv_bin;
+    p.s.init = pri->init_mode == FIRE_INIT_GIVEN ? pri->init_state : nullptr;
+    p.o.state = out->state;
+    p.o.ET = out->ET;
+    p.o.sdT = out->sdT;
+    p.o.alpha = out->alpha;
+    p.o.cov = out->cov;
+    p.o.var_ET = out->var_ET;
+    p.o.cost = out->cost;
+    p.o.rms = out->rms;
+    p.o.hfdi = out->hfdi;
+    p.o.status = out->status;
+    p.o.iters = out->iters;
+    int blocks = 0;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    CK(launch_lm(p, c->num_sms, st, &blocks));
+    c->last_launches = 1;
+    return FIRE_OK;
+  }
+
+  // host scene: stage inputs and outputs through one device buffer
+  const size_t s_rad = (size_t)n * c->t.nb * 4, s_wv = (size_t)n * 2;
+  const size_t s_init = pri->init_mode == FIRE_INIT_GIVEN ? szf * NS : 0;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  size_t need = al(s_rad) + al(s_wv) + al(s_init) + al(s_state) + 7 * al(szf) + al(s_cov) +
+                al(s_u8) + al(s_it);
+  if (need > c->stage_bytes) {
+    cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_bytes = 0;
+    fire_status_t e = dev_alloc((char **)&c->d_stage, need);
+    if (e != FIRE_OK) return e;
+    c->stage_bytes = need;
+  }
+  char *q = (char *)c->d_stage;
+  auto carve = [&](size_t b) { char *r = q; q += al(b); return r; };
+  float *d_rad = (float *)carve(s_rad);
+  uint16_t *d_wv = (uint16_t *)carve(s_wv);
+  float *d_init = s_init ? (float *)carve(s_init) : nullptr;
+  float *o_state = (float *)carve(s_state), *o_ET = (float *)carve(szf), *o_sdT = (float *)carve(szf);
+  float *o_alpha = (float *)carve(szf), *o_var = (float *)carve(szf), *o_cost = (float *)carve(szf);
+  float *o_rms = (float *)carve(szf), *o_hfdi = (float *)carve(szf), *o_cov = (float *)carve(s_cov);
+  uint8_t *o_status = (uint8_t *)carve(s_u8);
+  uint16_t *o_it = (uint16_t *)carve(s_it);
+  CK(cudaMemcpyAsync(d_rad, sc->radiance, s_rad, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_wv, sc->wv_bin, s_wv, cudaMemcpyHostToDevice, st));
+  if (d_init) CK(cudaMemcpyAsync(d_init, pri->init_state, s_init, cudaMemcpyHostToDevice, st));
+  p.s.rad = d_rad;
+  p.s.wv = d_wv;
+  p.s.init = d_init;
+  p.o.state = out->state ? o_state : nullptr;
+  p.o.ET = out->ET ? o_ET : nullptr;
+  p.o.sdT = out->sdT ? o_sdT : nullptr;
+  p.o.alpha = out->alpha ? o_alpha : nullptr;
+  p.o.var_ET = out->var_ET ? o_var : nullptr;
+  p.o.cost = out->cost ? o_cost : nullptr;
+  p.o.rms = out->rms ? o_rms : nullptr;
+  p.o.hfdi = out->hfdi ? o_hfdi : nullptr;
+  p.o.cov = out->cov ? o_cov : nullptr;
+  p.o.status = out->status ? o_status : nullptr;
+  p.o.iters = out->iters ? o_it : nullptr;
+  int blocks = 0;
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+  CK(launch_lm(p, c->num_sms, st, &blocks));
+  c->last_launches = 1;
+  struct { void *h; void *d; size_t b; } back[] = {
+      {out->state, o_state, s_state}, {out->ET, o_ET, szf}, {out->sdT, o_sdT, szf},
+      {out->alpha, o_alpha, szf}, {out->var_ET, o_var, szf}, {out->cost, o_cost, szf},
+      {out->rms, o_rms, szf}, {out->hfdi, o_hfdi, szf}, {out->cov, o_cov, s_cov},
+      {out->status, o_status, s_u8}, {out->iters, o_it, s_it}};
+  for (auto &b : back)
+    if (b.h) CK(cudaMemcpyAsync(b.h, b.d, b.b, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int err = 0;
+  CK(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  return err ? FIRE_ERR_TIMEOUT : FIRE_OK;
+}
+
+fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
+  if (!c || !s) return FIRE_ERR_ARG;
+  unsigned long long h[1 + ST_COUNT];
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(h, c->d_work, sizeof(h), cudaMemcpyDeviceToHost));
+  int err = 0;
+  CK(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  memset(s, 0, sizeof(*s));
+  const unsigned long long *v = h + 1;
+  s->n_pixels = v[ST_NPIX];
+  s->sum_it1 = v[ST_IT1];
+  s->sum_it2 = v[ST_IT2];
+  s->n_fp64_pixels = v[ST_FP64];
+  s->band_evals1 = v[ST_BAND1];
+  s->band_evals2 = v[ST_BAND2];
+  s->node_band_evals2 = v[ST_NODEBAND2];
+  for (int k = 0; k < 8; k++) s->status_counts[k] = v[ST_STATUS0 + k];
+  // algorithmic flops (FMA = 2): stage 1 per band and evaluation, stage 2 per
+  // band and evaluation plus 6 FMA per band and active grid node
+  const int K = c->t.K, P1 = K + 1;
+  const double f1 = 4.0 * K + 27.0 + 2.0 * P1 * (P1 + 1) / 2.0 + 3.0 * P1 + 4.0;
+  const double f2 = 30.0 + 2.0 * 21.0 + 3.0 * 6.0 + 4.0;
+  s->flops = f1 * (double)s->band_evals1 + f2 * (double)s->band_evals2 +
+             12.0 * (double)s->node_band_evals2;
+  s->kernel_launches = c->last_launches;
+  return err ? FIRE_ERR_TIMEOUT : FIRE_OK;
+}
+
+fire_status_t fire_forward(fire_ctx_t *c, int32_t mode, const float *state, const uint16_t *wv,
+                           int64_t n, float nrel, float nabs, uint64_t seed, uint64_t sid,
+                           int64_t pix0, float *L_out, fire_stream_t stream) {
+  if (!c) return FIRE_ERR_ARG;
+  if (mode != 1 && mode != 2) return FIRE_ERR_ARG;
+  if (n < 0 || !(nrel >= 0.f) || !(nabs >= 0.f)) return FIRE_ERR_ARG;
+  if (n == 0) return FIRE_OK;
+  if (!state || !wv || !L_out) return FIRE_ERR_ARG;
+  return cuda_status(launch_forward(c->t, mode, state, wv, n, nrel, nabs, seed, sid, pix0, L_out,
+                                    (cudaStream_t)stream));
+}
+
+fire_status_t fire_block_mean(const float *src, int32_t w, int32_t h, int32_t nb, int32_t blk,
+                              float *dst, fire_stream_t stream) {
+  if (!src || !dst || w < 0 || h < 0 || nb < 1 || blk < 1) return FIRE_ERR_ARG;
+  return cuda_status(launch_block_mean(src, w, h, nb, blk, dst, (cudaStream_t)stream));
+}
+
+}  // extern "C"

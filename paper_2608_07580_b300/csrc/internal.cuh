@@ -1,0 +1,106 @@
+// internal.cuh — device-side data structures shared by the kernels and the
+// C-ABI implementation of the per-pixel wildfire-temperature retrieval.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace firert {
+
+constexpr int kWarp = 32;
+constexpr int kMaxK = 8;
+constexpr int kMaxTgrid = 128;
+constexpr int kScratchPerNode = 8;   // floats per grid node in the warp scratch
+
+// per-pixel status codes (mirrors the header)
+enum : int {
+  PX_CONVERGED = 0, PX_MAXITER = 1, PX_NONFINITE = 2, PX_ALL_MASKED = 3, PX_CHOL_FAIL = 4,
+  PX_NOT_CANDIDATE = 5, PX_F_FP64 = 8, PX_F_NOT_IDENT = 16, PX_F_MLP_FALLBACK = 32,
+  PX_F_S1_MAXITER = 64
+};
+
+// Layout of the per-CTA shared-memory table image (floats). The image is
+// built once per context in global memory and bulk-copied into every CTA.
+struct ImageLayout {
+  int off_c2l;     // [nb]  c2 / lambda_b (K): Planck exponent numerator
+  int off_c1l5;    // [nb]  c1 lambda_b^-5 (W m^-2 sr^-1 nm^-1)
+  int off_endm;    // [K][nb] endmember reflectances
+  int off_win1;    // [nb]  1 if band in Omega_1 else 0
+  int off_win2;    // [nb]  1 if band in Omega_2^hot U Omega_2^smol else 0
+  int off_planck;  // [nt][n2s] B(lambda_b, T_j) for b in the stage-2 range
+  int n2s;         // stage-2 range padded to a multiple of 32
+  int total;       // floats, multiple of 4 (16-byte bulk copies)
+};
+
+struct KTables {
+  int nb, nwv, K, nt;
+  int b1lo, n1;            // stage-1 band range [b1lo, b1lo + n1)
+  int b2lo, n2;            // stage-2 band range [b2lo, b2lo + n2)
+  int bh, bl;              // HFDI band indices (2430 nm, 2061 nm)
+  float tglo, tgstep;      // temperature grid T_j = tglo + j * tgstep
+  const float4 *wvtab;     // [nwv][nb] (A tau_d tau_u, A rho_atm, S, tau_u), A = E0 cos/pi
+  const float *sat;        // [nb] or nullptr
+  const float *image;      // per-CTA table image in global memory
+  ImageLayout lay;
+};
+
+struct KConfig {
+  float lo1[kMaxK + 2], hi1[kMaxK + 2], pm1[kMaxK + 2], pp1[kMaxK + 2];
+  float lo2[6], hi2[6], pm2[6], pp2[6];
+  float init_alpha1, init_T1, init_sigma, init_mu_h_floor, init_mu_s_ceil;
+  float init_eta_lo, init_eta_hi;
+  int max_it1, max_it2;
+  float tau0, tol_g, tol_x, tol_f, kappa_max, dfloor;
+  float noise_rel, noise_abs;
+  int weighted;
+  float hfdi_thresh;
+  float ident_sd_et, ident_alpha_snr;
+};
+
+struct KScene {
+  int64_t n_pix;
+  const float *rad;        // [n_pix][nb]
+  const uint16_t *wv;      // [n_pix]
+  const float *init;       // [n_pix][K+8] or nullptr
+  int gate;                // 1: HFDI gate
+};
+
+struct KOut {
+  float *state, *ET, *sdT, *alpha, *cov, *var_ET, *cost, *rms, *hfdi;
+  uint8_t *status;
+  uint16_t *iters;
+};
+
+// device counters, indices into KWork::stats
+enum : int {
+  ST_NPIX = 0, ST_IT1, ST_IT2, ST_FP64, ST_BAND1, ST_BAND2, ST_NODEBAND2, ST_STATUS0,
+  ST_COUNT = ST_STATUS0 + 8
+};
+
+struct KWork {
+  unsigned long long *counter;  // work-claim counter (zeroed before launch)
+  unsigned long long *stats;    // [ST_COUNT]
+  int *err;                     // bounded-wait failure flag
+};
+
+struct LMLaunch {
+  KTables t;
+  KConfig c;
+  KScene s;
+  KOut o;
+  KWork w;
+};
+
+// host-side launchers (kernels_*.cu)
+cudaError_t launch_build_tables(const KTables &t, const float *wl, const float *e0, float cos_sza,
+                                const float *td, const float *tu, const float *ra, const float *sa,
+                                const float *endm, float *image, float4 *wvtab,
+                                const float win[6], cudaStream_t st);
+cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used);
+size_t lm_smem_bytes(const KTables &t);
+cudaError_t launch_forward(const KTables &t, int mode, const float *state, const uint16_t *wv,
+                           int64_t n, float noise_rel, float noise_abs, uint64_t seed,
+                           uint64_t stream_id, int64_t pix0, float *out, cudaStream_t st);
+cudaError_t launch_block_mean(const float *src, int w, int h, int nb, int blk, float *dst,
+                              cudaStream_t st);
+
+}  // namespace firert

@@ -1,0 +1,1075 @@
+// kernels_lm.cu — the per-pixel two-stage retrieval on sm_103a.
+//
+// One warp per pixel, persistent CTAs claiming pixels from a global counter.
+// Lanes own bands (lane + 32 i within each stage's window), so radiance and
+// the shared Planck table are read band-coalesced; the normal equations
+// J^T W J, J^T W r and the cost are reduced with warp shuffles, and every
+// lane then runs the same small solve on registers (uniform control flow).
+//
+// Stage 1 (Sec. 2.6): x1 = [x_surf(K), alpha1, T1] over Omega_1 with the
+// single-temperature Planck term computed on the SFU in the overflow-safe
+// form e^-x / (1 - e^-x). Stage 2: x2 = [mu_h, s_h, mu_s, s_s, eta, alpha]
+// over Omega_2 with the solar term fixed; the thermal term sums the Planck
+// grid (staged per CTA in shared memory by bulk copy) against normalised
+// Gaussian weights (Eq. thermal), and its Jacobian uses the weight moments
+// sum w (d - dbar) B and sum w (d^2 - m2) B.
+//
+// The iteration is Levenberg-Marquardt in the z coordinates of Eq. (affine):
+// Nielsen's damping update, a projected-Newton step (a variable whose step
+// leaves its bound is pinned there and the rest re-solved), the surface
+// fractions moved in the basis e_k - e_m (m = largest fraction) and then
+// projected onto the simplex (Sec. 2.6). Steps are solved in FP32 on the
+// diagonally scaled damped matrix; an ill-conditioned one (condition
+// estimate above kappa_max, or a failed pivot) is re-solved in FP64. The
+// final Laplace covariance is FP64.
+#include <float.h>
+
+#include "internal.cuh"
+
+namespace firert {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kClaim = 4;          // pixels claimed per atomic
+#ifndef LM_MINB
+#define LM_MINB 1
+#endif
+
+template <int N>
+__device__ __forceinline__ void warp_sum(float (&v)[N]) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] += __shfl_xor_sync(kFull, v[i], o);
+}
+
+__device__ __forceinline__ float warp_sum1(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <int I>
+struct IC { static constexpr int value = I; };
+template <int N, int I = 0, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+  if constexpr (I < N) {
+    f(IC<I>{});
+    static_for<N, I + 1>(f);
+  }
+}
+
+// packed upper-triangular index of (a, b), a <= b, for a P x P matrix
+template <int P>
+__device__ __forceinline__ constexpr int up(int a, int b) {
+  return a <= b ? a * P - (a * (a - 1)) / 2 + (b - a) : b * P - (b * (b - 1)) / 2 + (a - b);
+}
+
+// ------------------------------------------------------------- solve ----
+// Solve (H + lam D) d = rhs over the free variables on the diagonally scaled
+// matrix; pinned variables are identity rows with their displacement moved
+// to the right-hand side. Returns false on a non-positive pivot. kap is the
+// condition estimate (max L_ii / min L_ii)^2 over the free variables.
+template <int P, typename T>
+__device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
+                                             const float (&g)[P], float lam,
+                                             const float (&D)[P], const bool (&pin)[P],
+                                             float (&dr)[P], float &kap) {
+  T A[P * (P + 1) / 2];  // packed lower: (i, j), j <= i at i (i+1) / 2 + j
+  T y[P], d[P];
+#pragma unroll
+  for (int i = 0; i < P; i++) {
+    T r = pin[i] ? T(0) : (T)g[i];
+#pragma unroll
+    for (int j = 0; j < P; j++)
+      if (pin[j] && !pin[i]) r -= (T)H[up<P>(i, j)] * (T)dr[j];
+    y[i] = r;
+#pragma unroll
+    for (int j = 0; j <= i; j++) {
+      T m;
+      if (!pin[i] && !pin[j]) m = (T)H[up<P>(i, j)];
+      else m = (i == j) ? T(1) : T(0);
+      if (i == j && !pin[i]) m += (T)lam * (T)D[i];
+      A[i * (i + 1) / 2 + j] = m;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < P; i++) d[i] = sqrt(A[i * (i + 1) / 2 + i]);
+#pragma unroll
+  for (int i = 0; i < P; i++) {
+    y[i] /= d[i];
+#pragma unroll
+    for (int j = 0; j <= i; j++) A[i * (i + 1) / 2 + j] /= (d[i] * d[j]);
+  }
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < P; j++) {
+    T s = A[j * (j + 1) / 2 + j];
+#pragma unroll
+    for (int k = 0; k < j; k++) s -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+    ok = ok && (s > T(0));
+    T L = sqrt(s > T(0) ? s : T(1));
+    A[j * (j + 1) / 2 + j] = L;
+#pragma unroll
+    for (int i = j + 1; i < P; i++) {
+      T t = A[i * (i + 1) / 2 + j];
+#pragma unroll
+      for (int k = 0; k < j; k++) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+      A[i * (i + 1) / 2 + j] = t / L;
+    }
+  }
+  if (!ok) return false;
+  T lmax = T(0), lmin = T(1e30);
+#pragma unroll
+  for (int i = 0; i < P; i++)
+    if (!pin[i]) {
+      T l = A[i * (i + 1) / 2 + i];
+      lmax = l > lmax ? l : lmax;
+      lmin = l < lmin ? l : lmin;
+    }
+  kap = lmax > T(0) ? (float)((lmax / lmin) * (lmax / lmin)) : 1.f;
+#pragma unroll
+  for (int i = 0; i < P; i++) {
+    T s = y[i];
+#pragma unroll
+    for (int k = 0; k < i; k++) s -= A[i * (i + 1) / 2 + k] * y[k];
+    y[i] = s / A[i * (i + 1) / 2 + i];
+  }
+#pragma unroll
+  for (int i = P - 1; i >= 0; i--) {
+    T s = y[i];
+#pragma unroll
+    for (int k = i + 1; k < P; k++) s -= A[k * (k + 1) / 2 + i] * y[k];
+    y[i] = s / A[i * (i + 1) / 2 + i];
+  }
+#pragma unroll
+  for (int i = 0; i < P; i++)
+    if (!pin[i]) dr[i] = (float)(y[i] / d[i]);
+  return true;
+}
+
+// ------------------------------------------------------- pixel context --
+struct PixCtx {
+  const KTables *t;
+  const KConfig *c;
+  const float *img;       // shared-memory table image
+  float *wsc;             // this warp's node scratch [nt][8]
+  const float4 *wvrow;    // this pixel's water-vapour row of the atmosphere table
+  int lane;
+  int node_evals;         // sum over stage-2 evaluations of active nodes
+};
+
+// ------------------------------------------------------------ stage 1 ---
+template <int K, int S1>
+struct Stage1 {
+  static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2;
+  float Lobs[S1], w[S1];
+  float psc;
+  float sf, sa, sT;
+
+  // reduced variable a: fractions k != m in order, then alpha1, T1. These
+  // accessors select with compile-time indices (no local-memory indexing).
+  template <int A>
+  __device__ __forceinline__ static float rsel(const float (&v)[NX], int m) {
+    if constexpr (A >= K - 1) return v[A + 1];
+    else return A < m ? v[A] : v[A + 1];
+  }
+  template <int A>
+  __device__ __forceinline__ float lo_r(const KConfig &c, int m) const {
+    if constexpr (A >= K - 1) return c.lo1[A + 1];
+    else return A < m ? c.lo1[A] : c.lo1[A + 1];
+  }
+  template <int A>
+  __device__ __forceinline__ float hi_r(const KConfig &c, int m) const {
+    if constexpr (A >= K - 1) return c.hi1[A + 1];
+    else return A < m ? c.hi1[A] : c.hi1[A + 1];
+  }
+  template <int A>
+  __device__ __forceinline__ float sc_r(const KConfig &c, int m) const {
+    return 0.5f * (hi_r<A>(c, m) - lo_r<A>(c, m));
+  }
+  template <int A>
+  __device__ __forceinline__ static constexpr bool has_upper() { return A >= K - 1; }
+  __device__ __forceinline__ float scale(const KConfig &c, int i) const {
+    return 0.5f * (c.hi1[i] - c.lo1[i]);
+  }
+
+  __device__ __forceinline__ static int argmax_frac(const float (&x)[NX]) {
+    int m = 0;
+    float best = x[0];
+#pragma unroll
+    for (int k = 1; k < K; k++)
+      if (x[k] > best) { m = k; best = x[k]; }
+    return m;
+  }
+
+  // model, reduced Jacobian, normal equations and cost at x (all lanes get
+  // the warp totals). cd = unweighted data cost.
+  __device__ __forceinline__ void eval(PixCtx &pc, const float (&x)[NX], float (&H)[NH],
+                                       float (&g)[P], float &cst, float &cd, int &m) const {
+    const KTables &t = *pc.t;
+    const KConfig &c = *pc.c;
+    m = argmax_frac(x);
+    float acc[NH + P + 2];
+#pragma unroll
+    for (int i = 0; i < NH + P + 2; i++) acc[i] = 0.f;
+    const float a1 = x[K], invT = 1.f / x[K + 1];
+#pragma unroll
+    for (int s = 0; s < S1; s++) {
+      int bi = pc.lane + 32 * s;
+      if (bi < t.n1 && w[s] > 0.f) {
+        int b = t.b1lo + bi;
+        float4 q = __ldg(pc.wvrow + b);
+        float E[K];
+        float rho = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          E[k] = pc.img[t.lay.off_endm + k * t.nb + b];
+          rho = fmaf(x[k], E[k], rho);
+        }
+        float inv = __frcp_rn(1.f - q.z * rho);
+        float Ls = fmaf(q.x * rho, inv, q.y);
+        float xx = pc.img[t.lay.off_c2l + b] * invT;
+        float e = __expf(-xx);
+        float rom = __frcp_rn(1.f - e);
+        float B = pc.img[t.lay.off_c1l5 + b] * e * rom;
+        float dB = B * xx * invT * rom;
+        float r = Lobs[s] - fmaf(a1 * q.w, B, Ls);
+        float dL[K], dEm = 0.f;
+        const float qi2 = q.x * inv * inv * sf;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          dL[k] = qi2 * E[k];
+          dEm = (k == m) ? dL[k] : dEm;
+        }
+        float J[P];
+#pragma unroll
+        for (int a = 0; a < K - 1; a++) J[a] = (a < m ? dL[a] : dL[a + 1]) - dEm;
+        J[K - 1] = q.w * B * sa;
+        J[K] = a1 * q.w * dB * sT;
+        float wr = w[s] * r;
+        acc[NH + P] = fmaf(wr, r, acc[NH + P]);
+        acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
+#pragma unroll
+        for (int a = 0; a < P; a++) {
+          acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
+          float wj = w[s] * J[a];
+#pragma unroll
+          for (int bb = a; bb < P; bb++) acc[up<P>(a, bb)] = fmaf(wj, J[bb], acc[up<P>(a, bb)]);
+        }
+      }
+    }
+    warp_sum(acc);
+#pragma unroll
+    for (int i = 0; i < NH; i++) H[i] = acc[i];
+#pragma unroll
+    for (int a = 0; a < P; a++) g[a] = acc[NH + a];
+    cd = acc[NH + P + 1];
+    cst = acc[NH + P];
+    // weak Gaussian prior in z, pulled into the reduced basis (e_k - e_m)
+    float zr[NX], ppm = 0.f, rm = 0.f;
+#pragma unroll
+    for (int i = 0; i < NX; i++) {
+      zr[i] = c.hi1[i] > c.lo1[i] ? 2.f * (x[i] - c.lo1[i]) / (c.hi1[i] - c.lo1[i]) - 1.f : 0.f;
+      zr[i] -= c.pm1[i];
+      float ppi = psc * c.pp1[i];
+      cst += ppi * zr[i] * zr[i];
+      if (i < K && i == m) { ppm = ppi; rm = zr[i]; }
+    }
+#pragma unroll
+    for (int a = 0; a < K - 1; a++) {
+      float ppa = psc * (a < m ? c.pp1[a] : c.pp1[a + 1]);
+      float ra = a < m ? zr[a] : zr[a + 1];
+      g[a] -= ppa * ra - ppm * rm;
+      H[up<P>(a, a)] += ppa + ppm;
+#pragma unroll
+      for (int bb = a + 1; bb < K - 1; bb++) H[up<P>(a, bb)] += ppm;
+    }
+#pragma unroll
+    for (int a = K - 1; a < P; a++) {
+      g[a] -= psc * c.pp1[a + 1] * zr[a + 1];
+      H[up<P>(a, a)] += psc * c.pp1[a + 1];
+    }
+  }
+
+  // x + step (z units, reduced basis) -> projected trial point
+  __device__ __forceinline__ void apply(const KConfig &c, const float (&x)[NX], const float (&dr)[P],
+                                        int m, float (&xt)[NX]) const {
+    float sum = 0.f;
+#pragma unroll
+    for (int a = 0; a < K - 1; a++) sum += dr[a];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      float d = 0.f;
+      if (k < K - 1 && k < m) d = dr[k < K - 1 ? k : 0];
+      if (k > 0 && k > m) d = dr[k > 0 ? k - 1 : 0];
+      xt[k] = (k == m) ? x[k] - sf * sum : x[k] + sf * d;
+    }
+#pragma unroll
+    for (int i = K; i < K + 2; i++) {
+      float v = x[i] + scale(c, i) * dr[i - 1];
+      xt[i] = fminf(fmaxf(v, c.lo1[i]), c.hi1[i]);
+    }
+    simplex_project(xt);
+  }
+
+  // Euclidean projection of the fractions onto the unit simplex (sort-based)
+  __device__ __forceinline__ static void simplex_project(float (&x)[NX]) {
+    float u[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) u[k] = x[k];
+#pragma unroll
+    for (int i = 1; i < K; i++)
+#pragma unroll
+      for (int j = i; j > 0; j--)
+        if (u[j] > u[j - 1]) {
+          float tmp = u[j];
+          u[j] = u[j - 1];
+          u[j - 1] = tmp;
+        }
+    float cs = 0.f, theta = 0.f;
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+      cs += u[j];
+      float th = (cs - 1.f) / (float)(j + 1);
+      if (u[j] - th > 0.f) theta = th;
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) x[k] = fmaxf(x[k] - theta, 0.f);
+  }
+
+};
+
+// ------------------------------------------------------------ stage 2 ---
+template <int S2>
+struct Stage2 {
+  static constexpr int P = 6, NX = 6, NH = 21;
+  float y[S2], tu[S2], w[S2];
+  float psc;
+  float s[6];
+
+  template <int A>
+  __device__ __forceinline__ static float rsel(const float (&v)[NX], int) { return v[A]; }
+  template <int A>
+  __device__ __forceinline__ float lo_r(const KConfig &c, int) const { return c.lo2[A]; }
+  template <int A>
+  __device__ __forceinline__ float hi_r(const KConfig &c, int) const { return c.hi2[A]; }
+  template <int A>
+  __device__ __forceinline__ float sc_r(const KConfig &c, int) const { return s[A]; }
+  template <int A>
+  __device__ __forceinline__ static constexpr bool has_upper() { return true; }
+  __device__ __forceinline__ float scale(const KConfig &c, int i) const {
+    return 0.5f * (c.hi2[i] - c.lo2[i]);
+  }
+
+  __device__ __forceinline__ void eval(PixCtx &pc, const float (&x)[NX], float (&H)[NH],
+                                       float (&g)[P], float &cst, float &cd, int &m) const {
+    const KTables &t = *pc.t;
+    const KConfig &c = *pc.c;
+    m = 0;
+    const float mh = x[0], sh = x[1], ms = x[2], ss = x[3], eta = x[4], al = x[5];
+    // grid weights of the two components: lanes own nodes j = lane + 32 q
+    float uh[4], us[4], dh[4], ds[4];
+    float mom[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float ih = 0.5f / (sh * sh), is = 0.5f / (ss * ss);
+    unsigned act[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int j = pc.lane + 32 * q;
+      uh[q] = us[q] = dh[q] = ds[q] = 0.f;
+      if (j < t.nt) {
+        float T = t.tglo + (float)j * t.tgstep;
+        dh[q] = T - mh;
+        ds[q] = T - ms;
+        uh[q] = __expf(-dh[q] * dh[q] * ih);
+        us[q] = __expf(-ds[q] * ds[q] * is);
+      }
+      mom[0] += uh[q];
+      mom[1] += uh[q] * dh[q];
+      mom[2] += uh[q] * dh[q] * dh[q];
+      mom[3] += us[q];
+      mom[4] += us[q] * ds[q];
+      mom[5] += us[q] * ds[q] * ds[q];
+      act[q] = __ballot_sync(kFull, uh[q] > 1e-30f || us[q] > 1e-30f);
+    }
+    warp_sum(mom);
+    const float rUh = 1.f / mom[0], rUs = 1.f / mom[3];
+    const float dbh = mom[1] * rUh, m2h = mom[2] * rUh, dbs = mom[4] * rUs, m2s = mom[5] * rUs;
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int j = pc.lane + 32 * q;
+      if (j < t.nt) {
+        float wh = uh[q] * rUh, ws = us[q] * rUs;
+        float4 A = make_float4(wh, wh * (dh[q] - dbh), wh * (dh[q] * dh[q] - m2h), ws);
+        float4 B = make_float4(ws * (ds[q] - dbs), ws * (ds[q] * ds[q] - m2s), 0.f, 0.f);
+        reinterpret_cast<float4 *>(pc.wsc)[2 * j] = A;
+        reinterpret_cast<float4 *>(pc.wsc)[2 * j + 1] = B;
+      }
+    }
+    int jlo = t.nt, jhi = -1;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      if (act[q]) {
+        jlo = min(jlo, 32 * q + __ffs(act[q]) - 1);
+        jhi = max(jhi, 32 * q + 31 - __clz(act[q]));
+      }
+    __syncwarp();
+    // moment sums over the active nodes: 6 FMA per band and node
+    float S[S2][6];
+#pragma unroll
+    for (int s2 = 0; s2 < S2; s2++)
+#pragma unroll
+      for (int k = 0; k < 6; k++) S[s2][k] = 0.f;
+    const float *pl = pc.img + t.lay.off_planck + pc.lane;
+    const float4 *wv4 = reinterpret_cast<const float4 *>(pc.wsc);
+    for (int j = jlo; j <= jhi; j++) {
+      float4 A = wv4[2 * j], B = wv4[2 * j + 1];
+      const float *row = pl + j * t.lay.n2s;
+#pragma unroll
+      for (int s2 = 0; s2 < S2; s2++) {
+        float Bv = row[32 * s2];
+        S[s2][0] = fmaf(A.x, Bv, S[s2][0]);
+        S[s2][1] = fmaf(A.y, Bv, S[s2][1]);
+        S[s2][2] = fmaf(A.z, Bv, S[s2][2]);
+        S[s2][3] = fmaf(A.w, Bv, S[s2][3]);
+        S[s2][4] = fmaf(B.x, Bv, S[s2][4]);
+        S[s2][5] = fmaf(B.y, Bv, S[s2][5]);
+      }
+    }
+    pc.node_evals += (jhi >= jlo) ? (jhi - jlo + 1) : 0;
+    float acc[NH + P + 2];
+#pragma unroll
+    for (int i = 0; i < NH + P + 2; i++) acc[i] = 0.f;
+    const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
+    const float ish3 = ish2 / sh, iss3 = iss2 / ss;
+#pragma unroll
+    for (int s2 = 0; s2 < S2; s2++) {
+      if (w[s2] > 0.f) {
+        float Bh = S[s2][0], Bs = S[s2][3];
+        float Bm = eta * Bh + (1.f - eta) * Bs;
+        float atu = al * tu[s2];
+        float r = y[s2] - atu * Bm;
+        float J[6];
+        J[0] = atu * eta * S[s2][1] * ish2 * s[0];
+        J[1] = atu * eta * S[s2][2] * ish3 * s[1];
+        J[2] = atu * (1.f - eta) * S[s2][4] * iss2 * s[2];
+        J[3] = atu * (1.f - eta) * S[s2][5] * iss3 * s[3];
+        J[4] = atu * (Bh - Bs) * s[4];
+        J[5] = tu[s2] * Bm * s[5];
+        float wr = w[s2] * r;
+        acc[NH + P] = fmaf(wr, r, acc[NH + P]);
+        acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
+#pragma unroll
+        for (int a = 0; a < P; a++) {
+          acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
+          float wj = w[s2] * J[a];
+#pragma unroll
+          for (int bb = a; bb < P; bb++) acc[up<P>(a, bb)] = fmaf(wj, J[bb], acc[up<P>(a, bb)]);
+        }
+      }
+    }
+    warp_sum(acc);
+#pragma unroll
+    for (int i = 0; i < NH; i++) H[i] = acc[i];
+#pragma unroll
+    for (int a = 0; a < P; a++) g[a] = acc[NH + a];
+    cst = acc[NH + P];
+    cd = acc[NH + P + 1];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      float z = c.hi2[i] > c.lo2[i] ? 2.f * (x[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
+      float pp = psc * c.pp2[i];
+      cst += pp * (z - c.pm2[i]) * (z - c.pm2[i]);
+      g[i] -= pp * (z - c.pm2[i]);
+      H[up<P>(i, i)] += pp;
+    }
+  }
+
+  __device__ __forceinline__ void apply(const KConfig &c, const float (&x)[NX], const float (&dr)[P],
+                                        int, float (&xt)[NX]) const {
+#pragma unroll
+    for (int i = 0; i < 6; i++) xt[i] = fminf(fmaxf(x[i] + s[i] * dr[i], c.lo2[i]), c.hi2[i]);
+  }
+};
+
+// -------------------------------------------------------- LM driver -----
+struct LMResult {
+  int iters, status;
+  bool used64;
+  float cost, cdata;
+};
+
+template <class St>
+__device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::NX], int max_it,
+                                       float (&H)[St::NH], float (&g)[St::P], int &m,
+                                       LMResult &res) {
+  constexpr int P = St::P, NX = St::NX, NH = St::NH;
+  const KConfig &c = *pc.c;
+  float cst, cd;
+  S.eval(pc, x, H, g, cst, cd, m);
+  float lam = -1.f, nu = 2.f;
+  int it = 0, status = PX_MAXITER;
+  bool fresh = true, used64 = false;
+  bool act[P];
+#pragma unroll
+  for (int a = 0; a < P; a++) act[a] = false;
+  while (it < max_it) {
+    if (fresh) {
+      bool small = true;
+      float mx = 0.f;
+      static_for<P>([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        float xv = St::template rsel<a>(x, m);
+        bool lo_hit = xv <= S.template lo_r<a>(c, m);
+        bool hi_hit = St::template has_upper<a>() && xv >= S.template hi_r<a>(c, m);
+        act[a] = (lo_hit && g[a] <= 0.f) || (hi_hit && g[a] >= 0.f);
+        float haa = H[up<P>(a, a)];
+        if (!act[a]) {
+          if (fabsf(g[a]) > c.tol_g * sqrtf(haa * cst)) small = false;
+          mx = fmaxf(mx, haa);
+        }
+      });
+      if (small) { status = PX_CONVERGED; break; }
+      if (lam < 0.f) lam = c.tau0 * mx;
+      fresh = false;
+    }
+    // damping diagonal, projected-Newton solve with re-solve on bound hits
+    float D[P], dr[P];
+    bool pin[P];
+    float mxd = 0.f;
+#pragma unroll
+    for (int a = 0; a < P; a++)
+      if (!act[a]) mxd = fmaxf(mxd, H[up<P>(a, a)]);
+#pragma unroll
+    for (int a = 0; a < P; a++) {
+      D[a] = fmaxf(H[up<P>(a, a)], c.dfloor * mxd);
+      pin[a] = act[a];
+      dr[a] = 0.f;
+    }
+    bool ok = true;
+#pragma unroll 1
+    for (int pass = 0; pass <= P; pass++) {
+      int nf = 0;
+#pragma unroll
+      for (int a = 0; a < P; a++) nf += !pin[a];
+      if (nf == 0) break;
+      float kap = 0.f;
+      ok = damped_solve<P, float>(H, g, lam, D, pin, dr, kap);
+      if (!ok || !(kap <= c.kappa_max)) {
+        ok = damped_solve<P, double>(H, g, lam, D, pin, dr, kap);
+        used64 = true;
+      }
+      if (!ok) break;
+      bool viol = false;
+      static_for<P>([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        if (!pin[a]) {
+          float xv = St::template rsel<a>(x, m);
+          float sc = S.template sc_r<a>(c, m);
+          float lo = S.template lo_r<a>(c, m), hi = S.template hi_r<a>(c, m);
+          float xn = xv + sc * dr[a];
+          if (!(sc > 0.f)) { pin[a] = true; dr[a] = 0.f; viol = true; }
+          else if (xn < lo) { pin[a] = true; dr[a] = (lo - xv) / sc; viol = true; }
+          else if (St::template has_upper<a>() && xn > hi) {
+            pin[a] = true; dr[a] = (hi - xv) / sc; viol = true;
+          }
+        }
+      });
+      if (!viol) break;
+    }
+    if (!ok) {
+      lam *= nu; nu *= 2.f; it++;
+      if (!(lam < 1e30f)) { status = PX_CHOL_FAIL; break; }
+      continue;
+    }
+    float xt[NX];
+    S.apply(c, x, dr, m, xt);
+    float Dz[NX], dmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < NX; i++) {
+      float sc = S.scale(c, i);
+      Dz[i] = sc > 0.f ? (xt[i] - x[i]) / sc : 0.f;
+      dmax = fmaxf(dmax, fabsf(Dz[i]));
+    }
+    if (dmax < c.tol_x) { status = PX_CONVERGED; break; }
+    float Dr[P];
+    static_for<P>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      Dr[a] = St::template rsel<a>(Dz, m);
+    });
+    it++;
+    float Ht[NH], gt[P], ct, cdt;
+    int mt;
+    S.eval(pc, xt, Ht, gt, ct, cdt, mt);
+    float pred = 0.f;
+#pragma unroll
+    for (int a = 0; a < P; a++) {
+      pred += 2.f * g[a] * Dr[a];
+#pragma unroll
+      for (int b = 0; b < P; b++) pred -= Dr[a] * H[up<P>(a, b)] * Dr[b];
+    }
+    float rho = pred > 0.f ? (cst - ct) / pred : -1.f;
+    if (rho > 0.f) {
+      float rel = (cst - ct) / cst;
+#pragma unroll
+      for (int i = 0; i < NX; i++) x[i] = xt[i];
+#pragma unroll
+      for (int i = 0; i < NH; i++) H[i] = Ht[i];
+#pragma unroll
+      for (int a = 0; a < P; a++) g[a] = gt[a];
+      cst = ct;
+      cd = cdt;
+      m = mt;
+      float f = 2.f * rho - 1.f;
+      f = 1.f - f * f * f;
+      lam *= fmaxf(f, 1.f / 3.f);
+      nu = 2.f;
+      fresh = true;
+      if (rel < c.tol_f) { status = PX_CONVERGED; break; }
+    } else {
+      lam *= nu;
+      nu *= 2.f;
+    }
+  }
+  res.iters = it;
+  res.status = status;
+  res.used64 = used64;
+  res.cost = cst;
+  res.cdata = cd;
+}
+
+// -------------------------------------------- final covariance (FP64) ---
+// C = s2 (H_FF)^-1 over the free stage-2 variables (not on an outward-
+// pressed bound, non-zero diagonal), in physical units; writes the packed
+// upper triangle and returns var(E[T]) and var(alpha).
+__device__ __forceinline__ void laplace_cov(const KConfig &c, const float (&x)[6],
+                                            const float (&H)[21], const float (&g)[6], float s2,
+                                            float (&cov)[21], bool &cov_ok, double &vE,
+                                            double &va) {
+  bool fix[6], zc[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) {
+    bool act = (x[k] <= c.lo2[k] && g[k] <= 0.f) || (x[k] >= c.hi2[k] && g[k] >= 0.f);
+    zc[k] = !act && !(H[up<6>(k, k)] > 0.f);
+    fix[k] = act || zc[k];
+  }
+  double A[21], d[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) d[i] = fix[i] ? 1.0 : sqrt((double)H[up<6>(i, i)]);
+#pragma unroll
+  for (int i = 0; i < 6; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++)
+      A[i * (i + 1) / 2 + j] = (fix[i] || fix[j]) ? (i == j ? 1.0 : 0.0)
+                                                   : (double)H[up<6>(i, j)] / (d[i] * d[j]);
+  cov_ok = true;
+#pragma unroll
+  for (int j = 0; j < 6; j++) {
+    double s = A[j * (j + 1) / 2 + j];
+#pragma unroll
+    for (int k = 0; k < j; k++) s -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+    cov_ok = cov_ok && s > 0.0;
+    double L = sqrt(s > 0.0 ? s : 1.0);
+    A[j * (j + 1) / 2 + j] = L;
+#pragma unroll
+    for (int i = j + 1; i < 6; i++) {
+      double t = A[i * (i + 1) / 2 + j];
+#pragma unroll
+      for (int k = 0; k < j; k++) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+      A[i * (i + 1) / 2 + j] = t / L;
+    }
+  }
+  double Cx[6][6];
+#pragma unroll
+  for (int v = 0; v < 6; v++) {
+    double y[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) y[i] = (i == v) ? 1.0 : 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      double s = y[i];
+#pragma unroll
+      for (int k = 0; k < i; k++) s -= A[i * (i + 1) / 2 + k] * y[k];
+      y[i] = s / A[i * (i + 1) / 2 + i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; i--) {
+      double s = y[i];
+#pragma unroll
+      for (int k = i + 1; k < 6; k++) s -= A[k * (k + 1) / 2 + i] * y[k];
+      y[i] = s / A[i * (i + 1) / 2 + i];
+    }
+#pragma unroll
+    for (int u = 0; u < 6; u++) {
+      double sc = 0.25 * ((double)c.hi2[u] - c.lo2[u]) * ((double)c.hi2[v] - c.lo2[v]);
+      Cx[u][v] = (fix[u] || fix[v]) ? 0.0 : (double)s2 * y[u] / (d[u] * d[v]) * sc;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; k++)
+    if (zc[k]) Cx[k][k] = __longlong_as_double(0x7ff0000000000000ll);
+  int q = 0;
+#pragma unroll
+  for (int a = 0; a < 6; a++)
+#pragma unroll
+    for (int b = a; b < 6; b++) cov[q++] = cov_ok ? (float)Cx[a][b] : __int_as_float(0x7fc00000);
+  double gE[6] = {x[4], 0.0, 1.0 - x[4], 0.0, (double)x[0] - x[2], 0.0};
+  vE = 0.0;
+  bool inf = false;
+#pragma unroll
+  for (int a = 0; a < 6; a++) {
+    if (gE[a] == 0.0) continue;
+    if (zc[a]) inf = true;
+#pragma unroll
+    for (int b = 0; b < 6; b++)
+      if (gE[b] != 0.0 && !zc[a] && !zc[b]) vE += gE[a] * Cx[a][b] * gE[b];
+  }
+  if (inf) vE = __longlong_as_double(0x7ff0000000000000ll);
+  if (!cov_ok) vE = __longlong_as_double(0x7ff8000000000000ll);
+  va = Cx[5][5];
+}
+
+// ------------------------------------------------------------ kernel ----
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+template <int K, int S1, int S2, int WPB>
+__global__ void __launch_bounds__(WPB * 32, LM_MINB) lm_kernel(const __grid_constant__ LMLaunch p) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ unsigned long long cstat[ST_COUNT];
+  const KTables &t = p.t;
+  const KConfig &c = p.c;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
+
+  // stage the table image into shared memory with 1D bulk copies
+  const unsigned bytes = (unsigned)t.lay.total * 4u;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(&bar)), "r"(bytes) : "memory");
+    const unsigned chunk = 32768u;
+    for (unsigned off = 0; off < bytes; off += chunk) {
+      unsigned n = bytes - off < chunk ? bytes - off : chunk;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+          ::"r"(smem_u32(reinterpret_cast<char *>(smem) + off)),
+          "l"(reinterpret_cast<const char *>(t.image) + off), "r"(n), "r"(smem_u32(&bar))
+          : "memory");
+    }
+  }
+  __syncthreads();
+  {
+    unsigned done = 0;
+    for (long long spin = 0; spin < (1ll << 26) && !done; spin++) {
+      asm volatile(
+          "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
+          : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
+    }
+    if (!__syncthreads_and(done)) {
+      if (threadIdx.x == 0) atomicExch(p.w.err, 1);
+      // wait (bounded) for the copies still in flight before leaving
+      for (long long spin = 0; spin < (1ll << 26) && !done; spin++) {
+        asm volatile(
+            "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
+            : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
+      }
+      return;
+    }
+  }
+
+  PixCtx pc;
+  pc.t = &t;
+  pc.c = &c;
+  pc.img = smem;
+  pc.wsc = smem + t.lay.total + warp * kMaxTgrid * kScratchPerNode;
+  pc.lane = lane;
+  const int NSx = K + 8;
+  unsigned long long my_it1 = 0, my_it2 = 0, my_fp64 = 0, my_b1 = 0, my_b2 = 0, my_nb2 = 0;
+  unsigned long long my_n = 0, my_st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(p.w.counter, (unsigned long long)kClaim);
+    base = __shfl_sync(kFull, base, 0);
+    if (base >= (unsigned long long)p.s.n_pix) break;
+    for (int cidx = 0; cidx < kClaim; cidx++) {
+      const long long pix = (long long)base + cidx;
+      if (pix >= p.s.n_pix) break;
+      const float *row = p.s.rad + pix * t.nb;
+      const int wvb = p.s.wv[pix];
+      const bool wv_ok = wvb < t.nwv;   // an out-of-range bin is an invalid input
+      pc.wvrow = t.wvtab + (size_t)(wv_ok ? wvb : 0) * t.nb;
+      pc.node_evals = 0;
+      int status = 0, it1 = 0, it2 = 0;
+      // finite check over all bands
+      bool fin = true;
+      for (int b = lane; b < t.nb; b += 32) fin = fin && isfinite(__ldg(row + b));
+      fin = __all_sync(kFull, fin) && wv_ok;
+      float Lh = __ldg(row + t.bh), Ll = __ldg(row + t.bl);
+      float hf = (Lh - Ll) / (Lh + Ll);
+      float xs[NSx];
+#pragma unroll
+      for (int i = 0; i < NSx; i++) xs[i] = __int_as_float(0x7fc00000);
+      float ET = xs[0], sdT = xs[0], alpha = xs[0], cost = xs[0], rms = xs[0], vEf = xs[0];
+      float cov[21];
+#pragma unroll
+      for (int i = 0; i < 21; i++) cov[i] = xs[0];
+      if (!fin) {
+        status = PX_NONFINITE;
+        hf = xs[0];
+      } else if (p.s.gate && !(hf >= c.hfdi_thresh)) {
+        status = PX_NOT_CANDIDATE;
+      } else {
+        // ---- stage 1 setup: radiance, mask m(lambda), weights, prior scale
+        Stage1<K, S1> s1;
+        float nv1 = 0.f;
+        int n1u = 0;
+#pragma unroll
+        for (int s = 0; s < S1; s++) {
+          int bi = lane + 32 * s;
+          s1.Lobs[s] = 0.f;
+          s1.w[s] = 0.f;
+          if (bi < t.n1) {
+            int b = t.b1lo + bi;
+            float L = __ldg(row + b);
+            bool ok = pc.img[t.lay.off_win1 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
+            float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
+            s1.Lobs[s] = L;
+            s1.w[s] = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
+            if (ok) { nv1 += var; n1u++; }
+          }
+        }
+        nv1 = warp_sum1(nv1);
+        n1u = __reduce_add_sync(kFull, n1u);
+        s1.psc = c.weighted ? 1.f : nv1 / (float)max(n1u, 1);
+        s1.sf = 0.5f * (c.hi1[0] - c.lo1[0]);
+        s1.sa = 0.5f * (c.hi1[K] - c.lo1[K]);
+        s1.sT = 0.5f * (c.hi1[K + 1] - c.lo1[K + 1]);
+        // stage-2 band count (needed for the masked test)
+        Stage2<S2> s2;
+        float nv2 = 0.f;
+        int n2u = 0;
+#pragma unroll
+        for (int s = 0; s < S2; s++) {
+          int bi = lane + 32 * s;
+          s2.y[s] = 0.f;
+          s2.tu[s] = 0.f;
+          s2.w[s] = 0.f;
+          if (bi < t.n2) {
+            int b = t.b2lo + bi;
+            float L = __ldg(row + b);
+            bool ok = pc.img[t.lay.off_win2 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
+            float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
+            s2.y[s] = L;
+            s2.w[s] = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
+            if (ok) { nv2 += var; n2u++; }
+          }
+        }
+        nv2 = warp_sum1(nv2);
+        n2u = __reduce_add_sync(kFull, n2u);
+        s2.psc = c.weighted ? 1.f : nv2 / (float)max(n2u, 1);
+        if (n1u <= K + 2 || n2u <= 6) {
+          status = PX_ALL_MASKED;
+        } else {
+          // ---- stage 1
+          float x1[K + 2];
+          const float *ini = p.s.init ? p.s.init + pix * NSx : nullptr;
+          if (ini) {
+#pragma unroll
+            for (int i = 0; i < K + 2; i++) x1[i] = ini[i];
+            Stage1<K, S1>::simplex_project(x1);
+#pragma unroll
+            for (int i = K; i < K + 2; i++) x1[i] = fminf(fmaxf(x1[i], c.lo1[i]), c.hi1[i]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) x1[k] = 1.f / (float)K;
+            x1[K] = c.init_alpha1;
+            x1[K + 1] = c.init_T1;
+          }
+          float H1[Stage1<K, S1>::NH], g1[K + 1];
+          int m1;
+          LMResult r1;
+          lm_fit(s1, pc, x1, c.max_it1, H1, g1, m1, r1);
+          it1 = r1.iters;
+          if (r1.status == PX_MAXITER) status |= PX_F_S1_MAXITER;
+          if (r1.used64) status |= PX_F_FP64;
+          my_b1 += (unsigned long long)(r1.iters + 1) * (unsigned long long)t.n1;
+          // ---- stage 2 setup: y = L - Ls(x_surf), tau_up
+#pragma unroll
+          for (int s = 0; s < S2; s++) {
+            int bi = lane + 32 * s;
+            if (bi < t.n2) {
+              int b = t.b2lo + bi;
+              float4 q = __ldg(pc.wvrow + b);
+              float rho = 0.f;
+#pragma unroll
+              for (int k = 0; k < K; k++) rho = fmaf(x1[k], pc.img[t.lay.off_endm + k * t.nb + b], rho);
+              float Ls = q.y + q.x * rho / (1.f - q.z * rho);
+              s2.y[s] -= Ls;
+              s2.tu[s] = q.w;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 6; i++) s2.s[i] = 0.5f * (c.hi2[i] - c.lo2[i]);
+          float x2[6];
+          if (ini) {
+#pragma unroll
+            for (int i = 0; i < 6; i++) x2[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
+          } else {
+            float T1 = x1[K + 1];
+            x2[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
+            x2[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
+            x2[1] = fminf(fmaxf(c.init_sigma, c.lo2[1]), c.hi2[1]);
+            x2[3] = fminf(fmaxf(c.init_sigma, c.lo2[3]), c.hi2[3]);
+            x2[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
+            float e = x2[0] > x2[2] ? (T1 - x2[2]) / (x2[0] - x2[2]) : 0.5f;
+            x2[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
+          }
+          float H2[21], g2[6];
+          int m2;
+          LMResult r2;
+          lm_fit(s2, pc, x2, c.max_it2, H2, g2, m2, r2);
+          it2 = r2.iters;
+          if (r2.used64) status |= PX_F_FP64;
+          status |= r2.status;
+          my_b2 += (unsigned long long)(r2.iters + 1) * (unsigned long long)t.n2;
+          my_nb2 += (unsigned long long)pc.node_evals * (unsigned long long)t.n2;
+          // ---- outputs
+#pragma unroll
+          for (int i = 0; i < K + 2; i++) xs[i] = x1[i];
+#pragma unroll
+          for (int i = 0; i < 6; i++) xs[K + 2 + i] = x2[i];
+          ET = x2[4] * x2[0] + (1.f - x2[4]) * x2[2];
+          float dmu = x2[0] - x2[2];
+          sdT = sqrtf(x2[4] * x2[1] * x2[1] + (1.f - x2[4]) * x2[3] * x2[3] +
+                      x2[4] * (1.f - x2[4]) * dmu * dmu);
+          alpha = x2[5];
+          cost = r2.cost;
+          rms = sqrtf(r2.cdata / (float)n2u);
+          int nf = 0;
+#pragma unroll
+          for (int k = 0; k < 6; k++) {
+            bool act = (x2[k] <= c.lo2[k] && g2[k] <= 0.f) || (x2[k] >= c.hi2[k] && g2[k] >= 0.f);
+            nf += (!act && H2[up<6>(k, k)] > 0.f);
+          }
+          float s2v = c.weighted ? 1.f : r2.cost / (float)(n2u - nf);
+          bool cov_ok = true;
+          double vE = 0.0, va = 0.0;
+          if (nf > 0) {
+            laplace_cov(c, x2, H2, g2, s2v, cov, cov_ok, vE, va);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 21; i++) cov[i] = 0.f;
+            vE = 0.0;
+            va = 0.0;
+          }
+          vEf = (float)vE;
+          bool act_a = (x2[5] <= c.lo2[5] && g2[5] <= 0.f) || (x2[5] >= c.hi2[5] && g2[5] >= 0.f);
+          double sdE = sqrt(vE), sda = sqrt(va);
+          bool ident = cov_ok && isfinite(sdE) && sdE <= (double)c.ident_sd_et &&
+                       (double)x2[5] >= (double)c.ident_alpha_snr * sda && !act_a && x2[5] > 0.f;
+          if (!ident) status |= PX_F_NOT_IDENT;
+        }
+      }
+      // ---- write this pixel (lanes spread the stores)
+      if (p.o.state)
+        for (int i = lane; i < NSx; i += 32) {
+          float v = xs[0];
+#pragma unroll
+          for (int k = 0; k < NSx; k++) v = (k == i) ? xs[k] : v;
+          p.o.state[pix * NSx + i] = v;
+        }
+      if (p.o.cov && lane < 21) {
+        float v = cov[0];
+#pragma unroll
+        for (int k = 0; k < 21; k++) v = (k == lane) ? cov[k] : v;
+        p.o.cov[pix * 21 + lane] = v;
+      }
+      if (lane == 0) {
+        if (p.o.ET) p.o.ET[pix] = ET;
+        if (p.o.sdT) p.o.sdT[pix] = sdT;
+        if (p.o.alpha) p.o.alpha[pix] = alpha;
+        if (p.o.var_ET) p.o.var_ET[pix] = vEf;
+        if (p.o.cost) p.o.cost[pix] = cost;
+        if (p.o.rms) p.o.rms[pix] = rms;
+        if (p.o.hfdi) p.o.hfdi[pix] = hf;
+        if (p.o.status) p.o.status[pix] = (uint8_t)status;
+        if (p.o.iters) {
+          p.o.iters[2 * pix] = (uint16_t)it1;
+          p.o.iters[2 * pix + 1] = (uint16_t)it2;
+        }
+      }
+      my_n++;
+      my_it1 += it1;
+      my_it2 += it2;
+      my_fp64 += (status & PX_F_FP64) ? 1 : 0;
+      my_st[status & 7]++;
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&cstat[ST_NPIX], my_n);
+    atomicAdd(&cstat[ST_IT1], my_it1);
+    atomicAdd(&cstat[ST_IT2], my_it2);
+    atomicAdd(&cstat[ST_FP64], my_fp64);
+    atomicAdd(&cstat[ST_BAND1], my_b1);
+    atomicAdd(&cstat[ST_BAND2], my_b2);
+    atomicAdd(&cstat[ST_NODEBAND2], my_nb2);
+#pragma unroll
+    for (int k = 0; k < 8; k++) atomicAdd(&cstat[ST_STATUS0 + k], my_st[k]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
+    if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
+}
+
+constexpr int kWPB = 8;
+
+template <int K, int S1, int S2>
+cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used) {
+  auto kern = lm_kernel<K, S1, S2, kWPB>;
+  size_t smem = lm_smem_bytes(p.t);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWPB * 32, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  long long need = (p.s.n_pix + (long long)kWPB * kClaim - 1) / ((long long)kWPB * kClaim);
+  long long blocks = (long long)num_sms * occ;
+  if (blocks > need) blocks = need;
+  if (blocks < 1) blocks = 1;
+  kern<<<(int)blocks, kWPB * 32, smem, st>>>(p);
+  if (blocks_used) *blocks_used = (int)blocks;
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used) {
+  int s1 = (p.t.n1 + 31) / 32, s2 = (p.t.n2 + 31) / 32;
+  if (s1 <= 9 && s2 <= 7) return launch_t<K, 9, 7>(p, num_sms, st, blocks_used);
+  if (s1 <= 9 && s2 <= 9) return launch_t<K, 9, 9>(p, num_sms, st, blocks_used);
+  if (s1 <= 16 && s2 <= 16) return launch_t<K, 16, 16>(p, num_sms, st, blocks_used);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t lm_smem_bytes(const KTables &t) {
+  return (size_t)t.lay.total * 4 + (size_t)kWPB * kMaxTgrid * kScratchPerNode * 4;
+}
+
+cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used) {
+  switch (p.t.K) {
+    case 3: return launch_k<3>(p, num_sms, st, blocks_used);
+    case 5: return launch_k<5>(p, num_sms, st, blocks_used);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace firert

@@ -1,0 +1,278 @@
+"""ctypes binding of libfirert.so (include/firert.h).
+
+Argument marshalling only: every step of the retrieval runs in the library's
+CUDA kernels. Device arrays are torch CUDA tensors (torch is used for device
+memory and streams); host arrays are numpy arrays. There is no CPU fallback:
+if the library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfirert.so")
+
+MAX_ENDM = 8
+FIRE_MEM_DEVICE, FIRE_MEM_HOST = 0, 1
+FIRE_INIT_DEFAULT, FIRE_INIT_GIVEN, FIRE_INIT_MLP = 0, 1, 2
+FIRE_FIT_ALL, FIRE_FIT_HFDI = 0, 1
+PX_CONVERGED, PX_MAXITER, PX_NONFINITE, PX_ALL_MASKED, PX_CHOL_FAIL, PX_NOT_CANDIDATE = range(6)
+PX_F_FP64, PX_F_NOT_IDENT, PX_F_MLP_FALLBACK, PX_F_S1_MAXITER = 8, 16, 32, 64
+
+SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fire_ctx_destroy",
+           "fire_retrieve", "fire_forward", "fire_block_mean", "fire_get_stats",
+           "fire_window_bands", "fire_status_str")
+
+
+class FireError(RuntimeError):
+    pass
+
+
+class Tables_t(C.Structure):
+    _fields_ = [("n_bands", C.c_int32), ("n_wv", C.c_int32), ("n_endm", C.c_int32),
+                ("n_tgrid", C.c_int32), ("wavelength_nm", C.c_void_p), ("solar_irr", C.c_void_p),
+                ("cos_sza", C.c_float), ("tau_down", C.c_void_p), ("tau_up", C.c_void_p),
+                ("rho_atm", C.c_void_p), ("sph_alb", C.c_void_p), ("endmembers", C.c_void_p),
+                ("sat_level", C.c_void_p), ("tgrid_lo", C.c_float), ("tgrid_hi", C.c_float)]
+
+
+class Config_t(C.Structure):
+    _fields_ = [("win1_lo", C.c_float), ("win1_hi", C.c_float), ("win2h_lo", C.c_float),
+                ("win2h_hi", C.c_float), ("win2s_lo", C.c_float), ("win2s_hi", C.c_float),
+                ("max_it1", C.c_int32), ("max_it2", C.c_int32), ("tau0", C.c_float),
+                ("tol_g", C.c_float), ("tol_x", C.c_float), ("tol_f", C.c_float),
+                ("kappa_max", C.c_float), ("dfloor", C.c_float), ("noise_rel", C.c_float),
+                ("noise_abs", C.c_float), ("weighted", C.c_int32), ("hfdi_thresh", C.c_float),
+                ("hfdi_lambda_hi", C.c_float), ("hfdi_lambda_lo", C.c_float),
+                ("ident_sd_et", C.c_float), ("ident_alpha_snr", C.c_float)]
+
+
+class Priors_t(C.Structure):
+    _fields_ = [("lo1", C.c_float * (MAX_ENDM + 2)), ("hi1", C.c_float * (MAX_ENDM + 2)),
+                ("pm1", C.c_float * (MAX_ENDM + 2)), ("pp1", C.c_float * (MAX_ENDM + 2)),
+                ("lo2", C.c_float * 6), ("hi2", C.c_float * 6), ("pm2", C.c_float * 6),
+                ("pp2", C.c_float * 6), ("init_alpha1", C.c_float), ("init_T1", C.c_float),
+                ("init_sigma", C.c_float), ("init_mu_h_floor", C.c_float),
+                ("init_mu_s_ceil", C.c_float), ("init_eta_lo", C.c_float),
+                ("init_eta_hi", C.c_float), ("init_mode", C.c_int32), ("init_state", C.c_void_p)]
+
+
+class Scene_t(C.Structure):
+    _fields_ = [("n_pix", C.c_int64), ("radiance", C.c_void_p), ("wv_bin", C.c_void_p),
+                ("mem", C.c_int32), ("gate_mode", C.c_int32)]
+
+
+class Outputs_t(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("state", "ET", "sdT", "alpha", "cov", "var_ET", "cost",
+                                          "rms", "hfdi", "status", "iters")]
+
+
+class Stats_t(C.Structure):
+    _fields_ = [("n_pixels", C.c_uint64), ("sum_it1", C.c_uint64), ("sum_it2", C.c_uint64),
+                ("n_fp64_pixels", C.c_uint64), ("band_evals1", C.c_uint64),
+                ("band_evals2", C.c_uint64), ("node_band_evals2", C.c_uint64),
+                ("status_counts", C.c_uint64 * 8), ("flops", C.c_double),
+                ("kernel_launches", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise FireError(f"{LIB_PATH} is missing: build it with paper_2608_07580_b300.build")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, f32, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_uint64
+    lib.fire_default_config.argtypes = [C.POINTER(Config_t)]
+    lib.fire_default_priors.argtypes = [C.POINTER(Priors_t), i32, i32, f32, f32]
+    lib.fire_ctx_create.argtypes = [C.POINTER(vp), C.POINTER(Tables_t), C.POINTER(Config_t)]
+    lib.fire_ctx_create.restype = C.c_int
+    lib.fire_ctx_destroy.argtypes = [vp]
+    lib.fire_retrieve.argtypes = [vp, C.POINTER(Scene_t), C.POINTER(Priors_t),
+                                  C.POINTER(Outputs_t), vp]
+    lib.fire_retrieve.restype = C.c_int
+    lib.fire_forward.argtypes = [vp, i32, vp, vp, i64, f32, f32, u64, u64, i64, vp, vp]
+    lib.fire_forward.restype = C.c_int
+    lib.fire_block_mean.argtypes = [vp, i32, i32, i32, i32, vp, vp]
+    lib.fire_block_mean.restype = C.c_int
+    lib.fire_get_stats.argtypes = [vp, C.POINTER(Stats_t)]
+    lib.fire_get_stats.restype = C.c_int
+    lib.fire_window_bands.argtypes = [vp] + [C.POINTER(C.c_int32)] * 4
+    lib.fire_window_bands.restype = C.c_int
+    lib.fire_status_str.argtypes = [C.c_int]
+    lib.fire_status_str.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise FireError(f"{what}: {lib.fire_status_str(rc).decode()} ({rc})")
+
+
+def default_config(**overrides):
+    c = Config_t()
+    lib.fire_default_config(C.byref(c))
+    for k, v in overrides.items():
+        if k in ("win1", "win2h", "win2s"):
+            setattr(c, k + "_lo", v[0])
+            setattr(c, k + "_hi", v[1])
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def default_priors(n_endm, n_tgrid=64, tgrid=(350.0, 2200.0)):
+    p = Priors_t()
+    lib.fire_default_priors(C.byref(p), n_endm, n_tgrid, tgrid[0], tgrid[1])
+    return p
+
+
+def _f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype=None):
+    """Device pointer of a contiguous torch CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise FireError("device arguments must be CUDA tensors")
+    if not t.is_contiguous():
+        raise FireError("device arguments must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise FireError(f"expected {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+class Context:
+    """A retrieval context: scene tables resident on the current CUDA device."""
+
+    def __init__(self, tables, config=None, tgrid=(350.0, 2200.0)):
+        self._keep = [_f32(tables.wavelength_nm), _f32(tables.solar_irr), _f32(tables.tau_down),
+                      _f32(tables.tau_up), _f32(tables.rho_atm), _f32(tables.sph_alb),
+                      _f32(tables.endmembers), _f32(getattr(tables, "sat_level", None))]
+        k = self._keep
+        p = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+        self.n_bands = int(k[0].size)
+        self.n_endm = int(k[6].shape[0])
+        self.n_tgrid = int(getattr(tables, "n_tgrid", 64))
+        self.tgrid = tgrid
+        tb = Tables_t(self.n_bands, int(k[3].shape[0]), self.n_endm, self.n_tgrid, p(k[0]),
+                      p(k[1]), float(tables.cos_sza), p(k[2]), p(k[3]), p(k[4]), p(k[5]),
+                      p(k[6]), p(k[7]), tgrid[0], tgrid[1])
+        self.config = config if config is not None else default_config()
+        h = C.c_void_p()
+        _check(lib.fire_ctx_create(C.byref(h), C.byref(tb), C.byref(self.config)),
+               "fire_ctx_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.fire_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def default_priors(self):
+        return default_priors(self.n_endm, self.n_tgrid, self.tgrid)
+
+    def window_bands(self):
+        v = [C.c_int32() for _ in range(4)]
+        _check(lib.fire_window_bands(self._h, *[C.byref(x) for x in v]), "fire_window_bands")
+        return tuple(x.value for x in v)
+
+    def alloc_outputs(self, n, device=True):
+        """Output buffers for n pixels: torch CUDA tensors (device) or numpy (host)."""
+        ns = self.n_endm + 8
+        shapes = {"state": ((n, ns), "f4"), "ET": ((n,), "f4"), "sdT": ((n,), "f4"),
+                  "alpha": ((n,), "f4"), "cov": ((n, 21), "f4"), "var_ET": ((n,), "f4"),
+                  "cost": ((n,), "f4"), "rms": ((n,), "f4"), "hfdi": ((n,), "f4"),
+                  "status": ((n,), "u1"), "iters": ((n, 2), "u2")}
+        if device:
+            import torch
+            tm = {"f4": torch.float32, "u1": torch.uint8, "u2": torch.int16}
+            return {k: torch.empty(s, dtype=tm[d], device="cuda") for k, (s, d) in shapes.items()}
+        return {k: np.empty(s, dtype=d) for k, (s, d) in shapes.items()}
+
+    def retrieve(self, radiance, wv_bin, priors=None, init_state=None, gate_hfdi=False,
+                 outputs=None, stream=None):
+        """Fit every pixel. radiance [n, n_bands] float32 and wv_bin [n] (uint16
+        numpy or int16/uint16-bit torch): torch CUDA tensors for device
+        scenes, numpy arrays for host scenes (staged inside the call)."""
+        import torch
+        host = isinstance(radiance, np.ndarray)
+        n = int(radiance.shape[0])
+        if priors is None:
+            priors = self.default_priors()
+        if outputs is None:
+            outputs = self.alloc_outputs(n, device=not host)
+        pri = Priors_t()
+        C.memmove(C.byref(pri), C.byref(priors), C.sizeof(Priors_t))
+        if host:
+            rad = np.ascontiguousarray(radiance, dtype=np.float32)
+            wv = np.ascontiguousarray(wv_bin, dtype=np.uint16)
+            self._hold = [rad, wv]
+            sc = Scene_t(n, rad.ctypes.data, wv.ctypes.data, FIRE_MEM_HOST, int(bool(gate_hfdi)))
+            if init_state is not None:
+                ini = np.ascontiguousarray(init_state, dtype=np.float32)
+                self._hold.append(ini)
+                pri.init_mode, pri.init_state = FIRE_INIT_GIVEN, ini.ctypes.data
+            ptr = lambda k: None if outputs.get(k) is None else outputs[k].ctypes.data  # noqa
+            stream_p = C.c_void_p(0)
+        else:
+            sc = Scene_t(n, _dptr(radiance, torch.float32), _dptr(wv_bin), FIRE_MEM_DEVICE,
+                         int(bool(gate_hfdi)))
+            if wv_bin.element_size() != 2:
+                raise FireError("wv_bin must be a 16-bit tensor")
+            if init_state is not None:
+                pri.init_mode, pri.init_state = FIRE_INIT_GIVEN, _dptr(init_state, torch.float32)
+            ptr = lambda k: _dptr(outputs.get(k))  # noqa: E731
+            stream_p = _stream_ptr(stream)
+        o = Outputs_t(*[ptr(k) for k in ("state", "ET", "sdT", "alpha", "cov", "var_ET", "cost",
+                                         "rms", "hfdi", "status", "iters")])
+        _check(lib.fire_retrieve(self._h, C.byref(sc), C.byref(pri), C.byref(o), stream_p),
+               "fire_retrieve")
+        return outputs
+
+    def forward(self, mode, state, wv_bin, noise_rel=0.0, noise_abs=0.0, seed=0, stream_id=1,
+                pixel_offset=0, out=None, stream=None):
+        """Forward model (Eq. fm) on the device; state / wv_bin torch CUDA tensors."""
+        import torch
+        n = int(state.shape[0])
+        if out is None:
+            out = torch.empty((n, self.n_bands), dtype=torch.float32, device="cuda")
+        _check(lib.fire_forward(self._h, mode, _dptr(state, torch.float32), _dptr(wv_bin), n,
+                                noise_rel, noise_abs, seed, stream_id, pixel_offset,
+                                _dptr(out, torch.float32), _stream_ptr(stream)), "fire_forward")
+        return out
+
+    def stats(self):
+        s = Stats_t()
+        _check(lib.fire_get_stats(self._h, C.byref(s)), "fire_get_stats")
+        d = {f: getattr(s, f) for f, _ in Stats_t._fields_ if f != "status_counts"}
+        d["status_counts"] = list(s.status_counts)
+        return d
+
+
+def block_mean(src, width, height, n_bands, block=12, stream=None):
+    """Block mean of a BIP cube [height*width, n_bands] (torch CUDA) -> coarse cube."""
+    import torch
+    cw, ch = width // block, height // block
+    dst = torch.empty((ch * cw, n_bands), dtype=torch.float32, device="cuda")
+    _check(lib.fire_block_mean(_dptr(src, torch.float32), width, height, n_bands, block,
+                               _dptr(dst), _stream_ptr(stream)), "fire_block_mean")
+    return dst

@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every symbol include/*.h declares;
+host-side defaults and argument checks work without a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(fire_\w+)\s*\(", src, re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2608_07580_b300 import build
+    lib = C.CDLL(build.build())
+    declared = _declared()
+    assert {"fire_ctx_create", "fire_retrieve", "fire_forward"} <= declared
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+
+
+def test_binding_symbols_match_header():
+    from paper_2608_07580_b300 import firert
+    assert set(firert.SYMBOLS) <= _declared()
+
+
+def test_defaults_match_paper_and_oracle():
+    from paper_2608_07580_b300 import firert
+    import oracle
+    c = firert.default_config()
+    o = oracle.Config()
+    assert (c.win1_lo, c.win1_hi) == o.win1
+    assert (c.win2h_lo, c.win2h_hi) == o.win2h and (c.win2s_lo, c.win2s_hi) == o.win2s
+    assert c.max_it1 == o.max_it1 and c.max_it2 == o.max_it2
+    for k in ("tau0", "tol_g", "tol_x", "tol_f", "kappa_max", "dfloor", "noise_rel", "noise_abs",
+              "hfdi_thresh", "ident_sd_et", "ident_alpha_snr"):
+        assert abs(getattr(c, k) - getattr(o, k)) <= 1e-6 * abs(getattr(o, k)), k
+    p = firert.default_priors(3)
+    assert np.allclose(np.array(p.lo1[:5]), o.lo1, rtol=1e-6)
+    assert np.allclose(np.array(p.hi1[:5]), o.hi1, rtol=1e-6)
+    assert np.allclose(np.array(p.lo2[:]), o.lo2, rtol=1e-6)
+    assert np.allclose(np.array(p.hi2[:]), o.hi2, rtol=1e-6)
+    assert np.allclose(np.array(p.pm1[:5]), o.pm1) and np.allclose(np.array(p.pp1[:5]), o.pp1)
+    assert np.allclose(np.array(p.pm2[:]), o.pm2) and np.allclose(np.array(p.pp2[:]), o.pp2)
+    assert np.allclose([p.init_alpha1, p.init_T1, p.init_sigma, p.init_mu_h_floor, p.init_mu_s_ceil,
+                        p.init_eta_lo, p.init_eta_hi],
+                       [o.init_alpha1, o.init_T1, o.init_sigma, o.init_mu_h_floor, o.init_mu_s_ceil,
+                        *o.init_eta], rtol=1e-6)
+
+
+def test_null_arguments_are_rejected_without_gpu():
+    from paper_2608_07580_b300 import firert
+    lib = firert.lib
+    assert lib.fire_ctx_create(None, None, None) == 1
+    h = C.c_void_p()
+    assert lib.fire_ctx_create(C.byref(h), None, None) == 1
+    assert lib.fire_retrieve(None, None, None, None, None) == 1
+    assert lib.fire_status_str(4) == b"unsupported shape"

@@ -1,0 +1,208 @@
+"""GPU path (C-ABI through the ctypes binding) against the FP64 oracle on the
+same seeded inputs: forward model, full per-pixel retrieval (config 1:
+64x64x284), ragged and degenerate cases, host-staged path, determinism.
+
+Parity bar (per converged, identifiable pixel): |dE[T]| <= 0.5 K and
+|d alpha| <= 1e-3 * max(alpha_oracle, 1e-4), for >= 99.9 % of the pool."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from scenes import NOISE_ABS, NOISE_REL, config1, parity_stats
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fr():
+    from paper_2608_07580_b300 import firert
+    return firert
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return config1()
+
+
+@pytest.fixture(scope="module")
+def c1_oracle(c1):
+    t, tr, L = c1
+    return oracle.retrieve(t, L, tr.wv_bin)
+
+
+def _dev(torch, a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def _np(d):
+    return {k: v.cpu().numpy() if hasattr(v, "cpu") else v for k, v in d.items()}
+
+
+def _retrieve(fr, torch, t, L, wv, **kw):
+    ctx = fr.Context(t)
+    out = ctx.retrieve(_dev(torch, L, torch.float32), _dev(torch, wv.astype(np.int16), torch.int16),
+                       **kw)
+    torch.cuda.synchronize()
+    g = _np(out)
+    g["iters"] = g["iters"].astype(np.uint16)
+    return ctx, g
+
+
+def test_tables_and_forward_single_temperature(fr, torch):
+    t = synth.make_tables(path_reflectance=True)
+    ctx = fr.Context(t)
+    rng = np.random.default_rng(1)
+    n = 300
+    xs = rng.dirichlet(np.ones(3), n)
+    st = np.column_stack([xs, 10 ** rng.uniform(-4, -0.3, n), rng.uniform(400, 2100, n)])
+    wv = rng.integers(0, 16, n).astype(np.uint16)
+    Lg = ctx.forward(1, _dev(torch, st, torch.float32), _dev(torch, wv.astype(np.int16), torch.int16))
+    Lo = oracle.forward(t, 1, st.astype(np.float32).astype(np.float64), wv)
+    rel = np.abs(Lg.cpu().numpy() - Lo) / np.maximum(np.abs(Lo), 1e-6)
+    assert rel.max() < 1e-5
+
+
+def test_forward_mixture_matches_oracle(fr, torch):
+    t = synth.make_tables()
+    ctx = fr.Context(t)
+    rng = np.random.default_rng(2)
+    n = 300
+    xs = rng.dirichlet(np.ones(3), n)
+    x2 = np.column_stack([rng.uniform(900, 2100, n), rng.uniform(30, 400, n),
+                          rng.uniform(360, 990, n), rng.uniform(30, 400, n),
+                          rng.uniform(0, 1, n), 10 ** rng.uniform(-4, -0.3, n)])
+    st = np.column_stack([xs, x2])
+    wv = rng.integers(0, 16, n).astype(np.uint16)
+    Lg = ctx.forward(2, _dev(torch, st, torch.float32), _dev(torch, wv.astype(np.int16), torch.int16))
+    Lo = oracle.forward(t, 2, st.astype(np.float32).astype(np.float64), wv)
+    rel = np.abs(Lg.cpu().numpy() - Lo) / np.maximum(np.abs(Lo), 1e-6)
+    assert rel.max() < 2e-5
+
+
+def test_forward_noise_uses_the_counter_generator(fr, torch):
+    t = synth.make_tables()
+    ctx = fr.Context(t)
+    tr = synth.make_config1_truth(seed=5, width=16, height=16)
+    st = tr.state1()
+    Lg = ctx.forward(1, _dev(torch, st, torch.float32),
+                     _dev(torch, tr.wv_bin.astype(np.int16), torch.int16),
+                     NOISE_REL, NOISE_ABS, seed=5, stream_id=synth.STREAM_NOISE).cpu().numpy()
+    z = synth.noise_normals(5, np.arange(tr.n_pix), t.n_bands)
+    Lo = oracle.synth_radiance(t, 1, st.astype(np.float32).astype(np.float64), tr.wv_bin, z,
+                               NOISE_REL, NOISE_ABS)
+    sd = np.sqrt((NOISE_REL * Lo) ** 2 + NOISE_ABS ** 2)
+    assert np.max(np.abs(Lg - Lo) / sd) < 1e-3
+
+
+def test_block_mean(fr, torch):
+    rng = np.random.default_rng(3)
+    w, h, nb = 50, 37, 13
+    src = rng.normal(size=(h * w, nb)).astype(np.float32)
+    dst = fr.block_mean(_dev(torch, src, torch.float32), w, h, nb, 12).cpu().numpy()
+    ref = src.reshape(h, w, nb)[:36, :48].reshape(3, 12, 4, 12, nb).mean(axis=(1, 3)).reshape(-1, nb)
+    assert np.max(np.abs(dst - ref)) < 1e-5
+
+
+def test_config1_parity(fr, torch, c1, c1_oracle):
+    t, tr, L = c1
+    ctx, g = _retrieve(fr, torch, t, L, tr.wv_bin)
+    s = parity_stats(c1_oracle, g)
+    print("config1 parity:", {k: v for k, v in s.items() if k != "fail_idx"},
+          "fail:", s["fail_idx"][:10])
+    st = ctx.stats()
+    print("stats:", st)
+    assert st["n_pixels"] == tr.n_pix
+    assert s["pool"] >= 0.8 * s["oracle_conv_ident"]
+    assert s["rate"] >= 0.999
+    # the per-pixel outcome codes agree wherever the oracle's is not MAXITER
+    go, oo = g["status"] & 7, c1_oracle["status"] & 7
+    assert np.mean(go == oo) > 0.95
+
+
+def test_config1_surface_and_stage1(fr, torch, c1, c1_oracle):
+    t, tr, L = c1
+    _, g = _retrieve(fr, torch, t, L, tr.wv_bin)
+    o = c1_oracle
+    conv = ((o["status"] & 7) == 0) & ((g["status"] & 7) == 0)
+    # surface fractions agree tightly (well-conditioned linear part of stage 1)
+    assert np.percentile(np.abs(g["state"][conv, :3] - o["state"][conv, :3]).max(1), 99) < 1e-3
+
+
+def test_ragged_sizes_and_empty(fr, torch, c1, c1_oracle):
+    t, tr, L = c1
+    ctx = fr.Context(t)
+    for n in (0, 1, 7, 33, 129):
+        out = ctx.retrieve(_dev(torch, L[:n].reshape(n, -1), torch.float32),
+                           _dev(torch, tr.wv_bin[:n].astype(np.int16), torch.int16))
+        torch.cuda.synchronize()
+        if n:
+            g = out["ET"].cpu().numpy()
+            o = c1_oracle["ET"][:n]
+            conv = ((c1_oracle["status"][:n] & 23) == 0) & ((out["status"].cpu().numpy() & 7) == 0)
+            assert np.all(np.abs(g[conv] - o[conv]) <= 0.5)
+            assert ctx.stats()["n_pixels"] == n
+
+
+def test_degenerate_pixels(fr, torch):
+    t = synth.make_tables(sat_level=25.0)
+    tr = synth.make_config1_truth(seed=9, width=8, height=1, fire_frac=1.0, alpha_range=(0.3, 0.5),
+                                  t_range=(1400, 1500))
+    z = synth.noise_normals(9, np.arange(8), t.n_bands)
+    L = oracle.synth_radiance(t, 1, tr.state1(), tr.wv_bin, z, NOISE_REL, NOISE_ABS)
+    L[1, 40] = np.nan
+    L[2, :] = 30.0                      # every band saturated
+    o = oracle.retrieve(t, L, tr.wv_bin)
+    _, g = _retrieve(fr, torch, t, L, tr.wv_bin)
+    assert g["status"][1] & 7 == fr.PX_NONFINITE and o["status"][1] & 7 == oracle.NONFINITE
+    assert g["status"][2] & 7 == fr.PX_ALL_MASKED and o["status"][2] & 7 == oracle.ALL_MASKED
+    ok = [i for i in range(8) if i not in (1, 2) and (o["status"][i] & 23) == 0
+          and (g["status"][i] & 7) == 0]
+    assert len(ok) >= 3
+    assert np.all(np.abs(g["ET"][ok] - o["ET"][ok]) <= 0.5)
+
+
+def test_hfdi_gate(fr, torch, c1, c1_oracle):
+    t, tr, L = c1
+    _, g = _retrieve(fr, torch, t, L, tr.wv_bin, gate_hfdi=True)
+    o = oracle.retrieve(t, L, tr.wv_bin, oracle.Config(gate_hfdi=True))
+    assert np.array_equal(g["status"] & 7 == fr.PX_NOT_CANDIDATE,
+                          o["status"] & 7 == oracle.NOT_CANDIDATE)
+    assert np.allclose(g["hfdi"], o["hfdi"], atol=1e-5)
+
+
+def test_host_path_equals_device_path_and_is_deterministic(fr, torch, c1):
+    t, tr, L = c1
+    ctx, g1 = _retrieve(fr, torch, t, L, tr.wv_bin)
+    _, g2 = _retrieve(fr, torch, t, L, tr.wv_bin)
+    h = ctx.retrieve(L, tr.wv_bin)
+    for k in ("ET", "alpha", "state", "cov", "status", "iters"):
+        assert np.array_equal(g1[k], g2[k], equal_nan=True) if g1[k].dtype.kind == "f" \
+            else np.array_equal(g1[k], g2[k]), k
+        hk = h[k].astype(g1[k].dtype) if k == "iters" else h[k]
+        assert np.array_equal(g1[k], hk, equal_nan=True) if g1[k].dtype.kind == "f" \
+            else np.array_equal(g1[k], hk), k
+
+
+def test_given_init_matches_oracle(fr, torch, c1):
+    t, tr, L = c1
+    idx = np.flatnonzero(tr.kind == 1)[:64]
+    K = 3
+    init = np.column_stack([tr.x_surf[idx], tr.single[idx, 0], tr.single[idx, 1],
+                            np.maximum(tr.single[idx, 1], 950), np.full(idx.size, 60.0),
+                            np.full(idx.size, 600.0), np.full(idx.size, 60.0),
+                            np.full(idx.size, 0.8), tr.single[idx, 0]]).astype(np.float32)
+    o = oracle.retrieve(t, L[idx], tr.wv_bin[idx], init_state=init.astype(np.float64))
+    ctx = fr.Context(t)
+    out = ctx.retrieve(_dev(torch, L[idx], torch.float32),
+                       _dev(torch, tr.wv_bin[idx].astype(np.int16), torch.int16),
+                       init_state=_dev(torch, init, torch.float32))
+    torch.cuda.synchronize()
+    s = parity_stats(o, _np(out))
+    assert s["rate"] >= 0.99 and s["pool"] > 10
