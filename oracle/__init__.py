@@ -319,3 +319,44 @@ def retrieve(tables, radiance, wv_bin, cfg=None, init_state=None, n_threads=0):
                        C.c_void_p(wv.ctypes.data), C.c_int64(n), C.c_void_p(_ptr(ini)),
                        C.byref(o), C.c_int(n_threads))
     return out
+
+
+def mlp_forward(params, x):
+    """FP64 forward of the proposal MLP; params = dict W1,b1,W2,b2,W3,b3."""
+    W1, W2, W3 = (np.ascontiguousarray(params[k], np.float64) for k in ("W1", "W2", "W3"))
+    b1, b2, b3 = (np.ascontiguousarray(params[k], np.float64) for k in ("b1", "b2", "b3"))
+    x = np.ascontiguousarray(x, np.float64)
+    B, Din = x.shape
+    H, Dout = W1.shape[0], W3.shape[0]
+    a1, a2, z = np.empty((B, H)), np.empty((B, H)), np.empty((B, Dout))
+    v = C.c_void_p
+    lib().orc_mlp_forward(C.c_int(B), C.c_int(Din), C.c_int(H), C.c_int(Dout),
+                          *[v(a.ctypes.data) for a in (W1, b1, W2, b2, W3, b3, x, a1, a2, z)])
+    return a1, a2, z
+
+
+def mlp_backward(params, x, target, mask):
+    """Loss and FP64 gradients of the masked MSE in z-space."""
+    W1, W2, W3 = (np.ascontiguousarray(params[k], np.float64) for k in ("W1", "W2", "W3"))
+    x = np.ascontiguousarray(x, np.float64)
+    a1, a2, z = mlp_forward(params, x)
+    t = np.ascontiguousarray(target, np.float64)
+    mk = np.ascontiguousarray(mask, np.float64)
+    B, Din = x.shape
+    H, Dout = W1.shape[0], W3.shape[0]
+    g = {"W1": np.empty((H, Din)), "b1": np.empty(H), "W2": np.empty((H, H)), "b2": np.empty(H),
+         "W3": np.empty((Dout, H)), "b3": np.empty(Dout)}
+    v = C.c_void_p
+    lib().orc_mlp_backward.restype = C.c_double
+    loss = lib().orc_mlp_backward(C.c_int(B), C.c_int(Din), C.c_int(H), C.c_int(Dout),
+                                  *[v(a.ctypes.data) for a in (W1, W2, W3, x, a1, a2, z, t, mk,
+                                                               g["W1"], g["b1"], g["W2"], g["b2"],
+                                                               g["W3"], g["b3"])])
+    return loss, g, z
+
+
+def adam(w, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    vp = C.c_void_p
+    lib().orc_adam(C.c_int64(w.size), vp(w.ctypes.data), vp(g.ctypes.data), vp(m.ctypes.data),
+                   vp(v.ctypes.data), C.c_int(t), C.c_double(lr), C.c_double(b1), C.c_double(b2),
+                   C.c_double(eps))

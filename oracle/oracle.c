@@ -765,7 +765,11 @@ static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const d
   double Cz[36];
   memset(Cz, 0, sizeof(Cz));
   int cov_ok = 1;
-  if (nf > 0) {
+  /* alpha held on its lower bound: no thermal signal, so E[T] and its
+   * posterior are undefined */
+  int no_signal = r2.active[5] && x2[5] <= lo2[5];
+  if (no_signal) cov_ok = 0;
+  if (nf > 0 && !no_signal) {
     double A[36], dsc[6];
     for (int u = 0; u < nf; u++) dsc[u] = sqrt(r2.H[F[u] * 6 + F[u]]);
     for (int u = 0; u < nf; u++)
@@ -800,6 +804,7 @@ static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const d
     for (int b = 0; b < 6; b++)
       if (gE[b] != 0) vE += gE[a] * Cx[a * 6 + b] * gE[b];
   }
+  if (no_signal) vE = INFINITY;
   o->var_ET[i] = vE;
   double sdE = sqrt(vE), sda = sqrt(Cx[35]);
   int ident = cov_ok && isfinite(sdE) && sdE <= c->ident_sd_et && x2[5] >= c->ident_alpha_snr * sda &&
@@ -829,4 +834,97 @@ void orc_retrieve(const orc_tables_t *t, const orc_config_t *c, const float *rad
 /* array helper for tests: out[i] = B(lambda[i], T[i]) */
 void orc_planck_array(int64_t n, const double *lambda_nm, const double *T, double *out) {
   for (int64_t i = 0; i < n; i++) out[i] = orc_planck(lambda_nm[i], T[i]);
+}
+
+/* ------------------------------------------------ MLP proposal (a7) --- */
+/* Learned initial-state proposal (the task's learned extension; the paper
+ * has no network): z = tanh(W3 relu(W2 relu(W1 x + b1) + b2) + b3), weights
+ * row-major [out][in]. Plain FP64 definition, one sample at a time. */
+void orc_mlp_forward(int B, int Din, int H, int Dout, const double *W1, const double *b1,
+                     const double *W2, const double *b2, const double *W3, const double *b3,
+                     const double *x, double *a1, double *a2, double *z) {
+  for (int s = 0; s < B; s++) {
+    const double *xs = x + (size_t)s * Din;
+    double *A1 = a1 + (size_t)s * H, *A2 = a2 + (size_t)s * H, *Z = z + (size_t)s * Dout;
+    for (int o = 0; o < H; o++) {
+      double v = b1[o];
+      for (int i = 0; i < Din; i++) v += W1[(size_t)o * Din + i] * xs[i];
+      A1[o] = v;
+    }
+    for (int o = 0; o < H; o++) {
+      double v = b2[o];
+      for (int i = 0; i < H; i++) v += W2[(size_t)o * H + i] * (A1[i] > 0 ? A1[i] : 0.0);
+      A2[o] = v;
+    }
+    for (int o = 0; o < Dout; o++) {
+      double v = b3[o];
+      for (int i = 0; i < H; i++) v += W3[(size_t)o * H + i] * (A2[i] > 0 ? A2[i] : 0.0);
+      Z[o] = tanh(v);
+    }
+  }
+}
+
+/* Mean-squared error over the masked outputs and its gradients (chain rule
+ * through tanh and the two ReLUs). Returns the loss. */
+double orc_mlp_backward(int B, int Din, int H, int Dout, const double *W1, const double *W2,
+                        const double *W3, const double *x, const double *a1, const double *a2,
+                        const double *z, const double *t, const double *mask, double *gW1,
+                        double *gb1, double *gW2, double *gb2, double *gW3, double *gb3) {
+  double nused = 0;
+  for (int o = 0; o < Dout; o++) nused += mask[o];
+  double norm = 1.0 / (B * nused), loss = 0;
+  memset(gW1, 0, sizeof(double) * H * Din);
+  memset(gb1, 0, sizeof(double) * H);
+  memset(gW2, 0, sizeof(double) * H * H);
+  memset(gb2, 0, sizeof(double) * H);
+  memset(gW3, 0, sizeof(double) * Dout * H);
+  memset(gb3, 0, sizeof(double) * Dout);
+  double *dy = (double *)malloc(sizeof(double) * Dout);
+  double *d2 = (double *)malloc(sizeof(double) * H), *d1 = (double *)malloc(sizeof(double) * H);
+  for (int s = 0; s < B; s++) {
+    const double *xs = x + (size_t)s * Din, *A1 = a1 + (size_t)s * H, *A2 = a2 + (size_t)s * H;
+    const double *Z = z + (size_t)s * Dout, *T = t + (size_t)s * Dout;
+    for (int o = 0; o < Dout; o++) {
+      double e = (Z[o] - T[o]) * mask[o];
+      loss += e * e * norm;
+      dy[o] = 2.0 * e * norm * (1.0 - Z[o] * Z[o]);
+    }
+    for (int i = 0; i < H; i++) {
+      double v = 0;
+      for (int o = 0; o < Dout; o++) v += dy[o] * W3[(size_t)o * H + i];
+      d2[i] = A2[i] > 0 ? v : 0.0;
+    }
+    for (int i = 0; i < H; i++) {
+      double v = 0;
+      for (int o = 0; o < H; o++) v += d2[o] * W2[(size_t)o * H + i];
+      d1[i] = A1[i] > 0 ? v : 0.0;
+    }
+    for (int o = 0; o < Dout; o++) {
+      gb3[o] += dy[o];
+      for (int i = 0; i < H; i++) gW3[(size_t)o * H + i] += dy[o] * (A2[i] > 0 ? A2[i] : 0.0);
+    }
+    for (int o = 0; o < H; o++) {
+      gb2[o] += d2[o];
+      for (int i = 0; i < H; i++) gW2[(size_t)o * H + i] += d2[o] * (A1[i] > 0 ? A1[i] : 0.0);
+    }
+    for (int o = 0; o < H; o++) {
+      gb1[o] += d1[o];
+      for (int i = 0; i < Din; i++) gW1[(size_t)o * Din + i] += d1[o] * xs[i];
+    }
+  }
+  free(dy);
+  free(d2);
+  free(d1);
+  return loss;
+}
+
+/* Adam (Kingma & Ba 2014) on a flat parameter vector, step t >= 1. */
+void orc_adam(int64_t n, double *w, const double *g, double *m, double *v, int t, double lr,
+              double b1, double b2, double eps) {
+  double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+  for (int64_t i = 0; i < n; i++) {
+    m[i] = b1 * m[i] + (1 - b1) * g[i];
+    v[i] = b2 * v[i] + (1 - b2) * g[i] * g[i];
+    w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+  }
 }

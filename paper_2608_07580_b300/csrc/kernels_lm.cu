@@ -65,6 +65,17 @@ __device__ __forceinline__ constexpr int up(int a, int b) {
   return a <= b ? a * P - (a * (a - 1)) / 2 + (b - a) : b * P - (b * (b - 1)) / 2 + (a - b);
 }
 
+// Reciprocal square root without division: FP32 uses the SFU; FP64 refines an
+// FP32 seed with two Newton-Raphson steps y <- y (3 - x y^2) / 2 (quadratic
+// convergence: 2^-23 -> 2^-46 -> full precision).
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);
+  y = y * (1.5 - 0.5 * x * y * y);
+  return y;
+}
+
 // ------------------------------------------------------------- solve ----
 // Solve (H + lam D) d = rhs over the free variables on the diagonally scaled
 // matrix; pinned variables are identity rows with their displacement moved
@@ -76,7 +87,7 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
                                              const float (&D)[P], const bool (&pin)[P],
                                              float (&dr)[P], float &kap) {
   T A[P * (P + 1) / 2];  // packed lower: (i, j), j <= i at i (i+1) / 2 + j
-  T y[P], d[P];
+  T y[P], rd[P], il[P];
 #pragma unroll
   for (int i = 0; i < P; i++) {
     T r = pin[i] ? T(0) : (T)g[i];
@@ -93,13 +104,14 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
       A[i * (i + 1) / 2 + j] = m;
     }
   }
+  // diagonal (Jacobi) scaling: unit diagonal, scaled right-hand side
 #pragma unroll
-  for (int i = 0; i < P; i++) d[i] = sqrt(A[i * (i + 1) / 2 + i]);
+  for (int i = 0; i < P; i++) rd[i] = rsq(A[i * (i + 1) / 2 + i]);
 #pragma unroll
   for (int i = 0; i < P; i++) {
-    y[i] /= d[i];
+    y[i] *= rd[i];
 #pragma unroll
-    for (int j = 0; j <= i; j++) A[i * (i + 1) / 2 + j] /= (d[i] * d[j]);
+    for (int j = 0; j <= i; j++) A[i * (i + 1) / 2 + j] *= rd[i] * rd[j];
   }
   bool ok = true;
 #pragma unroll
@@ -108,14 +120,15 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
 #pragma unroll
     for (int k = 0; k < j; k++) s -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
     ok = ok && (s > T(0));
-    T L = sqrt(s > T(0) ? s : T(1));
-    A[j * (j + 1) / 2 + j] = L;
+    T r = rsq(s > T(0) ? s : T(1));
+    il[j] = r;                               // 1 / L_jj
+    A[j * (j + 1) / 2 + j] = (s > T(0) ? s : T(1)) * r;
 #pragma unroll
     for (int i = j + 1; i < P; i++) {
       T t = A[i * (i + 1) / 2 + j];
 #pragma unroll
       for (int k = 0; k < j; k++) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
-      A[i * (i + 1) / 2 + j] = t / L;
+      A[i * (i + 1) / 2 + j] = t * r;
     }
   }
   if (!ok) return false;
@@ -127,24 +140,24 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
       lmax = l > lmax ? l : lmax;
       lmin = l < lmin ? l : lmin;
     }
-  kap = lmax > T(0) ? (float)((lmax / lmin) * (lmax / lmin)) : 1.f;
+  kap = lmax > T(0) ? (float)(lmax * lmax) / (float)(lmin * lmin) : 1.f;
 #pragma unroll
   for (int i = 0; i < P; i++) {
     T s = y[i];
 #pragma unroll
     for (int k = 0; k < i; k++) s -= A[i * (i + 1) / 2 + k] * y[k];
-    y[i] = s / A[i * (i + 1) / 2 + i];
+    y[i] = s * il[i];
   }
 #pragma unroll
   for (int i = P - 1; i >= 0; i--) {
     T s = y[i];
 #pragma unroll
     for (int k = i + 1; k < P; k++) s -= A[k * (k + 1) / 2 + i] * y[k];
-    y[i] = s / A[i * (i + 1) / 2 + i];
+    y[i] = s * il[i];
   }
 #pragma unroll
   for (int i = 0; i < P; i++)
-    if (!pin[i]) dr[i] = (float)(y[i] / d[i]);
+    if (!pin[i]) dr[i] = (float)(y[i] * rd[i]);
   return true;
 }
 
@@ -162,7 +175,7 @@ struct PixCtx {
 // ------------------------------------------------------------ stage 1 ---
 template <int K, int S1>
 struct Stage1 {
-  static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2;
+  static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2, NS = S1;
   float Lobs[S1], w[S1];
   float psc;
   float sf, sa, sT;
@@ -206,13 +219,15 @@ struct Stage1 {
   // model, reduced Jacobian, normal equations and cost at x (all lanes get
   // the warp totals). cd = unweighted data cost.
   __device__ __forceinline__ void eval(PixCtx &pc, const float (&x)[NX], float (&H)[NH],
-                                       float (&g)[P], float &cst, float &cd, int &m) const {
+                                       float (&g)[P], float &cst, float &cd, int &m,
+                                       const float (&rold)[NS], float (&rnew)[NS],
+                                       float &dcd) const {
     const KTables &t = *pc.t;
     const KConfig &c = *pc.c;
     m = argmax_frac(x);
-    float acc[NH + P + 2];
+    float acc[NH + P + 3];
 #pragma unroll
-    for (int i = 0; i < NH + P + 2; i++) acc[i] = 0.f;
+    for (int i = 0; i < NH + P + 3; i++) acc[i] = 0.f;
     const float a1 = x[K], invT = 1.f / x[K + 1];
 #pragma unroll
     for (int s = 0; s < S1; s++) {
@@ -235,6 +250,8 @@ struct Stage1 {
         float B = pc.img[t.lay.off_c1l5 + b] * e * rom;
         float dB = B * xx * invT * rom;
         float r = Lobs[s] - fmaf(a1 * q.w, B, Ls);
+        rnew[s] = r;
+        acc[NH + P + 2] = fmaf(w[s] * (rold[s] - r), rold[s] + r, acc[NH + P + 2]);
         float dL[K], dEm = 0.f;
         const float qi2 = q.x * inv * inv * sf;
 #pragma unroll
@@ -266,6 +283,7 @@ struct Stage1 {
     for (int a = 0; a < P; a++) g[a] = acc[NH + a];
     cd = acc[NH + P + 1];
     cst = acc[NH + P];
+    dcd = acc[NH + P + 2];
     // weak Gaussian prior in z, pulled into the reduced basis (e_k - e_m)
     float zr[NX], ppm = 0.f, rm = 0.f;
 #pragma unroll
@@ -290,6 +308,21 @@ struct Stage1 {
       g[a] -= psc * c.pp1[a + 1] * zr[a + 1];
       H[up<P>(a, a)] += psc * c.pp1[a + 1];
     }
+  }
+
+  // prior(x_old) - prior(x_new), formed from differences of z
+  __device__ __forceinline__ float prior_drop(const KConfig &c, const float (&xo)[NX],
+                                              const float (&xn)[NX]) const {
+    float d = 0.f;
+#pragma unroll
+    for (int i = 0; i < NX; i++) {
+      if (c.hi1[i] > c.lo1[i] && c.pp1[i] > 0.f) {
+        float k = 2.f / (c.hi1[i] - c.lo1[i]);
+        float zo = k * (xo[i] - c.lo1[i]) - 1.f - c.pm1[i], zn = k * (xn[i] - c.lo1[i]) - 1.f - c.pm1[i];
+        d += psc * c.pp1[i] * (k * (xo[i] - xn[i])) * (zo + zn);
+      }
+    }
+    return d;
   }
 
   // x + step (z units, reduced basis) -> projected trial point
@@ -343,7 +376,7 @@ struct Stage1 {
 // ------------------------------------------------------------ stage 2 ---
 template <int S2>
 struct Stage2 {
-  static constexpr int P = 6, NX = 6, NH = 21;
+  static constexpr int P = 6, NX = 6, NH = 21, NS = S2;
   float y[S2], tu[S2], w[S2];
   float psc;
   float s[6];
@@ -363,7 +396,9 @@ struct Stage2 {
   }
 
   __device__ __forceinline__ void eval(PixCtx &pc, const float (&x)[NX], float (&H)[NH],
-                                       float (&g)[P], float &cst, float &cd, int &m) const {
+                                       float (&g)[P], float &cst, float &cd, int &m,
+                                       const float (&rold)[NS], float (&rnew)[NS],
+                                       float &dcd) const {
     const KTables &t = *pc.t;
     const KConfig &c = *pc.c;
     m = 0;
@@ -438,9 +473,9 @@ struct Stage2 {
       }
     }
     pc.node_evals += (jhi >= jlo) ? (jhi - jlo + 1) : 0;
-    float acc[NH + P + 2];
+    float acc[NH + P + 3];
 #pragma unroll
-    for (int i = 0; i < NH + P + 2; i++) acc[i] = 0.f;
+    for (int i = 0; i < NH + P + 3; i++) acc[i] = 0.f;
     const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
     const float ish3 = ish2 / sh, iss3 = iss2 / ss;
 #pragma unroll
@@ -450,6 +485,8 @@ struct Stage2 {
         float Bm = eta * Bh + (1.f - eta) * Bs;
         float atu = al * tu[s2];
         float r = y[s2] - atu * Bm;
+        rnew[s2] = r;
+        acc[NH + P + 2] = fmaf(w[s2] * (rold[s2] - r), rold[s2] + r, acc[NH + P + 2]);
         float J[6];
         J[0] = atu * eta * S[s2][1] * ish2 * s[0];
         J[1] = atu * eta * S[s2][2] * ish3 * s[1];
@@ -476,6 +513,7 @@ struct Stage2 {
     for (int a = 0; a < P; a++) g[a] = acc[NH + a];
     cst = acc[NH + P];
     cd = acc[NH + P + 1];
+    dcd = acc[NH + P + 2];
 #pragma unroll
     for (int i = 0; i < 6; i++) {
       float z = c.hi2[i] > c.lo2[i] ? 2.f * (x[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
@@ -484,6 +522,20 @@ struct Stage2 {
       g[i] -= pp * (z - c.pm2[i]);
       H[up<P>(i, i)] += pp;
     }
+  }
+
+  __device__ __forceinline__ float prior_drop(const KConfig &c, const float (&xo)[NX],
+                                              const float (&xn)[NX]) const {
+    float d = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      if (c.hi2[i] > c.lo2[i] && c.pp2[i] > 0.f) {
+        float k = 2.f / (c.hi2[i] - c.lo2[i]);
+        float zo = k * (xo[i] - c.lo2[i]) - 1.f - c.pm2[i], zn = k * (xn[i] - c.lo2[i]) - 1.f - c.pm2[i];
+        d += psc * c.pp2[i] * (k * (xo[i] - xn[i])) * (zo + zn);
+      }
+    }
+    return d;
   }
 
   __device__ __forceinline__ void apply(const KConfig &c, const float (&x)[NX], const float (&dr)[P],
@@ -504,10 +556,15 @@ template <class St>
 __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::NX], int max_it,
                                        float (&H)[St::NH], float (&g)[St::P], int &m,
                                        LMResult &res) {
-  constexpr int P = St::P, NX = St::NX, NH = St::NH;
+  constexpr int P = St::P, NX = St::NX, NH = St::NH, NS = St::NS;
   const KConfig &c = *pc.c;
-  float cst, cd;
-  S.eval(pc, x, H, g, cst, cd, m);
+  float cst, cd, dcd;
+  float r[NS], rt[NS];
+#pragma unroll
+  for (int i = 0; i < NS; i++) r[i] = 0.f;
+  S.eval(pc, x, H, g, cst, cd, m, r, rt, dcd);
+#pragma unroll
+  for (int i = 0; i < NS; i++) r[i] = rt[i];
   float lam = -1.f, nu = 2.f;
   int it = 0, status = PX_MAXITER;
   bool fresh = true, used64 = false;
@@ -599,9 +656,12 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
       Dr[a] = St::template rsel<a>(Dz, m);
     });
     it++;
-    float Ht[NH], gt[P], ct, cdt;
+    float Ht[NH], gt[P], ct, cdt, dct;
     int mt;
-    S.eval(pc, xt, Ht, gt, ct, cdt, mt);
+    S.eval(pc, xt, Ht, gt, ct, cdt, mt, r, rt, dct);
+    // actual decrease from residual differences (accurate where cost - ct
+    // would cancel in FP32)
+    const float drop = dct + S.prior_drop(c, x, xt);
     float pred = 0.f;
 #pragma unroll
     for (int a = 0; a < P; a++) {
@@ -609,9 +669,11 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
 #pragma unroll
       for (int b = 0; b < P; b++) pred -= Dr[a] * H[up<P>(a, b)] * Dr[b];
     }
-    float rho = pred > 0.f ? (cst - ct) / pred : -1.f;
+    float rho = pred > 0.f ? drop / pred : -1.f;
     if (rho > 0.f) {
-      float rel = (cst - ct) / cst;
+      float rel = drop / cst;
+#pragma unroll
+      for (int i = 0; i < NS; i++) r[i] = rt[i];
 #pragma unroll
       for (int i = 0; i < NX; i++) x[i] = xt[i];
 #pragma unroll
@@ -642,7 +704,9 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
 // -------------------------------------------- final covariance (FP64) ---
 // C = s2 (H_FF)^-1 over the free stage-2 variables (not on an outward-
 // pressed bound, non-zero diagonal), in physical units; writes the packed
-// upper triangle and returns var(E[T]) and var(alpha).
+// upper triangle and returns var(E[T]) and var(alpha). FP64 throughout,
+// division-free: Jacobi scaling and the Cholesky pivots use Newton-refined
+// reciprocal square roots, and C = L^-T L^-1 from the triangular inverse.
 __device__ __forceinline__ void laplace_cov(const KConfig &c, const float (&x)[6],
                                             const float (&H)[21], const float (&g)[6], float s2,
                                             float (&cov)[21], bool &cov_ok, double &vE,
@@ -654,15 +718,15 @@ __device__ __forceinline__ void laplace_cov(const KConfig &c, const float (&x)[6
     zc[k] = !act && !(H[up<6>(k, k)] > 0.f);
     fix[k] = act || zc[k];
   }
-  double A[21], d[6];
+  double A[21], rd[6], il[6];
 #pragma unroll
-  for (int i = 0; i < 6; i++) d[i] = fix[i] ? 1.0 : sqrt((double)H[up<6>(i, i)]);
+  for (int i = 0; i < 6; i++) rd[i] = fix[i] ? 1.0 : rsq((double)H[up<6>(i, i)]);
 #pragma unroll
   for (int i = 0; i < 6; i++)
 #pragma unroll
     for (int j = 0; j <= i; j++)
       A[i * (i + 1) / 2 + j] = (fix[i] || fix[j]) ? (i == j ? 1.0 : 0.0)
-                                                   : (double)H[up<6>(i, j)] / (d[i] * d[j]);
+                                                   : (double)H[up<6>(i, j)] * rd[i] * rd[j];
   cov_ok = true;
 #pragma unroll
   for (int j = 0; j < 6; j++) {
@@ -670,50 +734,45 @@ __device__ __forceinline__ void laplace_cov(const KConfig &c, const float (&x)[6
 #pragma unroll
     for (int k = 0; k < j; k++) s -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
     cov_ok = cov_ok && s > 0.0;
-    double L = sqrt(s > 0.0 ? s : 1.0);
-    A[j * (j + 1) / 2 + j] = L;
+    double r = rsq(s > 0.0 ? s : 1.0);
+    il[j] = r;
 #pragma unroll
     for (int i = j + 1; i < 6; i++) {
       double t = A[i * (i + 1) / 2 + j];
 #pragma unroll
       for (int k = 0; k < j; k++) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
-      A[i * (i + 1) / 2 + j] = t / L;
+      A[i * (i + 1) / 2 + j] = t * r;
     }
   }
-  double Cx[6][6];
+  // W = L^-1 (lower), by forward substitution of the unit vectors
+  double W[21];
 #pragma unroll
-  for (int v = 0; v < 6; v++) {
-    double y[6];
+  for (int v = 0; v < 6; v++)
 #pragma unroll
-    for (int i = 0; i < 6; i++) y[i] = (i == v) ? 1.0 : 0.0;
+    for (int i = v; i < 6; i++) {
+      double t = (i == v) ? 1.0 : 0.0;
 #pragma unroll
-    for (int i = 0; i < 6; i++) {
-      double s = y[i];
-#pragma unroll
-      for (int k = 0; k < i; k++) s -= A[i * (i + 1) / 2 + k] * y[k];
-      y[i] = s / A[i * (i + 1) / 2 + i];
+      for (int k = v; k < i; k++) t -= A[i * (i + 1) / 2 + k] * W[k * (k + 1) / 2 + v];
+      W[i * (i + 1) / 2 + v] = t * il[i];
     }
+  double Cx[21];   // packed upper, physical units
+  double sc[6];
 #pragma unroll
-    for (int i = 5; i >= 0; i--) {
-      double s = y[i];
-#pragma unroll
-      for (int k = i + 1; k < 6; k++) s -= A[k * (k + 1) / 2 + i] * y[k];
-      y[i] = s / A[i * (i + 1) / 2 + i];
-    }
-#pragma unroll
-    for (int u = 0; u < 6; u++) {
-      double sc = 0.25 * ((double)c.hi2[u] - c.lo2[u]) * ((double)c.hi2[v] - c.lo2[v]);
-      Cx[u][v] = (fix[u] || fix[v]) ? 0.0 : (double)s2 * y[u] / (d[u] * d[v]) * sc;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 6; k++)
-    if (zc[k]) Cx[k][k] = __longlong_as_double(0x7ff0000000000000ll);
+  for (int i = 0; i < 6; i++) sc[i] = 0.5 * ((double)c.hi2[i] - c.lo2[i]) * rd[i];
   int q = 0;
 #pragma unroll
   for (int a = 0; a < 6; a++)
 #pragma unroll
-    for (int b = a; b < 6; b++) cov[q++] = cov_ok ? (float)Cx[a][b] : __int_as_float(0x7fc00000);
+    for (int b = a; b < 6; b++) {
+      double t = 0.0;
+#pragma unroll
+      for (int k = b; k < 6; k++) t += W[k * (k + 1) / 2 + a] * W[k * (k + 1) / 2 + b];
+      double v = (fix[a] || fix[b]) ? 0.0 : (double)s2 * t * sc[a] * sc[b];
+      if (a == b && zc[a]) v = __longlong_as_double(0x7ff0000000000000ll);
+      Cx[q] = v;
+      cov[q] = cov_ok ? (float)v : __int_as_float(0x7fc00000);
+      q++;
+    }
   double gE[6] = {x[4], 0.0, 1.0 - x[4], 0.0, (double)x[0] - x[2], 0.0};
   vE = 0.0;
   bool inf = false;
@@ -723,11 +782,11 @@ __device__ __forceinline__ void laplace_cov(const KConfig &c, const float (&x)[6
     if (zc[a]) inf = true;
 #pragma unroll
     for (int b = 0; b < 6; b++)
-      if (gE[b] != 0.0 && !zc[a] && !zc[b]) vE += gE[a] * Cx[a][b] * gE[b];
+      if (gE[b] != 0.0 && !zc[a] && !zc[b]) vE += gE[a] * Cx[up<6>(a, b)] * gE[b];
   }
   if (inf) vE = __longlong_as_double(0x7ff0000000000000ll);
   if (!cov_ok) vE = __longlong_as_double(0x7ff8000000000000ll);
-  va = Cx[5][5];
+  va = Cx[up<6>(5, 5)];
 }
 
 // ------------------------------------------------------------ kernel ----
@@ -961,16 +1020,18 @@ __global__ void __launch_bounds__(WPB * 32, LM_MINB) lm_kernel(const __grid_cons
           float s2v = c.weighted ? 1.f : r2.cost / (float)(n2u - nf);
           bool cov_ok = true;
           double vE = 0.0, va = 0.0;
-          if (nf > 0) {
+          bool act_a = (x2[5] <= c.lo2[5] && g2[5] <= 0.f) || (x2[5] >= c.hi2[5] && g2[5] >= 0.f);
+          if (act_a && x2[5] <= c.lo2[5]) {
+            // no thermal signal: E[T] is undefined, so is its posterior
+            cov_ok = false;
+            vE = __longlong_as_double(0x7ff0000000000000ll);
+          } else if (nf > 0) {
             laplace_cov(c, x2, H2, g2, s2v, cov, cov_ok, vE, va);
           } else {
 #pragma unroll
             for (int i = 0; i < 21; i++) cov[i] = 0.f;
-            vE = 0.0;
-            va = 0.0;
           }
           vEf = (float)vE;
-          bool act_a = (x2[5] <= c.lo2[5] && g2[5] <= 0.f) || (x2[5] >= c.hi2[5] && g2[5] >= 0.f);
           double sdE = sqrt(vE), sda = sqrt(va);
           bool ident = cov_ok && isfinite(sdE) && sdE <= (double)c.ident_sd_et &&
                        (double)x2[5] >= (double)c.ident_alpha_snr * sda && !act_a && x2[5] > 0.f;
@@ -1009,7 +1070,8 @@ __global__ void __launch_bounds__(WPB * 32, LM_MINB) lm_kernel(const __grid_cons
       my_it1 += it1;
       my_it2 += it2;
       my_fp64 += (status & PX_F_FP64) ? 1 : 0;
-      my_st[status & 7]++;
+#pragma unroll
+      for (int k = 0; k < 8; k++) my_st[k] += ((status & 7) == k) ? 1ull : 0ull;
     }
   }
   if (lane == 0) {

@@ -139,7 +139,7 @@ def test_ragged_sizes_and_empty(fr, torch, c1, c1_oracle):
     t, tr, L = c1
     ctx = fr.Context(t)
     for n in (0, 1, 7, 33, 129):
-        out = ctx.retrieve(_dev(torch, L[:n].reshape(n, -1), torch.float32),
+        out = ctx.retrieve(_dev(torch, L[:n], torch.float32),
                            _dev(torch, tr.wv_bin[:n].astype(np.int16), torch.int16))
         torch.cuda.synchronize()
         if n:
