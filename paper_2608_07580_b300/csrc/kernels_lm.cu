@@ -552,126 +552,57 @@ struct LMResult {
   float cost, cdata;
 };
 
+// FP64 re-solve of an ill-conditioned step, kept out of line (cold path) so
+// the hot loop stays small in the instruction cache.
+template <int P>
+struct Solve64 {
+  float H[P * (P + 1) / 2], g[P], D[P], dr[P];
+  bool pin[P];
+  float lam, kap;
+};
+
+template <int P>
+__device__ __noinline__ bool solve_fp64(Solve64<P> &q) {
+  return damped_solve<P, double>(q.H, q.g, q.lam, q.D, q.pin, q.dr, q.kap);
+}
+
+// One stage of the fit. The model is evaluated at a single call site per
+// stage (start point, then every trial point) to keep the code compact.
 template <class St>
 __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::NX], int max_it,
                                        float (&H)[St::NH], float (&g)[St::P], int &m,
                                        LMResult &res) {
   constexpr int P = St::P, NX = St::NX, NH = St::NH, NS = St::NS;
   const KConfig &c = *pc.c;
-  float cst, cd, dcd;
-  float r[NS], rt[NS];
+  float cst = 0.f, cd = 0.f, pred = 0.f;
+  float r[NS], rt[NS], xt[NX];
 #pragma unroll
   for (int i = 0; i < NS; i++) r[i] = 0.f;
-  S.eval(pc, x, H, g, cst, cd, m, r, rt, dcd);
 #pragma unroll
-  for (int i = 0; i < NS; i++) r[i] = rt[i];
+  for (int i = 0; i < NX; i++) xt[i] = x[i];
   float lam = -1.f, nu = 2.f;
   int it = 0, status = PX_MAXITER;
-  bool fresh = true, used64 = false;
+  bool fresh = false, used64 = false, first = true;
   bool act[P];
 #pragma unroll
   for (int a = 0; a < P; a++) act[a] = false;
-  while (it < max_it) {
-    if (fresh) {
-      bool small = true;
-      float mx = 0.f;
-      static_for<P>([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        float xv = St::template rsel<a>(x, m);
-        bool lo_hit = xv <= S.template lo_r<a>(c, m);
-        bool hi_hit = St::template has_upper<a>() && xv >= S.template hi_r<a>(c, m);
-        act[a] = (lo_hit && g[a] <= 0.f) || (hi_hit && g[a] >= 0.f);
-        float haa = H[up<P>(a, a)];
-        if (!act[a]) {
-          if (fabsf(g[a]) > c.tol_g * sqrtf(haa * cst)) small = false;
-          mx = fmaxf(mx, haa);
-        }
-      });
-      if (small) { status = PX_CONVERGED; break; }
-      if (lam < 0.f) lam = c.tau0 * mx;
-      fresh = false;
-    }
-    // damping diagonal, projected-Newton solve with re-solve on bound hits
-    float D[P], dr[P];
-    bool pin[P];
-    float mxd = 0.f;
-#pragma unroll
-    for (int a = 0; a < P; a++)
-      if (!act[a]) mxd = fmaxf(mxd, H[up<P>(a, a)]);
-#pragma unroll
-    for (int a = 0; a < P; a++) {
-      D[a] = fmaxf(H[up<P>(a, a)], c.dfloor * mxd);
-      pin[a] = act[a];
-      dr[a] = 0.f;
-    }
-    bool ok = true;
 #pragma unroll 1
-    for (int pass = 0; pass <= P; pass++) {
-      int nf = 0;
-#pragma unroll
-      for (int a = 0; a < P; a++) nf += !pin[a];
-      if (nf == 0) break;
-      float kap = 0.f;
-      ok = damped_solve<P, float>(H, g, lam, D, pin, dr, kap);
-      if (!ok || !(kap <= c.kappa_max)) {
-        ok = damped_solve<P, double>(H, g, lam, D, pin, dr, kap);
-        used64 = true;
-      }
-      if (!ok) break;
-      bool viol = false;
-      static_for<P>([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        if (!pin[a]) {
-          float xv = St::template rsel<a>(x, m);
-          float sc = S.template sc_r<a>(c, m);
-          float lo = S.template lo_r<a>(c, m), hi = S.template hi_r<a>(c, m);
-          float xn = xv + sc * dr[a];
-          if (!(sc > 0.f)) { pin[a] = true; dr[a] = 0.f; viol = true; }
-          else if (xn < lo) { pin[a] = true; dr[a] = (lo - xv) / sc; viol = true; }
-          else if (St::template has_upper<a>() && xn > hi) {
-            pin[a] = true; dr[a] = (hi - xv) / sc; viol = true;
-          }
-        }
-      });
-      if (!viol) break;
-    }
-    if (!ok) {
-      lam *= nu; nu *= 2.f; it++;
-      if (!(lam < 1e30f)) { status = PX_CHOL_FAIL; break; }
-      continue;
-    }
-    float xt[NX];
-    S.apply(c, x, dr, m, xt);
-    float Dz[NX], dmax = 0.f;
-#pragma unroll
-    for (int i = 0; i < NX; i++) {
-      float sc = S.scale(c, i);
-      Dz[i] = sc > 0.f ? (xt[i] - x[i]) / sc : 0.f;
-      dmax = fmaxf(dmax, fabsf(Dz[i]));
-    }
-    if (dmax < c.tol_x) { status = PX_CONVERGED; break; }
-    float Dr[P];
-    static_for<P>([&](auto A_) {
-      constexpr int a = decltype(A_)::value;
-      Dr[a] = St::template rsel<a>(Dz, m);
-    });
-    it++;
+  for (;;) {
+    // ---- evaluate the model, Jacobian and normal equations at xt
     float Ht[NH], gt[P], ct, cdt, dct;
     int mt;
     S.eval(pc, xt, Ht, gt, ct, cdt, mt, r, rt, dct);
-    // actual decrease from residual differences (accurate where cost - ct
-    // would cancel in FP32)
-    const float drop = dct + S.prior_drop(c, x, xt);
-    float pred = 0.f;
-#pragma unroll
-    for (int a = 0; a < P; a++) {
-      pred += 2.f * g[a] * Dr[a];
-#pragma unroll
-      for (int b = 0; b < P; b++) pred -= Dr[a] * H[up<P>(a, b)] * Dr[b];
+    bool accept = first, done = false;
+    float rel = 1.f, rho = 1.f;
+    if (!first) {
+      // actual decrease from residual differences (accurate where cost - ct
+      // would cancel in FP32) against the Gauss-Newton prediction
+      const float drop = dct + S.prior_drop(c, x, xt);
+      rho = pred > 0.f ? drop / pred : -1.f;
+      accept = rho > 0.f;
+      rel = drop / cst;
     }
-    float rho = pred > 0.f ? drop / pred : -1.f;
-    if (rho > 0.f) {
-      float rel = drop / cst;
+    if (accept) {
 #pragma unroll
       for (int i = 0; i < NS; i++) r[i] = rt[i];
 #pragma unroll
@@ -683,16 +614,132 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
       cst = ct;
       cd = cdt;
       m = mt;
-      float f = 2.f * rho - 1.f;
-      f = 1.f - f * f * f;
-      lam *= fmaxf(f, 1.f / 3.f);
-      nu = 2.f;
+      if (!first) {
+        float f = 2.f * rho - 1.f;
+        f = 1.f - f * f * f;
+        lam *= fmaxf(f, 1.f / 3.f);
+        nu = 2.f;
+        if (rel < c.tol_f) { status = PX_CONVERGED; done = true; }
+      }
       fresh = true;
-      if (rel < c.tol_f) { status = PX_CONVERGED; break; }
     } else {
       lam *= nu;
       nu *= 2.f;
     }
+    first = false;
+    if (done) break;
+    // ---- produce the next trial point (or stop)
+    bool have_trial = false;
+#pragma unroll 1
+    while (it < max_it) {
+      if (fresh) {
+        bool small = true;
+        float mx = 0.f;
+        static_for<P>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          float xv = St::template rsel<a>(x, m);
+          bool lo_hit = xv <= S.template lo_r<a>(c, m);
+          bool hi_hit = St::template has_upper<a>() && xv >= S.template hi_r<a>(c, m);
+          act[a] = (lo_hit && g[a] <= 0.f) || (hi_hit && g[a] >= 0.f);
+          float haa = H[up<P>(a, a)];
+          if (!act[a]) {
+            if (fabsf(g[a]) > c.tol_g * sqrtf(haa * cst)) small = false;
+            mx = fmaxf(mx, haa);
+          }
+        });
+        if (small) { status = PX_CONVERGED; break; }
+        if (lam < 0.f) lam = c.tau0 * mx;
+        fresh = false;
+      }
+      // damping diagonal, projected-Newton solve with re-solve on bound hits
+      float D[P], dr[P];
+      bool pin[P];
+      float mxd = 0.f;
+#pragma unroll
+      for (int a = 0; a < P; a++)
+        if (!act[a]) mxd = fmaxf(mxd, H[up<P>(a, a)]);
+#pragma unroll
+      for (int a = 0; a < P; a++) {
+        D[a] = fmaxf(H[up<P>(a, a)], c.dfloor * mxd);
+        pin[a] = act[a];
+        dr[a] = 0.f;
+      }
+      bool ok = true;
+#pragma unroll 1
+      for (int pass = 0; pass <= P; pass++) {
+        int nf = 0;
+#pragma unroll
+        for (int a = 0; a < P; a++) nf += !pin[a];
+        if (nf == 0) break;
+        float kap = 0.f;
+        ok = damped_solve<P, float>(H, g, lam, D, pin, dr, kap);
+        if (!ok || !(kap <= c.kappa_max)) {
+          Solve64<P> q;
+#pragma unroll
+          for (int i = 0; i < NH; i++) q.H[i] = H[i];
+#pragma unroll
+          for (int a = 0; a < P; a++) {
+            q.g[a] = g[a];
+            q.D[a] = D[a];
+            q.pin[a] = pin[a];
+            q.dr[a] = dr[a];
+          }
+          q.lam = lam;
+          ok = solve_fp64<P>(q);
+#pragma unroll
+          for (int a = 0; a < P; a++) dr[a] = q.dr[a];
+          used64 = true;
+        }
+        if (!ok) break;
+        bool viol = false;
+        static_for<P>([&](auto A_) {
+          constexpr int a = decltype(A_)::value;
+          if (!pin[a]) {
+            float xv = St::template rsel<a>(x, m);
+            float sc = S.template sc_r<a>(c, m);
+            float lo = S.template lo_r<a>(c, m), hi = S.template hi_r<a>(c, m);
+            float xn = xv + sc * dr[a];
+            if (!(sc > 0.f)) { pin[a] = true; dr[a] = 0.f; viol = true; }
+            else if (xn < lo) { pin[a] = true; dr[a] = (lo - xv) / sc; viol = true; }
+            else if (St::template has_upper<a>() && xn > hi) {
+              pin[a] = true; dr[a] = (hi - xv) / sc; viol = true;
+            }
+          }
+        });
+        if (!viol) break;
+      }
+      if (!ok) {
+        lam *= nu; nu *= 2.f; it++;
+        if (!(lam < 1e30f)) { status = PX_CHOL_FAIL; break; }
+        continue;
+      }
+      S.apply(c, x, dr, m, xt);
+      float Dz[NX], dmax = 0.f;
+#pragma unroll
+      for (int i = 0; i < NX; i++) {
+        float sc = S.scale(c, i);
+        Dz[i] = sc > 0.f ? (xt[i] - x[i]) / sc : 0.f;
+        dmax = fmaxf(dmax, fabsf(Dz[i]));
+      }
+      if (dmax < c.tol_x) { status = PX_CONVERGED; break; }
+      float Dr[P];
+      static_for<P>([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        Dr[a] = St::template rsel<a>(Dz, m);
+      });
+      // predicted decrease of the Gauss-Newton model: 2 g.D - D.H.D
+      pred = 0.f;
+#pragma unroll
+      for (int a = 0; a < P; a++) {
+        pred += 2.f * g[a] * Dr[a];
+#pragma unroll
+        for (int b = 0; b < P; b++) pred -= Dr[a] * H[up<P>(a, b)] * Dr[b];
+      }
+      it++;
+      have_trial = true;
+      break;
+    }
+    if (!have_trial) break;
   }
   res.iters = it;
   res.status = status;
@@ -707,10 +754,22 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
 // upper triangle and returns var(E[T]) and var(alpha). FP64 throughout,
 // division-free: Jacobi scaling and the Cholesky pivots use Newton-refined
 // reciprocal square roots, and C = L^-T L^-1 from the triangular inverse.
-__device__ __forceinline__ void laplace_cov(const KConfig &c, const float (&x)[6],
-                                            const float (&H)[21], const float (&g)[6], float s2,
-                                            float (&cov)[21], bool &cov_ok, double &vE,
-                                            double &va) {
+struct CovIO {
+  float x[6], H[21], g[6], s2;
+  float cov[21];
+  bool cov_ok;
+  double vE, va;
+};
+
+__device__ __noinline__ void laplace_cov(const KConfig &c, CovIO &io) {
+  const float (&x)[6] = io.x;
+  const float (&H)[21] = io.H;
+  const float (&g)[6] = io.g;
+  const float s2 = io.s2;
+  float (&cov)[21] = io.cov;
+  bool &cov_ok = io.cov_ok;
+  double &vE = io.vE;
+  double &va = io.va;
   bool fix[6], zc[6];
 #pragma unroll
   for (int k = 0; k < 6; k++) {
@@ -1026,7 +1085,18 @@ __global__ void __launch_bounds__(WPB * 32, LM_MINB) lm_kernel(const __grid_cons
             cov_ok = false;
             vE = __longlong_as_double(0x7ff0000000000000ll);
           } else if (nf > 0) {
-            laplace_cov(c, x2, H2, g2, s2v, cov, cov_ok, vE, va);
+            CovIO io;
+#pragma unroll
+            for (int i = 0; i < 6; i++) { io.x[i] = x2[i]; io.g[i] = g2[i]; }
+#pragma unroll
+            for (int i = 0; i < 21; i++) io.H[i] = H2[i];
+            io.s2 = s2v;
+            laplace_cov(c, io);
+#pragma unroll
+            for (int i = 0; i < 21; i++) cov[i] = io.cov[i];
+            cov_ok = io.cov_ok;
+            vE = io.vE;
+            va = io.va;
           } else {
 #pragma unroll
             for (int i = 0; i < 21; i++) cov[i] = 0.f;
