@@ -203,6 +203,20 @@ fire_status_t fire_block_mean(const float *src, int32_t width, int32_t height,
                               int32_t n_bands, int32_t block, float *dst,
                               fire_stream_t stream);
 
+/* Normal equations of one stage at given states, for verification: the
+ * model, Jacobian, J^T W J + P, J^T W r - P (z - pm) and the cost of Eq. (loss)
+ * plus the prior, exactly as one iteration of the fit forms them, in the
+ * fit's z coordinates (Eq. affine); stage 1 uses the reduced simplex basis
+ * (fractions k != m, m = largest fraction, then alpha1, T1).
+ * Device pointers: radiance [n][n_bands], wv_bin [n], states [n][K+2]
+ * (stage 1: x_surf, alpha1, T1) or [n][K+6] (stage 2: x_surf, mu_h, s_h,
+ * mu_s, s_s, eta, alpha); outputs H [n][P][P], g [n][P], cost [n] with
+ * P = K+1 (stage 1) or 6. pri NULL = defaults. */
+fire_status_t fire_normal_equations(fire_ctx_t *ctx, int32_t stage, const float *radiance,
+                                    const uint16_t *wv_bin, const float *states, int64_t n,
+                                    const fire_priors_t *pri, float *H, float *g, float *cost,
+                                    fire_stream_t stream);
+
 /* Counters of the last fire_retrieve on this context (synchronises it). */
 fire_status_t fire_get_stats(fire_ctx_t *ctx, fire_stats_t *stats);
 

@@ -360,3 +360,21 @@ def adam(w, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     lib().orc_adam(C.c_int64(w.size), vp(w.ctypes.data), vp(g.ctypes.data), vp(m.ctypes.data),
                    vp(v.ctypes.data), C.c_int(t), C.c_double(lr), C.c_double(b1), C.c_double(b2),
                    C.c_double(eps))
+
+
+def normal_equations(tables, stage, radiance_row, wv_bin, x, cfg=None):
+    """(H, g, cost) of one stage at state x in the fit's reduced z coordinates."""
+    cfg = cfg or Config(n_endm=tables.n_endm, n_tgrid=tables.n_tgrid)
+    th = _TablesHolder(tables, (cfg.tgrid_lo, cfg.tgrid_hi))
+    c = cfg.to_c()
+    K = tables.n_endm
+    P = K + 1 if stage == 1 else 6
+    L = np.ascontiguousarray(radiance_row, dtype=np.float32)
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    H = np.zeros((P, P))
+    g = np.zeros(P)
+    cost = C.c_double()
+    lib().orc_normal_equations(C.byref(th.c), C.byref(c), C.c_int(stage), C.c_void_p(L.ctypes.data),
+                               C.c_int(int(wv_bin)), C.c_void_p(xx.ctypes.data),
+                               C.c_void_p(H.ctypes.data), C.c_void_p(g.ctypes.data), C.byref(cost))
+    return H, g, cost.value

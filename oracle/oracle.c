@@ -928,3 +928,58 @@ void orc_adam(int64_t n, double *w, const double *g, double *m, double *v, int t
     w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
   }
 }
+
+/* Normal equations of one stage at a given state (for parity tests of the
+ * GPU's Jacobian and reductions): H = J^T W J + psc P and g = J^T W r - psc
+ * P (z - pm) in the reduced z coordinates used by the fit (stage 1:
+ * fractions k != m with m = the largest, then alpha1, T1), plus the cost.
+ * x: stage 1 [x_surf(K), a1, T1]; stage 2 [x_surf(K), mu_h, s_h, mu_s,
+ * s_s, eta, a]. H is [P][P] row-major, g [P]. */
+void orc_normal_equations(const orc_tables_t *t, const orc_config_t *c, int stage,
+                          const float *Lrow, int w, const double *x, double *Hout, double *gout,
+                          double *cost_out) {
+  int K = t->n_endm, nb = t->n_bands;
+  double *Bt = planck_table(t);
+  pix_t *P = (pix_t *)malloc(sizeof(pix_t));
+  pix_tables(P, t, w, Bt);
+  double ws[ORC_MAXB];
+  int n = 0;
+  double sv = 0;
+  for (int b = 0; b < nb; b++) {
+    P->Lobs[b] = Lrow[b];
+    int ok = !(t->sat_level && Lrow[b] >= t->sat_level[b]);
+    double l = P->lam[b];
+    int in = stage == 1 ? (l >= c->win1_lo && l <= c->win1_hi)
+                        : ((l >= c->win2h_lo && l <= c->win2h_hi) || (l >= c->win2s_lo && l <= c->win2s_hi));
+    double var = c->noise_rel * c->noise_rel * P->Lobs[b] * P->Lobs[b] + c->noise_abs * c->noise_abs;
+    ws[b] = (ok && in) ? (c->weighted ? 1.0 / var : 1.0) : 0.0;
+    if (ws[b] > 0) { n++; sv += var; }
+  }
+  double psc = c->weighted ? 1.0 : sv / n;
+  lm_prob_t q1 = {1, K + 2, K, c->lo1, c->hi1, c->pm1, c->pp1, ws, 0, psc};
+  lm_prob_t q2 = {2, 6, 0, c->lo2, c->hi2, c->pm2, c->pp2, ws, 0, psc};
+  const lm_prob_t *q = stage == 1 ? &q1 : &q2;
+  const double *xx = stage == 1 ? x : x + K;
+  if (stage == 2)
+    for (int b = 0; b < nb; b++) P->Ls[b] = solar_term(P, b, x, NULL);
+  int p = q->p;
+  double L[ORC_MAXB], H[ORC_NS1 * ORC_NS1], g[ORC_NS1], E[ORC_NS1 * ORC_NS1];
+  double *J = (double *)malloc(sizeof(double) * nb * p);
+  evaluate(P, q, xx, L, J);
+  *cost_out = cost_of(P, q, xx, L);
+  normal_eq(P, q, xx, L, J, H, g);
+  int m, pr = reduced_basis(q, xx, E, &m);
+  for (int a = 0; a < pr; a++) {
+    gout[a] = 0;
+    for (int i = 0; i < p; i++) gout[a] += E[i * p + a] * g[i];
+    for (int bb = 0; bb < pr; bb++) {
+      double sacc = 0;
+      for (int i = 0; i < p; i++)
+        for (int k = 0; k < p; k++) sacc += E[i * p + a] * H[i * p + k] * E[k * p + bb];
+      Hout[a * pr + bb] = sacc;
+    }
+  }
+  free(J);
+  free(P);
+  free(Bt);
+}

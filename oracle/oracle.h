@@ -89,4 +89,7 @@ double orc_mlp_backward(int B, int Din, int H, int Dout, const double *W1, const
                         double *gb1, double *gW2, double *gb2, double *gW3, double *gb3);
 void orc_adam(int64_t n, double *w, const double *g, double *m, double *v, int t, double lr,
               double b1, double b2, double eps);
+void orc_normal_equations(const orc_tables_t *t, const orc_config_t *c, int stage,
+                          const float *Lrow, int w, const double *x, double *Hout, double *gout,
+                          double *cost_out);
 #endif

@@ -26,6 +26,10 @@ struct fire_ctx {
   // host staging for FIRE_MEM_HOST scenes
   void *d_stage = nullptr;
   size_t stage_bytes = 0;
+  // stage-1 -> stage-2 hand-over, grown on demand
+  float *d_s1x = nullptr;
+  int *d_s1meta = nullptr;
+  int64_t s1_cap = 0;
   int last_launches = 0;
 };
 
@@ -126,6 +130,19 @@ fire_status_t dev_alloc(T **p, size_t bytes) {
   return FIRE_OK;
 }
 
+fire_status_t ensure_s1(fire_ctx *c, int64_t n) {
+  if (n <= c->s1_cap) return FIRE_OK;
+  cudaFree(c->d_s1x);
+  cudaFree(c->d_s1meta);
+  c->d_s1x = nullptr;
+  c->d_s1meta = nullptr;
+  c->s1_cap = 0;
+  fire_status_t e = dev_alloc(&c->d_s1x, (size_t)n * (c->t.K + 2) * 4);
+  if (e == FIRE_OK) e = dev_alloc(&c->d_s1meta, (size_t)n * 4);
+  if (e == FIRE_OK) c->s1_cap = n;
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -215,6 +232,8 @@ void fire_ctx_destroy(fire_ctx_t *ctx) {
   cudaFree(ctx->d_work);
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_stage);
+  cudaFree(ctx->d_s1x);
+  cudaFree(ctx->d_s1meta);
   delete ctx;
 }
 
@@ -281,7 +300,7 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
   do {
     if ((st = dev_alloc(&c->d_image, (size_t)L.total * 4)) != FIRE_OK) break;
     if ((st = dev_alloc(&c->d_wvtab, (size_t)nwv * nb * sizeof(float4))) != FIRE_OK) break;
-    if ((st = dev_alloc(&c->d_work, (size_t)(1 + ST_COUNT) * 8)) != FIRE_OK) break;
+    if ((st = dev_alloc(&c->d_work, (size_t)(2 + ST_COUNT) * 8)) != FIRE_OK) break;
     if ((st = dev_alloc(&c->d_err, sizeof(int))) != FIRE_OK) break;
     if ((st = dev_alloc(&raw, nraw * 4)) != FIRE_OK) break;
     if (tb->sat_level) {
@@ -343,7 +362,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   if (!priors_valid(*pri, c->t.K)) return FIRE_ERR_ARG;
   if (pri->init_mode == FIRE_INIT_GIVEN && !pri->init_state) return FIRE_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  CK(cudaMemsetAsync(c->d_work, 0, (size_t)(1 + ST_COUNT) * 8, st));
+  CK(cudaMemsetAsync(c->d_work, 0, (size_t)(2 + ST_COUNT) * 8, st));
   c->last_launches = 0;
   if (sc->n_pix == 0) return FIRE_OK;
   if (!sc->radiance || !sc->wv_bin) return FIRE_ERR_ARG;
@@ -357,8 +376,14 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   p.s.n_pix = n;
   p.s.gate = sc->gate_mode == FIRE_FIT_HFDI;
   p.w.counter = c->d_work;
-  p.w.stats = c->d_work + 1;
+  p.w.stats = c->d_work + 2;
   p.w.err = c->d_err;
+  {
+    fire_status_t e = ensure_s1(c, n);
+    if (e != FIRE_OK) return e;
+  }
+  p.w.s1x = c->d_s1x;
+  p.w.s1meta = c->d_s1meta;
 
   // per-pixel output sizes (bytes), in the order staged for host scenes
   const size_t szf = (size_t)n * 4;
@@ -381,7 +406,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     int blocks = 0;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
     CK(launch_lm(p, c->num_sms, st, &blocks));
-    c->last_launches = 1;
+    c->last_launches = 2;
     return FIRE_OK;
   }
 
@@ -429,7 +454,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   int blocks = 0;
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   CK(launch_lm(p, c->num_sms, st, &blocks));
-  c->last_launches = 1;
+  c->last_launches = 2;
   struct { void *h; void *d; size_t b; } back[] = {
       {out->state, o_state, s_state}, {out->ET, o_ET, szf}, {out->sdT, o_sdT, szf},
       {out->alpha, o_alpha, szf}, {out->var_ET, o_var, szf}, {out->cost, o_cost, szf},
@@ -445,13 +470,13 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
 
 fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   if (!c || !s) return FIRE_ERR_ARG;
-  unsigned long long h[1 + ST_COUNT];
+  unsigned long long h[2 + ST_COUNT];
   CK(cudaDeviceSynchronize());
   CK(cudaMemcpy(h, c->d_work, sizeof(h), cudaMemcpyDeviceToHost));
   int err = 0;
   CK(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   memset(s, 0, sizeof(*s));
-  const unsigned long long *v = h + 1;
+  const unsigned long long *v = h + 2;
   s->n_pixels = v[ST_NPIX];
   s->sum_it1 = v[ST_IT1];
   s->sum_it2 = v[ST_IT2];
@@ -481,6 +506,30 @@ fire_status_t fire_forward(fire_ctx_t *c, int32_t mode, const float *state, cons
   if (!state || !wv || !L_out) return FIRE_ERR_ARG;
   return cuda_status(launch_forward(c->t, mode, state, wv, n, nrel, nabs, seed, sid, pix0, L_out,
                                     (cudaStream_t)stream));
+}
+
+fire_status_t fire_normal_equations(fire_ctx_t *c, int32_t stage, const float *radiance,
+                                    const uint16_t *wv_bin, const float *states, int64_t n,
+                                    const fire_priors_t *pri, float *H, float *g, float *cost,
+                                    fire_stream_t stream) {
+  if (!c || (stage != 1 && stage != 2) || n < 0) return FIRE_ERR_ARG;
+  if (n == 0) return FIRE_OK;
+  if (!radiance || !wv_bin || !states || !H || !g || !cost) return FIRE_ERR_ARG;
+  fire_priors_t pd;
+  if (!pri) {
+    fire_default_priors(&pd, c->t.K, c->t.nt, c->t.tglo, c->t.tglo + c->t.tgstep * (c->t.nt - 1));
+    pri = &pd;
+  }
+  if (!priors_valid(*pri, c->t.K)) return FIRE_ERR_ARG;
+  LMLaunch p;
+  memset(&p, 0, sizeof(p));
+  p.t = c->t;
+  fill_kconfig(p.c, c->cfg, *pri, c->t.K);
+  p.s.n_pix = n;
+  p.s.rad = radiance;
+  p.s.wv = wv_bin;
+  p.w.err = c->d_err;
+  return cuda_status(launch_normal_eq(p, stage, states, H, g, cost, (cudaStream_t)stream));
 }
 
 fire_status_t fire_block_mean(const float *src, int32_t w, int32_t h, int32_t nb, int32_t blk,

@@ -77,9 +77,11 @@ enum : int {
 };
 
 struct KWork {
-  unsigned long long *counter;  // work-claim counter (zeroed before launch)
+  unsigned long long *counter;  // [2] work-claim counters of the two stage kernels (zeroed)
   unsigned long long *stats;    // [ST_COUNT]
   int *err;                     // bounded-wait failure flag
+  float *s1x;                   // [n_pix][K+2] stage-1 result handed to stage 2
+  int *s1meta;                  // [n_pix] status bits | 256 if the pixel goes on to stage 2
 };
 
 struct LMLaunch {
@@ -97,6 +99,8 @@ cudaError_t launch_build_tables(const KTables &t, const float *wl, const float *
                                 const float win[6], cudaStream_t st);
 cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used);
 size_t lm_smem_bytes(const KTables &t);
+cudaError_t launch_normal_eq(const LMLaunch &p, int stage, const float *states, float *H, float *g,
+                             float *cost, cudaStream_t st);
 cudaError_t launch_forward(const KTables &t, int mode, const float *state, const uint16_t *wv,
                            int64_t n, float noise_rel, float noise_abs, uint64_t seed,
                            uint64_t stream_id, int64_t pix0, float *out, cudaStream_t st);

@@ -31,8 +31,11 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClaim = 4;          // pixels claimed per atomic
-#ifndef LM_MINB
-#define LM_MINB 1
+#ifndef LM1_MINB
+#define LM1_MINB 1
+#endif
+#ifndef LM2_MINB
+#define LM2_MINB 1
 #endif
 
 template <int N>
@@ -848,13 +851,153 @@ __device__ __noinline__ void laplace_cov(const KConfig &c, CovIO &io) {
   va = Cx[up<6>(5, 5)];
 }
 
-// ------------------------------------------------------------ kernel ----
+// ------------------------------------------------------------ kernels ---
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 
-template <int K, int S1, int S2, int WPB>
-__global__ void __launch_bounds__(WPB * 32, LM_MINB) lm_kernel(const __grid_constant__ LMLaunch p) {
+// Stage the per-CTA table image into shared memory with 1D bulk copies
+// completing on one mbarrier. The wait is bounded: on timeout the error flag
+// is set, the copies still in flight are waited for (bounded again) and the
+// CTA leaves (returns false).
+__device__ __forceinline__ bool stage_tables(const KTables &t, float *smem, unsigned long long *bar,
+                                             int *err) {
+  const unsigned bytes = (unsigned)t.lay.total * 4u;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    const unsigned chunk = 32768u;
+    for (unsigned off = 0; off < bytes; off += chunk) {
+      unsigned n = bytes - off < chunk ? bytes - off : chunk;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+          ::"r"(smem_u32(reinterpret_cast<char *>(smem) + off)),
+          "l"(reinterpret_cast<const char *>(t.image) + off), "r"(n), "r"(smem_u32(bar))
+          : "memory");
+    }
+  }
+  __syncthreads();
+  unsigned done = 0;
+  for (long long spin = 0; spin < (1ll << 26) && !done; spin++)
+    asm volatile(
+        "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
+        : "=r"(done) : "r"(smem_u32(bar)) : "memory");
+  if (__syncthreads_and(done)) return true;
+  if (threadIdx.x == 0) atomicExch(err, 1);
+  for (long long spin = 0; spin < (1ll << 26) && !done; spin++)
+    asm volatile(
+        "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
+        : "=r"(done) : "r"(smem_u32(bar)) : "memory");
+  return false;
+}
+
+// pixel-claim helper: lane 0 takes kClaim pixels from a global counter
+__device__ __forceinline__ long long claim(unsigned long long *ctr, int lane) {
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(ctr, (unsigned long long)kClaim);
+  return (long long)__shfl_sync(kFull, base, 0);
+}
+
+// stage-1 per-pixel setup: radiance, mask m(lambda) (saturation) x window,
+// weights and the prior scale (mean noise variance of the used bands)
+template <int K, int S1>
+__device__ __forceinline__ int setup1(Stage1<K, S1> &s1, const PixCtx &pc, const float *row) {
+  const KTables &t = *pc.t;
+  const KConfig &c = *pc.c;
+  float nv = 0.f;
+  int nu = 0;
+#pragma unroll
+  for (int s = 0; s < S1; s++) {
+    int bi = pc.lane + 32 * s;
+    s1.Lobs[s] = 0.f;
+    s1.w[s] = 0.f;
+    if (bi < t.n1) {
+      int b = t.b1lo + bi;
+      float L = __ldg(row + b);
+      bool ok = pc.img[t.lay.off_win1 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
+      float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
+      s1.Lobs[s] = L;
+      s1.w[s] = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
+      if (ok) { nv += var; nu++; }
+    }
+  }
+  nv = warp_sum1(nv);
+  nu = __reduce_add_sync(kFull, nu);
+  s1.psc = c.weighted ? 1.f : nv / (float)max(nu, 1);
+  s1.sf = 0.5f * (c.hi1[0] - c.lo1[0]);
+  s1.sa = 0.5f * (c.hi1[K] - c.lo1[K]);
+  s1.sT = 0.5f * (c.hi1[K + 1] - c.lo1[K + 1]);
+  return nu;
+}
+
+// stage-2 band count (mask x window) without building the stage state
+__device__ __forceinline__ int count2(const PixCtx &pc, const float *row) {
+  const KTables &t = *pc.t;
+  int nu = 0;
+  for (int bi = pc.lane; bi < t.n2; bi += 32) {
+    int b = t.b2lo + bi;
+    float L = __ldg(row + b);
+    nu += (pc.img[t.lay.off_win2 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b))) ? 1 : 0;
+  }
+  return __reduce_add_sync(kFull, nu);
+}
+
+// stage-2 per-pixel setup: y = L - Ls(x_surf) (solar term fixed, Eq. solar),
+// tau_up, weights, prior scale
+template <int K, int S2>
+__device__ __forceinline__ int setup2(Stage2<S2> &s2, const PixCtx &pc, const float *row,
+                                      const float (&xs)[K]) {
+  const KTables &t = *pc.t;
+  const KConfig &c = *pc.c;
+  float nv = 0.f;
+  int nu = 0;
+#pragma unroll
+  for (int s = 0; s < S2; s++) {
+    int bi = pc.lane + 32 * s;
+    s2.y[s] = 0.f;
+    s2.tu[s] = 0.f;
+    s2.w[s] = 0.f;
+    if (bi < t.n2) {
+      int b = t.b2lo + bi;
+      float L = __ldg(row + b);
+      bool ok = pc.img[t.lay.off_win2 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
+      float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
+      float4 q = __ldg(pc.wvrow + b);
+      float rho = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; k++) rho = fmaf(xs[k], pc.img[t.lay.off_endm + k * t.nb + b], rho);
+      s2.y[s] = L - (q.y + q.x * rho / (1.f - q.z * rho));
+      s2.tu[s] = q.w;
+      s2.w[s] = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
+      if (ok) { nv += var; nu++; }
+    }
+  }
+  nv = warp_sum1(nv);
+  nu = __reduce_add_sync(kFull, nu);
+  s2.psc = c.weighted ? 1.f : nv / (float)max(nu, 1);
+#pragma unroll
+  for (int i = 0; i < 6; i++) s2.s[i] = 0.5f * (c.hi2[i] - c.lo2[i]);
+  return nu;
+}
+
+__device__ __forceinline__ void flush_stats(unsigned long long *cstat, const unsigned long long *mine,
+                                            unsigned long long *gstats, int lane) {
+  if (lane == 0)
+    for (int i = 0; i < ST_COUNT; i++)
+      if (mine[i]) atomicAdd(&cstat[i], mine[i]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
+    if (cstat[i]) atomicAdd(gstats + i, cstat[i]);
+}
+
+constexpr int kFitted = 256;   // scratch flag: pixel goes on to stage 2
+
+// ---- stage 1: checks, HFDI gate, stage-1 fit -> scratch
+template <int K, int S1, int WPB>
+__global__ void __launch_bounds__(WPB * 32, LM1_MINB) lm_stage1_kernel(const __grid_constant__ LMLaunch p) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ unsigned long long cstat[ST_COUNT];
@@ -862,45 +1005,7 @@ __global__ void __launch_bounds__(WPB * 32, LM_MINB) lm_kernel(const __grid_cons
   const KConfig &c = p.c;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
-
-  // stage the table image into shared memory with 1D bulk copies
-  const unsigned bytes = (unsigned)t.lay.total * 4u;
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(smem_u32(&bar)), "r"(bytes) : "memory");
-    const unsigned chunk = 32768u;
-    for (unsigned off = 0; off < bytes; off += chunk) {
-      unsigned n = bytes - off < chunk ? bytes - off : chunk;
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-          ::"r"(smem_u32(reinterpret_cast<char *>(smem) + off)),
-          "l"(reinterpret_cast<const char *>(t.image) + off), "r"(n), "r"(smem_u32(&bar))
-          : "memory");
-    }
-  }
-  __syncthreads();
-  {
-    unsigned done = 0;
-    for (long long spin = 0; spin < (1ll << 26) && !done; spin++) {
-      asm volatile(
-          "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
-          : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
-    }
-    if (!__syncthreads_and(done)) {
-      if (threadIdx.x == 0) atomicExch(p.w.err, 1);
-      // wait (bounded) for the copies still in flight before leaving
-      for (long long spin = 0; spin < (1ll << 26) && !done; spin++) {
-        asm volatile(
-            "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
-            : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
-      }
-      return;
-    }
-  }
-
+  if (!stage_tables(t, smem, &bar, p.w.err)) return;
   PixCtx pc;
   pc.t = &t;
   pc.c = &c;
@@ -908,95 +1013,39 @@ __global__ void __launch_bounds__(WPB * 32, LM_MINB) lm_kernel(const __grid_cons
   pc.wsc = smem + t.lay.total + warp * kMaxTgrid * kScratchPerNode;
   pc.lane = lane;
   const int NSx = K + 8;
-  unsigned long long my_it1 = 0, my_it2 = 0, my_fp64 = 0, my_b1 = 0, my_b2 = 0, my_nb2 = 0;
-  unsigned long long my_n = 0, my_st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-
+  unsigned long long mine[ST_COUNT];
+#pragma unroll
+  for (int i = 0; i < ST_COUNT; i++) mine[i] = 0ull;
   for (;;) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(p.w.counter, (unsigned long long)kClaim);
-    base = __shfl_sync(kFull, base, 0);
-    if (base >= (unsigned long long)p.s.n_pix) break;
-    for (int cidx = 0; cidx < kClaim; cidx++) {
-      const long long pix = (long long)base + cidx;
+    const long long base = claim(p.w.counter, lane);
+    if (base >= p.s.n_pix) break;
+    for (int ci = 0; ci < kClaim; ci++) {
+      const long long pix = base + ci;
       if (pix >= p.s.n_pix) break;
       const float *row = p.s.rad + pix * t.nb;
       const int wvb = p.s.wv[pix];
       const bool wv_ok = wvb < t.nwv;   // an out-of-range bin is an invalid input
       pc.wvrow = t.wvtab + (size_t)(wv_ok ? wvb : 0) * t.nb;
-      pc.node_evals = 0;
-      int status = 0, it1 = 0, it2 = 0;
-      // finite check over all bands
       bool fin = true;
       for (int b = lane; b < t.nb; b += 32) fin = fin && isfinite(__ldg(row + b));
       fin = __all_sync(kFull, fin) && wv_ok;
-      float Lh = __ldg(row + t.bh), Ll = __ldg(row + t.bl);
+      const float Lh = __ldg(row + t.bh), Ll = __ldg(row + t.bl);
       float hf = (Lh - Ll) / (Lh + Ll);
-      float xs[NSx];
-#pragma unroll
-      for (int i = 0; i < NSx; i++) xs[i] = __int_as_float(0x7fc00000);
-      float ET = xs[0], sdT = xs[0], alpha = xs[0], cost = xs[0], rms = xs[0], vEf = xs[0];
-      float cov[21];
-#pragma unroll
-      for (int i = 0; i < 21; i++) cov[i] = xs[0];
+      int status = 0, it1 = 0;
+      bool fitted = false;
+      float x1[K + 2];
       if (!fin) {
         status = PX_NONFINITE;
-        hf = xs[0];
+        hf = __int_as_float(0x7fc00000);
       } else if (p.s.gate && !(hf >= c.hfdi_thresh)) {
         status = PX_NOT_CANDIDATE;
       } else {
-        // ---- stage 1 setup: radiance, mask m(lambda), weights, prior scale
         Stage1<K, S1> s1;
-        float nv1 = 0.f;
-        int n1u = 0;
-#pragma unroll
-        for (int s = 0; s < S1; s++) {
-          int bi = lane + 32 * s;
-          s1.Lobs[s] = 0.f;
-          s1.w[s] = 0.f;
-          if (bi < t.n1) {
-            int b = t.b1lo + bi;
-            float L = __ldg(row + b);
-            bool ok = pc.img[t.lay.off_win1 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
-            float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
-            s1.Lobs[s] = L;
-            s1.w[s] = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
-            if (ok) { nv1 += var; n1u++; }
-          }
-        }
-        nv1 = warp_sum1(nv1);
-        n1u = __reduce_add_sync(kFull, n1u);
-        s1.psc = c.weighted ? 1.f : nv1 / (float)max(n1u, 1);
-        s1.sf = 0.5f * (c.hi1[0] - c.lo1[0]);
-        s1.sa = 0.5f * (c.hi1[K] - c.lo1[K]);
-        s1.sT = 0.5f * (c.hi1[K + 1] - c.lo1[K + 1]);
-        // stage-2 band count (needed for the masked test)
-        Stage2<S2> s2;
-        float nv2 = 0.f;
-        int n2u = 0;
-#pragma unroll
-        for (int s = 0; s < S2; s++) {
-          int bi = lane + 32 * s;
-          s2.y[s] = 0.f;
-          s2.tu[s] = 0.f;
-          s2.w[s] = 0.f;
-          if (bi < t.n2) {
-            int b = t.b2lo + bi;
-            float L = __ldg(row + b);
-            bool ok = pc.img[t.lay.off_win2 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
-            float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
-            s2.y[s] = L;
-            s2.w[s] = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
-            if (ok) { nv2 += var; n2u++; }
-          }
-        }
-        nv2 = warp_sum1(nv2);
-        n2u = __reduce_add_sync(kFull, n2u);
-        s2.psc = c.weighted ? 1.f : nv2 / (float)max(n2u, 1);
+        const int n1u = setup1(s1, pc, row);
+        const int n2u = count2(pc, row);
         if (n1u <= K + 2 || n2u <= 6) {
           status = PX_ALL_MASKED;
         } else {
-          // ---- stage 1
-          float x1[K + 2];
           const float *ini = p.s.init ? p.s.init + pix * NSx : nullptr;
           if (ini) {
 #pragma unroll
@@ -1017,105 +1066,165 @@ __global__ void __launch_bounds__(WPB * 32, LM_MINB) lm_kernel(const __grid_cons
           it1 = r1.iters;
           if (r1.status == PX_MAXITER) status |= PX_F_S1_MAXITER;
           if (r1.used64) status |= PX_F_FP64;
-          my_b1 += (unsigned long long)(r1.iters + 1) * (unsigned long long)t.n1;
-          // ---- stage 2 setup: y = L - Ls(x_surf), tau_up
-#pragma unroll
-          for (int s = 0; s < S2; s++) {
-            int bi = lane + 32 * s;
-            if (bi < t.n2) {
-              int b = t.b2lo + bi;
-              float4 q = __ldg(pc.wvrow + b);
-              float rho = 0.f;
-#pragma unroll
-              for (int k = 0; k < K; k++) rho = fmaf(x1[k], pc.img[t.lay.off_endm + k * t.nb + b], rho);
-              float Ls = q.y + q.x * rho / (1.f - q.z * rho);
-              s2.y[s] -= Ls;
-              s2.tu[s] = q.w;
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < 6; i++) s2.s[i] = 0.5f * (c.hi2[i] - c.lo2[i]);
-          float x2[6];
-          if (ini) {
-#pragma unroll
-            for (int i = 0; i < 6; i++) x2[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
-          } else {
-            float T1 = x1[K + 1];
-            x2[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
-            x2[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
-            x2[1] = fminf(fmaxf(c.init_sigma, c.lo2[1]), c.hi2[1]);
-            x2[3] = fminf(fmaxf(c.init_sigma, c.lo2[3]), c.hi2[3]);
-            x2[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
-            float e = x2[0] > x2[2] ? (T1 - x2[2]) / (x2[0] - x2[2]) : 0.5f;
-            x2[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
-          }
-          float H2[21], g2[6];
-          int m2;
-          LMResult r2;
-          lm_fit(s2, pc, x2, c.max_it2, H2, g2, m2, r2);
-          it2 = r2.iters;
-          if (r2.used64) status |= PX_F_FP64;
-          status |= r2.status;
-          my_b2 += (unsigned long long)(r2.iters + 1) * (unsigned long long)t.n2;
-          my_nb2 += (unsigned long long)pc.node_evals * (unsigned long long)t.n2;
-          // ---- outputs
-#pragma unroll
-          for (int i = 0; i < K + 2; i++) xs[i] = x1[i];
-#pragma unroll
-          for (int i = 0; i < 6; i++) xs[K + 2 + i] = x2[i];
-          ET = x2[4] * x2[0] + (1.f - x2[4]) * x2[2];
-          float dmu = x2[0] - x2[2];
-          sdT = sqrtf(x2[4] * x2[1] * x2[1] + (1.f - x2[4]) * x2[3] * x2[3] +
-                      x2[4] * (1.f - x2[4]) * dmu * dmu);
-          alpha = x2[5];
-          cost = r2.cost;
-          rms = sqrtf(r2.cdata / (float)n2u);
-          int nf = 0;
-#pragma unroll
-          for (int k = 0; k < 6; k++) {
-            bool act = (x2[k] <= c.lo2[k] && g2[k] <= 0.f) || (x2[k] >= c.hi2[k] && g2[k] >= 0.f);
-            nf += (!act && H2[up<6>(k, k)] > 0.f);
-          }
-          float s2v = c.weighted ? 1.f : r2.cost / (float)(n2u - nf);
-          bool cov_ok = true;
-          double vE = 0.0, va = 0.0;
-          bool act_a = (x2[5] <= c.lo2[5] && g2[5] <= 0.f) || (x2[5] >= c.hi2[5] && g2[5] >= 0.f);
-          if (act_a && x2[5] <= c.lo2[5]) {
-            // no thermal signal: E[T] is undefined, so is its posterior
-            cov_ok = false;
-            vE = __longlong_as_double(0x7ff0000000000000ll);
-          } else if (nf > 0) {
-            CovIO io;
-#pragma unroll
-            for (int i = 0; i < 6; i++) { io.x[i] = x2[i]; io.g[i] = g2[i]; }
-#pragma unroll
-            for (int i = 0; i < 21; i++) io.H[i] = H2[i];
-            io.s2 = s2v;
-            laplace_cov(c, io);
-#pragma unroll
-            for (int i = 0; i < 21; i++) cov[i] = io.cov[i];
-            cov_ok = io.cov_ok;
-            vE = io.vE;
-            va = io.va;
-          } else {
-#pragma unroll
-            for (int i = 0; i < 21; i++) cov[i] = 0.f;
-          }
-          vEf = (float)vE;
-          double sdE = sqrt(vE), sda = sqrt(va);
-          bool ident = cov_ok && isfinite(sdE) && sdE <= (double)c.ident_sd_et &&
-                       (double)x2[5] >= (double)c.ident_alpha_snr * sda && !act_a && x2[5] > 0.f;
-          if (!ident) status |= PX_F_NOT_IDENT;
+          mine[ST_BAND1] += (unsigned long long)(r1.iters + 1) * (unsigned long long)t.n1;
+          mine[ST_IT1] += it1;
+          fitted = true;
         }
       }
-      // ---- write this pixel (lanes spread the stores)
-      if (p.o.state)
-        for (int i = lane; i < NSx; i += 32) {
-          float v = xs[0];
+      // hand-over to stage 2, or the final outputs of a pixel that is not fitted
+      if (lane == 0) {
+        p.w.s1meta[pix] = status | (fitted ? kFitted : 0);
+        if (p.o.hfdi) p.o.hfdi[pix] = hf;
+        if (p.o.iters) p.o.iters[2 * pix] = (uint16_t)it1;
+      }
+      if (fitted) {
+        if (lane < K + 2) {
+          float v = x1[0];
 #pragma unroll
-          for (int k = 0; k < NSx; k++) v = (k == i) ? xs[k] : v;
-          p.o.state[pix * NSx + i] = v;
+          for (int k = 0; k < K + 2; k++) v = (k == lane) ? x1[k] : v;
+          p.w.s1x[pix * (K + 2) + lane] = v;
         }
+      } else {
+        const float nan = __int_as_float(0x7fc00000);
+        if (p.o.state)
+          for (int i = lane; i < NSx; i += 32) p.o.state[pix * NSx + i] = nan;
+        if (p.o.cov && lane < 21) p.o.cov[pix * 21 + lane] = nan;
+        if (lane == 0) {
+          if (p.o.ET) p.o.ET[pix] = nan;
+          if (p.o.sdT) p.o.sdT[pix] = nan;
+          if (p.o.alpha) p.o.alpha[pix] = nan;
+          if (p.o.var_ET) p.o.var_ET[pix] = nan;
+          if (p.o.cost) p.o.cost[pix] = nan;
+          if (p.o.rms) p.o.rms[pix] = nan;
+          if (p.o.status) p.o.status[pix] = (uint8_t)status;
+          if (p.o.iters) p.o.iters[2 * pix + 1] = 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) mine[ST_STATUS0 + k] += ((status & 7) == k) ? 1ull : 0ull;
+      }
+      mine[ST_NPIX] += 1;
+    }
+  }
+  flush_stats(cstat, mine, p.w.stats, lane);
+}
+
+// ---- stage 2: mixture fit from the stage-1 hand-over, covariance, outputs
+template <int K, int S2, int WPB>
+__global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __grid_constant__ LMLaunch p) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ unsigned long long cstat[ST_COUNT];
+  const KTables &t = p.t;
+  const KConfig &c = p.c;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
+  if (!stage_tables(t, smem, &bar, p.w.err)) return;
+  PixCtx pc;
+  pc.t = &t;
+  pc.c = &c;
+  pc.img = smem;
+  pc.wsc = smem + t.lay.total + warp * kMaxTgrid * kScratchPerNode;
+  pc.lane = lane;
+  const int NSx = K + 8;
+  unsigned long long mine[ST_COUNT];
+#pragma unroll
+  for (int i = 0; i < ST_COUNT; i++) mine[i] = 0ull;
+  for (;;) {
+    const long long base = claim(p.w.counter + 1, lane);
+    if (base >= p.s.n_pix) break;
+    for (int ci = 0; ci < kClaim; ci++) {
+      const long long pix = base + ci;
+      if (pix >= p.s.n_pix) break;
+      const int meta = p.w.s1meta[pix];
+      if (!(meta & kFitted)) continue;
+      int status = meta & 0xff;
+      const float *row = p.s.rad + pix * t.nb;
+      pc.wvrow = t.wvtab + (size_t)p.s.wv[pix] * t.nb;
+      pc.node_evals = 0;
+      float x1[K + 2];
+#pragma unroll
+      for (int i = 0; i < K + 2; i++) x1[i] = p.w.s1x[pix * (K + 2) + i];
+      float xs[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) xs[k] = x1[k];
+      Stage2<S2> s2;
+      const int n2u = setup2<K, S2>(s2, pc, row, xs);
+      float x2[6];
+      const float *ini = p.s.init ? p.s.init + pix * NSx : nullptr;
+      if (ini) {
+#pragma unroll
+        for (int i = 0; i < 6; i++) x2[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
+      } else {
+        float T1 = x1[K + 1];
+        x2[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
+        x2[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
+        x2[1] = fminf(fmaxf(c.init_sigma, c.lo2[1]), c.hi2[1]);
+        x2[3] = fminf(fmaxf(c.init_sigma, c.lo2[3]), c.hi2[3]);
+        x2[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
+        float e = x2[0] > x2[2] ? (T1 - x2[2]) / (x2[0] - x2[2]) : 0.5f;
+        x2[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
+      }
+      float H2[21], g2[6];
+      int m2;
+      LMResult r2;
+      lm_fit(s2, pc, x2, c.max_it2, H2, g2, m2, r2);
+      if (r2.used64) status |= PX_F_FP64;
+      status |= r2.status;
+      mine[ST_IT2] += r2.iters;
+      mine[ST_BAND2] += (unsigned long long)(r2.iters + 1) * (unsigned long long)t.n2;
+      mine[ST_NODEBAND2] += (unsigned long long)pc.node_evals * (unsigned long long)t.n2;
+      // moment matching (Sec. 2.3)
+      const float ET = x2[4] * x2[0] + (1.f - x2[4]) * x2[2];
+      const float dmu = x2[0] - x2[2];
+      const float sdT = sqrtf(x2[4] * x2[1] * x2[1] + (1.f - x2[4]) * x2[3] * x2[3] +
+                              x2[4] * (1.f - x2[4]) * dmu * dmu);
+      const float rms = sqrtf(r2.cdata / (float)n2u);
+      int nf = 0;
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        bool act = (x2[k] <= c.lo2[k] && g2[k] <= 0.f) || (x2[k] >= c.hi2[k] && g2[k] >= 0.f);
+        nf += (!act && H2[up<6>(k, k)] > 0.f);
+      }
+      const float s2v = c.weighted ? 1.f : r2.cost / (float)(n2u - nf);
+      float cov[21];
+      bool cov_ok = true;
+      double vE = 0.0, va = 0.0;
+      const bool act_a = (x2[5] <= c.lo2[5] && g2[5] <= 0.f) || (x2[5] >= c.hi2[5] && g2[5] >= 0.f);
+      if (act_a && x2[5] <= c.lo2[5]) {
+        // no thermal signal: E[T] is undefined, so is its posterior
+        cov_ok = false;
+        vE = __longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+        for (int i = 0; i < 21; i++) cov[i] = __int_as_float(0x7fc00000);
+      } else if (nf > 0) {
+        CovIO io;
+#pragma unroll
+        for (int i = 0; i < 6; i++) { io.x[i] = x2[i]; io.g[i] = g2[i]; }
+#pragma unroll
+        for (int i = 0; i < 21; i++) io.H[i] = H2[i];
+        io.s2 = s2v;
+        laplace_cov(c, io);
+#pragma unroll
+        for (int i = 0; i < 21; i++) cov[i] = io.cov[i];
+        cov_ok = io.cov_ok;
+        vE = io.vE;
+        va = io.va;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 21; i++) cov[i] = 0.f;
+      }
+      const double sdE = sqrt(vE), sda = sqrt(va);
+      const bool ident = cov_ok && isfinite(sdE) && sdE <= (double)c.ident_sd_et &&
+                         (double)x2[5] >= (double)c.ident_alpha_snr * sda && !act_a && x2[5] > 0.f;
+      if (!ident) status |= PX_F_NOT_IDENT;
+      if (p.o.state && lane < NSx) {
+        float v = x1[0];
+#pragma unroll
+        for (int k = 0; k < K + 2; k++) v = (k == lane) ? x1[k] : v;
+#pragma unroll
+        for (int k = 0; k < 6; k++) v = (K + 2 + k == lane) ? x2[k] : v;
+        p.o.state[pix * NSx + lane] = v;
+      }
       if (p.o.cov && lane < 21) {
         float v = cov[0];
 #pragma unroll
@@ -1125,46 +1234,91 @@ __global__ void __launch_bounds__(WPB * 32, LM_MINB) lm_kernel(const __grid_cons
       if (lane == 0) {
         if (p.o.ET) p.o.ET[pix] = ET;
         if (p.o.sdT) p.o.sdT[pix] = sdT;
-        if (p.o.alpha) p.o.alpha[pix] = alpha;
-        if (p.o.var_ET) p.o.var_ET[pix] = vEf;
-        if (p.o.cost) p.o.cost[pix] = cost;
+        if (p.o.alpha) p.o.alpha[pix] = x2[5];
+        if (p.o.var_ET) p.o.var_ET[pix] = (float)vE;
+        if (p.o.cost) p.o.cost[pix] = r2.cost;
         if (p.o.rms) p.o.rms[pix] = rms;
-        if (p.o.hfdi) p.o.hfdi[pix] = hf;
         if (p.o.status) p.o.status[pix] = (uint8_t)status;
-        if (p.o.iters) {
-          p.o.iters[2 * pix] = (uint16_t)it1;
-          p.o.iters[2 * pix + 1] = (uint16_t)it2;
-        }
+        if (p.o.iters) p.o.iters[2 * pix + 1] = (uint16_t)r2.iters;
       }
-      my_n++;
-      my_it1 += it1;
-      my_it2 += it2;
-      my_fp64 += (status & PX_F_FP64) ? 1 : 0;
+      mine[ST_FP64] += (status & PX_F_FP64) ? 1ull : 0ull;
 #pragma unroll
-      for (int k = 0; k < 8; k++) my_st[k] += ((status & 7) == k) ? 1ull : 0ull;
+      for (int k = 0; k < 8; k++) mine[ST_STATUS0 + k] += ((status & 7) == k) ? 1ull : 0ull;
     }
   }
-  if (lane == 0) {
-    atomicAdd(&cstat[ST_NPIX], my_n);
-    atomicAdd(&cstat[ST_IT1], my_it1);
-    atomicAdd(&cstat[ST_IT2], my_it2);
-    atomicAdd(&cstat[ST_FP64], my_fp64);
-    atomicAdd(&cstat[ST_BAND1], my_b1);
-    atomicAdd(&cstat[ST_BAND2], my_b2);
-    atomicAdd(&cstat[ST_NODEBAND2], my_nb2);
+  flush_stats(cstat, mine, p.w.stats, lane);
+}
+
+// ---- one evaluation of a stage's normal equations per state (test hook)
+template <int K, int S1, int S2, int WPB>
+__global__ void __launch_bounds__(WPB * 32, 1) normal_eq_kernel(const __grid_constant__ LMLaunch p,
+                                                                int stage, const float *states,
+                                                                float *Hout, float *gout,
+                                                                float *cost_out) {
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) unsigned long long bar;
+  const KTables &t = p.t;
+  const KConfig &c = p.c;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (!stage_tables(t, smem, &bar, p.w.err)) return;
+  PixCtx pc;
+  pc.t = &t;
+  pc.c = &c;
+  pc.img = smem;
+  pc.wsc = smem + t.lay.total + warp * kMaxTgrid * kScratchPerNode;
+  pc.lane = lane;
+  const long long nw = (long long)gridDim.x * WPB;
+  for (long long pix = (long long)blockIdx.x * WPB + warp; pix < p.s.n_pix; pix += nw) {
+    const float *row = p.s.rad + pix * t.nb;
+    pc.wvrow = t.wvtab + (size_t)min((int)p.s.wv[pix], t.nwv - 1) * t.nb;
+    if (stage == 1) {
+      Stage1<K, S1> s1;
+      setup1(s1, pc, row);
+      constexpr int P = K + 1, NS = S1;
+      float x[K + 2], H[P * (P + 1) / 2], g[P], cst, cd, dcd, r0[NS], r1[NS];
+      int m;
 #pragma unroll
-    for (int k = 0; k < 8; k++) atomicAdd(&cstat[ST_STATUS0 + k], my_st[k]);
+      for (int i = 0; i < K + 2; i++) x[i] = states[pix * (K + 2) + i];
+#pragma unroll
+      for (int i = 0; i < NS; i++) r0[i] = 0.f;
+      s1.eval(pc, x, H, g, cst, cd, m, r0, r1, dcd);
+      if (lane == 0) {
+        for (int a = 0; a < P; a++) {
+          gout[pix * P + a] = g[a];
+          for (int b = 0; b < P; b++) Hout[pix * P * P + a * P + b] = H[up<P>(a, b)];
+        }
+        cost_out[pix] = cst;
+      }
+    } else {
+      float xs[K], x[6];
+#pragma unroll
+      for (int k = 0; k < K; k++) xs[k] = states[pix * (K + 6) + k];
+#pragma unroll
+      for (int i = 0; i < 6; i++) x[i] = states[pix * (K + 6) + K + i];
+      Stage2<S2> s2;
+      setup2<K, S2>(s2, pc, row, xs);
+      constexpr int NS = S2;
+      float H[21], g[6], cst, cd, dcd, r0[NS], r1[NS];
+      int m;
+#pragma unroll
+      for (int i = 0; i < NS; i++) r0[i] = 0.f;
+      s2.eval(pc, x, H, g, cst, cd, m, r0, r1, dcd);
+      if (lane == 0) {
+        for (int a = 0; a < 6; a++) {
+          gout[pix * 6 + a] = g[a];
+          for (int b = 0; b < 6; b++) Hout[pix * 36 + a * 6 + b] = H[up<6>(a, b)];
+        }
+        cost_out[pix] = cst;
+      }
+    }
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
-    if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
 }
 
 constexpr int kWPB = 8;
 
-template <int K, int S1, int S2>
-cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used) {
-  auto kern = lm_kernel<K, S1, S2, kWPB>;
+template <class Kern>
+cudaError_t launch_persistent(Kern kern, const LMLaunch &p, int num_sms, cudaStream_t st,
+                              int *blocks_used) {
   size_t smem = lm_smem_bytes(p.t);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1177,8 +1331,15 @@ cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *block
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
   kern<<<(int)blocks, kWPB * 32, smem, st>>>(p);
-  if (blocks_used) *blocks_used = (int)blocks;
+  if (blocks_used) *blocks_used += (int)blocks;
   return cudaGetLastError();
+}
+
+template <int K, int S1, int S2>
+cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used) {
+  cudaError_t e = launch_persistent(lm_stage1_kernel<K, S1, kWPB>, p, num_sms, st, blocks_used);
+  if (e != cudaSuccess) return e;
+  return launch_persistent(lm_stage2_kernel<K, S2, kWPB>, p, num_sms, st, blocks_used);
 }
 
 template <int K>
@@ -1187,6 +1348,25 @@ cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *block
   if (s1 <= 9 && s2 <= 7) return launch_t<K, 9, 7>(p, num_sms, st, blocks_used);
   if (s1 <= 9 && s2 <= 9) return launch_t<K, 9, 9>(p, num_sms, st, blocks_used);
   if (s1 <= 16 && s2 <= 16) return launch_t<K, 16, 16>(p, num_sms, st, blocks_used);
+  return cudaErrorInvalidValue;
+}
+
+template <int K>
+cudaError_t launch_ne_k(const LMLaunch &p, int stage, const float *states, float *H, float *g,
+                        float *cost, cudaStream_t st) {
+  int s1 = (p.t.n1 + 31) / 32, s2 = (p.t.n2 + 31) / 32;
+  size_t smem = lm_smem_bytes(p.t);
+  int blocks = (int)((p.s.n_pix + kWPB - 1) / kWPB);
+  if (blocks > 1024) blocks = 1024;
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, kWPB * 32, smem, st>>>(p, stage, states, H, g, cost);
+    return cudaGetLastError();
+  };
+  if (s1 <= 9 && s2 <= 7) return go(normal_eq_kernel<K, 9, 7, kWPB>);
+  if (s1 <= 9 && s2 <= 9) return go(normal_eq_kernel<K, 9, 9, kWPB>);
+  if (s1 <= 16 && s2 <= 16) return go(normal_eq_kernel<K, 16, 16, kWPB>);
   return cudaErrorInvalidValue;
 }
 
@@ -1200,6 +1380,16 @@ cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *bloc
   switch (p.t.K) {
     case 3: return launch_k<3>(p, num_sms, st, blocks_used);
     case 5: return launch_k<5>(p, num_sms, st, blocks_used);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_normal_eq(const LMLaunch &p, int stage, const float *states, float *H, float *g,
+                             float *cost, cudaStream_t st) {
+  if (p.s.n_pix <= 0) return cudaSuccess;
+  switch (p.t.K) {
+    case 3: return launch_ne_k<3>(p, stage, states, H, g, cost, st);
+    case 5: return launch_ne_k<5>(p, stage, states, H, g, cost, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -24,7 +24,7 @@ PX_F_FP64, PX_F_NOT_IDENT, PX_F_MLP_FALLBACK, PX_F_S1_MAXITER = 8, 16, 32, 64
 
 SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fire_ctx_destroy",
            "fire_retrieve", "fire_forward", "fire_block_mean", "fire_get_stats",
-           "fire_window_bands", "fire_status_str")
+           "fire_window_bands", "fire_status_str", "fire_normal_equations")
 
 
 class FireError(RuntimeError):
@@ -99,6 +99,9 @@ def _load():
     lib.fire_get_stats.restype = C.c_int
     lib.fire_window_bands.argtypes = [vp] + [C.POINTER(C.c_int32)] * 4
     lib.fire_window_bands.restype = C.c_int
+    lib.fire_normal_equations.argtypes = [vp, i32, vp, vp, vp, i64, C.POINTER(Priors_t), vp, vp,
+                                          vp, vp]
+    lib.fire_normal_equations.restype = C.c_int
     lib.fire_status_str.argtypes = [C.c_int]
     lib.fire_status_str.restype = C.c_char_p
     return lib
@@ -259,6 +262,21 @@ class Context:
                                 noise_rel, noise_abs, seed, stream_id, pixel_offset,
                                 _dptr(out, torch.float32), _stream_ptr(stream)), "fire_forward")
         return out
+
+    def normal_equations(self, stage, radiance, wv_bin, states, priors=None, stream=None):
+        """(H, g, cost) of one stage at the given states (device tensors)."""
+        import torch
+        n = int(states.shape[0])
+        P = self.n_endm + 1 if stage == 1 else 6
+        H = torch.empty((n, P, P), dtype=torch.float32, device="cuda")
+        g = torch.empty((n, P), dtype=torch.float32, device="cuda")
+        cost = torch.empty((n,), dtype=torch.float32, device="cuda")
+        pr = None if priors is None else C.byref(priors)
+        _check(lib.fire_normal_equations(self._h, stage, _dptr(radiance, torch.float32),
+                                         _dptr(wv_bin), _dptr(states, torch.float32), n, pr,
+                                         _dptr(H), _dptr(g), _dptr(cost), _stream_ptr(stream)),
+               "fire_normal_equations")
+        return H, g, cost
 
     def stats(self):
         s = Stats_t()

@@ -206,3 +206,32 @@ def test_given_init_matches_oracle(fr, torch, c1):
     torch.cuda.synchronize()
     s = parity_stats(o, _np(out))
     assert s["rate"] >= 0.99 and s["pool"] > 10
+
+
+@pytest.mark.parametrize("stage", [1, 2])
+def test_normal_equations_match_oracle(fr, torch, c1, stage):
+    """One iteration's J^T W J + P, J^T W r - P(z - pm) and cost, formed by the
+    kernel in FP32, against the oracle's FP64 at the same random states."""
+    t, tr, L = c1
+    rng = np.random.default_rng(20 + stage)
+    idx = np.concatenate([np.flatnonzero(tr.kind == 1)[:40], rng.choice(tr.n_pix, 24, replace=False)])
+    n = idx.size
+    xs = rng.dirichlet(np.ones(3), n)
+    if stage == 1:
+        st = np.column_stack([xs, 10 ** rng.uniform(-3.5, -0.5, n), rng.uniform(450, 2100, n)])
+    else:
+        st = np.column_stack([xs, rng.uniform(950, 2100, n), rng.uniform(35, 400, n),
+                              rng.uniform(380, 990, n), rng.uniform(35, 400, n),
+                              rng.uniform(0.05, 0.95, n), 10 ** rng.uniform(-3.5, -0.5, n)])
+    st = st.astype(np.float32)
+    ctx = fr.Context(t)
+    H, g, cost = ctx.normal_equations(stage, _dev(torch, L[idx], torch.float32),
+                                      _dev(torch, tr.wv_bin[idx].astype(np.int16), torch.int16),
+                                      _dev(torch, st, torch.float32))
+    H, g, cost = H.cpu().numpy(), g.cpu().numpy(), cost.cpu().numpy()
+    for j, i in enumerate(idx):
+        Ho, go, co = oracle.normal_equations(t, stage, L[i], tr.wv_bin[i], st[j].astype(np.float64))
+        d = np.sqrt(np.outer(np.diag(Ho), np.diag(Ho)))
+        assert np.max(np.abs(H[j] - Ho) / d) < 2e-4, (stage, i)
+        assert np.max(np.abs(g[j] - go) / np.sqrt(np.diag(Ho) * co)) < 2e-4, (stage, i)
+        assert abs(cost[j] - co) / co < 1e-4, (stage, i)
