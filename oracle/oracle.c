@@ -354,12 +354,17 @@ static int reduced_basis(const lm_prob_t *q, const double *x, double *E, int *m_
   return col;
 }
 
-/* Apply a z-step to x: box variables are clipped to [lo, hi], the simplex
- * group is projected onto the unit simplex (Sec. 2.6). */
-static void step_project(const lm_prob_t *q, const double *x, const double *dz, double *xt) {
+/* Apply a z-step to x: a variable pinned on a bound by the step solve is set
+ * exactly to that bound (pdir -1 = lo, +1 = hi, 0 = free), box variables
+ * are clipped to [lo, hi], the simplex group is projected onto the unit
+ * simplex (Sec. 2.6). */
+static void step_project(const lm_prob_t *q, const double *x, const double *dz, const int *pdir,
+                         double *xt) {
   for (int i = 0; i < q->p; i++) {
     double s = 0.5 * (q->hi[i] - q->lo[i]);
     xt[i] = x[i] + s * dz[i];
+    if (pdir[i] < 0) xt[i] = q->lo[i];
+    if (pdir[i] > 0) xt[i] = q->hi[i];
     if (i >= q->nsimp) {
       if (xt[i] < q->lo[i]) xt[i] = q->lo[i];
       if (xt[i] > q->hi[i]) xt[i] = q->hi[i];
@@ -429,9 +434,9 @@ static int lm_fit(const pix_t *P, const lm_prob_t *q, const orc_config_t *c, dou
     for (int a = 0; a < pr; a++)
       if (!act[a] && Hr[a * pr + a] > mxd) mxd = Hr[a * pr + a];
     for (int a = 0; a < pr; a++) Dg[a] = Hr[a * pr + a] < c->dfloor * mxd ? c->dfloor * mxd : Hr[a * pr + a];
-    int pin[ORC_NS1];
+    int pin[ORC_NS1], pdir[ORC_NS1];
     double dr[ORC_NS1];
-    for (int a = 0; a < pr; a++) { pin[a] = act[a]; dr[a] = 0.0; }
+    for (int a = 0; a < pr; a++) { pin[a] = act[a]; dr[a] = 0.0; pdir[a] = 0; }
     int ok = 0;
     for (int pass = 0; pass <= pr; pass++) {
       int F[ORC_NS1], nf = 0;
@@ -474,8 +479,10 @@ static int lm_fit(const pix_t *P, const lm_prob_t *q, const orc_config_t *c, dou
         double s = 0.5 * (q->hi[i] - q->lo[i]);
         double xn = x[i] + s * dr[a];
         if (!(s > 0)) { pin[a] = 1; dr[a] = 0.0; viol = 1; }
-        else if (xn < q->lo[i]) { pin[a] = 1; dr[a] = (q->lo[i] - x[i]) / s; viol = 1; }
-        else if (i >= q->nsimp && xn > q->hi[i]) { pin[a] = 1; dr[a] = (q->hi[i] - x[i]) / s; viol = 1; }
+        else if (xn < q->lo[i]) { pin[a] = 1; pdir[a] = -1; dr[a] = (q->lo[i] - x[i]) / s; viol = 1; }
+        else if (i >= q->nsimp && xn > q->hi[i]) {
+          pin[a] = 1; pdir[a] = 1; dr[a] = (q->hi[i] - x[i]) / s; viol = 1;
+        }
       }
       if (!viol) break;
     }
@@ -485,11 +492,16 @@ static int lm_fit(const pix_t *P, const lm_prob_t *q, const orc_config_t *c, dou
       if (!(lam < 1e300)) { status = ORC_CHOL_FAIL; break; }
       continue;
     }
+    int pfull[ORC_NS1];
     for (int i = 0; i < p; i++) {
       dz[i] = 0;
-      for (int a = 0; a < pr; a++) dz[i] += E[i * p + a] * dr[a];
+      pfull[i] = 0;
+      for (int a = 0; a < pr; a++) {
+        dz[i] += E[i * p + a] * dr[a];
+        if (E[i * p + a] == 1.0) pfull[i] = pdir[a];
+      }
     }
-    step_project(q, x, dz, xt);
+    step_project(q, x, dz, pfull, xt);
     /* actual step in z and its reduced coordinates */
     double Dz[ORC_NS1], Dr[ORC_NS1], dmax = 0;
     for (int i = 0; i < p; i++) {

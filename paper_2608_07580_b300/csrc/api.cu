@@ -29,6 +29,8 @@ struct fire_ctx {
   // stage-1 -> stage-2 hand-over, grown on demand
   float *d_s1x = nullptr;
   int *d_s1meta = nullptr;
+  float *d_s2x = nullptr;
+  float *d_s2g = nullptr;
   int64_t s1_cap = 0;
   int last_launches = 0;
 };
@@ -134,11 +136,16 @@ fire_status_t ensure_s1(fire_ctx *c, int64_t n) {
   if (n <= c->s1_cap) return FIRE_OK;
   cudaFree(c->d_s1x);
   cudaFree(c->d_s1meta);
+  cudaFree(c->d_s2x);
+  cudaFree(c->d_s2g);
   c->d_s1x = nullptr;
   c->d_s1meta = nullptr;
+  c->d_s2x = c->d_s2g = nullptr;
   c->s1_cap = 0;
   fire_status_t e = dev_alloc(&c->d_s1x, (size_t)n * (c->t.K + 2) * 4);
   if (e == FIRE_OK) e = dev_alloc(&c->d_s1meta, (size_t)n * 4);
+  if (e == FIRE_OK) e = dev_alloc(&c->d_s2x, (size_t)n * 31 * 4);
+  if (e == FIRE_OK) e = dev_alloc(&c->d_s2g, (size_t)n * 6 * 4);
   if (e == FIRE_OK) c->s1_cap = n;
   return e;
 }
@@ -234,6 +241,8 @@ void fire_ctx_destroy(fire_ctx_t *ctx) {
   cudaFree(ctx->d_stage);
   cudaFree(ctx->d_s1x);
   cudaFree(ctx->d_s1meta);
+  cudaFree(ctx->d_s2x);
+  cudaFree(ctx->d_s2g);
   delete ctx;
 }
 
@@ -384,6 +393,8 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   }
   p.w.s1x = c->d_s1x;
   p.w.s1meta = c->d_s1meta;
+  p.w.s2x = c->d_s2x;
+  p.w.s2g = c->d_s2g;
 
   // per-pixel output sizes (bytes), in the order staged for host scenes
   const size_t szf = (size_t)n * 4;
@@ -406,7 +417,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     int blocks = 0;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
     CK(launch_lm(p, c->num_sms, st, &blocks));
-    c->last_launches = 2;
+    c->last_launches = 3;
     return FIRE_OK;
   }
 
@@ -454,7 +465,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   int blocks = 0;
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   CK(launch_lm(p, c->num_sms, st, &blocks));
-  c->last_launches = 2;
+  c->last_launches = 3;
   struct { void *h; void *d; size_t b; } back[] = {
       {out->state, o_state, s_state}, {out->ET, o_ET, szf}, {out->sdT, o_sdT, szf},
       {out->alpha, o_alpha, szf}, {out->var_ET, o_var, szf}, {out->cost, o_cost, szf},

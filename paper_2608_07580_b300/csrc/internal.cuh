@@ -82,6 +82,8 @@ struct KWork {
   int *err;                     // bounded-wait failure flag
   float *s1x;                   // [n_pix][K+2] stage-1 result handed to stage 2
   int *s1meta;                  // [n_pix] status bits | 256 if the pixel goes on to stage 2
+  float *s2x;                   // [n_pix][31] stage-2 state, J^T W J + P, costs, counts
+  float *s2g;                   // [n_pix][6] stage-2 gradient at the final state
 };
 
 struct LMLaunch {

@@ -1,0 +1,227 @@
+// kernels_gemm.cu — BF16 tensor-core GEMM on sm_103a (tcgen05 + TMEM).
+//
+// C[M x N] = A[M x K] * B[N x K]^T with A, B bf16, K-major (row-major with K
+// contiguous), FP32 accumulation in tensor memory, and a fused epilogue:
+//   EPI_F32        C_f32 = acc (+ bias)
+//   EPI_BIAS_RELU  h = max(acc + bias, 0) -> bf16 (and optionally h^T)
+//   EPI_BIAS_TANH  z = tanh(acc + bias) -> f32
+//   EPI_RELU_MASK  d = acc * (mask > 0) -> bf16 (and optionally d^T)
+// One CTA (4 warps) computes a 128 x BN tile; K is consumed in 64-wide
+// chunks staged by cp.async into 128-byte-swizzled shared memory (the
+// canonical K-major SW128 layout), double-buffered. A single thread issues
+// tcgen05.mma (cta_group::1, kind::f16, M = 128, N = BN, K = 16 per
+// instruction) and commits to an mbarrier per stage; every wait is bounded
+// and sets an error flag on timeout. The accumulator is read back with
+// tcgen05.ld (32x32b) for the epilogue, one row per thread.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+namespace firert {
+namespace {
+
+constexpr int kBM = 128, kBK = 64;
+constexpr long long kSpin = 1ll << 24;
+
+__device__ __forceinline__ unsigned su32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// UMMA shared-memory descriptor, K-major, 128-byte swizzle: start address,
+// leading-byte offset (unused for this layout), stride-byte offset = 1024 B
+// between 8-row core-matrix groups, descriptor version 1, layout type 2.
+__device__ __forceinline__ uint64_t sdesc(unsigned saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(1u) << 16;
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  unsigned done = 0;
+  for (long long s = 0; s < kSpin && !done; s++)
+    asm volatile(
+        "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2; selp.u32 %0, 1, 0, P; }"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+
+// byte offset of the 16-byte chunk c (K elements 8c..8c+7) of row r inside a
+// K-major SW128 tile
+__device__ __forceinline__ unsigned swz(int r, int c) {
+  return (unsigned)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ void cp16(unsigned dst, const void *src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(valid ? 16 : 0) : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128) gemm_tn_kernel(GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char gsm[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ uint32_t tmem_slot;
+  constexpr int kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+  constexpr int kCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+  // stage buffers, 1024-byte aligned
+  unsigned char *base = gsm + ((1024 - (su32(gsm) & 1023)) & 1023);
+  unsigned char *As[2] = {base, base + kABytes};
+  unsigned char *Bs[2] = {base + 2 * kABytes, base + 2 * kABytes + kBBytes};
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int nk = (g.K + kBK - 1) / kBK;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(su32(&tmem_slot)), "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  auto load_chunk = [&](int kc, int s) {
+    const int k0 = kc * kBK;
+    for (int e = tid; e < kBM * 8; e += 128) {
+      int r = e >> 3, c = e & 7;
+      int gr = m0 + r, gk = k0 + c * 8;
+      bool ok = gr < g.M && gk < g.K;
+      const void *src = ok ? (const void *)(g.A + (size_t)gr * g.lda + gk) : (const void *)g.A;
+      cp16(su32(As[s]) + swz(r, c), src, ok);
+    }
+    for (int e = tid; e < BN * 8; e += 128) {
+      int r = e >> 3, c = e & 7;
+      int gr = n0 + r, gk = k0 + c * 8;
+      bool ok = gr < g.N && gk < g.K;
+      const void *src = ok ? (const void *)(g.B + (size_t)gr * g.ldb + gk) : (const void *)g.B;
+      cp16(su32(Bs[s]) + swz(r, c), src, ok);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  bool ok = true;
+  unsigned uses[2] = {0u, 0u};
+  load_chunk(0, 0);
+  if (nk > 1) load_chunk(1, 1);
+  constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+  for (int kc = 0; kc < nk; kc++) {
+    const int s = kc & 1;
+    if (kc + 1 < nk) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; kk++) {
+        uint64_t ad = sdesc(su32(As[s]) + kk * 32), bd = sdesc(su32(Bs[s]) + kk * 32);
+        uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
+            ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(su32(&bar[s])) : "memory");
+    }
+    uses[s]++;
+    if (kc + 2 < nk) {
+      // the stage is reused: wait until the MMAs that read it completed
+      if (!mbar_wait(su32(&bar[s]), (uses[s] - 1) & 1)) { ok = false; break; }
+      load_chunk(kc + 2, s);
+    }
+  }
+  // wait for the last commit of each stage that was used
+  for (int s = 0; s < 2 && ok; s++)
+    if (uses[s] && !mbar_wait(su32(&bar[s]), (uses[s] - 1) & 1)) ok = false;
+  if (!ok) {
+    if (tid == 0) atomicExch(g.err, 1);
+    // drain: bounded waits on whatever is still in flight, then free TMEM
+    for (int s = 0; s < 2; s++)
+      if (uses[s]) mbar_wait(su32(&bar[s]), (uses[s] - 1) & 1);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    const bool rv = row < g.M;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!rv) continue;
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        const int col = n0 + c0 + j;
+        if (col >= g.N) continue;
+        float a = __uint_as_float(v[j]);
+        if (g.bias) a += g.bias[col];
+        switch (g.epi) {
+          case EPI_BIAS_RELU: a = fmaxf(a, 0.f); break;
+          case EPI_BIAS_TANH: a = tanhf(a); break;
+          case EPI_RELU_MASK:
+            a = __bfloat162float(g.mask[(size_t)row * g.ldm + col]) > 0.f ? a : 0.f;
+            break;
+          default: break;
+        }
+        if (g.Cf) g.Cf[(size_t)row * g.ldc + col] = g.accumulate ? g.Cf[(size_t)row * g.ldc + col] + a : a;
+        if (g.Cb) g.Cb[(size_t)row * g.ldcb + col] = __float2bfloat16_rn(a);
+        if (g.CbT) g.CbT[(size_t)col * g.ldcbT + row] = __float2bfloat16_rn(a);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+template <int BN>
+cudaError_t launch_bn(const GemmArgs &g, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)(kBM * kBK * 2) + 2 * (size_t)(BN * kBK * 2) + 1024;
+  cudaError_t e = cudaFuncSetAttribute(gemm_tn_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN);
+  gemm_tn_kernel<BN><<<grid, 128, smem, st>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  if ((g.K & 7) || (g.lda & 7) || (g.ldb & 7)) return cudaErrorInvalidValue;  // 16-byte rows
+  if (g.N <= 16) return launch_bn<16>(g, st);
+  if (g.N <= 32) return launch_bn<32>(g, st);
+  if (g.N <= 64) return launch_bn<64>(g, st);
+  if (g.N <= 128) return launch_bn<128>(g, st);
+  return launch_bn<256>(g, st);
+}
+
+}  // namespace firert

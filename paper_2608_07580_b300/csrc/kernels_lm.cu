@@ -32,7 +32,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClaim = 4;          // pixels claimed per atomic
 #ifndef LM1_MINB
-#define LM1_MINB 1
+#define LM1_MINB 2
 #endif
 #ifndef LM2_MINB
 #define LM2_MINB 1
@@ -330,20 +330,23 @@ struct Stage1 {
 
   // x + step (z units, reduced basis) -> projected trial point
   __device__ __forceinline__ void apply(const KConfig &c, const float (&x)[NX], const float (&dr)[P],
-                                        int m, float (&xt)[NX]) const {
+                                        const signed char (&pd)[P], int m, float (&xt)[NX]) const {
     float sum = 0.f;
 #pragma unroll
     for (int a = 0; a < K - 1; a++) sum += dr[a];
 #pragma unroll
     for (int k = 0; k < K; k++) {
       float d = 0.f;
-      if (k < K - 1 && k < m) d = dr[k < K - 1 ? k : 0];
-      if (k > 0 && k > m) d = dr[k > 0 ? k - 1 : 0];
-      xt[k] = (k == m) ? x[k] - sf * sum : x[k] + sf * d;
+      bool at0 = false;   // pinned on its lower bound by the step solve
+      if (k < K - 1 && k < m) { d = dr[k < K - 1 ? k : 0]; at0 = pd[k < K - 1 ? k : 0] < 0; }
+      if (k > 0 && k > m) { d = dr[k > 0 ? k - 1 : 0]; at0 = pd[k > 0 ? k - 1 : 0] < 0; }
+      xt[k] = (k == m) ? x[k] - sf * sum : (at0 ? c.lo1[k] : x[k] + sf * d);
     }
 #pragma unroll
     for (int i = K; i < K + 2; i++) {
       float v = x[i] + scale(c, i) * dr[i - 1];
+      if (pd[i - 1] < 0) v = c.lo1[i];
+      if (pd[i - 1] > 0) v = c.hi1[i];
       xt[i] = fminf(fmaxf(v, c.lo1[i]), c.hi1[i]);
     }
     simplex_project(xt);
@@ -542,9 +545,14 @@ struct Stage2 {
   }
 
   __device__ __forceinline__ void apply(const KConfig &c, const float (&x)[NX], const float (&dr)[P],
-                                        int, float (&xt)[NX]) const {
+                                        const signed char (&pd)[P], int, float (&xt)[NX]) const {
 #pragma unroll
-    for (int i = 0; i < 6; i++) xt[i] = fminf(fmaxf(x[i] + s[i] * dr[i], c.lo2[i]), c.hi2[i]);
+    for (int i = 0; i < 6; i++) {
+      float v = x[i] + s[i] * dr[i];
+      if (pd[i] < 0) v = c.lo2[i];
+      if (pd[i] > 0) v = c.hi2[i];
+      xt[i] = fminf(fmaxf(v, c.lo2[i]), c.hi2[i]);
+    }
   }
 };
 
@@ -657,6 +665,7 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
       // damping diagonal, projected-Newton solve with re-solve on bound hits
       float D[P], dr[P];
       bool pin[P];
+      signed char pd[P];   // -1 / +1: pinned on lo / hi by the step solve
       float mxd = 0.f;
 #pragma unroll
       for (int a = 0; a < P; a++)
@@ -666,6 +675,7 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
         D[a] = fmaxf(H[up<P>(a, a)], c.dfloor * mxd);
         pin[a] = act[a];
         dr[a] = 0.f;
+        pd[a] = 0;
       }
       bool ok = true;
 #pragma unroll 1
@@ -703,9 +713,9 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
             float lo = S.template lo_r<a>(c, m), hi = S.template hi_r<a>(c, m);
             float xn = xv + sc * dr[a];
             if (!(sc > 0.f)) { pin[a] = true; dr[a] = 0.f; viol = true; }
-            else if (xn < lo) { pin[a] = true; dr[a] = (lo - xv) / sc; viol = true; }
+            else if (xn < lo) { pin[a] = true; pd[a] = -1; dr[a] = (lo - xv) / sc; viol = true; }
             else if (St::template has_upper<a>() && xn > hi) {
-              pin[a] = true; dr[a] = (hi - xv) / sc; viol = true;
+              pin[a] = true; pd[a] = 1; dr[a] = (hi - xv) / sc; viol = true;
             }
           }
         });
@@ -716,7 +726,7 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
         if (!(lam < 1e30f)) { status = PX_CHOL_FAIL; break; }
         continue;
       }
-      S.apply(c, x, dr, m, xt);
+      S.apply(c, x, dr, pd, m, xt);
       float Dz[NX], dmax = 0.f;
 #pragma unroll
       for (int i = 0; i < NX; i++) {
@@ -994,6 +1004,7 @@ __device__ __forceinline__ void flush_stats(unsigned long long *cstat, const uns
 }
 
 constexpr int kFitted = 256;   // scratch flag: pixel goes on to stage 2
+constexpr int kS2Hand = 31;    // floats handed from stage 2 to finalize per pixel
 
 // ---- stage 1: checks, HFDI gate, stage-1 fit -> scratch
 template <int K, int S1, int WPB>
@@ -1173,80 +1184,120 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
       mine[ST_IT2] += r2.iters;
       mine[ST_BAND2] += (unsigned long long)(r2.iters + 1) * (unsigned long long)t.n2;
       mine[ST_NODEBAND2] += (unsigned long long)pc.node_evals * (unsigned long long)t.n2;
-      // moment matching (Sec. 2.3)
-      const float ET = x2[4] * x2[0] + (1.f - x2[4]) * x2[2];
-      const float dmu = x2[0] - x2[2];
-      const float sdT = sqrtf(x2[4] * x2[1] * x2[1] + (1.f - x2[4]) * x2[3] * x2[3] +
-                              x2[4] * (1.f - x2[4]) * dmu * dmu);
-      const float rms = sqrtf(r2.cdata / (float)n2u);
-      int nf = 0;
+      // hand the final state and normal equations to the finalize kernel
+      float* hand = p.w.s2x + pix * kS2Hand;
+      if (lane < kS2Hand) {
+        float v = 0.f;
 #pragma unroll
-      for (int k = 0; k < 6; k++) {
-        bool act = (x2[k] <= c.lo2[k] && g2[k] <= 0.f) || (x2[k] >= c.hi2[k] && g2[k] >= 0.f);
-        nf += (!act && H2[up<6>(k, k)] > 0.f);
+        for (int k = 0; k < 6; k++) v = (lane == k) ? x2[k] : v;
+#pragma unroll
+        for (int k = 0; k < 21; k++) v = (lane == 6 + k) ? H2[k] : v;
+        v = (lane == 27) ? r2.cost : v;
+        v = (lane == 28) ? r2.cdata : v;
+        v = (lane == 29) ? __int_as_float(n2u) : v;
+        v = (lane == 30) ? __int_as_float(status | (r2.iters << 8)) : v;
+        hand[lane] = v;
       }
-      const float s2v = c.weighted ? 1.f : r2.cost / (float)(n2u - nf);
-      float cov[21];
-      bool cov_ok = true;
-      double vE = 0.0, va = 0.0;
-      const bool act_a = (x2[5] <= c.lo2[5] && g2[5] <= 0.f) || (x2[5] >= c.hi2[5] && g2[5] >= 0.f);
-      if (act_a && x2[5] <= c.lo2[5]) {
-        // no thermal signal: E[T] is undefined, so is its posterior
-        cov_ok = false;
-        vE = __longlong_as_double(0x7ff0000000000000ll);
+      if (lane < 6) {
+        float v = g2[0];
 #pragma unroll
-        for (int i = 0; i < 21; i++) cov[i] = __int_as_float(0x7fc00000);
-      } else if (nf > 0) {
-        CovIO io;
-#pragma unroll
-        for (int i = 0; i < 6; i++) { io.x[i] = x2[i]; io.g[i] = g2[i]; }
-#pragma unroll
-        for (int i = 0; i < 21; i++) io.H[i] = H2[i];
-        io.s2 = s2v;
-        laplace_cov(c, io);
-#pragma unroll
-        for (int i = 0; i < 21; i++) cov[i] = io.cov[i];
-        cov_ok = io.cov_ok;
-        vE = io.vE;
-        va = io.va;
-      } else {
-#pragma unroll
-        for (int i = 0; i < 21; i++) cov[i] = 0.f;
+        for (int k = 0; k < 6; k++) v = (lane == k) ? g2[k] : v;
+        p.w.s2g[pix * 6 + lane] = v;
       }
-      const double sdE = sqrt(vE), sda = sqrt(va);
-      const bool ident = cov_ok && isfinite(sdE) && sdE <= (double)c.ident_sd_et &&
-                         (double)x2[5] >= (double)c.ident_alpha_snr * sda && !act_a && x2[5] > 0.f;
-      if (!ident) status |= PX_F_NOT_IDENT;
-      if (p.o.state && lane < NSx) {
-        float v = x1[0];
-#pragma unroll
-        for (int k = 0; k < K + 2; k++) v = (k == lane) ? x1[k] : v;
-#pragma unroll
-        for (int k = 0; k < 6; k++) v = (K + 2 + k == lane) ? x2[k] : v;
-        p.o.state[pix * NSx + lane] = v;
-      }
-      if (p.o.cov && lane < 21) {
-        float v = cov[0];
-#pragma unroll
-        for (int k = 0; k < 21; k++) v = (k == lane) ? cov[k] : v;
-        p.o.cov[pix * 21 + lane] = v;
-      }
-      if (lane == 0) {
-        if (p.o.ET) p.o.ET[pix] = ET;
-        if (p.o.sdT) p.o.sdT[pix] = sdT;
-        if (p.o.alpha) p.o.alpha[pix] = x2[5];
-        if (p.o.var_ET) p.o.var_ET[pix] = (float)vE;
-        if (p.o.cost) p.o.cost[pix] = r2.cost;
-        if (p.o.rms) p.o.rms[pix] = rms;
-        if (p.o.status) p.o.status[pix] = (uint8_t)status;
-        if (p.o.iters) p.o.iters[2 * pix + 1] = (uint16_t)r2.iters;
-      }
-      mine[ST_FP64] += (status & PX_F_FP64) ? 1ull : 0ull;
-#pragma unroll
-      for (int k = 0; k < 8; k++) mine[ST_STATUS0 + k] += ((status & 7) == k) ? 1ull : 0ull;
     }
   }
   flush_stats(cstat, mine, p.w.stats, lane);
+}
+
+// ---- finalize: moment matching (Sec. 2.3), FP64 Laplace covariance,
+// identifiability and the outputs of every fitted pixel; one thread per
+// pixel, so the FP64 work is not repeated across the lanes of a warp
+__global__ void __launch_bounds__(128) finalize_kernel(const __grid_constant__ LMLaunch p, int K) {
+  __shared__ unsigned long long cstat[ST_COUNT];
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
+  __syncthreads();
+  const KConfig &c = p.c;
+  const int NSx = K + 8;
+  unsigned long long st_fp64 = 0, st_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < p.s.n_pix;
+       pix += (long long)gridDim.x * blockDim.x) {
+    if (!(p.w.s1meta[pix] & kFitted)) continue;
+    const float *hand = p.w.s2x + pix * kS2Hand;
+    CovIO io;
+#pragma unroll
+    for (int k = 0; k < 6; k++) { io.x[k] = hand[k]; io.g[k] = p.w.s2g[pix * 6 + k]; }
+#pragma unroll
+    for (int k = 0; k < 21; k++) io.H[k] = hand[6 + k];
+    const float cost = hand[27], cdata = hand[28];
+    const int n2u = __float_as_int(hand[29]), sw = __float_as_int(hand[30]);
+    int status = sw & 0xff;
+    const int it2 = sw >> 8;
+    const float *x2 = io.x;
+    const float ET = x2[4] * x2[0] + (1.f - x2[4]) * x2[2];
+    const float dmu = x2[0] - x2[2];
+    const float sdT = sqrtf(x2[4] * x2[1] * x2[1] + (1.f - x2[4]) * x2[3] * x2[3] +
+                            x2[4] * (1.f - x2[4]) * dmu * dmu);
+    const float rms = sqrtf(cdata / (float)n2u);
+    int nf = 0;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      bool act = (x2[k] <= c.lo2[k] && io.g[k] <= 0.f) || (x2[k] >= c.hi2[k] && io.g[k] >= 0.f);
+      nf += (!act && io.H[up<6>(k, k)] > 0.f);
+    }
+    io.s2 = c.weighted ? 1.f : cost / (float)(n2u - nf);
+    const bool act_a = (x2[5] <= c.lo2[5] && io.g[5] <= 0.f) || (x2[5] >= c.hi2[5] && io.g[5] >= 0.f);
+    if (act_a && x2[5] <= c.lo2[5]) {
+      // no thermal signal: E[T] is undefined, so is its posterior
+      io.cov_ok = false;
+      io.vE = __longlong_as_double(0x7ff0000000000000ll);
+      io.va = 0.0;
+#pragma unroll
+      for (int i = 0; i < 21; i++) io.cov[i] = __int_as_float(0x7fc00000);
+    } else if (nf > 0) {
+      laplace_cov(c, io);
+    } else {
+      io.cov_ok = true;
+      io.vE = io.va = 0.0;
+#pragma unroll
+      for (int i = 0; i < 21; i++) io.cov[i] = 0.f;
+    }
+    const double sdE = sqrt(io.vE), sda = sqrt(io.va);
+    const bool ident = io.cov_ok && isfinite(sdE) && sdE <= (double)c.ident_sd_et &&
+                       (double)x2[5] >= (double)c.ident_alpha_snr * sda && !act_a && x2[5] > 0.f;
+    if (!ident) status |= PX_F_NOT_IDENT;
+    if (p.o.state) {
+      for (int k = 0; k < K + 2; k++) p.o.state[pix * NSx + k] = p.w.s1x[pix * (K + 2) + k];
+      for (int k = 0; k < 6; k++) p.o.state[pix * NSx + K + 2 + k] = x2[k];
+    }
+    if (p.o.cov)
+      for (int k = 0; k < 21; k++) p.o.cov[pix * 21 + k] = io.cov[k];
+    if (p.o.ET) p.o.ET[pix] = ET;
+    if (p.o.sdT) p.o.sdT[pix] = sdT;
+    if (p.o.alpha) p.o.alpha[pix] = x2[5];
+    if (p.o.var_ET) p.o.var_ET[pix] = (float)io.vE;
+    if (p.o.cost) p.o.cost[pix] = cost;
+    if (p.o.rms) p.o.rms[pix] = rms;
+    if (p.o.status) p.o.status[pix] = (uint8_t)status;
+    if (p.o.iters) p.o.iters[2 * pix + 1] = (uint16_t)it2;
+    st_fp64 += (status & PX_F_FP64) ? 1ull : 0ull;
+#pragma unroll
+    for (int k = 0; k < 8; k++) st_s[k] += ((status & 7) == k) ? 1ull : 0ull;
+  }
+  // warp-aggregate, then one shared atomic per warp and counter
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    st_fp64 += __shfl_xor_sync(kFull, st_fp64, o);
+#pragma unroll
+    for (int k = 0; k < 8; k++) st_s[k] += __shfl_xor_sync(kFull, st_s[k], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (st_fp64) atomicAdd(&cstat[ST_FP64], st_fp64);
+    for (int k = 0; k < 8; k++)
+      if (st_s[k]) atomicAdd(&cstat[ST_STATUS0 + k], st_s[k]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
+    if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
 }
 
 // ---- one evaluation of a stage's normal equations per state (test hook)
@@ -1339,7 +1390,13 @@ template <int K, int S1, int S2>
 cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used) {
   cudaError_t e = launch_persistent(lm_stage1_kernel<K, S1, kWPB>, p, num_sms, st, blocks_used);
   if (e != cudaSuccess) return e;
-  return launch_persistent(lm_stage2_kernel<K, S2, kWPB>, p, num_sms, st, blocks_used);
+  e = launch_persistent(lm_stage2_kernel<K, S2, kWPB>, p, num_sms, st, blocks_used);
+  if (e != cudaSuccess) return e;
+  long long blocks = (p.s.n_pix + 127) / 128;
+  if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
+  finalize_kernel<<<(int)blocks, 128, 0, st>>>(p, K);
+  if (blocks_used) *blocks_used += (int)blocks;
+  return cudaGetLastError();
 }
 
 template <int K>
