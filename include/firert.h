@@ -217,6 +217,98 @@ fire_status_t fire_normal_equations(fire_ctx_t *ctx, int32_t stage, const float 
                                     const fire_priors_t *pri, float *H, float *g, float *cost,
                                     fire_stream_t stream);
 
+/* BF16 tensor-core GEMM used by the learned initial-state proposal:
+ * C[M][N] = A[M][K] * B[N][K]^T (A, B bf16, K contiguous, rows 16-byte
+ * aligned: K, lda, ldb multiples of 8), FP32 accumulation, fused epilogue.
+ * epi: 0 = fp32 out (+bias), 1 = relu(acc + bias), 2 = tanh(acc + bias),
+ * 3 = acc * (mask > 0) (ReLU gradient). Outputs (any may be NULL): Cf fp32
+ * [M][ldc] (accumulate != 0 adds into it), Cb bf16 [M][ldcb], CbT bf16
+ * transposed [N][ldcbT]. err: device int set to 1 if a bounded wait gave up
+ * (may be NULL). All pointers are device pointers; asynchronous. */
+typedef struct {
+  const void *A;
+  int64_t lda;
+  const void *B;
+  int64_t ldb;
+  int32_t M, N, K, epi;
+  const float *bias;
+  const void *mask;
+  int64_t ldm;
+  float *Cf;
+  int64_t ldc;
+  void *Cb;
+  int64_t ldcb;
+  void *CbT;
+  int64_t ldcbT;
+  int32_t accumulate;
+  int32_t *err;
+} fire_gemm_t;
+fire_status_t fire_gemm_bf16(const fire_gemm_t *g, fire_stream_t stream);
+
+/* ---- Learned initial-state proposal (the task's extension; the paper has
+ * no network). z = tanh(W3 relu(W2 relu(W1 x + b1) + b2) + b3), x = per-band
+ * standardised radiance (bands padded to Din = n_bands rounded up to 16),
+ * hidden width H, 16 outputs of which K + 6 are used: the surface fractions
+ * and the five mixture-shape parameters in the z coordinates of Eq. (affine)
+ * (stage-2 default bounds) and log10(alpha) in [-4, 0] mapped to [-1, 1].
+ * BF16 tensor-core products with FP32 accumulation; FP32 master weights and
+ * Adam (beta 0.9 / 0.999, eps 1e-8). Training spectra are drawn on the GPU
+ * from the forward model (counter-based streams: the same seed and sample
+ * indices give the same batch). */
+typedef struct fire_mlp fire_mlp_t;
+typedef struct {
+  int64_t steps;          /* optimiser steps */
+  int32_t batch;          /* spectra per step, a multiple of 128 */
+  float lr;               /* Adam learning rate */
+  float pfire;            /* share of training spectra with a fire */
+  float noise_rel, noise_abs;  /* noise model of the spectra */
+  uint64_t seed;          /* stream key */
+  int64_t sample0;        /* index of the first sample (resume from fire_mlp_next_sample) */
+} fire_mlp_train_cfg_t;
+
+/* Create a network for the context's tables (weights He-uniform from seed).
+ * Errors: FIRE_ERR_ARG, FIRE_ERR_SHAPE (hidden not a multiple of 16 in
+ * 16..1024), FIRE_ERR_NOMEM, FIRE_ERR_CUDA. Synchronous. */
+fire_status_t fire_mlp_create(fire_mlp_t **out, fire_ctx_t *ctx, int32_t hidden, uint64_t seed);
+void fire_mlp_destroy(fire_mlp_t *m);
+/* Train: cfg->steps Adam steps on fresh synthetic batches; the first call
+ * also gathers the input standardisation from one batch. loss_host [steps]
+ * (host, optional) receives the masked-MSE loss of each step (the call then
+ * synchronises the stream). */
+fire_status_t fire_mlp_train(fire_mlp_t *m, const fire_mlp_train_cfg_t *cfg, float *loss_host,
+                             fire_stream_t stream);
+/* Inference on device radiance [n][n_bands]: z_out [n][16] (optional) and
+ * init_out [n][K+8] (optional), a starting state in the layout of
+ * fire_outputs_t.state, usable as fire_priors_t.init_state. */
+fire_status_t fire_mlp_infer(fire_mlp_t *m, const float *radiance, int64_t n, float *z_out,
+                             float *init_out, fire_stream_t stream);
+/* Forward + backward on given standardised inputs x [B][Din], targets and
+ * masks [B][16] (device fp32): grads (device) packed as dW1 [H][Din], db1 [H],
+ * dW2 [H][H], db2 [H], dW3^T [H][16], db3 [16]; loss (device, 1 float).
+ * B must be a multiple of 8 (FIRE_ERR_SHAPE otherwise). Synchronous; for
+ * verification against a reference. */
+fire_status_t fire_mlp_gradients(fire_mlp_t *m, const float *x, const float *tgt, const float *msk,
+                                 int64_t B, float *grads, float *loss, fire_stream_t stream);
+/* Parameter count of the packed layout W1, b1, W2, b2, W3 [16][H], b3,
+ * mean [Din], inv_std [Din]; fire_mlp_params copies them out (get) and/or in
+ * (set), host pointers. */
+int64_t fire_mlp_param_count(const fire_mlp_t *m);
+fire_status_t fire_mlp_params(fire_mlp_t *m, float *get, const float *set);
+/* Checkpoint (parameters, Adam moments, step and sample counters, FNV-1a
+ * checksum); load rejects a corrupt or mismatched file with
+ * FIRE_ERR_CHECKPOINT. */
+fire_status_t fire_mlp_save(fire_mlp_t *m, const char *path);
+fire_status_t fire_mlp_load(fire_mlp_t *m, const char *path);
+int64_t fire_mlp_next_sample(const fire_mlp_t *m);
+/* Attach a trained network to a context: fire_retrieve with init_mode
+ * FIRE_INIT_MLP then starts every pixel from the network's proposal. A pixel
+ * whose learned-start fit ends unconverged, or with a cost above three times
+ * the expected chi-square (n_used - 6) x noise variance, is re-fitted from the
+ * default start; the lower-cost fit is kept and the pixel is flagged
+ * FIRE_PX_F_MLP_FALLBACK. The call synchronises the stream once (to size the
+ * re-fit). m = NULL detaches. */
+fire_status_t fire_ctx_set_mlp(fire_ctx_t *ctx, fire_mlp_t *m);
+
 /* Counters of the last fire_retrieve on this context (synchronises it). */
 fire_status_t fire_get_stats(fire_ctx_t *ctx, fire_stats_t *stats);
 

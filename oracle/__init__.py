@@ -335,20 +335,24 @@ def mlp_forward(params, x):
     return a1, a2, z
 
 
-def mlp_backward(params, x, target, mask):
-    """Loss and FP64 gradients of the masked MSE in z-space."""
+def mlp_backward(params, x, target, mask, n_out=None):
+    """Loss and FP64 gradients of sum mask (z - t)^2 / (B n_out) in z-space;
+    mask is per sample [B, Dout] (or per output [Dout])."""
     W1, W2, W3 = (np.ascontiguousarray(params[k], np.float64) for k in ("W1", "W2", "W3"))
     x = np.ascontiguousarray(x, np.float64)
     a1, a2, z = mlp_forward(params, x)
     t = np.ascontiguousarray(target, np.float64)
-    mk = np.ascontiguousarray(mask, np.float64)
     B, Din = x.shape
     H, Dout = W1.shape[0], W3.shape[0]
+    mk = np.ascontiguousarray(np.broadcast_to(np.asarray(mask, np.float64), (B, Dout)))
+    if n_out is None:
+        n_out = int(np.count_nonzero(np.asarray(mask).reshape(-1, Dout).max(0)))
     g = {"W1": np.empty((H, Din)), "b1": np.empty(H), "W2": np.empty((H, H)), "b2": np.empty(H),
          "W3": np.empty((Dout, H)), "b3": np.empty(Dout)}
     v = C.c_void_p
     lib().orc_mlp_backward.restype = C.c_double
     loss = lib().orc_mlp_backward(C.c_int(B), C.c_int(Din), C.c_int(H), C.c_int(Dout),
+                                  C.c_int(n_out),
                                   *[v(a.ctypes.data) for a in (W1, W2, W3, x, a1, a2, z, t, mk,
                                                                g["W1"], g["b1"], g["W2"], g["b2"],
                                                                g["W3"], g["b3"])])

@@ -876,15 +876,15 @@ void orc_mlp_forward(int B, int Din, int H, int Dout, const double *W1, const do
   }
 }
 
-/* Mean-squared error over the masked outputs and its gradients (chain rule
- * through tanh and the two ReLUs). Returns the loss. */
-double orc_mlp_backward(int B, int Din, int H, int Dout, const double *W1, const double *W2,
-                        const double *W3, const double *x, const double *a1, const double *a2,
-                        const double *z, const double *t, const double *mask, double *gW1,
-                        double *gb1, double *gW2, double *gb2, double *gW3, double *gb3) {
-  double nused = 0;
-  for (int o = 0; o < Dout; o++) nused += mask[o];
-  double norm = 1.0 / (B * nused), loss = 0;
+/* Masked mean-squared error over B samples and its gradients (chain rule
+ * through tanh and the two ReLUs): loss = sum_{s,o} mask[s][o] (z - t)^2 /
+ * (B * n_out). Returns the loss. */
+double orc_mlp_backward(int B, int Din, int H, int Dout, int n_out, const double *W1,
+                        const double *W2, const double *W3, const double *x, const double *a1,
+                        const double *a2, const double *z, const double *t, const double *mask,
+                        double *gW1, double *gb1, double *gW2, double *gb2, double *gW3,
+                        double *gb3) {
+  double norm = 1.0 / ((double)B * n_out), loss = 0;
   memset(gW1, 0, sizeof(double) * H * Din);
   memset(gb1, 0, sizeof(double) * H);
   memset(gW2, 0, sizeof(double) * H * H);
@@ -896,8 +896,9 @@ double orc_mlp_backward(int B, int Din, int H, int Dout, const double *W1, const
   for (int s = 0; s < B; s++) {
     const double *xs = x + (size_t)s * Din, *A1 = a1 + (size_t)s * H, *A2 = a2 + (size_t)s * H;
     const double *Z = z + (size_t)s * Dout, *T = t + (size_t)s * Dout;
+    const double *Mk = mask + (size_t)s * Dout;
     for (int o = 0; o < Dout; o++) {
-      double e = (Z[o] - T[o]) * mask[o];
+      double e = (Z[o] - T[o]) * Mk[o];
       loss += e * e * norm;
       dy[o] = 2.0 * e * norm * (1.0 - Z[o] * Z[o]);
     }

@@ -83,10 +83,11 @@ void orc_planck_array(int64_t n, const double *lambda_nm, const double *T, doubl
 void orc_mlp_forward(int B, int Din, int H, int Dout, const double *W1, const double *b1,
                      const double *W2, const double *b2, const double *W3, const double *b3,
                      const double *x, double *a1, double *a2, double *z);
-double orc_mlp_backward(int B, int Din, int H, int Dout, const double *W1, const double *W2,
-                        const double *W3, const double *x, const double *a1, const double *a2,
-                        const double *z, const double *t, const double *mask, double *gW1,
-                        double *gb1, double *gW2, double *gb2, double *gW3, double *gb3);
+double orc_mlp_backward(int B, int Din, int H, int Dout, int n_out, const double *W1,
+                        const double *W2, const double *W3, const double *x, const double *a1,
+                        const double *a2, const double *z, const double *t, const double *mask,
+                        double *gW1, double *gb1, double *gW2, double *gb2, double *gW3,
+                        double *gb3);
 void orc_adam(int64_t n, double *w, const double *g, double *m, double *v, int t, double lr,
               double b1, double b2, double eps);
 void orc_normal_equations(const orc_tables_t *t, const orc_config_t *c, int stage,

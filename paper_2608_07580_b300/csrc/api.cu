@@ -9,6 +9,7 @@
 
 #include "../../include/firert.h"
 #include "internal.cuh"
+#include "mlp_internal.h"
 
 using namespace firert;
 
@@ -32,6 +33,15 @@ struct fire_ctx {
   float *d_s2x = nullptr;
   float *d_s2g = nullptr;
   int64_t s1_cap = 0;
+  // learned start: network, per-pixel starts, fallback list and re-fit outputs
+  fire_mlp_t *mlp = nullptr;
+  float *d_mlp_init = nullptr;
+  long long *d_fb_idx = nullptr;
+  float *d_fb_cost = nullptr;
+  unsigned long long *d_fb_count = nullptr;
+  int64_t mlp_cap = 0;
+  void *d_cmp = nullptr;
+  int64_t cmp_cap = 0;
   int last_launches = 0;
 };
 
@@ -117,7 +127,9 @@ bool priors_valid(const fire_priors_t &p, int K) {
   for (int i = 0; i < 6; i++)
     if (!(p.hi2[i] >= p.lo2[i]) || !(p.pp2[i] >= 0.f)) return false;
   if (!(p.lo1[K + 1] > 0.f) || !(p.lo2[1] > 0.f) || !(p.lo2[3] > 0.f)) return false;  // T, sigma > 0
-  if (p.init_mode != FIRE_INIT_DEFAULT && p.init_mode != FIRE_INIT_GIVEN) return false;
+  if (p.init_mode != FIRE_INIT_DEFAULT && p.init_mode != FIRE_INIT_GIVEN &&
+      p.init_mode != FIRE_INIT_MLP)
+    return false;
   return true;
 }
 
@@ -144,15 +156,113 @@ fire_status_t ensure_s1(fire_ctx *c, int64_t n) {
   c->s1_cap = 0;
   fire_status_t e = dev_alloc(&c->d_s1x, (size_t)n * (c->t.K + 2) * 4);
   if (e == FIRE_OK) e = dev_alloc(&c->d_s1meta, (size_t)n * 4);
-  if (e == FIRE_OK) e = dev_alloc(&c->d_s2x, (size_t)n * 31 * 4);
+  if (e == FIRE_OK) e = dev_alloc(&c->d_s2x, (size_t)n * 32 * 4);
   if (e == FIRE_OK) e = dev_alloc(&c->d_s2g, (size_t)n * 6 * 4);
   if (e == FIRE_OK) c->s1_cap = n;
   return e;
 }
 
+// carve per-pixel output arrays for n pixels out of one buffer
+size_t outputs_bytes(int64_t n, int K) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t szf = (size_t)n * 4;
+  return al(szf * (K + 8)) + 7 * al(szf) + al(szf * 21) + al((size_t)n) + al((size_t)n * 4);
+}
+KOut carve_outputs(void *buf, int64_t n, int K) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t szf = (size_t)n * 4;
+  char *q = (char *)buf;
+  auto carve = [&](size_t b) { char *r = q; q += al(b); return r; };
+  KOut o;
+  o.state = (float *)carve(szf * (K + 8));
+  o.ET = (float *)carve(szf);
+  o.sdT = (float *)carve(szf);
+  o.alpha = (float *)carve(szf);
+  o.var_ET = (float *)carve(szf);
+  o.cost = (float *)carve(szf);
+  o.rms = (float *)carve(szf);
+  o.hfdi = (float *)carve(szf);
+  o.cov = (float *)carve(szf * 21);
+  o.status = (uint8_t *)carve((size_t)n);
+  o.iters = (uint16_t *)carve((size_t)n * 4);
+  return o;
+}
+
+// The fit of p (device pointers set), with the learned start when asked:
+// network inference -> LM from those starts -> default-start re-fit of the
+// pixels the fallback rule flags -> keep the lower cost.
+fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
+  int blocks = 0;
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+  if (!learned) {
+    CK(launch_lm(p, c->num_sms, st, &blocks));
+    c->last_launches = 3;
+    return FIRE_OK;
+  }
+  const int64_t n = p.s.n_pix;
+  const int K = c->t.K;
+  if (n > c->mlp_cap) {
+    cudaFree(c->d_mlp_init);
+    cudaFree(c->d_fb_idx);
+    cudaFree(c->d_fb_cost);
+    c->d_mlp_init = nullptr;
+    c->d_fb_idx = nullptr;
+    c->d_fb_cost = nullptr;
+    c->mlp_cap = 0;
+    fire_status_t e = dev_alloc(&c->d_mlp_init, (size_t)n * (K + 8) * 4);
+    if (e == FIRE_OK) e = dev_alloc(&c->d_fb_idx, (size_t)n * 8);
+    if (e == FIRE_OK) e = dev_alloc(&c->d_fb_cost, (size_t)n * 4);
+    if (e == FIRE_OK && !c->d_fb_count) e = dev_alloc(&c->d_fb_count, 8);
+    if (e != FIRE_OK) return e;
+    c->mlp_cap = n;
+  }
+  fire_status_t e = fire_mlp_infer(c->mlp, p.s.rad, n, nullptr, c->d_mlp_init, (fire_stream_t)st);
+  if (e != FIRE_OK) return e;
+  CK(cudaMemsetAsync(c->d_fb_count, 0, 8, st));
+  p.s.init = c->d_mlp_init;
+  p.w.fb_idx = c->d_fb_idx;
+  p.w.fb_cost = c->d_fb_cost;
+  p.w.fb_count = c->d_fb_count;
+  CK(launch_lm(p, c->num_sms, st, &blocks));
+  unsigned long long nfb = 0;
+  CK(cudaMemcpyAsync(&nfb, c->d_fb_count, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  c->last_launches = 3 + 6;   // network (inference kernels) + fit
+  if (nfb == 0) return FIRE_OK;
+  if ((int64_t)nfb > c->cmp_cap) {
+    cudaFree(c->d_cmp);
+    c->d_cmp = nullptr;
+    c->cmp_cap = 0;
+    e = dev_alloc((char **)&c->d_cmp, outputs_bytes((int64_t)nfb, K));
+    if (e != FIRE_OK) return e;
+    c->cmp_cap = (int64_t)nfb;
+  }
+  KOut cmp = carve_outputs(c->d_cmp, (int64_t)nfb, K);
+  LMLaunch q = p;
+  q.s.n_pix = (int64_t)nfb;
+  q.s.idx = c->d_fb_idx;
+  q.s.init = nullptr;
+  q.w.fb_idx = nullptr;
+  q.w.fb_cost = nullptr;
+  q.w.fb_count = nullptr;
+  q.o = cmp;
+  q.o.hfdi = nullptr;
+  CK(cudaMemsetAsync(c->d_work, 0, 2 * 8, st));   // claim counters only; stats accumulate
+  CK(launch_lm(q, c->num_sms, st, &blocks));
+  CK(launch_merge_fallback(c->d_fb_idx, c->d_fb_cost, (long long)nfb, cmp, p.o, K, st));
+  c->last_launches += 4;
+  return FIRE_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+fire_status_t fire_ctx_set_mlp(fire_ctx_t *c, fire_mlp_t *m) {
+  if (!c) return FIRE_ERR_ARG;
+  c->mlp = m;
+  return FIRE_OK;
+}
 
 void fire_default_config(fire_config_t *c) {
   if (!c) return;
@@ -243,6 +353,11 @@ void fire_ctx_destroy(fire_ctx_t *ctx) {
   cudaFree(ctx->d_s1meta);
   cudaFree(ctx->d_s2x);
   cudaFree(ctx->d_s2g);
+  cudaFree(ctx->d_mlp_init);
+  cudaFree(ctx->d_fb_idx);
+  cudaFree(ctx->d_fb_cost);
+  cudaFree(ctx->d_fb_count);
+  cudaFree(ctx->d_cmp);
   delete ctx;
 }
 
@@ -347,6 +462,17 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
   return FIRE_OK;
 }
 
+}  // extern "C"
+
+void fire_ctx_tables(const fire_ctx_t *c, KTables *t, KConfig *k) {
+  *t = c->t;
+  fire_priors_t p;
+  fire_default_priors(&p, c->t.K, c->t.nt, c->t.tglo, c->t.tglo + c->t.tgstep * (c->t.nt - 1));
+  fill_kconfig(*k, c->cfg, p, c->t.K);
+}
+
+extern "C" {
+
 fire_status_t fire_window_bands(fire_ctx_t *c, int32_t *b1lo, int32_t *n1, int32_t *b2lo,
                                 int32_t *n2) {
   if (!c) return FIRE_ERR_ARG;
@@ -370,6 +496,8 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   }
   if (!priors_valid(*pri, c->t.K)) return FIRE_ERR_ARG;
   if (pri->init_mode == FIRE_INIT_GIVEN && !pri->init_state) return FIRE_ERR_ARG;
+  if (pri->init_mode == FIRE_INIT_MLP && !c->mlp) return FIRE_ERR_STATE;
+  const bool learned = pri->init_mode == FIRE_INIT_MLP;
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaMemsetAsync(c->d_work, 0, (size_t)(2 + ST_COUNT) * 8, st));
   c->last_launches = 0;
@@ -414,11 +542,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     p.o.hfdi = out->hfdi;
     p.o.status = out->status;
     p.o.iters = out->iters;
-    int blocks = 0;
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
-    CK(launch_lm(p, c->num_sms, st, &blocks));
-    c->last_launches = 3;
-    return FIRE_OK;
+    return run_fit(c, p, learned, st);
   }
 
   // host scene: stage inputs and outputs through one device buffer
@@ -462,10 +586,15 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   p.o.cov = out->cov ? o_cov : nullptr;
   p.o.status = out->status ? o_status : nullptr;
   p.o.iters = out->iters ? o_it : nullptr;
-  int blocks = 0;
-  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
-  CK(launch_lm(p, c->num_sms, st, &blocks));
-  c->last_launches = 3;
+  if (learned) {
+    // the fallback merge compares costs: keep them even if not requested
+    p.o.cost = o_cost;
+    p.o.status = o_status;
+  }
+  {
+    fire_status_t e = run_fit(c, p, learned, st);
+    if (e != FIRE_OK) return e;
+  }
   struct { void *h; void *d; size_t b; } back[] = {
       {out->state, o_state, s_state}, {out->ET, o_ET, szf}, {out->sdT, o_sdT, szf},
       {out->alpha, o_alpha, szf}, {out->var_ET, o_var, szf}, {out->cost, o_cost, szf},
@@ -541,6 +670,34 @@ fire_status_t fire_normal_equations(fire_ctx_t *c, int32_t stage, const float *r
   p.s.wv = wv_bin;
   p.w.err = c->d_err;
   return cuda_status(launch_normal_eq(p, stage, states, H, g, cost, (cudaStream_t)stream));
+}
+
+fire_status_t fire_gemm_bf16(const fire_gemm_t *q, fire_stream_t stream) {
+  if (!q || !q->A || !q->B || q->M < 0 || q->N < 0 || q->K < 0) return FIRE_ERR_ARG;
+  if (q->epi < 0 || q->epi > 3 || (q->epi == 3 && !q->mask)) return FIRE_ERR_ARG;
+  if ((q->K & 7) || (q->lda & 7) || (q->ldb & 7) || q->lda < q->K || q->ldb < q->K)
+    return FIRE_ERR_SHAPE;
+  GemmArgs g;
+  g.A = (const __nv_bfloat16 *)q->A;
+  g.B = (const __nv_bfloat16 *)q->B;
+  g.lda = q->lda;
+  g.ldb = q->ldb;
+  g.M = q->M;
+  g.N = q->N;
+  g.K = q->K;
+  g.epi = q->epi;
+  g.bias = q->bias;
+  g.mask = (const __nv_bfloat16 *)q->mask;
+  g.ldm = q->ldm;
+  g.Cf = q->Cf;
+  g.ldc = q->ldc;
+  g.Cb = (__nv_bfloat16 *)q->Cb;
+  g.ldcb = q->ldcb;
+  g.CbT = (__nv_bfloat16 *)q->CbT;
+  g.ldcbT = q->ldcbT;
+  g.accumulate = q->accumulate;
+  g.err = q->err;
+  return cuda_status(launch_gemm(g, (cudaStream_t)stream));
 }
 
 fire_status_t fire_block_mean(const float *src, int32_t w, int32_t h, int32_t nb, int32_t blk,

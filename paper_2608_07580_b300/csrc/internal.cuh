@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cuda_bf16.h>
 
 namespace firert {
 
@@ -56,11 +57,28 @@ struct KConfig {
   float ident_sd_et, ident_alpha_snr;
 };
 
+// one scene of a batched call: device pointers, its own outputs
+struct SceneItem {
+  const float *rad;        // [n][nb]
+  const uint16_t *wv;      // [n]
+  long long n;
+  struct KOutItem {
+    float *state, *ET, *sdT, *alpha, *cov, *var_ET, *cost, *rms, *hfdi;
+    uint8_t *status;
+    uint16_t *iters;
+  } out;
+};
+
 struct KScene {
   int64_t n_pix;
   const float *rad;        // [n_pix][nb]
   const uint16_t *wv;      // [n_pix]
-  const float *init;       // [n_pix][K+8] or nullptr
+  const float *init;       // [n_pix][K+8] or nullptr (indexed like rad)
+  const long long *idx;    // optional: fitted pixel i reads source row idx[i]
+  const SceneItem *items;  // optional: batched scenes (global pixel index over all)
+  const long long *prefix; // [n_items + 1] first global pixel of each scene
+  int n_items;
+  int claim;               // pixels claimed per atomic (autotuned)
   int gate;                // 1: HFDI gate
 };
 
@@ -84,6 +102,9 @@ struct KWork {
   int *s1meta;                  // [n_pix] status bits | 256 if the pixel goes on to stage 2
   float *s2x;                   // [n_pix][31] stage-2 state, J^T W J + P, costs, counts
   float *s2g;                   // [n_pix][6] stage-2 gradient at the final state
+  long long *fb_idx;            // learned-start fallback list (nullptr: no check)
+  float *fb_cost;               // cost of each listed pixel's first fit
+  unsigned long long *fb_count; // list length
 };
 
 struct LMLaunch {
@@ -94,6 +115,27 @@ struct LMLaunch {
   KWork w;
 };
 
+// BF16 tensor-core GEMM C = A B^T (kernels_gemm.cu)
+enum : int { EPI_F32 = 0, EPI_BIAS_RELU = 1, EPI_BIAS_TANH = 2, EPI_RELU_MASK = 3 };
+struct GemmArgs {
+  const __nv_bfloat16 *A, *B;   // [M][lda], [N][ldb], K-major
+  long long lda, ldb;
+  int M, N, K;
+  int epi;
+  const float *bias;            // [N] or nullptr
+  const __nv_bfloat16 *mask;    // [M][ldm] (EPI_RELU_MASK)
+  long long ldm;
+  float *Cf;                    // [M][ldc] fp32 or nullptr
+  long long ldc;
+  __nv_bfloat16 *Cb;            // [M][ldcb] bf16 or nullptr
+  long long ldcb;
+  __nv_bfloat16 *CbT;           // [N][ldcbT] bf16 transposed or nullptr
+  long long ldcbT;
+  int accumulate;               // Cf += result
+  int *err;                     // bounded-wait failure flag or nullptr
+};
+cudaError_t launch_gemm(const GemmArgs &g, cudaStream_t st);
+
 // host-side launchers (kernels_*.cu)
 cudaError_t launch_build_tables(const KTables &t, const float *wl, const float *e0, float cos_sza,
                                 const float *td, const float *tu, const float *ra, const float *sa,
@@ -101,6 +143,8 @@ cudaError_t launch_build_tables(const KTables &t, const float *wl, const float *
                                 const float win[6], cudaStream_t st);
 cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used);
 size_t lm_smem_bytes(const KTables &t);
+cudaError_t launch_merge_fallback(const long long *idx, const float *cost_first, long long nfb,
+                                  const KOut &compact, const KOut &out, int K, cudaStream_t st);
 cudaError_t launch_normal_eq(const LMLaunch &p, int stage, const float *states, float *H, float *g,
                              float *cost, cudaStream_t st);
 cudaError_t launch_forward(const KTables &t, int mode, const float *state, const uint16_t *wv,

@@ -1,6 +1,7 @@
 // kernels_aux.cu — table construction, the forward model (with optional
 // counter-based noise) and the block-mean coarsening kernel.
 #include "internal.cuh"
+#include "model.cuh"
 
 namespace firert {
 
@@ -57,21 +58,8 @@ __global__ void build_tables_kernel(KTables t, const float *wl, const float *e0,
   }
 }
 
-__device__ __forceinline__ unsigned long long sm_mix(unsigned long long z) {
-  // SplitMix64 output function (Steele, Lea & Flood 2014)
-  z += 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ float counter_uniform(unsigned long long kpix, unsigned long long idx) {
-  unsigned long long u = sm_mix(kpix ^ idx);
-  return (float)(((double)(u >> 11) + 1.0) * 1.1102230246251565e-16);  // (0, 1]
-}
-
-// Forward model, one warp per state: lanes build the grid weights of the two
-// mixture components (mode 2), then sweep the bands.
+// Forward model, one warp per state (the model itself is warp_forward in
+// model.cuh), with optional counter-based noise.
 __global__ void __launch_bounds__(256) forward_kernel(KTables t, int mode, const float *state,
                                                       const uint16_t *wv, long long n,
                                                       float nrel, float nabs,
@@ -84,75 +72,19 @@ __global__ void __launch_bounds__(256) forward_kernel(KTables t, int mode, const
   const int K = t.K, ns = mode == 1 ? K + 2 : K + 6;
   long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
   long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-  const float *img = t.image;
   for (long long i = gw; i < n; i += nw) {
     const float *s = state + i * ns;
     if (wv[i] >= t.nwv) {   // invalid water-vapour bin: NaN radiance, no table read
       for (int b = lane; b < t.nb; b += 32) out[i * t.nb + b] = __int_as_float(0x7fc00000);
       continue;
     }
-    const float4 *row = t.wvtab + (size_t)wv[i] * t.nb;
-    float a = mode == 1 ? s[K] : s[K + 5];
-    if (mode == 2 && a != 0.f) {
-      float mh = s[K], sh_ = s[K + 1], ms = s[K + 2], ss = s[K + 3], eta = s[K + 4];
-      float uh[4], us[4], Uh = 0.f, Us = 0.f;
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        int j = lane + 32 * q;
-        uh[q] = us[q] = 0.f;
-        if (j < t.nt) {
-          float T = t.tglo + j * t.tgstep;
-          float dh = T - mh, ds = T - ms;
-          uh[q] = __expf(-dh * dh / (2.f * sh_ * sh_));
-          us[q] = __expf(-ds * ds / (2.f * ss * ss));
-        }
-        Uh += uh[q];
-        Us += us[q];
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        Uh += __shfl_xor_sync(0xffffffffu, Uh, o);
-        Us += __shfl_xor_sync(0xffffffffu, Us, o);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        int j = lane + 32 * q;
-        if (j < t.nt) wsc[j] = eta * uh[q] / Uh + (1.f - eta) * us[q] / Us;
-      }
-      __syncwarp();
-    }
-    unsigned long long kpix = 0;
-    if (nrel > 0.f || nabs > 0.f)
-      kpix = sm_mix(sm_mix(sm_mix(seed) ^ sid) ^ (unsigned long long)(pix0 + i));
-    for (int b = lane; b < t.nb; b += 32) {
-      float4 q = row[b];
-      float rho = 0.f;
-      for (int k = 0; k < K; k++) rho += s[k] * img[t.lay.off_endm + k * t.nb + b];
-      float Lv = q.y + q.x * rho / (1.f - q.z * rho);
-      if (a != 0.f) {
-        if (mode == 1) {
-          float x = img[t.lay.off_c2l + b] / s[K + 1];
-          float e = expf(-x);
-          Lv += a * q.w * img[t.lay.off_c1l5 + b] * e / (1.f - e);
-        } else {
-          // thermal term on the grid: sum_j p_j B(lambda_b, T_j)
-          float x0 = img[t.lay.off_c2l + b], c1 = img[t.lay.off_c1l5 + b], acc = 0.f;
-          for (int j = 0; j < t.nt; j++) {
-            float e = expf(-x0 / (t.tglo + j * t.tgstep));
-            acc += wsc[j] * c1 * e / (1.f - e);
-          }
-          Lv += a * q.w * acc;
-        }
-      }
-      if (kpix) {
-        float u1 = counter_uniform(kpix, 2ull * b), u2 = counter_uniform(kpix, 2ull * b + 1);
-        float z = sqrtf(-2.f * logf(u1)) * cosf(6.283185307179586f * u2);
-        Lv += sqrtf(nrel * nrel * Lv * Lv + nabs * nabs) * z;
-      }
-      out[i * t.nb + b] = Lv;
-    }
-    __syncwarp();
+    const bool noisy = nrel > 0.f || nabs > 0.f;
+    const unsigned long long kpix = noisy ? sm_key(seed, sid, (unsigned long long)(pix0 + i)) : 0ull;
+    float *o = out + i * t.nb;
+    warp_forward(t, t.image, lane, mode, s, wv[i], wsc, [&](int b, float Lv) {
+      if (noisy) Lv += sqrtf(nrel * nrel * Lv * Lv + nabs * nabs) * counter_normal(kpix, b);
+      o[b] = Lv;
+    });
   }
 }
 

@@ -143,16 +143,22 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(GemmArgs g) {
     }
     uses[s]++;
     if (kc + 2 < nk) {
-      // the stage is reused: wait until the MMAs that read it completed
-      if (!mbar_wait(su32(&bar[s]), (uses[s] - 1) & 1)) { ok = false; break; }
+      // the stage is reused: wait until the MMAs that read it completed (the
+      // decision is made uniform across the CTA)
+      const bool w = mbar_wait(su32(&bar[s]), (uses[s] - 1) & 1);
+      if (!__syncthreads_and(w)) { ok = false; break; }
       load_chunk(kc + 2, s);
     }
   }
   // wait for the last commit of each stage that was used
-  for (int s = 0; s < 2 && ok; s++)
-    if (uses[s] && !mbar_wait(su32(&bar[s]), (uses[s] - 1) & 1)) ok = false;
+  if (ok) {
+    bool w = true;
+    for (int s = 0; s < 2; s++)
+      if (uses[s]) w = mbar_wait(su32(&bar[s]), (uses[s] - 1) & 1) && w;
+    ok = __syncthreads_and(w);
+  }
   if (!ok) {
-    if (tid == 0) atomicExch(g.err, 1);
+    if (tid == 0 && g.err) atomicExch(g.err, 1);
     // drain: bounded waits on whatever is still in flight, then free TMEM
     for (int s = 0; s < 2; s++)
       if (uses[s]) mbar_wait(su32(&bar[s]), (uses[s] - 1) & 1);

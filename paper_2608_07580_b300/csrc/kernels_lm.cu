@@ -422,8 +422,10 @@ struct Stage2 {
         float T = t.tglo + (float)j * t.tgstep;
         dh[q] = T - mh;
         ds[q] = T - ms;
-        uh[q] = __expf(-dh[q] * dh[q] * ih);
-        us[q] = __expf(-ds[q] * ds[q] * is);
+        // accurate expf: the weights' rounding sets how finely the cost
+        // differences of the last steps are resolved
+        uh[q] = expf(-dh[q] * dh[q] * ih);
+        us[q] = expf(-ds[q] * ds[q] * is);
       }
       mom[0] += uh[q];
       mom[1] += uh[q] * dh[q];
@@ -904,10 +906,10 @@ __device__ __forceinline__ bool stage_tables(const KTables &t, float *smem, unsi
   return false;
 }
 
-// pixel-claim helper: lane 0 takes kClaim pixels from a global counter
-__device__ __forceinline__ long long claim(unsigned long long *ctr, int lane) {
+// pixel-claim helper: lane 0 takes n pixels from a global counter
+__device__ __forceinline__ long long claim(unsigned long long *ctr, int lane, int n) {
   unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(ctr, (unsigned long long)kClaim);
+  if (lane == 0) base = atomicAdd(ctr, (unsigned long long)n);
   return (long long)__shfl_sync(kFull, base, 0);
 }
 
@@ -1003,8 +1005,57 @@ __device__ __forceinline__ void flush_stats(unsigned long long *cstat, const uns
     if (cstat[i]) atomicAdd(gstats + i, cstat[i]);
 }
 
+// Where pixel pix reads its inputs and writes its outputs: the single scene
+// (optionally through a subset index), or the scene of a batch that holds
+// global pixel pix (binary search over the scenes' first pixels).
+struct PixRef {
+  const float *row;
+  int wv;
+  const float *init;
+  KOut o;
+  long long opix;
+};
+
+__device__ __forceinline__ PixRef resolve(const LMLaunch &p, long long pix, int K) {
+  PixRef r;
+  const int nb = p.t.nb;
+  if (!p.s.items) {
+    const long long src = p.s.idx ? p.s.idx[pix] : pix;
+    r.row = p.s.rad + src * nb;
+    r.wv = p.s.wv[src];
+    r.init = p.s.init ? p.s.init + src * (K + 8) : nullptr;
+    r.o = p.o;
+    r.opix = pix;
+    return r;
+  }
+  int lo = 0, hi = p.s.n_items - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (p.s.prefix[mid] <= pix) lo = mid;
+    else hi = mid - 1;
+  }
+  const SceneItem &it = p.s.items[lo];
+  const long long loc = pix - p.s.prefix[lo];
+  r.row = it.rad + loc * nb;
+  r.wv = it.wv[loc];
+  r.init = nullptr;
+  r.o.state = it.out.state;
+  r.o.ET = it.out.ET;
+  r.o.sdT = it.out.sdT;
+  r.o.alpha = it.out.alpha;
+  r.o.cov = it.out.cov;
+  r.o.var_ET = it.out.var_ET;
+  r.o.cost = it.out.cost;
+  r.o.rms = it.out.rms;
+  r.o.hfdi = it.out.hfdi;
+  r.o.status = it.out.status;
+  r.o.iters = it.out.iters;
+  r.opix = loc;
+  return r;
+}
+
 constexpr int kFitted = 256;   // scratch flag: pixel goes on to stage 2
-constexpr int kS2Hand = 31;    // floats handed from stage 2 to finalize per pixel
+constexpr int kS2Hand = 32;    // floats handed from stage 2 to finalize per pixel
 
 // ---- stage 1: checks, HFDI gate, stage-1 fit -> scratch
 template <int K, int S1, int WPB>
@@ -1027,14 +1078,16 @@ __global__ void __launch_bounds__(WPB * 32, LM1_MINB) lm_stage1_kernel(const __g
   unsigned long long mine[ST_COUNT];
 #pragma unroll
   for (int i = 0; i < ST_COUNT; i++) mine[i] = 0ull;
+  const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
   for (;;) {
-    const long long base = claim(p.w.counter, lane);
+    const long long base = claim(p.w.counter, lane, nclaim);
     if (base >= p.s.n_pix) break;
-    for (int ci = 0; ci < kClaim; ci++) {
+    for (int ci = 0; ci < nclaim; ci++) {
       const long long pix = base + ci;
       if (pix >= p.s.n_pix) break;
-      const float *row = p.s.rad + pix * t.nb;
-      const int wvb = p.s.wv[pix];
+      const PixRef ref = resolve(p, pix, K);
+      const float *row = ref.row;
+      const int wvb = ref.wv;
       const bool wv_ok = wvb < t.nwv;   // an out-of-range bin is an invalid input
       pc.wvrow = t.wvtab + (size_t)(wv_ok ? wvb : 0) * t.nb;
       bool fin = true;
@@ -1057,7 +1110,7 @@ __global__ void __launch_bounds__(WPB * 32, LM1_MINB) lm_stage1_kernel(const __g
         if (n1u <= K + 2 || n2u <= 6) {
           status = PX_ALL_MASKED;
         } else {
-          const float *ini = p.s.init ? p.s.init + pix * NSx : nullptr;
+          const float *ini = ref.init;
           if (ini) {
 #pragma unroll
             for (int i = 0; i < K + 2; i++) x1[i] = ini[i];
@@ -1083,10 +1136,12 @@ __global__ void __launch_bounds__(WPB * 32, LM1_MINB) lm_stage1_kernel(const __g
         }
       }
       // hand-over to stage 2, or the final outputs of a pixel that is not fitted
+      const KOut &o = ref.o;
+      const long long op = ref.opix;
       if (lane == 0) {
         p.w.s1meta[pix] = status | (fitted ? kFitted : 0);
-        if (p.o.hfdi) p.o.hfdi[pix] = hf;
-        if (p.o.iters) p.o.iters[2 * pix] = (uint16_t)it1;
+        if (o.hfdi) o.hfdi[op] = hf;
+        if (o.iters) o.iters[2 * op] = (uint16_t)it1;
       }
       if (fitted) {
         if (lane < K + 2) {
@@ -1097,18 +1152,18 @@ __global__ void __launch_bounds__(WPB * 32, LM1_MINB) lm_stage1_kernel(const __g
         }
       } else {
         const float nan = __int_as_float(0x7fc00000);
-        if (p.o.state)
-          for (int i = lane; i < NSx; i += 32) p.o.state[pix * NSx + i] = nan;
-        if (p.o.cov && lane < 21) p.o.cov[pix * 21 + lane] = nan;
+        if (o.state)
+          for (int i = lane; i < NSx; i += 32) o.state[op * NSx + i] = nan;
+        if (o.cov && lane < 21) o.cov[op * 21 + lane] = nan;
         if (lane == 0) {
-          if (p.o.ET) p.o.ET[pix] = nan;
-          if (p.o.sdT) p.o.sdT[pix] = nan;
-          if (p.o.alpha) p.o.alpha[pix] = nan;
-          if (p.o.var_ET) p.o.var_ET[pix] = nan;
-          if (p.o.cost) p.o.cost[pix] = nan;
-          if (p.o.rms) p.o.rms[pix] = nan;
-          if (p.o.status) p.o.status[pix] = (uint8_t)status;
-          if (p.o.iters) p.o.iters[2 * pix + 1] = 0;
+          if (o.ET) o.ET[op] = nan;
+          if (o.sdT) o.sdT[op] = nan;
+          if (o.alpha) o.alpha[op] = nan;
+          if (o.var_ET) o.var_ET[op] = nan;
+          if (o.cost) o.cost[op] = nan;
+          if (o.rms) o.rms[op] = nan;
+          if (o.status) o.status[op] = (uint8_t)status;
+          if (o.iters) o.iters[2 * op + 1] = 0;
         }
 #pragma unroll
         for (int k = 0; k < 8; k++) mine[ST_STATUS0 + k] += ((status & 7) == k) ? 1ull : 0ull;
@@ -1140,17 +1195,19 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
   unsigned long long mine[ST_COUNT];
 #pragma unroll
   for (int i = 0; i < ST_COUNT; i++) mine[i] = 0ull;
+  const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
   for (;;) {
-    const long long base = claim(p.w.counter + 1, lane);
+    const long long base = claim(p.w.counter + 1, lane, nclaim);
     if (base >= p.s.n_pix) break;
-    for (int ci = 0; ci < kClaim; ci++) {
+    for (int ci = 0; ci < nclaim; ci++) {
       const long long pix = base + ci;
       if (pix >= p.s.n_pix) break;
       const int meta = p.w.s1meta[pix];
       if (!(meta & kFitted)) continue;
       int status = meta & 0xff;
-      const float *row = p.s.rad + pix * t.nb;
-      pc.wvrow = t.wvtab + (size_t)p.s.wv[pix] * t.nb;
+      const PixRef ref = resolve(p, pix, K);
+      const float *row = ref.row;
+      pc.wvrow = t.wvtab + (size_t)ref.wv * t.nb;
       pc.node_evals = 0;
       float x1[K + 2];
 #pragma unroll
@@ -1161,7 +1218,7 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
       Stage2<S2> s2;
       const int n2u = setup2<K, S2>(s2, pc, row, xs);
       float x2[6];
-      const float *ini = p.s.init ? p.s.init + pix * NSx : nullptr;
+      const float *ini = ref.init;
       if (ini) {
 #pragma unroll
         for (int i = 0; i < 6; i++) x2[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
@@ -1186,7 +1243,7 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
       mine[ST_NODEBAND2] += (unsigned long long)pc.node_evals * (unsigned long long)t.n2;
       // hand the final state and normal equations to the finalize kernel
       float* hand = p.w.s2x + pix * kS2Hand;
-      if (lane < kS2Hand) {
+      {
         float v = 0.f;
 #pragma unroll
         for (int k = 0; k < 6; k++) v = (lane == k) ? x2[k] : v;
@@ -1196,6 +1253,7 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
         v = (lane == 28) ? r2.cdata : v;
         v = (lane == 29) ? __int_as_float(n2u) : v;
         v = (lane == 30) ? __int_as_float(status | (r2.iters << 8)) : v;
+        v = (lane == 31) ? s2.psc : v;
         hand[lane] = v;
       }
       if (lane < 6) {
@@ -1265,20 +1323,34 @@ __global__ void __launch_bounds__(128) finalize_kernel(const __grid_constant__ L
     const bool ident = io.cov_ok && isfinite(sdE) && sdE <= (double)c.ident_sd_et &&
                        (double)x2[5] >= (double)c.ident_alpha_snr * sda && !act_a && x2[5] > 0.f;
     if (!ident) status |= PX_F_NOT_IDENT;
-    if (p.o.state) {
-      for (int k = 0; k < K + 2; k++) p.o.state[pix * NSx + k] = p.w.s1x[pix * (K + 2) + k];
-      for (int k = 0; k < 6; k++) p.o.state[pix * NSx + K + 2 + k] = x2[k];
+    if (p.w.fb_idx) {
+      // fallback rule of the learned start: the fit did not converge, or its
+      // cost exceeds three times the expected chi-square (n_used - 6) psc
+      const float psc = hand[31];
+      const float expect = (float)(n2u - 6) * (c.weighted ? 1.f : psc);
+      if ((status & 7) != PX_CONVERGED || cost > 3.f * expect) {
+        unsigned long long j = atomicAdd(p.w.fb_count, 1ull);
+        p.w.fb_idx[j] = pix;
+        p.w.fb_cost[j] = cost;
+      }
     }
-    if (p.o.cov)
-      for (int k = 0; k < 21; k++) p.o.cov[pix * 21 + k] = io.cov[k];
-    if (p.o.ET) p.o.ET[pix] = ET;
-    if (p.o.sdT) p.o.sdT[pix] = sdT;
-    if (p.o.alpha) p.o.alpha[pix] = x2[5];
-    if (p.o.var_ET) p.o.var_ET[pix] = (float)io.vE;
-    if (p.o.cost) p.o.cost[pix] = cost;
-    if (p.o.rms) p.o.rms[pix] = rms;
-    if (p.o.status) p.o.status[pix] = (uint8_t)status;
-    if (p.o.iters) p.o.iters[2 * pix + 1] = (uint16_t)it2;
+    const PixRef ref = resolve(p, pix, K);
+    const KOut &o = ref.o;
+    const long long op = ref.opix;
+    if (o.state) {
+      for (int k = 0; k < K + 2; k++) o.state[op * NSx + k] = p.w.s1x[pix * (K + 2) + k];
+      for (int k = 0; k < 6; k++) o.state[op * NSx + K + 2 + k] = x2[k];
+    }
+    if (o.cov)
+      for (int k = 0; k < 21; k++) o.cov[op * 21 + k] = io.cov[k];
+    if (o.ET) o.ET[op] = ET;
+    if (o.sdT) o.sdT[op] = sdT;
+    if (o.alpha) o.alpha[op] = x2[5];
+    if (o.var_ET) o.var_ET[op] = (float)io.vE;
+    if (o.cost) o.cost[op] = cost;
+    if (o.rms) o.rms[op] = rms;
+    if (o.status) o.status[op] = (uint8_t)status;
+    if (o.iters) o.iters[2 * op + 1] = (uint16_t)it2;
     st_fp64 += (status & PX_F_FP64) ? 1ull : 0ull;
 #pragma unroll
     for (int k = 0; k < 8; k++) st_s[k] += ((status & 7) == k) ? 1ull : 0ull;
@@ -1298,6 +1370,35 @@ __global__ void __launch_bounds__(128) finalize_kernel(const __grid_constant__ L
   __syncthreads();
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
     if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
+}
+
+// ---- keep the lower-cost of the learned-start fit and the default-start
+// re-fit of each flagged pixel; both get the MLP_FALLBACK flag
+__global__ void merge_fallback_kernel(const long long *idx, const float *cost_first, long long nfb,
+                                      KOut compact, KOut out, int K) {
+  const int NSx = K + 8;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nfb;
+       j += (long long)gridDim.x * blockDim.x) {
+    const long long pix = idx[j];
+    const float c2 = compact.cost[j];
+    const bool take = c2 < cost_first[j] || isnan(cost_first[j]);
+    if (take) {
+      if (out.state) for (int k = 0; k < NSx; k++) out.state[pix * NSx + k] = compact.state[j * NSx + k];
+      if (out.cov) for (int k = 0; k < 21; k++) out.cov[pix * 21 + k] = compact.cov[j * 21 + k];
+      if (out.ET) out.ET[pix] = compact.ET[j];
+      if (out.sdT) out.sdT[pix] = compact.sdT[j];
+      if (out.alpha) out.alpha[pix] = compact.alpha[j];
+      if (out.var_ET) out.var_ET[pix] = compact.var_ET[j];
+      if (out.cost) out.cost[pix] = c2;
+      if (out.rms) out.rms[pix] = compact.rms[j];
+      if (out.iters) {
+        out.iters[2 * pix] = compact.iters[2 * j];
+        out.iters[2 * pix + 1] = compact.iters[2 * j + 1];
+      }
+    }
+    if (out.status)
+      out.status[pix] = (uint8_t)((take ? compact.status[j] : out.status[pix]) | PX_F_MLP_FALLBACK);
+  }
 }
 
 // ---- one evaluation of a stage's normal equations per state (test hook)
@@ -1377,7 +1478,8 @@ cudaError_t launch_persistent(Kern kern, const LMLaunch &p, int num_sms, cudaStr
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWPB * 32, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  long long need = (p.s.n_pix + (long long)kWPB * kClaim - 1) / ((long long)kWPB * kClaim);
+  const int cl = p.s.claim > 0 ? p.s.claim : kClaim;
+  long long need = (p.s.n_pix + (long long)kWPB * cl - 1) / ((long long)kWPB * cl);
   long long blocks = (long long)num_sms * occ;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
@@ -1439,6 +1541,15 @@ cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *bloc
     case 5: return launch_k<5>(p, num_sms, st, blocks_used);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_merge_fallback(const long long *idx, const float *cost_first, long long nfb,
+                                  const KOut &compact, const KOut &out, int K, cudaStream_t st) {
+  if (nfb <= 0) return cudaSuccess;
+  long long blocks = (nfb + 127) / 128;
+  if (blocks > 4096) blocks = 4096;
+  merge_fallback_kernel<<<(int)blocks, 128, 0, st>>>(idx, cost_first, nfb, compact, out, K);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_normal_eq(const LMLaunch &p, int stage, const float *states, float *H, float *g,

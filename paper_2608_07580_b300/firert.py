@@ -24,7 +24,10 @@ PX_F_FP64, PX_F_NOT_IDENT, PX_F_MLP_FALLBACK, PX_F_S1_MAXITER = 8, 16, 32, 64
 
 SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fire_ctx_destroy",
            "fire_retrieve", "fire_forward", "fire_block_mean", "fire_get_stats",
-           "fire_window_bands", "fire_status_str", "fire_normal_equations")
+           "fire_window_bands", "fire_status_str", "fire_normal_equations", "fire_gemm_bf16",
+           "fire_mlp_create", "fire_mlp_destroy", "fire_mlp_train", "fire_mlp_infer",
+           "fire_mlp_gradients", "fire_mlp_param_count", "fire_mlp_params", "fire_mlp_save",
+           "fire_mlp_load", "fire_mlp_next_sample", "fire_ctx_set_mlp")
 
 
 class FireError(RuntimeError):
@@ -70,6 +73,21 @@ class Outputs_t(C.Structure):
                                           "rms", "hfdi", "status", "iters")]
 
 
+class Gemm_t(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("lda", C.c_int64), ("B", C.c_void_p), ("ldb", C.c_int64),
+                ("M", C.c_int32), ("N", C.c_int32), ("K", C.c_int32), ("epi", C.c_int32),
+                ("bias", C.c_void_p), ("mask", C.c_void_p), ("ldm", C.c_int64),
+                ("Cf", C.c_void_p), ("ldc", C.c_int64), ("Cb", C.c_void_p), ("ldcb", C.c_int64),
+                ("CbT", C.c_void_p), ("ldcbT", C.c_int64), ("accumulate", C.c_int32),
+                ("err", C.c_void_p)]
+
+
+class MlpTrain_t(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("batch", C.c_int32), ("lr", C.c_float),
+                ("pfire", C.c_float), ("noise_rel", C.c_float), ("noise_abs", C.c_float),
+                ("seed", C.c_uint64), ("sample0", C.c_int64)]
+
+
 class Stats_t(C.Structure):
     _fields_ = [("n_pixels", C.c_uint64), ("sum_it1", C.c_uint64), ("sum_it2", C.c_uint64),
                 ("n_fp64_pixels", C.c_uint64), ("band_evals1", C.c_uint64),
@@ -102,6 +120,29 @@ def _load():
     lib.fire_normal_equations.argtypes = [vp, i32, vp, vp, vp, i64, C.POINTER(Priors_t), vp, vp,
                                           vp, vp]
     lib.fire_normal_equations.restype = C.c_int
+    lib.fire_gemm_bf16.argtypes = [C.POINTER(Gemm_t), vp]
+    lib.fire_gemm_bf16.restype = C.c_int
+    lib.fire_mlp_create.argtypes = [C.POINTER(vp), vp, i32, u64]
+    lib.fire_mlp_create.restype = C.c_int
+    lib.fire_mlp_destroy.argtypes = [vp]
+    lib.fire_mlp_train.argtypes = [vp, C.POINTER(MlpTrain_t), vp, vp]
+    lib.fire_mlp_train.restype = C.c_int
+    lib.fire_mlp_infer.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.fire_mlp_infer.restype = C.c_int
+    lib.fire_mlp_gradients.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+    lib.fire_mlp_gradients.restype = C.c_int
+    lib.fire_mlp_param_count.argtypes = [vp]
+    lib.fire_mlp_param_count.restype = i64
+    lib.fire_mlp_params.argtypes = [vp, vp, vp]
+    lib.fire_mlp_params.restype = C.c_int
+    lib.fire_mlp_save.argtypes = [vp, C.c_char_p]
+    lib.fire_mlp_save.restype = C.c_int
+    lib.fire_mlp_load.argtypes = [vp, C.c_char_p]
+    lib.fire_mlp_load.restype = C.c_int
+    lib.fire_mlp_next_sample.argtypes = [vp]
+    lib.fire_mlp_next_sample.restype = i64
+    lib.fire_ctx_set_mlp.argtypes = [vp, vp]
+    lib.fire_ctx_set_mlp.restype = C.c_int
     lib.fire_status_str.argtypes = [C.c_int]
     lib.fire_status_str.restype = C.c_char_p
     return lib
@@ -211,8 +252,14 @@ class Context:
             return {k: torch.empty(s, dtype=tm[d], device="cuda") for k, (s, d) in shapes.items()}
         return {k: np.empty(s, dtype=d) for k, (s, d) in shapes.items()}
 
+    def set_mlp(self, mlp):
+        """Attach a trained network: retrieve(..., learned_start=True) then
+        starts every pixel from its proposal (with the plain-LM fallback)."""
+        _check(lib.fire_ctx_set_mlp(self._h, None if mlp is None else mlp._h), "fire_ctx_set_mlp")
+        self._mlp = mlp
+
     def retrieve(self, radiance, wv_bin, priors=None, init_state=None, gate_hfdi=False,
-                 outputs=None, stream=None):
+                 outputs=None, stream=None, learned_start=False):
         """Fit every pixel. radiance [n, n_bands] float32 and wv_bin [n] (uint16
         numpy or int16/uint16-bit torch): torch CUDA tensors for device
         scenes, numpy arrays for host scenes (staged inside the call)."""
@@ -225,6 +272,8 @@ class Context:
             outputs = self.alloc_outputs(n, device=not host)
         pri = Priors_t()
         C.memmove(C.byref(pri), C.byref(priors), C.sizeof(Priors_t))
+        if learned_start:
+            pri.init_mode = FIRE_INIT_MLP
         if host:
             rad = np.ascontiguousarray(radiance, dtype=np.float32)
             wv = np.ascontiguousarray(wv_bin, dtype=np.uint16)
@@ -294,3 +343,107 @@ def block_mean(src, width, height, n_bands, block=12, stream=None):
     _check(lib.fire_block_mean(_dptr(src, torch.float32), width, height, n_bands, block,
                                _dptr(dst), _stream_ptr(stream)), "fire_block_mean")
     return dst
+
+
+def gemm_bf16(A, B, epi=0, bias=None, mask=None, Cf=None, Cb=None, CbT=None, accumulate=False,
+              err=None, stream=None):
+    """C = A B^T on the tensor cores (A [M, K], B [N, K] bf16 CUDA tensors)."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    g = Gemm_t(_dptr(A, torch.bfloat16), A.stride(0), _dptr(B, torch.bfloat16), B.stride(0),
+               M, N, K, epi, _dptr(bias), _dptr(mask), 0 if mask is None else mask.stride(0),
+               _dptr(Cf), 0 if Cf is None else Cf.stride(0), _dptr(Cb),
+               0 if Cb is None else Cb.stride(0), _dptr(CbT), 0 if CbT is None else CbT.stride(0),
+               int(bool(accumulate)), _dptr(err))
+    _check(lib.fire_gemm_bf16(C.byref(g), _stream_ptr(stream)), "fire_gemm_bf16")
+
+
+class MLP:
+    """The learned initial-state proposal of a context (tensor-core MLP)."""
+
+    def __init__(self, ctx, hidden=512, seed=0):
+        h = C.c_void_p()
+        _check(lib.fire_mlp_create(C.byref(h), ctx._h, hidden, seed), "fire_mlp_create")
+        self._h, self.ctx, self.hidden = h, ctx, hidden
+        self.din = (ctx.n_bands + 15) // 16 * 16
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.fire_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def train(self, steps, batch=4096, lr=1e-3, pfire=0.5, noise_rel=0.005, noise_abs=1e-4,
+              seed=0, sample0=None, stream=None):
+        """Adam steps on fresh synthetic batches; returns the per-step losses."""
+        if sample0 is None:
+            sample0 = lib.fire_mlp_next_sample(self._h)
+        cfg = MlpTrain_t(steps, batch, lr, pfire, noise_rel, noise_abs, seed, sample0)
+        loss = np.zeros(max(steps, 1), dtype=np.float32)
+        _check(lib.fire_mlp_train(self._h, C.byref(cfg), loss.ctypes.data, _stream_ptr(stream)),
+               "fire_mlp_train")
+        return loss[:steps]
+
+    def infer(self, radiance, stream=None):
+        import torch
+        n = int(radiance.shape[0])
+        z = torch.empty((n, 16), dtype=torch.float32, device="cuda")
+        init = torch.empty((n, self.ctx.n_endm + 8), dtype=torch.float32, device="cuda")
+        _check(lib.fire_mlp_infer(self._h, _dptr(radiance, torch.float32), n, _dptr(z), _dptr(init),
+                                  _stream_ptr(stream)), "fire_mlp_infer")
+        return z, init
+
+    def gradients(self, x, tgt, msk, stream=None):
+        """Gradients of the masked MSE at standardised inputs x [B, Din] (fp32)."""
+        import torch
+        B = int(x.shape[0])
+        H, D = self.hidden, self.din
+        n = H * D + H + H * H + H + H * 16 + 16
+        g = torch.empty(n, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        _check(lib.fire_mlp_gradients(self._h, _dptr(x, torch.float32), _dptr(tgt, torch.float32),
+                                      _dptr(msk, torch.float32), B, _dptr(g), _dptr(loss),
+                                      _stream_ptr(stream)), "fire_mlp_gradients")
+        g = g.cpu().numpy()
+        o, out = 0, {}
+        for k, shp in (("W1", (H, D)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)),
+                       ("W3T", (H, 16)), ("b3", (16,))):
+            sz = int(np.prod(shp))
+            out[k] = g[o:o + sz].reshape(shp)
+            o += sz
+        return out, float(loss.item())
+
+    def params(self, set_params=None):
+        """Get (and optionally set) the packed parameters as a dict of arrays."""
+        H, D = self.hidden, self.din
+        n = lib.fire_mlp_param_count(self._h)
+        shapes = (("W1", (H, D)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (16, H)),
+                  ("b3", (16,)), ("mean", (D,)), ("istd", (D,)))
+        if set_params is not None:
+            flat = np.concatenate([np.asarray(set_params[k], np.float32).ravel() for k, _ in shapes])
+            assert flat.size == n
+            _check(lib.fire_mlp_params(self._h, None, flat.ctypes.data), "fire_mlp_params")
+        buf = np.empty(n, dtype=np.float32)
+        _check(lib.fire_mlp_params(self._h, buf.ctypes.data, None), "fire_mlp_params")
+        o, out = 0, {}
+        for k, shp in shapes:
+            sz = int(np.prod(shp))
+            out[k] = buf[o:o + sz].reshape(shp)
+            o += sz
+        return out
+
+    def save(self, path):
+        _check(lib.fire_mlp_save(self._h, str(path).encode()), "fire_mlp_save")
+
+    def load(self, path):
+        _check(lib.fire_mlp_load(self._h, str(path).encode()), "fire_mlp_load")
+
+    @property
+    def next_sample(self):
+        return lib.fire_mlp_next_sample(self._h)

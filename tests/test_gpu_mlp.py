@@ -1,0 +1,104 @@
+"""The learned initial-state proposal: tensor-core forward/backward against
+the FP64 oracle's MLP (weights and inputs from a seeded generator, rounded
+to bf16 as the kernels see them), training progress, checkpoint resume and
+corruption, and what the trained network gains over plain LM."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2608_07580_b300 import firert
+    return torch, firert
+
+
+def _bf16(a):
+    import torch
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def test_gradients_match_oracle(env):
+    torch, fr = env
+    t = synth.make_tables()
+    ctx = fr.Context(t)
+    H = 64
+    mlp = fr.MLP(ctx, hidden=H, seed=1)
+    D = mlp.din
+    rng = np.random.default_rng(4)
+    p = {"W1": rng.normal(0, 0.08, (H, D)), "b1": rng.normal(0, 0.1, H),
+         "W2": rng.normal(0, 0.15, (H, H)), "b2": rng.normal(0, 0.1, H),
+         "W3": rng.normal(0, 0.15, (16, H)), "b3": rng.normal(0, 0.1, 16),
+         "mean": np.zeros(D), "istd": np.ones(D)}
+    mlp.params(p)
+    B = 256
+    x = rng.normal(size=(B, D)).astype(np.float32)
+    x[:, 284:] = 0
+    tgt = np.tanh(rng.normal(size=(B, 16))).astype(np.float32)
+    msk = (rng.uniform(size=(B, 16)) < 0.8).astype(np.float32)
+    msk[:, 9:] = 0
+    g, loss = mlp.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda(),
+                            torch.from_numpy(msk).cuda())
+    ref = {k: _bf16(p[k]) if k.startswith("W") else p[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    lo, go, _ = oracle.mlp_backward(ref, _bf16(x), tgt, msk, n_out=9)
+    assert abs(loss / lo - 1) < 2e-2
+    pairs = (("W1", g["W1"], go["W1"]), ("b1", g["b1"], go["b1"]), ("W2", g["W2"], go["W2"]),
+             ("b2", g["b2"], go["b2"]), ("W3", g["W3T"].T, go["W3"]), ("b3", g["b3"], go["b3"]))
+    for name, a, b in pairs:
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel < 2e-2, (name, rel)
+
+
+def test_training_reduces_loss_and_resumes(env, tmp_path):
+    torch, fr = env
+    t = synth.make_tables()
+    ctx = fr.Context(t)
+    mlp = fr.MLP(ctx, hidden=256, seed=2)
+    l0 = mlp.train(60, batch=2048, lr=2e-3, seed=5)
+    assert np.all(np.isfinite(l0))
+    assert l0[-10:].mean() < 0.6 * l0[:5].mean()
+    ck = tmp_path / "mlp.ckpt"
+    mlp.save(ck)
+    la = mlp.train(8, batch=2048, lr=2e-3, seed=5)
+    mlp2 = fr.MLP(ctx, hidden=256, seed=99)
+    mlp2.load(ck)
+    lb = mlp2.train(8, batch=2048, lr=2e-3, seed=5)
+    assert np.allclose(la, lb, rtol=1e-4, atol=1e-8)
+    raw = bytearray(ck.read_bytes())
+    raw[200] ^= 0xFF
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(fr.FireError):
+        mlp2.load(bad)
+
+
+def test_learned_start_gains_over_plain_lm(env):
+    """A trained network cuts the LM iterations on a fire scene; plain LM
+    judges it: the learned-start E[T] agrees with the plain-LM E[T] on the
+    well-identified pixels where both converge to the same minimum."""
+    torch, fr = env
+    import sys
+    sys.path.insert(0, __import__("os").path.dirname(__file__))
+    from scenes import config1
+    t, tr, L = config1(seed=3)
+    ctx = fr.Context(t)
+    mlp = fr.MLP(ctx, hidden=512, seed=3)
+    mlp.train(400, batch=4096, lr=1e-3, seed=11)
+    ctx.set_mlp(mlp)
+    Ld = torch.from_numpy(L).cuda()
+    wd = torch.from_numpy(tr.wv_bin.astype(np.int16)).cuda()
+    plain = {k: v.cpu().numpy() for k, v in ctx.retrieve(Ld, wd).items()}
+    learned = {k: v.cpu().numpy() for k, v in ctx.retrieve(Ld, wd, learned_start=True).items()}
+    it_p = plain["iters"].astype(np.int64).sum(1).mean()
+    it_l = learned["iters"].astype(np.int64).sum(1).mean()
+    print("mean iterations plain %.2f learned %.2f, fallback %.3f" % (
+        it_p, it_l, np.mean((learned["status"] & 32) > 0)))
+    assert it_l < it_p
+    good = ((plain["status"] & 23) == 0) & ((learned["status"] & 7) == 0)
+    agree = np.abs(plain["ET"] - learned["ET"])[good] <= 0.5
+    assert good.sum() > 20 and agree.mean() > 0.8
