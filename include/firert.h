@@ -152,7 +152,8 @@ typedef struct {
 /* Counters of the last retrieve call (read after the stream synchronises). */
 typedef struct {
   uint64_t n_pixels, sum_it1, sum_it2, n_fp64_pixels;
-  uint64_t band_evals1, band_evals2, node_band_evals2;  /* work units */
+  uint64_t band_evals1, band_evals2, node_band_evals2;  /* work units: full evaluations */
+  uint64_t trial_band_evals2, trial_node_band_evals2;   /* stage-2 decrease-only trials */
   uint64_t status_counts[8];
   double flops;                     /* algorithmic flops of the fit */
   int32_t kernel_launches;
@@ -308,6 +309,44 @@ int64_t fire_mlp_next_sample(const fire_mlp_t *m);
  * FIRE_PX_F_MLP_FALLBACK. The call synchronises the stream once (to size the
  * re-fit). m = NULL detaches. */
 fire_status_t fire_ctx_set_mlp(fire_ctx_t *ctx, fire_mlp_t *m);
+
+/* ---- Batched uneven scenes (one persistent launch over all pixels of all
+ * scenes; device pointers; default start only). Scenes of any size share the
+ * context's tables; each has its own outputs (any may be NULL). */
+typedef struct {
+  int64_t n_pix;
+  const float *radiance;     /* [n_pix][n_bands] */
+  const uint16_t *wv_bin;    /* [n_pix] */
+  fire_outputs_t out;
+} fire_batch_item_t;
+/* Errors: FIRE_ERR_ARG (bad item, init_mode not DEFAULT), FIRE_ERR_NOMEM,
+ * FIRE_ERR_CUDA. Synchronises the stream once to upload the scene table. */
+fire_status_t fire_retrieve_batch(fire_ctx_t *ctx, const fire_batch_item_t *items, int32_t n_items,
+                                  const fire_priors_t *pri, int32_t gate_mode,
+                                  fire_stream_t stream);
+/* CUDA graph of the whole batched fit (scene-table upload, counter resets,
+ * the three kernels) over the given buffers; replay it with
+ * fire_graph_launch after refilling those buffers with new scenes of the
+ * same sizes. The graph owns its scratch (stage hand-over, counters), so
+ * later calls on the context leave it valid, but two replays of one graph
+ * must not overlap; fire_get_stats does not see graph replays. The context
+ * must outlive the graph (its tables are read by the replays). */
+typedef struct fire_graph fire_graph_t;
+fire_status_t fire_graph_capture(fire_ctx_t *ctx, const fire_batch_item_t *items, int32_t n_items,
+                                 const fire_priors_t *pri, int32_t gate_mode, fire_graph_t **out);
+fire_status_t fire_graph_launch(fire_graph_t *g, fire_stream_t stream);
+void fire_graph_destroy(fire_graph_t *g);
+/* Autotuner: times each launch shape (stage-1 occupancy variant 0 = one CTA
+ * of 8 warps per SM with up to 255 registers, 1 = two CTAs with 128; pixels
+ * per work claim 1, 2, 4, 8) on the n given device pixels and keeps the
+ * fastest for the context. fire_set_tuning sets a shape directly. */
+typedef struct {
+  int32_t variant, claim;
+  float ms;
+} fire_tune_t;
+fire_status_t fire_autotune(fire_ctx_t *ctx, const float *radiance, const uint16_t *wv_bin, int64_t n,
+                            fire_tune_t *best, fire_stream_t stream);
+fire_status_t fire_set_tuning(fire_ctx_t *ctx, int32_t variant, int32_t claim);
 
 /* Counters of the last fire_retrieve on this context (synchronises it). */
 fire_status_t fire_get_stats(fire_ctx_t *ctx, fire_stats_t *stats);

@@ -13,37 +13,8 @@
 
 using namespace firert;
 
-struct fire_ctx {
-  int device = 0;
-  int num_sms = 0;
-  fire_config_t cfg;
-  KTables t;
-  // device buffers
-  float *d_image = nullptr;
-  float4 *d_wvtab = nullptr;
-  float *d_sat = nullptr;
-  unsigned long long *d_work = nullptr;  // [0] counter, [1..] stats
-  int *d_err = nullptr;
-  // host staging for FIRE_MEM_HOST scenes
-  void *d_stage = nullptr;
-  size_t stage_bytes = 0;
-  // stage-1 -> stage-2 hand-over, grown on demand
-  float *d_s1x = nullptr;
-  int *d_s1meta = nullptr;
-  float *d_s2x = nullptr;
-  float *d_s2g = nullptr;
-  int64_t s1_cap = 0;
-  // learned start: network, per-pixel starts, fallback list and re-fit outputs
-  fire_mlp_t *mlp = nullptr;
-  float *d_mlp_init = nullptr;
-  long long *d_fb_idx = nullptr;
-  float *d_fb_cost = nullptr;
-  unsigned long long *d_fb_count = nullptr;
-  int64_t mlp_cap = 0;
-  void *d_cmp = nullptr;
-  int64_t cmp_cap = 0;
-  int last_launches = 0;
-};
+#include "ctx_internal.h"
+
 
 namespace {
 
@@ -188,6 +159,10 @@ KOut carve_outputs(void *buf, int64_t n, int K) {
   return o;
 }
 
+}  // namespace
+
+namespace firert {
+
 // The fit of p (device pointers set), with the learned start when asked:
 // network inference -> LM from those starts -> default-start re-fit of the
 // pixels the fallback rule flags -> keep the lower cost.
@@ -195,7 +170,7 @@ fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
   int blocks = 0;
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   if (!learned) {
-    CK(launch_lm(p, c->num_sms, st, &blocks));
+    CK(launch_lm(p, c->num_sms, st, &blocks, c->tune_variant));
     c->last_launches = 3;
     return FIRE_OK;
   }
@@ -220,10 +195,11 @@ fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
   if (e != FIRE_OK) return e;
   CK(cudaMemsetAsync(c->d_fb_count, 0, 8, st));
   p.s.init = c->d_mlp_init;
+  p.s.init_best = 1;
   p.w.fb_idx = c->d_fb_idx;
   p.w.fb_cost = c->d_fb_cost;
   p.w.fb_count = c->d_fb_count;
-  CK(launch_lm(p, c->num_sms, st, &blocks));
+  CK(launch_lm(p, c->num_sms, st, &blocks, c->tune_variant));
   unsigned long long nfb = 0;
   CK(cudaMemcpyAsync(&nfb, c->d_fb_count, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -242,19 +218,43 @@ fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
   q.s.n_pix = (int64_t)nfb;
   q.s.idx = c->d_fb_idx;
   q.s.init = nullptr;
+  q.s.init_best = 0;
   q.w.fb_idx = nullptr;
   q.w.fb_cost = nullptr;
   q.w.fb_count = nullptr;
   q.o = cmp;
   q.o.hfdi = nullptr;
   CK(cudaMemsetAsync(c->d_work, 0, 2 * 8, st));   // claim counters only; stats accumulate
-  CK(launch_lm(q, c->num_sms, st, &blocks));
+  CK(launch_lm(q, c->num_sms, st, &blocks, c->tune_variant));
   CK(launch_merge_fallback(c->d_fb_idx, c->d_fb_cost, (long long)nfb, cmp, p.o, K, st));
   c->last_launches += 4;
   return FIRE_OK;
 }
 
-}  // namespace
+// common launch set-up of a fit over n pixels (tables, constants, scratch)
+fire_status_t prepare_launch(fire_ctx *c, const fire_priors_t *pri, int64_t n, int gate, LMLaunch &p,
+                             bool ctx_scratch) {
+  memset(&p, 0, sizeof(p));
+  p.t = c->t;
+  fill_kconfig(p.c, c->cfg, *pri, c->t.K);
+  p.s.n_pix = n;
+  p.s.gate = gate;
+  p.s.claim = c->tune_claim;
+  p.w.counter = c->d_work;
+  p.w.stats = c->d_work + 2;
+  p.w.err = c->d_err;
+  if (!ctx_scratch) return FIRE_OK;
+  fire_status_t e = ensure_s1(c, n);
+  if (e != FIRE_OK) return e;
+  p.w.s1x = c->d_s1x;
+  p.w.s1meta = c->d_s1meta;
+  p.w.s2x = c->d_s2x;
+  p.w.s2g = c->d_s2g;
+  return FIRE_OK;
+}
+
+}  // namespace firert
+
 
 extern "C" {
 
@@ -358,6 +358,8 @@ void fire_ctx_destroy(fire_ctx_t *ctx) {
   cudaFree(ctx->d_fb_cost);
   cudaFree(ctx->d_fb_count);
   cudaFree(ctx->d_cmp);
+  cudaFree(ctx->d_items);
+  cudaFree(ctx->d_prefix);
   delete ctx;
 }
 
@@ -507,22 +509,10 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   const int K = c->t.K, NS = K + 8;
 
   LMLaunch p;
-  memset(&p, 0, sizeof(p));
-  p.t = c->t;
-  fill_kconfig(p.c, c->cfg, *pri, K);
-  p.s.n_pix = n;
-  p.s.gate = sc->gate_mode == FIRE_FIT_HFDI;
-  p.w.counter = c->d_work;
-  p.w.stats = c->d_work + 2;
-  p.w.err = c->d_err;
   {
-    fire_status_t e = ensure_s1(c, n);
+    fire_status_t e = prepare_launch(c, pri, n, sc->gate_mode == FIRE_FIT_HFDI, p);
     if (e != FIRE_OK) return e;
   }
-  p.w.s1x = c->d_s1x;
-  p.w.s1meta = c->d_s1meta;
-  p.w.s2x = c->d_s2x;
-  p.w.s2g = c->d_s2g;
 
   // per-pixel output sizes (bytes), in the order staged for host scenes
   const size_t szf = (size_t)n * 4;
@@ -624,14 +614,19 @@ fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   s->band_evals1 = v[ST_BAND1];
   s->band_evals2 = v[ST_BAND2];
   s->node_band_evals2 = v[ST_NODEBAND2];
+  s->trial_band_evals2 = v[ST_TRIAL2];
+  s->trial_node_band_evals2 = v[ST_TRIALNODE2];
   for (int k = 0; k < 8; k++) s->status_counts[k] = v[ST_STATUS0 + k];
-  // algorithmic flops (FMA = 2): stage 1 per band and evaluation, stage 2 per
-  // band and evaluation plus 6 FMA per band and active grid node
+  // algorithmic flops (FMA = 2): stage 1 per band and evaluation; stage 2 per
+  // band and full evaluation plus 6 FMA per band and active grid node, and
+  // per band and trial evaluation plus 2 FMA per band and active node
   const int K = c->t.K, P1 = K + 1;
   const double f1 = 4.0 * K + 27.0 + 2.0 * P1 * (P1 + 1) / 2.0 + 3.0 * P1 + 4.0;
   const double f2 = 30.0 + 2.0 * 21.0 + 3.0 * 6.0 + 4.0;
+  const double f2t = 8.0;
   s->flops = f1 * (double)s->band_evals1 + f2 * (double)s->band_evals2 +
-             12.0 * (double)s->node_band_evals2;
+             12.0 * (double)s->node_band_evals2 + f2t * (double)s->trial_band_evals2 +
+             4.0 * (double)s->trial_node_band_evals2;
   s->kernel_launches = c->last_launches;
   return err ? FIRE_ERR_TIMEOUT : FIRE_OK;
 }

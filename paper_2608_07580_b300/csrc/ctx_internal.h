@@ -1,0 +1,50 @@
+// ctx_internal.h — the context behind fire_ctx_t (host side).
+#pragma once
+#include "../../include/firert.h"
+#include "internal.cuh"
+
+struct fire_ctx {
+  int device = 0;
+  int num_sms = 0;
+  fire_config_t cfg;
+  firert::KTables t;
+  // device buffers
+  float *d_image = nullptr;
+  float4 *d_wvtab = nullptr;
+  float *d_sat = nullptr;
+  unsigned long long *d_work = nullptr;  // [0] counter, [1..] stats
+  int *d_err = nullptr;
+  // host staging for FIRE_MEM_HOST scenes
+  void *d_stage = nullptr;
+  size_t stage_bytes = 0;
+  // stage-1 -> stage-2 hand-over, grown on demand
+  float *d_s1x = nullptr;
+  int *d_s1meta = nullptr;
+  float *d_s2x = nullptr;
+  float *d_s2g = nullptr;
+  int64_t s1_cap = 0;
+  // learned start: network, per-pixel starts, fallback list and re-fit outputs
+  fire_mlp_t *mlp = nullptr;
+  float *d_mlp_init = nullptr;
+  long long *d_fb_idx = nullptr;
+  float *d_fb_cost = nullptr;
+  unsigned long long *d_fb_count = nullptr;
+  int64_t mlp_cap = 0;
+  void *d_cmp = nullptr;
+  int64_t cmp_cap = 0;
+  int last_launches = 0;
+  // autotuned launch shape: stage-1 occupancy variant and pixels per claim
+  int tune_variant = 0;
+  int tune_claim = 4;
+  // batched calls: scene descriptors on the device
+  firert::SceneItem *d_items = nullptr;
+  long long *d_prefix = nullptr;
+  int items_cap = 0;
+};
+
+namespace firert {
+fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st);
+// ctx_scratch false: the caller provides the stage hand-over buffers
+fire_status_t prepare_launch(fire_ctx *c, const fire_priors_t *pri, int64_t n, int gate, LMLaunch &p,
+                             bool ctx_scratch = true);
+}  // namespace firert

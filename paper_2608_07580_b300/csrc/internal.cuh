@@ -80,6 +80,8 @@ struct KScene {
   int n_items;
   int claim;               // pixels claimed per atomic (autotuned)
   int gate;                // 1: HFDI gate
+  int init_best;           // 1: stage 2 starts from the lower-cost of the given
+                           //    start and the stage-1-derived one (learned start)
 };
 
 struct KOut {
@@ -90,7 +92,8 @@ struct KOut {
 
 // device counters, indices into KWork::stats
 enum : int {
-  ST_NPIX = 0, ST_IT1, ST_IT2, ST_FP64, ST_BAND1, ST_BAND2, ST_NODEBAND2, ST_STATUS0,
+  ST_NPIX = 0, ST_IT1, ST_IT2, ST_FP64, ST_BAND1, ST_BAND2, ST_NODEBAND2, ST_TRIAL2, ST_TRIALNODE2,
+  ST_STATUS0,
   ST_COUNT = ST_STATUS0 + 8
 };
 
@@ -141,7 +144,8 @@ cudaError_t launch_build_tables(const KTables &t, const float *wl, const float *
                                 const float *td, const float *tu, const float *ra, const float *sa,
                                 const float *endm, float *image, float4 *wvtab,
                                 const float win[6], cudaStream_t st);
-cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used);
+cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used,
+                      int variant = 0);
 size_t lm_smem_bytes(const KTables &t);
 cudaError_t launch_merge_fallback(const long long *idx, const float *cost_first, long long nfb,
                                   const KOut &compact, const KOut &out, int K, cudaStream_t st);

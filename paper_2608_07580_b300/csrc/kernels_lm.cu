@@ -31,9 +31,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClaim = 4;          // pixels claimed per atomic
-#ifndef LM1_MINB
-#define LM1_MINB 2
-#endif
 #ifndef LM2_MINB
 #define LM2_MINB 1
 #endif
@@ -172,12 +169,14 @@ struct PixCtx {
   float *wsc;             // this warp's node scratch [nt][8]
   const float4 *wvrow;    // this pixel's water-vapour row of the atmosphere table
   int lane;
-  int node_evals;         // sum over stage-2 evaluations of active nodes
+  int node_evals;         // sum over stage-2 full evaluations of active nodes
+  int trial_nodes;        // sum over stage-2 trial (decrease-only) evaluations
 };
 
 // ------------------------------------------------------------ stage 1 ---
 template <int K, int S1>
 struct Stage1 {
+  static constexpr bool kTrialDrop = false;
   static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2, NS = S1;
   float Lobs[S1], w[S1];
   float psc;
@@ -383,6 +382,7 @@ struct Stage1 {
 template <int S2>
 struct Stage2 {
   static constexpr int P = 6, NX = 6, NH = 21, NS = S2;
+  static constexpr bool kTrialDrop = true;
   float y[S2], tu[S2], w[S2];
   float psc;
   float s[6];
@@ -532,6 +532,105 @@ struct Stage2 {
     }
   }
 
+  // Gaussian weight u_o = exp(-a_o^2/2), a = (T - mu)/sigma, of one node at
+  // the current state and its change du under the step (dmu, dsig): the
+  // exponent change is formed from the parameter differences,
+  //   a_t - a_o = -(dmu sigma_o + (T - mu_o) dsig) / (sigma_t sigma_o),
+  // and du = u_o expm1(-dq), so du is resolved relative to itself.
+  __device__ __forceinline__ static void node_step(float T, float mu, float sg, float mut, float sgt,
+                                                   float dmu, float dsg, float &u, float &du) {
+    const float ao = (T - mu) / sg, at = (T - mut) / sgt;
+    const float da = -(dmu * sg + (T - mu) * dsg) / (sgt * sg);
+    const float dq = 0.5f * da * (at + ao);
+    u = expf(-0.5f * ao * ao);
+    du = fabsf(dq) < 0.5f ? u * expm1f(-dq) : expf(-0.5f * at * at) - u;
+  }
+
+  // Data-term decrease of the trial step x -> xt, sum_b w_b dM_b (2 r_b -
+  // dM_b) with r the residuals at x and dM_b = tu_b (a_t dBm_b + (a_t - a)
+  // Bm_b) the model increment: Bm and dBm are the node sums of the current
+  // mixture weights and of their increments (the weight differences formed
+  // node by node from the exact parameter differences). The decrease is then
+  // accurate relative to itself, where the difference of two FP32 costs (or
+  // of two FP32 model values) would be lost below the model's rounding.
+  // 2 FMA per band and node.
+  __device__ __forceinline__ float trial_drop(PixCtx &pc, const float (&x)[NX], const float (&xt)[NX],
+                                              const float (&r)[NS]) const {
+    const KTables &t = *pc.t;
+    const float eo = x[4], ao = x[5], et = xt[4], at = xt[5];
+    float uho[4], uso[4], duh[4], dus[4];
+    float U[4] = {0.f, 0.f, 0.f, 0.f};
+    unsigned act[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int j = pc.lane + 32 * q;
+      uho[q] = uso[q] = duh[q] = dus[q] = 0.f;
+      if (j < t.nt) {
+        float T = t.tglo + (float)j * t.tgstep;
+        node_step(T, x[0], x[1], xt[0], xt[1], xt[0] - x[0], xt[1] - x[1], uho[q], duh[q]);
+        node_step(T, x[2], x[3], xt[2], xt[3], xt[2] - x[2], xt[3] - x[3], uso[q], dus[q]);
+      }
+      U[0] += uho[q];
+      U[1] += duh[q];
+      U[2] += uso[q];
+      U[3] += dus[q];
+      act[q] = __ballot_sync(kFull, uho[q] > 1e-30f || uso[q] > 1e-30f || uho[q] + duh[q] > 1e-30f ||
+                                        uso[q] + dus[q] > 1e-30f);
+    }
+    warp_sum(U);
+    const float rho_ = 1.f / U[0], rso = 1.f / U[2];
+    const float rht = 1.f / (U[0] + U[1]), rst = 1.f / (U[2] + U[3]);
+    const float kh = U[1] * rho_, ks = U[3] * rso;
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      int j = pc.lane + 32 * q;
+      if (j < t.nt) {
+        // w_t - w_o = (du - u_o dU/U_o) / U_t per component
+        float who = uho[q] * rho_, wso = uso[q] * rso;
+        float dwh = (duh[q] - uho[q] * kh) * rht, dws = (dus[q] - uso[q] * ks) * rst;
+        float Wo = eo * who + (1.f - eo) * wso;
+        float dW = et * dwh + (1.f - et) * dws + (et - eo) * (who - wso);
+        reinterpret_cast<float2 *>(pc.wsc)[4 * j] = make_float2(Wo, dW);
+      }
+    }
+    int jlo = t.nt, jhi = -1;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      if (act[q]) {
+        jlo = min(jlo, 32 * q + __ffs(act[q]) - 1);
+        jhi = max(jhi, 32 * q + 31 - __clz(act[q]));
+      }
+    __syncwarp();
+    float Bo[S2], dB[S2];
+#pragma unroll
+    for (int s2 = 0; s2 < S2; s2++) Bo[s2] = dB[s2] = 0.f;
+    const float *pl = pc.img + t.lay.off_planck + pc.lane;
+    const float2 *wv2 = reinterpret_cast<const float2 *>(pc.wsc);
+    for (int j = jlo; j <= jhi; j++) {
+      float2 A = wv2[4 * j];
+      const float *row = pl + j * t.lay.n2s;
+#pragma unroll
+      for (int s2 = 0; s2 < S2; s2++) {
+        float Bv = row[32 * s2];
+        Bo[s2] = fmaf(A.x, Bv, Bo[s2]);
+        dB[s2] = fmaf(A.y, Bv, dB[s2]);
+      }
+    }
+    pc.trial_nodes += (jhi >= jlo) ? (jhi - jlo + 1) : 0;
+    float d = 0.f;
+    const float da_ = at - ao;
+#pragma unroll
+    for (int s2 = 0; s2 < S2; s2++) {
+      if (w[s2] > 0.f) {
+        float dM = tu[s2] * fmaf(at, dB[s2], da_ * Bo[s2]);
+        d = fmaf(w[s2] * dM, 2.f * r[s2] - dM, d);
+      }
+    }
+    __syncwarp();
+    return warp_sum1(d);
+  }
+
   __device__ __forceinline__ float prior_drop(const KConfig &c, const float (&xo)[NX],
                                               const float (&xn)[NX]) const {
     float d = 0.f;
@@ -560,7 +659,7 @@ struct Stage2 {
 
 // -------------------------------------------------------- LM driver -----
 struct LMResult {
-  int iters, status;
+  int iters, full, status;   // trial steps; full model + Jacobian evaluations
   bool used64;
   float cost, cdata;
 };
@@ -594,7 +693,7 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
 #pragma unroll
   for (int i = 0; i < NX; i++) xt[i] = x[i];
   float lam = -1.f, nu = 2.f;
-  int it = 0, status = PX_MAXITER;
+  int it = 0, status = PX_MAXITER, nfull = 0;
   bool fresh = false, used64 = false, first = true;
   bool act[P];
 #pragma unroll
@@ -602,18 +701,33 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
 #pragma unroll 1
   for (;;) {
     // ---- evaluate the model, Jacobian and normal equations at xt
-    float Ht[NH], gt[P], ct, cdt, dct;
-    int mt;
-    S.eval(pc, xt, Ht, gt, ct, cdt, mt, r, rt, dct);
+    float Ht[NH], gt[P], ct = 0.f, cdt = 0.f, dct = 0.f;
+    int mt = 0;
     bool accept = first, done = false;
     float rel = 1.f, rho = 1.f;
-    if (!first) {
-      // actual decrease from residual differences (accurate where cost - ct
-      // would cancel in FP32) against the Gauss-Newton prediction
-      const float drop = dct + S.prior_drop(c, x, xt);
-      rho = pred > 0.f ? drop / pred : -1.f;
-      accept = rho > 0.f;
-      rel = drop / cst;
+    if constexpr (St::kTrialDrop) {
+      // decrease-only trial evaluation; the full one follows acceptance
+      if (!first) {
+        const float drop = S.trial_drop(pc, x, xt, r) + S.prior_drop(c, x, xt);
+        rho = pred > 0.f ? drop / pred : -1.f;
+        accept = rho > 0.f;
+        rel = drop / cst;
+      }
+      if (accept) {
+        S.eval(pc, xt, Ht, gt, ct, cdt, mt, r, rt, dct);
+        nfull++;
+      }
+    } else {
+      S.eval(pc, xt, Ht, gt, ct, cdt, mt, r, rt, dct);
+      nfull++;
+      if (!first) {
+        // actual decrease from residual differences (accurate where cost - ct
+        // would cancel in FP32) against the Gauss-Newton prediction
+        const float drop = dct + S.prior_drop(c, x, xt);
+        rho = pred > 0.f ? drop / pred : -1.f;
+        accept = rho > 0.f;
+        rel = drop / cst;
+      }
     }
     if (accept) {
 #pragma unroll
@@ -757,6 +871,7 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
     if (!have_trial) break;
   }
   res.iters = it;
+  res.full = nfull;
   res.status = status;
   res.used64 = used64;
   res.cost = cst;
@@ -1058,8 +1173,8 @@ constexpr int kFitted = 256;   // scratch flag: pixel goes on to stage 2
 constexpr int kS2Hand = 32;    // floats handed from stage 2 to finalize per pixel
 
 // ---- stage 1: checks, HFDI gate, stage-1 fit -> scratch
-template <int K, int S1, int WPB>
-__global__ void __launch_bounds__(WPB * 32, LM1_MINB) lm_stage1_kernel(const __grid_constant__ LMLaunch p) {
+template <int K, int S1, int WPB, int MINB>
+__global__ void __launch_bounds__(WPB * 32, MINB) lm_stage1_kernel(const __grid_constant__ LMLaunch p) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ unsigned long long cstat[ST_COUNT];
@@ -1130,7 +1245,7 @@ __global__ void __launch_bounds__(WPB * 32, LM1_MINB) lm_stage1_kernel(const __g
           it1 = r1.iters;
           if (r1.status == PX_MAXITER) status |= PX_F_S1_MAXITER;
           if (r1.used64) status |= PX_F_FP64;
-          mine[ST_BAND1] += (unsigned long long)(r1.iters + 1) * (unsigned long long)t.n1;
+          mine[ST_BAND1] += (unsigned long long)r1.full * (unsigned long long)t.n1;
           mine[ST_IT1] += it1;
           fitted = true;
         }
@@ -1191,7 +1306,6 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
   pc.img = smem;
   pc.wsc = smem + t.lay.total + warp * kMaxTgrid * kScratchPerNode;
   pc.lane = lane;
-  const int NSx = K + 8;
   unsigned long long mine[ST_COUNT];
 #pragma unroll
   for (int i = 0; i < ST_COUNT; i++) mine[i] = 0ull;
@@ -1209,6 +1323,7 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
       const float *row = ref.row;
       pc.wvrow = t.wvtab + (size_t)ref.wv * t.nb;
       pc.node_evals = 0;
+      pc.trial_nodes = 0;
       float x1[K + 2];
 #pragma unroll
       for (int i = 0; i < K + 2; i++) x1[i] = p.w.s1x[pix * (K + 2) + i];
@@ -1222,15 +1337,36 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
       if (ini) {
 #pragma unroll
         for (int i = 0; i < 6; i++) x2[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
-      } else {
+      }
+      if (!ini || p.s.init_best) {
+        float xd[6];
         float T1 = x1[K + 1];
-        x2[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
-        x2[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
-        x2[1] = fminf(fmaxf(c.init_sigma, c.lo2[1]), c.hi2[1]);
-        x2[3] = fminf(fmaxf(c.init_sigma, c.lo2[3]), c.hi2[3]);
-        x2[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
-        float e = x2[0] > x2[2] ? (T1 - x2[2]) / (x2[0] - x2[2]) : 0.5f;
-        x2[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
+        xd[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
+        xd[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
+        xd[1] = fminf(fmaxf(c.init_sigma, c.lo2[1]), c.hi2[1]);
+        xd[3] = fminf(fmaxf(c.init_sigma, c.lo2[3]), c.hi2[3]);
+        xd[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
+        float e = xd[0] > xd[2] ? (T1 - xd[2]) / (xd[0] - xd[2]) : 0.5f;
+        xd[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
+        bool take_d = !ini;
+        if (ini) {
+          // cost(xd) - cost(x2) from the data-term decreases of both starts
+          // against the thermal-free model (residuals y), plus the prior
+          float z2[6], zd[6];
+#pragma unroll
+          for (int i = 0; i < 6; i++) {
+            z2[i] = x2[i];
+            zd[i] = xd[i];
+          }
+          z2[5] = 0.f;
+          zd[5] = 0.f;
+          const float Dp = s2.trial_drop(pc, z2, x2, s2.y), Dd = s2.trial_drop(pc, zd, xd, s2.y);
+          take_d = !(Dp - Dd + s2.prior_drop(c, xd, x2) > 0.f);
+        }
+        if (take_d) {
+#pragma unroll
+          for (int i = 0; i < 6; i++) x2[i] = xd[i];
+        }
       }
       float H2[21], g2[6];
       int m2;
@@ -1239,8 +1375,10 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
       if (r2.used64) status |= PX_F_FP64;
       status |= r2.status;
       mine[ST_IT2] += r2.iters;
-      mine[ST_BAND2] += (unsigned long long)(r2.iters + 1) * (unsigned long long)t.n2;
+      mine[ST_BAND2] += (unsigned long long)r2.full * (unsigned long long)t.n2;
       mine[ST_NODEBAND2] += (unsigned long long)pc.node_evals * (unsigned long long)t.n2;
+      mine[ST_TRIAL2] += (unsigned long long)r2.iters * (unsigned long long)t.n2;
+      mine[ST_TRIALNODE2] += (unsigned long long)pc.trial_nodes * (unsigned long long)t.n2;
       // hand the final state and normal equations to the finalize kernel
       float* hand = p.w.s2x + pix * kS2Hand;
       {
@@ -1489,8 +1627,11 @@ cudaError_t launch_persistent(Kern kern, const LMLaunch &p, int num_sms, cudaStr
 }
 
 template <int K, int S1, int S2>
-cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used) {
-  cudaError_t e = launch_persistent(lm_stage1_kernel<K, S1, kWPB>, p, num_sms, st, blocks_used);
+cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant) {
+  // variant bit 0: stage 1 with two CTAs per SM (128 registers) instead of one
+  cudaError_t e = (variant & 1)
+                      ? launch_persistent(lm_stage1_kernel<K, S1, kWPB, 2>, p, num_sms, st, blocks_used)
+                      : launch_persistent(lm_stage1_kernel<K, S1, kWPB, 1>, p, num_sms, st, blocks_used);
   if (e != cudaSuccess) return e;
   e = launch_persistent(lm_stage2_kernel<K, S2, kWPB>, p, num_sms, st, blocks_used);
   if (e != cudaSuccess) return e;
@@ -1502,11 +1643,11 @@ cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *block
 }
 
 template <int K>
-cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used) {
+cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant) {
   int s1 = (p.t.n1 + 31) / 32, s2 = (p.t.n2 + 31) / 32;
-  if (s1 <= 9 && s2 <= 7) return launch_t<K, 9, 7>(p, num_sms, st, blocks_used);
-  if (s1 <= 9 && s2 <= 9) return launch_t<K, 9, 9>(p, num_sms, st, blocks_used);
-  if (s1 <= 16 && s2 <= 16) return launch_t<K, 16, 16>(p, num_sms, st, blocks_used);
+  if (s1 <= 9 && s2 <= 7) return launch_t<K, 9, 7>(p, num_sms, st, blocks_used, variant);
+  if (s1 <= 9 && s2 <= 9) return launch_t<K, 9, 9>(p, num_sms, st, blocks_used, variant);
+  if (s1 <= 16 && s2 <= 16) return launch_t<K, 16, 16>(p, num_sms, st, blocks_used, variant);
   return cudaErrorInvalidValue;
 }
 
@@ -1535,10 +1676,10 @@ size_t lm_smem_bytes(const KTables &t) {
   return (size_t)t.lay.total * 4 + (size_t)kWPB * kMaxTgrid * kScratchPerNode * 4;
 }
 
-cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used) {
+cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant) {
   switch (p.t.K) {
-    case 3: return launch_k<3>(p, num_sms, st, blocks_used);
-    case 5: return launch_k<5>(p, num_sms, st, blocks_used);
+    case 3: return launch_k<3>(p, num_sms, st, blocks_used, variant);
+    case 5: return launch_k<5>(p, num_sms, st, blocks_used, variant);
     default: return cudaErrorInvalidValue;
   }
 }

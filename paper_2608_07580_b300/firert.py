@@ -27,7 +27,9 @@ SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fir
            "fire_window_bands", "fire_status_str", "fire_normal_equations", "fire_gemm_bf16",
            "fire_mlp_create", "fire_mlp_destroy", "fire_mlp_train", "fire_mlp_infer",
            "fire_mlp_gradients", "fire_mlp_param_count", "fire_mlp_params", "fire_mlp_save",
-           "fire_mlp_load", "fire_mlp_next_sample", "fire_ctx_set_mlp")
+           "fire_mlp_load", "fire_mlp_next_sample", "fire_ctx_set_mlp", "fire_retrieve_batch",
+           "fire_graph_capture", "fire_graph_launch", "fire_graph_destroy", "fire_autotune",
+           "fire_set_tuning")
 
 
 class FireError(RuntimeError):
@@ -82,6 +84,15 @@ class Gemm_t(C.Structure):
                 ("err", C.c_void_p)]
 
 
+class BatchItem_t(C.Structure):
+    _fields_ = [("n_pix", C.c_int64), ("radiance", C.c_void_p), ("wv_bin", C.c_void_p),
+                ("out", Outputs_t)]
+
+
+class Tune_t(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("claim", C.c_int32), ("ms", C.c_float)]
+
+
 class MlpTrain_t(C.Structure):
     _fields_ = [("steps", C.c_int64), ("batch", C.c_int32), ("lr", C.c_float),
                 ("pfire", C.c_float), ("noise_rel", C.c_float), ("noise_abs", C.c_float),
@@ -92,6 +103,7 @@ class Stats_t(C.Structure):
     _fields_ = [("n_pixels", C.c_uint64), ("sum_it1", C.c_uint64), ("sum_it2", C.c_uint64),
                 ("n_fp64_pixels", C.c_uint64), ("band_evals1", C.c_uint64),
                 ("band_evals2", C.c_uint64), ("node_band_evals2", C.c_uint64),
+                ("trial_band_evals2", C.c_uint64), ("trial_node_band_evals2", C.c_uint64),
                 ("status_counts", C.c_uint64 * 8), ("flops", C.c_double),
                 ("kernel_launches", C.c_int32)]
 
@@ -143,6 +155,18 @@ def _load():
     lib.fire_mlp_next_sample.restype = i64
     lib.fire_ctx_set_mlp.argtypes = [vp, vp]
     lib.fire_ctx_set_mlp.restype = C.c_int
+    lib.fire_retrieve_batch.argtypes = [vp, C.POINTER(BatchItem_t), i32, C.POINTER(Priors_t), i32, vp]
+    lib.fire_retrieve_batch.restype = C.c_int
+    lib.fire_graph_capture.argtypes = [vp, C.POINTER(BatchItem_t), i32, C.POINTER(Priors_t), i32,
+                                       C.POINTER(vp)]
+    lib.fire_graph_capture.restype = C.c_int
+    lib.fire_graph_launch.argtypes = [vp, vp]
+    lib.fire_graph_launch.restype = C.c_int
+    lib.fire_graph_destroy.argtypes = [vp]
+    lib.fire_autotune.argtypes = [vp, vp, vp, i64, C.POINTER(Tune_t), vp]
+    lib.fire_autotune.restype = C.c_int
+    lib.fire_set_tuning.argtypes = [vp, i32, i32]
+    lib.fire_set_tuning.restype = C.c_int
     lib.fire_status_str.argtypes = [C.c_int]
     lib.fire_status_str.restype = C.c_char_p
     return lib
@@ -312,6 +336,47 @@ class Context:
                                 _dptr(out, torch.float32), _stream_ptr(stream)), "fire_forward")
         return out
 
+    def _items(self, scenes, outputs):
+        import torch
+        arr = (BatchItem_t * len(scenes))()
+        for i, ((rad, wv), out) in enumerate(zip(scenes, outputs)):
+            ptr = lambda k: _dptr(out.get(k))  # noqa: E731
+            arr[i] = BatchItem_t(int(rad.shape[0]), _dptr(rad, torch.float32), _dptr(wv),
+                                 Outputs_t(*[ptr(k) for k in ("state", "ET", "sdT", "alpha", "cov",
+                                                              "var_ET", "cost", "rms", "hfdi",
+                                                              "status", "iters")]))
+        return arr
+
+    def retrieve_batch(self, scenes, outputs=None, priors=None, gate_hfdi=False, stream=None):
+        """Fit several scenes [(radiance, wv_bin), ...] (device tensors) in one launch."""
+        if outputs is None:
+            outputs = [self.alloc_outputs(int(r.shape[0])) for r, _ in scenes]
+        arr = self._items(scenes, outputs)
+        pr = None if priors is None else C.byref(priors)
+        _check(lib.fire_retrieve_batch(self._h, arr, len(scenes), pr, int(bool(gate_hfdi)),
+                                       _stream_ptr(stream)), "fire_retrieve_batch")
+        return outputs
+
+    def capture_batch(self, scenes, outputs, priors=None, gate_hfdi=False):
+        """CUDA graph of retrieve_batch over these buffers (replay with .launch())."""
+        arr = self._items(scenes, outputs)
+        h = C.c_void_p()
+        pr = None if priors is None else C.byref(priors)
+        _check(lib.fire_graph_capture(self._h, arr, len(scenes), pr, int(bool(gate_hfdi)),
+                                      C.byref(h)), "fire_graph_capture")
+        return BatchGraph(h, self, scenes, outputs)
+
+    def autotune(self, radiance, wv_bin, stream=None):
+        import torch
+        t = Tune_t()
+        _check(lib.fire_autotune(self._h, _dptr(radiance, torch.float32), _dptr(wv_bin),
+                                 int(radiance.shape[0]), C.byref(t), _stream_ptr(stream)),
+               "fire_autotune")
+        return {"variant": t.variant, "claim": t.claim, "ms": t.ms}
+
+    def set_tuning(self, variant, claim):
+        _check(lib.fire_set_tuning(self._h, variant, claim), "fire_set_tuning")
+
     def normal_equations(self, stage, radiance, wv_bin, states, priors=None, stream=None):
         """(H, g, cost) of one stage at the given states (device tensors)."""
         import torch
@@ -357,6 +422,24 @@ def gemm_bf16(A, B, epi=0, bias=None, mask=None, Cf=None, Cb=None, CbT=None, acc
                0 if Cb is None else Cb.stride(0), _dptr(CbT), 0 if CbT is None else CbT.stride(0),
                int(bool(accumulate)), _dptr(err))
     _check(lib.fire_gemm_bf16(C.byref(g), _stream_ptr(stream)), "fire_gemm_bf16")
+
+
+class BatchGraph:
+    """A captured batched fit; keeps its buffers alive."""
+
+    def __init__(self, h, ctx, scenes, outputs):
+        self._h, self.ctx, self._keep = h, ctx, (scenes, outputs)
+
+    def launch(self, stream=None):
+        _check(lib.fire_graph_launch(self._h, _stream_ptr(stream)), "fire_graph_launch")
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                lib.fire_graph_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
 
 
 class MLP:

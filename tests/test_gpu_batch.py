@@ -1,0 +1,144 @@
+"""Batched uneven scenes in one persistent launch, CUDA-graph replay of that
+launch, and the launch-shape autotuner. Each pixel's fit is the same
+arithmetic whichever scene table, claim size or graph it runs under, so the
+batched outputs equal, bit for bit, those of fitting the scenes one by one."""
+import numpy as np
+import pytest
+
+import oracle
+from scenes import config1, parity_stats
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("state", "ET", "sdT", "alpha", "cov", "var_ET", "cost", "rms", "hfdi", "status", "iters")
+
+
+@pytest.fixture(scope="module")
+def fr():
+    from paper_2608_07580_b300 import firert
+    return firert
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return config1()
+
+
+def _dev(torch, a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def _np(d):
+    return {k: v.cpu().numpy() for k, v in d.items() if hasattr(v, "cpu")}
+
+
+def _same(a, b):
+    for k in KEYS:
+        if a[k].dtype.kind == "f":
+            assert np.array_equal(a[k], b[k], equal_nan=True), k
+        else:
+            assert np.array_equal(a[k], b[k]), k
+
+
+def _split(n, sizes):
+    edges = np.cumsum([0] + list(sizes))
+    assert edges[-1] <= n
+    return [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:])]
+
+
+def test_batch_equals_scene_by_scene(fr, torch, c1):
+    t, tr, L = c1
+    ctx = fr.Context(t)
+    Ld = _dev(torch, L, torch.float32)
+    wd = _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)
+    whole = _np(ctx.retrieve(Ld, wd))
+    parts = _split(tr.n_pix, [0, 1, 37, 500, 2048, 3, tr.n_pix - 2589])
+    scenes = [(Ld[a:b], wd[a:b]) for a, b in parts]
+    outs = ctx.retrieve_batch(scenes)
+    torch.cuda.synchronize()
+    assert ctx.stats()["n_pixels"] == tr.n_pix
+    for (a, b), o in zip(parts, outs):
+        o = _np(o)
+        _same({k: whole[k][a:b] for k in KEYS}, o)
+
+
+def test_batch_hfdi_gate_and_rejects_learned_start(fr, torch, c1):
+    t, tr, L = c1
+    ctx = fr.Context(t)
+    Ld = _dev(torch, L, torch.float32)
+    wd = _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)
+    whole = _np(ctx.retrieve(Ld, wd, gate_hfdi=True))
+    parts = _split(tr.n_pix, [1000, 96, tr.n_pix - 1096])
+    outs = ctx.retrieve_batch([(Ld[a:b], wd[a:b]) for a, b in parts], gate_hfdi=True)
+    torch.cuda.synchronize()
+    for (a, b), o in zip(parts, outs):
+        _same({k: whole[k][a:b] for k in KEYS}, _np(o))
+    pri = ctx.default_priors()
+    pri.init_mode = fr.FIRE_INIT_MLP
+    with pytest.raises(fr.FireError):
+        ctx.retrieve_batch([(Ld[:10], wd[:10])], priors=pri)
+
+
+def test_graph_replay_follows_new_inputs(fr, torch, c1):
+    t, tr, L = c1
+    ctx = fr.Context(t)
+    n = tr.n_pix
+    parts = _split(n, [700, 1, n - 701])
+    Lbuf = _dev(torch, L, torch.float32)
+    wbuf = _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)
+    scenes = [(Lbuf[a:b], wbuf[a:b]) for a, b in parts]
+    outs = [ctx.alloc_outputs(b - a) for a, b in parts]
+    g = ctx.capture_batch(scenes, outs)
+    # new inputs in the same buffers: the scene reversed pixel-wise
+    perm = np.arange(n)[::-1].copy()
+    Lbuf.copy_(_dev(torch, L[perm], torch.float32))
+    wbuf.copy_(_dev(torch, tr.wv_bin[perm].astype(np.int16), torch.int16))
+    for _ in range(2):                                   # replays are repeatable
+        g.launch()
+        torch.cuda.synchronize()
+        got = [_np(o) for o in outs]
+        ref = _np(fr.Context(t).retrieve(_dev(torch, L[perm], torch.float32),
+                                         _dev(torch, tr.wv_bin[perm].astype(np.int16), torch.int16)))
+        for (a, b), o in zip(parts, got):
+            _same({k: ref[k][a:b] for k in KEYS}, o)
+
+
+def test_claim_size_does_not_change_results(fr, torch, c1):
+    t, tr, L = c1
+    ctx = fr.Context(t)
+    Ld = _dev(torch, L[:1500], torch.float32)
+    wd = _dev(torch, tr.wv_bin[:1500].astype(np.int16), torch.int16)
+    base = None
+    for claim in (1, 2, 8, 32):
+        ctx.set_tuning(0, claim)
+        o = _np(ctx.retrieve(Ld, wd))
+        if base is None:
+            base = o
+        else:
+            _same(base, o)
+    with pytest.raises(fr.FireError):
+        ctx.set_tuning(2, 4)
+
+
+def test_autotune_picks_a_valid_shape_and_keeps_parity(fr, torch, c1):
+    t, tr, L = c1
+    ctx = fr.Context(t)
+    Ld = _dev(torch, L, torch.float32)
+    wd = _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)
+    best = ctx.autotune(Ld, wd)
+    print("autotune:", best)
+    assert best["variant"] in (0, 1) and best["claim"] in (1, 2, 4, 8) and best["ms"] > 0
+    idx = np.arange(1024)
+    o = oracle.retrieve(t, L[idx], tr.wv_bin[idx])
+    for variant in (0, 1):
+        ctx.set_tuning(variant, 4)
+        g = _np(ctx.retrieve(Ld[:1024], wd[:1024]))
+        s = parity_stats(o, g)
+        assert s["pool"] >= 0.8 * s["oracle_conv_ident"]
+        assert s["rate"] >= 0.99, (variant, s)
