@@ -156,6 +156,7 @@ typedef struct {
   uint64_t trial_band_evals2, trial_node_band_evals2;   /* stage-2 decrease-only trials */
   uint64_t status_counts[8];
   double flops;                     /* algorithmic flops of the fit */
+  double flops1, flops2;            /* ... of which stage 1 and stage 2 */
   int32_t kernel_launches;
 } fire_stats_t;
 
@@ -336,10 +337,12 @@ fire_status_t fire_graph_capture(fire_ctx_t *ctx, const fire_batch_item_t *items
                                  const fire_priors_t *pri, int32_t gate_mode, fire_graph_t **out);
 fire_status_t fire_graph_launch(fire_graph_t *g, fire_stream_t stream);
 void fire_graph_destroy(fire_graph_t *g);
-/* Autotuner: times each launch shape (stage-1 occupancy variant 0 = one CTA
- * of 8 warps per SM with up to 255 registers, 1 = two CTAs with 128; pixels
- * per work claim 1, 2, 4, 8) on the n given device pixels and keeps the
- * fastest for the context. fire_set_tuning sets a shape directly. */
+/* Autotuner: times each launch shape on the n given device pixels and keeps
+ * the fastest for the context. variant bit 0: stage 1 as one CTA of 8 warps
+ * per SM (up to 255 registers) or two (128); bits 1-2: stage 2 as one CTA
+ * of 8, 12 or 16 warps per SM (255, 168 or 128 registers); claim: pixels
+ * per work claim (1, 2, 4, 8). fire_set_tuning sets a shape directly
+ * (variant 0..5, claim 1..64). */
 typedef struct {
   int32_t variant, claim;
   float ms;
@@ -347,6 +350,14 @@ typedef struct {
 fire_status_t fire_autotune(fire_ctx_t *ctx, const float *radiance, const uint16_t *wv_bin, int64_t n,
                             fire_tune_t *best, fire_stream_t stream);
 fire_status_t fire_set_tuning(fire_ctx_t *ctx, int32_t variant, int32_t claim);
+
+/* Per-kernel timing. With timing on, every fit launch records CUDA events
+ * on its stream around the stage-1, stage-2 and finalize kernels (no
+ * synchronisation). fire_get_kernel_times waits for the last one and
+ * returns the summed milliseconds of each kernel [3] over the fits since
+ * the last call (or since timing was switched on), and their number. */
+fire_status_t fire_set_kernel_timing(fire_ctx_t *ctx, int32_t on);
+fire_status_t fire_get_kernel_times(fire_ctx_t *ctx, float *ms, int32_t *n_fits);
 
 /* Counters of the last fire_retrieve on this context (synchronises it). */
 fire_status_t fire_get_stats(fire_ctx_t *ctx, fire_stats_t *stats);

@@ -166,11 +166,23 @@ namespace firert {
 // The fit of p (device pointers set), with the learned start when asked:
 // network inference -> LM from those starts -> default-start re-fit of the
 // pixels the fallback rule flags -> keep the lower cost.
+cudaEvent_t *timing_events(fire_ctx *c) {
+  if (!c->timing) return nullptr;
+  while (c->tev.size() < c->tev_used + 4) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->tev.push_back(e);
+  }
+  cudaEvent_t *ev = c->tev.data() + c->tev_used;
+  c->tev_used += 4;
+  return ev;
+}
+
 fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
   int blocks = 0;
   CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   if (!learned) {
-    CK(launch_lm(p, c->num_sms, st, &blocks, c->tune_variant));
+    CK(launch_lm(p, c->num_sms, st, &blocks, c->tune_variant, timing_events(c)));
     c->last_launches = 3;
     return FIRE_OK;
   }
@@ -199,7 +211,7 @@ fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
   p.w.fb_idx = c->d_fb_idx;
   p.w.fb_cost = c->d_fb_cost;
   p.w.fb_count = c->d_fb_count;
-  CK(launch_lm(p, c->num_sms, st, &blocks, c->tune_variant));
+  CK(launch_lm(p, c->num_sms, st, &blocks, c->tune_variant, timing_events(c)));
   unsigned long long nfb = 0;
   CK(cudaMemcpyAsync(&nfb, c->d_fb_count, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -360,6 +372,7 @@ void fire_ctx_destroy(fire_ctx_t *ctx) {
   cudaFree(ctx->d_cmp);
   cudaFree(ctx->d_items);
   cudaFree(ctx->d_prefix);
+  for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -598,6 +611,31 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   return err ? FIRE_ERR_TIMEOUT : FIRE_OK;
 }
 
+fire_status_t fire_set_kernel_timing(fire_ctx_t *c, int32_t on) {
+  if (!c) return FIRE_ERR_ARG;
+  c->timing = on != 0;
+  c->tev_used = 0;
+  return FIRE_OK;
+}
+
+fire_status_t fire_get_kernel_times(fire_ctx_t *c, float *ms, int32_t *n_fits) {
+  if (!c || !ms) return FIRE_ERR_ARG;
+  ms[0] = ms[1] = ms[2] = 0.f;
+  const size_t n = c->tev_used / 4;
+  if (n_fits) *n_fits = (int32_t)n;
+  if (n == 0) return FIRE_OK;
+  CK(cudaEventSynchronize(c->tev[c->tev_used - 1]));
+  for (size_t i = 0; i < n; i++) {
+    for (int k = 0; k < 3; k++) {
+      float v = 0.f;
+      CK(cudaEventElapsedTime(&v, c->tev[4 * i + k], c->tev[4 * i + k + 1]));
+      ms[k] += v;
+    }
+  }
+  c->tev_used = 0;
+  return FIRE_OK;
+}
+
 fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   if (!c || !s) return FIRE_ERR_ARG;
   unsigned long long h[2 + ST_COUNT];
@@ -624,9 +662,10 @@ fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   const double f1 = 4.0 * K + 27.0 + 2.0 * P1 * (P1 + 1) / 2.0 + 3.0 * P1 + 4.0;
   const double f2 = 30.0 + 2.0 * 21.0 + 3.0 * 6.0 + 4.0;
   const double f2t = 8.0;
-  s->flops = f1 * (double)s->band_evals1 + f2 * (double)s->band_evals2 +
-             12.0 * (double)s->node_band_evals2 + f2t * (double)s->trial_band_evals2 +
-             4.0 * (double)s->trial_node_band_evals2;
+  s->flops1 = f1 * (double)s->band_evals1;
+  s->flops2 = f2 * (double)s->band_evals2 + 12.0 * (double)s->node_band_evals2 +
+              f2t * (double)s->trial_band_evals2 + 4.0 * (double)s->trial_node_band_evals2;
+  s->flops = s->flops1 + s->flops2;
   s->kernel_launches = c->last_launches;
   return err ? FIRE_ERR_TIMEOUT : FIRE_OK;
 }

@@ -1,5 +1,7 @@
 // ctx_internal.h — the context behind fire_ctx_t (host side).
 #pragma once
+#include <vector>
+
 #include "../../include/firert.h"
 #include "internal.cuh"
 
@@ -40,9 +42,15 @@ struct fire_ctx {
   firert::SceneItem *d_items = nullptr;
   long long *d_prefix = nullptr;
   int items_cap = 0;
+  // per-kernel timing: 4 events per fit launch, summed on request
+  bool timing = false;
+  std::vector<cudaEvent_t> tev;
+  size_t tev_used = 0;
 };
 
 namespace firert {
+// the next 4 timing events of the context (nullptr when timing is off)
+cudaEvent_t *timing_events(fire_ctx *c);
 fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st);
 // ctx_scratch false: the caller provides the stage hand-over buffers
 fire_status_t prepare_launch(fire_ctx *c, const fire_priors_t *pri, int64_t n, int gate, LMLaunch &p,

@@ -144,9 +144,11 @@ cudaError_t launch_build_tables(const KTables &t, const float *wl, const float *
                                 const float *td, const float *tu, const float *ra, const float *sa,
                                 const float *endm, float *image, float4 *wvtab,
                                 const float win[6], cudaStream_t st);
+// ev: optional 4 events recorded before stage 1, after stage 1, after
+// stage 2 and after the finalize kernel (per-kernel timing)
 cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used,
-                      int variant = 0);
-size_t lm_smem_bytes(const KTables &t);
+                      int variant = 0, cudaEvent_t *ev = nullptr);
+size_t lm_smem_bytes(const KTables &t, int warps_per_cta = 8);
 cudaError_t launch_merge_fallback(const long long *idx, const float *cost_first, long long nfb,
                                   const KOut &compact, const KOut &out, int K, cudaStream_t st);
 cudaError_t launch_normal_eq(const LMLaunch &p, int stage, const float *states, float *H, float *g,

@@ -31,9 +31,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClaim = 4;          // pixels claimed per atomic
-#ifndef LM2_MINB
-#define LM2_MINB 1
-#endif
+constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in dynamic shared memory per CTA
 
 template <int N>
 __device__ __forceinline__ void warp_sum(float (&v)[N]) {
@@ -161,6 +159,16 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
   return true;
 }
 
+// per-warp shared scratch: node weights [nt][8], then (stage 2) the band
+// buffers [4][S2 * 32] of the band-slot count the kernel is instantiated for
+__host__ __device__ __forceinline__ int s2_slots(int n2) {
+  const int s2 = (n2 + 31) / 32;
+  return s2 <= 7 ? 7 : (s2 <= 9 ? 9 : 16);
+}
+__host__ __device__ __forceinline__ int warp_scratch_floats(const KTables &t) {
+  return t.nt * kScratchPerNode + 4 * 32 * s2_slots(t.n2);
+}
+
 // ------------------------------------------------------- pixel context --
 struct PixCtx {
   const KTables *t;
@@ -176,7 +184,6 @@ struct PixCtx {
 // ------------------------------------------------------------ stage 1 ---
 template <int K, int S1>
 struct Stage1 {
-  static constexpr bool kTrialDrop = false;
   static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2, NS = S1;
   float Lobs[S1], w[S1];
   float psc;
@@ -382,10 +389,17 @@ struct Stage1 {
 template <int S2>
 struct Stage2 {
   static constexpr int P = 6, NX = 6, NH = 21, NS = S2;
-  static constexpr bool kTrialDrop = true;
-  float y[S2], tu[S2], w[S2];
+  static constexpr int NB = S2 * 32;   // band slots per buffer
+  // this warp's band buffers in shared memory, [4][NB]: y (radiance minus
+  // the fixed solar term), tu (tau_up), w (loss weight), r (residual at the
+  // current state); lane l owns slots l + 32 s
+  float *bb;
   float psc;
-  float s[6];
+
+  __device__ __forceinline__ float &yb(int i) const { return bb[i]; }
+  __device__ __forceinline__ float &tub(int i) const { return bb[NB + i]; }
+  __device__ __forceinline__ float &wb(int i) const { return bb[2 * NB + i]; }
+  __device__ __forceinline__ float &rb(int i) const { return bb[3 * NB + i]; }
 
   template <int A>
   __device__ __forceinline__ static float rsel(const float (&v)[NX], int) { return v[A]; }
@@ -394,20 +408,21 @@ struct Stage2 {
   template <int A>
   __device__ __forceinline__ float hi_r(const KConfig &c, int) const { return c.hi2[A]; }
   template <int A>
-  __device__ __forceinline__ float sc_r(const KConfig &c, int) const { return s[A]; }
+  __device__ __forceinline__ float sc_r(const KConfig &c, int) const {
+    return 0.5f * (c.hi2[A] - c.lo2[A]);
+  }
   template <int A>
   __device__ __forceinline__ static constexpr bool has_upper() { return true; }
   __device__ __forceinline__ float scale(const KConfig &c, int i) const {
     return 0.5f * (c.hi2[i] - c.lo2[i]);
   }
 
+  // model, Jacobian (z-scaled), normal equations and cost at x; writes the
+  // residuals into the r buffer. All lanes get the warp totals.
   __device__ __forceinline__ void eval(PixCtx &pc, const float (&x)[NX], float (&H)[NH],
-                                       float (&g)[P], float &cst, float &cd, int &m,
-                                       const float (&rold)[NS], float (&rnew)[NS],
-                                       float &dcd) const {
+                                       float (&g)[P], float &cst, float &cd) const {
     const KTables &t = *pc.t;
     const KConfig &c = *pc.c;
-    m = 0;
     const float mh = x[0], sh = x[1], ms = x[2], ss = x[3], eta = x[4], al = x[5];
     // grid weights of the two components: lanes own nodes j = lane + 32 q
     float uh[4], us[4], dh[4], ds[4];
@@ -422,8 +437,6 @@ struct Stage2 {
         float T = t.tglo + (float)j * t.tgstep;
         dh[q] = T - mh;
         ds[q] = T - ms;
-        // accurate expf: the weights' rounding sets how finely the cost
-        // differences of the last steps are resolved
         uh[q] = expf(-dh[q] * dh[q] * ih);
         us[q] = expf(-ds[q] * ds[q] * is);
       }
@@ -481,37 +494,43 @@ struct Stage2 {
       }
     }
     pc.node_evals += (jhi >= jlo) ? (jhi - jlo + 1) : 0;
-    float acc[NH + P + 3];
+    float acc[NH + P + 2];
 #pragma unroll
-    for (int i = 0; i < NH + P + 3; i++) acc[i] = 0.f;
+    for (int i = 0; i < NH + P + 2; i++) acc[i] = 0.f;
     const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
     const float ish3 = ish2 / sh, iss3 = iss2 / ss;
+    const float sc0 = scale(c, 0), sc1 = scale(c, 1), sc2 = scale(c, 2), sc3 = scale(c, 3);
+    const float sc4 = scale(c, 4), sc5 = scale(c, 5);
 #pragma unroll
     for (int s2 = 0; s2 < S2; s2++) {
-      if (w[s2] > 0.f) {
+      const int i = pc.lane + 32 * s2;
+      const float wv = wb(i);
+      if (wv > 0.f) {
         float Bh = S[s2][0], Bs = S[s2][3];
         float Bm = eta * Bh + (1.f - eta) * Bs;
-        float atu = al * tu[s2];
-        float r = y[s2] - atu * Bm;
-        rnew[s2] = r;
-        acc[NH + P + 2] = fmaf(w[s2] * (rold[s2] - r), rold[s2] + r, acc[NH + P + 2]);
+        float tuv = tub(i);
+        float atu = al * tuv;
+        float r = yb(i) - atu * Bm;
+        rb(i) = r;
         float J[6];
-        J[0] = atu * eta * S[s2][1] * ish2 * s[0];
-        J[1] = atu * eta * S[s2][2] * ish3 * s[1];
-        J[2] = atu * (1.f - eta) * S[s2][4] * iss2 * s[2];
-        J[3] = atu * (1.f - eta) * S[s2][5] * iss3 * s[3];
-        J[4] = atu * (Bh - Bs) * s[4];
-        J[5] = tu[s2] * Bm * s[5];
-        float wr = w[s2] * r;
+        J[0] = atu * eta * S[s2][1] * ish2 * sc0;
+        J[1] = atu * eta * S[s2][2] * ish3 * sc1;
+        J[2] = atu * (1.f - eta) * S[s2][4] * iss2 * sc2;
+        J[3] = atu * (1.f - eta) * S[s2][5] * iss3 * sc3;
+        J[4] = atu * (Bh - Bs) * sc4;
+        J[5] = tuv * Bm * sc5;
+        float wr = wv * r;
         acc[NH + P] = fmaf(wr, r, acc[NH + P]);
         acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
 #pragma unroll
         for (int a = 0; a < P; a++) {
           acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
-          float wj = w[s2] * J[a];
+          float wj = wv * J[a];
 #pragma unroll
-          for (int bb = a; bb < P; bb++) acc[up<P>(a, bb)] = fmaf(wj, J[bb], acc[up<P>(a, bb)]);
+          for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
         }
+      } else {
+        rb(i) = 0.f;
       }
     }
     warp_sum(acc);
@@ -521,7 +540,6 @@ struct Stage2 {
     for (int a = 0; a < P; a++) g[a] = acc[NH + a];
     cst = acc[NH + P];
     cd = acc[NH + P + 1];
-    dcd = acc[NH + P + 2];
 #pragma unroll
     for (int i = 0; i < 6; i++) {
       float z = c.hi2[i] > c.lo2[i] ? 2.f * (x[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
@@ -530,6 +548,7 @@ struct Stage2 {
       g[i] -= pp * (z - c.pm2[i]);
       H[up<P>(i, i)] += pp;
     }
+    __syncwarp();
   }
 
   // Gaussian weight u_o = exp(-a_o^2/2), a = (T - mu)/sigma, of one node at
@@ -537,10 +556,10 @@ struct Stage2 {
   // exponent change is formed from the parameter differences,
   //   a_t - a_o = -(dmu sigma_o + (T - mu_o) dsig) / (sigma_t sigma_o),
   // and du = u_o expm1(-dq), so du is resolved relative to itself.
-  __device__ __forceinline__ static void node_step(float T, float mu, float sg, float mut, float sgt,
+  __device__ __forceinline__ static void node_step(float T, float mu, float isg, float mut, float isgt,
                                                    float dmu, float dsg, float &u, float &du) {
-    const float ao = (T - mu) / sg, at = (T - mut) / sgt;
-    const float da = -(dmu * sg + (T - mu) * dsg) / (sgt * sg);
+    const float ao = (T - mu) * isg, at = (T - mut) * isgt;
+    const float da = -fmaf((T - mu) * dsg, isg, dmu) * isgt;
     const float dq = 0.5f * da * (at + ao);
     u = expf(-0.5f * ao * ao);
     du = fabsf(dq) < 0.5f ? u * expm1f(-dq) : expf(-0.5f * at * at) - u;
@@ -554,21 +573,22 @@ struct Stage2 {
   // accurate relative to itself, where the difference of two FP32 costs (or
   // of two FP32 model values) would be lost below the model's rounding.
   // 2 FMA per band and node.
-  __device__ __forceinline__ float trial_drop(PixCtx &pc, const float (&x)[NX], const float (&xt)[NX],
-                                              const float (&r)[NS]) const {
+  __device__ __forceinline__ float trial_drop(PixCtx &pc, const float (&x)[NX],
+                                              const float (&xt)[NX], bool r_is_y = false) const {
     const KTables &t = *pc.t;
     const float eo = x[4], ao = x[5], et = xt[4], at = xt[5];
     float uho[4], uso[4], duh[4], dus[4];
     float U[4] = {0.f, 0.f, 0.f, 0.f};
     unsigned act[4];
+    const float ih = 1.f / x[1], iht = 1.f / xt[1], is = 1.f / x[3], ist = 1.f / xt[3];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       int j = pc.lane + 32 * q;
       uho[q] = uso[q] = duh[q] = dus[q] = 0.f;
       if (j < t.nt) {
         float T = t.tglo + (float)j * t.tgstep;
-        node_step(T, x[0], x[1], xt[0], xt[1], xt[0] - x[0], xt[1] - x[1], uho[q], duh[q]);
-        node_step(T, x[2], x[3], xt[2], xt[3], xt[2] - x[2], xt[3] - x[3], uso[q], dus[q]);
+        node_step(T, x[0], ih, xt[0], iht, xt[0] - x[0], xt[1] - x[1], uho[q], duh[q]);
+        node_step(T, x[2], is, xt[2], ist, xt[2] - x[2], xt[3] - x[3], uso[q], dus[q]);
       }
       U[0] += uho[q];
       U[1] += duh[q];
@@ -622,9 +642,12 @@ struct Stage2 {
     const float da_ = at - ao;
 #pragma unroll
     for (int s2 = 0; s2 < S2; s2++) {
-      if (w[s2] > 0.f) {
-        float dM = tu[s2] * fmaf(at, dB[s2], da_ * Bo[s2]);
-        d = fmaf(w[s2] * dM, 2.f * r[s2] - dM, d);
+      const int i = pc.lane + 32 * s2;
+      const float wv = wb(i);
+      if (wv > 0.f) {
+        float dM = tub(i) * fmaf(at, dB[s2], da_ * Bo[s2]);
+        float r = r_is_y ? yb(i) : rb(i);
+        d = fmaf(wv * dM, 2.f * r - dM, d);
       }
     }
     __syncwarp();
@@ -649,7 +672,7 @@ struct Stage2 {
                                         const signed char (&pd)[P], int, float (&xt)[NX]) const {
 #pragma unroll
     for (int i = 0; i < 6; i++) {
-      float v = x[i] + s[i] * dr[i];
+      float v = x[i] + scale(c, i) * dr[i];
       if (pd[i] < 0) v = c.lo2[i];
       if (pd[i] > 0) v = c.hi2[i];
       xt[i] = fminf(fmaxf(v, c.lo2[i]), c.hi2[i]);
@@ -680,54 +703,188 @@ __device__ __noinline__ bool solve_fp64(Solve64<P> &q) {
 
 // One stage of the fit. The model is evaluated at a single call site per
 // stage (start point, then every trial point) to keep the code compact.
+// State of the damped iteration shared by the two stage drivers.
+template <int P>
+struct LMIter {
+  float lam = -1.f, nu = 2.f, pred = 0.f;
+  int it = 0, status = PX_MAXITER;
+  bool fresh = true, used64 = false;
+  bool act[P];
+};
+
+// From the normal equations (H, g) at the current state x: the convergence
+// test (when they are fresh), then the damped projected-Newton step and the
+// trial point xt with its predicted decrease. Returns false when the fit
+// stops (converged, step below tol_x, damping overflow, iteration cap).
+template <class St>
+__device__ __forceinline__ bool next_trial(const St &S, const KConfig &c, const float (&x)[St::NX],
+                                           const float (&H)[St::NH], const float (&g)[St::P], int m,
+                                           float cst, int max_it, LMIter<St::P> &L,
+                                           float (&xt)[St::NX]) {
+  constexpr int P = St::P, NX = St::NX;
+#pragma unroll 1
+  while (L.it < max_it) {
+    if (L.fresh) {
+      bool small = true;
+      float mx = 0.f;
+      static_for<P>([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        float xv = St::template rsel<a>(x, m);
+        bool lo_hit = xv <= S.template lo_r<a>(c, m);
+        bool hi_hit = St::template has_upper<a>() && xv >= S.template hi_r<a>(c, m);
+        L.act[a] = (lo_hit && g[a] <= 0.f) || (hi_hit && g[a] >= 0.f);
+        float haa = H[up<P>(a, a)];
+        if (!L.act[a]) {
+          if (fabsf(g[a]) > c.tol_g * sqrtf(haa * cst)) small = false;
+          mx = fmaxf(mx, haa);
+        }
+      });
+      if (small) { L.status = PX_CONVERGED; return false; }
+      if (L.lam < 0.f) L.lam = c.tau0 * mx;
+      L.fresh = false;
+    }
+    // damping diagonal, projected-Newton solve with re-solve on bound hits
+    float D[P], dr[P];
+    bool pin[P];
+    signed char pd[P];   // -1 / +1: pinned on lo / hi by the step solve
+    float mxd = 0.f;
+#pragma unroll
+    for (int a = 0; a < P; a++)
+      if (!L.act[a]) mxd = fmaxf(mxd, H[up<P>(a, a)]);
+#pragma unroll
+    for (int a = 0; a < P; a++) {
+      D[a] = fmaxf(H[up<P>(a, a)], c.dfloor * mxd);
+      pin[a] = L.act[a];
+      dr[a] = 0.f;
+      pd[a] = 0;
+    }
+    bool ok = true;
+#pragma unroll 1
+    for (int pass = 0; pass <= P; pass++) {
+      int nf = 0;
+#pragma unroll
+      for (int a = 0; a < P; a++) nf += !pin[a];
+      if (nf == 0) break;
+      float kap = 0.f;
+      ok = damped_solve<P, float>(H, g, L.lam, D, pin, dr, kap);
+      if (!ok || !(kap <= c.kappa_max)) {
+        Solve64<P> q;
+#pragma unroll
+        for (int i = 0; i < St::NH; i++) q.H[i] = H[i];
+#pragma unroll
+        for (int a = 0; a < P; a++) {
+          q.g[a] = g[a];
+          q.D[a] = D[a];
+          q.pin[a] = pin[a];
+          q.dr[a] = dr[a];
+        }
+        q.lam = L.lam;
+        ok = solve_fp64<P>(q);
+#pragma unroll
+        for (int a = 0; a < P; a++) dr[a] = q.dr[a];
+        L.used64 = true;
+      }
+      if (!ok) break;
+      bool viol = false;
+      static_for<P>([&](auto A_) {
+        constexpr int a = decltype(A_)::value;
+        if (!pin[a]) {
+          float xv = St::template rsel<a>(x, m);
+          float sc = S.template sc_r<a>(c, m);
+          float lo = S.template lo_r<a>(c, m), hi = S.template hi_r<a>(c, m);
+          float xn = xv + sc * dr[a];
+          if (!(sc > 0.f)) { pin[a] = true; dr[a] = 0.f; viol = true; }
+          else if (xn < lo) { pin[a] = true; pd[a] = -1; dr[a] = (lo - xv) / sc; viol = true; }
+          else if (St::template has_upper<a>() && xn > hi) {
+            pin[a] = true; pd[a] = 1; dr[a] = (hi - xv) / sc; viol = true;
+          }
+        }
+      });
+      if (!viol) break;
+    }
+    if (!ok) {
+      L.lam *= L.nu; L.nu *= 2.f; L.it++;
+      if (!(L.lam < 1e30f)) { L.status = PX_CHOL_FAIL; return false; }
+      continue;
+    }
+    S.apply(c, x, dr, pd, m, xt);
+    float Dz[NX], dmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < NX; i++) {
+      float sc = S.scale(c, i);
+      Dz[i] = sc > 0.f ? (xt[i] - x[i]) / sc : 0.f;
+      dmax = fmaxf(dmax, fabsf(Dz[i]));
+    }
+    if (dmax < c.tol_x) { L.status = PX_CONVERGED; return false; }
+    float Dr[P];
+    static_for<P>([&](auto A_) {
+      constexpr int a = decltype(A_)::value;
+      Dr[a] = St::template rsel<a>(Dz, m);
+    });
+    // predicted decrease of the Gauss-Newton model: 2 g.D - D.H.D
+    float pred = 0.f;
+#pragma unroll
+    for (int a = 0; a < P; a++) {
+      pred += 2.f * g[a] * Dr[a];
+#pragma unroll
+      for (int b = 0; b < P; b++) pred -= Dr[a] * H[up<P>(a, b)] * Dr[b];
+    }
+    L.pred = pred;
+    L.it++;
+    return true;
+  }
+  return false;
+}
+
+// Nielsen damping update after a step with gain ratio rho
+template <int P>
+__device__ __forceinline__ void damping_update(LMIter<P> &L, bool accept, float rho) {
+  if (accept) {
+    float f = 2.f * rho - 1.f;
+    f = 1.f - f * f * f;
+    L.lam *= fmaxf(f, 1.f / 3.f);
+    L.nu = 2.f;
+    L.fresh = true;
+  } else {
+    L.lam *= L.nu;
+    L.nu *= 2.f;
+  }
+}
+
+// Stage-1 driver: every trial point is evaluated in full (model, Jacobian,
+// normal equations); the decrease comes from residual differences.
 template <class St>
 __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::NX], int max_it,
                                        float (&H)[St::NH], float (&g)[St::P], int &m,
                                        LMResult &res) {
   constexpr int P = St::P, NX = St::NX, NH = St::NH, NS = St::NS;
   const KConfig &c = *pc.c;
-  float cst = 0.f, cd = 0.f, pred = 0.f;
+  float cst = 0.f, cd = 0.f;
   float r[NS], rt[NS], xt[NX];
 #pragma unroll
   for (int i = 0; i < NS; i++) r[i] = 0.f;
 #pragma unroll
   for (int i = 0; i < NX; i++) xt[i] = x[i];
-  float lam = -1.f, nu = 2.f;
-  int it = 0, status = PX_MAXITER, nfull = 0;
-  bool fresh = false, used64 = false, first = true;
-  bool act[P];
+  LMIter<P> L;
+  int nfull = 0;
+  bool first = true;
 #pragma unroll
-  for (int a = 0; a < P; a++) act[a] = false;
+  for (int a = 0; a < P; a++) L.act[a] = false;
 #pragma unroll 1
   for (;;) {
-    // ---- evaluate the model, Jacobian and normal equations at xt
-    float Ht[NH], gt[P], ct = 0.f, cdt = 0.f, dct = 0.f;
-    int mt = 0;
+    float Ht[NH], gt[P], ct, cdt, dct;
+    int mt;
+    S.eval(pc, xt, Ht, gt, ct, cdt, mt, r, rt, dct);
+    nfull++;
     bool accept = first, done = false;
     float rel = 1.f, rho = 1.f;
-    if constexpr (St::kTrialDrop) {
-      // decrease-only trial evaluation; the full one follows acceptance
-      if (!first) {
-        const float drop = S.trial_drop(pc, x, xt, r) + S.prior_drop(c, x, xt);
-        rho = pred > 0.f ? drop / pred : -1.f;
-        accept = rho > 0.f;
-        rel = drop / cst;
-      }
-      if (accept) {
-        S.eval(pc, xt, Ht, gt, ct, cdt, mt, r, rt, dct);
-        nfull++;
-      }
-    } else {
-      S.eval(pc, xt, Ht, gt, ct, cdt, mt, r, rt, dct);
-      nfull++;
-      if (!first) {
-        // actual decrease from residual differences (accurate where cost - ct
-        // would cancel in FP32) against the Gauss-Newton prediction
-        const float drop = dct + S.prior_drop(c, x, xt);
-        rho = pred > 0.f ? drop / pred : -1.f;
-        accept = rho > 0.f;
-        rel = drop / cst;
-      }
+    if (!first) {
+      // actual decrease from residual differences (accurate where cost - ct
+      // would cancel in FP32) against the Gauss-Newton prediction
+      const float drop = dct + S.prior_drop(c, x, xt);
+      rho = L.pred > 0.f ? drop / L.pred : -1.f;
+      accept = rho > 0.f;
+      rel = drop / cst;
     }
     if (accept) {
 #pragma unroll
@@ -741,139 +898,54 @@ __device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::N
       cst = ct;
       cd = cdt;
       m = mt;
-      if (!first) {
-        float f = 2.f * rho - 1.f;
-        f = 1.f - f * f * f;
-        lam *= fmaxf(f, 1.f / 3.f);
-        nu = 2.f;
-        if (rel < c.tol_f) { status = PX_CONVERGED; done = true; }
-      }
-      fresh = true;
-    } else {
-      lam *= nu;
-      nu *= 2.f;
+      if (!first && rel < c.tol_f) { L.status = PX_CONVERGED; done = true; }
     }
+    if (!first) damping_update(L, accept, rho);
     first = false;
     if (done) break;
-    // ---- produce the next trial point (or stop)
-    bool have_trial = false;
-#pragma unroll 1
-    while (it < max_it) {
-      if (fresh) {
-        bool small = true;
-        float mx = 0.f;
-        static_for<P>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          float xv = St::template rsel<a>(x, m);
-          bool lo_hit = xv <= S.template lo_r<a>(c, m);
-          bool hi_hit = St::template has_upper<a>() && xv >= S.template hi_r<a>(c, m);
-          act[a] = (lo_hit && g[a] <= 0.f) || (hi_hit && g[a] >= 0.f);
-          float haa = H[up<P>(a, a)];
-          if (!act[a]) {
-            if (fabsf(g[a]) > c.tol_g * sqrtf(haa * cst)) small = false;
-            mx = fmaxf(mx, haa);
-          }
-        });
-        if (small) { status = PX_CONVERGED; break; }
-        if (lam < 0.f) lam = c.tau0 * mx;
-        fresh = false;
-      }
-      // damping diagonal, projected-Newton solve with re-solve on bound hits
-      float D[P], dr[P];
-      bool pin[P];
-      signed char pd[P];   // -1 / +1: pinned on lo / hi by the step solve
-      float mxd = 0.f;
-#pragma unroll
-      for (int a = 0; a < P; a++)
-        if (!act[a]) mxd = fmaxf(mxd, H[up<P>(a, a)]);
-#pragma unroll
-      for (int a = 0; a < P; a++) {
-        D[a] = fmaxf(H[up<P>(a, a)], c.dfloor * mxd);
-        pin[a] = act[a];
-        dr[a] = 0.f;
-        pd[a] = 0;
-      }
-      bool ok = true;
-#pragma unroll 1
-      for (int pass = 0; pass <= P; pass++) {
-        int nf = 0;
-#pragma unroll
-        for (int a = 0; a < P; a++) nf += !pin[a];
-        if (nf == 0) break;
-        float kap = 0.f;
-        ok = damped_solve<P, float>(H, g, lam, D, pin, dr, kap);
-        if (!ok || !(kap <= c.kappa_max)) {
-          Solve64<P> q;
-#pragma unroll
-          for (int i = 0; i < NH; i++) q.H[i] = H[i];
-#pragma unroll
-          for (int a = 0; a < P; a++) {
-            q.g[a] = g[a];
-            q.D[a] = D[a];
-            q.pin[a] = pin[a];
-            q.dr[a] = dr[a];
-          }
-          q.lam = lam;
-          ok = solve_fp64<P>(q);
-#pragma unroll
-          for (int a = 0; a < P; a++) dr[a] = q.dr[a];
-          used64 = true;
-        }
-        if (!ok) break;
-        bool viol = false;
-        static_for<P>([&](auto A_) {
-          constexpr int a = decltype(A_)::value;
-          if (!pin[a]) {
-            float xv = St::template rsel<a>(x, m);
-            float sc = S.template sc_r<a>(c, m);
-            float lo = S.template lo_r<a>(c, m), hi = S.template hi_r<a>(c, m);
-            float xn = xv + sc * dr[a];
-            if (!(sc > 0.f)) { pin[a] = true; dr[a] = 0.f; viol = true; }
-            else if (xn < lo) { pin[a] = true; pd[a] = -1; dr[a] = (lo - xv) / sc; viol = true; }
-            else if (St::template has_upper<a>() && xn > hi) {
-              pin[a] = true; pd[a] = 1; dr[a] = (hi - xv) / sc; viol = true;
-            }
-          }
-        });
-        if (!viol) break;
-      }
-      if (!ok) {
-        lam *= nu; nu *= 2.f; it++;
-        if (!(lam < 1e30f)) { status = PX_CHOL_FAIL; break; }
-        continue;
-      }
-      S.apply(c, x, dr, pd, m, xt);
-      float Dz[NX], dmax = 0.f;
-#pragma unroll
-      for (int i = 0; i < NX; i++) {
-        float sc = S.scale(c, i);
-        Dz[i] = sc > 0.f ? (xt[i] - x[i]) / sc : 0.f;
-        dmax = fmaxf(dmax, fabsf(Dz[i]));
-      }
-      if (dmax < c.tol_x) { status = PX_CONVERGED; break; }
-      float Dr[P];
-      static_for<P>([&](auto A_) {
-        constexpr int a = decltype(A_)::value;
-        Dr[a] = St::template rsel<a>(Dz, m);
-      });
-      // predicted decrease of the Gauss-Newton model: 2 g.D - D.H.D
-      pred = 0.f;
-#pragma unroll
-      for (int a = 0; a < P; a++) {
-        pred += 2.f * g[a] * Dr[a];
-#pragma unroll
-        for (int b = 0; b < P; b++) pred -= Dr[a] * H[up<P>(a, b)] * Dr[b];
-      }
-      it++;
-      have_trial = true;
-      break;
-    }
-    if (!have_trial) break;
+    if (!next_trial(S, c, x, H, g, m, cst, max_it, L, xt)) break;
   }
-  res.iters = it;
+  res.iters = L.it;
   res.full = nfull;
-  res.status = status;
-  res.used64 = used64;
+  res.status = L.status;
+  res.used64 = L.used64;
+  res.cost = cst;
+  res.cdata = cd;
+}
+
+// Stage-2 driver: a trial point is judged by the decrease-only evaluation
+// in increment form; the full evaluation runs only at accepted points and
+// writes the new state's normal equations and residuals in place.
+template <class St>
+__device__ __forceinline__ void lm_fit2(const St &S, PixCtx &pc, float (&x)[St::NX], int max_it,
+                                        float (&H)[St::NH], float (&g)[St::P], LMResult &res) {
+  constexpr int P = St::P, NX = St::NX;
+  const KConfig &c = *pc.c;
+  float cst = 0.f, cd = 0.f, xt[NX];
+  LMIter<P> L;
+#pragma unroll
+  for (int a = 0; a < P; a++) L.act[a] = false;
+  S.eval(pc, x, H, g, cst, cd);
+  int nfull = 1;
+#pragma unroll 1
+  while (next_trial(S, c, x, H, g, 0, cst, max_it, L, xt)) {
+    const float drop = S.trial_drop(pc, x, xt) + S.prior_drop(c, x, xt);
+    const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
+    const bool accept = rho > 0.f;
+    damping_update(L, accept, rho);
+    if (accept) {
+      const float rel = drop / cst;   // relative to the cost before the step
+#pragma unroll
+      for (int i = 0; i < NX; i++) x[i] = xt[i];
+      S.eval(pc, x, H, g, cst, cd);
+      nfull++;
+      if (rel < c.tol_f) { L.status = PX_CONVERGED; break; }
+    }
+  }
+  res.iters = L.it;
+  res.full = nfull;
+  res.status = L.status;
+  res.used64 = L.used64;
   res.cost = cst;
   res.cdata = cd;
 }
@@ -1084,9 +1156,7 @@ __device__ __forceinline__ int setup2(Stage2<S2> &s2, const PixCtx &pc, const fl
 #pragma unroll
   for (int s = 0; s < S2; s++) {
     int bi = pc.lane + 32 * s;
-    s2.y[s] = 0.f;
-    s2.tu[s] = 0.f;
-    s2.w[s] = 0.f;
+    float yv = 0.f, tv = 0.f, wv = 0.f;
     if (bi < t.n2) {
       int b = t.b2lo + bi;
       float L = __ldg(row + b);
@@ -1096,17 +1166,20 @@ __device__ __forceinline__ int setup2(Stage2<S2> &s2, const PixCtx &pc, const fl
       float rho = 0.f;
 #pragma unroll
       for (int k = 0; k < K; k++) rho = fmaf(xs[k], pc.img[t.lay.off_endm + k * t.nb + b], rho);
-      s2.y[s] = L - (q.y + q.x * rho / (1.f - q.z * rho));
-      s2.tu[s] = q.w;
-      s2.w[s] = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
+      yv = L - (q.y + q.x * rho / (1.f - q.z * rho));
+      tv = q.w;
+      wv = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
       if (ok) { nv += var; nu++; }
     }
+    s2.yb(bi) = yv;
+    s2.tub(bi) = tv;
+    s2.wb(bi) = wv;
+    s2.rb(bi) = yv;
   }
+  __syncwarp();
   nv = warp_sum1(nv);
   nu = __reduce_add_sync(kFull, nu);
   s2.psc = c.weighted ? 1.f : nv / (float)max(nu, 1);
-#pragma unroll
-  for (int i = 0; i < 6; i++) s2.s[i] = 0.5f * (c.hi2[i] - c.lo2[i]);
   return nu;
 }
 
@@ -1187,7 +1260,7 @@ __global__ void __launch_bounds__(WPB * 32, MINB) lm_stage1_kernel(const __grid_
   pc.t = &t;
   pc.c = &c;
   pc.img = smem;
-  pc.wsc = smem + t.lay.total + warp * kMaxTgrid * kScratchPerNode;
+  pc.wsc = smem + t.lay.total + warp * warp_scratch_floats(t);
   pc.lane = lane;
   const int NSx = K + 8;
   unsigned long long mine[ST_COUNT];
@@ -1291,7 +1364,7 @@ __global__ void __launch_bounds__(WPB * 32, MINB) lm_stage1_kernel(const __grid_
 
 // ---- stage 2: mixture fit from the stage-1 hand-over, covariance, outputs
 template <int K, int S2, int WPB>
-__global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __grid_constant__ LMLaunch p) {
+__global__ void __launch_bounds__(WPB * 32, 1) lm_stage2_kernel(const __grid_constant__ LMLaunch p) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ unsigned long long cstat[ST_COUNT];
@@ -1304,7 +1377,7 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
   pc.t = &t;
   pc.c = &c;
   pc.img = smem;
-  pc.wsc = smem + t.lay.total + warp * kMaxTgrid * kScratchPerNode;
+  pc.wsc = smem + t.lay.total + warp * warp_scratch_floats(t);
   pc.lane = lane;
   unsigned long long mine[ST_COUNT];
 #pragma unroll
@@ -1331,6 +1404,7 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
 #pragma unroll
       for (int k = 0; k < K; k++) xs[k] = x1[k];
       Stage2<S2> s2;
+      s2.bb = pc.wsc + t.nt * kScratchPerNode;
       const int n2u = setup2<K, S2>(s2, pc, row, xs);
       float x2[6];
       const float *ini = ref.init;
@@ -1360,7 +1434,7 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
           }
           z2[5] = 0.f;
           zd[5] = 0.f;
-          const float Dp = s2.trial_drop(pc, z2, x2, s2.y), Dd = s2.trial_drop(pc, zd, xd, s2.y);
+          const float Dp = s2.trial_drop(pc, z2, x2, true), Dd = s2.trial_drop(pc, zd, xd, true);
           take_d = !(Dp - Dd + s2.prior_drop(c, xd, x2) > 0.f);
         }
         if (take_d) {
@@ -1369,9 +1443,8 @@ __global__ void __launch_bounds__(WPB * 32, LM2_MINB) lm_stage2_kernel(const __g
         }
       }
       float H2[21], g2[6];
-      int m2;
       LMResult r2;
-      lm_fit(s2, pc, x2, c.max_it2, H2, g2, m2, r2);
+      lm_fit2(s2, pc, x2, c.max_it2, H2, g2, r2);
       if (r2.used64) status |= PX_F_FP64;
       status |= r2.status;
       mine[ST_IT2] += r2.iters;
@@ -1555,7 +1628,7 @@ __global__ void __launch_bounds__(WPB * 32, 1) normal_eq_kernel(const __grid_con
   pc.t = &t;
   pc.c = &c;
   pc.img = smem;
-  pc.wsc = smem + t.lay.total + warp * kMaxTgrid * kScratchPerNode;
+  pc.wsc = smem + t.lay.total + warp * warp_scratch_floats(t);
   pc.lane = lane;
   const long long nw = (long long)gridDim.x * WPB;
   for (long long pix = (long long)blockIdx.x * WPB + warp; pix < p.s.n_pix; pix += nw) {
@@ -1586,13 +1659,10 @@ __global__ void __launch_bounds__(WPB * 32, 1) normal_eq_kernel(const __grid_con
 #pragma unroll
       for (int i = 0; i < 6; i++) x[i] = states[pix * (K + 6) + K + i];
       Stage2<S2> s2;
+      s2.bb = pc.wsc + t.nt * kScratchPerNode;
       setup2<K, S2>(s2, pc, row, xs);
-      constexpr int NS = S2;
-      float H[21], g[6], cst, cd, dcd, r0[NS], r1[NS];
-      int m;
-#pragma unroll
-      for (int i = 0; i < NS; i++) r0[i] = 0.f;
-      s2.eval(pc, x, H, g, cst, cd, m, r0, r1, dcd);
+      float H[21], g[6], cst, cd;
+      s2.eval(pc, x, H, g, cst, cd);
       if (lane == 0) {
         for (int a = 0; a < 6; a++) {
           gout[pix * 6 + a] = g[a];
@@ -1606,48 +1676,65 @@ __global__ void __launch_bounds__(WPB * 32, 1) normal_eq_kernel(const __grid_con
 
 constexpr int kWPB = 8;
 
-template <class Kern>
+template <int WPB, class Kern>
 cudaError_t launch_persistent(Kern kern, const LMLaunch &p, int num_sms, cudaStream_t st,
                               int *blocks_used) {
-  size_t smem = lm_smem_bytes(p.t);
+  size_t smem = lm_smem_bytes(p.t, WPB);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWPB * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WPB * 32, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const int cl = p.s.claim > 0 ? p.s.claim : kClaim;
-  long long need = (p.s.n_pix + (long long)kWPB * cl - 1) / ((long long)kWPB * cl);
+  long long need = (p.s.n_pix + (long long)WPB * cl - 1) / ((long long)WPB * cl);
   long long blocks = (long long)num_sms * occ;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  kern<<<(int)blocks, kWPB * 32, smem, st>>>(p);
+  kern<<<(int)blocks, WPB * 32, smem, st>>>(p);
   if (blocks_used) *blocks_used += (int)blocks;
   return cudaGetLastError();
 }
 
 template <int K, int S1, int S2>
-cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant) {
+cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant,
+                     cudaEvent_t *ev) {
+  cudaError_t e;
+  if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   // variant bit 0: stage 1 with two CTAs per SM (128 registers) instead of one
-  cudaError_t e = (variant & 1)
-                      ? launch_persistent(lm_stage1_kernel<K, S1, kWPB, 2>, p, num_sms, st, blocks_used)
-                      : launch_persistent(lm_stage1_kernel<K, S1, kWPB, 1>, p, num_sms, st, blocks_used);
+  e = (variant & 1)
+          ? launch_persistent<kWPB>(lm_stage1_kernel<K, S1, kWPB, 2>, p, num_sms, st, blocks_used)
+          : launch_persistent<kWPB>(lm_stage1_kernel<K, S1, kWPB, 1>, p, num_sms, st, blocks_used);
   if (e != cudaSuccess) return e;
-  e = launch_persistent(lm_stage2_kernel<K, S2, kWPB>, p, num_sms, st, blocks_used);
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
+  // variant bits 1-2: stage 2 with 8, 12 or 16 warps per CTA (one CTA per
+  // SM; up to 255, 168 or 128 registers)
+  int v2 = (variant >> 1) & 3;
+  if (v2 == 2 && lm_smem_bytes(p.t, 16) > kMaxSmemPerCta) v2 = 1;   // too many band slots
+  if (v2 == 1 && lm_smem_bytes(p.t, 12) > kMaxSmemPerCta) v2 = 0;
+  switch (v2) {
+    case 1: e = launch_persistent<12>(lm_stage2_kernel<K, S2, 12>, p, num_sms, st, blocks_used); break;
+    case 2: e = launch_persistent<16>(lm_stage2_kernel<K, S2, 16>, p, num_sms, st, blocks_used); break;
+    default: e = launch_persistent<kWPB>(lm_stage2_kernel<K, S2, kWPB>, p, num_sms, st, blocks_used);
+  }
   if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   long long blocks = (p.s.n_pix + 127) / 128;
   if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
   finalize_kernel<<<(int)blocks, 128, 0, st>>>(p, K);
   if (blocks_used) *blocks_used += (int)blocks;
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev) return cudaEventRecord(ev[3], st);
+  return cudaSuccess;
 }
 
 template <int K>
-cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant) {
+cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant,
+                     cudaEvent_t *ev) {
   int s1 = (p.t.n1 + 31) / 32, s2 = (p.t.n2 + 31) / 32;
-  if (s1 <= 9 && s2 <= 7) return launch_t<K, 9, 7>(p, num_sms, st, blocks_used, variant);
-  if (s1 <= 9 && s2 <= 9) return launch_t<K, 9, 9>(p, num_sms, st, blocks_used, variant);
-  if (s1 <= 16 && s2 <= 16) return launch_t<K, 16, 16>(p, num_sms, st, blocks_used, variant);
+  if (s1 <= 9 && s2 <= 7) return launch_t<K, 9, 7>(p, num_sms, st, blocks_used, variant, ev);
+  if (s1 <= 9 && s2 <= 9) return launch_t<K, 9, 9>(p, num_sms, st, blocks_used, variant, ev);
+  if (s1 <= 16 && s2 <= 16) return launch_t<K, 16, 16>(p, num_sms, st, blocks_used, variant, ev);
   return cudaErrorInvalidValue;
 }
 
@@ -1655,7 +1742,7 @@ template <int K>
 cudaError_t launch_ne_k(const LMLaunch &p, int stage, const float *states, float *H, float *g,
                         float *cost, cudaStream_t st) {
   int s1 = (p.t.n1 + 31) / 32, s2 = (p.t.n2 + 31) / 32;
-  size_t smem = lm_smem_bytes(p.t);
+  size_t smem = lm_smem_bytes(p.t, kWPB);
   int blocks = (int)((p.s.n_pix + kWPB - 1) / kWPB);
   if (blocks > 1024) blocks = 1024;
   auto go = [&](auto kern) {
@@ -1672,14 +1759,15 @@ cudaError_t launch_ne_k(const LMLaunch &p, int stage, const float *states, float
 
 }  // namespace
 
-size_t lm_smem_bytes(const KTables &t) {
-  return (size_t)t.lay.total * 4 + (size_t)kWPB * kMaxTgrid * kScratchPerNode * 4;
+size_t lm_smem_bytes(const KTables &t, int wpb) {
+  return (size_t)t.lay.total * 4 + (size_t)wpb * warp_scratch_floats(t) * 4;
 }
 
-cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant) {
+cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant,
+                      cudaEvent_t *ev) {
   switch (p.t.K) {
-    case 3: return launch_k<3>(p, num_sms, st, blocks_used, variant);
-    case 5: return launch_k<5>(p, num_sms, st, blocks_used, variant);
+    case 3: return launch_k<3>(p, num_sms, st, blocks_used, variant, ev);
+    case 5: return launch_k<5>(p, num_sms, st, blocks_used, variant, ev);
     default: return cudaErrorInvalidValue;
   }
 }

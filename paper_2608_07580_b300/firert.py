@@ -29,7 +29,7 @@ SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fir
            "fire_mlp_gradients", "fire_mlp_param_count", "fire_mlp_params", "fire_mlp_save",
            "fire_mlp_load", "fire_mlp_next_sample", "fire_ctx_set_mlp", "fire_retrieve_batch",
            "fire_graph_capture", "fire_graph_launch", "fire_graph_destroy", "fire_autotune",
-           "fire_set_tuning")
+           "fire_set_tuning", "fire_set_kernel_timing", "fire_get_kernel_times")
 
 
 class FireError(RuntimeError):
@@ -105,6 +105,7 @@ class Stats_t(C.Structure):
                 ("band_evals2", C.c_uint64), ("node_band_evals2", C.c_uint64),
                 ("trial_band_evals2", C.c_uint64), ("trial_node_band_evals2", C.c_uint64),
                 ("status_counts", C.c_uint64 * 8), ("flops", C.c_double),
+                ("flops1", C.c_double), ("flops2", C.c_double),
                 ("kernel_launches", C.c_int32)]
 
 
@@ -165,6 +166,10 @@ def _load():
     lib.fire_graph_destroy.argtypes = [vp]
     lib.fire_autotune.argtypes = [vp, vp, vp, i64, C.POINTER(Tune_t), vp]
     lib.fire_autotune.restype = C.c_int
+    lib.fire_set_kernel_timing.argtypes = [vp, i32]
+    lib.fire_set_kernel_timing.restype = C.c_int
+    lib.fire_get_kernel_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_int32)]
+    lib.fire_get_kernel_times.restype = C.c_int
     lib.fire_set_tuning.argtypes = [vp, i32, i32]
     lib.fire_set_tuning.restype = C.c_int
     lib.fire_status_str.argtypes = [C.c_int]
@@ -373,6 +378,16 @@ class Context:
                                  int(radiance.shape[0]), C.byref(t), _stream_ptr(stream)),
                "fire_autotune")
         return {"variant": t.variant, "claim": t.claim, "ms": t.ms}
+
+    def set_kernel_timing(self, on=True):
+        _check(lib.fire_set_kernel_timing(self._h, int(bool(on))), "fire_set_kernel_timing")
+
+    def kernel_times(self):
+        """Summed ms of (stage 1, stage 2, finalize) over the timed fits, and their count."""
+        ms = (C.c_float * 3)()
+        n = C.c_int32()
+        _check(lib.fire_get_kernel_times(self._h, ms, C.byref(n)), "fire_get_kernel_times")
+        return list(ms), n.value
 
     def set_tuning(self, variant, claim):
         _check(lib.fire_set_tuning(self._h, variant, claim), "fire_set_tuning")
