@@ -231,6 +231,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-mlp", action="store_true")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="launch shape 0..2 (default: autotuned on a tenth of the scene)")
+    ap.add_argument("--claim", type=int, default=2)
     ap.add_argument("--mlp-steps", type=int, default=3000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -262,6 +265,14 @@ def main():
     rad = ctx.forward(mode, st_d, wv_d, 0.005, 1e-4, seed=tr.seed, stream_id=synth.STREAM_NOISE,
                       pixel_offset=rank * n)
     del st_d
+    # launch shape (lanes per pixel of each stage, pixels per claim) picked by
+    # the library's autotuner on the first tenth of the scene, untimed
+    n_tune = min(n, max(1, n // 10))
+    if args.variant is None:
+        tune = ctx.autotune(rad[:n_tune], wv_d[:n_tune])
+    else:
+        ctx.set_tuning(args.variant, args.claim)
+        tune, n_tune = {"variant": args.variant, "claim": args.claim}, 0
     out = ctx.alloc_outputs(n)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
@@ -376,6 +387,8 @@ def main():
                        "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush needed)"
                        if args.workload != "small" else "small; not L2-flushed",
                        "init": "plain LM (default start)",
+                       "launch_shape": {"variant": tune["variant"], "claim": tune["claim"],
+                                        "tuned_on_px": n_tune},
                        "mean_iters": [round(it1, 2), round(it2, 2)],
                        "fp64_pixels": stats["n_fp64_pixels"],
                        "status_counts": stats["status_counts"]},

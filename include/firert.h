@@ -338,11 +338,13 @@ fire_status_t fire_graph_capture(fire_ctx_t *ctx, const fire_batch_item_t *items
 fire_status_t fire_graph_launch(fire_graph_t *g, fire_stream_t stream);
 void fire_graph_destroy(fire_graph_t *g);
 /* Autotuner: times each launch shape on the n given device pixels and keeps
- * the fastest for the context. variant bit 0: stage 1 as one CTA of 8 warps
- * per SM (up to 255 registers) or two (128); bits 1-2: stage 2 as one CTA
- * of 8, 12 or 16 warps per SM (255, 168 or 128 registers); claim: pixels
- * per work claim (1, 2, 4, 8). fire_set_tuning sets a shape directly
- * (variant 0..5, claim 1..64). */
+ * the fastest for the context. variant picks the lanes per pixel of stage 1:
+ * 0 = 16 lanes (two pixels per warp), 1 = 8 lanes (four per warp), 2 = 32
+ * lanes (one per warp); stage 2 always fits one pixel per warp. claim:
+ * pixels per work claim (1, 2, 4, 8). Each stage runs one persistent CTA per
+ * SM with as many warps as its shared memory allows (at most 12 for stage 1,
+ * 8 for stage 2). fire_set_tuning sets a shape directly (variant 0..2,
+ * claim 1..64). */
 typedef struct {
   int32_t variant, claim;
   float ms;

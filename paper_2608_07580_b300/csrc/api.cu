@@ -90,19 +90,6 @@ void fill_kconfig(KConfig &k, const fire_config_t &c, const fire_priors_t &p, in
   k.ident_alpha_snr = c.ident_alpha_snr;
 }
 
-bool priors_valid(const fire_priors_t &p, int K) {
-  for (int i = 0; i < K; i++)
-    if (p.lo1[i] != 0.f || p.hi1[i] != 1.f) return false;  // fractions live on [0, 1]
-  for (int i = 0; i < K + 2; i++)
-    if (!(p.hi1[i] >= p.lo1[i]) || !(p.pp1[i] >= 0.f)) return false;
-  for (int i = 0; i < 6; i++)
-    if (!(p.hi2[i] >= p.lo2[i]) || !(p.pp2[i] >= 0.f)) return false;
-  if (!(p.lo1[K + 1] > 0.f) || !(p.lo2[1] > 0.f) || !(p.lo2[3] > 0.f)) return false;  // T, sigma > 0
-  if (p.init_mode != FIRE_INIT_DEFAULT && p.init_mode != FIRE_INIT_GIVEN &&
-      p.init_mode != FIRE_INIT_MLP)
-    return false;
-  return true;
-}
 
 template <class T>
 fire_status_t dev_alloc(T **p, size_t bytes) {
@@ -160,6 +147,24 @@ KOut carve_outputs(void *buf, int64_t n, int K) {
 }
 
 }  // namespace
+
+namespace firert {
+
+bool priors_valid(const fire_priors_t &p, int K) {
+  for (int i = 0; i < K; i++)
+    if (p.lo1[i] != 0.f || p.hi1[i] != 1.f) return false;  // fractions live on [0, 1]
+  for (int i = 0; i < K + 2; i++)
+    if (!(p.hi1[i] >= p.lo1[i]) || !(p.pp1[i] >= 0.f)) return false;
+  for (int i = 0; i < 6; i++)
+    if (!(p.hi2[i] >= p.lo2[i]) || !(p.pp2[i] >= 0.f)) return false;
+  if (!(p.lo1[K + 1] > 0.f) || !(p.lo2[1] > 0.f) || !(p.lo2[3] > 0.f)) return false;  // T, sigma > 0
+  if (p.init_mode != FIRE_INIT_DEFAULT && p.init_mode != FIRE_INIT_GIVEN &&
+      p.init_mode != FIRE_INIT_MLP)
+    return false;
+  return true;
+}
+
+}  // namespace firert
 
 namespace firert {
 
@@ -656,15 +661,14 @@ fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   s->trial_node_band_evals2 = v[ST_TRIALNODE2];
   for (int k = 0; k < 8; k++) s->status_counts[k] = v[ST_STATUS0 + k];
   // algorithmic flops (FMA = 2): stage 1 per band and evaluation; stage 2 per
-  // band and full evaluation plus 6 FMA per band and active grid node, and
-  // per band and trial evaluation plus 2 FMA per band and active node
+  // band and evaluation (Jacobian, normal equations, cost and its
+  // increment-form decrease) plus 7 FMA per band and grid node (the six
+  // weight-moment sums and the weight-increment sum)
   const int K = c->t.K, P1 = K + 1;
   const double f1 = 4.0 * K + 27.0 + 2.0 * P1 * (P1 + 1) / 2.0 + 3.0 * P1 + 4.0;
-  const double f2 = 30.0 + 2.0 * 21.0 + 3.0 * 6.0 + 4.0;
-  const double f2t = 8.0;
+  const double f2 = 30.0 + 2.0 * 21.0 + 3.0 * 6.0 + 4.0 + 6.0;
   s->flops1 = f1 * (double)s->band_evals1;
-  s->flops2 = f2 * (double)s->band_evals2 + 12.0 * (double)s->node_band_evals2 +
-              f2t * (double)s->trial_band_evals2 + 4.0 * (double)s->trial_node_band_evals2;
+  s->flops2 = f2 * (double)s->band_evals2 + 14.0 * (double)s->node_band_evals2;
   s->flops = s->flops1 + s->flops2;
   s->kernel_launches = c->last_launches;
   return err ? FIRE_ERR_TIMEOUT : FIRE_OK;

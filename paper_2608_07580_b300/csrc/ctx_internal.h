@@ -49,6 +49,8 @@ struct fire_ctx {
 };
 
 namespace firert {
+// bounds, prior and start-rule checks of a priors block
+bool priors_valid(const fire_priors_t &p, int K);
 // the next 4 timing events of the context (nullptr when timing is off)
 cudaEvent_t *timing_events(fire_ctx *c);
 fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st);

@@ -1,10 +1,14 @@
 // kernels_lm.cu — the per-pixel two-stage retrieval on sm_103a.
 //
-// One warp per pixel, persistent CTAs claiming pixels from a global counter.
-// Lanes own bands (lane + 32 i within each stage's window), so radiance and
-// the shared Planck table are read band-coalesced; the normal equations
-// J^T W J, J^T W r and the cost are reduced with warp shuffles, and every
-// lane then runs the same small solve on registers (uniform control flow).
+// G lanes of a warp fit one pixel (32 / G pixels per warp; G = 8, 16 or 32
+// by launch shape), in persistent CTAs whose groups claim pixels from a
+// global counter. A group's lanes own band slots (sub + G s within each
+// stage's window), so radiance and the shared Planck table are read
+// band-coalesced; the normal equations J^T W J, J^T W r and the cost are
+// reduced with shuffles inside the group, and every lane of the group then
+// runs the same small solve on registers. Each round, every group with a
+// pixel takes one LM step, so the groups of a warp evaluate the model in
+// step; a pixel that converges hands over and its group takes the next.
 //
 // Stage 1 (Sec. 2.6): x1 = [x_surf(K), alpha1, T1] over Omega_1 with the
 // single-temperature Planck term computed on the SFU in the overflow-safe
@@ -32,20 +36,11 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kClaim = 4;          // pixels claimed per atomic
 constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in dynamic shared memory per CTA
-
-template <int N>
-__device__ __forceinline__ void warp_sum(float (&v)[N]) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1)
-#pragma unroll
-    for (int i = 0; i < N; i++) v[i] += __shfl_xor_sync(kFull, v[i], o);
-}
-
-__device__ __forceinline__ float warp_sum1(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
+// Stage-1 steps whose predicted decrease is below this fraction of the cost
+// are judged by the increment-form decrease: the decrease from residual
+// differences is accurate to a few 1e-6 of the cost, so above 1e-3 of it the
+// acceptance is decided correctly either way.
+constexpr float kIncBelow = 1e-3f;
 
 template <int I>
 struct IC { static constexpr int value = I; };
@@ -72,6 +67,12 @@ __device__ __forceinline__ double rsq(double x) {
   y = y * (1.5 - 0.5 * x * y * y);
   y = y * (1.5 - 0.5 * x * y * y);
   return y;
+}
+
+// expm1(y) for |y| < 0.05 by its Taylor series to y^5 (truncation below
+// |y|^6 / 720 < 2.2e-11 relative)
+__device__ __forceinline__ float em1_small(float y) {
+  return y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
 }
 
 // ------------------------------------------------------------- solve ----
@@ -159,527 +160,6 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
   return true;
 }
 
-// per-warp shared scratch: node weights [nt][8], then (stage 2) the band
-// buffers [4][S2 * 32] of the band-slot count the kernel is instantiated for
-__host__ __device__ __forceinline__ int s2_slots(int n2) {
-  const int s2 = (n2 + 31) / 32;
-  return s2 <= 7 ? 7 : (s2 <= 9 ? 9 : 16);
-}
-__host__ __device__ __forceinline__ int warp_scratch_floats(const KTables &t) {
-  return t.nt * kScratchPerNode + 4 * 32 * s2_slots(t.n2);
-}
-
-// ------------------------------------------------------- pixel context --
-struct PixCtx {
-  const KTables *t;
-  const KConfig *c;
-  const float *img;       // shared-memory table image
-  float *wsc;             // this warp's node scratch [nt][8]
-  const float4 *wvrow;    // this pixel's water-vapour row of the atmosphere table
-  int lane;
-  int node_evals;         // sum over stage-2 full evaluations of active nodes
-  int trial_nodes;        // sum over stage-2 trial (decrease-only) evaluations
-};
-
-// ------------------------------------------------------------ stage 1 ---
-template <int K, int S1>
-struct Stage1 {
-  static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2, NS = S1;
-  float Lobs[S1], w[S1];
-  float psc;
-  float sf, sa, sT;
-
-  // reduced variable a: fractions k != m in order, then alpha1, T1. These
-  // accessors select with compile-time indices (no local-memory indexing).
-  template <int A>
-  __device__ __forceinline__ static float rsel(const float (&v)[NX], int m) {
-    if constexpr (A >= K - 1) return v[A + 1];
-    else return A < m ? v[A] : v[A + 1];
-  }
-  template <int A>
-  __device__ __forceinline__ float lo_r(const KConfig &c, int m) const {
-    if constexpr (A >= K - 1) return c.lo1[A + 1];
-    else return A < m ? c.lo1[A] : c.lo1[A + 1];
-  }
-  template <int A>
-  __device__ __forceinline__ float hi_r(const KConfig &c, int m) const {
-    if constexpr (A >= K - 1) return c.hi1[A + 1];
-    else return A < m ? c.hi1[A] : c.hi1[A + 1];
-  }
-  template <int A>
-  __device__ __forceinline__ float sc_r(const KConfig &c, int m) const {
-    return 0.5f * (hi_r<A>(c, m) - lo_r<A>(c, m));
-  }
-  template <int A>
-  __device__ __forceinline__ static constexpr bool has_upper() { return A >= K - 1; }
-  __device__ __forceinline__ float scale(const KConfig &c, int i) const {
-    return 0.5f * (c.hi1[i] - c.lo1[i]);
-  }
-
-  __device__ __forceinline__ static int argmax_frac(const float (&x)[NX]) {
-    int m = 0;
-    float best = x[0];
-#pragma unroll
-    for (int k = 1; k < K; k++)
-      if (x[k] > best) { m = k; best = x[k]; }
-    return m;
-  }
-
-  // model, reduced Jacobian, normal equations and cost at x (all lanes get
-  // the warp totals). cd = unweighted data cost.
-  __device__ __forceinline__ void eval(PixCtx &pc, const float (&x)[NX], float (&H)[NH],
-                                       float (&g)[P], float &cst, float &cd, int &m,
-                                       const float (&rold)[NS], float (&rnew)[NS],
-                                       float &dcd) const {
-    const KTables &t = *pc.t;
-    const KConfig &c = *pc.c;
-    m = argmax_frac(x);
-    float acc[NH + P + 3];
-#pragma unroll
-    for (int i = 0; i < NH + P + 3; i++) acc[i] = 0.f;
-    const float a1 = x[K], invT = 1.f / x[K + 1];
-#pragma unroll
-    for (int s = 0; s < S1; s++) {
-      int bi = pc.lane + 32 * s;
-      if (bi < t.n1 && w[s] > 0.f) {
-        int b = t.b1lo + bi;
-        float4 q = __ldg(pc.wvrow + b);
-        float E[K];
-        float rho = 0.f;
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-          E[k] = pc.img[t.lay.off_endm + k * t.nb + b];
-          rho = fmaf(x[k], E[k], rho);
-        }
-        float inv = __frcp_rn(1.f - q.z * rho);
-        float Ls = fmaf(q.x * rho, inv, q.y);
-        float xx = pc.img[t.lay.off_c2l + b] * invT;
-        float e = __expf(-xx);
-        float rom = __frcp_rn(1.f - e);
-        float B = pc.img[t.lay.off_c1l5 + b] * e * rom;
-        float dB = B * xx * invT * rom;
-        float r = Lobs[s] - fmaf(a1 * q.w, B, Ls);
-        rnew[s] = r;
-        acc[NH + P + 2] = fmaf(w[s] * (rold[s] - r), rold[s] + r, acc[NH + P + 2]);
-        float dL[K], dEm = 0.f;
-        const float qi2 = q.x * inv * inv * sf;
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-          dL[k] = qi2 * E[k];
-          dEm = (k == m) ? dL[k] : dEm;
-        }
-        float J[P];
-#pragma unroll
-        for (int a = 0; a < K - 1; a++) J[a] = (a < m ? dL[a] : dL[a + 1]) - dEm;
-        J[K - 1] = q.w * B * sa;
-        J[K] = a1 * q.w * dB * sT;
-        float wr = w[s] * r;
-        acc[NH + P] = fmaf(wr, r, acc[NH + P]);
-        acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
-#pragma unroll
-        for (int a = 0; a < P; a++) {
-          acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
-          float wj = w[s] * J[a];
-#pragma unroll
-          for (int bb = a; bb < P; bb++) acc[up<P>(a, bb)] = fmaf(wj, J[bb], acc[up<P>(a, bb)]);
-        }
-      }
-    }
-    warp_sum(acc);
-#pragma unroll
-    for (int i = 0; i < NH; i++) H[i] = acc[i];
-#pragma unroll
-    for (int a = 0; a < P; a++) g[a] = acc[NH + a];
-    cd = acc[NH + P + 1];
-    cst = acc[NH + P];
-    dcd = acc[NH + P + 2];
-    // weak Gaussian prior in z, pulled into the reduced basis (e_k - e_m)
-    float zr[NX], ppm = 0.f, rm = 0.f;
-#pragma unroll
-    for (int i = 0; i < NX; i++) {
-      zr[i] = c.hi1[i] > c.lo1[i] ? 2.f * (x[i] - c.lo1[i]) / (c.hi1[i] - c.lo1[i]) - 1.f : 0.f;
-      zr[i] -= c.pm1[i];
-      float ppi = psc * c.pp1[i];
-      cst += ppi * zr[i] * zr[i];
-      if (i < K && i == m) { ppm = ppi; rm = zr[i]; }
-    }
-#pragma unroll
-    for (int a = 0; a < K - 1; a++) {
-      float ppa = psc * (a < m ? c.pp1[a] : c.pp1[a + 1]);
-      float ra = a < m ? zr[a] : zr[a + 1];
-      g[a] -= ppa * ra - ppm * rm;
-      H[up<P>(a, a)] += ppa + ppm;
-#pragma unroll
-      for (int bb = a + 1; bb < K - 1; bb++) H[up<P>(a, bb)] += ppm;
-    }
-#pragma unroll
-    for (int a = K - 1; a < P; a++) {
-      g[a] -= psc * c.pp1[a + 1] * zr[a + 1];
-      H[up<P>(a, a)] += psc * c.pp1[a + 1];
-    }
-  }
-
-  // prior(x_old) - prior(x_new), formed from differences of z
-  __device__ __forceinline__ float prior_drop(const KConfig &c, const float (&xo)[NX],
-                                              const float (&xn)[NX]) const {
-    float d = 0.f;
-#pragma unroll
-    for (int i = 0; i < NX; i++) {
-      if (c.hi1[i] > c.lo1[i] && c.pp1[i] > 0.f) {
-        float k = 2.f / (c.hi1[i] - c.lo1[i]);
-        float zo = k * (xo[i] - c.lo1[i]) - 1.f - c.pm1[i], zn = k * (xn[i] - c.lo1[i]) - 1.f - c.pm1[i];
-        d += psc * c.pp1[i] * (k * (xo[i] - xn[i])) * (zo + zn);
-      }
-    }
-    return d;
-  }
-
-  // x + step (z units, reduced basis) -> projected trial point
-  __device__ __forceinline__ void apply(const KConfig &c, const float (&x)[NX], const float (&dr)[P],
-                                        const signed char (&pd)[P], int m, float (&xt)[NX]) const {
-    float sum = 0.f;
-#pragma unroll
-    for (int a = 0; a < K - 1; a++) sum += dr[a];
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      float d = 0.f;
-      bool at0 = false;   // pinned on its lower bound by the step solve
-      if (k < K - 1 && k < m) { d = dr[k < K - 1 ? k : 0]; at0 = pd[k < K - 1 ? k : 0] < 0; }
-      if (k > 0 && k > m) { d = dr[k > 0 ? k - 1 : 0]; at0 = pd[k > 0 ? k - 1 : 0] < 0; }
-      xt[k] = (k == m) ? x[k] - sf * sum : (at0 ? c.lo1[k] : x[k] + sf * d);
-    }
-#pragma unroll
-    for (int i = K; i < K + 2; i++) {
-      float v = x[i] + scale(c, i) * dr[i - 1];
-      if (pd[i - 1] < 0) v = c.lo1[i];
-      if (pd[i - 1] > 0) v = c.hi1[i];
-      xt[i] = fminf(fmaxf(v, c.lo1[i]), c.hi1[i]);
-    }
-    simplex_project(xt);
-  }
-
-  // Euclidean projection of the fractions onto the unit simplex (sort-based)
-  __device__ __forceinline__ static void simplex_project(float (&x)[NX]) {
-    float u[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) u[k] = x[k];
-#pragma unroll
-    for (int i = 1; i < K; i++)
-#pragma unroll
-      for (int j = i; j > 0; j--)
-        if (u[j] > u[j - 1]) {
-          float tmp = u[j];
-          u[j] = u[j - 1];
-          u[j - 1] = tmp;
-        }
-    float cs = 0.f, theta = 0.f;
-#pragma unroll
-    for (int j = 0; j < K; j++) {
-      cs += u[j];
-      float th = (cs - 1.f) / (float)(j + 1);
-      if (u[j] - th > 0.f) theta = th;
-    }
-#pragma unroll
-    for (int k = 0; k < K; k++) x[k] = fmaxf(x[k] - theta, 0.f);
-  }
-
-};
-
-// ------------------------------------------------------------ stage 2 ---
-template <int S2>
-struct Stage2 {
-  static constexpr int P = 6, NX = 6, NH = 21, NS = S2;
-  static constexpr int NB = S2 * 32;   // band slots per buffer
-  // this warp's band buffers in shared memory, [4][NB]: y (radiance minus
-  // the fixed solar term), tu (tau_up), w (loss weight), r (residual at the
-  // current state); lane l owns slots l + 32 s
-  float *bb;
-  float psc;
-
-  __device__ __forceinline__ float &yb(int i) const { return bb[i]; }
-  __device__ __forceinline__ float &tub(int i) const { return bb[NB + i]; }
-  __device__ __forceinline__ float &wb(int i) const { return bb[2 * NB + i]; }
-  __device__ __forceinline__ float &rb(int i) const { return bb[3 * NB + i]; }
-
-  template <int A>
-  __device__ __forceinline__ static float rsel(const float (&v)[NX], int) { return v[A]; }
-  template <int A>
-  __device__ __forceinline__ float lo_r(const KConfig &c, int) const { return c.lo2[A]; }
-  template <int A>
-  __device__ __forceinline__ float hi_r(const KConfig &c, int) const { return c.hi2[A]; }
-  template <int A>
-  __device__ __forceinline__ float sc_r(const KConfig &c, int) const {
-    return 0.5f * (c.hi2[A] - c.lo2[A]);
-  }
-  template <int A>
-  __device__ __forceinline__ static constexpr bool has_upper() { return true; }
-  __device__ __forceinline__ float scale(const KConfig &c, int i) const {
-    return 0.5f * (c.hi2[i] - c.lo2[i]);
-  }
-
-  // model, Jacobian (z-scaled), normal equations and cost at x; writes the
-  // residuals into the r buffer. All lanes get the warp totals.
-  __device__ __forceinline__ void eval(PixCtx &pc, const float (&x)[NX], float (&H)[NH],
-                                       float (&g)[P], float &cst, float &cd) const {
-    const KTables &t = *pc.t;
-    const KConfig &c = *pc.c;
-    const float mh = x[0], sh = x[1], ms = x[2], ss = x[3], eta = x[4], al = x[5];
-    // grid weights of the two components: lanes own nodes j = lane + 32 q
-    float uh[4], us[4], dh[4], ds[4];
-    float mom[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const float ih = 0.5f / (sh * sh), is = 0.5f / (ss * ss);
-    unsigned act[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int j = pc.lane + 32 * q;
-      uh[q] = us[q] = dh[q] = ds[q] = 0.f;
-      if (j < t.nt) {
-        float T = t.tglo + (float)j * t.tgstep;
-        dh[q] = T - mh;
-        ds[q] = T - ms;
-        uh[q] = expf(-dh[q] * dh[q] * ih);
-        us[q] = expf(-ds[q] * ds[q] * is);
-      }
-      mom[0] += uh[q];
-      mom[1] += uh[q] * dh[q];
-      mom[2] += uh[q] * dh[q] * dh[q];
-      mom[3] += us[q];
-      mom[4] += us[q] * ds[q];
-      mom[5] += us[q] * ds[q] * ds[q];
-      act[q] = __ballot_sync(kFull, uh[q] > 1e-30f || us[q] > 1e-30f);
-    }
-    warp_sum(mom);
-    const float rUh = 1.f / mom[0], rUs = 1.f / mom[3];
-    const float dbh = mom[1] * rUh, m2h = mom[2] * rUh, dbs = mom[4] * rUs, m2s = mom[5] * rUs;
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int j = pc.lane + 32 * q;
-      if (j < t.nt) {
-        float wh = uh[q] * rUh, ws = us[q] * rUs;
-        float4 A = make_float4(wh, wh * (dh[q] - dbh), wh * (dh[q] * dh[q] - m2h), ws);
-        float4 B = make_float4(ws * (ds[q] - dbs), ws * (ds[q] * ds[q] - m2s), 0.f, 0.f);
-        reinterpret_cast<float4 *>(pc.wsc)[2 * j] = A;
-        reinterpret_cast<float4 *>(pc.wsc)[2 * j + 1] = B;
-      }
-    }
-    int jlo = t.nt, jhi = -1;
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-      if (act[q]) {
-        jlo = min(jlo, 32 * q + __ffs(act[q]) - 1);
-        jhi = max(jhi, 32 * q + 31 - __clz(act[q]));
-      }
-    __syncwarp();
-    // moment sums over the active nodes: 6 FMA per band and node
-    float S[S2][6];
-#pragma unroll
-    for (int s2 = 0; s2 < S2; s2++)
-#pragma unroll
-      for (int k = 0; k < 6; k++) S[s2][k] = 0.f;
-    const float *pl = pc.img + t.lay.off_planck + pc.lane;
-    const float4 *wv4 = reinterpret_cast<const float4 *>(pc.wsc);
-    for (int j = jlo; j <= jhi; j++) {
-      float4 A = wv4[2 * j], B = wv4[2 * j + 1];
-      const float *row = pl + j * t.lay.n2s;
-#pragma unroll
-      for (int s2 = 0; s2 < S2; s2++) {
-        float Bv = row[32 * s2];
-        S[s2][0] = fmaf(A.x, Bv, S[s2][0]);
-        S[s2][1] = fmaf(A.y, Bv, S[s2][1]);
-        S[s2][2] = fmaf(A.z, Bv, S[s2][2]);
-        S[s2][3] = fmaf(A.w, Bv, S[s2][3]);
-        S[s2][4] = fmaf(B.x, Bv, S[s2][4]);
-        S[s2][5] = fmaf(B.y, Bv, S[s2][5]);
-      }
-    }
-    pc.node_evals += (jhi >= jlo) ? (jhi - jlo + 1) : 0;
-    float acc[NH + P + 2];
-#pragma unroll
-    for (int i = 0; i < NH + P + 2; i++) acc[i] = 0.f;
-    const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
-    const float ish3 = ish2 / sh, iss3 = iss2 / ss;
-    const float sc0 = scale(c, 0), sc1 = scale(c, 1), sc2 = scale(c, 2), sc3 = scale(c, 3);
-    const float sc4 = scale(c, 4), sc5 = scale(c, 5);
-#pragma unroll
-    for (int s2 = 0; s2 < S2; s2++) {
-      const int i = pc.lane + 32 * s2;
-      const float wv = wb(i);
-      if (wv > 0.f) {
-        float Bh = S[s2][0], Bs = S[s2][3];
-        float Bm = eta * Bh + (1.f - eta) * Bs;
-        float tuv = tub(i);
-        float atu = al * tuv;
-        float r = yb(i) - atu * Bm;
-        rb(i) = r;
-        float J[6];
-        J[0] = atu * eta * S[s2][1] * ish2 * sc0;
-        J[1] = atu * eta * S[s2][2] * ish3 * sc1;
-        J[2] = atu * (1.f - eta) * S[s2][4] * iss2 * sc2;
-        J[3] = atu * (1.f - eta) * S[s2][5] * iss3 * sc3;
-        J[4] = atu * (Bh - Bs) * sc4;
-        J[5] = tuv * Bm * sc5;
-        float wr = wv * r;
-        acc[NH + P] = fmaf(wr, r, acc[NH + P]);
-        acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
-#pragma unroll
-        for (int a = 0; a < P; a++) {
-          acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
-          float wj = wv * J[a];
-#pragma unroll
-          for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
-        }
-      } else {
-        rb(i) = 0.f;
-      }
-    }
-    warp_sum(acc);
-#pragma unroll
-    for (int i = 0; i < NH; i++) H[i] = acc[i];
-#pragma unroll
-    for (int a = 0; a < P; a++) g[a] = acc[NH + a];
-    cst = acc[NH + P];
-    cd = acc[NH + P + 1];
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-      float z = c.hi2[i] > c.lo2[i] ? 2.f * (x[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
-      float pp = psc * c.pp2[i];
-      cst += pp * (z - c.pm2[i]) * (z - c.pm2[i]);
-      g[i] -= pp * (z - c.pm2[i]);
-      H[up<P>(i, i)] += pp;
-    }
-    __syncwarp();
-  }
-
-  // Gaussian weight u_o = exp(-a_o^2/2), a = (T - mu)/sigma, of one node at
-  // the current state and its change du under the step (dmu, dsig): the
-  // exponent change is formed from the parameter differences,
-  //   a_t - a_o = -(dmu sigma_o + (T - mu_o) dsig) / (sigma_t sigma_o),
-  // and du = u_o expm1(-dq), so du is resolved relative to itself.
-  __device__ __forceinline__ static void node_step(float T, float mu, float isg, float mut, float isgt,
-                                                   float dmu, float dsg, float &u, float &du) {
-    const float ao = (T - mu) * isg, at = (T - mut) * isgt;
-    const float da = -fmaf((T - mu) * dsg, isg, dmu) * isgt;
-    const float dq = 0.5f * da * (at + ao);
-    u = expf(-0.5f * ao * ao);
-    du = fabsf(dq) < 0.5f ? u * expm1f(-dq) : expf(-0.5f * at * at) - u;
-  }
-
-  // Data-term decrease of the trial step x -> xt, sum_b w_b dM_b (2 r_b -
-  // dM_b) with r the residuals at x and dM_b = tu_b (a_t dBm_b + (a_t - a)
-  // Bm_b) the model increment: Bm and dBm are the node sums of the current
-  // mixture weights and of their increments (the weight differences formed
-  // node by node from the exact parameter differences). The decrease is then
-  // accurate relative to itself, where the difference of two FP32 costs (or
-  // of two FP32 model values) would be lost below the model's rounding.
-  // 2 FMA per band and node.
-  __device__ __forceinline__ float trial_drop(PixCtx &pc, const float (&x)[NX],
-                                              const float (&xt)[NX], bool r_is_y = false) const {
-    const KTables &t = *pc.t;
-    const float eo = x[4], ao = x[5], et = xt[4], at = xt[5];
-    float uho[4], uso[4], duh[4], dus[4];
-    float U[4] = {0.f, 0.f, 0.f, 0.f};
-    unsigned act[4];
-    const float ih = 1.f / x[1], iht = 1.f / xt[1], is = 1.f / x[3], ist = 1.f / xt[3];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int j = pc.lane + 32 * q;
-      uho[q] = uso[q] = duh[q] = dus[q] = 0.f;
-      if (j < t.nt) {
-        float T = t.tglo + (float)j * t.tgstep;
-        node_step(T, x[0], ih, xt[0], iht, xt[0] - x[0], xt[1] - x[1], uho[q], duh[q]);
-        node_step(T, x[2], is, xt[2], ist, xt[2] - x[2], xt[3] - x[3], uso[q], dus[q]);
-      }
-      U[0] += uho[q];
-      U[1] += duh[q];
-      U[2] += uso[q];
-      U[3] += dus[q];
-      act[q] = __ballot_sync(kFull, uho[q] > 1e-30f || uso[q] > 1e-30f || uho[q] + duh[q] > 1e-30f ||
-                                        uso[q] + dus[q] > 1e-30f);
-    }
-    warp_sum(U);
-    const float rho_ = 1.f / U[0], rso = 1.f / U[2];
-    const float rht = 1.f / (U[0] + U[1]), rst = 1.f / (U[2] + U[3]);
-    const float kh = U[1] * rho_, ks = U[3] * rso;
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      int j = pc.lane + 32 * q;
-      if (j < t.nt) {
-        // w_t - w_o = (du - u_o dU/U_o) / U_t per component
-        float who = uho[q] * rho_, wso = uso[q] * rso;
-        float dwh = (duh[q] - uho[q] * kh) * rht, dws = (dus[q] - uso[q] * ks) * rst;
-        float Wo = eo * who + (1.f - eo) * wso;
-        float dW = et * dwh + (1.f - et) * dws + (et - eo) * (who - wso);
-        reinterpret_cast<float2 *>(pc.wsc)[4 * j] = make_float2(Wo, dW);
-      }
-    }
-    int jlo = t.nt, jhi = -1;
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-      if (act[q]) {
-        jlo = min(jlo, 32 * q + __ffs(act[q]) - 1);
-        jhi = max(jhi, 32 * q + 31 - __clz(act[q]));
-      }
-    __syncwarp();
-    float Bo[S2], dB[S2];
-#pragma unroll
-    for (int s2 = 0; s2 < S2; s2++) Bo[s2] = dB[s2] = 0.f;
-    const float *pl = pc.img + t.lay.off_planck + pc.lane;
-    const float2 *wv2 = reinterpret_cast<const float2 *>(pc.wsc);
-    for (int j = jlo; j <= jhi; j++) {
-      float2 A = wv2[4 * j];
-      const float *row = pl + j * t.lay.n2s;
-#pragma unroll
-      for (int s2 = 0; s2 < S2; s2++) {
-        float Bv = row[32 * s2];
-        Bo[s2] = fmaf(A.x, Bv, Bo[s2]);
-        dB[s2] = fmaf(A.y, Bv, dB[s2]);
-      }
-    }
-    pc.trial_nodes += (jhi >= jlo) ? (jhi - jlo + 1) : 0;
-    float d = 0.f;
-    const float da_ = at - ao;
-#pragma unroll
-    for (int s2 = 0; s2 < S2; s2++) {
-      const int i = pc.lane + 32 * s2;
-      const float wv = wb(i);
-      if (wv > 0.f) {
-        float dM = tub(i) * fmaf(at, dB[s2], da_ * Bo[s2]);
-        float r = r_is_y ? yb(i) : rb(i);
-        d = fmaf(wv * dM, 2.f * r - dM, d);
-      }
-    }
-    __syncwarp();
-    return warp_sum1(d);
-  }
-
-  __device__ __forceinline__ float prior_drop(const KConfig &c, const float (&xo)[NX],
-                                              const float (&xn)[NX]) const {
-    float d = 0.f;
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-      if (c.hi2[i] > c.lo2[i] && c.pp2[i] > 0.f) {
-        float k = 2.f / (c.hi2[i] - c.lo2[i]);
-        float zo = k * (xo[i] - c.lo2[i]) - 1.f - c.pm2[i], zn = k * (xn[i] - c.lo2[i]) - 1.f - c.pm2[i];
-        d += psc * c.pp2[i] * (k * (xo[i] - xn[i])) * (zo + zn);
-      }
-    }
-    return d;
-  }
-
-  __device__ __forceinline__ void apply(const KConfig &c, const float (&x)[NX], const float (&dr)[P],
-                                        const signed char (&pd)[P], int, float (&xt)[NX]) const {
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-      float v = x[i] + scale(c, i) * dr[i];
-      if (pd[i] < 0) v = c.lo2[i];
-      if (pd[i] > 0) v = c.hi2[i];
-      xt[i] = fminf(fmaxf(v, c.lo2[i]), c.hi2[i]);
-    }
-  }
-};
-
 // -------------------------------------------------------- LM driver -----
 struct LMResult {
   int iters, full, status;   // trial steps; full model + Jacobian evaluations
@@ -701,8 +181,6 @@ __device__ __noinline__ bool solve_fp64(Solve64<P> &q) {
   return damped_solve<P, double>(q.H, q.g, q.lam, q.D, q.pin, q.dr, q.kap);
 }
 
-// One stage of the fit. The model is evaluated at a single call site per
-// stage (start point, then every trial point) to keep the code compact.
 // State of the damped iteration shared by the two stage drivers.
 template <int P>
 struct LMIter {
@@ -851,104 +329,543 @@ __device__ __forceinline__ void damping_update(LMIter<P> &L, bool accept, float 
   }
 }
 
-// Stage-1 driver: every trial point is evaluated in full (model, Jacobian,
-// normal equations); the decrease comes from residual differences.
-template <class St>
-__device__ __forceinline__ void lm_fit(const St &S, PixCtx &pc, float (&x)[St::NX], int max_it,
-                                       float (&H)[St::NH], float (&g)[St::P], int &m,
-                                       LMResult &res) {
-  constexpr int P = St::P, NX = St::NX, NH = St::NH, NS = St::NS;
-  const KConfig &c = *pc.c;
-  float cst = 0.f, cd = 0.f;
-  float r[NS], rt[NS], xt[NX];
+// ------------------------------------------------------- pixel groups ---
+// G consecutive lanes of a warp fit one pixel, so a warp carries 32 / G
+// pixels. Reductions are xor shuffles restricted to the group's lanes, so a
+// group needs no other group to make progress; the fit loop keeps the
+// groups of a warp in step where the work is (every active group evaluates
+// the model at the same point of each round).
+template <int G>
+struct Grp {
+  int lane, sub;
+  unsigned mask;
+  __device__ __forceinline__ explicit Grp(int l)
+      : lane(l), sub(l & (G - 1)),
+        mask(G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (l & ~(G - 1)))) {}
+  template <int N>
+  __device__ __forceinline__ void sum(float (&v)[N]) const {
 #pragma unroll
-  for (int i = 0; i < NS; i++) r[i] = 0.f;
+    for (int o = G / 2; o; o >>= 1)
 #pragma unroll
-  for (int i = 0; i < NX; i++) xt[i] = x[i];
-  LMIter<P> L;
-  int nfull = 0;
-  bool first = true;
-#pragma unroll
-  for (int a = 0; a < P; a++) L.act[a] = false;
-#pragma unroll 1
-  for (;;) {
-    float Ht[NH], gt[P], ct, cdt, dct;
-    int mt;
-    S.eval(pc, xt, Ht, gt, ct, cdt, mt, r, rt, dct);
-    nfull++;
-    bool accept = first, done = false;
-    float rel = 1.f, rho = 1.f;
-    if (!first) {
-      // actual decrease from residual differences (accurate where cost - ct
-      // would cancel in FP32) against the Gauss-Newton prediction
-      const float drop = dct + S.prior_drop(c, x, xt);
-      rho = L.pred > 0.f ? drop / L.pred : -1.f;
-      accept = rho > 0.f;
-      rel = drop / cst;
-    }
-    if (accept) {
-#pragma unroll
-      for (int i = 0; i < NS; i++) r[i] = rt[i];
-#pragma unroll
-      for (int i = 0; i < NX; i++) x[i] = xt[i];
-#pragma unroll
-      for (int i = 0; i < NH; i++) H[i] = Ht[i];
-#pragma unroll
-      for (int a = 0; a < P; a++) g[a] = gt[a];
-      cst = ct;
-      cd = cdt;
-      m = mt;
-      if (!first && rel < c.tol_f) { L.status = PX_CONVERGED; done = true; }
-    }
-    if (!first) damping_update(L, accept, rho);
-    first = false;
-    if (done) break;
-    if (!next_trial(S, c, x, H, g, m, cst, max_it, L, xt)) break;
+      for (int i = 0; i < N; i++) v[i] += __shfl_xor_sync(mask, v[i], o);
   }
-  res.iters = L.it;
-  res.full = nfull;
-  res.status = L.status;
-  res.used64 = L.used64;
-  res.cost = cst;
-  res.cdata = cd;
+  __device__ __forceinline__ float sum1(float v) const {
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+  }
+  __device__ __forceinline__ int isum(int v) const {
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+  }
+  __device__ __forceinline__ bool all(bool p) const { return __all_sync(mask, p); }
+  __device__ __forceinline__ long long bcast(long long v) const {
+    return __shfl_sync(mask, v, lane & ~(G - 1));
+  }
+  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+};
+
+// Per-pixel shared scratch of one group: stage 2 node weights [nt][8], then
+// band buffers of nbs = G * ceil(n / G) slots each (slot i = sub + G s).
+// The stride between groups is congruent to G modulo 32 floats, so that the
+// groups of a warp, reading the same slot or node, hit different banks.
+__host__ __device__ __forceinline__ int band_slots(int n, int G) { return G * ((n + G - 1) / G); }
+__host__ __device__ __forceinline__ int pix_stride1(const KTables &t, int G) {
+  int f = 8 * band_slots(t.n1, G);
+  return f + ((G - f % 32) % 32 + 32) % 32;
+}
+__host__ __device__ __forceinline__ int pix_stride2(const KTables &t, int G) {
+  int f = t.nt * kScratchPerNode + 5 * band_slots(t.n2, G);
+  return f + ((G - f % 32) % 32 + 32) % 32;
+}
+// table-image floats a stage needs: stage 1 stops before the Planck grid
+__host__ __device__ __forceinline__ int image_floats(const KTables &t, int stage) {
+  return stage == 1 ? ((t.lay.off_planck + 3) & ~3) : t.lay.total;
 }
 
-// Stage-2 driver: a trial point is judged by the decrease-only evaluation
-// in increment form; the full evaluation runs only at accepted points and
-// writes the new state's normal equations and residuals in place.
-template <class St>
-__device__ __forceinline__ void lm_fit2(const St &S, PixCtx &pc, float (&x)[St::NX], int max_it,
-                                        float (&H)[St::NH], float (&g)[St::P], LMResult &res) {
-  constexpr int P = St::P, NX = St::NX;
-  const KConfig &c = *pc.c;
-  float cst = 0.f, cd = 0.f, xt[NX];
-  LMIter<P> L;
+// ------------------------------------------------------- pixel context --
+struct PixCtx {
+  const KTables *t;
+  const KConfig *c;
+  const float *img;       // shared-memory table image
+  float *node;            // this group's node scratch [nt][8] (stage 2)
+  const float4 *wvrow;    // this pixel's water-vapour row of the atmosphere table
+};
+
+// ------------------------------------------------------------ stage 1 ---
+template <int K, int G>
+struct Stage1 {
+  static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2;
+  // band buffers in shared memory, [8][nbs]: observed radiance, weight,
+  // and for the current and the trial state (index rc, rc ^ 1) the residual,
+  // the Planck factor B(lambda_b, T1) and 1 / (1 - S_b rho_b)
+  float *bb;
+  int nbs;
+  float psc;
+  float sf, sa, sT;
+
+  __device__ __forceinline__ float &Lo(int i) const { return bb[i]; }
+  __device__ __forceinline__ float &W(int i) const { return bb[nbs + i]; }
+  __device__ __forceinline__ float &R(int k, int i) const { return bb[(2 + k) * nbs + i]; }
+
+  // reduced variable a: fractions k != m in order, then alpha1, T1. These
+  // accessors select with compile-time indices (no local-memory indexing).
+  template <int A>
+  __device__ __forceinline__ static float rsel(const float (&v)[NX], int m) {
+    if constexpr (A >= K - 1) return v[A + 1];
+    else return A < m ? v[A] : v[A + 1];
+  }
+  template <int A>
+  __device__ __forceinline__ float lo_r(const KConfig &c, int m) const {
+    if constexpr (A >= K - 1) return c.lo1[A + 1];
+    else return A < m ? c.lo1[A] : c.lo1[A + 1];
+  }
+  template <int A>
+  __device__ __forceinline__ float hi_r(const KConfig &c, int m) const {
+    if constexpr (A >= K - 1) return c.hi1[A + 1];
+    else return A < m ? c.hi1[A] : c.hi1[A + 1];
+  }
+  template <int A>
+  __device__ __forceinline__ float sc_r(const KConfig &c, int m) const {
+    return 0.5f * (hi_r<A>(c, m) - lo_r<A>(c, m));
+  }
+  template <int A>
+  __device__ __forceinline__ static constexpr bool has_upper() { return A >= K - 1; }
+  __device__ __forceinline__ float scale(const KConfig &c, int i) const {
+    return 0.5f * (c.hi1[i] - c.lo1[i]);
+  }
+
+  __device__ __forceinline__ static int argmax_frac(const float (&x)[NX]) {
+    int m = 0;
+    float best = x[0];
 #pragma unroll
-  for (int a = 0; a < P; a++) L.act[a] = false;
-  S.eval(pc, x, H, g, cst, cd);
-  int nfull = 1;
+    for (int k = 1; k < K; k++)
+      if (x[k] > best) { m = k; best = x[k]; }
+    return m;
+  }
+
+  // model, reduced Jacobian, normal equations and cost at x (all lanes of
+  // the group get the totals); writes the residuals, Planck factors and
+  // solar denominators into set rn and returns the data-cost decrease from
+  // the state xo, whose set is 1 - rn. cd = unweighted data cost. The
+  // decrease is formed from residual differences, or, with inc (small
+  // steps, whose decrease the difference of two FP32 model values no longer
+  // resolves), in increment form: dM_b = dLs_b + tu_b (d alpha B_o + alpha
+  // dB_b) with
+  //   dLs_b = A_b drho_b / ((1 - S_b rho_t)(1 - S_b rho_o)),
+  //   dB_b = B_o expm1(-dx_b) / (1 - e^-x_t), dx_b = -(c2/lambda_b) dT / (T_t T_o),
+  // each increment formed from the exact parameter differences.
+  __device__ __forceinline__ void eval(const PixCtx &pc, const Grp<G> &gp, const float (&x)[NX],
+                                       int rn, float (&H)[NH], float (&g)[P], float &cst,
+                                       float &cd, float &drop, int &m, const float (&xo)[NX],
+                                       bool inc) const {
+    const KTables &t = *pc.t;
+    const KConfig &c = *pc.c;
+    m = argmax_frac(x);
+    float acc[NH + P + 3];
+#pragma unroll
+    for (int i = 0; i < NH + P + 3; i++) acc[i] = 0.f;
+    const float a1 = x[K], invT = 1.f / x[K + 1];
+    const float dTT = (x[K + 1] - xo[K + 1]) * invT / xo[K + 1];
+    const float dal = a1 - xo[K];
+    float dxs[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) dxs[k] = x[k] - xo[k];
+    const float *ro = bb + (3 - rn) * nbs, *bo = bb + (5 - rn) * nbs, *vo = bb + (7 - rn) * nbs;
+    float *rw = bb + (2 + rn) * nbs, *bw = bb + (4 + rn) * nbs, *vw = bb + (6 + rn) * nbs;
+#pragma unroll 2
+    for (int i = gp.sub; i < t.n1; i += G) {
+      const float wv = W(i);
+      if (wv > 0.f) {
+        int b = t.b1lo + i;
+        float4 q = __ldg(pc.wvrow + b);
+        float E[K];
+        float rho = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          E[k] = pc.img[t.lay.off_endm + k * t.nb + b];
+          rho = fmaf(x[k], E[k], rho);
+        }
+        float inv = __frcp_rn(1.f - q.z * rho);
+        float Ls = fmaf(q.x * rho, inv, q.y);
+        float xx = pc.img[t.lay.off_c2l + b] * invT;
+        float e = __expf(-xx);
+        float rom = __frcp_rn(1.f - e);
+        float B = pc.img[t.lay.off_c1l5 + b] * e * rom;
+        float dB = B * xx * invT * rom;
+        float r = Lo(i) - fmaf(a1 * q.w, B, Ls);
+        float rold = ro[i];
+        rw[i] = r;
+        bw[i] = B;
+        vw[i] = inv;
+        if (inc) {
+          float drho = 0.f;
+#pragma unroll
+          for (int k = 0; k < K; k++) drho = fmaf(dxs[k], E[k], drho);
+          const float dLs = q.x * drho * inv * vo[i];
+          const float Bo = bo[i];
+          const float dx = -pc.img[t.lay.off_c2l + b] * dTT;
+          const float dB = fabsf(dx) < 0.05f ? Bo * em1_small(-dx) * rom
+                                             : (fabsf(dx) < 1.f ? Bo * expm1f(-dx) * rom : B - Bo);
+          const float dM = fmaf(q.w, fmaf(dal, Bo, a1 * dB), dLs);
+          acc[NH + P + 2] = fmaf(wv * dM, 2.f * rold - dM, acc[NH + P + 2]);
+        } else {
+          acc[NH + P + 2] = fmaf(wv * (rold - r), rold + r, acc[NH + P + 2]);
+        }
+        float dL[K], dEm = 0.f;
+        const float qi2 = q.x * inv * inv * sf;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+          dL[k] = qi2 * E[k];
+          dEm = (k == m) ? dL[k] : dEm;
+        }
+        float J[P];
+#pragma unroll
+        for (int a = 0; a < K - 1; a++) J[a] = (a < m ? dL[a] : dL[a + 1]) - dEm;
+        J[K - 1] = q.w * B * sa;
+        J[K] = a1 * q.w * dB * sT;
+        float wr = wv * r;
+        acc[NH + P] = fmaf(wr, r, acc[NH + P]);
+        acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
+#pragma unroll
+        for (int a = 0; a < P; a++) {
+          acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
+          float wj = wv * J[a];
+#pragma unroll
+          for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
+        }
+      }
+    }
+    gp.sum(acc);
+#pragma unroll
+    for (int i = 0; i < NH; i++) H[i] = acc[i];
+#pragma unroll
+    for (int a = 0; a < P; a++) g[a] = acc[NH + a];
+    cd = acc[NH + P + 1];
+    cst = acc[NH + P];
+    drop = acc[NH + P + 2];
+    // weak Gaussian prior in z, pulled into the reduced basis (e_k - e_m)
+    float zr[NX], ppm = 0.f, rm = 0.f;
+#pragma unroll
+    for (int i = 0; i < NX; i++) {
+      zr[i] = c.hi1[i] > c.lo1[i] ? 2.f * (x[i] - c.lo1[i]) / (c.hi1[i] - c.lo1[i]) - 1.f : 0.f;
+      zr[i] -= c.pm1[i];
+      float ppi = psc * c.pp1[i];
+      cst += ppi * zr[i] * zr[i];
+      if (i < K && i == m) { ppm = ppi; rm = zr[i]; }
+    }
+#pragma unroll
+    for (int a = 0; a < K - 1; a++) {
+      float ppa = psc * (a < m ? c.pp1[a] : c.pp1[a + 1]);
+      float ra = a < m ? zr[a] : zr[a + 1];
+      g[a] -= ppa * ra - ppm * rm;
+      H[up<P>(a, a)] += ppa + ppm;
+#pragma unroll
+      for (int bb_ = a + 1; bb_ < K - 1; bb_++) H[up<P>(a, bb_)] += ppm;
+    }
+#pragma unroll
+    for (int a = K - 1; a < P; a++) {
+      g[a] -= psc * c.pp1[a + 1] * zr[a + 1];
+      H[up<P>(a, a)] += psc * c.pp1[a + 1];
+    }
+    gp.sync();
+  }
+
+  // prior(x_old) - prior(x_new), formed from differences of z
+  __device__ __forceinline__ float prior_drop(const KConfig &c, const float (&xo)[NX],
+                                              const float (&xn)[NX]) const {
+    float d = 0.f;
+#pragma unroll
+    for (int i = 0; i < NX; i++) {
+      if (c.hi1[i] > c.lo1[i] && c.pp1[i] > 0.f) {
+        float k = 2.f / (c.hi1[i] - c.lo1[i]);
+        float zo = k * (xo[i] - c.lo1[i]) - 1.f - c.pm1[i], zn = k * (xn[i] - c.lo1[i]) - 1.f - c.pm1[i];
+        d += psc * c.pp1[i] * (k * (xo[i] - xn[i])) * (zo + zn);
+      }
+    }
+    return d;
+  }
+
+  // x + step (z units, reduced basis) -> projected trial point
+  __device__ __forceinline__ void apply(const KConfig &c, const float (&x)[NX], const float (&dr)[P],
+                                        const signed char (&pd)[P], int m, float (&xt)[NX]) const {
+    float sum = 0.f;
+#pragma unroll
+    for (int a = 0; a < K - 1; a++) sum += dr[a];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      float d = 0.f;
+      bool at0 = false;   // pinned on its lower bound by the step solve
+      if (k < K - 1 && k < m) { d = dr[k < K - 1 ? k : 0]; at0 = pd[k < K - 1 ? k : 0] < 0; }
+      if (k > 0 && k > m) { d = dr[k > 0 ? k - 1 : 0]; at0 = pd[k > 0 ? k - 1 : 0] < 0; }
+      xt[k] = (k == m) ? x[k] - sf * sum : (at0 ? c.lo1[k] : x[k] + sf * d);
+    }
+#pragma unroll
+    for (int i = K; i < K + 2; i++) {
+      float v = x[i] + scale(c, i) * dr[i - 1];
+      if (pd[i - 1] < 0) v = c.lo1[i];
+      if (pd[i - 1] > 0) v = c.hi1[i];
+      xt[i] = fminf(fmaxf(v, c.lo1[i]), c.hi1[i]);
+    }
+    simplex_project(xt);
+  }
+
+  // Euclidean projection of the fractions onto the unit simplex (sort-based)
+  __device__ __forceinline__ static void simplex_project(float (&x)[NX]) {
+    float u[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) u[k] = x[k];
+#pragma unroll
+    for (int i = 1; i < K; i++)
+#pragma unroll
+      for (int j = i; j > 0; j--)
+        if (u[j] > u[j - 1]) {
+          float tmp = u[j];
+          u[j] = u[j - 1];
+          u[j - 1] = tmp;
+        }
+    float cs = 0.f, theta = 0.f;
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+      cs += u[j];
+      float th = (cs - 1.f) / (float)(j + 1);
+      if (u[j] - th > 0.f) theta = th;
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) x[k] = fmaxf(x[k] - theta, 0.f);
+  }
+};
+
+// ------------------------------------------------------------ stage 2 ---
+constexpr int kChunk2 = 7;   // stage-2 band slots per lane accumulated per node pass
+
+template <int G>
+struct Stage2 {
+  static constexpr int P = 6, NX = 6, NH = 21;
+  // band buffers in shared memory, [5][nbs]: y (radiance minus the fixed
+  // solar term), tau_up, weight, and the residuals of the current and of the
+  // trial state (index rc, rc ^ 1)
+  float *bb;
+  int nbs;
+  float psc;
+
+  __device__ __forceinline__ float &Y(int i) const { return bb[i]; }
+  __device__ __forceinline__ float &TU(int i) const { return bb[nbs + i]; }
+  __device__ __forceinline__ float &W(int i) const { return bb[2 * nbs + i]; }
+  __device__ __forceinline__ float &R(int k, int i) const { return bb[(3 + k) * nbs + i]; }
+
+  template <int A>
+  __device__ __forceinline__ static float rsel(const float (&v)[NX], int) { return v[A]; }
+  template <int A>
+  __device__ __forceinline__ float lo_r(const KConfig &c, int) const { return c.lo2[A]; }
+  template <int A>
+  __device__ __forceinline__ float hi_r(const KConfig &c, int) const { return c.hi2[A]; }
+  template <int A>
+  __device__ __forceinline__ float sc_r(const KConfig &c, int) const {
+    return 0.5f * (c.hi2[A] - c.lo2[A]);
+  }
+  template <int A>
+  __device__ __forceinline__ static constexpr bool has_upper() { return true; }
+  __device__ __forceinline__ float scale(const KConfig &c, int i) const {
+    return 0.5f * (c.hi2[i] - c.lo2[i]);
+  }
+
+  // Gaussian weight u_o = exp(-a_o^2/2), a = (T - mu)/sigma, of one node at
+  // the current state and its change du under the step to (mut, sgt): the
+  // exponent change is formed from the parameter differences,
+  //   a_t - a_o = -(dmu sigma_o + (T - mu_o) dsig) / (sigma_t sigma_o),
+  // and du = u_o expm1(-dq), so du is resolved relative to itself.
+  __device__ __forceinline__ static void node_step(float T, float mu, float isg, float mut, float isgt,
+                                                   float dmu, float dsg, float &u, float &du) {
+    const float ao = (T - mu) * isg, at = (T - mut) * isgt;
+    const float da = -fmaf((T - mu) * dsg, isg, dmu) * isgt;
+    const float dq = 0.5f * da * (at + ao);
+    u = expf(-0.5f * ao * ao);
+    du = fabsf(dq) < 0.5f ? u * expm1f(-dq) : expf(-0.5f * at * at) - u;
+  }
+
+  // Model, Jacobian (z-scaled), normal equations and cost at the trial
+  // state xt, with the residuals written into buffer rn; and the data-cost
+  // decrease from the current state x (residuals in buffer 1 - rn) in
+  // increment form: sum_b w_b dM_b (2 r_b - dM_b) with dM_b = tu_b (a_t
+  // dBm_b + (a_t - a) (Bm_b - dBm_b)), where dBm is the node sum of the
+  // mixture-weight increments, formed node by node from the exact parameter
+  // differences. The decrease is then accurate relative to itself, where
+  // the difference of two FP32 model values would be lost below their
+  // rounding. 7 FMA per band and node.
+  __device__ __forceinline__ void eval(const PixCtx &pc, const Grp<G> &gp, const float (&x)[NX],
+                                       const float (&xt)[NX], int rn, float (&H)[NH],
+                                       float (&g)[P], float &cst, float &cd, float &drop) const {
+    const KTables &t = *pc.t;
+    const KConfig &c = *pc.c;
+    const float mh = xt[0], sh = xt[1], ms = xt[2], ss = xt[3], eta = xt[4], al = xt[5];
+    const float eo = x[4], ao = x[5];
+    // node pass 1: weights at xt from the weights at x and their increments
+    float mom[10];   // U_h, M1_h, M2_h, U_s, M1_s, M2_s at xt; U_h, dU_h, U_s, dU_s at x
+#pragma unroll
+    for (int k = 0; k < 10; k++) mom[k] = 0.f;
+    {
+      const float ih = 1.f / x[1], iht = 1.f / sh, is = 1.f / x[3], ist = 1.f / ss;
+      const float dmh = mh - x[0], dsh = sh - x[1], dms = ms - x[2], dss = ss - x[3];
+      float4 *nd = reinterpret_cast<float4 *>(pc.node);
+      for (int j = gp.sub; j < t.nt; j += G) {
+        const float T = t.tglo + (float)j * t.tgstep;
+        float uh, duh, us, dus;
+        node_step(T, x[0], ih, mh, iht, dmh, dsh, uh, duh);
+        node_step(T, x[2], is, ms, ist, dms, dss, us, dus);
+        const float uth = uh + duh, uts = us + dus, dh = T - mh, ds = T - ms;
+        mom[0] += uth;
+        mom[1] += uth * dh;
+        mom[2] += uth * dh * dh;
+        mom[3] += uts;
+        mom[4] += uts * ds;
+        mom[5] += uts * ds * ds;
+        mom[6] += uh;
+        mom[7] += duh;
+        mom[8] += us;
+        mom[9] += dus;
+        nd[2 * j] = make_float4(uh, duh, us, dus);
+      }
+    }
+    gp.sum(mom);
+    {
+      // node pass 2: normalised weights, their moment-weighted forms and
+      // the increment of the mixture weight
+      const float rUh = 1.f / mom[0], rUs = 1.f / mom[3];
+      const float dbh = mom[1] * rUh, m2h = mom[2] * rUh, dbs = mom[4] * rUs, m2s = mom[5] * rUs;
+      const float rUho = 1.f / mom[6], rUso = 1.f / mom[8];
+      const float kh = mom[7] * rUho, ks = mom[9] * rUso;
+      float4 *nd = reinterpret_cast<float4 *>(pc.node);
+      for (int j = gp.sub; j < t.nt; j += G) {
+        const float T = t.tglo + (float)j * t.tgstep;
+        const float4 u = nd[2 * j];
+        const float dh = T - mh, ds = T - ms;
+        const float wh = (u.x + u.y) * rUh, ws = (u.z + u.w) * rUs;
+        const float dwh = (u.y - u.x * kh) * rUh, dws = (u.w - u.z * ks) * rUs;
+        const float dW = eta * dwh + (1.f - eta) * dws + (eta - eo) * (u.x * rUho - u.z * rUso);
+        nd[2 * j] = make_float4(wh, wh * (dh - dbh), wh * (dh * dh - m2h), ws);
+        nd[2 * j + 1] = make_float4(ws * (ds - dbs), ws * (ds * ds - m2s), dW, 0.f);
+      }
+    }
+    gp.sync();
+    float acc[NH + P + 3];
+#pragma unroll
+    for (int i = 0; i < NH + P + 3; i++) acc[i] = 0.f;
+    const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
+    const float ish3 = ish2 / sh, iss3 = iss2 / ss;
+    const float sc0 = scale(c, 0), sc1 = scale(c, 1), sc2 = scale(c, 2), sc3 = scale(c, 3);
+    const float sc4 = scale(c, 4), sc5 = scale(c, 5);
+    const float da_ = al - ao;
+    const float *ro = bb + (4 - rn) * nbs;
+    float *rw = bb + (3 + rn) * nbs;
+    const float4 *nd = reinterpret_cast<const float4 *>(pc.node);
+    const float *pl = pc.img + t.lay.off_planck + gp.sub;
+    const int ns = nbs / G;
 #pragma unroll 1
-  while (next_trial(S, c, x, H, g, 0, cst, max_it, L, xt)) {
-    const float drop = S.trial_drop(pc, x, xt) + S.prior_drop(c, x, xt);
-    const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
-    const bool accept = rho > 0.f;
-    damping_update(L, accept, rho);
-    if (accept) {
-      const float rel = drop / cst;   // relative to the cost before the step
+    for (int s0 = 0; s0 < ns; s0 += kChunk2) {
+      // moment sums over the grid nodes for kChunk2 band slots of this lane
+      float S[kChunk2][7];
 #pragma unroll
-      for (int i = 0; i < NX; i++) x[i] = xt[i];
-      S.eval(pc, x, H, g, cst, cd);
-      nfull++;
-      if (rel < c.tol_f) { L.status = PX_CONVERGED; break; }
+      for (int k = 0; k < kChunk2; k++)
+#pragma unroll
+        for (int q = 0; q < 7; q++) S[k][q] = 0.f;
+      const float *pls = pl + G * s0;
+#pragma unroll 2
+      for (int j = 0; j < t.nt; j++) {
+        const float4 A = nd[2 * j], B = nd[2 * j + 1];
+        const float *row = pls + j * t.lay.n2s;
+#pragma unroll
+        for (int k = 0; k < kChunk2; k++) {
+          const float Bv = (s0 + k < ns) ? row[G * k] : 0.f;
+          S[k][0] = fmaf(A.x, Bv, S[k][0]);
+          S[k][1] = fmaf(A.y, Bv, S[k][1]);
+          S[k][2] = fmaf(A.z, Bv, S[k][2]);
+          S[k][3] = fmaf(A.w, Bv, S[k][3]);
+          S[k][4] = fmaf(B.x, Bv, S[k][4]);
+          S[k][5] = fmaf(B.y, Bv, S[k][5]);
+          S[k][6] = fmaf(B.z, Bv, S[k][6]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kChunk2; k++) {
+        const int i = gp.sub + G * (s0 + k);
+        if (s0 + k < ns && i < t.n2) {
+          const float wv = W(i);
+          if (wv > 0.f) {
+            const float Bh = S[k][0], Bs = S[k][3];
+            const float Bm = eta * Bh + (1.f - eta) * Bs;
+            const float tuv = TU(i);
+            const float atu = al * tuv;
+            const float r = Y(i) - atu * Bm;
+            rw[i] = r;
+            const float dM = tuv * fmaf(al, S[k][6], da_ * (Bm - S[k][6]));
+            acc[NH + P + 2] = fmaf(wv * dM, 2.f * ro[i] - dM, acc[NH + P + 2]);
+            float J[6];
+            J[0] = atu * eta * S[k][1] * ish2 * sc0;
+            J[1] = atu * eta * S[k][2] * ish3 * sc1;
+            J[2] = atu * (1.f - eta) * S[k][4] * iss2 * sc2;
+            J[3] = atu * (1.f - eta) * S[k][5] * iss3 * sc3;
+            J[4] = atu * (Bh - Bs) * sc4;
+            J[5] = tuv * Bm * sc5;
+            const float wr = wv * r;
+            acc[NH + P] = fmaf(wr, r, acc[NH + P]);
+            acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
+#pragma unroll
+            for (int a = 0; a < P; a++) {
+              acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
+              const float wj = wv * J[a];
+#pragma unroll
+              for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
+            }
+          }
+        }
+      }
+    }
+    gp.sum(acc);
+#pragma unroll
+    for (int i = 0; i < NH; i++) H[i] = acc[i];
+#pragma unroll
+    for (int a = 0; a < P; a++) g[a] = acc[NH + a];
+    cst = acc[NH + P];
+    cd = acc[NH + P + 1];
+    drop = acc[NH + P + 2];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      float z = c.hi2[i] > c.lo2[i] ? 2.f * (xt[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
+      float pp = psc * c.pp2[i];
+      cst += pp * (z - c.pm2[i]) * (z - c.pm2[i]);
+      g[i] -= pp * (z - c.pm2[i]);
+      H[up<P>(i, i)] += pp;
+    }
+    gp.sync();
+  }
+
+  __device__ __forceinline__ float prior_drop(const KConfig &c, const float (&xo)[NX],
+                                              const float (&xn)[NX]) const {
+    float d = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      if (c.hi2[i] > c.lo2[i] && c.pp2[i] > 0.f) {
+        float k = 2.f / (c.hi2[i] - c.lo2[i]);
+        float zo = k * (xo[i] - c.lo2[i]) - 1.f - c.pm2[i], zn = k * (xn[i] - c.lo2[i]) - 1.f - c.pm2[i];
+        d += psc * c.pp2[i] * (k * (xo[i] - xn[i])) * (zo + zn);
+      }
+    }
+    return d;
+  }
+
+  __device__ __forceinline__ void apply(const KConfig &c, const float (&x)[NX], const float (&dr)[P],
+                                        const signed char (&pd)[P], int, float (&xt)[NX]) const {
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      float v = x[i] + scale(c, i) * dr[i];
+      if (pd[i] < 0) v = c.lo2[i];
+      if (pd[i] > 0) v = c.hi2[i];
+      xt[i] = fminf(fmaxf(v, c.lo2[i]), c.hi2[i]);
     }
   }
-  res.iters = L.it;
-  res.full = nfull;
-  res.status = L.status;
-  res.used64 = L.used64;
-  res.cost = cst;
-  res.cdata = cd;
-}
+};
 
 // -------------------------------------------- final covariance (FP64) ---
 // C = s2 (H_FF)^-1 over the free stage-2 variables (not on an outward-
@@ -1055,13 +972,13 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 
-// Stage the per-CTA table image into shared memory with 1D bulk copies
+// Stage the first nfloats of the per-CTA table image into shared memory with 1D bulk copies
 // completing on one mbarrier. The wait is bounded: on timeout the error flag
 // is set, the copies still in flight are waited for (bounded again) and the
 // CTA leaves (returns false).
-__device__ __forceinline__ bool stage_tables(const KTables &t, float *smem, unsigned long long *bar,
-                                             int *err) {
-  const unsigned bytes = (unsigned)t.lay.total * 4u;
+__device__ __forceinline__ bool stage_tables(const KTables &t, float *smem, int nfloats,
+                                             unsigned long long *bar, int *err) {
+  const unsigned bytes = (unsigned)nfloats * 4u;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1093,72 +1010,76 @@ __device__ __forceinline__ bool stage_tables(const KTables &t, float *smem, unsi
   return false;
 }
 
-// pixel-claim helper: lane 0 takes n pixels from a global counter
-__device__ __forceinline__ long long claim(unsigned long long *ctr, int lane, int n) {
+// pixel-claim helper: the group's first lane takes n pixels from a global
+// counter and shares the first index with the group
+template <int G>
+__device__ __forceinline__ long long claim(unsigned long long *ctr, const Grp<G> &gp, int n) {
   unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(ctr, (unsigned long long)n);
-  return (long long)__shfl_sync(kFull, base, 0);
+  if (gp.sub == 0) base = atomicAdd(ctr, (unsigned long long)n);
+  return gp.bcast((long long)base);
 }
 
 // stage-1 per-pixel setup: radiance, mask m(lambda) (saturation) x window,
 // weights and the prior scale (mean noise variance of the used bands)
-template <int K, int S1>
-__device__ __forceinline__ int setup1(Stage1<K, S1> &s1, const PixCtx &pc, const float *row) {
+template <int K, int G>
+__device__ __forceinline__ int setup1(Stage1<K, G> &s1, const PixCtx &pc, const Grp<G> &gp,
+                                      const float *row) {
   const KTables &t = *pc.t;
   const KConfig &c = *pc.c;
   float nv = 0.f;
   int nu = 0;
-#pragma unroll
-  for (int s = 0; s < S1; s++) {
-    int bi = pc.lane + 32 * s;
-    s1.Lobs[s] = 0.f;
-    s1.w[s] = 0.f;
-    if (bi < t.n1) {
-      int b = t.b1lo + bi;
+  for (int i = gp.sub; i < s1.nbs; i += G) {
+    float Lv = 0.f, wv = 0.f;
+    if (i < t.n1) {
+      int b = t.b1lo + i;
       float L = __ldg(row + b);
       bool ok = pc.img[t.lay.off_win1 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
       float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
-      s1.Lobs[s] = L;
-      s1.w[s] = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
+      Lv = L;
+      wv = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
       if (ok) { nv += var; nu++; }
     }
+    s1.Lo(i) = Lv;
+    s1.W(i) = wv;
+#pragma unroll
+    for (int k = 2; k < 8; k++) s1.bb[k * s1.nbs + i] = 0.f;
   }
-  nv = warp_sum1(nv);
-  nu = __reduce_add_sync(kFull, nu);
+  nv = gp.sum1(nv);
+  nu = gp.isum(nu);
   s1.psc = c.weighted ? 1.f : nv / (float)max(nu, 1);
   s1.sf = 0.5f * (c.hi1[0] - c.lo1[0]);
   s1.sa = 0.5f * (c.hi1[K] - c.lo1[K]);
   s1.sT = 0.5f * (c.hi1[K + 1] - c.lo1[K + 1]);
+  gp.sync();
   return nu;
 }
 
 // stage-2 band count (mask x window) without building the stage state
-__device__ __forceinline__ int count2(const PixCtx &pc, const float *row) {
+template <int G>
+__device__ __forceinline__ int count2(const PixCtx &pc, const Grp<G> &gp, const float *row) {
   const KTables &t = *pc.t;
   int nu = 0;
-  for (int bi = pc.lane; bi < t.n2; bi += 32) {
+  for (int bi = gp.sub; bi < t.n2; bi += G) {
     int b = t.b2lo + bi;
     float L = __ldg(row + b);
     nu += (pc.img[t.lay.off_win2 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b))) ? 1 : 0;
   }
-  return __reduce_add_sync(kFull, nu);
+  return gp.isum(nu);
 }
 
 // stage-2 per-pixel setup: y = L - Ls(x_surf) (solar term fixed, Eq. solar),
 // tau_up, weights, prior scale
-template <int K, int S2>
-__device__ __forceinline__ int setup2(Stage2<S2> &s2, const PixCtx &pc, const float *row,
-                                      const float (&xs)[K]) {
+template <int K, int G>
+__device__ __forceinline__ int setup2(Stage2<G> &s2, const PixCtx &pc, const Grp<G> &gp,
+                                      const float *row, const float (&xs)[K]) {
   const KTables &t = *pc.t;
   const KConfig &c = *pc.c;
   float nv = 0.f;
   int nu = 0;
-#pragma unroll
-  for (int s = 0; s < S2; s++) {
-    int bi = pc.lane + 32 * s;
+  for (int i = gp.sub; i < s2.nbs; i += G) {
     float yv = 0.f, tv = 0.f, wv = 0.f;
-    if (bi < t.n2) {
-      int b = t.b2lo + bi;
+    if (i < t.n2) {
+      int b = t.b2lo + i;
       float L = __ldg(row + b);
       bool ok = pc.img[t.lay.off_win2 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
       float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
@@ -1171,26 +1092,17 @@ __device__ __forceinline__ int setup2(Stage2<S2> &s2, const PixCtx &pc, const fl
       wv = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
       if (ok) { nv += var; nu++; }
     }
-    s2.yb(bi) = yv;
-    s2.tub(bi) = tv;
-    s2.wb(bi) = wv;
-    s2.rb(bi) = yv;
+    s2.Y(i) = yv;
+    s2.TU(i) = tv;
+    s2.W(i) = wv;
+    s2.R(0, i) = yv;
+    s2.R(1, i) = yv;
   }
-  __syncwarp();
-  nv = warp_sum1(nv);
-  nu = __reduce_add_sync(kFull, nu);
+  nv = gp.sum1(nv);
+  nu = gp.isum(nu);
   s2.psc = c.weighted ? 1.f : nv / (float)max(nu, 1);
+  gp.sync();
   return nu;
-}
-
-__device__ __forceinline__ void flush_stats(unsigned long long *cstat, const unsigned long long *mine,
-                                            unsigned long long *gstats, int lane) {
-  if (lane == 0)
-    for (int i = 0; i < ST_COUNT; i++)
-      if (mine[i]) atomicAdd(&cstat[i], mine[i]);
-  __syncthreads();
-  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
-    if (cstat[i]) atomicAdd(gstats + i, cstat[i]);
 }
 
 // Where pixel pix reads its inputs and writes its outputs: the single scene
@@ -1245,105 +1157,126 @@ __device__ __forceinline__ PixRef resolve(const LMLaunch &p, long long pix, int 
 constexpr int kFitted = 256;   // scratch flag: pixel goes on to stage 2
 constexpr int kS2Hand = 32;    // floats handed from stage 2 to finalize per pixel
 
+// value k of a compile-time-indexed list, chosen by a runtime k (select
+// chain: no local-memory indexing)
+template <int N>
+__device__ __forceinline__ float pick(const float (&v)[N], int k) {
+  float r = v[0];
+#pragma unroll
+  for (int i = 1; i < N; i++) r = (k == i) ? v[i] : r;
+  return r;
+}
+
+// Each round of the two stage kernels: groups without a pixel take the next
+// one (and settle at once the pixels that are not fitted); then every group
+// with a pixel runs one LM step: the damped step from the current normal
+// equations, the evaluation at the trial point, and its acceptance. The
+// evaluation is the same code at the same point of the round for every
+// group, so the groups of a warp evaluate in step. A warp leaves when all
+// its groups have run out of pixels.
+
 // ---- stage 1: checks, HFDI gate, stage-1 fit -> scratch
-template <int K, int S1, int WPB, int MINB>
-__global__ void __launch_bounds__(WPB * 32, MINB) lm_stage1_kernel(const __grid_constant__ LMLaunch p) {
+template <int K, int G, int MAXW>
+__global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_constant__ LMLaunch p) {
+  constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2;
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ unsigned long long cstat[ST_COUNT];
   const KTables &t = p.t;
   const KConfig &c = p.c;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
-  if (!stage_tables(t, smem, &bar, p.w.err)) return;
+  const int img_f = image_floats(t, 1);
+  if (!stage_tables(t, smem, img_f, &bar, p.w.err)) return;
+  const Grp<G> gp(lane);
   PixCtx pc;
   pc.t = &t;
   pc.c = &c;
   pc.img = smem;
-  pc.wsc = smem + t.lay.total + warp * warp_scratch_floats(t);
-  pc.lane = lane;
+  pc.node = nullptr;
+  pc.wvrow = t.wvtab;
+  Stage1<K, G> S;
+  S.nbs = band_slots(t.n1, G);
+  S.bb = smem + img_f + (threadIdx.x / G) * pix_stride1(t, G);
   const int NSx = K + 8;
-  unsigned long long mine[ST_COUNT];
-#pragma unroll
-  for (int i = 0; i < ST_COUNT; i++) mine[i] = 0ull;
+  const long long n = p.s.n_pix;
   const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
+  long long next = 0, end = 0, pix = 0, opix = 0;
+  uint16_t *iters_out = nullptr;
+  bool active = false, done = false, first = false;
+  float x[NX], xt[NX], H[NH], g[P], cst = 0.f;
+  int m = 0, rc = 0, nfull = 0, status = 0;
+  LMIter<P> L;
   for (;;) {
-    const long long base = claim(p.w.counter, lane, nclaim);
-    if (base >= p.s.n_pix) break;
-    for (int ci = 0; ci < nclaim; ci++) {
-      const long long pix = base + ci;
-      if (pix >= p.s.n_pix) break;
+    // ---- take pixels until one is to be fitted
+    while (!active && !done) {
+      if (next >= end) {
+        const long long b = claim(p.w.counter, gp, nclaim);
+        if (b >= n) { done = true; break; }
+        next = b;
+        end = min(b + (long long)nclaim, n);
+      }
+      pix = next++;
       const PixRef ref = resolve(p, pix, K);
       const float *row = ref.row;
       const int wvb = ref.wv;
       const bool wv_ok = wvb < t.nwv;   // an out-of-range bin is an invalid input
       pc.wvrow = t.wvtab + (size_t)(wv_ok ? wvb : 0) * t.nb;
       bool fin = true;
-      for (int b = lane; b < t.nb; b += 32) fin = fin && isfinite(__ldg(row + b));
-      fin = __all_sync(kFull, fin) && wv_ok;
+      for (int b = gp.sub; b < t.nb; b += G) fin = fin && isfinite(__ldg(row + b));
+      fin = gp.all(fin) && wv_ok;
       const float Lh = __ldg(row + t.bh), Ll = __ldg(row + t.bl);
       float hf = (Lh - Ll) / (Lh + Ll);
-      int status = 0, it1 = 0;
-      bool fitted = false;
-      float x1[K + 2];
+      status = 0;
+      bool fit = false;
       if (!fin) {
         status = PX_NONFINITE;
         hf = __int_as_float(0x7fc00000);
       } else if (p.s.gate && !(hf >= c.hfdi_thresh)) {
         status = PX_NOT_CANDIDATE;
       } else {
-        Stage1<K, S1> s1;
-        const int n1u = setup1(s1, pc, row);
-        const int n2u = count2(pc, row);
-        if (n1u <= K + 2 || n2u <= 6) {
-          status = PX_ALL_MASKED;
-        } else {
-          const float *ini = ref.init;
-          if (ini) {
-#pragma unroll
-            for (int i = 0; i < K + 2; i++) x1[i] = ini[i];
-            Stage1<K, S1>::simplex_project(x1);
-#pragma unroll
-            for (int i = K; i < K + 2; i++) x1[i] = fminf(fmaxf(x1[i], c.lo1[i]), c.hi1[i]);
-          } else {
-#pragma unroll
-            for (int k = 0; k < K; k++) x1[k] = 1.f / (float)K;
-            x1[K] = c.init_alpha1;
-            x1[K + 1] = c.init_T1;
-          }
-          float H1[Stage1<K, S1>::NH], g1[K + 1];
-          int m1;
-          LMResult r1;
-          lm_fit(s1, pc, x1, c.max_it1, H1, g1, m1, r1);
-          it1 = r1.iters;
-          if (r1.status == PX_MAXITER) status |= PX_F_S1_MAXITER;
-          if (r1.used64) status |= PX_F_FP64;
-          mine[ST_BAND1] += (unsigned long long)r1.full * (unsigned long long)t.n1;
-          mine[ST_IT1] += it1;
-          fitted = true;
-        }
+        const int n1u = setup1(S, pc, gp, row);
+        const int n2u = count2(pc, gp, row);
+        if (n1u <= K + 2 || n2u <= 6) status = PX_ALL_MASKED;
+        else fit = true;
       }
-      // hand-over to stage 2, or the final outputs of a pixel that is not fitted
       const KOut &o = ref.o;
       const long long op = ref.opix;
-      if (lane == 0) {
-        p.w.s1meta[pix] = status | (fitted ? kFitted : 0);
-        if (o.hfdi) o.hfdi[op] = hf;
-        if (o.iters) o.iters[2 * op] = (uint16_t)it1;
-      }
-      if (fitted) {
-        if (lane < K + 2) {
-          float v = x1[0];
+      if (gp.sub == 0 && o.hfdi) o.hfdi[op] = hf;
+      if (fit) {
+        const float *ini = ref.init;
+        if (ini) {
 #pragma unroll
-          for (int k = 0; k < K + 2; k++) v = (k == lane) ? x1[k] : v;
-          p.w.s1x[pix * (K + 2) + lane] = v;
+          for (int i = 0; i < NX; i++) x[i] = ini[i];
+          Stage1<K, G>::simplex_project(x);
+#pragma unroll
+          for (int i = K; i < NX; i++) x[i] = fminf(fmaxf(x[i], c.lo1[i]), c.hi1[i]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < K; k++) x[k] = 1.f / (float)K;
+          x[K] = c.init_alpha1;
+          x[K + 1] = c.init_T1;
         }
+#pragma unroll
+        for (int i = 0; i < NX; i++) xt[i] = x[i];
+        L = LMIter<P>();
+#pragma unroll
+        for (int a = 0; a < P; a++) L.act[a] = false;
+        first = true;
+        rc = 0;
+        nfull = 0;
+        opix = op;
+        iters_out = o.iters;
+        active = true;
       } else {
+        // settled without a fit: the outputs of the pixel are final here
         const float nan = __int_as_float(0x7fc00000);
         if (o.state)
-          for (int i = lane; i < NSx; i += 32) o.state[op * NSx + i] = nan;
-        if (o.cov && lane < 21) o.cov[op * 21 + lane] = nan;
-        if (lane == 0) {
+          for (int i = gp.sub; i < NSx; i += G) o.state[op * NSx + i] = nan;
+        if (o.cov)
+          for (int i = gp.sub; i < 21; i += G) o.cov[op * 21 + i] = nan;
+        if (gp.sub == 0) {
+          p.w.s1meta[pix] = status;
           if (o.ET) o.ET[op] = nan;
           if (o.sdT) o.sdT[op] = nan;
           if (o.alpha) o.alpha[op] = nan;
@@ -1351,131 +1284,227 @@ __global__ void __launch_bounds__(WPB * 32, MINB) lm_stage1_kernel(const __grid_
           if (o.cost) o.cost[op] = nan;
           if (o.rms) o.rms[op] = nan;
           if (o.status) o.status[op] = (uint8_t)status;
-          if (o.iters) o.iters[2 * op + 1] = 0;
+          if (o.iters) {
+            o.iters[2 * op] = 0;
+            o.iters[2 * op + 1] = 0;
+          }
+          atomicAdd(&cstat[ST_STATUS0 + (status & 7)], 1ull);
+          atomicAdd(&cstat[ST_NPIX], 1ull);
         }
-#pragma unroll
-        for (int k = 0; k < 8; k++) mine[ST_STATUS0 + k] += ((status & 7) == k) ? 1ull : 0ull;
       }
-      mine[ST_NPIX] += 1;
+    }
+    if (__all_sync(kFull, done)) break;
+    if (!active) continue;
+    // ---- one LM step of this group's pixel
+    bool go = first || next_trial(S, c, x, H, g, m, cst, c.max_it1, L, xt);
+    if (go) {
+      float Ht[NH], gt[P], ct, cdt, drop;
+      int mt;
+      // small steps: decrease in increment form (FP32 resolution)
+      const bool inc = !first && L.pred < kIncBelow * cst;
+      S.eval(pc, gp, xt, rc ^ 1, Ht, gt, ct, cdt, drop, mt, x, inc);
+      nfull++;
+      bool accept = first;
+      if (!first) {
+        drop += S.prior_drop(c, x, xt);
+        const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
+        accept = rho > 0.f;
+        damping_update(L, accept, rho);
+        if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
+      }
+      if (accept) {
+#pragma unroll
+        for (int i = 0; i < NX; i++) x[i] = xt[i];
+#pragma unroll
+        for (int i = 0; i < NH; i++) H[i] = Ht[i];
+#pragma unroll
+        for (int a = 0; a < P; a++) g[a] = gt[a];
+        cst = ct;
+        m = mt;
+        rc ^= 1;
+      }
+      first = false;
+    }
+    if (!go) {
+      // ---- stage 1 done: hand the state to stage 2
+      if (L.status == PX_MAXITER) status |= PX_F_S1_MAXITER;
+      if (L.used64) status |= PX_F_FP64;
+      if (gp.sub < NX) p.w.s1x[pix * NX + gp.sub] = pick(x, gp.sub);
+      if (gp.sub == 0) {
+        p.w.s1meta[pix] = status | kFitted;
+        if (iters_out) iters_out[2 * opix] = (uint16_t)L.it;
+        atomicAdd(&cstat[ST_BAND1], (unsigned long long)nfull * (unsigned long long)t.n1);
+        atomicAdd(&cstat[ST_IT1], (unsigned long long)L.it);
+        atomicAdd(&cstat[ST_NPIX], 1ull);
+      }
+      active = false;
     }
   }
-  flush_stats(cstat, mine, p.w.stats, lane);
+  __syncthreads();
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
+    if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
 }
 
-// ---- stage 2: mixture fit from the stage-1 hand-over, covariance, outputs
-template <int K, int S2, int WPB>
-__global__ void __launch_bounds__(WPB * 32, 1) lm_stage2_kernel(const __grid_constant__ LMLaunch p) {
+// ---- stage 2: mixture fit from the stage-1 hand-over -> finalize scratch
+template <int K, int G, int MAXW>
+__global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_constant__ LMLaunch p) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ unsigned long long cstat[ST_COUNT];
   const KTables &t = p.t;
   const KConfig &c = p.c;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
-  if (!stage_tables(t, smem, &bar, p.w.err)) return;
+  const int img_f = image_floats(t, 2);
+  if (!stage_tables(t, smem, img_f, &bar, p.w.err)) return;
+  const Grp<G> gp(lane);
+  float *mine = smem + img_f + (threadIdx.x / G) * pix_stride2(t, G);
   PixCtx pc;
   pc.t = &t;
   pc.c = &c;
   pc.img = smem;
-  pc.wsc = smem + t.lay.total + warp * warp_scratch_floats(t);
-  pc.lane = lane;
-  unsigned long long mine[ST_COUNT];
-#pragma unroll
-  for (int i = 0; i < ST_COUNT; i++) mine[i] = 0ull;
+  pc.node = mine;
+  pc.wvrow = t.wvtab;
+  Stage2<G> S;
+  S.nbs = band_slots(t.n2, G);
+  S.bb = mine + t.nt * kScratchPerNode;
+  const long long n = p.s.n_pix;
   const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
+  long long next = 0, end = 0, pix = 0;
+  bool active = false, done = false, first = false, alt = false;
+  float x[6], xt[6], xa[6], H[21], g[6], cst = 0.f, cd = 0.f;
+  int rc = 0, nfull = 0, status = 0, n2u = 0;
+  LMIter<6> L;
   for (;;) {
-    const long long base = claim(p.w.counter + 1, lane, nclaim);
-    if (base >= p.s.n_pix) break;
-    for (int ci = 0; ci < nclaim; ci++) {
-      const long long pix = base + ci;
-      if (pix >= p.s.n_pix) break;
+    while (!active && !done) {
+      if (next >= end) {
+        const long long b = claim(p.w.counter + 1, gp, nclaim);
+        if (b >= n) { done = true; break; }
+        next = b;
+        end = min(b + (long long)nclaim, n);
+      }
+      pix = next++;
       const int meta = p.w.s1meta[pix];
       if (!(meta & kFitted)) continue;
-      int status = meta & 0xff;
+      status = meta & 0xff;
       const PixRef ref = resolve(p, pix, K);
-      const float *row = ref.row;
       pc.wvrow = t.wvtab + (size_t)ref.wv * t.nb;
-      pc.node_evals = 0;
-      pc.trial_nodes = 0;
       float x1[K + 2];
 #pragma unroll
       for (int i = 0; i < K + 2; i++) x1[i] = p.w.s1x[pix * (K + 2) + i];
       float xs[K];
 #pragma unroll
       for (int k = 0; k < K; k++) xs[k] = x1[k];
-      Stage2<S2> s2;
-      s2.bb = pc.wsc + t.nt * kScratchPerNode;
-      const int n2u = setup2<K, S2>(s2, pc, row, xs);
-      float x2[6];
+      n2u = setup2<K>(S, pc, gp, ref.row, xs);
+      // the start derived from the stage-1 result
+      const float T1 = x1[K + 1];
+      x[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
+      x[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
+      x[1] = fminf(fmaxf(c.init_sigma, c.lo2[1]), c.hi2[1]);
+      x[3] = fminf(fmaxf(c.init_sigma, c.lo2[3]), c.hi2[3]);
+      x[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
+      const float e = x[0] > x[2] ? (T1 - x[2]) / (x[0] - x[2]) : 0.5f;
+      x[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
+      alt = false;
       const float *ini = ref.init;
       if (ini) {
+        float xg[6];
 #pragma unroll
-        for (int i = 0; i < 6; i++) x2[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
-      }
-      if (!ini || p.s.init_best) {
-        float xd[6];
-        float T1 = x1[K + 1];
-        xd[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
-        xd[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
-        xd[1] = fminf(fmaxf(c.init_sigma, c.lo2[1]), c.hi2[1]);
-        xd[3] = fminf(fmaxf(c.init_sigma, c.lo2[3]), c.hi2[3]);
-        xd[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
-        float e = xd[0] > xd[2] ? (T1 - xd[2]) / (xd[0] - xd[2]) : 0.5f;
-        xd[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
-        bool take_d = !ini;
-        if (ini) {
-          // cost(xd) - cost(x2) from the data-term decreases of both starts
-          // against the thermal-free model (residuals y), plus the prior
-          float z2[6], zd[6];
+        for (int i = 0; i < 6; i++) xg[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
+        if (p.s.init_best) {
+          // learned start: after the derived start, the proposal is tried
+          // as a step and kept if its cost is lower
 #pragma unroll
-          for (int i = 0; i < 6; i++) {
-            z2[i] = x2[i];
-            zd[i] = xd[i];
-          }
-          z2[5] = 0.f;
-          zd[5] = 0.f;
-          const float Dp = s2.trial_drop(pc, z2, x2, true), Dd = s2.trial_drop(pc, zd, xd, true);
-          take_d = !(Dp - Dd + s2.prior_drop(c, xd, x2) > 0.f);
-        }
-        if (take_d) {
+          for (int i = 0; i < 6; i++) xa[i] = xg[i];
+          alt = true;
+        } else {
 #pragma unroll
-          for (int i = 0; i < 6; i++) x2[i] = xd[i];
+          for (int i = 0; i < 6; i++) x[i] = xg[i];
         }
       }
-      float H2[21], g2[6];
-      LMResult r2;
-      lm_fit2(s2, pc, x2, c.max_it2, H2, g2, r2);
-      if (r2.used64) status |= PX_F_FP64;
-      status |= r2.status;
-      mine[ST_IT2] += r2.iters;
-      mine[ST_BAND2] += (unsigned long long)r2.full * (unsigned long long)t.n2;
-      mine[ST_NODEBAND2] += (unsigned long long)pc.node_evals * (unsigned long long)t.n2;
-      mine[ST_TRIAL2] += (unsigned long long)r2.iters * (unsigned long long)t.n2;
-      mine[ST_TRIALNODE2] += (unsigned long long)pc.trial_nodes * (unsigned long long)t.n2;
-      // hand the final state and normal equations to the finalize kernel
-      float* hand = p.w.s2x + pix * kS2Hand;
-      {
-        float v = 0.f;
 #pragma unroll
-        for (int k = 0; k < 6; k++) v = (lane == k) ? x2[k] : v;
+      for (int i = 0; i < 6; i++) xt[i] = x[i];
+      L = LMIter<6>();
 #pragma unroll
-        for (int k = 0; k < 21; k++) v = (lane == 6 + k) ? H2[k] : v;
-        v = (lane == 27) ? r2.cost : v;
-        v = (lane == 28) ? r2.cdata : v;
-        v = (lane == 29) ? __int_as_float(n2u) : v;
-        v = (lane == 30) ? __int_as_float(status | (r2.iters << 8)) : v;
-        v = (lane == 31) ? s2.psc : v;
-        hand[lane] = v;
-      }
-      if (lane < 6) {
-        float v = g2[0];
+      for (int a = 0; a < 6; a++) L.act[a] = false;
+      first = true;
+      rc = 0;
+      nfull = 0;
+      active = true;
+    }
+    if (__all_sync(kFull, done)) break;
+    if (!active) continue;
+    bool go = true, probe = false;
+    if (!first) {
+      if (alt) {
 #pragma unroll
-        for (int k = 0; k < 6; k++) v = (lane == k) ? g2[k] : v;
-        p.w.s2g[pix * 6 + lane] = v;
+        for (int i = 0; i < 6; i++) xt[i] = xa[i];
+        alt = false;
+        probe = true;
+      } else {
+        go = next_trial(S, c, x, H, g, 0, cst, c.max_it2, L, xt);
       }
     }
+    if (go) {
+      float Ht[21], gt[6], ct, cdt, drop;
+      S.eval(pc, gp, x, xt, rc ^ 1, Ht, gt, ct, cdt, drop);
+      nfull++;
+      bool accept = first;
+      if (!first) {
+        drop += S.prior_drop(c, x, xt);
+        if (probe) {
+          accept = drop > 0.f;
+        } else {
+          const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
+          accept = rho > 0.f;
+          damping_update(L, accept, rho);
+          if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
+        }
+      }
+      if (accept) {
+#pragma unroll
+        for (int i = 0; i < 6; i++) x[i] = xt[i];
+#pragma unroll
+        for (int i = 0; i < 21; i++) H[i] = Ht[i];
+#pragma unroll
+        for (int a = 0; a < 6; a++) g[a] = gt[a];
+        cst = ct;
+        cd = cdt;
+        rc ^= 1;
+      }
+      first = false;
+    }
+    if (!go) {
+      // ---- hand the final state and normal equations to the finalize kernel
+      if (L.used64) status |= PX_F_FP64;
+      status |= L.status;
+      float* hand = p.w.s2x + pix * kS2Hand;
+#pragma unroll
+      for (int k = 0; k < 32; k++) {
+        if ((k & (G - 1)) != gp.sub) continue;
+        float v;
+        if (k < 6) v = x[k];
+        else if (k < 27) v = H[k - 6];
+        else if (k == 27) v = cst;
+        else if (k == 28) v = cd;
+        else if (k == 29) v = __int_as_float(n2u);
+        else if (k == 30) v = __int_as_float(status | (L.it << 8));
+        else v = S.psc;
+        hand[k] = v;
+      }
+      if (gp.sub < 6) p.w.s2g[pix * 6 + gp.sub] = pick(g, gp.sub);
+      if (gp.sub == 0) {
+        atomicAdd(&cstat[ST_IT2], (unsigned long long)L.it);
+        atomicAdd(&cstat[ST_BAND2], (unsigned long long)nfull * (unsigned long long)t.n2);
+        atomicAdd(&cstat[ST_NODEBAND2],
+                  (unsigned long long)nfull * (unsigned long long)t.nt * (unsigned long long)t.n2);
+      }
+      active = false;
+    }
   }
-  flush_stats(cstat, mine, p.w.stats, lane);
+  __syncthreads();
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
+    if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
 }
 
 // ---- finalize: moment matching (Sec. 2.3), FP64 Laplace covariance,
@@ -1612,40 +1641,43 @@ __global__ void merge_fallback_kernel(const long long *idx, const float *cost_fi
   }
 }
 
-// ---- one evaluation of a stage's normal equations per state (test hook)
-template <int K, int S1, int S2, int WPB>
-__global__ void __launch_bounds__(WPB * 32, 1) normal_eq_kernel(const __grid_constant__ LMLaunch p,
-                                                                int stage, const float *states,
-                                                                float *Hout, float *gout,
-                                                                float *cost_out) {
+// ---- one evaluation of a stage's normal equations per state (test hook),
+// through the same evaluation code as the fit, one pixel per group
+template <int K, int G, int MAXW>
+__global__ void __launch_bounds__(MAXW * 32, 1) normal_eq_kernel(const __grid_constant__ LMLaunch p,
+                                                                 int stage, const float *states,
+                                                                 float *Hout, float *gout,
+                                                                 float *cost_out) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) unsigned long long bar;
   const KTables &t = p.t;
   const KConfig &c = p.c;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (!stage_tables(t, smem, &bar, p.w.err)) return;
+  const int lane = threadIdx.x & 31;
+  const int img_f = image_floats(t, stage);
+  if (!stage_tables(t, smem, img_f, &bar, p.w.err)) return;
+  const Grp<G> gp(lane);
+  const int gid = threadIdx.x / G, groups = blockDim.x / G;
   PixCtx pc;
   pc.t = &t;
   pc.c = &c;
   pc.img = smem;
-  pc.wsc = smem + t.lay.total + warp * warp_scratch_floats(t);
-  pc.lane = lane;
-  const long long nw = (long long)gridDim.x * WPB;
-  for (long long pix = (long long)blockIdx.x * WPB + warp; pix < p.s.n_pix; pix += nw) {
+  const long long ng = (long long)gridDim.x * groups;
+  for (long long pix = (long long)blockIdx.x * groups + gid; pix < p.s.n_pix; pix += ng) {
     const float *row = p.s.rad + pix * t.nb;
     pc.wvrow = t.wvtab + (size_t)min((int)p.s.wv[pix], t.nwv - 1) * t.nb;
     if (stage == 1) {
-      Stage1<K, S1> s1;
-      setup1(s1, pc, row);
-      constexpr int P = K + 1, NS = S1;
-      float x[K + 2], H[P * (P + 1) / 2], g[P], cst, cd, dcd, r0[NS], r1[NS];
+      constexpr int P = K + 1;
+      Stage1<K, G> s1;
+      s1.nbs = band_slots(t.n1, G);
+      s1.bb = smem + img_f + gid * pix_stride1(t, G);
+      pc.node = nullptr;
+      setup1(s1, pc, gp, row);
+      float x[K + 2], H[P * (P + 1) / 2], g[P], cst, cd, drop;
       int m;
 #pragma unroll
       for (int i = 0; i < K + 2; i++) x[i] = states[pix * (K + 2) + i];
-#pragma unroll
-      for (int i = 0; i < NS; i++) r0[i] = 0.f;
-      s1.eval(pc, x, H, g, cst, cd, m, r0, r1, dcd);
-      if (lane == 0) {
+      s1.eval(pc, gp, x, 1, H, g, cst, cd, drop, m, x, false);
+      if (gp.sub == 0) {
         for (int a = 0; a < P; a++) {
           gout[pix * P + a] = g[a];
           for (int b = 0; b < P; b++) Hout[pix * P * P + a * P + b] = H[up<P>(a, b)];
@@ -1653,17 +1685,20 @@ __global__ void __launch_bounds__(WPB * 32, 1) normal_eq_kernel(const __grid_con
         cost_out[pix] = cst;
       }
     } else {
+      float *mine = smem + img_f + gid * pix_stride2(t, G);
+      pc.node = mine;
+      Stage2<G> s2;
+      s2.nbs = band_slots(t.n2, G);
+      s2.bb = mine + t.nt * kScratchPerNode;
       float xs[K], x[6];
 #pragma unroll
       for (int k = 0; k < K; k++) xs[k] = states[pix * (K + 6) + k];
 #pragma unroll
       for (int i = 0; i < 6; i++) x[i] = states[pix * (K + 6) + K + i];
-      Stage2<S2> s2;
-      s2.bb = pc.wsc + t.nt * kScratchPerNode;
-      setup2<K, S2>(s2, pc, row, xs);
-      float H[21], g[6], cst, cd;
-      s2.eval(pc, x, H, g, cst, cd);
-      if (lane == 0) {
+      setup2<K>(s2, pc, gp, row, xs);
+      float H[21], g[6], cst, cd, drop;
+      s2.eval(pc, gp, x, x, 1, H, g, cst, cd, drop);
+      if (gp.sub == 0) {
         for (int a = 0; a < 6; a++) {
           gout[pix * 6 + a] = g[a];
           for (int b = 0; b < 6; b++) Hout[pix * 36 + a * 6 + b] = H[up<6>(a, b)];
@@ -1674,50 +1709,76 @@ __global__ void __launch_bounds__(WPB * 32, 1) normal_eq_kernel(const __grid_con
   }
 }
 
-constexpr int kWPB = 8;
+// Launch shapes. A stage kernel runs as one persistent CTA per SM of up to
+// MAXW warps (the register budget follows from MAXW: 65536 / (32 MAXW)),
+// with G lanes per pixel; the warps actually launched are as many as the
+// shared memory of the table image plus one scratch block per pixel allows.
+struct Shape { int G, maxw; };
+constexpr Shape kShape1[3] = {{16, 12}, {8, 12}, {32, 8}};
+// stage 2 runs one pixel per warp: at two or four pixels per warp its longer
+// node passes per lane cost more than the shared solve saves (measured)
+constexpr Shape kShape2 = {32, 8};
 
-template <int WPB, class Kern>
+size_t stage_smem(const KTables &t, int stage, int G, int wpb) {
+  const int per = stage == 1 ? pix_stride1(t, G) : pix_stride2(t, G);
+  return ((size_t)image_floats(t, stage) + (size_t)wpb * (32 / G) * per) * 4;
+}
+
+int fit_warps(const KTables &t, int stage, int G, int maxw) {
+  int w = maxw;
+  while (w > 1 && stage_smem(t, stage, G, w) > kMaxSmemPerCta) w--;
+  return stage_smem(t, stage, G, w) <= kMaxSmemPerCta ? w : 0;
+}
+
+template <class Kern>
 cudaError_t launch_persistent(Kern kern, const LMLaunch &p, int num_sms, cudaStream_t st,
-                              int *blocks_used) {
-  size_t smem = lm_smem_bytes(p.t, WPB);
+                              int *blocks_used, int stage, int G, int maxw) {
+  const int wpb = fit_warps(p.t, stage, G, maxw);
+  if (wpb < 1) return cudaErrorInvalidConfiguration;
+  const size_t smem = stage_smem(p.t, stage, G, wpb);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WPB * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const int cl = p.s.claim > 0 ? p.s.claim : kClaim;
-  long long need = (p.s.n_pix + (long long)WPB * cl - 1) / ((long long)WPB * cl);
+  const long long per_cta = (long long)wpb * (32 / G) * cl;
+  long long need = (p.s.n_pix + per_cta - 1) / per_cta;
   long long blocks = (long long)num_sms * occ;
   if (blocks > need) blocks = need;
   if (blocks < 1) blocks = 1;
-  kern<<<(int)blocks, WPB * 32, smem, st>>>(p);
+  kern<<<(int)blocks, wpb * 32, smem, st>>>(p);
   if (blocks_used) *blocks_used += (int)blocks;
   return cudaGetLastError();
 }
 
-template <int K, int S1, int S2>
-cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant,
+template <int K>
+cudaError_t launch_stage1(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu, int v) {
+  const Shape s = kShape1[v];
+  switch (v) {
+    case 1: return launch_persistent(lm_stage1_kernel<K, 8, 12>, p, num_sms, st, bu, 1, s.G, s.maxw);
+    case 2: return launch_persistent(lm_stage1_kernel<K, 32, 8>, p, num_sms, st, bu, 1, s.G, s.maxw);
+    default: return launch_persistent(lm_stage1_kernel<K, 16, 12>, p, num_sms, st, bu, 1, s.G, s.maxw);
+  }
+}
+
+template <int K>
+cudaError_t launch_stage2(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu) {
+  return launch_persistent(lm_stage2_kernel<K, kShape2.G, kShape2.maxw>, p, num_sms, st, bu, 2,
+                           kShape2.G, kShape2.maxw);
+}
+
+template <int K>
+cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant,
                      cudaEvent_t *ev) {
+  // variant = stage-1 shape
+  const int v1 = variant % 3;
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
-  // variant bit 0: stage 1 with two CTAs per SM (128 registers) instead of one
-  e = (variant & 1)
-          ? launch_persistent<kWPB>(lm_stage1_kernel<K, S1, kWPB, 2>, p, num_sms, st, blocks_used)
-          : launch_persistent<kWPB>(lm_stage1_kernel<K, S1, kWPB, 1>, p, num_sms, st, blocks_used);
-  if (e != cudaSuccess) return e;
+  if ((e = launch_stage1<K>(p, num_sms, st, blocks_used, v1)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-  // variant bits 1-2: stage 2 with 8, 12 or 16 warps per CTA (one CTA per
-  // SM; up to 255, 168 or 128 registers)
-  int v2 = (variant >> 1) & 3;
-  if (v2 == 2 && lm_smem_bytes(p.t, 16) > kMaxSmemPerCta) v2 = 1;   // too many band slots
-  if (v2 == 1 && lm_smem_bytes(p.t, 12) > kMaxSmemPerCta) v2 = 0;
-  switch (v2) {
-    case 1: e = launch_persistent<12>(lm_stage2_kernel<K, S2, 12>, p, num_sms, st, blocks_used); break;
-    case 2: e = launch_persistent<16>(lm_stage2_kernel<K, S2, 16>, p, num_sms, st, blocks_used); break;
-    default: e = launch_persistent<kWPB>(lm_stage2_kernel<K, S2, kWPB>, p, num_sms, st, blocks_used);
-  }
-  if (e != cudaSuccess) return e;
+  if ((e = launch_stage2<K>(p, num_sms, st, blocks_used)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   long long blocks = (p.s.n_pix + 127) / 128;
   if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
@@ -1729,38 +1790,30 @@ cudaError_t launch_t(const LMLaunch &p, int num_sms, cudaStream_t st, int *block
 }
 
 template <int K>
-cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant,
-                     cudaEvent_t *ev) {
-  int s1 = (p.t.n1 + 31) / 32, s2 = (p.t.n2 + 31) / 32;
-  if (s1 <= 9 && s2 <= 7) return launch_t<K, 9, 7>(p, num_sms, st, blocks_used, variant, ev);
-  if (s1 <= 9 && s2 <= 9) return launch_t<K, 9, 9>(p, num_sms, st, blocks_used, variant, ev);
-  if (s1 <= 16 && s2 <= 16) return launch_t<K, 16, 16>(p, num_sms, st, blocks_used, variant, ev);
-  return cudaErrorInvalidValue;
-}
-
-template <int K>
 cudaError_t launch_ne_k(const LMLaunch &p, int stage, const float *states, float *H, float *g,
                         float *cost, cudaStream_t st) {
-  int s1 = (p.t.n1 + 31) / 32, s2 = (p.t.n2 + 31) / 32;
-  size_t smem = lm_smem_bytes(p.t, kWPB);
-  int blocks = (int)((p.s.n_pix + kWPB - 1) / kWPB);
-  if (blocks > 1024) blocks = 1024;
-  auto go = [&](auto kern) {
+  // the lanes per pixel of the default fit shapes
+  auto go = [&](auto kern, int G, int maxw) {
+    const int wpb = fit_warps(p.t, stage, G, maxw);
+    if (wpb < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = stage_smem(p.t, stage, G, wpb);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<blocks, kWPB * 32, smem, st>>>(p, stage, states, H, g, cost);
+    const int per = wpb * (32 / G);
+    int blocks = (int)((p.s.n_pix + per - 1) / per);
+    if (blocks > 1024) blocks = 1024;
+    kern<<<blocks, wpb * 32, smem, st>>>(p, stage, states, H, g, cost);
     return cudaGetLastError();
   };
-  if (s1 <= 9 && s2 <= 7) return go(normal_eq_kernel<K, 9, 7, kWPB>);
-  if (s1 <= 9 && s2 <= 9) return go(normal_eq_kernel<K, 9, 9, kWPB>);
-  if (s1 <= 16 && s2 <= 16) return go(normal_eq_kernel<K, 16, 16, kWPB>);
-  return cudaErrorInvalidValue;
+  if (stage == 1) return go(normal_eq_kernel<K, 16, 8>, 16, 8);
+  return go(normal_eq_kernel<K, 32, 8>, 32, 8);
 }
 
 }  // namespace
 
-size_t lm_smem_bytes(const KTables &t, int wpb) {
-  return (size_t)t.lay.total * 4 + (size_t)wpb * warp_scratch_floats(t) * 4;
+size_t lm_smem_bytes(const KTables &t, int) {
+  // the smallest launch: one warp of the widest-group stage-2 shape
+  return stage_smem(t, 2, 32, 1);
 }
 
 cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant,
