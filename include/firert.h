@@ -353,6 +353,27 @@ fire_status_t fire_autotune(fire_ctx_t *ctx, const float *radiance, const uint16
                             fire_tune_t *best, fire_stream_t stream);
 fire_status_t fire_set_tuning(fire_ctx_t *ctx, int32_t variant, int32_t claim);
 
+/* ---- Fit without allocation (an addition of this library; the paper has
+ * no counterpart). The plain-LM fit of a device scene of at most
+ * FIRE_STATIC_MAX_PIX pixels whose scratch (stage hand-over, work
+ * counters, statistics, error word; about 3.2 MB) is one file-scope device
+ * array of the library: the call makes no cudaMalloc/cudaFree and calls no
+ * allocating routine; it clears the counters that must start at zero on
+ * the stream and launches the three fit kernels with the context's launch
+ * shape, so its results equal fire_retrieve's.
+ * - The first call on each device looks up the array's address
+ *   (cudaGetSymbolAddress): make it before capturing the call in a graph.
+ * - All calls share the one array: two calls whose executions overlap (on
+ *   different streams, threads or contexts) race and corrupt each other.
+ * - Scene and outputs must be device memory; init_mode DEFAULT or GIVEN.
+ * - Errors: FIRE_ERR_SHAPE if n_pix > FIRE_STATIC_MAX_PIX; FIRE_ERR_ARG
+ *   for a host scene, the learned start or bad priors; FIRE_ERR_CUDA.
+ * fire_get_stats does not see these calls. */
+#define FIRE_STATIC_MAX_PIX 16384
+fire_status_t fire_retrieve_static(fire_ctx_t *ctx, const fire_scene_t *scene,
+                                   const fire_priors_t *priors, const fire_outputs_t *out,
+                                   fire_stream_t stream);
+
 /* Per-kernel timing. With timing on, every fit launch records CUDA events
  * on its stream around the stage-1, stage-2 and finalize kernels (no
  * synchronisation). fire_get_kernel_times waits for the last one and

@@ -10,7 +10,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", f) for f in ("api.cu", "kernels_lm.cu", "kernels_aux.cu",
-                                               "kernels_gemm.cu", "kernels_mlp.cu", "mlp.cu", "batch.cu")]
+                                               "kernels_gemm.cu", "kernels_mlp.cu", "mlp.cu", "batch.cu",
+                                         "noalloc.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("internal.cuh", "model.cuh", "mlp_internal.h",
                                                        "ctx_internal.h")] + \
     [os.path.join(ROOT, "include", "firert.h")]

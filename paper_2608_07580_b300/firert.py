@@ -21,6 +21,7 @@ FIRE_INIT_DEFAULT, FIRE_INIT_GIVEN, FIRE_INIT_MLP = 0, 1, 2
 FIRE_FIT_ALL, FIRE_FIT_HFDI = 0, 1
 PX_CONVERGED, PX_MAXITER, PX_NONFINITE, PX_ALL_MASKED, PX_CHOL_FAIL, PX_NOT_CANDIDATE = range(6)
 PX_F_FP64, PX_F_NOT_IDENT, PX_F_MLP_FALLBACK, PX_F_S1_MAXITER = 8, 16, 32, 64
+STATIC_MAX_PIX = 16384           # scene limit of Context.retrieve_static
 
 SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fire_ctx_destroy",
            "fire_retrieve", "fire_forward", "fire_block_mean", "fire_get_stats",
@@ -29,7 +30,8 @@ SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fir
            "fire_mlp_gradients", "fire_mlp_param_count", "fire_mlp_params", "fire_mlp_save",
            "fire_mlp_load", "fire_mlp_next_sample", "fire_ctx_set_mlp", "fire_retrieve_batch",
            "fire_graph_capture", "fire_graph_launch", "fire_graph_destroy", "fire_autotune",
-           "fire_set_tuning", "fire_set_kernel_timing", "fire_get_kernel_times")
+           "fire_set_tuning", "fire_set_kernel_timing", "fire_get_kernel_times",
+           "fire_retrieve_static")
 
 
 class FireError(RuntimeError):
@@ -166,6 +168,9 @@ def _load():
     lib.fire_graph_destroy.argtypes = [vp]
     lib.fire_autotune.argtypes = [vp, vp, vp, i64, C.POINTER(Tune_t), vp]
     lib.fire_autotune.restype = C.c_int
+    lib.fire_retrieve_static.argtypes = [vp, C.POINTER(Scene_t), C.POINTER(Priors_t),
+                                         C.POINTER(Outputs_t), vp]
+    lib.fire_retrieve_static.restype = C.c_int
     lib.fire_set_kernel_timing.argtypes = [vp, i32]
     lib.fire_set_kernel_timing.restype = C.c_int
     lib.fire_get_kernel_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_int32)]
@@ -327,6 +332,32 @@ class Context:
                                          "rms", "hfdi", "status", "iters")])
         _check(lib.fire_retrieve(self._h, C.byref(sc), C.byref(pri), C.byref(o), stream_p),
                "fire_retrieve")
+        return outputs
+
+    def retrieve_static(self, radiance, wv_bin, priors=None, init_state=None, gate_hfdi=False,
+                        outputs=None, stream=None):
+        """fire_retrieve_static: the plain-LM fit of a device scene (at most
+        STATIC_MAX_PIX pixels) through the library's static scratch, without
+        any allocation inside the call."""
+        import torch
+        n = int(radiance.shape[0])
+        if priors is None:
+            priors = self.default_priors()
+        if outputs is None:
+            outputs = self.alloc_outputs(n)
+        pri = Priors_t()
+        C.memmove(C.byref(pri), C.byref(priors), C.sizeof(Priors_t))
+        if wv_bin.element_size() != 2:
+            raise FireError("wv_bin must be a 16-bit tensor")
+        if init_state is not None:
+            pri.init_mode, pri.init_state = FIRE_INIT_GIVEN, _dptr(init_state, torch.float32)
+        sc = Scene_t(n, _dptr(radiance, torch.float32), _dptr(wv_bin), FIRE_MEM_DEVICE,
+                     int(bool(gate_hfdi)))
+        o = Outputs_t(*[_dptr(outputs.get(k)) for k in ("state", "ET", "sdT", "alpha", "cov",
+                                                       "var_ET", "cost", "rms", "hfdi",
+                                                       "status", "iters")])
+        _check(lib.fire_retrieve_static(self._h, C.byref(sc), C.byref(pri), C.byref(o),
+                                        _stream_ptr(stream)), "fire_retrieve_static")
         return outputs
 
     def forward(self, mode, state, wv_bin, noise_rel=0.0, noise_abs=0.0, seed=0, stream_id=1,

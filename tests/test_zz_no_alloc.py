@@ -1,0 +1,49 @@
+"""fire_retrieve_static (the fit through the library's static device
+scratch, no allocation in the call) against fire_retrieve on the same
+inputs: two calls in a row, each equal to the allocating entry point bit
+for bit; oversize scenes and the learned start are rejected. The file name
+makes pytest collect it last, after every other test has used the library."""
+import numpy as np
+import pytest
+
+from scenes import config1
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("state", "ET", "sdT", "alpha", "cov", "var_ET", "cost", "rms", "hfdi", "status", "iters")
+
+
+def _np(d):
+    return {k: v.cpu().numpy() for k, v in d.items() if hasattr(v, "cpu")}
+
+
+def test_static_equals_retrieve_twice_in_a_row():
+    import torch
+    from paper_2608_07580_b300 import firert as fr
+    t, tr, L = config1()
+    ctx = fr.Context(t)
+    Ld = torch.from_numpy(L).cuda()
+    wd = torch.from_numpy(tr.wv_bin.astype(np.int16)).cuda()
+    for sl in (slice(0, 4096), slice(1000, 2234)):      # two calls, the second ragged
+        ref = _np(ctx.retrieve(Ld[sl].contiguous(), wd[sl].contiguous()))
+        got = _np(ctx.retrieve_static(Ld[sl].contiguous(), wd[sl].contiguous()))
+        torch.cuda.synchronize()
+        for k in KEYS:
+            assert np.array_equal(ref[k], got[k], equal_nan=True), (sl, k)
+        assert np.all((got["status"] & 7) < 8)
+
+
+def test_static_rejects_oversize_and_learned_start():
+    import torch
+    from paper_2608_07580_b300 import firert as fr
+    t, tr, L = config1(width=16, height=16)
+    ctx = fr.Context(t)
+    big = torch.zeros((fr.STATIC_MAX_PIX + 1, t.n_bands), dtype=torch.float32, device="cuda")
+    wbig = torch.zeros((fr.STATIC_MAX_PIX + 1,), dtype=torch.int16, device="cuda")
+    with pytest.raises(fr.FireError, match="shape"):
+        ctx.retrieve_static(big, wbig)
+    pri = ctx.default_priors()
+    pri.init_mode = fr.FIRE_INIT_MLP
+    with pytest.raises(fr.FireError):
+        ctx.retrieve_static(torch.from_numpy(L).cuda(), torch.from_numpy(tr.wv_bin.astype(np.int16)).cuda(),
+                            priors=pri)
