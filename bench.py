@@ -232,7 +232,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-mlp", action="store_true")
     ap.add_argument("--variant", type=int, default=None,
-                    help="launch shape 0..2 (default: autotuned on a tenth of the scene)")
+                    help="launch shape 0..5 (default: autotuned on a tenth of the scene)")
     ap.add_argument("--claim", type=int, default=2)
     ap.add_argument("--mlp-steps", type=int, default=3000)
     args = ap.parse_args()

@@ -338,13 +338,13 @@ fire_status_t fire_graph_capture(fire_ctx_t *ctx, const fire_batch_item_t *items
 fire_status_t fire_graph_launch(fire_graph_t *g, fire_stream_t stream);
 void fire_graph_destroy(fire_graph_t *g);
 /* Autotuner: times each launch shape on the n given device pixels and keeps
- * the fastest for the context. variant picks the lanes per pixel of stage 1:
- * 0 = 16 lanes (two pixels per warp), 1 = 8 lanes (four per warp), 2 = 32
- * lanes (one per warp); stage 2 always fits one pixel per warp. claim:
- * pixels per work claim (1, 2, 4, 8). Each stage runs one persistent CTA per
- * SM with as many warps as its shared memory allows (at most 12 for stage 1,
- * 8 for stage 2). fire_set_tuning sets a shape directly (variant 0..2,
- * claim 1..64). */
+ * the fastest for the context. variant = 3 * s2 + s1: s1 picks the lanes
+ * per pixel of stage 1 (0 = 16 lanes, two pixels per warp; 1 = 8 lanes,
+ * four per warp; 2 = 32 lanes, one per warp), s2 those of stage 2 (0 = 32
+ * lanes; 1 = 16). claim: pixels per work claim (1, 2, 4, 8). Each stage
+ * runs one persistent CTA per SM with as many warps as its shared memory
+ * allows (at most 12 for stage 1, 8 for stage 2). fire_set_tuning sets a
+ * shape directly (variant 0..5, claim 1..64). */
 typedef struct {
   int32_t variant, claim;
   float ms;

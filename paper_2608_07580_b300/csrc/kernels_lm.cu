@@ -34,13 +34,21 @@ namespace firert {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+#ifdef FIRE_FAST_RCP
+#define RCP(x) __fdividef(1.f, (x))
+#else
+#define RCP(x) __frcp_rn(x)
+#endif
 constexpr int kClaim = 4;          // pixels claimed per atomic
 constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in dynamic shared memory per CTA
 // Stage-1 steps whose predicted decrease is below this fraction of the cost
 // are judged by the increment-form decrease: the decrease from residual
 // differences is accurate to a few 1e-6 of the cost, so above 1e-3 of it the
 // acceptance is decided correctly either way.
-constexpr float kIncBelow = 1e-3f;
+#ifndef FIRE_INC_BELOW
+#define FIRE_INC_BELOW 1e-3f
+#endif
+constexpr float kIncBelow = FIRE_INC_BELOW;
 
 template <int I>
 struct IC { static constexpr int value = I; };
@@ -487,11 +495,11 @@ struct Stage1 {
           E[k] = pc.img[t.lay.off_endm + k * t.nb + b];
           rho = fmaf(x[k], E[k], rho);
         }
-        float inv = __frcp_rn(1.f - q.z * rho);
+        float inv = RCP(1.f - q.z * rho);
         float Ls = fmaf(q.x * rho, inv, q.y);
         float xx = pc.img[t.lay.off_c2l + b] * invT;
         float e = __expf(-xx);
-        float rom = __frcp_rn(1.f - e);
+        float rom = RCP(1.f - e);
         float B = pc.img[t.lay.off_c1l5 + b] * e * rom;
         float dB = B * xx * invT * rom;
         float r = Lo(i) - fmaf(a1 * q.w, B, Ls);
@@ -1294,9 +1302,11 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
       }
     }
     if (__all_sync(kFull, done)) break;
-    if (!active) continue;
-    // ---- one LM step of this group's pixel
-    bool go = first || next_trial(S, c, x, H, g, m, cst, c.max_it1, L, xt);
+    // ---- one LM step of this group's pixel: the step, then (with every
+    // lane of the warp reconverged) the evaluation
+    bool go = false;
+    if (active) go = first || next_trial(S, c, x, H, g, m, cst, c.max_it1, L, xt);
+    __syncwarp();
     if (go) {
       float Ht[NH], gt[P], ct, cdt, drop;
       int mt;
@@ -1325,7 +1335,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
       }
       first = false;
     }
-    if (!go) {
+    __syncwarp();
+    if (active && !go) {
       // ---- stage 1 done: hand the state to stage 2
       if (L.status == PX_MAXITER) status |= PX_F_S1_MAXITER;
       if (L.used64) status |= PX_F_FP64;
@@ -1433,9 +1444,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       active = true;
     }
     if (__all_sync(kFull, done)) break;
-    if (!active) continue;
-    bool go = true, probe = false;
-    if (!first) {
+    bool go = active, probe = false;
+    if (active && !first) {
       if (alt) {
 #pragma unroll
         for (int i = 0; i < 6; i++) xt[i] = xa[i];
@@ -1445,6 +1455,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
         go = next_trial(S, c, x, H, g, 0, cst, c.max_it2, L, xt);
       }
     }
+    __syncwarp();
     if (go) {
       float Ht[21], gt[6], ct, cdt, drop;
       S.eval(pc, gp, x, xt, rc ^ 1, Ht, gt, ct, cdt, drop);
@@ -1474,7 +1485,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       }
       first = false;
     }
-    if (!go) {
+    __syncwarp();
+    if (active && !go) {
       // ---- hand the final state and normal equations to the finalize kernel
       if (L.used64) status |= PX_F_FP64;
       status |= L.status;
@@ -1715,9 +1727,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) normal_eq_kernel(const __grid_co
 // shared memory of the table image plus one scratch block per pixel allows.
 struct Shape { int G, maxw; };
 constexpr Shape kShape1[3] = {{16, 12}, {8, 12}, {32, 8}};
-// stage 2 runs one pixel per warp: at two or four pixels per warp its longer
-// node passes per lane cost more than the shared solve saves (measured)
-constexpr Shape kShape2 = {32, 8};
+constexpr Shape kShape2[2] = {{32, 8}, {16, 8}};
 
 size_t stage_smem(const KTables &t, int stage, int G, int wpb) {
   const int per = stage == 1 ? pix_stride1(t, G) : pix_stride2(t, G);
@@ -1764,21 +1774,22 @@ cudaError_t launch_stage1(const LMLaunch &p, int num_sms, cudaStream_t st, int *
 }
 
 template <int K>
-cudaError_t launch_stage2(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu) {
-  return launch_persistent(lm_stage2_kernel<K, kShape2.G, kShape2.maxw>, p, num_sms, st, bu, 2,
-                           kShape2.G, kShape2.maxw);
+cudaError_t launch_stage2(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu, int v) {
+  const Shape s = kShape2[v];
+  if (v == 1) return launch_persistent(lm_stage2_kernel<K, 16, 8>, p, num_sms, st, bu, 2, s.G, s.maxw);
+  return launch_persistent(lm_stage2_kernel<K, 32, 8>, p, num_sms, st, bu, 2, s.G, s.maxw);
 }
 
 template <int K>
 cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant,
                      cudaEvent_t *ev) {
-  // variant = stage-1 shape
-  const int v1 = variant % 3;
+  // variant = 3 * (stage-2 shape) + (stage-1 shape)
+  const int v1 = variant % 3, v2 = (variant / 3) % 2;
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   if ((e = launch_stage1<K>(p, num_sms, st, blocks_used, v1)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-  if ((e = launch_stage2<K>(p, num_sms, st, blocks_used)) != cudaSuccess) return e;
+  if ((e = launch_stage2<K>(p, num_sms, st, blocks_used, v2)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   long long blocks = (p.s.n_pix + 127) / 128;
   if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
