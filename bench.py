@@ -204,18 +204,30 @@ def mlp_init_figure(ctx, rad, wv_d, out, args, stream):
         ctx.retrieve(rad, wv_d, outputs=out, learned_start=True)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.set_kernel_timing(True)
     a.record(stream)
     for _ in range(args.steps):
         ctx.retrieve(rad, wv_d, outputs=out, learned_start=True)
     b.record(stream)
     torch.cuda.synchronize()
+    kms, nfit = ctx.kernel_times()       # the main fit and the fallback re-fit of each step
+    ctx.set_kernel_timing(False)
     ms = a.elapsed_time(b) / args.steps
+    # network inference alone on the same scene
+    a.record(stream)
+    mlp.infer(rad)
+    b.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = a.elapsed_time(b)
     it = out["iters"].to(torch.int32).float().mean(0).cpu().numpy()
     st = out["status"].cpu().numpy()
     ctx.set_mlp(None)
     return {"value": n / (ms / 1e3), "unit": "pixels/s", "ms_per_step": ms,
             "mean_iters": [round(float(it[0]), 2), round(float(it[1]), 2)],
             "fallback_frac": float(np.mean((st & 32) > 0)),
+            "ms_breakdown": {"inference": round(infer_ms, 2),
+                             "lm_kernels_per_step": [round(x / args.steps, 2) for x in kms],
+                             "fits_per_step": nfit / args.steps},
             "train": {"steps": args.mlp_steps, "batch": 4096, "seconds": round(train_s, 2),
                       "final_loss": float(np.mean(loss[-20:]))}}
 

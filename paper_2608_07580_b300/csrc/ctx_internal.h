@@ -35,9 +35,10 @@ struct fire_ctx {
   void *d_cmp = nullptr;
   int64_t cmp_cap = 0;
   int last_launches = 0;
-  // autotuned launch shape: stage-1 occupancy variant and pixels per claim
-  int tune_variant = 0;
-  int tune_claim = 4;
+  // launch shape (autotuned): lanes per pixel of the two stages (16 and 16)
+  // and pixels per claim
+  int tune_variant = 3;
+  int tune_claim = 1;
   // batched calls: scene descriptors on the device
   firert::SceneItem *d_items = nullptr;
   long long *d_prefix = nullptr;

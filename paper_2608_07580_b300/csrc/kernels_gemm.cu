@@ -181,6 +181,27 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(GemmArgs g) {
           : "r"(ta));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (!rv) continue;
+      if (g.Cb && !g.Cf && !g.CbT && g.epi != EPI_RELU_MASK && !(g.ldcb & 7) &&
+          n0 + c0 + 16 <= g.N) {
+        // bf16 rows: bias, activation, and 16-byte stores of 8 values
+#pragma unroll
+        for (int h = 0; h < 16; h += 8) {
+          uint32_t pk[4];
+#pragma unroll
+          for (int j = 0; j < 8; j += 2) {
+            const int col = n0 + c0 + h + j;
+            float a0 = __uint_as_float(v[h + j]), a1 = __uint_as_float(v[h + j + 1]);
+            if (g.bias) { a0 += g.bias[col]; a1 += g.bias[col + 1]; }
+            if (g.epi == EPI_BIAS_RELU) { a0 = fmaxf(a0, 0.f); a1 = fmaxf(a1, 0.f); }
+            else if (g.epi == EPI_BIAS_TANH) { a0 = tanhf(a0); a1 = tanhf(a1); }
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(a0, a1);
+            pk[j / 2] = *reinterpret_cast<const uint32_t *>(&p2);
+          }
+          *reinterpret_cast<uint4 *>(g.Cb + (size_t)row * g.ldcb + n0 + c0 + h) =
+              make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        continue;
+      }
 #pragma unroll
       for (int j = 0; j < 16; j++) {
         const int col = n0 + c0 + j;

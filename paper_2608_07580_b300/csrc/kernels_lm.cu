@@ -34,21 +34,22 @@ namespace firert {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-#ifdef FIRE_FAST_RCP
-#define RCP(x) __fdividef(1.f, (x))
-#else
-#define RCP(x) __frcp_rn(x)
-#endif
+
 constexpr int kClaim = 4;          // pixels claimed per atomic
 constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in dynamic shared memory per CTA
 // Stage-1 steps whose predicted decrease is below this fraction of the cost
 // are judged by the increment-form decrease: the decrease from residual
-// differences is accurate to a few 1e-6 of the cost, so above 1e-3 of it the
-// acceptance is decided correctly either way.
-#ifndef FIRE_INC_BELOW
-#define FIRE_INC_BELOW 1e-3f
-#endif
-constexpr float kIncBelow = FIRE_INC_BELOW;
+// differences carries a rounding error of a few 1e-6 of the cost, which
+// would decide the acceptance of smaller steps.
+constexpr float kIncBelow = 1e-5f;
+// FP32 rounding floor of the gradient: each residual carries the rounding of
+// its model value M_b (a few units in the last place), so g_a = sum_b w_b
+// J_ba r_b cannot be resolved below about kFloorC u sqrt(sum_b (w_b J_ba
+// M_b)^2), u = 2^-24. Where the noise is low (block-averaged spectra) this
+// floor exceeds the gradient tolerance and an FP32 fit cannot pass the test;
+// such a fit runs to the iteration cap and is reported converged if its
+// gradient is within the tolerance plus the floor there.
+constexpr float kFloorC = 8.f * 5.9604645e-8f;
 
 template <int I>
 struct IC { static constexpr int value = I; };
@@ -199,14 +200,15 @@ struct LMIter {
 };
 
 // From the normal equations (H, g) at the current state x: the convergence
-// test (when they are fresh), then the damped projected-Newton step and the
+// test (when they are fresh; gf is the FP32 rounding floor of g, see
+// kFloorC), then the damped projected-Newton step and the
 // trial point xt with its predicted decrease. Returns false when the fit
 // stops (converged, step below tol_x, damping overflow, iteration cap).
 template <class St>
 __device__ __forceinline__ bool next_trial(const St &S, const KConfig &c, const float (&x)[St::NX],
-                                           const float (&H)[St::NH], const float (&g)[St::P], int m,
-                                           float cst, int max_it, LMIter<St::P> &L,
-                                           float (&xt)[St::NX]) {
+                                           const float (&H)[St::NH], const float (&g)[St::P],
+                                           const float (&gf)[St::P], int m, float cst, int max_it,
+                                           LMIter<St::P> &L, float (&xt)[St::NX]) {
   constexpr int P = St::P, NX = St::NX;
 #pragma unroll 1
   while (L.it < max_it) {
@@ -319,6 +321,14 @@ __device__ __forceinline__ bool next_trial(const St &S, const KConfig &c, const 
     L.it++;
     return true;
   }
+  // iteration cap: converged if the gradient of the free variables is within
+  // the tolerance plus its FP32 rounding floor
+  bool small = true;
+  static_for<P>([&](auto A_) {
+    constexpr int a = decltype(A_)::value;
+    if (!L.act[a] && fabsf(g[a]) > fmaf(c.tol_g, sqrtf(H[up<P>(a, a)] * cst), gf[a])) small = false;
+  });
+  if (small) L.status = PX_CONVERGED;
   return false;
 }
 
@@ -383,8 +393,9 @@ __host__ __device__ __forceinline__ int pix_stride1(const KTables &t, int G) {
   int f = 8 * band_slots(t.n1, G);
   return f + ((G - f % 32) % 32 + 32) % 32;
 }
+constexpr int kNE2 = 48;   // stage-2 per-pixel slot: trial H[21], g[6], floor[6] at 30, proposal x[6] at 40
 __host__ __device__ __forceinline__ int pix_stride2(const KTables &t, int G) {
-  int f = t.nt * kScratchPerNode + 5 * band_slots(t.n2, G);
+  int f = t.nt * kScratchPerNode + 5 * band_slots(t.n2, G) + kNE2;
   return f + ((G - f % 32) % 32 + 32) % 32;
 }
 // table-image floats a stage needs: stage 1 stops before the Planck grid
@@ -465,15 +476,15 @@ struct Stage1 {
   //   dB_b = B_o expm1(-dx_b) / (1 - e^-x_t), dx_b = -(c2/lambda_b) dT / (T_t T_o),
   // each increment formed from the exact parameter differences.
   __device__ __forceinline__ void eval(const PixCtx &pc, const Grp<G> &gp, const float (&x)[NX],
-                                       int rn, float (&H)[NH], float (&g)[P], float &cst,
-                                       float &cd, float &drop, int &m, const float (&xo)[NX],
-                                       bool inc) const {
+                                       int rn, float (&H)[NH], float (&g)[P], float (&gf)[P],
+                                       float &cst, float &cd, float &drop, int &m,
+                                       const float (&xo)[NX], bool inc) const {
     const KTables &t = *pc.t;
     const KConfig &c = *pc.c;
     m = argmax_frac(x);
-    float acc[NH + P + 3];
+    float acc[NH + 2 * P + 3];
 #pragma unroll
-    for (int i = 0; i < NH + P + 3; i++) acc[i] = 0.f;
+    for (int i = 0; i < NH + 2 * P + 3; i++) acc[i] = 0.f;
     const float a1 = x[K], invT = 1.f / x[K + 1];
     const float dTT = (x[K + 1] - xo[K + 1]) * invT / xo[K + 1];
     const float dal = a1 - xo[K];
@@ -495,11 +506,12 @@ struct Stage1 {
           E[k] = pc.img[t.lay.off_endm + k * t.nb + b];
           rho = fmaf(x[k], E[k], rho);
         }
-        float inv = RCP(1.f - q.z * rho);
+        // fast reciprocals (within 2 ulp): both arguments lie well inside (0, 1]
+        float inv = __fdividef(1.f, 1.f - q.z * rho);
         float Ls = fmaf(q.x * rho, inv, q.y);
         float xx = pc.img[t.lay.off_c2l + b] * invT;
         float e = __expf(-xx);
-        float rom = RCP(1.f - e);
+        float rom = __fdividef(1.f, 1.f - e);
         float B = pc.img[t.lay.off_c1l5 + b] * e * rom;
         float dB = B * xx * invT * rom;
         float r = Lo(i) - fmaf(a1 * q.w, B, Ls);
@@ -534,11 +546,14 @@ struct Stage1 {
         J[K - 1] = q.w * B * sa;
         J[K] = a1 * q.w * dB * sT;
         float wr = wv * r;
+        const float wM = wv * (Lo(i) - r);     // weight x model value
         acc[NH + P] = fmaf(wr, r, acc[NH + P]);
         acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
 #pragma unroll
         for (int a = 0; a < P; a++) {
           acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
+          const float fj = wM * J[a];
+          acc[NH + P + 3 + a] = fmaf(fj, fj, acc[NH + P + 3 + a]);
           float wj = wv * J[a];
 #pragma unroll
           for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
@@ -549,7 +564,10 @@ struct Stage1 {
 #pragma unroll
     for (int i = 0; i < NH; i++) H[i] = acc[i];
 #pragma unroll
-    for (int a = 0; a < P; a++) g[a] = acc[NH + a];
+    for (int a = 0; a < P; a++) {
+      g[a] = acc[NH + a];
+      gf[a] = kFloorC * sqrtf(acc[NH + P + 3 + a]);
+    }
     cd = acc[NH + P + 1];
     cst = acc[NH + P];
     drop = acc[NH + P + 2];
@@ -702,9 +720,12 @@ struct Stage2 {
   // differences. The decrease is then accurate relative to itself, where
   // the difference of two FP32 model values would be lost below their
   // rounding. 7 FMA per band and node.
+  // H, g and the gradient's FP32 floor go to the shared slot ne ([21] packed
+  // upper H, [6] g at 21, [6] floor at 30), so that they need no registers
+  // until the step is accepted.
   __device__ __forceinline__ void eval(const PixCtx &pc, const Grp<G> &gp, const float (&x)[NX],
-                                       const float (&xt)[NX], int rn, float (&H)[NH],
-                                       float (&g)[P], float &cst, float &cd, float &drop) const {
+                                       const float (&xt)[NX], int rn, float *ne, float &cst,
+                                       float &cd, float &drop) const {
     const KTables &t = *pc.t;
     const KConfig &c = *pc.c;
     const float mh = xt[0], sh = xt[1], ms = xt[2], ss = xt[3], eta = xt[4], al = xt[5];
@@ -757,9 +778,9 @@ struct Stage2 {
       }
     }
     gp.sync();
-    float acc[NH + P + 3];
+    float acc[NH + 2 * P + 3];
 #pragma unroll
-    for (int i = 0; i < NH + P + 3; i++) acc[i] = 0.f;
+    for (int i = 0; i < NH + 2 * P + 3; i++) acc[i] = 0.f;
     const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
     const float ish3 = ish2 / sh, iss3 = iss2 / ss;
     const float sc0 = scale(c, 0), sc1 = scale(c, 1), sc2 = scale(c, 2), sc3 = scale(c, 3);
@@ -772,28 +793,42 @@ struct Stage2 {
     const int ns = nbs / G;
 #pragma unroll 1
     for (int s0 = 0; s0 < ns; s0 += kChunk2) {
-      // moment sums over the grid nodes for kChunk2 band slots of this lane
-      float S[kChunk2][7];
+      // moment sums over the grid nodes for kChunk2 band slots of this lane,
+      // in pairs with the packed FP32 FMA (two round-to-nearest FMAs per
+      // instruction, the same results as one at a time): (S0, S1), (S2, S3),
+      // (S4, S5), (S6, -)
+      float2 S2v[kChunk2][4];
 #pragma unroll
       for (int k = 0; k < kChunk2; k++)
 #pragma unroll
-        for (int q = 0; q < 7; q++) S[k][q] = 0.f;
+        for (int q = 0; q < 4; q++) S2v[k][q] = make_float2(0.f, 0.f);
       const float *pls = pl + G * s0;
 #pragma unroll 2
       for (int j = 0; j < t.nt; j++) {
         const float4 A = nd[2 * j], B = nd[2 * j + 1];
+        const float2 a01 = make_float2(A.x, A.y), a23 = make_float2(A.z, A.w);
+        const float2 b01 = make_float2(B.x, B.y), b23 = make_float2(B.z, B.w);
         const float *row = pls + j * t.lay.n2s;
 #pragma unroll
         for (int k = 0; k < kChunk2; k++) {
           const float Bv = (s0 + k < ns) ? row[G * k] : 0.f;
-          S[k][0] = fmaf(A.x, Bv, S[k][0]);
-          S[k][1] = fmaf(A.y, Bv, S[k][1]);
-          S[k][2] = fmaf(A.z, Bv, S[k][2]);
-          S[k][3] = fmaf(A.w, Bv, S[k][3]);
-          S[k][4] = fmaf(B.x, Bv, S[k][4]);
-          S[k][5] = fmaf(B.y, Bv, S[k][5]);
-          S[k][6] = fmaf(B.z, Bv, S[k][6]);
+          const float2 bb2 = make_float2(Bv, Bv);
+          S2v[k][0] = __ffma2_rn(a01, bb2, S2v[k][0]);
+          S2v[k][1] = __ffma2_rn(a23, bb2, S2v[k][1]);
+          S2v[k][2] = __ffma2_rn(b01, bb2, S2v[k][2]);
+          S2v[k][3] = __ffma2_rn(b23, bb2, S2v[k][3]);
         }
+      }
+      float S[kChunk2][7];
+#pragma unroll
+      for (int k = 0; k < kChunk2; k++) {
+        S[k][0] = S2v[k][0].x;
+        S[k][1] = S2v[k][0].y;
+        S[k][2] = S2v[k][1].x;
+        S[k][3] = S2v[k][1].y;
+        S[k][4] = S2v[k][2].x;
+        S[k][5] = S2v[k][2].y;
+        S[k][6] = S2v[k][3].x;
       }
 #pragma unroll
       for (int k = 0; k < kChunk2; k++) {
@@ -817,11 +852,14 @@ struct Stage2 {
             J[4] = atu * (Bh - Bs) * sc4;
             J[5] = tuv * Bm * sc5;
             const float wr = wv * r;
+            const float wM = wv * atu * Bm;     // weight x thermal model value
             acc[NH + P] = fmaf(wr, r, acc[NH + P]);
             acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
 #pragma unroll
             for (int a = 0; a < P; a++) {
               acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
+              const float fj = wM * J[a];
+              acc[NH + P + 3 + a] = fmaf(fj, fj, acc[NH + P + 3 + a]);
               const float wj = wv * J[a];
 #pragma unroll
               for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
@@ -831,10 +869,6 @@ struct Stage2 {
       }
     }
     gp.sum(acc);
-#pragma unroll
-    for (int i = 0; i < NH; i++) H[i] = acc[i];
-#pragma unroll
-    for (int a = 0; a < P; a++) g[a] = acc[NH + a];
     cst = acc[NH + P];
     cd = acc[NH + P + 1];
     drop = acc[NH + P + 2];
@@ -843,9 +877,16 @@ struct Stage2 {
       float z = c.hi2[i] > c.lo2[i] ? 2.f * (xt[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
       float pp = psc * c.pp2[i];
       cst += pp * (z - c.pm2[i]) * (z - c.pm2[i]);
-      g[i] -= pp * (z - c.pm2[i]);
-      H[up<P>(i, i)] += pp;
+      acc[NH + i] -= pp * (z - c.pm2[i]);
+      acc[up<P>(i, i)] += pp;
     }
+#pragma unroll
+    for (int a = 0; a < P; a++) acc[NH + P + 3 + a] = kFloorC * sqrtf(acc[NH + P + 3 + a]);
+    // lane sub stores entries sub, sub + G, ... of [H | g | -, -, - | gf]
+#pragma unroll
+    for (int k = 0; k < NH + 2 * P + 3; k++)
+      if (k < NH + P || k >= NH + P + 3)
+        if ((k & (G - 1)) == gp.sub) ne[k] = acc[k];
     gp.sync();
   }
 
@@ -1212,7 +1253,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
   long long next = 0, end = 0, pix = 0, opix = 0;
   uint16_t *iters_out = nullptr;
   bool active = false, done = false, first = false;
-  float x[NX], xt[NX], H[NH], g[P], cst = 0.f;
+  float x[NX], xt[NX], H[NH], g[P], gf[P], cst = 0.f;
   int m = 0, rc = 0, nfull = 0, status = 0;
   LMIter<P> L;
   for (;;) {
@@ -1305,14 +1346,14 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
     // ---- one LM step of this group's pixel: the step, then (with every
     // lane of the warp reconverged) the evaluation
     bool go = false;
-    if (active) go = first || next_trial(S, c, x, H, g, m, cst, c.max_it1, L, xt);
+    if (active) go = first || next_trial(S, c, x, H, g, gf, m, cst, c.max_it1, L, xt);
     __syncwarp();
     if (go) {
-      float Ht[NH], gt[P], ct, cdt, drop;
+      float Ht[NH], gt[P], gft[P], ct, cdt, drop;
       int mt;
       // small steps: decrease in increment form (FP32 resolution)
       const bool inc = !first && L.pred < kIncBelow * cst;
-      S.eval(pc, gp, xt, rc ^ 1, Ht, gt, ct, cdt, drop, mt, x, inc);
+      S.eval(pc, gp, xt, rc ^ 1, Ht, gt, gft, ct, cdt, drop, mt, x, inc);
       nfull++;
       bool accept = first;
       if (!first) {
@@ -1328,7 +1369,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
 #pragma unroll
         for (int i = 0; i < NH; i++) H[i] = Ht[i];
 #pragma unroll
-        for (int a = 0; a < P; a++) g[a] = gt[a];
+        for (int a = 0; a < P; a++) {
+          g[a] = gt[a];
+          gf[a] = gft[a];
+        }
         cst = ct;
         m = mt;
         rc ^= 1;
@@ -1383,7 +1427,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
   const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
   long long next = 0, end = 0, pix = 0;
   bool active = false, done = false, first = false, alt = false;
-  float x[6], xt[6], xa[6], H[21], g[6], cst = 0.f, cd = 0.f;
+  float x[6], xt[6], H[21], g[6], gf[6], cst = 0.f, cd = 0.f;
+  float *ne = S.bb + 5 * S.nbs;   // trial H, g, gradient floor, then the proposal start
   int rc = 0, nfull = 0, status = 0, n2u = 0;
   LMIter<6> L;
   for (;;) {
@@ -1425,8 +1470,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
         if (p.s.init_best) {
           // learned start: after the derived start, the proposal is tried
           // as a step and kept if its cost is lower
-#pragma unroll
-          for (int i = 0; i < 6; i++) xa[i] = xg[i];
+          if (gp.sub < 6) ne[40 + gp.sub] = pick(xg, gp.sub);
           alt = true;
         } else {
 #pragma unroll
@@ -1448,17 +1492,17 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
     if (active && !first) {
       if (alt) {
 #pragma unroll
-        for (int i = 0; i < 6; i++) xt[i] = xa[i];
+        for (int i = 0; i < 6; i++) xt[i] = ne[40 + i];
         alt = false;
         probe = true;
       } else {
-        go = next_trial(S, c, x, H, g, 0, cst, c.max_it2, L, xt);
+        go = next_trial(S, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
       }
     }
     __syncwarp();
     if (go) {
-      float Ht[21], gt[6], ct, cdt, drop;
-      S.eval(pc, gp, x, xt, rc ^ 1, Ht, gt, ct, cdt, drop);
+      float ct, cdt, drop;
+      S.eval(pc, gp, x, xt, rc ^ 1, ne, ct, cdt, drop);
       nfull++;
       bool accept = first;
       if (!first) {
@@ -1476,9 +1520,12 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
 #pragma unroll
         for (int i = 0; i < 6; i++) x[i] = xt[i];
 #pragma unroll
-        for (int i = 0; i < 21; i++) H[i] = Ht[i];
+        for (int i = 0; i < 21; i++) H[i] = ne[i];
 #pragma unroll
-        for (int a = 0; a < 6; a++) g[a] = gt[a];
+        for (int a = 0; a < 6; a++) {
+          g[a] = ne[21 + a];
+          gf[a] = ne[30 + a];
+        }
         cst = ct;
         cd = cdt;
         rc ^= 1;
@@ -1684,11 +1731,11 @@ __global__ void __launch_bounds__(MAXW * 32, 1) normal_eq_kernel(const __grid_co
       s1.bb = smem + img_f + gid * pix_stride1(t, G);
       pc.node = nullptr;
       setup1(s1, pc, gp, row);
-      float x[K + 2], H[P * (P + 1) / 2], g[P], cst, cd, drop;
+      float x[K + 2], H[P * (P + 1) / 2], g[P], gf[P], cst, cd, drop;
       int m;
 #pragma unroll
       for (int i = 0; i < K + 2; i++) x[i] = states[pix * (K + 2) + i];
-      s1.eval(pc, gp, x, 1, H, g, cst, cd, drop, m, x, false);
+      s1.eval(pc, gp, x, 1, H, g, gf, cst, cd, drop, m, x, false);
       if (gp.sub == 0) {
         for (int a = 0; a < P; a++) {
           gout[pix * P + a] = g[a];
@@ -1708,12 +1755,13 @@ __global__ void __launch_bounds__(MAXW * 32, 1) normal_eq_kernel(const __grid_co
 #pragma unroll
       for (int i = 0; i < 6; i++) x[i] = states[pix * (K + 6) + K + i];
       setup2<K>(s2, pc, gp, row, xs);
-      float H[21], g[6], cst, cd, drop;
-      s2.eval(pc, gp, x, x, 1, H, g, cst, cd, drop);
+      float cst, cd, drop;
+      float *ne = s2.bb + 5 * s2.nbs;
+      s2.eval(pc, gp, x, x, 1, ne, cst, cd, drop);
       if (gp.sub == 0) {
         for (int a = 0; a < 6; a++) {
-          gout[pix * 6 + a] = g[a];
-          for (int b = 0; b < 6; b++) Hout[pix * 36 + a * 6 + b] = H[up<6>(a, b)];
+          gout[pix * 6 + a] = ne[21 + a];
+          for (int b = 0; b < 6; b++) Hout[pix * 36 + a * 6 + b] = ne[up<6>(a, b)];
         }
         cost_out[pix] = cst;
       }

@@ -191,13 +191,16 @@ def test_host_path_equals_device_path_and_is_deterministic(fr, torch, c1):
 
 
 def test_given_init_matches_oracle(fr, torch, c1):
+    """A given start (the truth, written in the mixture's form: the single
+    temperature as the hot mean above 1000 K, else as the smouldering mean)
+    for every fire pixel of the scene."""
     t, tr, L = c1
-    idx = np.flatnonzero(tr.kind == 1)[:64]
-    K = 3
-    init = np.column_stack([tr.x_surf[idx], tr.single[idx, 0], tr.single[idx, 1],
-                            np.maximum(tr.single[idx, 1], 950), np.full(idx.size, 60.0),
-                            np.full(idx.size, 600.0), np.full(idx.size, 60.0),
-                            np.full(idx.size, 0.8), tr.single[idx, 0]]).astype(np.float32)
+    idx = np.flatnonzero(tr.kind == 1)
+    T = tr.single[idx, 1]
+    init = np.column_stack([tr.x_surf[idx], tr.single[idx, 0], T,
+                            np.clip(T, 900, 2200), np.full(idx.size, 60.0),
+                            np.clip(T, 350, 1000), np.full(idx.size, 60.0),
+                            (T >= 1000).astype(float), tr.single[idx, 0]]).astype(np.float32)
     o = oracle.retrieve(t, L[idx], tr.wv_bin[idx], init_state=init.astype(np.float64))
     ctx = fr.Context(t)
     out = ctx.retrieve(_dev(torch, L[idx], torch.float32),
@@ -205,7 +208,8 @@ def test_given_init_matches_oracle(fr, torch, c1):
                        init_state=_dev(torch, init, torch.float32))
     torch.cuda.synchronize()
     s = parity_stats(o, _np(out))
-    assert s["rate"] >= 0.99 and s["pool"] > 10
+    print("given start:", {k: v for k, v in s.items() if k != "fail_idx"})
+    assert s["rate"] >= 0.99 and s["pool"] > 50
 
 
 @pytest.mark.parametrize("stage", [1, 2])
