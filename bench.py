@@ -182,9 +182,11 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-# dram bytes (read + write) per launch of each kernel from the committed ncu
-# capture of this workload; None once the kernel has changed since
-PROFILED_TRAFFIC = {}
+# DRAM bytes (read + write) per pixel of each LM kernel, from the ncu capture
+# of the 256 x 1024 sub-chunk (profiles/lm_stage*_medium.md: 309.6 MB and
+# 315.5 MB over 262,144 px); a launch reads each pixel's inputs once, so its
+# traffic scales with the pixels it fits
+PROFILED_TRAFFIC_PER_PX = {"lm_stage2_kernel": 309.64e6 / 262144, "lm_stage1_kernel": 315.49e6 / 262144}
 
 
 def mlp_init_figure(ctx, rad, wv_d, out, args, stream):
@@ -338,7 +340,9 @@ def main():
     kdom = int(np.argmax(per_ms[:2]))
     achieved = flops[kdom] / (per_ms[kdom] / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": PROFILED_TRAFFIC.get(names[kdom]),
+            "frac": achieved / peak_tflops,
+            "traffic": (PROFILED_TRAFFIC_PER_PX[names[kdom]] * n
+                        if names[kdom] in PROFILED_TRAFFIC_PER_PX else None),
             "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
             "kernel": names[kdom], "flops_per_launch": flops[kdom],
             "kernels": {names[i]: {"ms": per_ms[i], "share": per_ms[i] / max(sum(per_ms), 1e-9),

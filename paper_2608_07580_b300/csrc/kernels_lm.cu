@@ -30,10 +30,19 @@
 
 #include "internal.cuh"
 
+
 namespace firert {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// Loop shapes of the stage kernels. The per-iteration code of an LM step runs
+// once per round as straight-line code and is fetch-bound (ncu: instruction
+// fetch stalls first), so the band and node loops stay rolled: measured on
+// the flight-line chunk, unrolling them by 2 cost 17 % in stage 1 and 7 % in
+// stage 2; rolling the Jacobian assembly over a chunk's slots saved another
+// 2.5 % in stage 2.
+constexpr int kBand1Unroll = 1, kNodeUnroll = 1;
+constexpr int kSlotUnroll = 1;   // stage-2 Jacobian assembly over a chunk's band slots
 
 constexpr int kClaim = 4;          // pixels claimed per atomic
 constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in dynamic shared memory per CTA
@@ -482,9 +491,9 @@ struct Stage1 {
     const KTables &t = *pc.t;
     const KConfig &c = *pc.c;
     m = argmax_frac(x);
-    float acc[NH + 2 * P + 3];
+    float acc[NH + P + 5];
 #pragma unroll
-    for (int i = 0; i < NH + 2 * P + 3; i++) acc[i] = 0.f;
+    for (int i = 0; i < NH + P + 5; i++) acc[i] = 0.f;
     const float a1 = x[K], invT = 1.f / x[K + 1];
     const float dTT = (x[K + 1] - xo[K + 1]) * invT / xo[K + 1];
     const float dal = a1 - xo[K];
@@ -493,7 +502,7 @@ struct Stage1 {
     for (int k = 0; k < K; k++) dxs[k] = x[k] - xo[k];
     const float *ro = bb + (3 - rn) * nbs, *bo = bb + (5 - rn) * nbs, *vo = bb + (7 - rn) * nbs;
     float *rw = bb + (2 + rn) * nbs, *bw = bb + (4 + rn) * nbs, *vw = bb + (6 + rn) * nbs;
-#pragma unroll 2
+#pragma unroll kBand1Unroll
     for (int i = gp.sub; i < t.n1; i += G) {
       const float wv = W(i);
       if (wv > 0.f) {
@@ -549,11 +558,11 @@ struct Stage1 {
         const float wM = wv * (Lo(i) - r);     // weight x model value
         acc[NH + P] = fmaf(wr, r, acc[NH + P]);
         acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
+        acc[NH + P + 3] = fmaf(wM, wM, acc[NH + P + 3]);
+        acc[NH + P + 4] += wv;
 #pragma unroll
         for (int a = 0; a < P; a++) {
           acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
-          const float fj = wM * J[a];
-          acc[NH + P + 3 + a] = fmaf(fj, fj, acc[NH + P + 3 + a]);
           float wj = wv * J[a];
 #pragma unroll
           for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
@@ -563,10 +572,13 @@ struct Stage1 {
     gp.sum(acc);
 #pragma unroll
     for (int i = 0; i < NH; i++) H[i] = acc[i];
+    // FP32 floor of g_a: kFloorC sqrt(sum_b (w_b J_ba M_b)^2), estimated as
+    // kFloorC sqrt(H_aa sum_b w_b^2 M_b^2 / sum_b w_b) (data part of H_aa)
+    const float m2 = acc[NH + P + 3] / fmaxf(acc[NH + P + 4], 1e-30f);
 #pragma unroll
     for (int a = 0; a < P; a++) {
       g[a] = acc[NH + a];
-      gf[a] = kFloorC * sqrtf(acc[NH + P + 3 + a]);
+      gf[a] = kFloorC * sqrtf(acc[up<P>(a, a)] * m2);
     }
     cd = acc[NH + P + 1];
     cst = acc[NH + P];
@@ -778,9 +790,9 @@ struct Stage2 {
       }
     }
     gp.sync();
-    float acc[NH + 2 * P + 3];
+    float acc[NH + P + 5];
 #pragma unroll
-    for (int i = 0; i < NH + 2 * P + 3; i++) acc[i] = 0.f;
+    for (int i = 0; i < NH + P + 5; i++) acc[i] = 0.f;
     const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
     const float ish3 = ish2 / sh, iss3 = iss2 / ss;
     const float sc0 = scale(c, 0), sc1 = scale(c, 1), sc2 = scale(c, 2), sc3 = scale(c, 3);
@@ -803,7 +815,7 @@ struct Stage2 {
 #pragma unroll
         for (int q = 0; q < 4; q++) S2v[k][q] = make_float2(0.f, 0.f);
       const float *pls = pl + G * s0;
-#pragma unroll 2
+#pragma unroll kNodeUnroll
       for (int j = 0; j < t.nt; j++) {
         const float4 A = nd[2 * j], B = nd[2 * j + 1];
         const float2 a01 = make_float2(A.x, A.y), a23 = make_float2(A.z, A.w);
@@ -830,7 +842,7 @@ struct Stage2 {
         S[k][5] = S2v[k][2].y;
         S[k][6] = S2v[k][3].x;
       }
-#pragma unroll
+#pragma unroll kSlotUnroll
       for (int k = 0; k < kChunk2; k++) {
         const int i = gp.sub + G * (s0 + k);
         if (s0 + k < ns && i < t.n2) {
@@ -855,11 +867,11 @@ struct Stage2 {
             const float wM = wv * atu * Bm;     // weight x thermal model value
             acc[NH + P] = fmaf(wr, r, acc[NH + P]);
             acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
+            acc[NH + P + 3] = fmaf(wM, wM, acc[NH + P + 3]);
+            acc[NH + P + 4] += wv;
 #pragma unroll
             for (int a = 0; a < P; a++) {
               acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
-              const float fj = wM * J[a];
-              acc[NH + P + 3 + a] = fmaf(fj, fj, acc[NH + P + 3 + a]);
               const float wj = wv * J[a];
 #pragma unroll
               for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
@@ -872,6 +884,11 @@ struct Stage2 {
     cst = acc[NH + P];
     cd = acc[NH + P + 1];
     drop = acc[NH + P + 2];
+    // FP32 floor of g_a (as in stage 1), from the data part of H_aa
+    float gfl[P];
+    const float m2 = acc[NH + P + 3] / fmaxf(acc[NH + P + 4], 1e-30f);
+#pragma unroll
+    for (int a = 0; a < P; a++) gfl[a] = kFloorC * sqrtf(acc[up<P>(a, a)] * m2);
 #pragma unroll
     for (int i = 0; i < 6; i++) {
       float z = c.hi2[i] > c.lo2[i] ? 2.f * (xt[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
@@ -880,13 +897,13 @@ struct Stage2 {
       acc[NH + i] -= pp * (z - c.pm2[i]);
       acc[up<P>(i, i)] += pp;
     }
+    // lane sub stores entries sub, sub + G, ... of [H | g], then the floor at 30
 #pragma unroll
-    for (int a = 0; a < P; a++) acc[NH + P + 3 + a] = kFloorC * sqrtf(acc[NH + P + 3 + a]);
-    // lane sub stores entries sub, sub + G, ... of [H | g | -, -, - | gf]
+    for (int k = 0; k < NH + P; k++)
+      if ((k & (G - 1)) == gp.sub) ne[k] = acc[k];
 #pragma unroll
-    for (int k = 0; k < NH + 2 * P + 3; k++)
-      if (k < NH + P || k >= NH + P + 3)
-        if ((k & (G - 1)) == gp.sub) ne[k] = acc[k];
+    for (int a = 0; a < P; a++)
+      if (((30 + a) & (G - 1)) == gp.sub) ne[30 + a] = gfl[a];
     gp.sync();
   }
 
