@@ -183,10 +183,10 @@ def run_reference(args):
 
 
 # DRAM bytes (read + write) per pixel of each LM kernel, from the ncu capture
-# of the 256 x 1024 sub-chunk (profiles/lm_stage*_medium.md: 309.6 MB and
-# 315.5 MB over 262,144 px); a launch reads each pixel's inputs once, so its
+# of the 256 x 1024 sub-chunk (profiles/lm_stage*_medium.md: 305.3 MB and
+# 316.7 MB over 262,144 px); a launch reads each pixel's inputs once, so its
 # traffic scales with the pixels it fits
-PROFILED_TRAFFIC_PER_PX = {"lm_stage2_kernel": 309.64e6 / 262144, "lm_stage1_kernel": 315.49e6 / 262144}
+PROFILED_TRAFFIC_PER_PX = {"lm_stage2_kernel": 309.10e6 / 262144, "lm_stage1_kernel": 316.68e6 / 262144}
 
 
 def mlp_init_figure(ctx, rad, wv_d, out, args, stream):

@@ -179,6 +179,8 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
 }
 
 // -------------------------------------------------------- LM driver -----
+template <int G>
+struct Grp;
 struct LMResult {
   int iters, full, status;   // trial steps; full model + Jacobian evaluations
   bool used64;
@@ -214,10 +216,11 @@ struct LMIter {
 // trial point xt with its predicted decrease. Returns false when the fit
 // stops (converged, step below tol_x, damping overflow, iteration cap).
 template <class St>
-__device__ __forceinline__ bool next_trial(const St &S, const KConfig &c, const float (&x)[St::NX],
-                                           const float (&H)[St::NH], const float (&g)[St::P],
-                                           const float (&gf)[St::P], int m, float cst, int max_it,
-                                           LMIter<St::P> &L, float (&xt)[St::NX]) {
+__device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, const KConfig &c,
+                                           const float (&x)[St::NX], const float (&H)[St::NH],
+                                           const float (&g)[St::P], const float (&gf)[St::P], int m,
+                                           float cst, int max_it, LMIter<St::P> &L,
+                                           float (&xt)[St::NX]) {
   constexpr int P = St::P, NX = St::NX;
 #pragma unroll 1
   while (L.it < max_it) {
@@ -265,20 +268,29 @@ __device__ __forceinline__ bool next_trial(const St &S, const KConfig &c, const 
       float kap = 0.f;
       ok = damped_solve<P, float>(H, g, L.lam, D, pin, dr, kap);
       if (!ok || !(kap <= c.kappa_max)) {
-        Solve64<P> q;
+        // FP64 re-solve by the group's first lane only (the FP64 pipe is a
+        // sixty-fourth of the FP32 one), the step broadcast to the group
+        bool ok64 = false;
+        if (gp.sub == 0) {
+          Solve64<P> q;
 #pragma unroll
-        for (int i = 0; i < St::NH; i++) q.H[i] = H[i];
+          for (int i = 0; i < St::NH; i++) q.H[i] = H[i];
 #pragma unroll
-        for (int a = 0; a < P; a++) {
-          q.g[a] = g[a];
-          q.D[a] = D[a];
-          q.pin[a] = pin[a];
-          q.dr[a] = dr[a];
+          for (int a = 0; a < P; a++) {
+            q.g[a] = g[a];
+            q.D[a] = D[a];
+            q.pin[a] = pin[a];
+            q.dr[a] = dr[a];
+          }
+          q.lam = L.lam;
+          ok64 = solve_fp64<P>(q);
+#pragma unroll
+          for (int a = 0; a < P; a++) dr[a] = q.dr[a];
         }
-        q.lam = L.lam;
-        ok = solve_fp64<P>(q);
+        const int lead = gp.lane & ~(St::GL - 1);
+        ok = __shfl_sync(gp.mask, ok64 ? 1 : 0, lead) != 0;
 #pragma unroll
-        for (int a = 0; a < P; a++) dr[a] = q.dr[a];
+        for (int a = 0; a < P; a++) dr[a] = __shfl_sync(gp.mask, dr[a], lead);
         L.used64 = true;
       }
       if (!ok) break;
@@ -424,7 +436,7 @@ struct PixCtx {
 // ------------------------------------------------------------ stage 1 ---
 template <int K, int G>
 struct Stage1 {
-  static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2;
+  static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2, GL = G;
   // band buffers in shared memory, [8][nbs]: observed radiance, weight,
   // and for the current and the trial state (index rc, rc ^ 1) the residual,
   // the Planck factor B(lambda_b, T1) and 1 / (1 - S_b rho_b)
@@ -680,7 +692,7 @@ constexpr int kChunk2 = 7;   // stage-2 band slots per lane accumulated per node
 
 template <int G>
 struct Stage2 {
-  static constexpr int P = 6, NX = 6, NH = 21;
+  static constexpr int P = 6, NX = 6, NH = 21, GL = G;
   // band buffers in shared memory, [5][nbs]: y (radiance minus the fixed
   // solar term), tau_up, weight, and the residuals of the current and of the
   // trial state (index rc, rc ^ 1)
@@ -1363,7 +1375,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
     // ---- one LM step of this group's pixel: the step, then (with every
     // lane of the warp reconverged) the evaluation
     bool go = false;
-    if (active) go = first || next_trial(S, c, x, H, g, gf, m, cst, c.max_it1, L, xt);
+    if (active) go = first || next_trial(S, gp, c, x, H, g, gf, m, cst, c.max_it1, L, xt);
     __syncwarp();
     if (go) {
       float Ht[NH], gt[P], gft[P], ct, cdt, drop;
@@ -1513,7 +1525,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
         alt = false;
         probe = true;
       } else {
-        go = next_trial(S, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
+        go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
       }
     }
     __syncwarp();
