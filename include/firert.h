@@ -340,11 +340,17 @@ void fire_graph_destroy(fire_graph_t *g);
 /* Autotuner: times each launch shape on the n given device pixels and keeps
  * the fastest for the context. variant = 3 * s2 + s1: s1 picks the lanes
  * per pixel of stage 1 (0 = 16 lanes, two pixels per warp; 1 = 8 lanes,
- * four per warp; 2 = 32 lanes, one per warp), s2 those of stage 2 (0 = 32
- * lanes; 1 = 16). claim: pixels per work claim (1, 2, 4, 8). Each stage
- * runs one persistent CTA per SM with as many warps as its shared memory
- * allows (at most 12 for stage 1, 8 for stage 2). fire_set_tuning sets a
- * shape directly (variant 0..5, claim 1..64). */
+ * four per warp; 2 = 32 lanes, one per warp), s2 the stage-2 evaluation
+ * (0 = FP32 with 32 lanes per pixel; 1 = FP32 with 16; 2 = 16 lanes per
+ * pixel, 16 pixels per CTA, with the grid-node sums of the CTA's pixels as
+ * one bf16x3 tensor-core product per round; tables with more than 64 grid
+ * nodes or 256 stage-2 bands take 1 instead). claim: pixels per work claim
+ * (1, 2, 4, 8). Each stage runs one persistent CTA per SM with as many warps
+ * as its shared memory allows (at most 12 for stage 1, 8 for stage 2). A
+ * new context starts at variant 6 where the tables allow it, else 3.
+ * fire_set_tuning sets a shape directly (variant 0..8, claim 1..64); the
+ * stage-2 evaluation of the set shape is also the one that
+ * fire_normal_equations uses. */
 typedef struct {
   int32_t variant, claim;
   float ms;

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", f) for f in ("api.cu", "kernels_lm.cu", "kernels_aux.cu",
                                                "kernels_gemm.cu", "kernels_mlp.cu", "mlp.cu", "batch.cu",
                                          "noalloc.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("internal.cuh", "model.cuh", "mlp_internal.h",
+DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("internal.cuh", "model.cuh", "mlp_internal.h", "tc.cuh",
                                                        "ctx_internal.h")] + \
     [os.path.join(ROOT, "include", "firert.h")]
 LIB = os.path.join(HERE, "libfirert.so")

@@ -361,6 +361,7 @@ const char *fire_status_str(fire_status_t s) {
 void fire_ctx_destroy(fire_ctx_t *ctx) {
   if (!ctx) return;
   cudaFree(ctx->d_image);
+  cudaFree(ctx->d_plop);
   cudaFree(ctx->d_wvtab);
   cudaFree(ctx->d_sat);
   cudaFree(ctx->d_work);
@@ -432,6 +433,7 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
   L.n2s = (t.n2 + 31) & ~31;
   L.off_planck = take(nt * L.n2s);
   L.total = o;
+  t.plrows = (t.n2 + 7) & ~7;
   if (lm_smem_bytes(t) > 200 * 1024) {
     delete c;
     return FIRE_ERR_SHAPE;
@@ -443,6 +445,7 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
   size_t nraw = (size_t)nb * 2 + (size_t)nwv * nb * 4 + (size_t)K * nb;
   do {
     if ((st = dev_alloc(&c->d_image, (size_t)L.total * 4)) != FIRE_OK) break;
+    if ((st = dev_alloc(&c->d_plop, planck_operand_bytes(t))) != FIRE_OK) break;
     if ((st = dev_alloc(&c->d_wvtab, (size_t)nwv * nb * sizeof(float4))) != FIRE_OK) break;
     if ((st = dev_alloc(&c->d_work, (size_t)(2 + ST_COUNT) * 8)) != FIRE_OK) break;
     if ((st = dev_alloc(&c->d_err, sizeof(int))) != FIRE_OK) break;
@@ -471,6 +474,10 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
     if ((st = cuda_status(launch_build_tables(t, d_wl, d_e0, tb->cos_sza, d_td, d_tu, d_ra, d_sa,
                                               d_en, c->d_image, c->d_wvtab, win, 0))) != FIRE_OK)
       break;
+    if ((st = cuda_status(launch_planck_operand(t, c->d_plop, 0))) != FIRE_OK) break;
+    t.plop = c->d_plop;
+    // the tensor-core stage 2 where the tables fit it
+    c->tune_variant = lm_tc_ok(t) ? 6 : 3;
     st = cuda_status(cudaDeviceSynchronize());
   } while (0);
   if (raw) cudaFree(raw);
@@ -707,7 +714,8 @@ fire_status_t fire_normal_equations(fire_ctx_t *c, int32_t stage, const float *r
   p.s.rad = radiance;
   p.s.wv = wv_bin;
   p.w.err = c->d_err;
-  return cuda_status(launch_normal_eq(p, stage, states, H, g, cost, (cudaStream_t)stream));
+  return cuda_status(launch_normal_eq(p, stage, states, H, g, cost, (cudaStream_t)stream,
+                                      c->tune_variant));
 }
 
 fire_status_t fire_gemm_bf16(const fire_gemm_t *q, fire_stream_t stream) {

@@ -234,14 +234,14 @@ fire_status_t fire_autotune(fire_ctx_t *c, const float *radiance, const uint16_t
   cudaStream_t st = (cudaStream_t)stream;
   fire_priors_t pd;
   fire_default_priors(&pd, c->t.K, c->t.nt, c->t.tglo, c->t.tglo + c->t.tgstep * (c->t.nt - 1));
-  const int variants[6] = {0, 1, 2, 3, 4, 5}, claims[4] = {1, 2, 4, 8};
+  const int variants[9] = {0, 1, 2, 3, 4, 5, 6, 7, 8}, claims[4] = {1, 2, 4, 8};
   cudaEvent_t a, b;
   BCK(cudaEventCreate(&a));
   BCK(cudaEventCreate(&b));
   float best_ms = 1e30f;
   int bv = c->tune_variant, bc = c->tune_claim;
   fire_status_t e = FIRE_OK;
-  for (int vi = 0; vi < 6 && e == FIRE_OK; vi++)
+  for (int vi = 0; vi < 9 && e == FIRE_OK; vi++)
     for (int ci = 0; ci < 4 && e == FIRE_OK; ci++) {
       c->tune_variant = variants[vi];
       c->tune_claim = claims[ci];
@@ -279,7 +279,7 @@ fire_status_t fire_autotune(fire_ctx_t *c, const float *radiance, const uint16_t
 }
 
 fire_status_t fire_set_tuning(fire_ctx_t *c, int32_t variant, int32_t claim) {
-  if (!c || variant < 0 || variant > 5 || claim < 1 || claim > 64) return FIRE_ERR_ARG;
+  if (!c || variant < 0 || variant > 8 || claim < 1 || claim > 64) return FIRE_ERR_ARG;
   c->tune_variant = variant;
   c->tune_claim = claim;
   return FIRE_OK;

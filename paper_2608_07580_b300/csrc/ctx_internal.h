@@ -12,6 +12,7 @@ struct fire_ctx {
   firert::KTables t;
   // device buffers
   float *d_image = nullptr;
+  unsigned char *d_plop = nullptr;   // stage-2 Planck grid as the tensor-core operand
   float4 *d_wvtab = nullptr;
   float *d_sat = nullptr;
   unsigned long long *d_work = nullptr;  // [0] counter, [1..] stats
@@ -35,8 +36,9 @@ struct fire_ctx {
   void *d_cmp = nullptr;
   int64_t cmp_cap = 0;
   int last_launches = 0;
-  // launch shape (autotuned): lanes per pixel of the two stages (16 and 16)
-  // and pixels per claim
+  // launch shape (autotuned): variant = 3 * stage-2 shape + stage-1 shape
+  // (set at creation to the tensor-core stage 2 with 16 lanes per pixel in
+  // stage 1 where the tables fit it) and pixels per claim
   int tune_variant = 3;
   int tune_claim = 1;
   // batched calls: scene descriptors on the device

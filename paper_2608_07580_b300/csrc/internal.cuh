@@ -42,6 +42,10 @@ struct KTables {
   const float *sat;        // [nb] or nullptr
   const float *image;      // per-CTA table image in global memory
   ImageLayout lay;
+  // stage-2 Planck grid as the bf16 tensor-core operand: three parts
+  // (hi, mid, lo), each plrows x 64 nodes, K-major 128-byte-swizzled rows
+  const unsigned char *plop;
+  int plrows;              // n2 rounded up to a multiple of 8
 };
 
 struct KConfig {
@@ -151,8 +155,15 @@ cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *bloc
 size_t lm_smem_bytes(const KTables &t, int warps_per_cta = 8);
 cudaError_t launch_merge_fallback(const long long *idx, const float *cost_first, long long nfb,
                                   const KOut &compact, const KOut &out, int K, cudaStream_t st);
+// variant: the launch shape whose stage-2 evaluation is used (as launch_lm)
 cudaError_t launch_normal_eq(const LMLaunch &p, int stage, const float *states, float *H, float *g,
-                             float *cost, cudaStream_t st);
+                             float *cost, cudaStream_t st, int variant = 0);
+// stage-2 tensor-core path: operand size, its construction from the table
+// image, and whether the tables fit the path (grid nodes <= 64, stage-2
+// bands <= 256, shared memory)
+size_t planck_operand_bytes(const KTables &t);
+cudaError_t launch_planck_operand(const KTables &t, unsigned char *out, cudaStream_t st);
+bool lm_tc_ok(const KTables &t);
 cudaError_t launch_forward(const KTables &t, int mode, const float *state, const uint16_t *wv,
                            int64_t n, float noise_rel, float noise_abs, uint64_t seed,
                            uint64_t stream_id, int64_t pix0, float *out, cudaStream_t st);

@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace firert {
 namespace {
@@ -24,42 +25,13 @@ namespace {
 constexpr int kBM = 128, kBK = 64;
 constexpr long long kSpin = 1ll << 24;
 
-__device__ __forceinline__ unsigned su32(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-// UMMA shared-memory descriptor, K-major, 128-byte swizzle: start address,
-// leading-byte offset (unused for this layout), stride-byte offset = 1024 B
-// between 8-row core-matrix groups, descriptor version 1, layout type 2.
-__device__ __forceinline__ uint64_t sdesc(unsigned saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)(1u) << 16;
-  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-// instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
+using tc::idesc_bf16;
+using tc::sdesc;
+using tc::su32;
+using tc::swz;
 
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  unsigned done = 0;
-  for (long long s = 0; s < kSpin && !done; s++)
-    asm volatile(
-        "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2; selp.u32 %0, 1, 0, P; }"
-        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-  return done != 0;
-}
-
-// byte offset of the 16-byte chunk c (K elements 8c..8c+7) of row r inside a
-// K-major SW128 tile
-__device__ __forceinline__ unsigned swz(int r, int c) {
-  return (unsigned)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+  return tc::mbar_wait(bar, parity, kSpin);
 }
 
 __device__ __forceinline__ void cp16(unsigned dst, const void *src, bool valid) {

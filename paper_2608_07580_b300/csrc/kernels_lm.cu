@@ -26,9 +26,11 @@
 // diagonally scaled damped matrix; an ill-conditioned one (condition
 // estimate above kappa_max, or a failed pivot) is re-solved in FP64. The
 // final Laplace covariance is FP64.
+#include <cuda_bf16.h>
 #include <float.h>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 
 namespace firert {
@@ -1054,15 +1056,21 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
 // completing on one mbarrier. The wait is bounded: on timeout the error flag
 // is set, the copies still in flight are waited for (bounded again) and the
 // CTA leaves (returns false).
+// The table image (its first nfloats floats) goes to the start of the
+// dynamic shared memory; an optional second region (bytes2 bytes from src2 to
+// dst2, both 16-byte aligned, bytes2 a multiple of 16) rides on the same
+// mbarrier.
 __device__ __forceinline__ bool stage_tables(const KTables &t, float *smem, int nfloats,
-                                             unsigned long long *bar, int *err) {
+                                             unsigned long long *bar, int *err,
+                                             void *dst2 = nullptr, const void *src2 = nullptr,
+                                             unsigned bytes2 = 0) {
   const unsigned bytes = (unsigned)nfloats * 4u;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+                 ::"r"(smem_u32(bar)), "r"(bytes + bytes2) : "memory");
     const unsigned chunk = 32768u;
     for (unsigned off = 0; off < bytes; off += chunk) {
       unsigned n = bytes - off < chunk ? bytes - off : chunk;
@@ -1070,6 +1078,14 @@ __device__ __forceinline__ bool stage_tables(const KTables &t, float *smem, int 
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
           ::"r"(smem_u32(reinterpret_cast<char *>(smem) + off)),
           "l"(reinterpret_cast<const char *>(t.image) + off), "r"(n), "r"(smem_u32(bar))
+          : "memory");
+    }
+    for (unsigned off = 0; off < bytes2; off += chunk) {
+      unsigned n = bytes2 - off < chunk ? bytes2 - off : chunk;
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+          ::"r"(smem_u32(reinterpret_cast<char *>(dst2) + off)),
+          "l"(reinterpret_cast<const char *>(src2) + off), "r"(n), "r"(smem_u32(bar))
           : "memory");
     }
   }
@@ -1595,6 +1611,674 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
     if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
 }
 
+// ------------------------------------------ stage 2 on the tensor cores ---
+// The grid-node sums of the stage-2 evaluation, S_k(b) = sum_j c_kj
+// B(lambda_b, T_j) for the seven node coefficients of a pixel (the weights
+// of each component times 1, d - dbar and d^2 - m2, and the mixture-weight
+// increment), are one dense product per CTA and round once the pixels of
+// the CTA evaluate together:
+//   D[band b][8 s + k] = sum_j Bgrid[b][j] C[8 s + k][j],
+// M = 128 bands per tile (two tiles cover up to 256 bands), N = 16 pixel
+// slots x 8 coefficients, K = 64 nodes. Both operands are split into three
+// bf16 parts (x = x0 + x1 + x2, each part the bf16 rounding of what the
+// previous ones leave, 27 significant bits together) and the six products
+// of parts whose orders add up to at most 2 are accumulated in FP32 in
+// tensor memory, smallest first: the dropped products are below 2^-26 of
+// the sum, under FP32 rounding. The Planck operand is built once per
+// context; the coefficient operand is written each round by the pixels'
+// groups.
+//
+// A round: (1) every group with a trial point forms its node coefficients
+// (two node passes, as in the FP32 evaluation) and writes their parts as its
+// 8 rows of the coefficient operand; (2) one thread issues the MMAs and
+// commits them to an mbarrier; (3) with the sums in tensor memory, warp w
+// reads lane quarter w & 3 (32 bands of each tile) and forms, for the 8
+// pixel slots of its half, each band's residual, Jacobian row and
+// contributions to J^T W J, J^T W r, the cost and the increment-form
+// decrease; a reduce-scatter across the warp leaves one of the 32 sums per
+// lane, written as the quarter's partial; (4) each group adds its four
+// quarters' partials.
+namespace tcs2 {
+constexpr int G = 16, kWarps = 8, kSlots = kWarps * 32 / G;   // 16 pixels per CTA
+constexpr int kN = kSlots * 8;            // D columns
+constexpr int kCoPart = kN * 128;         // bytes of one part of the coefficient operand
+constexpr int kPrm = 16;                  // per-slot parameters of the band phase
+constexpr int kPartStride = 4 * 32 + 16;  // per-slot partial sums [4 quarters][32], padded
+constexpr long long kSpinMMA = 1ll << 24;
+
+// per-slot block: band buffers [5][nbs] (y, tau_up, weight, residuals),
+// the ne slot, the parameters; stride congruent to 16 modulo 32 floats so
+// the two groups of a warp hit different banks
+__host__ __device__ __forceinline__ int slot_floats(const KTables &t) {
+  const int f = 5 * band_slots(t.n2, G) + kNE2 + kPrm;
+  return f + ((16 - f % 32) % 32 + 32) % 32;
+}
+struct Lay {
+  int head_bytes;          // table image up to the Planck grid
+  int pl_bytes, co_bytes;  // operands (offsets from the 1024-aligned base)
+  int slots_off, parts_off, total;   // bytes from the aligned base; total dynamic bytes
+};
+__host__ __device__ __forceinline__ Lay layout(const KTables &t) {
+  Lay L;
+  L.head_bytes = image_floats(t, 1) * 4;
+  L.pl_bytes = 3 * t.plrows * 128;
+  L.co_bytes = 3 * kCoPart;
+  L.slots_off = L.pl_bytes + L.co_bytes;
+  L.parts_off = L.slots_off + kSlots * slot_floats(t) * 4;
+  L.total = L.head_bytes + 1024 + L.parts_off + kSlots * kPartStride * 4;
+  return L;
+}
+
+__device__ __forceinline__ void split3(float v, __nv_bfloat16 &p0, __nv_bfloat16 &p1,
+                                       __nv_bfloat16 &p2) {
+  p0 = __float2bfloat16_rn(v);
+  float r = v - __bfloat162float(p0);
+  p1 = __float2bfloat16_rn(r);
+  r -= __bfloat162float(p1);
+  p2 = __float2bfloat16_rn(r);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// (1) node coefficients of the slot's pixel at xt, with the mixture-weight
+// increment from x, as rows 8 slot + k (k < 7) of the coefficient operand;
+// lane sub holds nodes 2 sub, 2 sub + 1, 2 sub + 32, 2 sub + 33; then the
+// band-phase parameters of the slot
+__device__ __forceinline__ void coef(const KTables &t, const KConfig &c, const Grp<G> &gp,
+                                     const float (&x)[6], const float (&xt)[6], unsigned char *co,
+                                     int slot, float *prm, int rn) {
+  const float mh = xt[0], sh = xt[1], ms = xt[2], ss = xt[3], eta = xt[4], al = xt[5];
+  const float eo = x[4];
+  const float ih = 1.f / x[1], iht = 1.f / sh, is = 1.f / x[3], ist = 1.f / ss;
+  const float dmh = mh - x[0], dsh = sh - x[1], dms = ms - x[2], dss = ss - x[3];
+  float uh[4], duh[4], us[4], dus[4];
+  float mom[10];
+#pragma unroll
+  for (int k = 0; k < 10; k++) mom[k] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int j = 2 * gp.sub + (q & 1) + 32 * (q >> 1);
+    uh[q] = duh[q] = us[q] = dus[q] = 0.f;
+    if (j < t.nt) {
+      const float T = t.tglo + (float)j * t.tgstep;
+      Stage2<G>::node_step(T, x[0], ih, mh, iht, dmh, dsh, uh[q], duh[q]);
+      Stage2<G>::node_step(T, x[2], is, ms, ist, dms, dss, us[q], dus[q]);
+      const float uth = uh[q] + duh[q], uts = us[q] + dus[q], dh = T - mh, ds = T - ms;
+      mom[0] += uth;
+      mom[1] += uth * dh;
+      mom[2] += uth * dh * dh;
+      mom[3] += uts;
+      mom[4] += uts * ds;
+      mom[5] += uts * ds * ds;
+      mom[6] += uh[q];
+      mom[7] += duh[q];
+      mom[8] += us[q];
+      mom[9] += dus[q];
+    }
+  }
+  gp.sum(mom);
+  const float rUh = 1.f / mom[0], rUs = 1.f / mom[3];
+  const float dbh = mom[1] * rUh, m2h = mom[2] * rUh, dbs = mom[4] * rUs, m2s = mom[5] * rUs;
+  const float rUho = 1.f / mom[6], rUso = 1.f / mom[8];
+  const float kh = mom[7] * rUho, ks = mom[9] * rUso;
+  const unsigned cob = tc::su32(co);
+#pragma unroll
+  for (int pr = 0; pr < 2; pr++) {
+    const int j0 = 2 * gp.sub + 32 * pr;
+    if (j0 >= t.nt) continue;
+    float cf[2][7];
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      const int q = 2 * pr + e, j = j0 + e;
+      const float T = t.tglo + (float)j * t.tgstep;
+      const float dh = T - mh, ds = T - ms;
+      const float wh = (uh[q] + duh[q]) * rUh, ws = (us[q] + dus[q]) * rUs;
+      const float dwh = (duh[q] - uh[q] * kh) * rUh, dws = (dus[q] - us[q] * ks) * rUs;
+      const bool in = j < t.nt;
+      cf[e][0] = in ? wh : 0.f;
+      cf[e][1] = in ? wh * (dh - dbh) : 0.f;
+      cf[e][2] = in ? wh * (dh * dh - m2h) : 0.f;
+      cf[e][3] = in ? ws : 0.f;
+      cf[e][4] = in ? ws * (ds - dbs) : 0.f;
+      cf[e][5] = in ? ws * (ds * ds - m2s) : 0.f;
+      cf[e][6] = in ? eta * dwh + (1.f - eta) * dws + (eta - eo) * (uh[q] * rUho - us[q] * rUso) : 0.f;
+    }
+    const unsigned cc = (unsigned)(j0 & 7) * 2u;
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+      __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+      split3(cf[0][k], a0, a1, a2);
+      split3(cf[1][k], b0, b1, b2);
+      const unsigned off = cob + tc::swz(8 * slot + k, j0 >> 3) + cc;
+      asm volatile("st.shared.b32 [%0], %1;" ::"r"(off), "r"(pack2(a0, b0)) : "memory");
+      asm volatile("st.shared.b32 [%0], %1;" ::"r"(off + kCoPart), "r"(pack2(a1, b1)) : "memory");
+      asm volatile("st.shared.b32 [%0], %1;" ::"r"(off + 2 * kCoPart), "r"(pack2(a2, b2)) : "memory");
+    }
+  }
+  // band-phase parameters: [1] eta, [2] alpha, [3] alpha - alpha_o, [4..7]
+  // the Jacobian factors of mu_h, s_h, mu_s, s_s, [8] [9] z scales of eta and
+  // alpha, [10] the residual buffer written; [0] (the flag) is set by the caller
+  const float sc0 = 0.5f * (c.hi2[0] - c.lo2[0]), sc1 = 0.5f * (c.hi2[1] - c.lo2[1]);
+  const float sc2 = 0.5f * (c.hi2[2] - c.lo2[2]), sc3 = 0.5f * (c.hi2[3] - c.lo2[3]);
+  const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
+  float v = 0.f;
+  switch (gp.sub) {
+    case 1: v = eta; break;
+    case 2: v = al; break;
+    case 3: v = al - x[5]; break;
+    case 4: v = eta * ish2 * sc0; break;
+    case 5: v = eta * (ish2 / sh) * sc1; break;
+    case 6: v = (1.f - eta) * iss2 * sc2; break;
+    case 7: v = (1.f - eta) * (iss2 / ss) * sc3; break;
+    case 8: v = 0.5f * (c.hi2[4] - c.lo2[4]); break;
+    case 9: v = 0.5f * (c.hi2[5] - c.lo2[5]); break;
+    case 10: v = (float)rn; break;
+    default: break;
+  }
+  if (gp.sub >= 1 && gp.sub <= 10) prm[gp.sub] = v;
+}
+
+// (2) the six part products, smallest first, for each band tile
+__device__ __forceinline__ void mma(uint32_t tmem, unsigned pl, unsigned co, int plrows, int ntile,
+                                    unsigned bar) {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  constexpr uint32_t idesc = tc::idesc_bf16(128, kN);
+  constexpr int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
+  for (int m = 0; m < ntile; m++) {
+#pragma unroll
+    for (int pr = 0; pr < 6; pr++)
+#pragma unroll
+      for (int kk = 0; kk < 4; kk++) {
+        const uint64_t ad = tc::sdesc(pl + (unsigned)(pa[pr] * plrows * 128 + m * 16384 + kk * 32));
+        const uint64_t bd = tc::sdesc(co + (unsigned)(pb[pr] * kCoPart + kk * 32));
+        const uint32_t acc = (pr > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
+            ::"r"(tmem + (uint32_t)(128 * m)), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+      }
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(ta));
+#pragma unroll
+  for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// reduce-scatter of 32 values over the warp: lane l returns the warp total
+// of value l
+__device__ __forceinline__ float reduce_scatter(float (&v)[32], int l) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool hi = (l & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; i++) {
+      const float send = hi ? v[i] : v[i + o];
+      const float keep = hi ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  return v[0];
+}
+
+// (3) band phase: warp w, lane quarter q = w & 3, slots 8 (w >> 2) .. + 7
+__device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slots, int sstride,
+                                     float *parts, int nbs) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, q = w & 3, h = w >> 2;
+  const int ntile = (t.n2 + 127) >> 7;
+  constexpr int NH = 21, P = 6;
+#pragma unroll 1
+  for (int s = 8 * h; s < 8 * h + 8; s++) {
+    float *sb = slots + s * sstride;
+    const float *prm = sb + 5 * nbs + kNE2;
+    if (prm[0] == 0.f) continue;
+    float v[2][8];
+    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(8 * s), v[0]);
+    if (ntile > 1) tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 + 8 * s), v[1]);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const float eta = prm[1], al = prm[2], da = prm[3];
+    const float f0 = prm[4], f1 = prm[5], f2 = prm[6], f3 = prm[7], sc4 = prm[8], sc5 = prm[9];
+    const int rn = prm[10] != 0.f ? 1 : 0;
+    const float *Y = sb, *TU = sb + nbs, *W = sb + 2 * nbs;
+    const float *ro = sb + (4 - rn) * nbs;
+    float *rw = sb + (3 + rn) * nbs;
+    float acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) acc[i] = 0.f;
+#pragma unroll
+    for (int m = 0; m < 2; m++) {
+      const int b = 128 * m + 32 * q + l;
+      if (m < ntile && b < t.n2) {
+        const float wv = W[b];
+        if (wv > 0.f) {
+          const float *S = v[m];
+          const float Bh = S[0], Bs = S[3];
+          const float Bm = eta * Bh + (1.f - eta) * Bs;
+          const float tuv = TU[b];
+          const float atu = al * tuv;
+          const float r = Y[b] - atu * Bm;
+          rw[b] = r;
+          const float dM = tuv * fmaf(al, S[6], da * (Bm - S[6]));
+          acc[NH + P + 2] = fmaf(wv * dM, 2.f * ro[b] - dM, acc[NH + P + 2]);
+          float J[6];
+          J[0] = atu * S[1] * f0;
+          J[1] = atu * S[2] * f1;
+          J[2] = atu * S[4] * f2;
+          J[3] = atu * S[5] * f3;
+          J[4] = atu * (Bh - Bs) * sc4;
+          J[5] = tuv * Bm * sc5;
+          const float wr = wv * r;
+          const float wM = wv * atu * Bm;
+          acc[NH + P] = fmaf(wr, r, acc[NH + P]);
+          acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
+          acc[NH + P + 3] = fmaf(wM, wM, acc[NH + P + 3]);
+          acc[NH + P + 4] += wv;
+#pragma unroll
+          for (int a = 0; a < P; a++) {
+            acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
+            const float wj = wv * J[a];
+#pragma unroll
+            for (int b2 = a; b2 < P; b2++) acc[up<P>(a, b2)] = fmaf(wj, J[b2], acc[up<P>(a, b2)]);
+          }
+        }
+      }
+    }
+    parts[s * kPartStride + q * 32 + l] = reduce_scatter(acc, l);
+  }
+}
+
+// (4) the slot's totals: H, g and the floor to ne (as the FP32 evaluation),
+// cost, data cost and decrease to the caller
+__device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, float *ps,
+                                     const float (&xt)[6], float psc, float *ne, float &cst,
+                                     float &cd, float &drop) {
+  constexpr int NH = 21, P = 6;
+  float a = 0.f, b = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    a += ps[q * 32 + gp.sub];
+    b += ps[q * 32 + gp.sub + 16];
+  }
+  gp.sync();
+  ps[gp.sub] = a;
+  ps[gp.sub + 16] = b;
+  gp.sync();
+  float acc[32];
+#pragma unroll
+  for (int i = 0; i < 32; i++) acc[i] = ps[i];
+  cst = acc[NH + P];
+  cd = acc[NH + P + 1];
+  drop = acc[NH + P + 2];
+  float gfl[P];
+  const float m2 = acc[NH + P + 3] / fmaxf(acc[NH + P + 4], 1e-30f);
+#pragma unroll
+  for (int i = 0; i < P; i++) gfl[i] = kFloorC * sqrtf(acc[up<P>(i, i)] * m2);
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    float z = c.hi2[i] > c.lo2[i] ? 2.f * (xt[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
+    float pp = psc * c.pp2[i];
+    cst += pp * (z - c.pm2[i]) * (z - c.pm2[i]);
+    acc[NH + i] -= pp * (z - c.pm2[i]);
+    acc[up<P>(i, i)] += pp;
+  }
+#pragma unroll
+  for (int k = 0; k < NH + P; k++)
+    if ((k & (G - 1)) == gp.sub) ne[k] = acc[k];
+#pragma unroll
+  for (int i = 0; i < P; i++)
+    if (((30 + i) & (G - 1)) == gp.sub) ne[30 + i] = gfl[i];
+  gp.sync();
+}
+
+// CTA set-up: tables and Planck operand staged, coefficient operand zeroed,
+// the MMA mbarrier initialised, tensor memory allocated (128 columns per
+// band tile). Returns false (nothing allocated) if the staging timed out.
+struct Cta {
+  unsigned char *base;      // 1024-aligned: Planck operand, coefficient operand, slots, parts
+  float *slots, *parts;
+  int sstride, nbs, ntile, cols;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ bool setup(const LMLaunch &p, float *smem, unsigned long long *bar,
+                                      unsigned long long *mbar, uint32_t *tslot, Cta &C) {
+  const KTables &t = p.t;
+  const Lay L = layout(t);
+  const unsigned a = tc::su32(smem) + (unsigned)L.head_bytes;
+  C.base = reinterpret_cast<unsigned char *>(smem) + L.head_bytes + ((1024u - (a & 1023u)) & 1023u);
+  C.slots = reinterpret_cast<float *>(C.base + L.slots_off);
+  C.parts = reinterpret_cast<float *>(C.base + L.parts_off);
+  C.sstride = slot_floats(t);
+  C.nbs = band_slots(t.n2, G);
+  C.ntile = (t.n2 + 127) >> 7;
+  C.cols = C.ntile > 1 ? 256 : 128;
+  if (!stage_tables(t, smem, image_floats(t, 1), bar, p.w.err, C.base, t.plop,
+                    (unsigned)L.pl_bytes))
+    return false;
+  uint4 *co = reinterpret_cast<uint4 *>(C.base + L.pl_bytes);
+  for (int i = threadIdx.x; i < L.co_bytes / 16; i += blockDim.x) co[i] = make_uint4(0, 0, 0, 0);
+  for (int i = threadIdx.x; i < kSlots; i += blockDim.x)
+    C.slots[i * C.sstride + 5 * C.nbs + kNE2] = 0.f;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(tc::su32(tslot)), "r"(C.cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  C.tmem = *tslot;
+  return true;
+}
+
+// one CTA-wide evaluation round after the groups wrote their coefficients
+// (flag prm[0] set by every group); false if the MMA wait timed out
+__device__ __forceinline__ bool round(const KTables &t, Cta &C, unsigned long long *mbar,
+                                      unsigned &phase) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0)
+    mma(C.tmem, tc::su32(C.base), tc::su32(C.base + 3 * t.plrows * 128), t.plrows, C.ntile,
+        tc::su32(mbar));
+  const bool w = tc::mbar_wait(tc::su32(mbar), phase, kSpinMMA);
+  phase ^= 1u;
+  if (!__syncthreads_and(w)) return false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  band(t, C.tmem, C.slots, C.sstride, C.parts, C.nbs);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  return true;
+}
+
+// release: on a timed-out round, a bounded wait for the outstanding commit;
+// then tensor memory is freed
+__device__ __forceinline__ void release(const Cta &C, unsigned long long *mbar, unsigned phase,
+                                        bool ok, int *err) {
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    tc::mbar_wait(tc::su32(mbar), phase ^ 1u, kSpinMMA);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(C.tmem), "r"(C.cols));
+}
+
+// Planck operand: part p, row b (stage-2 band), node j at
+// p * plrows * 128 + swz(b, j / 8) + 2 (j % 8); zero outside n2 x nt
+__global__ void planck_operand_kernel(const KTables t, const float *image, unsigned char *out) {
+  const int nchunk = t.plrows * 8;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nchunk; e += gridDim.x * blockDim.x) {
+    const int b = e >> 3, c = e & 7;
+    uint32_t w[3][4];
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+      __nv_bfloat16 p[2][3];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int j = 8 * c + 2 * h + u;
+        const float v = (b < t.n2 && j < t.nt) ? image[t.lay.off_planck + j * t.lay.n2s + b] : 0.f;
+        split3(v, p[u][0], p[u][1], p[u][2]);
+      }
+#pragma unroll
+      for (int q = 0; q < 3; q++) w[q][h] = pack2(p[0][q], p[1][q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+      *reinterpret_cast<uint4 *>(out + (size_t)q * t.plrows * 128 + tc::swz(b, c)) =
+          make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+  }
+}
+}  // namespace tcs2
+
+// ---- stage 2 with the grid-node sums on the tensor cores: the fit of
+// lm_stage2_kernel (16 lanes per pixel, 8 warps), with the evaluation a
+// CTA-wide round (tcs2) so that the CTA's 16 pixels share one product
+template <int K>
+__global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_constant__ LMLaunch p) {
+  constexpr int G = tcs2::G;
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) unsigned long long bar, mbar;
+  __shared__ unsigned long long cstat[ST_COUNT];
+  __shared__ uint32_t tslot;
+  const KTables &t = p.t;
+  const KConfig &c = p.c;
+  const int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
+  tcs2::Cta C;
+  if (!tcs2::setup(p, smem, &bar, &mbar, &tslot, C)) return;
+  const Grp<G> gp(lane);
+  const int slot = threadIdx.x / G;
+  float *mine = C.slots + slot * C.sstride;
+  unsigned char *co = C.base + 3 * t.plrows * 128;
+  PixCtx pc;
+  pc.t = &t;
+  pc.c = &c;
+  pc.img = smem;
+  pc.node = nullptr;
+  pc.wvrow = t.wvtab;
+  Stage2<G> S;
+  S.nbs = C.nbs;
+  S.bb = mine;
+  float *ne = mine + 5 * S.nbs;   // trial H, g, gradient floor, then the proposal start
+  float *prm = ne + kNE2;
+  const long long n = p.s.n_pix;
+  const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
+  long long next = 0, end = 0, pix = 0;
+  bool active = false, done = false, first = false, alt = false, ok = true;
+  float x[6], xt[6], H[21], g[6], gf[6], cst = 0.f, cd = 0.f;
+  int rc = 0, nfull = 0, status = 0, n2u = 0;
+  unsigned phase = 0;
+  LMIter<6> L;
+  for (;;) {
+    while (!active && !done) {
+      if (next >= end) {
+        const long long b = claim(p.w.counter + 1, gp, nclaim);
+        if (b >= n) { done = true; break; }
+        next = b;
+        end = min(b + (long long)nclaim, n);
+      }
+      pix = next++;
+      const int meta = p.w.s1meta[pix];
+      if (!(meta & kFitted)) continue;
+      status = meta & 0xff;
+      const PixRef ref = resolve(p, pix, K);
+      pc.wvrow = t.wvtab + (size_t)ref.wv * t.nb;
+      float x1[K + 2];
+#pragma unroll
+      for (int i = 0; i < K + 2; i++) x1[i] = p.w.s1x[pix * (K + 2) + i];
+      float xs[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) xs[k] = x1[k];
+      n2u = setup2<K>(S, pc, gp, ref.row, xs);
+      const float T1 = x1[K + 1];
+      x[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
+      x[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
+      x[1] = fminf(fmaxf(c.init_sigma, c.lo2[1]), c.hi2[1]);
+      x[3] = fminf(fmaxf(c.init_sigma, c.lo2[3]), c.hi2[3]);
+      x[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
+      const float e = x[0] > x[2] ? (T1 - x[2]) / (x[0] - x[2]) : 0.5f;
+      x[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
+      alt = false;
+      const float *ini = ref.init;
+      if (ini) {
+        float xg[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) xg[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
+        if (p.s.init_best) {
+          if (gp.sub < 6) ne[40 + gp.sub] = pick(xg, gp.sub);
+          alt = true;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 6; i++) x[i] = xg[i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 6; i++) xt[i] = x[i];
+      L = LMIter<6>();
+#pragma unroll
+      for (int a = 0; a < 6; a++) L.act[a] = false;
+      first = true;
+      rc = 0;
+      nfull = 0;
+      active = true;
+    }
+    if (__syncthreads_and(done)) break;
+    bool go = active, probe = false;
+    if (active && !first) {
+      if (alt) {
+#pragma unroll
+        for (int i = 0; i < 6; i++) xt[i] = ne[40 + i];
+        alt = false;
+        probe = true;
+      } else {
+        go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
+      }
+    }
+    if (go) tcs2::coef(t, c, gp, x, xt, co, slot, prm, rc ^ 1);
+    if (gp.sub == 0) prm[0] = go ? 1.f : 0.f;
+    if (!tcs2::round(t, C, &mbar, phase)) { ok = false; break; }
+    if (go) {
+      float ct, cdt, drop;
+      tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, xt, S.psc, ne, ct, cdt, drop);
+      nfull++;
+      bool accept = first;
+      if (!first) {
+        drop += S.prior_drop(c, x, xt);
+        if (probe) {
+          accept = drop > 0.f;
+        } else {
+          const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
+          accept = rho > 0.f;
+          damping_update(L, accept, rho);
+          if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
+        }
+      }
+      if (accept) {
+#pragma unroll
+        for (int i = 0; i < 6; i++) x[i] = xt[i];
+#pragma unroll
+        for (int i = 0; i < 21; i++) H[i] = ne[i];
+#pragma unroll
+        for (int a = 0; a < 6; a++) {
+          g[a] = ne[21 + a];
+          gf[a] = ne[30 + a];
+        }
+        cst = ct;
+        cd = cdt;
+        rc ^= 1;
+      }
+      first = false;
+    }
+    if (active && !go) {
+      // ---- hand the final state and normal equations to the finalize kernel
+      if (L.used64) status |= PX_F_FP64;
+      status |= L.status;
+      float *hand = p.w.s2x + pix * kS2Hand;
+#pragma unroll
+      for (int k = 0; k < 32; k++) {
+        if ((k & (G - 1)) != gp.sub) continue;
+        float v;
+        if (k < 6) v = x[k];
+        else if (k < 27) v = H[k - 6];
+        else if (k == 27) v = cst;
+        else if (k == 28) v = cd;
+        else if (k == 29) v = __int_as_float(n2u);
+        else if (k == 30) v = __int_as_float(status | (L.it << 8));
+        else v = S.psc;
+        hand[k] = v;
+      }
+      if (gp.sub < 6) p.w.s2g[pix * 6 + gp.sub] = pick(g, gp.sub);
+      if (gp.sub == 0) {
+        atomicAdd(&cstat[ST_IT2], (unsigned long long)L.it);
+        atomicAdd(&cstat[ST_BAND2], (unsigned long long)nfull * (unsigned long long)t.n2);
+        atomicAdd(&cstat[ST_NODEBAND2],
+                  (unsigned long long)nfull * (unsigned long long)t.nt * (unsigned long long)t.n2);
+      }
+      active = false;
+    }
+  }
+  tcs2::release(C, &mbar, phase, ok, p.w.err);
+  for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
+    if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
+}
+
+// ---- one stage-2 evaluation per state through the tensor-core round (test
+// hook of the normal equations): 16 states per CTA and round
+template <int K>
+__global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_constant__ LMLaunch p,
+                                                              const float *states, float *Hout,
+                                                              float *gout, float *cost_out) {
+  constexpr int G = tcs2::G;
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) unsigned long long bar, mbar;
+  __shared__ uint32_t tslot;
+  const KTables &t = p.t;
+  const KConfig &c = p.c;
+  tcs2::Cta C;
+  if (!tcs2::setup(p, smem, &bar, &mbar, &tslot, C)) return;
+  const Grp<G> gp(threadIdx.x & 31);
+  const int slot = threadIdx.x / G;
+  float *mine = C.slots + slot * C.sstride;
+  unsigned char *co = C.base + 3 * t.plrows * 128;
+  PixCtx pc;
+  pc.t = &t;
+  pc.c = &c;
+  pc.img = smem;
+  pc.node = nullptr;
+  Stage2<G> S;
+  S.nbs = C.nbs;
+  S.bb = mine;
+  float *ne = mine + 5 * S.nbs;
+  float *prm = ne + kNE2;
+  unsigned phase = 0;
+  bool ok = true;
+  for (long long b0 = (long long)blockIdx.x * tcs2::kSlots; b0 < p.s.n_pix;
+       b0 += (long long)gridDim.x * tcs2::kSlots) {
+    const long long pix = b0 + slot;
+    const bool has = pix < p.s.n_pix;
+    float x[6];
+    if (has) {
+      pc.wvrow = t.wvtab + (size_t)min((int)p.s.wv[pix], t.nwv - 1) * t.nb;
+      float xs[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) xs[k] = states[pix * (K + 6) + k];
+#pragma unroll
+      for (int i = 0; i < 6; i++) x[i] = states[pix * (K + 6) + K + i];
+      setup2<K>(S, pc, gp, p.s.rad + pix * t.nb, xs);
+      tcs2::coef(t, c, gp, x, x, co, slot, prm, 1);
+    }
+    if (gp.sub == 0) prm[0] = has ? 1.f : 0.f;
+    if (!tcs2::round(t, C, &mbar, phase)) { ok = false; break; }
+    if (has) {
+      float cst, cd, drop;
+      tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, x, S.psc, ne, cst, cd, drop);
+      if (gp.sub == 0) {
+        for (int a = 0; a < 6; a++) {
+          gout[pix * 6 + a] = ne[21 + a];
+          for (int b = 0; b < 6; b++) Hout[pix * 36 + a * 6 + b] = ne[up<6>(a, b)];
+        }
+        cost_out[pix] = cst;
+      }
+    }
+    __syncthreads();
+  }
+  tcs2::release(C, &mbar, phase, ok, p.w.err);
+}
+
 // ---- finalize: moment matching (Sec. 2.3), FP64 Laplace covariance,
 // identifiability and the outputs of every fitted pixel; one thread per
 // pixel, so the FP64 work is not repeated across the lanes of a warp
@@ -1851,7 +2535,27 @@ cudaError_t launch_stage1(const LMLaunch &p, int num_sms, cudaStream_t st, int *
 }
 
 template <int K>
+cudaError_t launch_stage2_tc(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu) {
+  const size_t smem = (size_t)tcs2::layout(p.t).total;
+  cudaError_t e = cudaFuncSetAttribute(lm_stage2_tc_kernel<K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int cl = p.s.claim > 0 ? p.s.claim : kClaim;
+  const long long per_cta = (long long)tcs2::kSlots * cl;
+  long long blocks = (p.s.n_pix + per_cta - 1) / per_cta;
+  if (blocks > num_sms) blocks = num_sms;
+  if (blocks < 1) blocks = 1;
+  lm_stage2_tc_kernel<K><<<(int)blocks, tcs2::kWarps * 32, smem, st>>>(p);
+  if (bu) *bu += (int)blocks;
+  return cudaGetLastError();
+}
+
+template <int K>
 cudaError_t launch_stage2(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu, int v) {
+  if (v == 2) {
+    if (lm_tc_ok(p.t)) return launch_stage2_tc<K>(p, num_sms, st, bu);
+    v = 1;   // tables outside the tensor-core path: the FP32 shape of 16 lanes
+  }
   const Shape s = kShape2[v];
   if (v == 1) return launch_persistent(lm_stage2_kernel<K, 16, 8>, p, num_sms, st, bu, 2, s.G, s.maxw);
   return launch_persistent(lm_stage2_kernel<K, 32, 8>, p, num_sms, st, bu, 2, s.G, s.maxw);
@@ -1860,8 +2564,9 @@ cudaError_t launch_stage2(const LMLaunch &p, int num_sms, cudaStream_t st, int *
 template <int K>
 cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *blocks_used, int variant,
                      cudaEvent_t *ev) {
-  // variant = 3 * (stage-2 shape) + (stage-1 shape)
-  const int v1 = variant % 3, v2 = (variant / 3) % 2;
+  // variant = 3 * (stage-2 shape) + (stage-1 shape); stage-2 shape 2 is the
+  // tensor-core evaluation
+  const int v1 = variant % 3, v2 = (variant / 3) % 3;
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   if ((e = launch_stage1<K>(p, num_sms, st, blocks_used, v1)) != cudaSuccess) return e;
@@ -1879,7 +2584,17 @@ cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *block
 
 template <int K>
 cudaError_t launch_ne_k(const LMLaunch &p, int stage, const float *states, float *H, float *g,
-                        float *cost, cudaStream_t st) {
+                        float *cost, cudaStream_t st, int variant) {
+  if (stage == 2 && (variant / 3) % 3 == 2 && lm_tc_ok(p.t)) {
+    const size_t smem = (size_t)tcs2::layout(p.t).total;
+    cudaError_t e = cudaFuncSetAttribute(normal_eq_tc_kernel<K>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    long long blocks = (p.s.n_pix + tcs2::kSlots - 1) / tcs2::kSlots;
+    if (blocks > 1024) blocks = 1024;
+    normal_eq_tc_kernel<K><<<(int)blocks, tcs2::kWarps * 32, smem, st>>>(p, states, H, g, cost);
+    return cudaGetLastError();
+  }
   // the lanes per pixel of the default fit shapes
   auto go = [&](auto kern, int G, int maxw) {
     const int wpb = fit_warps(p.t, stage, G, maxw);
@@ -1898,6 +2613,19 @@ cudaError_t launch_ne_k(const LMLaunch &p, int stage, const float *states, float
 }
 
 }  // namespace
+
+size_t planck_operand_bytes(const KTables &t) { return (size_t)3 * t.plrows * 128; }
+
+cudaError_t launch_planck_operand(const KTables &t, unsigned char *out, cudaStream_t st) {
+  const int n = t.plrows * 8;
+  tcs2::planck_operand_kernel<<<(n + 255) / 256, 256, 0, st>>>(t, t.image, out);
+  return cudaGetLastError();
+}
+
+bool lm_tc_ok(const KTables &t) {
+  return t.plop && t.nt <= 64 && t.n2 <= 256 &&
+         (size_t)tcs2::layout(t).total <= kMaxSmemPerCta;
+}
 
 size_t lm_smem_bytes(const KTables &t, int) {
   // the smallest launch: one warp of the widest-group stage-2 shape
@@ -1923,11 +2651,11 @@ cudaError_t launch_merge_fallback(const long long *idx, const float *cost_first,
 }
 
 cudaError_t launch_normal_eq(const LMLaunch &p, int stage, const float *states, float *H, float *g,
-                             float *cost, cudaStream_t st) {
+                             float *cost, cudaStream_t st, int variant) {
   if (p.s.n_pix <= 0) return cudaSuccess;
   switch (p.t.K) {
-    case 3: return launch_ne_k<3>(p, stage, states, H, g, cost, st);
-    case 5: return launch_ne_k<5>(p, stage, states, H, g, cost, st);
+    case 3: return launch_ne_k<3>(p, stage, states, H, g, cost, st, variant);
+    case 5: return launch_ne_k<5>(p, stage, states, H, g, cost, st, variant);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -114,16 +114,17 @@ def test_claim_size_does_not_change_results(fr, torch, c1):
     ctx = fr.Context(t)
     Ld = _dev(torch, L[:1500], torch.float32)
     wd = _dev(torch, tr.wv_bin[:1500].astype(np.int16), torch.int16)
-    base = None
-    for claim in (1, 2, 8, 32):
-        ctx.set_tuning(0, claim)
-        o = _np(ctx.retrieve(Ld, wd))
-        if base is None:
-            base = o
-        else:
-            _same(base, o)
+    for variant in (0, 6):          # FP32 stage 2 with 32 lanes; tensor-core stage 2
+        base = None
+        for claim in (1, 2, 8, 32):
+            ctx.set_tuning(variant, claim)
+            o = _np(ctx.retrieve(Ld, wd))
+            if base is None:
+                base = o
+            else:
+                _same(base, o)
     with pytest.raises(fr.FireError):
-        ctx.set_tuning(6, 4)
+        ctx.set_tuning(9, 4)
 
 
 def test_autotune_picks_a_valid_shape_and_keeps_parity(fr, torch, c1):
@@ -133,10 +134,10 @@ def test_autotune_picks_a_valid_shape_and_keeps_parity(fr, torch, c1):
     wd = _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)
     best = ctx.autotune(Ld, wd)
     print("autotune:", best)
-    assert best["variant"] in range(6) and best["claim"] in (1, 2, 4, 8) and best["ms"] > 0
+    assert best["variant"] in range(9) and best["claim"] in (1, 2, 4, 8) and best["ms"] > 0
     idx = np.arange(1024)
     o = oracle.retrieve(t, L[idx], tr.wv_bin[idx])
-    for variant in range(6):
+    for variant in range(9):
         ctx.set_tuning(variant, 4)
         g = _np(ctx.retrieve(Ld[:1024], wd[:1024]))
         s = parity_stats(o, g)
