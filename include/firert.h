@@ -93,8 +93,12 @@ typedef struct {
   float tol_g;                      /* |g_i| <= tol_g sqrt(H_ii cost) */
   float tol_x;                      /* max |step| in z below tol_x */
   float tol_f;                      /* relative cost decrease below tol_f */
-  float kappa_max;                  /* condition estimate that switches the
-                                       step solve to FP64 */
+  float kappa_max;                  /* condition estimate (max L_ii / min
+                                       L_ii)^2 of the Jacobi-scaled damped
+                                       matrix above which the step is
+                                       re-solved in FP64 (default 1e6: the
+                                       FP32 solve's relative error bound
+                                       kappa 2^-24 stays below 6 %) */
   float dfloor;                     /* damping diagonal floor (relative) */
   float noise_rel, noise_abs;       /* noise model sd^2 = (rel L)^2 + abs^2 */
   int32_t weighted;                 /* 0: Eq. (loss) as printed; 1: 1/sd^2 */
@@ -153,7 +157,7 @@ typedef struct {
 typedef struct {
   uint64_t n_pixels, sum_it1, sum_it2, n_fp64_pixels;
   uint64_t band_evals1, band_evals2, node_band_evals2;  /* work units: full evaluations */
-  uint64_t trial_band_evals2, trial_node_band_evals2;   /* stage-2 decrease-only trials */
+  uint64_t solves64_1, solves64_2;  /* FP64 re-solves of ill-conditioned steps, per stage */
   uint64_t status_counts[8];
   double flops;                     /* algorithmic flops of the fit */
   double flops1, flops2;            /* ... of which stage 1 and stage 2 */

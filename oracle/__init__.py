@@ -116,7 +116,7 @@ class Config:
     tol_g: float = 1e-6
     tol_x: float = 1e-7
     tol_f: float = 1e-10
-    kappa_max: float = 1e5
+    kappa_max: float = 1e6
     dfloor: float = 1e-12
     noise_rel: float = 0.005
     noise_abs: float = 1e-4

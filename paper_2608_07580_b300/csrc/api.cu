@@ -296,7 +296,7 @@ void fire_default_config(fire_config_t *c) {
   c->tol_g = 1e-6f;
   c->tol_x = 1e-7f;
   c->tol_f = 1e-10f;
-  c->kappa_max = 1e5f;
+  c->kappa_max = 1e6f;
   c->dfloor = 1e-12f;
   c->noise_rel = 0.005f;
   c->noise_abs = 1e-4f;
@@ -664,8 +664,8 @@ fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   s->band_evals1 = v[ST_BAND1];
   s->band_evals2 = v[ST_BAND2];
   s->node_band_evals2 = v[ST_NODEBAND2];
-  s->trial_band_evals2 = v[ST_TRIAL2];
-  s->trial_node_band_evals2 = v[ST_TRIALNODE2];
+  s->solves64_1 = v[ST_S64_1];
+  s->solves64_2 = v[ST_S64_2];
   for (int k = 0; k < 8; k++) s->status_counts[k] = v[ST_STATUS0 + k];
   // algorithmic flops (FMA = 2): stage 1 per band and evaluation; stage 2 per
   // band and evaluation (Jacobian, normal equations, cost and its

@@ -96,10 +96,21 @@ __device__ __forceinline__ float em1_small(float y) {
 }
 
 // ------------------------------------------------------------- solve ----
+// reciprocal square root for the step solve: the SFU in FP32; in FP64 an FP32
+// seed and one Newton-Raphson step (2^-22 -> below 2^-43, past the FP32
+// rounding that the normal matrix itself carries)
+__device__ __forceinline__ float rsq_step(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq_step(double x) {
+  const double y = (double)rsqrtf((float)x);
+  return y * (1.5 - 0.5 * x * y * y);
+}
+
 // Solve (H + lam D) d = rhs over the free variables on the diagonally scaled
 // matrix; pinned variables are identity rows with their displacement moved
 // to the right-hand side. Returns false on a non-positive pivot. kap is the
-// condition estimate (max L_ii / min L_ii)^2 over the free variables.
+// condition estimate (max L_ii / min L_ii)^2 over the free variables. T is
+// the precision of the whole solve (FP32, or FP64 for an ill-conditioned
+// matrix; the FP32 inputs convert to FP64 exactly).
 template <int P, typename T>
 __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
                                              const float (&g)[P], float lam,
@@ -125,7 +136,7 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
   }
   // diagonal (Jacobi) scaling: unit diagonal, scaled right-hand side
 #pragma unroll
-  for (int i = 0; i < P; i++) rd[i] = rsq(A[i * (i + 1) / 2 + i]);
+  for (int i = 0; i < P; i++) rd[i] = rsq_step(A[i * (i + 1) / 2 + i]);
 #pragma unroll
   for (int i = 0; i < P; i++) {
     y[i] *= rd[i];
@@ -139,7 +150,7 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
 #pragma unroll
     for (int k = 0; k < j; k++) s -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
     ok = ok && (s > T(0));
-    T r = rsq(s > T(0) ? s : T(1));
+    T r = rsq_step(s > T(0) ? s : T(1));
     il[j] = r;                               // 1 / L_jj
     A[j * (j + 1) / 2 + j] = (s > T(0) ? s : T(1)) * r;
 #pragma unroll
@@ -151,15 +162,16 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
     }
   }
   if (!ok) return false;
-  T lmax = T(0), lmin = T(1e30);
+  // the condition estimate needs no more than FP32
+  float lmax = 0.f, lmin = 1e30f;
 #pragma unroll
   for (int i = 0; i < P; i++)
     if (!pin[i]) {
-      T l = A[i * (i + 1) / 2 + i];
-      lmax = l > lmax ? l : lmax;
-      lmin = l < lmin ? l : lmin;
+      const float l = (float)A[i * (i + 1) / 2 + i];
+      lmax = fmaxf(l, lmax);
+      lmin = fminf(l, lmin);
     }
-  kap = lmax > T(0) ? (float)(lmax * lmax) / (float)(lmin * lmin) : 1.f;
+  kap = lmax > 0.f ? (lmax * lmax) / (lmin * lmin) : 1.f;
 #pragma unroll
   for (int i = 0; i < P; i++) {
     T s = y[i];
@@ -207,7 +219,7 @@ __device__ __noinline__ bool solve_fp64(Solve64<P> &q) {
 template <int P>
 struct LMIter {
   float lam = -1.f, nu = 2.f, pred = 0.f;
-  int it = 0, status = PX_MAXITER;
+  int it = 0, status = PX_MAXITER, n64 = 0;   // n64: FP64 step solves
   bool fresh = true, used64 = false;
   bool act[P];
 };
@@ -294,6 +306,7 @@ __device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, c
 #pragma unroll
         for (int a = 0; a < P; a++) dr[a] = __shfl_sync(gp.mask, dr[a], lead);
         L.used64 = true;
+        L.n64++;
       }
       if (!ok) break;
       bool viol = false;
@@ -1435,6 +1448,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
         if (iters_out) iters_out[2 * opix] = (uint16_t)L.it;
         atomicAdd(&cstat[ST_BAND1], (unsigned long long)nfull * (unsigned long long)t.n1);
         atomicAdd(&cstat[ST_IT1], (unsigned long long)L.it);
+        atomicAdd(&cstat[ST_S64_1], (unsigned long long)L.n64);
         atomicAdd(&cstat[ST_NPIX], 1ull);
       }
       active = false;
@@ -1599,6 +1613,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       if (gp.sub < 6) p.w.s2g[pix * 6 + gp.sub] = pick(g, gp.sub);
       if (gp.sub == 0) {
         atomicAdd(&cstat[ST_IT2], (unsigned long long)L.it);
+        atomicAdd(&cstat[ST_S64_2], (unsigned long long)L.n64);
         atomicAdd(&cstat[ST_BAND2], (unsigned long long)nfull * (unsigned long long)t.n2);
         atomicAdd(&cstat[ST_NODEBAND2],
                   (unsigned long long)nfull * (unsigned long long)t.nt * (unsigned long long)t.n2);
@@ -1617,7 +1632,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
 // of each component times 1, d - dbar and d^2 - m2, and the mixture-weight
 // increment), are one dense product per CTA and round once the pixels of
 // the CTA evaluate together:
-//   D[band b][8 s + k] = sum_j Bgrid[b][j] C[8 s + k][j],
+//   D[band b][8 s + k'] = sum_j Bgrid[b][j] C[8 s + k'][j], k' = k (even s) or k ^ 4 (odd s),
 // M = 128 bands per tile (two tiles cover up to 256 bands), N = 16 pixel
 // slots x 8 coefficients, K = 64 nodes. Both operands are split into three
 // bf16 parts (x = x0 + x1 + x2, each part the bf16 rounding of what the
@@ -1746,12 +1761,15 @@ __device__ __forceinline__ void coef(const KTables &t, const KConfig &c, const G
       cf[e][6] = in ? eta * dwh + (1.f - eta) * dws + (eta - eo) * (uh[q] * rUho - us[q] * rUso) : 0.f;
     }
     const unsigned cc = (unsigned)(j0 & 7) * 2u;
+    // coefficient k of an odd slot goes to row k ^ 4 of the slot's eight, so
+    // that the two groups of a warp store to disjoint swizzled chunks
+    const int kx = (slot & 1) << 2;
 #pragma unroll
     for (int k = 0; k < 7; k++) {
       __nv_bfloat16 a0, a1, a2, b0, b1, b2;
       split3(cf[0][k], a0, a1, a2);
       split3(cf[1][k], b0, b1, b2);
-      const unsigned off = cob + tc::swz(8 * slot + k, j0 >> 3) + cc;
+      const unsigned off = cob + tc::swz(8 * slot + (k ^ kx), j0 >> 3) + cc;
       asm volatile("st.shared.b32 [%0], %1;" ::"r"(off), "r"(pack2(a0, b0)) : "memory");
       asm volatile("st.shared.b32 [%0], %1;" ::"r"(off + kCoPart), "r"(pack2(a1, b1)) : "memory");
       asm volatile("st.shared.b32 [%0], %1;" ::"r"(off + 2 * kCoPart), "r"(pack2(a2, b2)) : "memory");
@@ -1845,6 +1863,16 @@ __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slo
     tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(8 * s), v[0]);
     if (ntile > 1) tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 + 8 * s), v[1]);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (s & 1) {   // odd slots hold coefficient k in column k ^ 4
+#pragma unroll
+      for (int m = 0; m < 2; m++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          const float u = v[m][i];
+          v[m][i] = v[m][i + 4];
+          v[m][i + 4] = u;
+        }
+    }
     const float eta = prm[1], al = prm[2], da = prm[3];
     const float f0 = prm[4], f1 = prm[5], f2 = prm[6], f3 = prm[7], sc4 = prm[8], sc5 = prm[9];
     const int rn = prm[10] != 0.f ? 1 : 0;
@@ -2083,10 +2111,22 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
   int rc = 0, nfull = 0, status = 0, n2u = 0;
   unsigned phase = 0;
   LMIter<6> L;
+  // claim ahead: while a pixel is fitted, the group's first lane takes the
+  // group's next claim (its result is first read a round later), and the
+  // round after that the claimed pixels' inputs are prefetched into L2, so
+  // that the next set-up waits on neither the atomic nor HBM
+  unsigned long long pfb = 0;   // first lane: base index of the claim held in reserve
+  int pfs = 0;                  // 0: none held, 1: claimed, 2: prefetched
   for (;;) {
     while (!active && !done) {
       if (next >= end) {
-        const long long b = claim(p.w.counter + 1, gp, nclaim);
+        long long b;
+        if (pfs) {
+          b = gp.bcast((long long)pfb);
+          pfs = 0;
+        } else {
+          b = claim(p.w.counter + 1, gp, nclaim);
+        }
         if (b >= n) { done = true; break; }
         next = b;
         end = min(b + (long long)nclaim, n);
@@ -2135,6 +2175,30 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       rc = 0;
       nfull = 0;
       active = true;
+    }
+    if (active && next >= end) {
+      if (pfs == 0) {
+        if (gp.sub == 0) pfb = atomicAdd(p.w.counter + 1, (unsigned long long)nclaim);
+        pfs = 1;
+      } else if (pfs == 1) {
+        const long long b = gp.bcast((long long)pfb);
+        if (b < n && !p.s.items && !p.s.idx) {
+          // 11 lines per pixel: 8 of the stage-2 radiance window, the
+          // stage-1 status word, the stage-1 state and the WV bin
+          const long long e_end = min((long long)nclaim, n - b) * 11;
+          for (long long e = gp.sub; e < e_end; e += G) {
+            const long long q = b + e / 11;
+            const int l = (int)(e % 11);
+            const void *a;
+            if (l < 8) a = p.s.rad + q * t.nb + min(t.b2lo + 32 * l, t.nb - 1);
+            else if (l == 8) a = p.w.s1meta + q;
+            else if (l == 9) a = p.w.s1x + q * (K + 2);
+            else a = p.s.wv + q;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+          }
+        }
+        pfs = 2;
+      }
     }
     if (__syncthreads_and(done)) break;
     bool go = active, probe = false;
@@ -2204,6 +2268,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       if (gp.sub < 6) p.w.s2g[pix * 6 + gp.sub] = pick(g, gp.sub);
       if (gp.sub == 0) {
         atomicAdd(&cstat[ST_IT2], (unsigned long long)L.it);
+        atomicAdd(&cstat[ST_S64_2], (unsigned long long)L.n64);
         atomicAdd(&cstat[ST_BAND2], (unsigned long long)nfull * (unsigned long long)t.n2);
         atomicAdd(&cstat[ST_NODEBAND2],
                   (unsigned long long)nfull * (unsigned long long)t.nt * (unsigned long long)t.n2);
