@@ -189,6 +189,25 @@ def run_reference(args):
 PROFILED_TRAFFIC_PER_PX = {"lm_stage2_kernel": 309.10e6 / 262144, "lm_stage1_kernel": 316.68e6 / 262144}
 
 
+def tensor_figure(stats, n2, ms_per_fit, n_fits, peaks):
+    """bf16 tensor-core work of the tensor-core stage 2: each evaluation
+    round runs, per band tile of 128, six part products of M x N x K =
+    128 x TC_N x 64 (M bands, N pixel slots x 8 node coefficients, K 64
+    nodes). Executed flops over the kernel's event time, against the measured
+    bf16 GEMM peak (sustained: the kernel runs for hundreds of ms)."""
+    ntile = (n2 + 127) // 128
+    rounds = stats["mma_rounds2"] / max(n_fits, 1)
+    fl = rounds * ntile * 6 * 2.0 * 128 * TC_N * 64
+    peak = float(peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1400.0)
+    tf = fl / (ms_per_fit / 1e3) / 1e12
+    return {"rounds_per_fit": rounds, "bf16_flops_per_fit": fl, "tflops": tf, "peak": peak,
+            "frac": tf / peak, "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"
+            if peaks.get("bf16_tflops_sustained") else "fallback 1.4 PFLOP/s sustained"}
+
+
+TC_N = 128    # D columns per tensor-core round: 16 pixel slots x 8 node coefficients
+
+
 def mlp_init_figure(ctx, rad, wv_d, out, args, stream):
     """The same scene with the learned start: the network is trained on the
     GPU first (untimed), then each timed step runs inference, the LM from the
@@ -334,7 +353,9 @@ def main():
     avg_launch_s = float(np.mean(launch_ms)) / 1e3
     # per-kernel durations from the events the library records around each
     # kernel of every fit in the timed region; the dominant kernel's roofline
-    names = ("lm_stage1_kernel", "lm_stage2_kernel", "finalize_kernel")
+    tc2 = (tune["variant"] // 3) % 3 == 2     # stage 2 with the node sums on the tensor cores
+    names = ("lm_stage1_kernel", "lm_stage2_tc_kernel" if tc2 else "lm_stage2_kernel",
+             "finalize_kernel")
     per_ms = [m / max(n_fits, 1) for m in kern_ms]
     flops = (stats["flops1"], stats["flops2"], None)
     kdom = int(np.argmax(per_ms[:2]))
@@ -350,6 +371,8 @@ def main():
                                        "frac": flops[i] / (per_ms[i] / 1e3) / 1e12 / peak_tflops}
                                       if flops[i] else {})} for i in range(3)},
             "whole_fit_tflops": stats["flops"] / avg_launch_s / 1e12,
+            **({"stage2_tensor": tensor_figure(stats, ctx.window_bands()[3], per_ms[1], n_fits,
+                                               peaks)} if tc2 else {}),
             "hbm_gbs_equiv": (n * (t.n_bands * 4 + 2 + (3 + 8 + 21 + 7) * 4 + 5)) / avg_launch_s / 1e9}
 
     # end to end through the same C ABI with pinned host buffers

@@ -158,6 +158,7 @@ typedef struct {
   uint64_t n_pixels, sum_it1, sum_it2, n_fp64_pixels;
   uint64_t band_evals1, band_evals2, node_band_evals2;  /* work units: full evaluations */
   uint64_t solves64_1, solves64_2;  /* FP64 re-solves of ill-conditioned steps, per stage */
+  uint64_t mma_rounds2;             /* tensor-core stage 2: evaluation rounds (one product each) */
   uint64_t status_counts[8];
   double flops;                     /* algorithmic flops of the fit */
   double flops1, flops2;            /* ... of which stage 1 and stage 2 */

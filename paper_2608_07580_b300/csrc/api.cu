@@ -666,6 +666,7 @@ fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   s->node_band_evals2 = v[ST_NODEBAND2];
   s->solves64_1 = v[ST_S64_1];
   s->solves64_2 = v[ST_S64_2];
+  s->mma_rounds2 = v[ST_MMA2];
   for (int k = 0; k < 8; k++) s->status_counts[k] = v[ST_STATUS0 + k];
   // algorithmic flops (FMA = 2): stage 1 per band and evaluation; stage 2 per
   // band and evaluation (Jacobian, normal equations, cost and its

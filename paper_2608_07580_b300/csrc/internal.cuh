@@ -96,7 +96,7 @@ struct KOut {
 
 // device counters, indices into KWork::stats
 enum : int {
-  ST_NPIX = 0, ST_IT1, ST_IT2, ST_FP64, ST_BAND1, ST_BAND2, ST_NODEBAND2, ST_S64_1, ST_S64_2,
+  ST_NPIX = 0, ST_IT1, ST_IT2, ST_FP64, ST_BAND1, ST_BAND2, ST_NODEBAND2, ST_S64_1, ST_S64_2, ST_MMA2,
   ST_STATUS0,
   ST_COUNT = ST_STATUS0 + 8
 };

@@ -2117,6 +2117,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
   // that the next set-up waits on neither the atomic nor HBM
   unsigned long long pfb = 0;   // first lane: base index of the claim held in reserve
   int pfs = 0;                  // 0: none held, 1: claimed, 2: prefetched
+  unsigned long long nround = 0;
   for (;;) {
     while (!active && !done) {
       if (next >= end) {
@@ -2215,6 +2216,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
     if (go) tcs2::coef(t, c, gp, x, xt, co, slot, prm, rc ^ 1);
     if (gp.sub == 0) prm[0] = go ? 1.f : 0.f;
     if (!tcs2::round(t, C, &mbar, phase)) { ok = false; break; }
+    nround++;
     if (go) {
       float ct, cdt, drop;
       tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, xt, S.psc, ne, ct, cdt, drop);
@@ -2277,6 +2279,8 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
     }
   }
   tcs2::release(C, &mbar, phase, ok, p.w.err);
+  if (threadIdx.x == 0) atomicAdd(&cstat[ST_MMA2], nround);
+  __syncthreads();
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
     if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
 }

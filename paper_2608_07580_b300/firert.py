@@ -105,7 +105,7 @@ class Stats_t(C.Structure):
     _fields_ = [("n_pixels", C.c_uint64), ("sum_it1", C.c_uint64), ("sum_it2", C.c_uint64),
                 ("n_fp64_pixels", C.c_uint64), ("band_evals1", C.c_uint64),
                 ("band_evals2", C.c_uint64), ("node_band_evals2", C.c_uint64),
-                ("solves64_1", C.c_uint64), ("solves64_2", C.c_uint64),
+                ("solves64_1", C.c_uint64), ("solves64_2", C.c_uint64), ("mma_rounds2", C.c_uint64),
                 ("status_counts", C.c_uint64 * 8), ("flops", C.c_double),
                 ("flops1", C.c_double), ("flops2", C.c_double),
                 ("kernel_launches", C.c_int32)]
