@@ -205,7 +205,7 @@ def tensor_figure(stats, n2, ms_per_fit, n_fits, peaks):
             if peaks.get("bf16_tflops_sustained") else "fallback 1.4 PFLOP/s sustained"}
 
 
-TC_N = 128    # D columns per tensor-core round: 16 pixel slots x 8 node coefficients
+TC_N = 64     # D columns per tensor-core round: one cohort's 8 pixel slots x 8 node coefficients
 
 
 def mlp_init_figure(ctx, rad, wv_d, out, args, stream):

@@ -1655,7 +1655,13 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
 // quarters' partials.
 namespace tcs2 {
 constexpr int G = 16, kWarps = 8, kSlots = kWarps * 32 / G;   // 16 pixels per CTA
-constexpr int kN = kSlots * 8;            // D columns
+// two cohorts of 4 warps (one per TMEM lane quarter) and 8 pixel slots each,
+// with their own product, mbarrier and named barrier: a cohort waits only
+// for its own 8 pixels, and one cohort's CUDA-core work overlaps the other's
+// product
+constexpr int kCohorts = 2, kCoSlots = kSlots / kCohorts, kCoThreads = kWarps * 32 / kCohorts;
+constexpr int kN = kSlots * 8;            // coefficient rows
+constexpr int kNc = kCoSlots * 8;         // D columns of one cohort and band tile
 constexpr int kCoPart = kN * 128;         // bytes of one part of the coefficient operand
 constexpr int kPrm = 16;                  // per-slot parameters of the band phase
 constexpr int kPartStride = 4 * 32 + 16;  // per-slot partial sums [4 quarters][32], padded
@@ -1798,11 +1804,12 @@ __device__ __forceinline__ void coef(const KTables &t, const KConfig &c, const G
   if (gp.sub >= 1 && gp.sub <= 10) prm[gp.sub] = v;
 }
 
-// (2) the six part products, smallest first, for each band tile
+// (2) the six part products of one cohort (its 64 coefficient rows),
+// smallest first, for each band tile; D of tile m at column 64 m
 __device__ __forceinline__ void mma(uint32_t tmem, unsigned pl, unsigned co, int plrows, int ntile,
                                     unsigned bar) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  constexpr uint32_t idesc = tc::idesc_bf16(128, kN);
+  constexpr uint32_t idesc = tc::idesc_bf16(128, kNc);
   constexpr int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
   for (int m = 0; m < ntile; m++) {
 #pragma unroll
@@ -1815,7 +1822,7 @@ __device__ __forceinline__ void mma(uint32_t tmem, unsigned pl, unsigned co, int
         asm volatile(
             "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
-            ::"r"(tmem + (uint32_t)(128 * m)), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            ::"r"(tmem + (uint32_t)(kNc * m)), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
       }
   }
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -1848,7 +1855,8 @@ __device__ __forceinline__ float reduce_scatter(float (&v)[32], int l) {
   return v[0];
 }
 
-// (3) band phase: warp w, lane quarter q = w & 3, slots 8 (w >> 2) .. + 7
+// (3) band phase: warp w, lane quarter q = w & 3, slots 8 h .. 8 h + 7 of its
+// cohort h = w >> 2
 __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slots, int sstride,
                                      float *parts, int nbs) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, q = w & 3, h = w >> 2;
@@ -1860,8 +1868,10 @@ __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slo
     const float *prm = sb + 5 * nbs + kNE2;
     if (prm[0] == 0.f) continue;
     float v[2][8];
-    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(8 * s), v[0]);
-    if (ntile > 1) tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 + 8 * s), v[1]);
+    // the cohort's columns start at h * 64 * ntile; tile m at + 64 m
+    const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(h * kNc * ntile + 8 * (s - 8 * h));
+    tmem_ld8(ta, v[0]);
+    if (ntile > 1) tmem_ld8(ta + (uint32_t)kNc, v[1]);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (s & 1) {   // odd slots hold coefficient k in column k ^ 4
 #pragma unroll
@@ -1977,8 +1987,21 @@ struct Cta {
   uint32_t tmem;
 };
 
+// named barrier of a cohort's 128 threads (barrier 0 is the CTA's)
+__device__ __forceinline__ void co_sync(int h) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + h), "r"(kCoThreads) : "memory");
+}
+__device__ __forceinline__ bool co_and(int h, bool p) {
+  int r;
+  asm volatile(
+      "{ .reg .pred pi, po; setp.ne.s32 pi, %1, 0; bar.red.and.pred po, %2, %3, pi; selp.s32 %0, 1, 0, po; }"
+      : "=r"(r) : "r"((int)p), "r"(1 + h), "r"(kCoThreads) : "memory");
+  return r != 0;
+}
+
 __device__ __forceinline__ bool setup(const LMLaunch &p, float *smem, unsigned long long *bar,
                                       unsigned long long *mbar, uint32_t *tslot, Cta &C) {
+  // mbar: one per cohort
   const KTables &t = p.t;
   const Lay L = layout(t);
   const unsigned a = tc::su32(smem) + (unsigned)L.head_bytes;
@@ -1997,7 +2020,8 @@ __device__ __forceinline__ bool setup(const LMLaunch &p, float *smem, unsigned l
   for (int i = threadIdx.x; i < kSlots; i += blockDim.x)
     C.slots[i * C.sstride + 5 * C.nbs + kNE2] = 0.f;
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(mbar)));
+    for (int h = 0; h < kCohorts; h++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(mbar + h)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if ((threadIdx.x >> 5) == 0) {
@@ -2012,27 +2036,29 @@ __device__ __forceinline__ bool setup(const LMLaunch &p, float *smem, unsigned l
   return true;
 }
 
-// one CTA-wide evaluation round after the groups wrote their coefficients
-// (flag prm[0] set by every group); false if the MMA wait timed out
-__device__ __forceinline__ bool round(const KTables &t, Cta &C, unsigned long long *mbar,
+// one evaluation round of cohort h after its groups wrote their
+// coefficients (flag prm[0] set by every group); mbar is the cohort's;
+// false if the MMA wait timed out
+__device__ __forceinline__ bool round(const KTables &t, Cta &C, int h, unsigned long long *mbar,
                                       unsigned &phase) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  __syncthreads();
-  if (threadIdx.x == 0)
-    mma(C.tmem, tc::su32(C.base), tc::su32(C.base + 3 * t.plrows * 128), t.plrows, C.ntile,
-        tc::su32(mbar));
+  co_sync(h);
+  if (threadIdx.x == kCoThreads * h)
+    mma(C.tmem + (uint32_t)(h * kNc * C.ntile), tc::su32(C.base),
+        tc::su32(C.base + 3 * t.plrows * 128 + h * kNc * 128), t.plrows, C.ntile, tc::su32(mbar));
   const bool w = tc::mbar_wait(tc::su32(mbar), phase, kSpinMMA);
   phase ^= 1u;
-  if (!__syncthreads_and(w)) return false;
+  if (!co_and(h, w)) return false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   band(t, C.tmem, C.slots, C.sstride, C.parts, C.nbs);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  co_sync(h);
   return true;
 }
 
-// release: on a timed-out round, a bounded wait for the outstanding commit;
-// then tensor memory is freed
+// release (both cohorts): on a timed-out round, a bounded wait for the
+// cohort's outstanding commit (mbar is the cohort's); then tensor memory is
+// freed
 __device__ __forceinline__ void release(const Cta &C, unsigned long long *mbar, unsigned phase,
                                         bool ok, int *err) {
   if (!ok) {
@@ -2074,12 +2100,13 @@ __global__ void planck_operand_kernel(const KTables t, const float *image, unsig
 
 // ---- stage 2 with the grid-node sums on the tensor cores: the fit of
 // lm_stage2_kernel (16 lanes per pixel, 8 warps), with the evaluation a
-// CTA-wide round (tcs2) so that the CTA's 16 pixels share one product
+// round of each 4-warp cohort (tcs2) so that a cohort's 8 pixels share one
+// product
 template <int K>
 __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_constant__ LMLaunch p) {
   constexpr int G = tcs2::G;
   extern __shared__ __align__(128) float smem[];
-  __shared__ __align__(8) unsigned long long bar, mbar;
+  __shared__ __align__(8) unsigned long long bar, mbar[tcs2::kCohorts];
   __shared__ unsigned long long cstat[ST_COUNT];
   __shared__ uint32_t tslot;
   const KTables &t = p.t;
@@ -2087,7 +2114,8 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
   const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
   tcs2::Cta C;
-  if (!tcs2::setup(p, smem, &bar, &mbar, &tslot, C)) return;
+  if (!tcs2::setup(p, smem, &bar, mbar, &tslot, C)) return;
+  const int hc = threadIdx.x / tcs2::kCoThreads;   // cohort
   const Grp<G> gp(lane);
   const int slot = threadIdx.x / G;
   float *mine = C.slots + slot * C.sstride;
@@ -2201,7 +2229,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
         pfs = 2;
       }
     }
-    if (__syncthreads_and(done)) break;
+    if (tcs2::co_and(hc, done)) break;
     bool go = active, probe = false;
     if (active && !first) {
       if (alt) {
@@ -2215,7 +2243,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
     }
     if (go) tcs2::coef(t, c, gp, x, xt, co, slot, prm, rc ^ 1);
     if (gp.sub == 0) prm[0] = go ? 1.f : 0.f;
-    if (!tcs2::round(t, C, &mbar, phase)) { ok = false; break; }
+    if (!tcs2::round(t, C, hc, &mbar[hc], phase)) { ok = false; break; }
     nround++;
     if (go) {
       float ct, cdt, drop;
@@ -2278,8 +2306,8 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       active = false;
     }
   }
-  tcs2::release(C, &mbar, phase, ok, p.w.err);
-  if (threadIdx.x == 0) atomicAdd(&cstat[ST_MMA2], nround);
+  tcs2::release(C, &mbar[hc], phase, ok, p.w.err);
+  if (threadIdx.x % tcs2::kCoThreads == 0) atomicAdd(&cstat[ST_MMA2], nround);
   __syncthreads();
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x)
     if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
@@ -2293,12 +2321,13 @@ __global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_const
                                                               float *gout, float *cost_out) {
   constexpr int G = tcs2::G;
   extern __shared__ __align__(128) float smem[];
-  __shared__ __align__(8) unsigned long long bar, mbar;
+  __shared__ __align__(8) unsigned long long bar, mbar[tcs2::kCohorts];
   __shared__ uint32_t tslot;
   const KTables &t = p.t;
   const KConfig &c = p.c;
   tcs2::Cta C;
-  if (!tcs2::setup(p, smem, &bar, &mbar, &tslot, C)) return;
+  if (!tcs2::setup(p, smem, &bar, mbar, &tslot, C)) return;
+  const int hc = threadIdx.x / tcs2::kCoThreads;   // cohort
   const Grp<G> gp(threadIdx.x & 31);
   const int slot = threadIdx.x / G;
   float *mine = C.slots + slot * C.sstride;
@@ -2331,7 +2360,7 @@ __global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_const
       tcs2::coef(t, c, gp, x, x, co, slot, prm, 1);
     }
     if (gp.sub == 0) prm[0] = has ? 1.f : 0.f;
-    if (!tcs2::round(t, C, &mbar, phase)) { ok = false; break; }
+    if (!tcs2::round(t, C, hc, &mbar[hc], phase)) { ok = false; break; }
     if (has) {
       float cst, cd, drop;
       tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, x, S.psc, ne, cst, cd, drop);
@@ -2343,9 +2372,9 @@ __global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_const
         cost_out[pix] = cst;
       }
     }
-    __syncthreads();
+    tcs2::co_sync(hc);
   }
-  tcs2::release(C, &mbar, phase, ok, p.w.err);
+  tcs2::release(C, &mbar[hc], phase, ok, p.w.err);
 }
 
 // ---- finalize: moment matching (Sec. 2.3), FP64 Laplace covariance,
