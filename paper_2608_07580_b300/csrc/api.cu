@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "../../include/firert.h"
@@ -360,6 +361,8 @@ const char *fire_status_str(fire_status_t s) {
 
 void fire_ctx_destroy(fire_ctx_t *ctx) {
   if (!ctx) return;
+  for (cudaEvent_t e : ctx->chunk_ev) cudaEventDestroy(e);
+  if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
   cudaFree(ctx->d_image);
   cudaFree(ctx->d_plop);
   cudaFree(ctx->d_wvtab);
@@ -510,6 +513,11 @@ fire_status_t fire_window_bands(fire_ctx_t *c, int32_t *b1lo, int32_t *n1, int32
   return FIRE_OK;
 }
 
+// host scenes of at least two minimum chunks are fitted in up to kChunks
+// chunks, the copies of each overlapping the fits of the others
+static constexpr int64_t kChunkMin = 65536;
+static constexpr int kChunks = 4;
+
 fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_priors_t *pri,
                             const fire_outputs_t *out, fire_stream_t stream) {
   if (!c || !sc || !out) return FIRE_ERR_ARG;
@@ -584,9 +592,6 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   float *o_rms = (float *)carve(szf), *o_hfdi = (float *)carve(szf), *o_cov = (float *)carve(s_cov);
   uint8_t *o_status = (uint8_t *)carve(s_u8);
   uint16_t *o_it = (uint16_t *)carve(s_it);
-  CK(cudaMemcpyAsync(d_rad, sc->radiance, s_rad, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(d_wv, sc->wv_bin, s_wv, cudaMemcpyHostToDevice, st));
-  if (d_init) CK(cudaMemcpyAsync(d_init, pri->init_state, s_init, cudaMemcpyHostToDevice, st));
   p.s.rad = d_rad;
   p.s.wv = d_wv;
   p.s.init = d_init;
@@ -606,6 +611,86 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     p.o.cost = o_cost;
     p.o.status = o_status;
   }
+  if (!learned && n >= 2 * kChunkMin) {
+    // plain or given start: the scene in chunks whose copies overlap the
+    // fits of the others; each pixel's fit is independent of the chunking,
+    // so the results are those of one launch bit for bit
+    const int64_t cs = std::max<int64_t>(kChunkMin, (n + kChunks - 1) / kChunks);
+    const int nch = (int)((n + cs - 1) / cs);
+    if (!c->copy_st) CK(cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
+    while ((int)c->chunk_ev.size() < 2 * nch + 2) {
+      cudaEvent_t e;
+      CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      c->chunk_ev.push_back(e);
+    }
+    cudaEvent_t *ev_in = c->chunk_ev.data(), *ev_fit = ev_in + nch;
+    cudaEvent_t ev_start = ev_in[2 * nch], ev_done = ev_in[2 * nch + 1];
+    cudaStream_t cp = c->copy_st;
+    // the copies start after the caller's earlier work on the staging buffer
+    CK(cudaEventRecord(ev_start, st));
+    CK(cudaStreamWaitEvent(cp, ev_start, 0));
+    for (int i = 0; i < nch; i++) {
+      const int64_t a = i * cs, m = std::min(cs, n - a);
+      CK(cudaMemcpyAsync(d_rad + a * c->t.nb, sc->radiance + a * c->t.nb, (size_t)m * c->t.nb * 4,
+                         cudaMemcpyHostToDevice, cp));
+      CK(cudaMemcpyAsync(d_wv + a, sc->wv_bin + a, (size_t)m * 2, cudaMemcpyHostToDevice, cp));
+      if (d_init)
+        CK(cudaMemcpyAsync(d_init + a * NS, pri->init_state + a * NS, (size_t)m * NS * 4,
+                           cudaMemcpyHostToDevice, cp));
+      CK(cudaEventRecord(ev_in[i], cp));
+    }
+    int blocks = 0;
+    c->last_launches = 0;
+    for (int i = 0; i < nch; i++) {
+      const int64_t a = i * cs, m = std::min(cs, n - a);
+      LMLaunch q = p;
+      q.s.n_pix = m;
+      q.s.rad = d_rad + a * c->t.nb;
+      q.s.wv = d_wv + a;
+      q.s.init = d_init ? d_init + a * NS : nullptr;
+      auto off = [&](auto *ptr, int64_t w) { return ptr ? ptr + a * w : ptr; };
+      q.o.state = off(p.o.state, NS);
+      q.o.ET = off(p.o.ET, 1);
+      q.o.sdT = off(p.o.sdT, 1);
+      q.o.alpha = off(p.o.alpha, 1);
+      q.o.var_ET = off(p.o.var_ET, 1);
+      q.o.cost = off(p.o.cost, 1);
+      q.o.rms = off(p.o.rms, 1);
+      q.o.hfdi = off(p.o.hfdi, 1);
+      q.o.cov = off(p.o.cov, 21);
+      q.o.status = off(p.o.status, 1);
+      q.o.iters = off(p.o.iters, 2);
+      CK(cudaStreamWaitEvent(st, ev_in[i], 0));
+      CK(cudaMemsetAsync(c->d_work, 0, 2 * 8, st));   // claim counters; statistics accumulate
+      CK(launch_lm(q, c->num_sms, st, &blocks, c->tune_variant));
+      c->last_launches += 3;
+      CK(cudaEventRecord(ev_fit[i], st));
+      CK(cudaStreamWaitEvent(cp, ev_fit[i], 0));
+      struct { void *h; void *d; size_t b; } back[] = {
+          {out->state, q.o.state, (size_t)m * NS * 4}, {out->ET, q.o.ET, (size_t)m * 4},
+          {out->sdT, q.o.sdT, (size_t)m * 4}, {out->alpha, q.o.alpha, (size_t)m * 4},
+          {out->var_ET, q.o.var_ET, (size_t)m * 4}, {out->cost, q.o.cost, (size_t)m * 4},
+          {out->rms, q.o.rms, (size_t)m * 4}, {out->hfdi, q.o.hfdi, (size_t)m * 4},
+          {out->cov, q.o.cov, (size_t)m * 21 * 4}, {out->status, q.o.status, (size_t)m},
+          {out->iters, q.o.iters, (size_t)m * 4}};
+      const size_t eo[] = {(size_t)a * NS * 4, (size_t)a * 4, (size_t)a * 4, (size_t)a * 4,
+                           (size_t)a * 4, (size_t)a * 4, (size_t)a * 4, (size_t)a * 4,
+                           (size_t)a * 21 * 4, (size_t)a, (size_t)a * 4};
+      for (int k = 0; k < 11; k++)
+        if (back[k].h)
+          CK(cudaMemcpyAsync((char *)back[k].h + eo[k], back[k].d, back[k].b,
+                             cudaMemcpyDeviceToHost, cp));
+    }
+    CK(cudaEventRecord(ev_done, cp));
+    CK(cudaStreamWaitEvent(st, ev_done, 0));
+    CK(cudaStreamSynchronize(st));
+    int err = 0;
+    CK(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return err ? FIRE_ERR_TIMEOUT : FIRE_OK;
+  }
+  CK(cudaMemcpyAsync(d_rad, sc->radiance, s_rad, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_wv, sc->wv_bin, s_wv, cudaMemcpyHostToDevice, st));
+  if (d_init) CK(cudaMemcpyAsync(d_init, pri->init_state, s_init, cudaMemcpyHostToDevice, st));
   {
     fire_status_t e = run_fit(c, p, learned, st);
     if (e != FIRE_OK) return e;

@@ -48,6 +48,10 @@ struct fire_ctx {
   // per-kernel timing: 4 events per fit launch, summed on request
   bool timing = false;
   std::vector<cudaEvent_t> tev;
+  // host scenes: a copy stream and per-chunk events, so that the copies of
+  // one chunk overlap the fit of another (created on first use)
+  cudaStream_t copy_st = nullptr;
+  std::vector<cudaEvent_t> chunk_ev;
   size_t tev_used = 0;
 };
 

@@ -190,6 +190,26 @@ def test_host_path_equals_device_path_and_is_deterministic(fr, torch, c1):
             else np.array_equal(g1[k], hk), k
 
 
+def test_chunked_host_path_equals_device_path(fr, torch):
+    """A host scene of 153,600 pixels is fitted in chunks whose copies overlap
+    the fits of the other chunks (three chunks, the last one ragged): every
+    output equals the device path's bit for bit."""
+    t = synth.make_tables()
+    tr = synth.make_config2_truth(seed=5, width=256, height=600)
+    ctx = fr.Context(t)
+    st = torch.from_numpy(tr.state2().astype(np.float32)).cuda()
+    wv = torch.from_numpy(tr.wv_bin.astype(np.int16)).cuda()
+    rad = ctx.forward(2, st, wv, NOISE_REL, NOISE_ABS, seed=tr.seed, stream_id=synth.STREAM_NOISE)
+    g = {k: v.cpu().numpy() for k, v in ctx.retrieve(rad, wv).items()}
+    L = np.ascontiguousarray(rad.cpu().numpy())
+    h = ctx.retrieve(L, tr.wv_bin)
+    assert ctx.stats()["kernel_launches"] == 9        # three chunks x three kernels
+    for k in ("ET", "sdT", "alpha", "state", "cov", "cost", "status", "iters", "hfdi"):
+        hk = h[k].astype(g[k].dtype) if k == "iters" else h[k]
+        assert np.array_equal(g[k], hk, equal_nan=True) if g[k].dtype.kind == "f" \
+            else np.array_equal(g[k], hk), k
+
+
 def test_given_init_matches_oracle(fr, torch, c1):
     """A given start (the truth, written in the mixture's form: the single
     temperature as the hot mean above 1000 K, else as the smouldering mean)
