@@ -1314,22 +1314,11 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
   float x[NX], xt[NX], H[NH], g[P], gf[P], cst = 0.f;
   int m = 0, rc = 0, nfull = 0, status = 0;
   LMIter<P> L;
-  // claim ahead (as in the tensor-core stage 2): the group's next claim is
-  // taken while a pixel is fitted, and its radiance rows are prefetched into
-  // L2 a round later
-  unsigned long long pfb = 0;   // first lane: base index of the claim held in reserve
-  int pfs = 0;                  // 0: none held, 1: claimed, 2: prefetched
   for (;;) {
     // ---- take pixels until one is to be fitted
     while (!active && !done) {
       if (next >= end) {
-        long long b;
-        if (pfs) {
-          b = gp.bcast((long long)pfb);
-          pfs = 0;
-        } else {
-          b = claim(p.w.counter, gp, nclaim);
-        }
+        const long long b = claim(p.w.counter, gp, nclaim);
         if (b >= n) { done = true; break; }
         next = b;
         end = min(b + (long long)nclaim, n);
@@ -1409,26 +1398,6 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
           atomicAdd(&cstat[ST_STATUS0 + (status & 7)], 1ull);
           atomicAdd(&cstat[ST_NPIX], 1ull);
         }
-      }
-    }
-    if (active && next >= end) {
-      if (pfs == 0) {
-        if (gp.sub == 0) pfb = atomicAdd(p.w.counter, (unsigned long long)nclaim);
-        pfs = 1;
-      } else if (pfs == 1) {
-        const long long b = gp.bcast((long long)pfb);
-        if (b < n && !p.s.items && !p.s.idx) {
-          // 10 lines per pixel: the radiance row (9 lines of 128 B) and the WV bin
-          const long long e_end = min((long long)nclaim, n - b) * 10;
-          for (long long e = gp.sub; e < e_end; e += G) {
-            const long long q = b + e / 10;
-            const int l = (int)(e % 10);
-            const void *a = l < 9 ? (const void *)(p.s.rad + q * t.nb + min(32 * l, t.nb - 1))
-                                  : (const void *)(p.s.wv + q);
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-          }
-        }
-        pfs = 2;
       }
     }
     if (__all_sync(kFull, done)) break;
@@ -1679,11 +1648,11 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
 // 8 rows of the coefficient operand; (2) one thread issues the MMAs and
 // commits them to an mbarrier; (3) with the sums in tensor memory, warp w
 // reads lane quarter w & 3 (32 bands of each tile) and forms, for the 8
-// pixel slots of its cohort, each band's residual, Jacobian row and
+// pixel slots of its half, each band's residual, Jacobian row and
 // contributions to J^T W J, J^T W r, the cost and the increment-form
-// decrease; the warp's 32 sums go through a shared-memory tile, lane l
-// adding column l, and are written as the quarter's partial; (4) each group
-// adds its four quarters' partials.
+// decrease; a reduce-scatter across the warp leaves one of the 32 sums per
+// lane, written as the quarter's partial; (4) each group adds its four
+// quarters' partials.
 namespace tcs2 {
 constexpr int G = 16, kWarps = 8, kSlots = kWarps * 32 / G;   // 16 pixels per CTA
 // two cohorts of 4 warps (one per TMEM lane quarter) and 8 pixel slots each,
@@ -1870,34 +1839,27 @@ __device__ __forceinline__ void tmem_ld8(uint32_t ta, float (&v)[8]) {
   for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// (3) band phase: warp w, lane quarter q = w & 3, slots 8 h .. 8 h + 7 of its
-// cohort h = w >> 2
-// Warp total of 32 values through shared memory: each lane stores its 32
-// values as a row of a 32 x 32 tile (16-byte chunks XOR-swizzled by the row,
-// so that stores and column reads are free of bank conflicts), then lane l
-// adds column l. tile: 4 KB of this warp's own.
-__device__ __forceinline__ float column_sum(const float (&v)[32], int l, float *tile) {
+// reduce-scatter of 32 values over the warp: lane l returns the warp total
+// of value l
+__device__ __forceinline__ float reduce_scatter(float (&v)[32], int l) {
 #pragma unroll
-  for (int c4 = 0; c4 < 8; c4++)
-    *reinterpret_cast<float4 *>(tile + 32 * l + 4 * ((c4 ^ l) & 7)) =
-        make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
-  __syncwarp();
-  float r = 0.f;
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool hi = (l & o) != 0;
 #pragma unroll
-  for (int row = 0; row < 32; row++) r += tile[32 * row + 4 * (((l >> 2) ^ row) & 7) + (l & 3)];
-  __syncwarp();
-  return r;
+    for (int i = 0; i < o; i++) {
+      const float send = hi ? v[i] : v[i + o];
+      const float keep = hi ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  return v[0];
 }
 
+// (3) band phase: warp w, lane quarter q = w & 3, slots 8 h .. 8 h + 7 of its
+// cohort h = w >> 2
 __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slots, int sstride,
-                                     float *parts, int nbs, unsigned char *co) {
+                                     float *parts, int nbs) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, q = w & 3, h = w >> 2;
-  // reduction tile: the cohort's own rows of coefficient-operand parts 1 and
-  // 2 (8 KB each), free from the completion of its product until its next
-  // coefficients; part 0 is left alone, as the last Planck part's tile-1
-  // rows beyond the bands read into it
-  float *tile = reinterpret_cast<float *>(co + (1 + (q >> 1)) * kCoPart + h * kNc * 128 +
-                                          (q & 1) * 4096);
   const int ntile = (t.n2 + 127) >> 7;
   constexpr int NH = 21, P = 6;
 #pragma unroll 1
@@ -1968,7 +1930,7 @@ __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slo
         }
       }
     }
-    parts[s * kPartStride + q * 32 + l] = column_sum(acc, l, tile);
+    parts[s * kPartStride + q * 32 + l] = reduce_scatter(acc, l);
   }
 }
 
@@ -2088,7 +2050,7 @@ __device__ __forceinline__ bool round(const KTables &t, Cta &C, int h, unsigned 
   phase ^= 1u;
   if (!co_and(h, w)) return false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  band(t, C.tmem, C.slots, C.sstride, C.parts, C.nbs, C.base + 3 * t.plrows * 128);
+  band(t, C.tmem, C.slots, C.sstride, C.parts, C.nbs);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   co_sync(h);
   return true;
