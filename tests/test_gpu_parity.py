@@ -266,3 +266,46 @@ def test_normal_equations_match_oracle(fr, torch, c1, stage, variant):
         assert e[0] < 2e-4 and e[1] < 2e-4 and e[2] < 1e-4, (stage, variant, i, e)
     print(f"stage {stage} variant {variant}: max rel. error H {worst[0]:.2e} g {worst[1]:.2e} "
           f"cost {worst[2]:.2e}")
+
+
+@pytest.fixture(scope="module")
+def small_tables_scene():
+    # 160 bands put 120 bands in the stage-2 window (one 128-band tile of the
+    # tensor-core product); a 40-node grid leaves 24 of the product's 64
+    # nodes as zero padding
+    return config1(seed=7, width=48, height=48, n_bands=160, n_tgrid=40)
+
+
+@pytest.mark.parametrize("variant", [3, 6])
+def test_other_table_shapes_match_oracle(fr, torch, small_tables_scene, variant):
+    """Tables other than the default 284 bands x 64 nodes, through the FP32
+    (3) and the tensor-core (6) stage-2 evaluation: one evaluation's normal
+    equations at random states, and the retrieval, against the oracle."""
+    t, tr, L = small_tables_scene
+    ctx = fr.Context(t)
+    ctx.set_tuning(variant, 1)
+    assert ctx.window_bands()[3] <= 128
+    rng = np.random.default_rng(31)
+    idx = np.concatenate([np.flatnonzero(tr.kind == 1)[:24], rng.choice(tr.n_pix, 16, replace=False)])
+    n = idx.size
+    st = np.column_stack([rng.dirichlet(np.ones(3), n), rng.uniform(950, 2100, n),
+                          rng.uniform(60, 400, n), rng.uniform(380, 990, n),
+                          rng.uniform(60, 400, n), rng.uniform(0.05, 0.95, n),
+                          10 ** rng.uniform(-3.5, -0.5, n)]).astype(np.float32)
+    H, g, cost = ctx.normal_equations(2, _dev(torch, L[idx], torch.float32),
+                                      _dev(torch, tr.wv_bin[idx].astype(np.int16), torch.int16),
+                                      _dev(torch, st, torch.float32))
+    H, g, cost = H.cpu().numpy(), g.cpu().numpy(), cost.cpu().numpy()
+    for j, i in enumerate(idx):
+        Ho, go, co = oracle.normal_equations(t, 2, L[i], tr.wv_bin[i], st[j].astype(np.float64))
+        d = np.sqrt(np.outer(np.diag(Ho), np.diag(Ho)))
+        e = (np.max(np.abs(H[j] - Ho) / d), np.max(np.abs(g[j] - go) / np.sqrt(np.diag(Ho) * co)),
+             abs(cost[j] - co) / co)
+        assert e[0] < 2e-4 and e[1] < 2e-4 and e[2] < 1e-4, (variant, i, e)
+    o = oracle.retrieve(t, L, tr.wv_bin)
+    out = _np(ctx.retrieve(_dev(torch, L, torch.float32),
+                           _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)))
+    s = parity_stats(o, out)
+    print(f"variant {variant}:", {k: v for k, v in s.items() if k != "fail_idx"})
+    assert s["pool"] >= 0.8 * s["oracle_conv_ident"] and s["pool"] >= 15
+    assert s["rate"] >= 0.97
