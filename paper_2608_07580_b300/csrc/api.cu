@@ -513,10 +513,14 @@ fire_status_t fire_window_bands(fire_ctx_t *c, int32_t *b1lo, int32_t *n1, int32
   return FIRE_OK;
 }
 
-// host scenes of at least two minimum chunks are fitted in up to kChunks
-// chunks, the copies of each overlapping the fits of the others
+// host scenes of at least two minimum chunks are fitted in chunks whose
+// copies overlap the fits of the others: a small first chunk (its copy is
+// the only one nothing overlaps), larger middle ones, and a small last one
+// (its outputs are the only ones copied back after the last fit); sixteenths
+// of the scene, no chunk under kChunkMin pixels
 static constexpr int64_t kChunkMin = 65536;
-static constexpr int kChunks = 4;
+static constexpr int kChunks = 5;
+static constexpr int kChunkSixteenths[kChunks] = {1, 3, 5, 5, 2};
 
 fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_priors_t *pri,
                             const fire_outputs_t *out, fire_stream_t stream) {
@@ -615,8 +619,15 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     // plain or given start: the scene in chunks whose copies overlap the
     // fits of the others; each pixel's fit is independent of the chunking,
     // so the results are those of one launch bit for bit
-    const int64_t cs = std::max<int64_t>(kChunkMin, (n + kChunks - 1) / kChunks);
-    const int nch = (int)((n + cs - 1) / cs);
+    int64_t c0[kChunks + 1];
+    int nch = 0;
+    c0[0] = 0;
+    for (int k = 0; k < kChunks && c0[nch] < n; k++) {
+      int64_t m = std::max<int64_t>(kChunkMin, n * kChunkSixteenths[k] / 16);
+      if (n - c0[nch] - m < kChunkMin || k == kChunks - 1) m = n - c0[nch];   // the rest
+      c0[nch + 1] = c0[nch] + m;
+      nch++;
+    }
     if (!c->copy_st) CK(cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
     while ((int)c->chunk_ev.size() < 2 * nch + 2) {
       cudaEvent_t e;
@@ -630,7 +641,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     CK(cudaEventRecord(ev_start, st));
     CK(cudaStreamWaitEvent(cp, ev_start, 0));
     for (int i = 0; i < nch; i++) {
-      const int64_t a = i * cs, m = std::min(cs, n - a);
+      const int64_t a = c0[i], m = c0[i + 1] - c0[i];
       CK(cudaMemcpyAsync(d_rad + a * c->t.nb, sc->radiance + a * c->t.nb, (size_t)m * c->t.nb * 4,
                          cudaMemcpyHostToDevice, cp));
       CK(cudaMemcpyAsync(d_wv + a, sc->wv_bin + a, (size_t)m * 2, cudaMemcpyHostToDevice, cp));
@@ -642,7 +653,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     int blocks = 0;
     c->last_launches = 0;
     for (int i = 0; i < nch; i++) {
-      const int64_t a = i * cs, m = std::min(cs, n - a);
+      const int64_t a = c0[i], m = c0[i + 1] - c0[i];
       LMLaunch q = p;
       q.s.n_pix = m;
       q.s.rad = d_rad + a * c->t.nb;
