@@ -426,7 +426,7 @@ struct Grp {
 // groups of a warp, reading the same slot or node, hit different banks.
 __host__ __device__ __forceinline__ int band_slots(int n, int G) { return G * ((n + G - 1) / G); }
 __host__ __device__ __forceinline__ int pix_stride1(const KTables &t, int G) {
-  int f = 8 * band_slots(t.n1, G);
+  int f = 4 * band_slots(t.n1, G);
   return f + ((G - f % 32) % 32 + 32) % 32;
 }
 constexpr int kNE2 = 48;   // stage-2 per-pixel slot: trial H[21], g[6], floor[6] at 30, proposal x[6] at 40
@@ -437,6 +437,12 @@ __host__ __device__ __forceinline__ int pix_stride2(const KTables &t, int G) {
 // table-image floats a stage needs: stage 1 stops before the Planck grid
 __host__ __device__ __forceinline__ int image_floats(const KTables &t, int stage) {
   return stage == 1 ? ((t.lay.off_planck + 3) & ~3) : t.lay.total;
+}
+// the water-vapour table [nwv][nb] float4, staged in shared memory by stage 1
+// when it takes at most 96 KB (16 bins x 284 bands: 71 KB), else read from
+// global memory
+__host__ __device__ __forceinline__ int wvtab_floats(const KTables &t) {
+  return t.nwv * t.nb * 16 <= 96 * 1024 ? t.nwv * t.nb * 4 : 0;
 }
 
 // ------------------------------------------------------- pixel context --
@@ -452,9 +458,8 @@ struct PixCtx {
 template <int K, int G>
 struct Stage1 {
   static constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2, GL = G;
-  // band buffers in shared memory, [8][nbs]: observed radiance, weight,
-  // and for the current and the trial state (index rc, rc ^ 1) the residual,
-  // the Planck factor B(lambda_b, T1) and 1 / (1 - S_b rho_b)
+  // band buffers in shared memory, [4][nbs]: observed radiance, weight, and
+  // the residuals of the current and the trial state (index rc, rc ^ 1)
   float *bb;
   int nbs;
   float psc;
@@ -501,16 +506,17 @@ struct Stage1 {
   }
 
   // model, reduced Jacobian, normal equations and cost at x (all lanes of
-  // the group get the totals); writes the residuals, Planck factors and
-  // solar denominators into set rn and returns the data-cost decrease from
-  // the state xo, whose set is 1 - rn. cd = unweighted data cost. The
+  // the group get the totals); writes the residuals into set rn and returns
+  // the data-cost decrease from the state xo, whose residuals are set 1 - rn. cd = unweighted data cost. The
   // decrease is formed from residual differences, or, with inc (small
   // steps, whose decrease the difference of two FP32 model values no longer
   // resolves), in increment form: dM_b = dLs_b + tu_b (d alpha B_o + alpha
   // dB_b) with
   //   dLs_b = A_b drho_b / ((1 - S_b rho_t)(1 - S_b rho_o)),
   //   dB_b = B_o expm1(-dx_b) / (1 - e^-x_t), dx_b = -(c2/lambda_b) dT / (T_t T_o),
-  // each increment formed from the exact parameter differences.
+  // each increment formed from the exact parameter differences; B_o and
+  // 1 / (1 - S_b rho_o) are recomputed at xo with the instructions that
+  // formed them when xo was evaluated.
   __device__ __forceinline__ void eval(const PixCtx &pc, const Grp<G> &gp, const float (&x)[NX],
                                        int rn, float (&H)[NH], float (&g)[P], float (&gf)[P],
                                        float &cst, float &cd, float &drop, int &m,
@@ -521,20 +527,20 @@ struct Stage1 {
     float acc[NH + P + 5];
 #pragma unroll
     for (int i = 0; i < NH + P + 5; i++) acc[i] = 0.f;
-    const float a1 = x[K], invT = 1.f / x[K + 1];
+    const float a1 = x[K], invT = 1.f / x[K + 1], invTo = 1.f / xo[K + 1];
     const float dTT = (x[K + 1] - xo[K + 1]) * invT / xo[K + 1];
     const float dal = a1 - xo[K];
     float dxs[K];
 #pragma unroll
     for (int k = 0; k < K; k++) dxs[k] = x[k] - xo[k];
-    const float *ro = bb + (3 - rn) * nbs, *bo = bb + (5 - rn) * nbs, *vo = bb + (7 - rn) * nbs;
-    float *rw = bb + (2 + rn) * nbs, *bw = bb + (4 + rn) * nbs, *vw = bb + (6 + rn) * nbs;
+    const float *ro = bb + (3 - rn) * nbs;
+    float *rw = bb + (2 + rn) * nbs;
 #pragma unroll kBand1Unroll
     for (int i = gp.sub; i < t.n1; i += G) {
       const float wv = W(i);
       if (wv > 0.f) {
         int b = t.b1lo + i;
-        float4 q = __ldg(pc.wvrow + b);
+        const float4 q = pc.wvrow[b];
         float E[K];
         float rho = 0.f;
 #pragma unroll
@@ -545,23 +551,27 @@ struct Stage1 {
         // fast reciprocals (within 2 ulp): both arguments lie well inside (0, 1]
         float inv = __fdividef(1.f, 1.f - q.z * rho);
         float Ls = fmaf(q.x * rho, inv, q.y);
-        float xx = pc.img[t.lay.off_c2l + b] * invT;
+        const float c2l = pc.img[t.lay.off_c2l + b], c1l5 = pc.img[t.lay.off_c1l5 + b];
+        float xx = c2l * invT;
         float e = __expf(-xx);
         float rom = __fdividef(1.f, 1.f - e);
-        float B = pc.img[t.lay.off_c1l5 + b] * e * rom;
+        float B = c1l5 * e * rom;
         float dB = B * xx * invT * rom;
         float r = Lo(i) - fmaf(a1 * q.w, B, Ls);
         float rold = ro[i];
         rw[i] = r;
-        bw[i] = B;
-        vw[i] = inv;
         if (inc) {
-          float drho = 0.f;
+          float drho = 0.f, rho_o = 0.f;
 #pragma unroll
-          for (int k = 0; k < K; k++) drho = fmaf(dxs[k], E[k], drho);
-          const float dLs = q.x * drho * inv * vo[i];
-          const float Bo = bo[i];
-          const float dx = -pc.img[t.lay.off_c2l + b] * dTT;
+          for (int k = 0; k < K; k++) {
+            drho = fmaf(dxs[k], E[k], drho);
+            rho_o = fmaf(xo[k], E[k], rho_o);
+          }
+          const float inv_o = __fdividef(1.f, 1.f - q.z * rho_o);
+          const float e_o = __expf(-(c2l * invTo));
+          const float Bo = c1l5 * e_o * __fdividef(1.f, 1.f - e_o);
+          const float dLs = q.x * drho * inv * inv_o;
+          const float dx = -c2l * dTT;
           const float dB = fabsf(dx) < 0.05f ? Bo * em1_small(-dx) * rom
                                              : (fabsf(dx) < 1.f ? Bo * expm1f(-dx) * rom : B - Bo);
           const float dM = fmaf(q.w, fmaf(dal, Bo, a1 * dB), dLs);
@@ -1149,7 +1159,7 @@ __device__ __forceinline__ int setup1(Stage1<K, G> &s1, const PixCtx &pc, const 
     s1.Lo(i) = Lv;
     s1.W(i) = wv;
 #pragma unroll
-    for (int k = 2; k < 8; k++) s1.bb[k * s1.nbs + i] = 0.f;
+    for (int k = 2; k < 4; k++) s1.bb[k * s1.nbs + i] = 0.f;
   }
   nv = gp.sum1(nv);
   nu = gp.isum(nu);
@@ -1293,18 +1303,22 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
   const KConfig &c = p.c;
   const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
-  const int img_f = image_floats(t, 1);
-  if (!stage_tables(t, smem, img_f, &bar, p.w.err)) return;
+  // the table head, then the whole water-vapour table, then the pixels'
+  // band buffers
+  const int img_f = image_floats(t, 1), wv_f = wvtab_floats(t);
+  const float4 *wvs = wv_f ? reinterpret_cast<const float4 *>(smem + img_f) : t.wvtab;
+  if (!stage_tables(t, smem, img_f, &bar, p.w.err, smem + img_f, t.wvtab, (unsigned)wv_f * 4u))
+    return;
   const Grp<G> gp(lane);
   PixCtx pc;
   pc.t = &t;
   pc.c = &c;
   pc.img = smem;
   pc.node = nullptr;
-  pc.wvrow = t.wvtab;
+  pc.wvrow = wvs;
   Stage1<K, G> S;
   S.nbs = band_slots(t.n1, G);
-  S.bb = smem + img_f + (threadIdx.x / G) * pix_stride1(t, G);
+  S.bb = smem + img_f + wv_f + (threadIdx.x / G) * pix_stride1(t, G);
   const int NSx = K + 8;
   const long long n = p.s.n_pix;
   const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
@@ -1328,7 +1342,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
       const float *row = ref.row;
       const int wvb = ref.wv;
       const bool wv_ok = wvb < t.nwv;   // an out-of-range bin is an invalid input
-      pc.wvrow = t.wvtab + (size_t)(wv_ok ? wvb : 0) * t.nb;
+      pc.wvrow = wvs + (size_t)(wv_ok ? wvb : 0) * t.nb;
       bool fin = true;
       for (int b = gp.sub; b < t.nb; b += G) fin = fin && isfinite(__ldg(row + b));
       fin = gp.all(fin) && wv_ok;
@@ -2590,7 +2604,8 @@ constexpr Shape kShape2[2] = {{32, 8}, {16, 8}};
 
 size_t stage_smem(const KTables &t, int stage, int G, int wpb) {
   const int per = stage == 1 ? pix_stride1(t, G) : pix_stride2(t, G);
-  return ((size_t)image_floats(t, stage) + (size_t)wpb * (32 / G) * per) * 4;
+  const size_t head = (size_t)image_floats(t, stage) + (stage == 1 ? (size_t)wvtab_floats(t) : 0);
+  return (head + (size_t)wpb * (32 / G) * per) * 4;
 }
 
 int fit_warps(const KTables &t, int stage, int G, int maxw) {
