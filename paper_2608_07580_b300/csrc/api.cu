@@ -363,6 +363,8 @@ void fire_ctx_destroy(fire_ctx_t *ctx) {
   if (!ctx) return;
   for (cudaEvent_t e : ctx->chunk_ev) cudaEventDestroy(e);
   if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
+  if (ctx->fit_st2) cudaStreamDestroy(ctx->fit_st2);
+  cudaFree(ctx->d_ctr);
   cudaFree(ctx->d_image);
   cudaFree(ctx->d_plop);
   cudaFree(ctx->d_wvtab);
@@ -617,8 +619,11 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   }
   if (!learned && n >= 2 * kChunkMin) {
     // plain or given start: the scene in chunks whose copies overlap the
-    // fits of the others; each pixel's fit is independent of the chunking,
-    // so the results are those of one launch bit for bit
+    // fits of the others; consecutive chunks fit on two streams, each with
+    // its own claim counters and its slice of the stage scratch, so a
+    // chunk's fit starts on the SMs that the previous chunk's last pixels
+    // leave idle. Each pixel's fit is independent of the chunking, so the
+    // results are those of one launch bit for bit
     int64_t c0[kChunks + 1];
     int nch = 0;
     c0[0] = 0;
@@ -629,6 +634,11 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
       nch++;
     }
     if (!c->copy_st) CK(cudaStreamCreateWithFlags(&c->copy_st, cudaStreamNonBlocking));
+    if (!c->fit_st2) CK(cudaStreamCreateWithFlags(&c->fit_st2, cudaStreamNonBlocking));
+    if (!c->d_ctr) {
+      fire_status_t e = dev_alloc(&c->d_ctr, (size_t)2 * kChunks * 8);
+      if (e != FIRE_OK) return e;
+    }
     while ((int)c->chunk_ev.size() < 2 * nch + 2) {
       cudaEvent_t e;
       CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -636,10 +646,13 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     }
     cudaEvent_t *ev_in = c->chunk_ev.data(), *ev_fit = ev_in + nch;
     cudaEvent_t ev_start = ev_in[2 * nch], ev_done = ev_in[2 * nch + 1];
-    cudaStream_t cp = c->copy_st;
-    // the copies start after the caller's earlier work on the staging buffer
+    cudaStream_t cp = c->copy_st, fs[2] = {st, c->fit_st2};
+    // copies and fits start after the caller's earlier work on the staging
+    // buffer and the cleared statistics
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
     CK(cudaEventRecord(ev_start, st));
     CK(cudaStreamWaitEvent(cp, ev_start, 0));
+    CK(cudaStreamWaitEvent(fs[1], ev_start, 0));
     for (int i = 0; i < nch; i++) {
       const int64_t a = c0[i], m = c0[i + 1] - c0[i];
       CK(cudaMemcpyAsync(d_rad + a * c->t.nb, sc->radiance + a * c->t.nb, (size_t)m * c->t.nb * 4,
@@ -671,11 +684,17 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
       q.o.cov = off(p.o.cov, 21);
       q.o.status = off(p.o.status, 1);
       q.o.iters = off(p.o.iters, 2);
-      CK(cudaStreamWaitEvent(st, ev_in[i], 0));
-      CK(cudaMemsetAsync(c->d_work, 0, 2 * 8, st));   // claim counters; statistics accumulate
-      CK(launch_lm(q, c->num_sms, st, &blocks, c->tune_variant));
+      q.w.counter = c->d_ctr + 2 * i;
+      q.w.s1x = p.w.s1x + a * (c->t.K + 2);
+      q.w.s1meta = p.w.s1meta + a;
+      q.w.s2x = p.w.s2x + a * 32;
+      q.w.s2g = p.w.s2g + a * 6;
+      cudaStream_t si = fs[i & 1];
+      CK(cudaStreamWaitEvent(si, ev_in[i], 0));
+      CK(cudaMemsetAsync(q.w.counter, 0, 2 * 8, si));   // claim counters; statistics accumulate
+      CK(launch_lm(q, c->num_sms, si, &blocks, c->tune_variant));
       c->last_launches += 3;
-      CK(cudaEventRecord(ev_fit[i], st));
+      CK(cudaEventRecord(ev_fit[i], si));
       CK(cudaStreamWaitEvent(cp, ev_fit[i], 0));
       struct { void *h; void *d; size_t b; } back[] = {
           {out->state, q.o.state, (size_t)m * NS * 4}, {out->ET, q.o.ET, (size_t)m * 4},

@@ -52,6 +52,10 @@ struct fire_ctx {
   // one chunk overlap the fit of another (created on first use)
   cudaStream_t copy_st = nullptr;
   std::vector<cudaEvent_t> chunk_ev;
+  // ... and a second compute stream with claim counters per chunk, so that
+  // one chunk's fit can start on the SMs that another chunk's tail frees
+  cudaStream_t fit_st2 = nullptr;
+  unsigned long long *d_ctr = nullptr;
   size_t tev_used = 0;
 };
 
