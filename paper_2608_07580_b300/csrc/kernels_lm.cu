@@ -95,6 +95,20 @@ __device__ __forceinline__ float em1_small(float y) {
   return y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
 }
 
+// expm1(y) for |y| < 0.5 by its Taylor series to y^9 (truncation below
+// |y|^10 / 10! e^|y| < 5e-10 |y|): nine FMAs, no branches
+__device__ __forceinline__ float em1_mid(float y) {
+  float p = fmaf(y, 1.f / 362880.f, 1.f / 40320.f);
+  p = fmaf(y, p, 1.f / 5040.f);
+  p = fmaf(y, p, 1.f / 720.f);
+  p = fmaf(y, p, 1.f / 120.f);
+  p = fmaf(y, p, 1.f / 24.f);
+  p = fmaf(y, p, 1.f / 6.f);
+  p = fmaf(y, p, 0.5f);
+  p = fmaf(y, p, 1.f);
+  return y * p;
+}
+
 // ------------------------------------------------------------- solve ----
 // reciprocal square root for the step solve: the SFU in FP32; in FP64 an FP32
 // seed and one Newton-Raphson step (2^-22 -> below 2^-43, past the FP32
@@ -527,6 +541,12 @@ struct Stage1 {
     float acc[NH + P + 5];
 #pragma unroll
     for (int i = 0; i < NH + P + 5; i++) acc[i] = 0.f;
+    // P = 4 (three endmembers): the normal-equation and cost sums in pairs
+    // for the packed FP32 FMA (two round-to-nearest FMAs per instruction, the
+    // same results as one at a time)
+    float2 pk[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) pk[i] = make_float2(0.f, 0.f);
     const float a1 = x[K], invT = 1.f / x[K + 1], invTo = 1.f / xo[K + 1];
     const float dTT = (x[K + 1] - xo[K + 1]) * invT / xo[K + 1];
     const float dal = a1 - xo[K];
@@ -593,18 +613,40 @@ struct Stage1 {
         J[K] = a1 * q.w * dB * sT;
         float wr = wv * r;
         const float wM = wv * (Lo(i) - r);     // weight x model value
-        acc[NH + P] = fmaf(wr, r, acc[NH + P]);
-        acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
-        acc[NH + P + 3] = fmaf(wM, wM, acc[NH + P + 3]);
-        acc[NH + P + 4] += wv;
+        if constexpr (P == 4) {
+          const float wj0 = wv * J[0], wj1 = wv * J[1], wj2 = wv * J[2], wj3 = wv * J[3];
+          const float2 wr2 = make_float2(wr, wr);
+          pk[0] = __ffma2_rn(make_float2(wj0, wj0), make_float2(J[0], J[1]), pk[0]);   // H00 H01
+          pk[1] = __ffma2_rn(make_float2(wj0, wj0), make_float2(J[2], J[3]), pk[1]);   // H02 H03
+          pk[2] = __ffma2_rn(make_float2(wj1, wj1), make_float2(J[1], J[2]), pk[2]);   // H11 H12
+          pk[3] = __ffma2_rn(make_float2(wj2, wj2), make_float2(J[2], J[3]), pk[3]);   // H22 H23
+          pk[4] = __ffma2_rn(make_float2(wj1, wj3), make_float2(J[3], J[3]), pk[4]);   // H13 H33
+          pk[5] = __ffma2_rn(make_float2(J[0], J[1]), wr2, pk[5]);                     // g0 g1
+          pk[6] = __ffma2_rn(make_float2(J[2], J[3]), wr2, pk[6]);                     // g2 g3
+          pk[7] = __ffma2_rn(make_float2(wr, r), make_float2(r, r), pk[7]);            // cost, data cost
+          pk[8] = __ffma2_rn(make_float2(wM, wv), make_float2(wM, 1.f), pk[8]);        // w^2 M^2, w
+        } else {
+          acc[NH + P] = fmaf(wr, r, acc[NH + P]);
+          acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
+          acc[NH + P + 3] = fmaf(wM, wM, acc[NH + P + 3]);
+          acc[NH + P + 4] += wv;
 #pragma unroll
-        for (int a = 0; a < P; a++) {
-          acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
-          float wj = wv * J[a];
+          for (int a = 0; a < P; a++) {
+            acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
+            float wj = wv * J[a];
 #pragma unroll
-          for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
+            for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
+          }
         }
       }
+    }
+    if constexpr (P == 4) {
+      acc[0] = pk[0].x; acc[1] = pk[0].y; acc[2] = pk[1].x; acc[3] = pk[1].y;
+      acc[4] = pk[2].x; acc[5] = pk[2].y; acc[6] = pk[4].x; acc[7] = pk[3].x;
+      acc[8] = pk[3].y; acc[9] = pk[4].y;
+      acc[NH] = pk[5].x; acc[NH + 1] = pk[5].y; acc[NH + 2] = pk[6].x; acc[NH + 3] = pk[6].y;
+      acc[NH + P] = pk[7].x; acc[NH + P + 1] = pk[7].y;
+      acc[NH + P + 3] = pk[8].x; acc[NH + P + 4] = pk[8].y;
     }
     gp.sum(acc);
 #pragma unroll
@@ -757,7 +799,7 @@ struct Stage2 {
     const float da = -fmaf((T - mu) * dsg, isg, dmu) * isgt;
     const float dq = 0.5f * da * (at + ao);
     u = expf(-0.5f * ao * ao);
-    du = fabsf(dq) < 0.5f ? u * expm1f(-dq) : expf(-0.5f * at * at) - u;
+    du = fabsf(dq) < 0.5f ? u * em1_mid(-dq) : expf(-0.5f * at * at) - u;
   }
 
   // Model, Jacobian (z-scaled), normal equations and cost at the trial
@@ -1786,13 +1828,19 @@ __device__ __forceinline__ void coef(const KTables &t, const KConfig &c, const G
     const int kx = (slot & 1) << 2;
 #pragma unroll
     for (int k = 0; k < 7; k++) {
-      __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-      split3(cf[0][k], a0, a1, a2);
-      split3(cf[1][k], b0, b1, b2);
+      // the three parts of the node pair (j0, j0 + 1), two lanes per
+      // conversion (node j0 in the low half, at the lower address)
+      const float2 v = make_float2(cf[0][k], cf[1][k]);
+      const __nv_bfloat162 h0 = __float22bfloat162_rn(v);
+      const float2 f0 = __bfloat1622float2(h0);
+      const float2 r1 = make_float2(v.x - f0.x, v.y - f0.y);
+      const __nv_bfloat162 h1 = __float22bfloat162_rn(r1);
+      const float2 f1 = __bfloat1622float2(h1);
+      const __nv_bfloat162 h2 = __float22bfloat162_rn(make_float2(r1.x - f1.x, r1.y - f1.y));
       const unsigned off = cob + tc::swz(8 * slot + (k ^ kx), j0 >> 3) + cc;
-      asm volatile("st.shared.b32 [%0], %1;" ::"r"(off), "r"(pack2(a0, b0)) : "memory");
-      asm volatile("st.shared.b32 [%0], %1;" ::"r"(off + kCoPart), "r"(pack2(a1, b1)) : "memory");
-      asm volatile("st.shared.b32 [%0], %1;" ::"r"(off + 2 * kCoPart), "r"(pack2(a2, b2)) : "memory");
+      asm volatile("st.shared.b32 [%0], %1;" ::"r"(off), "r"(*reinterpret_cast<const uint32_t *>(&h0)) : "memory");
+      asm volatile("st.shared.b32 [%0], %1;" ::"r"(off + kCoPart), "r"(*reinterpret_cast<const uint32_t *>(&h1)) : "memory");
+      asm volatile("st.shared.b32 [%0], %1;" ::"r"(off + 2 * kCoPart), "r"(*reinterpret_cast<const uint32_t *>(&h2)) : "memory");
     }
   }
   // band-phase parameters: [1] eta, [2] alpha, [3] alpha - alpha_o, [4..7]
