@@ -538,15 +538,14 @@ struct Stage1 {
     const KTables &t = *pc.t;
     const KConfig &c = *pc.c;
     m = argmax_frac(x);
-    float acc[NH + P + 5];
+    // Each lane takes its bands in consecutive pairs (i0, i0 + 1), i0 = 2 sub
+    // + 2 G s, and forms both with the packed FP32 instructions (two
+    // round-to-nearest operations per instruction); the pair's two partial
+    // sums are added at the end. A masked band of a pair (weight 0) adds
+    // exact zeros.
+    float2 sm[NH + P + 5];
 #pragma unroll
-    for (int i = 0; i < NH + P + 5; i++) acc[i] = 0.f;
-    // P = 4 (three endmembers): the normal-equation and cost sums in pairs
-    // for the packed FP32 FMA (two round-to-nearest FMAs per instruction, the
-    // same results as one at a time)
-    float2 pk[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) pk[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < NH + P + 5; i++) sm[i] = make_float2(0.f, 0.f);
     const float a1 = x[K], invT = 1.f / x[K + 1], invTo = 1.f / xo[K + 1];
     const float dTT = (x[K + 1] - xo[K + 1]) * invT / xo[K + 1];
     const float dal = a1 - xo[K];
@@ -555,99 +554,101 @@ struct Stage1 {
     for (int k = 0; k < K; k++) dxs[k] = x[k] - xo[k];
     const float *ro = bb + (3 - rn) * nbs;
     float *rw = bb + (2 + rn) * nbs;
+    const float2 one = make_float2(1.f, 1.f), a1v = make_float2(a1, a1);
+    const float2 invTv = make_float2(invT, invT);
 #pragma unroll kBand1Unroll
-    for (int i = gp.sub; i < t.n1; i += G) {
-      const float wv = W(i);
-      if (wv > 0.f) {
-        int b = t.b1lo + i;
-        const float4 q = pc.wvrow[b];
-        float E[K];
-        float rho = 0.f;
+    for (int i0 = 2 * gp.sub; i0 < t.n1; i0 += 2 * G) {
+      const float2 wv = *reinterpret_cast<const float2 *>(&W(i0));
+      if (!(wv.x > 0.f) && !(wv.y > 0.f)) continue;
+      const int b0 = t.b1lo + i0, b1 = min(b0 + 1, t.nb - 1);
+      const float4 qa = pc.wvrow[b0], qb = pc.wvrow[b1];
+      const float2 qx = make_float2(qa.x, qb.x), qy = make_float2(qa.y, qb.y);
+      const float2 nqz = make_float2(-qa.z, -qb.z), qw = make_float2(qa.w, qb.w);
+      float2 E[K];
+      float2 rho = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        const float *ek = pc.img + t.lay.off_endm + k * t.nb;
+        E[k] = make_float2(ek[b0], ek[b1]);
+        rho = __ffma2_rn(make_float2(x[k], x[k]), E[k], rho);
+      }
+      // fast reciprocals (within 2 ulp): both arguments lie well inside (0, 1]
+      const float2 den = __ffma2_rn(nqz, rho, one);
+      const float2 inv = make_float2(__fdividef(1.f, den.x), __fdividef(1.f, den.y));
+      const float2 Ls = __ffma2_rn(__fmul2_rn(qx, rho), inv, qy);
+      const float2 c2l = make_float2(pc.img[t.lay.off_c2l + b0], pc.img[t.lay.off_c2l + b1]);
+      const float2 c1l5 = make_float2(pc.img[t.lay.off_c1l5 + b0], pc.img[t.lay.off_c1l5 + b1]);
+      const float2 xx = __fmul2_rn(c2l, invTv);
+      const float2 e = make_float2(__expf(-xx.x), __expf(-xx.y));
+      const float2 rom = make_float2(__fdividef(1.f, 1.f - e.x), __fdividef(1.f, 1.f - e.y));
+      const float2 B = __fmul2_rn(__fmul2_rn(c1l5, e), rom);
+      const float2 dB = __fmul2_rn(__fmul2_rn(__fmul2_rn(B, xx), invTv), rom);
+      const float2 Lo2 = *reinterpret_cast<const float2 *>(&Lo(i0));
+      const float2 mod = __ffma2_rn(__fmul2_rn(a1v, qw), B, Ls);
+      // a masked band's residual is taken as 0, so that it adds nothing to
+      // the unweighted data cost either
+      const float2 r = make_float2(wv.x > 0.f ? Lo2.x - mod.x : 0.f, wv.y > 0.f ? Lo2.y - mod.y : 0.f);
+      const float2 rold = *reinterpret_cast<const float2 *>(ro + i0);
+      *reinterpret_cast<float2 *>(rw + i0) = r;
+      if (inc) {
+        float2 drho = make_float2(0.f, 0.f), rho_o = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < K; k++) {
-          E[k] = pc.img[t.lay.off_endm + k * t.nb + b];
-          rho = fmaf(x[k], E[k], rho);
+          drho = __ffma2_rn(make_float2(dxs[k], dxs[k]), E[k], drho);
+          rho_o = __ffma2_rn(make_float2(xo[k], xo[k]), E[k], rho_o);
         }
-        // fast reciprocals (within 2 ulp): both arguments lie well inside (0, 1]
-        float inv = __fdividef(1.f, 1.f - q.z * rho);
-        float Ls = fmaf(q.x * rho, inv, q.y);
-        const float c2l = pc.img[t.lay.off_c2l + b], c1l5 = pc.img[t.lay.off_c1l5 + b];
-        float xx = c2l * invT;
-        float e = __expf(-xx);
-        float rom = __fdividef(1.f, 1.f - e);
-        float B = c1l5 * e * rom;
-        float dB = B * xx * invT * rom;
-        float r = Lo(i) - fmaf(a1 * q.w, B, Ls);
-        float rold = ro[i];
-        rw[i] = r;
-        if (inc) {
-          float drho = 0.f, rho_o = 0.f;
+        const float2 den_o = __ffma2_rn(nqz, rho_o, one);
+        const float2 inv_o = make_float2(__fdividef(1.f, den_o.x), __fdividef(1.f, den_o.y));
+        const float2 xo2 = __fmul2_rn(c2l, make_float2(invTo, invTo));
+        const float2 e_o = make_float2(__expf(-xo2.x), __expf(-xo2.y));
+        const float2 Bo = __fmul2_rn(__fmul2_rn(c1l5, e_o),
+                                     make_float2(__fdividef(1.f, 1.f - e_o.x), __fdividef(1.f, 1.f - e_o.y)));
+        const float2 dLs = __fmul2_rn(__fmul2_rn(__fmul2_rn(qx, drho), inv), inv_o);
+        const float2 dx = __fmul2_rn(c2l, make_float2(-dTT, -dTT));
+        float2 dBi;
+        dBi.x = fabsf(dx.x) < 0.05f ? Bo.x * em1_small(-dx.x) * rom.x
+                                    : (fabsf(dx.x) < 1.f ? Bo.x * expm1f(-dx.x) * rom.x : B.x - Bo.x);
+        dBi.y = fabsf(dx.y) < 0.05f ? Bo.y * em1_small(-dx.y) * rom.y
+                                    : (fabsf(dx.y) < 1.f ? Bo.y * expm1f(-dx.y) * rom.y : B.y - Bo.y);
+        const float2 dM = __ffma2_rn(qw, __ffma2_rn(make_float2(dal, dal), Bo, __fmul2_rn(a1v, dBi)), dLs);
+        const float2 t2 = __ffma2_rn(make_float2(2.f, 2.f), rold, make_float2(-dM.x, -dM.y));
+        sm[NH + P + 2] = __ffma2_rn(__fmul2_rn(wv, dM), t2, sm[NH + P + 2]);
+      } else {
+        sm[NH + P + 2] = __ffma2_rn(__fmul2_rn(wv, make_float2(rold.x - r.x, rold.y - r.y)),
+                                    __fadd2_rn(rold, r), sm[NH + P + 2]);
+      }
+      float2 dL[K], dEm = make_float2(0.f, 0.f);
+      const float2 qi2 = __fmul2_rn(__fmul2_rn(__fmul2_rn(qx, inv), inv), make_float2(sf, sf));
 #pragma unroll
-          for (int k = 0; k < K; k++) {
-            drho = fmaf(dxs[k], E[k], drho);
-            rho_o = fmaf(xo[k], E[k], rho_o);
-          }
-          const float inv_o = __fdividef(1.f, 1.f - q.z * rho_o);
-          const float e_o = __expf(-(c2l * invTo));
-          const float Bo = c1l5 * e_o * __fdividef(1.f, 1.f - e_o);
-          const float dLs = q.x * drho * inv * inv_o;
-          const float dx = -c2l * dTT;
-          const float dB = fabsf(dx) < 0.05f ? Bo * em1_small(-dx) * rom
-                                             : (fabsf(dx) < 1.f ? Bo * expm1f(-dx) * rom : B - Bo);
-          const float dM = fmaf(q.w, fmaf(dal, Bo, a1 * dB), dLs);
-          acc[NH + P + 2] = fmaf(wv * dM, 2.f * rold - dM, acc[NH + P + 2]);
-        } else {
-          acc[NH + P + 2] = fmaf(wv * (rold - r), rold + r, acc[NH + P + 2]);
-        }
-        float dL[K], dEm = 0.f;
-        const float qi2 = q.x * inv * inv * sf;
+      for (int k = 0; k < K; k++) {
+        dL[k] = __fmul2_rn(qi2, E[k]);
+        dEm = (k == m) ? dL[k] : dEm;
+      }
+      float2 J[P];
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-          dL[k] = qi2 * E[k];
-          dEm = (k == m) ? dL[k] : dEm;
-        }
-        float J[P];
+      for (int a = 0; a < K - 1; a++) {
+        const float2 d = a < m ? dL[a] : dL[a + 1];
+        J[a] = make_float2(d.x - dEm.x, d.y - dEm.y);
+      }
+      J[K - 1] = __fmul2_rn(__fmul2_rn(qw, B), make_float2(sa, sa));
+      J[K] = __fmul2_rn(__fmul2_rn(__fmul2_rn(a1v, qw), dB), make_float2(sT, sT));
+      const float2 wr = __fmul2_rn(wv, r);
+      const float2 wM = __fmul2_rn(wv, make_float2(Lo2.x - r.x, Lo2.y - r.y));   // weight x model value
+      sm[NH + P] = __ffma2_rn(wr, r, sm[NH + P]);
+      sm[NH + P + 1] = __ffma2_rn(r, r, sm[NH + P + 1]);
+      sm[NH + P + 3] = __ffma2_rn(wM, wM, sm[NH + P + 3]);
+      sm[NH + P + 4] = __fadd2_rn(sm[NH + P + 4], wv);
 #pragma unroll
-        for (int a = 0; a < K - 1; a++) J[a] = (a < m ? dL[a] : dL[a + 1]) - dEm;
-        J[K - 1] = q.w * B * sa;
-        J[K] = a1 * q.w * dB * sT;
-        float wr = wv * r;
-        const float wM = wv * (Lo(i) - r);     // weight x model value
-        if constexpr (P == 4) {
-          const float wj0 = wv * J[0], wj1 = wv * J[1], wj2 = wv * J[2], wj3 = wv * J[3];
-          const float2 wr2 = make_float2(wr, wr);
-          pk[0] = __ffma2_rn(make_float2(wj0, wj0), make_float2(J[0], J[1]), pk[0]);   // H00 H01
-          pk[1] = __ffma2_rn(make_float2(wj0, wj0), make_float2(J[2], J[3]), pk[1]);   // H02 H03
-          pk[2] = __ffma2_rn(make_float2(wj1, wj1), make_float2(J[1], J[2]), pk[2]);   // H11 H12
-          pk[3] = __ffma2_rn(make_float2(wj2, wj2), make_float2(J[2], J[3]), pk[3]);   // H22 H23
-          pk[4] = __ffma2_rn(make_float2(wj1, wj3), make_float2(J[3], J[3]), pk[4]);   // H13 H33
-          pk[5] = __ffma2_rn(make_float2(J[0], J[1]), wr2, pk[5]);                     // g0 g1
-          pk[6] = __ffma2_rn(make_float2(J[2], J[3]), wr2, pk[6]);                     // g2 g3
-          pk[7] = __ffma2_rn(make_float2(wr, r), make_float2(r, r), pk[7]);            // cost, data cost
-          pk[8] = __ffma2_rn(make_float2(wM, wv), make_float2(wM, 1.f), pk[8]);        // w^2 M^2, w
-        } else {
-          acc[NH + P] = fmaf(wr, r, acc[NH + P]);
-          acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
-          acc[NH + P + 3] = fmaf(wM, wM, acc[NH + P + 3]);
-          acc[NH + P + 4] += wv;
+      for (int a = 0; a < P; a++) {
+        sm[NH + a] = __ffma2_rn(J[a], wr, sm[NH + a]);
+        const float2 wj = __fmul2_rn(wv, J[a]);
 #pragma unroll
-          for (int a = 0; a < P; a++) {
-            acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
-            float wj = wv * J[a];
-#pragma unroll
-            for (int bb_ = a; bb_ < P; bb_++) acc[up<P>(a, bb_)] = fmaf(wj, J[bb_], acc[up<P>(a, bb_)]);
-          }
-        }
+        for (int bb_ = a; bb_ < P; bb_++) sm[up<P>(a, bb_)] = __ffma2_rn(wj, J[bb_], sm[up<P>(a, bb_)]);
       }
     }
-    if constexpr (P == 4) {
-      acc[0] = pk[0].x; acc[1] = pk[0].y; acc[2] = pk[1].x; acc[3] = pk[1].y;
-      acc[4] = pk[2].x; acc[5] = pk[2].y; acc[6] = pk[4].x; acc[7] = pk[3].x;
-      acc[8] = pk[3].y; acc[9] = pk[4].y;
-      acc[NH] = pk[5].x; acc[NH + 1] = pk[5].y; acc[NH + 2] = pk[6].x; acc[NH + 3] = pk[6].y;
-      acc[NH + P] = pk[7].x; acc[NH + P + 1] = pk[7].y;
-      acc[NH + P + 3] = pk[8].x; acc[NH + P + 4] = pk[8].y;
-    }
+    float acc[NH + P + 5];
+#pragma unroll
+    for (int i = 0; i < NH + P + 5; i++) acc[i] = sm[i].x + sm[i].y;
     gp.sum(acc);
 #pragma unroll
     for (int i = 0; i < NH; i++) H[i] = acc[i];
