@@ -89,12 +89,6 @@ __device__ __forceinline__ double rsq(double x) {
   return y;
 }
 
-// expm1(y) for |y| < 0.05 by its Taylor series to y^5 (truncation below
-// |y|^6 / 720 < 2.2e-11 relative)
-__device__ __forceinline__ float em1_small(float y) {
-  return y * fmaf(y, fmaf(y, fmaf(y, fmaf(y, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f), 1.f);
-}
-
 // expm1(y) for |y| < 0.5 by its Taylor series to y^9 (truncation below
 // |y|^10 / 10! e^|y| < 5e-10 |y|): nine FMAs, no branches
 __device__ __forceinline__ float em1_mid(float y) {
@@ -107,6 +101,19 @@ __device__ __forceinline__ float em1_mid(float y) {
   p = fmaf(y, p, 0.5f);
   p = fmaf(y, p, 1.f);
   return y * p;
+}
+// the same for a pair, with the packed FP32 FMA
+__device__ __forceinline__ float2 em1_mid2(float2 y) {
+  float2 p = __ffma2_rn(y, make_float2(1.f / 362880.f, 1.f / 362880.f),
+                        make_float2(1.f / 40320.f, 1.f / 40320.f));
+  p = __ffma2_rn(y, p, make_float2(1.f / 5040.f, 1.f / 5040.f));
+  p = __ffma2_rn(y, p, make_float2(1.f / 720.f, 1.f / 720.f));
+  p = __ffma2_rn(y, p, make_float2(1.f / 120.f, 1.f / 120.f));
+  p = __ffma2_rn(y, p, make_float2(1.f / 24.f, 1.f / 24.f));
+  p = __ffma2_rn(y, p, make_float2(1.f / 6.f, 1.f / 6.f));
+  p = __ffma2_rn(y, p, make_float2(0.5f, 0.5f));
+  p = __ffma2_rn(y, p, make_float2(1.f, 1.f));
+  return __fmul2_rn(y, p);
 }
 
 // ------------------------------------------------------------- solve ----
@@ -527,7 +534,8 @@ struct Stage1 {
   // resolves), in increment form: dM_b = dLs_b + tu_b (d alpha B_o + alpha
   // dB_b) with
   //   dLs_b = A_b drho_b / ((1 - S_b rho_t)(1 - S_b rho_o)),
-  //   dB_b = B_o expm1(-dx_b) / (1 - e^-x_t), dx_b = -(c2/lambda_b) dT / (T_t T_o),
+  //   dB_b = B_o expm1(-dx_b) / (1 - e^-x_t), dx_b = -(c2/lambda_b) dT / (T_t T_o)
+  //   (expm1 by its Taylor series for |dx_b| < 0.5, else B_t - B_o),
   // each increment formed from the exact parameter differences; B_o and
   // 1 / (1 - S_b rho_o) are recomputed at xo with the instructions that
   // formed them when xo was evaluated.
@@ -605,11 +613,12 @@ struct Stage1 {
                                      make_float2(__fdividef(1.f, 1.f - e_o.x), __fdividef(1.f, 1.f - e_o.y)));
         const float2 dLs = __fmul2_rn(__fmul2_rn(__fmul2_rn(qx, drho), inv), inv_o);
         const float2 dx = __fmul2_rn(c2l, make_float2(-dTT, -dTT));
+        // dB = B_o expm1(-dx) / (1 - e^-x_t), equal to B - B_o, which has no
+        // cancellation left once |dx| >= 0.5
+        const float2 pm = __fmul2_rn(__fmul2_rn(Bo, em1_mid2(make_float2(-dx.x, -dx.y))), rom);
         float2 dBi;
-        dBi.x = fabsf(dx.x) < 0.05f ? Bo.x * em1_small(-dx.x) * rom.x
-                                    : (fabsf(dx.x) < 1.f ? Bo.x * expm1f(-dx.x) * rom.x : B.x - Bo.x);
-        dBi.y = fabsf(dx.y) < 0.05f ? Bo.y * em1_small(-dx.y) * rom.y
-                                    : (fabsf(dx.y) < 1.f ? Bo.y * expm1f(-dx.y) * rom.y : B.y - Bo.y);
+        dBi.x = fabsf(dx.x) < 0.5f ? pm.x : B.x - Bo.x;
+        dBi.y = fabsf(dx.y) < 0.5f ? pm.y : B.y - Bo.y;
         const float2 dM = __ffma2_rn(qw, __ffma2_rn(make_float2(dal, dal), Bo, __fmul2_rn(a1v, dBi)), dLs);
         const float2 t2 = __ffma2_rn(make_float2(2.f, 2.f), rold, make_float2(-dM.x, -dM.y));
         sm[NH + P + 2] = __ffma2_rn(__fmul2_rn(wv, dM), t2, sm[NH + P + 2]);
