@@ -68,6 +68,8 @@ void fill_kconfig(KConfig &k, const fire_config_t &c, const fire_priors_t &p, in
     k.pm2[i] = p.pm2[i];
     k.pp2[i] = p.pp2[i];
   }
+  for (int i = 0; i < K + 2; i++) k.zk1[i] = k.hi1[i] > k.lo1[i] ? 2.f / (k.hi1[i] - k.lo1[i]) : 0.f;
+  for (int i = 0; i < 6; i++) k.zk2[i] = k.hi2[i] > k.lo2[i] ? 2.f / (k.hi2[i] - k.lo2[i]) : 0.f;
   k.init_alpha1 = p.init_alpha1;
   k.init_T1 = p.init_T1;
   k.init_sigma = p.init_sigma;

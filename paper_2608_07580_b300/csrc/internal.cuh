@@ -51,6 +51,7 @@ struct KTables {
 struct KConfig {
   float lo1[kMaxK + 2], hi1[kMaxK + 2], pm1[kMaxK + 2], pp1[kMaxK + 2];
   float lo2[6], hi2[6], pm2[6], pp2[6];
+  float zk1[kMaxK + 2], zk2[6];   // 2 / (hi - lo), the z scale of Eq. (affine); 0 if hi = lo
   float init_alpha1, init_T1, init_sigma, init_mu_h_floor, init_mu_s_ceil;
   float init_eta_lo, init_eta_hi;
   int max_it1, max_it2;

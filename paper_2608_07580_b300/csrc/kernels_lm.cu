@@ -356,8 +356,7 @@ __device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, c
     float Dz[NX], dmax = 0.f;
 #pragma unroll
     for (int i = 0; i < NX; i++) {
-      float sc = S.scale(c, i);
-      Dz[i] = sc > 0.f ? (xt[i] - x[i]) / sc : 0.f;
+      Dz[i] = (xt[i] - x[i]) * S.zk(c, i);   // 1 / scale, 0 for a fixed variable
       dmax = fmaxf(dmax, fabsf(Dz[i]));
     }
     if (dmax < c.tol_x) { L.status = PX_CONVERGED; return false; }
@@ -516,6 +515,7 @@ struct Stage1 {
   __device__ __forceinline__ float scale(const KConfig &c, int i) const {
     return 0.5f * (c.hi1[i] - c.lo1[i]);
   }
+  __device__ __forceinline__ float zk(const KConfig &c, int i) const { return c.zk1[i]; }
 
   __device__ __forceinline__ static int argmax_frac(const float (&x)[NX]) {
     int m = 0;
@@ -676,7 +676,7 @@ struct Stage1 {
     float zr[NX], ppm = 0.f, rm = 0.f;
 #pragma unroll
     for (int i = 0; i < NX; i++) {
-      zr[i] = c.hi1[i] > c.lo1[i] ? 2.f * (x[i] - c.lo1[i]) / (c.hi1[i] - c.lo1[i]) - 1.f : 0.f;
+      zr[i] = c.zk1[i] > 0.f ? fmaf(x[i] - c.lo1[i], c.zk1[i], -1.f) : 0.f;
       zr[i] -= c.pm1[i];
       float ppi = psc * c.pp1[i];
       cst += ppi * zr[i] * zr[i];
@@ -706,7 +706,7 @@ struct Stage1 {
 #pragma unroll
     for (int i = 0; i < NX; i++) {
       if (c.hi1[i] > c.lo1[i] && c.pp1[i] > 0.f) {
-        float k = 2.f / (c.hi1[i] - c.lo1[i]);
+        const float k = c.zk1[i];
         float zo = k * (xo[i] - c.lo1[i]) - 1.f - c.pm1[i], zn = k * (xn[i] - c.lo1[i]) - 1.f - c.pm1[i];
         d += psc * c.pp1[i] * (k * (xo[i] - xn[i])) * (zo + zn);
       }
@@ -797,6 +797,7 @@ struct Stage2 {
   __device__ __forceinline__ float scale(const KConfig &c, int i) const {
     return 0.5f * (c.hi2[i] - c.lo2[i]);
   }
+  __device__ __forceinline__ float zk(const KConfig &c, int i) const { return c.zk2[i]; }
 
   // Gaussian weight u_o = exp(-a_o^2/2), a = (T - mu)/sigma, of one node at
   // the current state and its change du under the step to (mut, sgt): the
@@ -980,7 +981,7 @@ struct Stage2 {
     for (int a = 0; a < P; a++) gfl[a] = kFloorC * sqrtf(acc[up<P>(a, a)] * m2);
 #pragma unroll
     for (int i = 0; i < 6; i++) {
-      float z = c.hi2[i] > c.lo2[i] ? 2.f * (xt[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
+      float z = c.zk2[i] > 0.f ? fmaf(xt[i] - c.lo2[i], c.zk2[i], -1.f) : 0.f;
       float pp = psc * c.pp2[i];
       cst += pp * (z - c.pm2[i]) * (z - c.pm2[i]);
       acc[NH + i] -= pp * (z - c.pm2[i]);
@@ -1002,7 +1003,7 @@ struct Stage2 {
 #pragma unroll
     for (int i = 0; i < 6; i++) {
       if (c.hi2[i] > c.lo2[i] && c.pp2[i] > 0.f) {
-        float k = 2.f / (c.hi2[i] - c.lo2[i]);
+        const float k = c.zk2[i];
         float zo = k * (xo[i] - c.lo2[i]) - 1.f - c.pm2[i], zn = k * (xn[i] - c.lo2[i]) - 1.f - c.pm2[i];
         d += psc * c.pp2[i] * (k * (xo[i] - xn[i])) * (zo + zn);
       }
@@ -2034,7 +2035,7 @@ __device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, float *
   for (int i = 0; i < P; i++) gfl[i] = kFloorC * sqrtf(acc[up<P>(i, i)] * m2);
 #pragma unroll
   for (int i = 0; i < 6; i++) {
-    float z = c.hi2[i] > c.lo2[i] ? 2.f * (xt[i] - c.lo2[i]) / (c.hi2[i] - c.lo2[i]) - 1.f : 0.f;
+    float z = c.zk2[i] > 0.f ? fmaf(xt[i] - c.lo2[i], c.zk2[i], -1.f) : 0.f;
     float pp = psc * c.pp2[i];
     cst += pp * (z - c.pm2[i]) * (z - c.pm2[i]);
     acc[NH + i] -= pp * (z - c.pm2[i]);
