@@ -183,11 +183,11 @@ def run_reference(args):
 
 
 # DRAM bytes (read + write) per pixel of each LM kernel, from the ncu captures
-# of the 256 x 1024 sub-chunk (profiles/lm_stage*_medium.md: 301.8 MB, 309.1 MB
-# and 314.3 MB over 262,144 px); a launch reads each pixel's inputs once, so its
+# of the 256 x 1024 sub-chunk (profiles/lm_stage*_medium.md: 300.1 MB, 309.1 MB
+# and 315.1 MB over 262,144 px); a launch reads each pixel's inputs once, so its
 # traffic scales with the pixels it fits
-PROFILED_TRAFFIC_PER_PX = {"lm_stage2_tc_kernel": 301.77e6 / 262144, "lm_stage2_kernel": 309.10e6 / 262144,
-                           "lm_stage1_kernel": 314.27e6 / 262144}
+PROFILED_TRAFFIC_PER_PX = {"lm_stage2_tc_kernel": 300.10e6 / 262144, "lm_stage2_kernel": 309.10e6 / 262144,
+                           "lm_stage1_kernel": 315.09e6 / 262144}
 
 
 def tensor_figure(stats, n2, ms_per_fit, n_fits, peaks):
