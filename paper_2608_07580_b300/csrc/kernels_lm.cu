@@ -82,9 +82,6 @@ __device__ __forceinline__ constexpr int up(int a, int b) {
 // FP32 seed with two Newton-Raphson steps y <- y (3 - x y^2) / 2 (quadratic
 // convergence: 2^-23 -> 2^-46 -> full precision).
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-// square root for thresholds and floor estimates (a few ulp; no IEEE
-// rounding needed there): v rsqrt(v), 0 for v <= 0
-__device__ __forceinline__ float sqrt_est(float v) { return v > 0.f ? v * rsqrtf(v) : 0.f; }
 __device__ __forceinline__ double rsq(double x) {
   double y = (double)rsqrtf((float)x);
   y = y * (1.5 - 0.5 * x * y * y);
@@ -274,7 +271,7 @@ __device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, c
         L.act[a] = (lo_hit && g[a] <= 0.f) || (hi_hit && g[a] >= 0.f);
         float haa = H[up<P>(a, a)];
         if (!L.act[a]) {
-          if (fabsf(g[a]) > c.tol_g * sqrt_est(haa * cst)) small = false;
+          if (fabsf(g[a]) > c.tol_g * sqrtf(haa * cst)) small = false;
           mx = fmaxf(mx, haa);
         }
       });
@@ -386,7 +383,7 @@ __device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, c
   bool small = true;
   static_for<P>([&](auto A_) {
     constexpr int a = decltype(A_)::value;
-    if (!L.act[a] && fabsf(g[a]) > fmaf(c.tol_g, sqrt_est(H[up<P>(a, a)] * cst), gf[a])) small = false;
+    if (!L.act[a] && fabsf(g[a]) > fmaf(c.tol_g, sqrtf(H[up<P>(a, a)] * cst), gf[a])) small = false;
   });
   if (small) L.status = PX_CONVERGED;
   return false;
@@ -671,7 +668,7 @@ struct Stage1 {
 #pragma unroll
     for (int a = 0; a < P; a++) {
       g[a] = acc[NH + a];
-      gf[a] = kFloorC * sqrt_est(acc[up<P>(a, a)] * m2);
+      gf[a] = kFloorC * sqrtf(acc[up<P>(a, a)] * m2);
     }
     cd = acc[NH + P + 1];
     cst = acc[NH + P];
@@ -760,7 +757,7 @@ struct Stage1 {
 #pragma unroll
     for (int j = 0; j < K; j++) {
       cs += u[j];
-      float th = (cs - 1.f) * (1.f / (float)(j + 1));
+      float th = (cs - 1.f) / (float)(j + 1);
       if (u[j] - th > 0.f) theta = th;
     }
 #pragma unroll
@@ -982,7 +979,7 @@ struct Stage2 {
     float gfl[P];
     const float m2 = __fdividef(acc[NH + P + 3], fmaxf(acc[NH + P + 4], 1e-30f));
 #pragma unroll
-    for (int a = 0; a < P; a++) gfl[a] = kFloorC * sqrt_est(acc[up<P>(a, a)] * m2);
+    for (int a = 0; a < P; a++) gfl[a] = kFloorC * sqrtf(acc[up<P>(a, a)] * m2);
 #pragma unroll
     for (int i = 0; i < 6; i++) {
       float z = c.zk2[i] > 0.f ? fmaf(xt[i] - c.lo2[i], c.zk2[i], -1.f) : 0.f;
@@ -2036,7 +2033,7 @@ __device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, float *
   float gfl[P];
   const float m2 = __fdividef(acc[NH + P + 3], fmaxf(acc[NH + P + 4], 1e-30f));
 #pragma unroll
-  for (int i = 0; i < P; i++) gfl[i] = kFloorC * sqrt_est(acc[up<P>(i, i)] * m2);
+  for (int i = 0; i < P; i++) gfl[i] = kFloorC * sqrtf(acc[up<P>(i, i)] * m2);
 #pragma unroll
   for (int i = 0; i < 6; i++) {
     float z = c.zk2[i] > 0.f ? fmaf(xt[i] - c.lo2[i], c.zk2[i], -1.f) : 0.f;
