@@ -192,8 +192,7 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
       lmax = fmaxf(l, lmax);
       lmin = fminf(l, lmin);
     }
-  // (a threshold test: a fast division is enough)
-  kap = lmax > 0.f ? __fdividef(lmax * lmax, lmin * lmin) : 1.f;
+  kap = lmax > 0.f ? (lmax * lmax) / (lmin * lmin) : 1.f;
 #pragma unroll
   for (int i = 0; i < P; i++) {
     T s = y[i];
@@ -556,7 +555,7 @@ struct Stage1 {
 #pragma unroll
     for (int i = 0; i < NH + P + 5; i++) sm[i] = make_float2(0.f, 0.f);
     const float a1 = x[K], invT = 1.f / x[K + 1], invTo = 1.f / xo[K + 1];
-    const float dTT = (x[K + 1] - xo[K + 1]) * invT * invTo;
+    const float dTT = (x[K + 1] - xo[K + 1]) * invT / xo[K + 1];
     const float dal = a1 - xo[K];
     float dxs[K];
 #pragma unroll
@@ -664,7 +663,7 @@ struct Stage1 {
     for (int i = 0; i < NH; i++) H[i] = acc[i];
     // FP32 floor of g_a: kFloorC sqrt(sum_b (w_b J_ba M_b)^2), estimated as
     // kFloorC sqrt(H_aa sum_b w_b^2 M_b^2 / sum_b w_b) (data part of H_aa)
-    const float m2 = __fdividef(acc[NH + P + 3], fmaxf(acc[NH + P + 4], 1e-30f));
+    const float m2 = acc[NH + P + 3] / fmaxf(acc[NH + P + 4], 1e-30f);
 #pragma unroll
     for (int a = 0; a < P; a++) {
       g[a] = acc[NH + a];
@@ -885,7 +884,7 @@ struct Stage2 {
 #pragma unroll
     for (int i = 0; i < NH + P + 5; i++) acc[i] = 0.f;
     const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
-    const float ish3 = ish2 * (1.f / sh), iss3 = iss2 * (1.f / ss);
+    const float ish3 = ish2 / sh, iss3 = iss2 / ss;
     const float sc0 = scale(c, 0), sc1 = scale(c, 1), sc2 = scale(c, 2), sc3 = scale(c, 3);
     const float sc4 = scale(c, 4), sc5 = scale(c, 5);
     const float da_ = al - ao;
@@ -977,7 +976,7 @@ struct Stage2 {
     drop = acc[NH + P + 2];
     // FP32 floor of g_a (as in stage 1), from the data part of H_aa
     float gfl[P];
-    const float m2 = __fdividef(acc[NH + P + 3], fmaxf(acc[NH + P + 4], 1e-30f));
+    const float m2 = acc[NH + P + 3] / fmaxf(acc[NH + P + 4], 1e-30f);
 #pragma unroll
     for (int a = 0; a < P; a++) gfl[a] = kFloorC * sqrtf(acc[up<P>(a, a)] * m2);
 #pragma unroll
@@ -1484,10 +1483,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
       bool accept = first;
       if (!first) {
         drop += S.prior_drop(c, x, xt);
-        const float rho = L.pred > 0.f ? __fdividef(drop, L.pred) : -1.f;
+        const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
         accept = rho > 0.f;
         damping_update(L, accept, rho);
-        if (accept && drop < c.tol_f * cst) { L.status = PX_CONVERGED; go = false; }
+        if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
       }
       if (accept) {
 #pragma unroll
@@ -1637,10 +1636,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
         if (probe) {
           accept = drop > 0.f;
         } else {
-          const float rho = L.pred > 0.f ? __fdividef(drop, L.pred) : -1.f;
+          const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
           accept = rho > 0.f;
           damping_update(L, accept, rho);
-          if (accept && drop < c.tol_f * cst) { L.status = PX_CONVERGED; go = false; }
+          if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
         }
       }
       if (accept) {
@@ -1867,9 +1866,9 @@ __device__ __forceinline__ void coef(const KTables &t, const KConfig &c, const G
     case 2: v = al; break;
     case 3: v = al - x[5]; break;
     case 4: v = eta * ish2 * sc0; break;
-    case 5: v = eta * (ish2 * iht) * sc1; break;
+    case 5: v = eta * (ish2 / sh) * sc1; break;
     case 6: v = (1.f - eta) * iss2 * sc2; break;
-    case 7: v = (1.f - eta) * (iss2 * ist) * sc3; break;
+    case 7: v = (1.f - eta) * (iss2 / ss) * sc3; break;
     case 8: v = 0.5f * (c.hi2[4] - c.lo2[4]); break;
     case 9: v = 0.5f * (c.hi2[5] - c.lo2[5]); break;
     case 10: v = (float)rn; break;
@@ -2031,7 +2030,7 @@ __device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, float *
   cd = acc[NH + P + 1];
   drop = acc[NH + P + 2];
   float gfl[P];
-  const float m2 = __fdividef(acc[NH + P + 3], fmaxf(acc[NH + P + 4], 1e-30f));
+  const float m2 = acc[NH + P + 3] / fmaxf(acc[NH + P + 4], 1e-30f);
 #pragma unroll
   for (int i = 0; i < P; i++) gfl[i] = kFloorC * sqrtf(acc[up<P>(i, i)] * m2);
 #pragma unroll
@@ -2329,10 +2328,10 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
         if (probe) {
           accept = drop > 0.f;
         } else {
-          const float rho = L.pred > 0.f ? __fdividef(drop, L.pred) : -1.f;
+          const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
           accept = rho > 0.f;
           damping_update(L, accept, rho);
-          if (accept && drop < c.tol_f * cst) { L.status = PX_CONVERGED; go = false; }
+          if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
         }
       }
       if (accept) {
