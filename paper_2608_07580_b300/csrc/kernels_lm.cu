@@ -78,10 +78,9 @@ __device__ __forceinline__ constexpr int up(int a, int b) {
   return a <= b ? a * P - (a * (a - 1)) / 2 + (b - a) : b * P - (b * (b - 1)) / 2 + (a - b);
 }
 
-// Reciprocal square root without division: FP32 uses the SFU; FP64 refines an
-// FP32 seed with two Newton-Raphson steps y <- y (3 - x y^2) / 2 (quadratic
+// Reciprocal square root without division for the FP64 covariance: an FP32
+// seed refined with two Newton-Raphson steps y <- y (3 - x y^2) / 2 (quadratic
 // convergence: 2^-23 -> 2^-46 -> full precision).
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) {
   double y = (double)rsqrtf((float)x);
   y = y * (1.5 - 0.5 * x * y * y);
