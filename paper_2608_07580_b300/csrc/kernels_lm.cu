@@ -2109,26 +2109,23 @@ __device__ __forceinline__ bool setup(const LMLaunch &p, float *smem, unsigned l
 }
 
 // one evaluation round of cohort h after its groups wrote their
-// coefficients (flag prm[0] set by every group); mbar is the cohort's.
-// Returns 1 after the evaluation, 0 if the MMA wait timed out, and 2 (no
-// evaluation) when every thread of the cohort passed done: the loop-exit
-// test rides on the round's first barrier.
-constexpr int kRoundDone = 2;
-__device__ __forceinline__ int round(const KTables &t, Cta &C, int h, unsigned long long *mbar,
-                                     unsigned &phase, bool done = false) {
+// coefficients (flag prm[0] set by every group); mbar is the cohort's;
+// false if the MMA wait timed out
+__device__ __forceinline__ bool round(const KTables &t, Cta &C, int h, unsigned long long *mbar,
+                                      unsigned &phase) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (co_and(h, done)) return kRoundDone;
+  co_sync(h);
   if (threadIdx.x == kCoThreads * h)
     mma(C.tmem + (uint32_t)(h * kNc * C.ntile), tc::su32(C.base),
         tc::su32(C.base + 3 * t.plrows * 128 + h * kNc * 128), t.plrows, C.ntile, tc::su32(mbar));
   const bool w = tc::mbar_wait(tc::su32(mbar), phase, kSpinMMA);
   phase ^= 1u;
-  if (!co_and(h, w)) return 0;
+  if (!co_and(h, w)) return false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   band(t, C.tmem, C.slots, C.sstride, C.parts, C.nbs);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   co_sync(h);
-  return 1;
+  return true;
 }
 
 // release (both cohorts): on a timed-out round, a bounded wait for the
@@ -2304,6 +2301,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
         pfs = 2;
       }
     }
+    if (tcs2::co_and(hc, done)) break;
     bool go = active, probe = false;
     if (active && !first) {
       if (alt) {
@@ -2317,9 +2315,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
     }
     if (go) tcs2::coef(t, c, gp, x, xt, co, slot, prm, rc ^ 1);
     if (gp.sub == 0) prm[0] = go ? 1.f : 0.f;
-    const int rr = tcs2::round(t, C, hc, &mbar[hc], phase, done);
-    if (rr == tcs2::kRoundDone) break;
-    if (rr == 0) { ok = false; break; }
+    if (!tcs2::round(t, C, hc, &mbar[hc], phase)) { ok = false; break; }
     nround++;
     if (go) {
       float ct, cdt, drop;
@@ -2436,7 +2432,7 @@ __global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_const
       tcs2::coef(t, c, gp, x, x, co, slot, prm, 1);
     }
     if (gp.sub == 0) prm[0] = has ? 1.f : 0.f;
-    if (tcs2::round(t, C, hc, &mbar[hc], phase) == 0) { ok = false; break; }
+    if (!tcs2::round(t, C, hc, &mbar[hc], phase)) { ok = false; break; }
     if (has) {
       float cst, cd, drop;
       tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, x, S.psc, ne, cst, cd, drop);
