@@ -189,10 +189,18 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
+MAX_BANDS, MAX_ENDM, MAX_TGRID = 512, 8, 256   # ORC_MAXB, ORC_MAXK, ORC_MAXT of oracle.h
+
+
 class _TablesHolder:
     """Keeps the numpy arrays alive while the C struct points at them."""
 
     def __init__(self, t, tgrid=(350.0, 2200.0)):
+        # the C code's per-band, per-endmember and per-node work arrays have
+        # fixed sizes (oracle.h): larger tables are refused here
+        if not (0 < t.n_bands <= MAX_BANDS and 0 < t.n_endm <= MAX_ENDM and 0 < t.n_tgrid <= MAX_TGRID):
+            raise ValueError(f"oracle tables limited to {MAX_BANDS} bands, {MAX_ENDM} endmembers, "
+                             f"{MAX_TGRID} grid nodes")
         f = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)  # noqa
         self.arrs = [f(t.wavelength_nm), f(t.solar_irr), f(t.tau_down), f(t.tau_up),
                      f(t.rho_atm), f(t.sph_alb), f(t.endmembers), f(t.sat_level)]

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 from scenes import config1, parity_stats
 
 pytestmark = pytest.mark.gpu
@@ -143,3 +144,24 @@ def test_autotune_picks_a_valid_shape_and_keeps_parity(fr, torch, c1):
         s = parity_stats(o, g)
         assert s["pool"] >= 0.8 * s["oracle_conv_ident"]
         assert s["rate"] >= 0.99, (variant, s)
+
+
+def test_tensor_core_shape_falls_back_beyond_its_tables(fr, torch):
+    """With 512 bands the stage-2 window holds 384 bands, beyond the
+    tensor-core product's two band tiles: launch shape 6 then runs the FP32
+    stage 2 with 16 lanes per pixel, so its results equal shape 3's bit for
+    bit, and so do its normal equations."""
+    t = synth.make_tables(n_bands=512)
+    tr = synth.make_config1_truth(seed=9, width=24, height=16, fire_frac=0.3)
+    z = synth.noise_normals(9, np.arange(tr.n_pix), t.n_bands)
+    L = oracle.synth_radiance(t, 1, tr.state1(), tr.wv_bin, z, 0.005, 1e-4)
+    ctx = fr.Context(t)
+    assert ctx.window_bands()[3] > 256
+    Ld = _dev(torch, L, torch.float32)
+    wd = _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)
+    outs = []
+    for variant in (3, 6):
+        ctx.set_tuning(variant, 1)
+        outs.append(_np(ctx.retrieve(Ld, wd)))
+    _same(outs[0], outs[1])
+    assert np.isfinite(outs[0]["ET"][(outs[0]["status"] & 7) == 0]).any()

@@ -426,3 +426,12 @@ def test_defaults_follow_paper_constants():
     assert c.hfdi_lambdas == tuple(g["hfdi_bands_nm"]["value"])
     s1, s2 = g["stage_steps"]["value"]
     assert c.max_it1 >= s1 and c.max_it2 >= s2
+
+
+def test_oracle_refuses_tables_beyond_its_work_arrays():
+    """The C oracle's work arrays hold 512 bands, 8 endmembers and 256 grid
+    nodes; larger tables are refused before any C code runs."""
+    import pytest
+    t = synth.make_tables(n_bands=520)
+    with pytest.raises(ValueError):
+        oracle.synth_radiance(t, 1, np.zeros((1, 5)), np.zeros(1, np.int64))
