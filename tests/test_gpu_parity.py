@@ -309,3 +309,53 @@ def test_other_table_shapes_match_oracle(fr, torch, small_tables_scene, variant)
     print(f"variant {variant}:", {k: v for k, v in s.items() if k != "fail_idx"})
     assert s["pool"] >= 0.8 * s["oracle_conv_ident"] and s["pool"] >= 15
     assert s["rate"] >= 0.97
+
+
+@pytest.fixture(scope="module")
+def five_endmember_scene():
+    """Tables with five endmembers (the two added: a flat 0.10 ash and a
+    rising dry-grass spectrum, resampled like the others) and a 48 x 48
+    single-temperature scene drawn over them."""
+    import dataclasses
+    t = synth.make_tables()
+    lam = t.wavelength_nm.astype(np.float64)
+    ash = np.full_like(lam, 0.10)
+    grass = 0.05 + 0.30 * np.clip((lam - 400.0) / 1800.0, 0.0, 1.0)
+    t5 = dataclasses.replace(t, endmembers=np.ascontiguousarray(
+        np.vstack([t.endmembers, ash[None], grass[None]]), dtype=np.float32))
+    tr = synth.make_config1_truth(seed=11, width=48, height=48, n_endm=5)
+    z = synth.noise_normals(11, np.arange(tr.n_pix), t5.n_bands)
+    L = oracle.synth_radiance(t5, 1, tr.state1(), tr.wv_bin, z, NOISE_REL, NOISE_ABS)
+    return t5, tr, L
+
+
+@pytest.mark.parametrize("variant", [3, 6])
+def test_five_endmembers_match_oracle(fr, torch, five_endmember_scene, variant):
+    """K = 5 (the second compiled endmember count) through both stage-2
+    evaluations: the stage-1 normal equations at random states and the
+    retrieval against the oracle."""
+    t, tr, L = five_endmember_scene
+    ctx = fr.Context(t)
+    ctx.set_tuning(variant, 1)
+    rng = np.random.default_rng(41)
+    idx = np.concatenate([np.flatnonzero(tr.kind == 1)[:16], rng.choice(tr.n_pix, 16, replace=False)])
+    n = idx.size
+    st = np.column_stack([rng.dirichlet(np.ones(5), n), 10 ** rng.uniform(-3.5, -0.5, n),
+                          rng.uniform(450, 2100, n)]).astype(np.float32)
+    H, g, cost = ctx.normal_equations(1, _dev(torch, L[idx], torch.float32),
+                                      _dev(torch, tr.wv_bin[idx].astype(np.int16), torch.int16),
+                                      _dev(torch, st, torch.float32))
+    H, g, cost = H.cpu().numpy(), g.cpu().numpy(), cost.cpu().numpy()
+    for j, i in enumerate(idx):
+        Ho, go, co = oracle.normal_equations(t, 1, L[i], tr.wv_bin[i], st[j].astype(np.float64))
+        d = np.sqrt(np.outer(np.diag(Ho), np.diag(Ho)))
+        assert np.max(np.abs(H[j] - Ho) / d) < 2e-4, (variant, i)
+        assert np.max(np.abs(g[j] - go) / np.sqrt(np.diag(Ho) * co)) < 2e-4, (variant, i)
+        assert abs(cost[j] - co) / co < 1e-4, (variant, i)
+    o = oracle.retrieve(t, L, tr.wv_bin)
+    out = _np(ctx.retrieve(_dev(torch, L, torch.float32),
+                           _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)))
+    s = parity_stats(o, out)
+    print(f"K=5 variant {variant}:", {k: v for k, v in s.items() if k != "fail_idx"})
+    assert s["pool"] >= 0.8 * s["oracle_conv_ident"] and s["pool"] >= 15
+    assert s["rate"] >= 0.97
