@@ -359,3 +359,36 @@ def test_five_endmembers_match_oracle(fr, torch, five_endmember_scene, variant):
     print(f"K=5 variant {variant}:", {k: v for k, v in s.items() if k != "fail_idx"})
     assert s["pool"] >= 0.8 * s["oracle_conv_ident"] and s["pool"] >= 15
     assert s["rate"] >= 0.97
+
+
+def test_path_reflectance_retrieval_matches_oracle(fr, torch):
+    """Tables with path reflectance and spherical albedo (the full solar term
+    of Eq. solar, with its denominator 1 - S rho): stage-1 normal equations at
+    random states and the retrieval of a 48 x 48 scene against the oracle."""
+    t = synth.make_tables(path_reflectance=True)
+    tr = synth.make_config1_truth(seed=13, width=48, height=48)
+    z = synth.noise_normals(13, np.arange(tr.n_pix), t.n_bands)
+    L = oracle.synth_radiance(t, 1, tr.state1(), tr.wv_bin, z, NOISE_REL, NOISE_ABS)
+    ctx = fr.Context(t)
+    rng = np.random.default_rng(43)
+    idx = np.concatenate([np.flatnonzero(tr.kind == 1)[:16], rng.choice(tr.n_pix, 16, replace=False)])
+    n = idx.size
+    st = np.column_stack([rng.dirichlet(np.ones(3), n), 10 ** rng.uniform(-3.5, -0.5, n),
+                          rng.uniform(450, 2100, n)]).astype(np.float32)
+    H, g, cost = ctx.normal_equations(1, _dev(torch, L[idx], torch.float32),
+                                      _dev(torch, tr.wv_bin[idx].astype(np.int16), torch.int16),
+                                      _dev(torch, st, torch.float32))
+    H, g, cost = H.cpu().numpy(), g.cpu().numpy(), cost.cpu().numpy()
+    for j, i in enumerate(idx):
+        Ho, go, co = oracle.normal_equations(t, 1, L[i], tr.wv_bin[i], st[j].astype(np.float64))
+        d = np.sqrt(np.outer(np.diag(Ho), np.diag(Ho)))
+        assert np.max(np.abs(H[j] - Ho) / d) < 2e-4, i
+        assert np.max(np.abs(g[j] - go) / np.sqrt(np.diag(Ho) * co)) < 2e-4, i
+        assert abs(cost[j] - co) / co < 1e-4, i
+    o = oracle.retrieve(t, L, tr.wv_bin)
+    out = _np(ctx.retrieve(_dev(torch, L, torch.float32),
+                           _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)))
+    s = parity_stats(o, out)
+    print("path reflectance:", {k: v for k, v in s.items() if k != "fail_idx"})
+    assert s["pool"] >= 0.8 * s["oracle_conv_ident"] and s["pool"] >= 15
+    assert s["rate"] >= 0.97
