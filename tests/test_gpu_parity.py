@@ -392,3 +392,36 @@ def test_path_reflectance_retrieval_matches_oracle(fr, torch):
     print("path reflectance:", {k: v for k, v in s.items() if k != "fail_idx"})
     assert s["pool"] >= 0.8 * s["oracle_conv_ident"] and s["pool"] >= 15
     assert s["rate"] >= 0.97
+
+
+@pytest.mark.parametrize("variant", [3, 6])
+def test_noise_weighted_loss_matches_oracle(fr, torch, c1, variant):
+    """The noise-weighted loss (weights 1 / sd_b^2 of the noise model) on both
+    sides: stage-2 normal equations at random states and the retrieval."""
+    t, tr, L = c1
+    ctx = fr.Context(t, fr.default_config(weighted=1))
+    ctx.set_tuning(variant, 1)
+    cfg = oracle.Config(weighted=True)
+    rng = np.random.default_rng(47)
+    idx = np.concatenate([np.flatnonzero(tr.kind == 1)[:16], rng.choice(tr.n_pix, 16, replace=False)])
+    n = idx.size
+    st = np.column_stack([rng.dirichlet(np.ones(3), n), rng.uniform(950, 2100, n), rng.uniform(35, 400, n),
+                          rng.uniform(380, 990, n), rng.uniform(35, 400, n),
+                          rng.uniform(0.05, 0.95, n), 10 ** rng.uniform(-3.5, -0.5, n)]).astype(np.float32)
+    H, g, cost = ctx.normal_equations(2, _dev(torch, L[idx], torch.float32),
+                                      _dev(torch, tr.wv_bin[idx].astype(np.int16), torch.int16),
+                                      _dev(torch, st, torch.float32))
+    H, g, cost = H.cpu().numpy(), g.cpu().numpy(), cost.cpu().numpy()
+    for j, i in enumerate(idx):
+        Ho, go, co = oracle.normal_equations(t, 2, L[i], tr.wv_bin[i], st[j].astype(np.float64), cfg=cfg)
+        d = np.sqrt(np.outer(np.diag(Ho), np.diag(Ho)))
+        assert np.max(np.abs(H[j] - Ho) / d) < 2e-4, (variant, i)
+        assert np.max(np.abs(g[j] - go) / np.sqrt(np.diag(Ho) * co)) < 2e-4, (variant, i)
+        assert abs(cost[j] - co) / co < 1e-4, (variant, i)
+    o = oracle.retrieve(t, L, tr.wv_bin, cfg=cfg)
+    out = _np(ctx.retrieve(_dev(torch, L, torch.float32),
+                           _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)))
+    s = parity_stats(o, out)
+    print(f"weighted, variant {variant}:", {k: v for k, v in s.items() if k != "fail_idx"})
+    assert s["pool"] >= 0.8 * s["oracle_conv_ident"] and s["pool"] >= 15
+    assert s["rate"] >= 0.97
