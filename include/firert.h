@@ -80,16 +80,19 @@ typedef struct {
   float tgrid_lo, tgrid_hi;
 } fire_tables_t;
 
-/* Solver constants. Windows follow Sec. 2.3/2.6; the iteration caps read the
- * paper's 30/100 optimiser steps as caps (50/100); the rest are this
- * library's stated choices (the paper gives no LM constants). Fill with
- * fire_default_config and edit. */
+/* Solver constants. Windows follow Sec. 2.3/2.6; everything else is this
+ * library's stated choice (the paper gives no LM constants). The iteration
+ * caps (100 / 400 trial steps) are set well above what the damped iteration
+ * needs (stage 2 of the near-degenerate mixture: median ~70, up to ~300 on
+ * flaming pixels), so that a fit stops on a convergence test rather than on
+ * the cap. Fill with fire_default_config and edit. */
 typedef struct {
   float win1_lo, win1_hi;           /* Omega_1 (nm) */
   float win2h_lo, win2h_hi;         /* Omega_2^hot */
   float win2s_lo, win2s_hi;         /* Omega_2^smol; stage 2 fits the union */
   int32_t max_it1, max_it2;         /* trial steps per stage */
-  float tau0;                       /* initial damping = tau0 * max diag */
+  float tau0;                       /* initial damping: the damped matrix is
+                                       H + lambda diag(H), lambda starts at tau0 */
   float tol_g;                      /* |g_i| <= tol_g sqrt(H_ii cost) */
   float tol_x;                      /* max |step| in z below tol_x */
   float tol_f;                      /* relative cost decrease below tol_f */
@@ -106,6 +109,10 @@ typedef struct {
   float hfdi_lambda_hi, hfdi_lambda_lo; /* 2430 nm, 2061 nm */
   float ident_sd_et;                /* identifiable: Laplace sd(E[T]) <= this */
   float ident_alpha_snr;            /* ... and alpha >= snr * sd(alpha) */
+  int64_t wait_spins;               /* polls of a bounded device-side wait (table
+                                       staging, tensor-core product) before it gives
+                                       up and the call reports FIRE_ERR_TIMEOUT;
+                                       0 = the default 2^26 */
 } fire_config_t;
 
 /* Priors: bounds of Eq. (affine), a weak diagonal Gaussian prior in z
@@ -122,6 +129,11 @@ typedef struct {
   int32_t init_mode;                /* FIRE_INIT_* */
   const float *init_state;          /* [n_pix][n_endm + 8] when GIVEN, same
                                        memory kind as the scene */
+  const float *noise_sd;            /* HOST [n_bands] per-band noise sd (> 0), or
+                                       NULL. Given, the loss of Eq. (loss) is
+                                       weighted by 1 / noise_sd_b^2 (and the
+                                       covariance is not rescaled); NULL leaves
+                                       fire_config_t.weighted in charge. */
 } fire_priors_t;
 
 /* One scene: BIP radiance [n_pix][n_bands] fp32 (W m^-2 sr^-1 nm^-1) and
@@ -146,11 +158,16 @@ typedef struct {
  *   var_ET                    delta-method variance of E[T]
  *   cost                      final stage-2 cost; rms: unweighted residual rms
  *   hfdi                      HFDI of the pixel
- *   status, iters [n_pix][2]  status byte; trial steps of stage 1 and 2 */
+ *   status, iters [n_pix][2]  status byte; trial steps of stage 1 and 2
+ *   resid_spec                optional residual spectrum (below) */
 typedef struct {
   float *state, *ET, *sdT, *alpha, *cov, *var_ET, *cost, *rms, *hfdi;
   uint8_t *status;
   uint16_t *iters;
+  float *resid_spec;                /* [n_pix][n_bands]: L_b - M_b(x) of the full
+                                       forward model Eq. (fm) at the final state,
+                                       every band (Sec. 3.2's spectral residuals);
+                                       NaN rows for pixels not fitted */
 } fire_outputs_t;
 
 /* Counters of the last retrieve call (read after the stream synchronises). */
@@ -163,6 +180,8 @@ typedef struct {
   double flops;                     /* algorithmic flops of the fit */
   double flops1, flops2;            /* ... of which stage 1 and stage 2 */
   int32_t kernel_launches;
+  uint64_t n_post64;                /* pixels whose posterior normal matrix was
+                                       formed in FP64 (alpha clear of noise) */
 } fire_stats_t;
 
 typedef struct fire_ctx fire_ctx_t;
@@ -184,8 +203,11 @@ void fire_ctx_destroy(fire_ctx_t *ctx);
 
 /* Retrieve every pixel of one scene (Sec. 2.6 stage 1 then stage 2, per
  * pixel, on the GPU). pri NULL = defaults. n_pix == 0 is a no-op.
- * Errors: FIRE_ERR_ARG, FIRE_ERR_SHAPE, FIRE_ERR_NOMEM (host staging),
- * FIRE_ERR_CUDA, FIRE_ERR_TIMEOUT (table staging wait gave up). */
+ * Errors: FIRE_ERR_ARG, FIRE_ERR_SHAPE, FIRE_ERR_NOMEM (scratch, host
+ * staging), FIRE_ERR_CUDA, FIRE_ERR_TIMEOUT (a bounded device wait gave up;
+ * the outputs are then incomplete). A host scene's call synchronises and
+ * returns the timeout itself; a device scene's call returns before the fit
+ * runs, and the timeout is reported by the next fire_get_stats. */
 fire_status_t fire_retrieve(fire_ctx_t *ctx, const fire_scene_t *scene,
                             const fire_priors_t *pri, const fire_outputs_t *out,
                             fire_stream_t stream);
@@ -366,21 +388,27 @@ fire_status_t fire_set_tuning(fire_ctx_t *ctx, int32_t variant, int32_t claim);
 
 /* ---- Fit without allocation (an addition of this library; the paper has
  * no counterpart). The plain-LM fit of a device scene of at most
- * FIRE_STATIC_MAX_PIX pixels whose scratch (stage hand-over, work
- * counters, statistics, error word; about 3.2 MB) is one file-scope device
- * array of the library: the call makes no cudaMalloc/cudaFree and calls no
- * allocating routine; it clears the counters that must start at zero on
- * the stream and launches the three fit kernels with the context's launch
+ * FIRE_STATIC_MAX_PIX pixels whose scratch (stage hand-over, work counters
+ * and statistics; at most FIRE_STATIC_SCRATCH_BYTES) is one file-scope
+ * device array of the library: the call makes no cudaMalloc/cudaFree and
+ * calls no allocating routine; it clears the counters that must start at
+ * zero on the stream and launches the fit kernels with the context's launch
  * shape, so its results equal fire_retrieve's.
  * - The first call on each device looks up the array's address
  *   (cudaGetSymbolAddress): make it before capturing the call in a graph.
+ *   The address is kept for the life of the process; a cudaDeviceReset
+ *   (which drops the device's copy of the array) invalidates it.
  * - All calls share the one array: two calls whose executions overlap (on
  *   different streams, threads or contexts) race and corrupt each other.
  * - Scene and outputs must be device memory; init_mode DEFAULT or GIVEN.
  * - Errors: FIRE_ERR_SHAPE if n_pix > FIRE_STATIC_MAX_PIX; FIRE_ERR_ARG
- *   for a host scene, the learned start or bad priors; FIRE_ERR_CUDA.
- * fire_get_stats does not see these calls. */
+ *   for a host scene, the learned start or bad priors; FIRE_ERR_CUDA. The
+ *   call returns before the fit runs: a bounded device wait that gives up
+ *   during it is recorded in the context's error word and reported as
+ *   FIRE_ERR_TIMEOUT by the next fire_get_stats on the context (whose
+ *   counters do not include these calls). */
 #define FIRE_STATIC_MAX_PIX 16384
+#define FIRE_STATIC_SCRATCH_BYTES (3u * 1024u * 1024u + 256u * 1024u)
 fire_status_t fire_retrieve_static(fire_ctx_t *ctx, const fire_scene_t *scene,
                                    const fire_priors_t *priors, const fire_outputs_t *out,
                                    fire_stream_t stream);
@@ -399,6 +427,19 @@ fire_status_t fire_get_stats(fire_ctx_t *ctx, fire_stats_t *stats);
 /* Band index ranges of the two fitting windows (for tests and reporting). */
 fire_status_t fire_window_bands(fire_ctx_t *ctx, int32_t *b1_lo, int32_t *n1,
                                 int32_t *b2_lo, int32_t *n2);
+
+/* Device allocator hook. The library's device allocations (context tables
+ * and workspace, host-scene staging, learned-start and batch buffers, the
+ * network's weights) go through alloc(bytes, user) while a hook is set, and
+ * each such block is later returned through the free function that was set
+ * when it was made (so the hook may change at any time). alloc returning
+ * NULL makes the call that needed the memory return FIRE_ERR_NOMEM. alloc
+ * NULL restores cudaMalloc / cudaFree for later allocations. Process-wide;
+ * the functions must be callable from any thread that calls the library.
+ * Pinned host memory (graph scene tables) does not use the hook. */
+typedef void *(*fire_alloc_fn)(size_t bytes, void *user);
+typedef void (*fire_free_fn)(void *ptr, void *user);
+void fire_set_allocator(fire_alloc_fn alloc, fire_free_fn free_fn, void *user);
 
 const char *fire_status_str(fire_status_t s);
 

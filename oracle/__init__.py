@@ -81,7 +81,8 @@ class Config_t(C.Structure):
                 ("noise_rel", C.c_double), ("noise_abs", C.c_double), ("weighted", C.c_int32),
                 ("gate_hfdi", C.c_int32), ("hfdi_thresh", C.c_double),
                 ("hfdi_lambda_hi", C.c_double), ("hfdi_lambda_lo", C.c_double),
-                ("ident_sd_et", C.c_double), ("ident_alpha_snr", C.c_double)]
+                ("ident_sd_et", C.c_double), ("ident_alpha_snr", C.c_double),
+                ("noise_sd", C.c_void_p)]
 
 
 class Outputs_t(C.Structure):
@@ -94,9 +95,12 @@ class Outputs_t(C.Structure):
 class Config:
     """Retrieval constants. Windows: Sec. 2.3 and 2.6 (Omega_1 = [350, 2500] nm,
     Omega_2^hot ~ [900, 1800], Omega_2^smol ~ [1500, 2500]); HFDI gate -0.1
-    at 2430/2061 nm (Sec. 2.1); iteration caps 50/100 read from the paper's
-    30/100 optimiser steps (Sec. 2.6); everything else is the build's stated
-    choice (the paper prints no LM constants and no bounds)."""
+    at 2430/2061 nm (Sec. 2.1); everything else is the build's stated choice
+    (the paper prints no LM constants and no bounds). The iteration caps
+    100/400 lie well above what the damped iteration needs, so that a fit
+    stops on a convergence test; the weak prior pulls T1 and the mixture
+    shape towards the box centre (precision 1) and alpha towards 0 only at
+    1e-6 (regularising J^T J where alpha vanishes)."""
     n_endm: int = 3
     n_tgrid: int = 64
     tgrid_lo: float = 350.0
@@ -110,10 +114,10 @@ class Config:
     init_mu_h_floor: float = 1000.0
     init_mu_s_ceil: float = 700.0
     init_eta: tuple = (0.05, 0.95)
-    max_it1: int = 50
-    max_it2: int = 100
-    tau0: float = 1e-3
-    tol_g: float = 1e-6
+    max_it1: int = 100
+    max_it2: int = 400
+    tau0: float = 1.0
+    tol_g: float = 1e-8
     tol_x: float = 1e-7
     tol_f: float = 1e-10
     kappa_max: float = 1e6
@@ -123,12 +127,13 @@ class Config:
     weighted: bool = False
     prior_prec_T1: float = 1.0
     prior_prec_mix: float = 1.0
-    prior_prec_alpha: float = 1.0
+    prior_prec_alpha: float = 1e-6
     gate_hfdi: bool = False
     hfdi_thresh: float = -0.1
     hfdi_lambdas: tuple = (2430.0, 2061.0)
     ident_sd_et: float = 100.0
     ident_alpha_snr: float = 3.0
+    noise_sd: np.ndarray = None      # per-band noise sd [n_bands]: weights 1 / sd^2
     lo1: np.ndarray = None
     hi1: np.ndarray = None
     lo2: np.ndarray = None
@@ -182,6 +187,10 @@ class Config:
         c.gate_hfdi, c.hfdi_thresh = int(self.gate_hfdi), self.hfdi_thresh
         c.hfdi_lambda_hi, c.hfdi_lambda_lo = self.hfdi_lambdas
         c.ident_sd_et, c.ident_alpha_snr = self.ident_sd_et, self.ident_alpha_snr
+        if self.noise_sd is not None:
+            # the C struct points into this array: keep it alive with the struct
+            c._noise_sd = np.ascontiguousarray(self.noise_sd, dtype=np.float32)
+            c.noise_sd = c._noise_sd.ctypes.data
         return c
 
 
@@ -372,6 +381,36 @@ def adam(w, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     lib().orc_adam(C.c_int64(w.size), vp(w.ctypes.data), vp(g.ctypes.data), vp(m.ctypes.data),
                    vp(v.ctypes.data), C.c_int(t), C.c_double(lr), C.c_double(b1), C.c_double(b2),
                    C.c_double(eps))
+
+
+def posterior_at(tables, radiance, wv_bin, states, cfg=None):
+    """The outputs that follow from given final states alone, per pixel
+    (radiance [n, n_bands] fp32, states [n, K+8] in the layout of retrieve's
+    state): E[T], sigma[T], stage-2 cost, rms, Laplace covariance [n, 21],
+    var(E[T]) and the identifiability flag, as the fit's last step forms them."""
+    cfg = cfg or Config(n_endm=tables.n_endm, n_tgrid=tables.n_tgrid)
+    th = _TablesHolder(tables, (cfg.tgrid_lo, cfg.tgrid_hi))
+    c = cfg.to_c()
+    L = np.ascontiguousarray(radiance, dtype=np.float32)
+    X = np.ascontiguousarray(states, dtype=np.float64)
+    n = L.shape[0]
+    out = {k: np.empty(n) for k in ("ET", "sdT", "cost", "rms", "var_ET")}
+    out["cov"] = np.empty((n, 21))
+    out["ident"] = np.zeros(n, dtype=bool)
+    d = C.c_double
+    for i in range(n):
+        v = [d() for _ in range(5)]
+        cv = np.empty(21)
+        idf = C.c_int()
+        lib().orc_posterior_at(C.byref(th.c), C.byref(c), C.c_void_p(L[i].ctypes.data),
+                               C.c_int(int(wv_bin[i])), C.c_void_p(X[i].ctypes.data),
+                               *[C.byref(x) for x in v[:4]], C.c_void_p(cv.ctypes.data),
+                               C.byref(v[4]), C.byref(idf))
+        for k, x in zip(("ET", "sdT", "cost", "rms", "var_ET"), v):
+            out[k][i] = x.value
+        out["cov"][i] = cv
+        out["ident"][i] = bool(idf.value)
+    return out
 
 
 def normal_equations(tables, stage, radiance_row, wv_bin, x, cfg=None):

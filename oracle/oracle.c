@@ -418,12 +418,9 @@ static int lm_fit(const pix_t *P, const lm_prob_t *q, const orc_config_t *c, dou
       for (int a = 0; a < pr; a++)
         if (!act[a] && fabs(gr[a]) > c->tol_g * sqrt(Hr[a * pr + a] * cost)) small = 0;
       if (small) { status = ORC_CONVERGED; break; }
-      if (lam < 0) {
-        double mx = 0;
-        for (int a = 0; a < pr; a++)
-          if (!act[a] && Hr[a * pr + a] > mx) mx = Hr[a * pr + a];
-        lam = c->tau0 * mx;
-      }
+      /* initial damping: D = diag(Hr) below, so lam is the relative damping
+       * of each diagonal and starts at tau0 */
+      if (lam < 0) lam = c->tau0;
       fresh = 0;
     }
     /* damped solve (Hr_FF + lam D) d = gr_F, D = diag(Hr) floored, on the
@@ -631,6 +628,121 @@ void orc_synth_radiance(const orc_tables_t *t, int mode, const double *state,
 }
 
 /* ------------------------------------------------------ retrieval ----- */
+/* Noise variance of band b at radiance L: the caller's per-band sd when
+ * given, else the noise model (rel L)^2 + abs^2. */
+static double noise_var(const orc_config_t *c, int b, double L) {
+  if (c->noise_sd) return (double)c->noise_sd[b] * c->noise_sd[b];
+  return c->noise_rel * c->noise_rel * L * L + c->noise_abs * c->noise_abs;
+}
+
+/* The loss is noise-weighted (w_b = 1 / variance) when the caller gives
+ * per-band sd or asks for the noise model's weights; otherwise it is
+ * Eq. (loss) as printed (w_b = 1 on unmasked bands). */
+static int loss_weighted(const orc_config_t *c) { return c->weighted || c->noise_sd != NULL; }
+
+/* Per-pixel set-up shared by the fit and the posterior: observed radiance,
+ * mask m(lambda) (saturation, Eq. loss), band weights, the two windows'
+ * weights w1 / w2 and used-band counts, and the prior scales (mean noise
+ * variance of each window's used bands under the unweighted loss, 1 under
+ * a weighted one). */
+static void pixel_setup(pix_t *P, const orc_tables_t *t, const orc_config_t *c, const float *Lrow,
+                        double *w1, double *w2, int *n1, int *n2, double *psc1, double *psc2) {
+  int nb = t->n_bands;
+  double s1 = 0, s2 = 0;
+  *n1 = *n2 = 0;
+  for (int b = 0; b < nb; b++) {
+    P->Lobs[b] = Lrow[b];
+    int ok = !(t->sat_level && Lrow[b] >= t->sat_level[b]);   /* m(lambda), Eq. (loss) */
+    double var = noise_var(c, b, P->Lobs[b]);
+    P->wgt[b] = ok ? (loss_weighted(c) ? 1.0 / var : 1.0) : 0.0;
+    double l = P->lam[b];
+    int in1 = l >= c->win1_lo && l <= c->win1_hi;
+    int in2 = (l >= c->win2h_lo && l <= c->win2h_hi) || (l >= c->win2s_lo && l <= c->win2s_hi);
+    w1[b] = in1 ? P->wgt[b] : 0.0;
+    w2[b] = in2 ? P->wgt[b] : 0.0;
+    if (w1[b] > 0) { (*n1)++; s1 += var; }
+    if (w2[b] > 0) { (*n2)++; s2 += var; }
+  }
+  *psc1 = loss_weighted(c) || *n1 == 0 ? 1.0 : s1 / *n1;
+  *psc2 = loss_weighted(c) || *n2 == 0 ? 1.0 : s2 / *n2;
+}
+
+/* Posterior at the final stage-2 state x2 (the outputs of Sec. 2.3 and the
+ * Laplace covariance): from the normal matrix H = J^T W J + P at x2 in the z
+ * coordinates of Eq. (affine), its active set, the cost and the used-band
+ * count. C = s2 (H_FF)^-1 over the free variables, in FP64, in physical
+ * units (s_i s_j); fixed (active) variables get zero rows; a free variable
+ * with a zero column has infinite variance. var(E[T]) = gE^T C gE with gE =
+ * dE/dx2. With alpha held on its lower bound there is no thermal signal:
+ * E[T] and its posterior are undefined (covariance NaN, var(E[T]) = inf).
+ * Identifiable: Laplace sd(E[T]) <= ident_sd_et and alpha >= snr sd(alpha),
+ * alpha free and positive. Writes cv[21] (packed upper) and var(E[T]);
+ * returns 1 if identifiable. */
+static int posterior(const orc_config_t *c, const double *x2, const double *H, const int *active,
+                     double cost, int n_used, double *cv, double *var_ET) {
+  const double *lo2 = c->lo2, *hi2 = c->hi2;
+  int F[6], nf = 0, zero_col[6] = {0};
+  for (int k = 0; k < 6; k++) {
+    if (active[k]) continue;
+    if (!(H[k * 6 + k] > 0)) { zero_col[k] = 1; continue; }
+    F[nf++] = k;
+  }
+  double s2 = loss_weighted(c) ? 1.0 : cost / (double)(n_used - nf);
+  double Cz[36];
+  memset(Cz, 0, sizeof(Cz));
+  int cov_ok = 1;
+  int no_signal = active[5] && x2[5] <= lo2[5];
+  if (no_signal) cov_ok = 0;
+  if (nf > 0 && !no_signal) {
+    double A[36], dsc[6];
+    for (int u = 0; u < nf; u++) dsc[u] = sqrt(H[F[u] * 6 + F[u]]);
+    for (int u = 0; u < nf; u++)
+      for (int v = 0; v < nf; v++) A[u * nf + v] = H[F[u] * 6 + F[v]] / (dsc[u] * dsc[v]);
+    if (orc_cholesky(A, nf) != 0) cov_ok = 0;
+    else {
+      for (int v = 0; v < nf; v++) {
+        double e[6] = {0};
+        e[v] = 1.0;
+        orc_chol_solve(A, nf, e);
+        for (int u = 0; u < nf; u++) Cz[F[u] * 6 + F[v]] = s2 * e[u] / (dsc[u] * dsc[v]);
+      }
+    }
+  }
+  double sc[6];
+  for (int k = 0; k < 6; k++) sc[k] = 0.5 * (hi2[k] - lo2[k]);
+  double Cx[36];
+  for (int a = 0; a < 6; a++)
+    for (int b = 0; b < 6; b++) {
+      Cx[a * 6 + b] = cov_ok ? Cz[a * 6 + b] * sc[a] * sc[b] : NAN;
+      if (a == b && zero_col[a]) Cx[a * 6 + b] = INFINITY;
+    }
+  int q = 0;
+  for (int a = 0; a < 6; a++)
+    for (int b = a; b < 6; b++) cv[q++] = Cx[a * 6 + b];
+  double gE[6] = {x2[4], 0, 1.0 - x2[4], 0, x2[0] - x2[2], 0};
+  double vE = 0;
+  for (int a = 0; a < 6; a++) {
+    if (gE[a] == 0) continue;
+    if (zero_col[a]) { vE = INFINITY; break; }
+    for (int b = 0; b < 6; b++)
+      if (gE[b] != 0) vE += gE[a] * Cx[a * 6 + b] * gE[b];
+  }
+  if (no_signal) vE = INFINITY;
+  *var_ET = vE;
+  double sdE = sqrt(vE), sda = sqrt(Cx[35]);
+  return cov_ok && isfinite(sdE) && sdE <= c->ident_sd_et && x2[5] >= c->ident_alpha_snr * sda &&
+         !active[5] && x2[5] > 0;
+}
+
+/* unweighted residual rms of the stage-2 model over the used bands */
+static double stage2_rms(const pix_t *P, const double *x2, const double *w2, int n_used) {
+  double L[ORC_MAXB], cdata = 0;
+  eval_stage2(P, x2, w2, L, NULL);
+  for (int b = 0; b < P->nb; b++)
+    if (w2[b] > 0) cdata += (P->Lobs[b] - L[b]) * (P->Lobs[b] - L[b]);
+  return sqrt(cdata / n_used);
+}
+
 static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const double *Bt,
                            const float *Lrow, int w, const double *init, orc_outputs_t *o,
                            int64_t i) {
@@ -652,40 +764,11 @@ static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const d
 
   pix_t *P = (pix_t *)malloc(sizeof(pix_t));
   pix_tables(P, t, w, Bt);
-  for (int b = 0; b < nb; b++) {
-    P->Lobs[b] = Lrow[b];
-    int ok = !(t->sat_level && Lrow[b] >= t->sat_level[b]);   /* m(lambda), Eq. (loss) */
-    double wt = 1.0;
-    if (c->weighted)
-      wt = 1.0 / (c->noise_rel * c->noise_rel * P->Lobs[b] * P->Lobs[b] + c->noise_abs * c->noise_abs);
-    P->wgt[b] = ok ? wt : 0.0;
-  }
-  double w1[ORC_MAXB], w2[ORC_MAXB];
-  int n1 = 0, n2 = 0;
-  for (int b = 0; b < nb; b++) {
-    double l = P->lam[b];
-    int in1 = l >= c->win1_lo && l <= c->win1_hi;
-    int in2 = (l >= c->win2h_lo && l <= c->win2h_hi) || (l >= c->win2s_lo && l <= c->win2s_hi);
-    w1[b] = in1 ? P->wgt[b] : 0.0;
-    w2[b] = in2 ? P->wgt[b] : 0.0;
-    n1 += w1[b] > 0;
-    n2 += w2[b] > 0;
-  }
+  double w1[ORC_MAXB], w2[ORC_MAXB], psc1, psc2;
+  int n1, n2;
+  pixel_setup(P, t, c, Lrow, w1, w2, &n1, &n2, &psc1, &psc2);
   int status = 0;
   if (n1 <= K + 2 || n2 <= 6) { o->status[i] = ORC_ALL_MASKED; free(P); return; }
-  /* prior scale: mean noise variance (rel^2 L^2 + abs^2) over the used bands of
-   * each stage in the unweighted loss; 1 when the loss is noise-weighted */
-  double psc1 = 1.0, psc2 = 1.0;
-  if (!c->weighted) {
-    double s1 = 0, s2 = 0;
-    for (int b = 0; b < nb; b++) {
-      double v = c->noise_rel * c->noise_rel * P->Lobs[b] * P->Lobs[b] + c->noise_abs * c->noise_abs;
-      if (w1[b] > 0) s1 += v;
-      if (w2[b] > 0) s2 += v;
-    }
-    psc1 = s1 / n1;
-    psc2 = s2 / n2;
-  }
 
   /* stage 1: x1 = [x_surf, a1, T1] */
   double x1[ORC_NS1];
@@ -752,78 +835,48 @@ static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const d
   o->cost[i] = r2.cost;
   o->kappa[i] = r1.kappa > r2.kappa ? r1.kappa : r2.kappa;
   o->n_used[i] = r2.n_used;
-  double cdata = 0;
-  {
-    double L[ORC_MAXB];
-    eval_stage2(P, x2, w2, L, NULL);
-    for (int b = 0; b < nb; b++)
-      if (w2[b] > 0) cdata += (P->Lobs[b] - L[b]) * (P->Lobs[b] - L[b]);
-  }
-  o->rms[i] = sqrt(cdata / r2.n_used);
-
-  /* Laplace covariance C = s2 (J^T W J + P)^-1 over the free variables at
-   * the final state, FP64, converted to physical units (s_i s_j). Fixed
-   * (active) variables get zero rows; a free variable with a zero column
-   * has infinite variance. */
-  int F[6], nf = 0, zero_col[6] = {0};
-  double hmax = 0;
-  for (int k = 0; k < 6; k++) if (r2.H[k * 6 + k] > hmax) hmax = r2.H[k * 6 + k];
-  for (int k = 0; k < 6; k++) {
-    if (r2.active[k]) continue;
-    if (!(r2.H[k * 6 + k] > 0)) { zero_col[k] = 1; continue; }
-    F[nf++] = k;
-  }
-  double s2 = c->weighted ? 1.0 : r2.cost / (double)(r2.n_used - nf);
-  double Cz[36];
-  memset(Cz, 0, sizeof(Cz));
-  int cov_ok = 1;
-  /* alpha held on its lower bound: no thermal signal, so E[T] and its
-   * posterior are undefined */
-  int no_signal = r2.active[5] && x2[5] <= lo2[5];
-  if (no_signal) cov_ok = 0;
-  if (nf > 0 && !no_signal) {
-    double A[36], dsc[6];
-    for (int u = 0; u < nf; u++) dsc[u] = sqrt(r2.H[F[u] * 6 + F[u]]);
-    for (int u = 0; u < nf; u++)
-      for (int v = 0; v < nf; v++) A[u * nf + v] = r2.H[F[u] * 6 + F[v]] / (dsc[u] * dsc[v]);
-    if (orc_cholesky(A, nf) != 0) cov_ok = 0;
-    else {
-      for (int v = 0; v < nf; v++) {
-        double e[6] = {0};
-        e[v] = 1.0;
-        orc_chol_solve(A, nf, e);
-        for (int u = 0; u < nf; u++) Cz[F[u] * 6 + F[v]] = s2 * e[u] / (dsc[u] * dsc[v]);
-      }
-    }
-  }
-  double sc[6];
-  for (int k = 0; k < 6; k++) sc[k] = 0.5 * (hi2[k] - lo2[k]);
-  double Cx[36];
-  for (int a = 0; a < 6; a++)
-    for (int b = 0; b < 6; b++) {
-      Cx[a * 6 + b] = cov_ok ? Cz[a * 6 + b] * sc[a] * sc[b] : NAN;
-      if (a == b && zero_col[a]) Cx[a * 6 + b] = INFINITY;
-    }
-  int q = 0;
-  for (int a = 0; a < 6; a++)
-    for (int b = a; b < 6; b++) cv[q++] = Cx[a * 6 + b];
-  /* var(E[T]) = g^T C g, g = dE/dx2 = (eta, 0, 1-eta, 0, mu_h - mu_s, 0) */
-  double gE[6] = {x2[4], 0, 1.0 - x2[4], 0, x2[0] - x2[2], 0};
-  double vE = 0;
-  for (int a = 0; a < 6; a++) {
-    if (gE[a] == 0) continue;
-    if (zero_col[a]) { vE = INFINITY; break; }
-    for (int b = 0; b < 6; b++)
-      if (gE[b] != 0) vE += gE[a] * Cx[a * 6 + b] * gE[b];
-  }
-  if (no_signal) vE = INFINITY;
-  o->var_ET[i] = vE;
-  double sdE = sqrt(vE), sda = sqrt(Cx[35]);
-  int ident = cov_ok && isfinite(sdE) && sdE <= c->ident_sd_et && x2[5] >= c->ident_alpha_snr * sda &&
-              !r2.active[5] && x2[5] > 0;
-  if (!ident) status |= ORC_F_NOT_IDENT;
+  o->rms[i] = stage2_rms(P, x2, w2, r2.n_used);
+  if (!posterior(c, x2, r2.H, r2.active, r2.cost, r2.n_used, cv, &o->var_ET[i])) status |= ORC_F_NOT_IDENT;
   o->status[i] = status;
   free(P);
+}
+
+/* The outputs that follow from a given final state alone (the posterior
+ * step of the retrieval, for checking it apart from the fit): at state
+ * [x_surf(K), a1, T1, mu_h, s_h, mu_s, s_s, eta, a] the stage-2 cost of
+ * Eq. (loss) plus the prior, its normal matrix and active set, then E[T],
+ * sigma[T] (Sec. 2.3), the Laplace covariance, var(E[T]), the unweighted
+ * residual rms and the identifiability flag, exactly as the fit's last step
+ * forms them. The surface fractions fix the solar term of stage 2. */
+void orc_posterior_at(const orc_tables_t *t, const orc_config_t *c, const float *Lrow, int w,
+                      const double *state, double *ET, double *sdT, double *cost, double *rms,
+                      double *cov21, double *var_ET, int *ident) {
+  int K = t->n_endm, nb = t->n_bands;
+  double *Bt = planck_table(t);
+  pix_t *P = (pix_t *)malloc(sizeof(pix_t));
+  pix_tables(P, t, w, Bt);
+  double w1[ORC_MAXB], w2[ORC_MAXB], psc1, psc2;
+  int n1, n2;
+  pixel_setup(P, t, c, Lrow, w1, w2, &n1, &n2, &psc1, &psc2);
+  for (int b = 0; b < nb; b++) P->Ls[b] = solar_term(P, b, state, NULL);
+  const double *x2 = state + K + 2;
+  lm_prob_t q2 = {2, 6, 0, c->lo2, c->hi2, c->pm2, c->pp2, w2, 0, psc2};
+  double L[ORC_MAXB], H[36], g[6];
+  double *J = (double *)malloc(sizeof(double) * nb * 6);
+  evaluate(P, &q2, x2, L, J);
+  *cost = cost_of(P, &q2, x2, L);
+  normal_eq(P, &q2, x2, L, J, H, g);
+  int active[6];
+  for (int k = 0; k < 6; k++)
+    active[k] = (x2[k] <= c->lo2[k] && g[k] <= 0) || (x2[k] >= c->hi2[k] && g[k] >= 0);
+  double V;
+  orc_moments(x2, ET, &V);
+  *sdT = sqrt(V);
+  *rms = stage2_rms(P, x2, w2, n2);
+  *ident = posterior(c, x2, H, active, *cost, n2, cov21, var_ET);
+  free(J);
+  free(P);
+  free(Bt);
 }
 
 void orc_retrieve(const orc_tables_t *t, const orc_config_t *c, const float *radiance,
@@ -964,11 +1017,11 @@ void orc_normal_equations(const orc_tables_t *t, const orc_config_t *c, int stag
     double l = P->lam[b];
     int in = stage == 1 ? (l >= c->win1_lo && l <= c->win1_hi)
                         : ((l >= c->win2h_lo && l <= c->win2h_hi) || (l >= c->win2s_lo && l <= c->win2s_hi));
-    double var = c->noise_rel * c->noise_rel * P->Lobs[b] * P->Lobs[b] + c->noise_abs * c->noise_abs;
-    ws[b] = (ok && in) ? (c->weighted ? 1.0 / var : 1.0) : 0.0;
+    double var = noise_var(c, b, P->Lobs[b]);
+    ws[b] = (ok && in) ? (loss_weighted(c) ? 1.0 / var : 1.0) : 0.0;
     if (ws[b] > 0) { n++; sv += var; }
   }
-  double psc = c->weighted ? 1.0 : sv / n;
+  double psc = loss_weighted(c) ? 1.0 : sv / n;
   lm_prob_t q1 = {1, K + 2, K, c->lo1, c->hi1, c->pm1, c->pp1, ws, 0, psc};
   lm_prob_t q2 = {2, 6, 0, c->lo2, c->hi2, c->pm2, c->pp2, ws, 0, psc};
   const lm_prob_t *q = stage == 1 ? &q1 : &q2;

@@ -53,6 +53,8 @@ typedef struct {
   int32_t gate_hfdi;
   double hfdi_thresh, hfdi_lambda_hi, hfdi_lambda_lo;
   double ident_sd_et, ident_alpha_snr;
+  const float *noise_sd;              /* [n_bands] per-band noise sd, or NULL; when given
+                                         the loss is weighted by 1 / sd_b^2 */
 } orc_config_t;
 
 typedef struct {
@@ -90,6 +92,9 @@ double orc_mlp_backward(int B, int Din, int H, int Dout, int n_out, const double
                         double *gb3);
 void orc_adam(int64_t n, double *w, const double *g, double *m, double *v, int t, double lr,
               double b1, double b2, double eps);
+void orc_posterior_at(const orc_tables_t *t, const orc_config_t *c, const float *Lrow, int w,
+                      const double *state, double *ET, double *sdT, double *cost, double *rms,
+                      double *cov21, double *var_ET, int *ident);
 void orc_normal_equations(const orc_tables_t *t, const orc_config_t *c, int stage,
                           const float *Lrow, int w, const double *x, double *Hout, double *gout,
                           double *cost_out);

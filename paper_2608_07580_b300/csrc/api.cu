@@ -54,7 +54,7 @@ int nearest_band(const float *wl, int nb, float lam) {
   return best;
 }
 
-void fill_kconfig(KConfig &k, const fire_config_t &c, const fire_priors_t &p, int K) {
+void fill_kconfig(KConfig &k, const fire_config_t &c, const fire_priors_t &p, int K, int nb) {
   memset(&k, 0, sizeof(k));
   for (int i = 0; i < K + 2; i++) {
     k.lo1[i] = p.lo1[i];
@@ -87,16 +87,20 @@ void fill_kconfig(KConfig &k, const fire_config_t &c, const fire_priors_t &p, in
   k.dfloor = c.dfloor;
   k.noise_rel = c.noise_rel;
   k.noise_abs = c.noise_abs;
-  k.weighted = c.weighted;
+  k.weighted = c.weighted || p.noise_sd ? 1 : 0;
   k.hfdi_thresh = c.hfdi_thresh;
   k.ident_sd_et = c.ident_sd_et;
   k.ident_alpha_snr = c.ident_alpha_snr;
+  k.wait_spins = c.wait_spins > 0 ? (long long)c.wait_spins : (1ll << 26);
+  k.has_nsd = p.noise_sd ? 1 : 0;
+  if (p.noise_sd)
+    for (int b = 0; b < nb && b < kMaxBands; b++) k.nsd[b] = p.noise_sd[b];
 }
 
 
 template <class T>
 fire_status_t dev_alloc(T **p, size_t bytes) {
-  cudaError_t e = cudaMalloc((void **)p, bytes);
+  cudaError_t e = dev_malloc((void **)p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
@@ -107,10 +111,10 @@ fire_status_t dev_alloc(T **p, size_t bytes) {
 
 fire_status_t ensure_s1(fire_ctx *c, int64_t n) {
   if (n <= c->s1_cap) return FIRE_OK;
-  cudaFree(c->d_s1x);
-  cudaFree(c->d_s1meta);
-  cudaFree(c->d_s2x);
-  cudaFree(c->d_s2g);
+  dev_free(c->d_s1x);
+  dev_free(c->d_s1meta);
+  dev_free(c->d_s2x);
+  dev_free(c->d_s2g);
   c->d_s1x = nullptr;
   c->d_s1meta = nullptr;
   c->d_s2x = c->d_s2g = nullptr;
@@ -123,13 +127,15 @@ fire_status_t ensure_s1(fire_ctx *c, int64_t n) {
   return e;
 }
 
-// carve per-pixel output arrays for n pixels out of one buffer
-size_t outputs_bytes(int64_t n, int K) {
+// carve per-pixel output arrays for n pixels out of one buffer (the
+// residual spectrum [n][nb] only when nb > 0)
+size_t outputs_bytes(int64_t n, int K, int nb = 0) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t szf = (size_t)n * 4;
-  return al(szf * (K + 8)) + 7 * al(szf) + al(szf * 21) + al((size_t)n) + al((size_t)n * 4);
+  return al(szf * (K + 8)) + 7 * al(szf) + al(szf * 21) + al((size_t)n) + al((size_t)n * 4) +
+         al(szf * nb);
 }
-KOut carve_outputs(void *buf, int64_t n, int K) {
+KOut carve_outputs(void *buf, int64_t n, int K, int nb = 0) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t szf = (size_t)n * 4;
   char *q = (char *)buf;
@@ -146,6 +152,7 @@ KOut carve_outputs(void *buf, int64_t n, int K) {
   o.cov = (float *)carve(szf * 21);
   o.status = (uint8_t *)carve((size_t)n);
   o.iters = (uint16_t *)carve((size_t)n * 4);
+  o.resid = nb > 0 ? (float *)carve(szf * nb) : nullptr;
   return o;
 }
 
@@ -164,6 +171,13 @@ bool priors_valid(const fire_priors_t &p, int K) {
   if (p.init_mode != FIRE_INIT_DEFAULT && p.init_mode != FIRE_INIT_GIVEN &&
       p.init_mode != FIRE_INIT_MLP)
     return false;
+  return true;
+}
+
+bool noise_sd_valid(const fire_priors_t &p, int nb) {
+  if (!p.noise_sd) return true;
+  for (int b = 0; b < nb; b++)
+    if (!(p.noise_sd[b] > 0.f) || !isfinite(p.noise_sd[b])) return false;
   return true;
 }
 
@@ -197,9 +211,9 @@ fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
   const int64_t n = p.s.n_pix;
   const int K = c->t.K;
   if (n > c->mlp_cap) {
-    cudaFree(c->d_mlp_init);
-    cudaFree(c->d_fb_idx);
-    cudaFree(c->d_fb_cost);
+    dev_free(c->d_mlp_init);
+    dev_free(c->d_fb_idx);
+    dev_free(c->d_fb_cost);
     c->d_mlp_init = nullptr;
     c->d_fb_idx = nullptr;
     c->d_fb_cost = nullptr;
@@ -226,14 +240,14 @@ fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
   c->last_launches = 3 + 6;   // network (inference kernels) + fit
   if (nfb == 0) return FIRE_OK;
   if ((int64_t)nfb > c->cmp_cap) {
-    cudaFree(c->d_cmp);
+    dev_free(c->d_cmp);
     c->d_cmp = nullptr;
     c->cmp_cap = 0;
-    e = dev_alloc((char **)&c->d_cmp, outputs_bytes((int64_t)nfb, K));
+    e = dev_alloc((char **)&c->d_cmp, outputs_bytes((int64_t)nfb, K, c->t.nb));
     if (e != FIRE_OK) return e;
     c->cmp_cap = (int64_t)nfb;
   }
-  KOut cmp = carve_outputs(c->d_cmp, (int64_t)nfb, K);
+  KOut cmp = carve_outputs(c->d_cmp, (int64_t)nfb, K, p.o.resid ? c->t.nb : 0);
   LMLaunch q = p;
   q.s.n_pix = (int64_t)nfb;
   q.s.idx = c->d_fb_idx;
@@ -246,7 +260,7 @@ fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
   q.o.hfdi = nullptr;
   CK(cudaMemsetAsync(c->d_work, 0, 2 * 8, st));   // claim counters only; stats accumulate
   CK(launch_lm(q, c->num_sms, st, &blocks, c->tune_variant));
-  CK(launch_merge_fallback(c->d_fb_idx, c->d_fb_cost, (long long)nfb, cmp, p.o, K, st));
+  CK(launch_merge_fallback(c->d_fb_idx, c->d_fb_cost, (long long)nfb, cmp, p.o, K, c->t.nb, st));
   c->last_launches += 4;
   return FIRE_OK;
 }
@@ -255,8 +269,9 @@ fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st) {
 fire_status_t prepare_launch(fire_ctx *c, const fire_priors_t *pri, int64_t n, int gate, LMLaunch &p,
                              bool ctx_scratch) {
   memset(&p, 0, sizeof(p));
+  if (!priors_valid(*pri, c->t.K) || !noise_sd_valid(*pri, c->t.nb)) return FIRE_ERR_ARG;
   p.t = c->t;
-  fill_kconfig(p.c, c->cfg, *pri, c->t.K);
+  fill_kconfig(p.c, c->cfg, *pri, c->t.K, c->t.nb);
   p.s.n_pix = n;
   p.s.gate = gate;
   p.s.claim = c->tune_claim;
@@ -293,10 +308,10 @@ void fire_default_config(fire_config_t *c) {
   c->win2h_hi = 1800.f;
   c->win2s_lo = 1500.f;
   c->win2s_hi = 2500.f;
-  c->max_it1 = 50;
-  c->max_it2 = 100;
-  c->tau0 = 1e-3f;
-  c->tol_g = 1e-6f;
+  c->max_it1 = 100;
+  c->max_it2 = 400;
+  c->tau0 = 1.f;
+  c->tol_g = 1e-8f;
   c->tol_x = 1e-7f;
   c->tol_f = 1e-10f;
   c->kappa_max = 1e6f;
@@ -324,8 +339,11 @@ void fire_default_priors(fire_priors_t *p, int32_t K, int32_t nt, float tlo, flo
   p->hi1[K] = 1.f;
   p->lo1[K + 1] = tlo;  // T1 on the temperature grid
   p->hi1[K + 1] = thi;
-  p->pm1[K] = -1.f;     // weak prior: alpha towards 0, T1 towards the grid centre
-  p->pp1[K] = 1.f;
+  // weak prior in z: alpha towards 0 at 1e-6 (it only regularises J^T J
+  // where alpha vanishes); T1 and the mixture shape towards the box centre
+  // at 1 (the regulariser of the near-degenerate mixture)
+  p->pm1[K] = -1.f;
+  p->pp1[K] = 1e-6f;
   p->pm1[K + 1] = 0.f;
   p->pp1[K + 1] = 1.f;
   const float lo2[6] = {900.f, dT, tlo, dT, 0.f, 0.f};
@@ -334,7 +352,7 @@ void fire_default_priors(fire_priors_t *p, int32_t K, int32_t nt, float tlo, flo
     p->lo2[i] = lo2[i];
     p->hi2[i] = hi2[i];
     p->pm2[i] = i == 5 ? -1.f : 0.f;
-    p->pp2[i] = 1.f;
+    p->pp2[i] = i == 5 ? 1e-6f : 1.f;
   }
   p->init_alpha1 = 0.01f;
   p->init_T1 = 800.f;
@@ -366,25 +384,27 @@ void fire_ctx_destroy(fire_ctx_t *ctx) {
   for (cudaEvent_t e : ctx->chunk_ev) cudaEventDestroy(e);
   if (ctx->copy_st) cudaStreamDestroy(ctx->copy_st);
   if (ctx->fit_st2) cudaStreamDestroy(ctx->fit_st2);
-  cudaFree(ctx->d_ctr);
-  cudaFree(ctx->d_image);
-  cudaFree(ctx->d_plop);
-  cudaFree(ctx->d_wvtab);
-  cudaFree(ctx->d_sat);
-  cudaFree(ctx->d_work);
-  cudaFree(ctx->d_err);
-  cudaFree(ctx->d_stage);
-  cudaFree(ctx->d_s1x);
-  cudaFree(ctx->d_s1meta);
-  cudaFree(ctx->d_s2x);
-  cudaFree(ctx->d_s2g);
-  cudaFree(ctx->d_mlp_init);
-  cudaFree(ctx->d_fb_idx);
-  cudaFree(ctx->d_fb_cost);
-  cudaFree(ctx->d_fb_count);
-  cudaFree(ctx->d_cmp);
-  cudaFree(ctx->d_items);
-  cudaFree(ctx->d_prefix);
+  dev_free(ctx->d_ctr);
+  dev_free(ctx->d_image);
+  dev_free(ctx->d_planck_full);
+  dev_free(ctx->d_planck64);
+  dev_free(ctx->d_plop);
+  dev_free(ctx->d_wvtab);
+  dev_free(ctx->d_sat);
+  dev_free(ctx->d_work);
+  dev_free(ctx->d_err);
+  dev_free(ctx->d_stage);
+  dev_free(ctx->d_s1x);
+  dev_free(ctx->d_s1meta);
+  dev_free(ctx->d_s2x);
+  dev_free(ctx->d_s2g);
+  dev_free(ctx->d_mlp_init);
+  dev_free(ctx->d_fb_idx);
+  dev_free(ctx->d_fb_cost);
+  dev_free(ctx->d_fb_count);
+  dev_free(ctx->d_cmp);
+  dev_free(ctx->d_items);
+  dev_free(ctx->d_prefix);
   for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   delete ctx;
 }
@@ -452,10 +472,13 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
   size_t nraw = (size_t)nb * 2 + (size_t)nwv * nb * 4 + (size_t)K * nb;
   do {
     if ((st = dev_alloc(&c->d_image, (size_t)L.total * 4)) != FIRE_OK) break;
+    if ((st = dev_alloc(&c->d_planck_full, (size_t)nt * nb * 4)) != FIRE_OK) break;
+    if ((st = dev_alloc(&c->d_planck64, (size_t)nt * t.n2 * 8)) != FIRE_OK) break;
     if ((st = dev_alloc(&c->d_plop, planck_operand_bytes(t))) != FIRE_OK) break;
     if ((st = dev_alloc(&c->d_wvtab, (size_t)nwv * nb * sizeof(float4))) != FIRE_OK) break;
     if ((st = dev_alloc(&c->d_work, (size_t)(2 + ST_COUNT) * 8)) != FIRE_OK) break;
     if ((st = dev_alloc(&c->d_err, sizeof(int))) != FIRE_OK) break;
+    if ((st = cuda_status(cudaMemset(c->d_err, 0, sizeof(int)))) != FIRE_OK) break;
     if ((st = dev_alloc(&raw, nraw * 4)) != FIRE_OK) break;
     if (tb->sat_level) {
       if ((st = dev_alloc(&c->d_sat, (size_t)nb * 4)) != FIRE_OK) break;
@@ -483,11 +506,15 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
       break;
     if ((st = cuda_status(launch_planck_operand(t, c->d_plop, 0))) != FIRE_OK) break;
     t.plop = c->d_plop;
+    if ((st = cuda_status(launch_planck_full(t, d_wl, c->d_planck_full, 0))) != FIRE_OK) break;
+    t.planck_full = c->d_planck_full;
+    if ((st = cuda_status(launch_planck64(t, d_wl, c->d_planck64, 0))) != FIRE_OK) break;
+    t.planck64 = c->d_planck64;
     // the tensor-core stage 2 where the tables fit it
     c->tune_variant = lm_tc_ok(t) ? 6 : 3;
     st = cuda_status(cudaDeviceSynchronize());
   } while (0);
-  if (raw) cudaFree(raw);
+  if (raw) dev_free(raw);
   if (st != FIRE_OK) {
     fire_ctx_destroy(c);
     return st;
@@ -502,7 +529,7 @@ void fire_ctx_tables(const fire_ctx_t *c, KTables *t, KConfig *k) {
   *t = c->t;
   fire_priors_t p;
   fire_default_priors(&p, c->t.K, c->t.nt, c->t.tglo, c->t.tglo + c->t.tgstep * (c->t.nt - 1));
-  fill_kconfig(*k, c->cfg, p, c->t.K);
+  fill_kconfig(*k, c->cfg, p, c->t.K, c->t.nb);
 }
 
 extern "C" {
@@ -573,17 +600,20 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     p.o.hfdi = out->hfdi;
     p.o.status = out->status;
     p.o.iters = out->iters;
+    p.o.resid = out->resid_spec;
+    p.s.want_resid = out->resid_spec != nullptr;
     return run_fit(c, p, learned, st);
   }
 
   // host scene: stage inputs and outputs through one device buffer
   const size_t s_rad = (size_t)n * c->t.nb * 4, s_wv = (size_t)n * 2;
   const size_t s_init = pri->init_mode == FIRE_INIT_GIVEN ? szf * NS : 0;
+  const size_t s_res = out->resid_spec ? s_rad : 0;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   size_t need = al(s_rad) + al(s_wv) + al(s_init) + al(s_state) + 7 * al(szf) + al(s_cov) +
-                al(s_u8) + al(s_it);
+                al(s_u8) + al(s_it) + al(s_res);
   if (need > c->stage_bytes) {
-    cudaFree(c->d_stage);
+    dev_free(c->d_stage);
     c->d_stage = nullptr;
     c->stage_bytes = 0;
     fire_status_t e = dev_alloc((char **)&c->d_stage, need);
@@ -600,6 +630,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   float *o_rms = (float *)carve(szf), *o_hfdi = (float *)carve(szf), *o_cov = (float *)carve(s_cov);
   uint8_t *o_status = (uint8_t *)carve(s_u8);
   uint16_t *o_it = (uint16_t *)carve(s_it);
+  float *o_res = s_res ? (float *)carve(s_res) : nullptr;
   p.s.rad = d_rad;
   p.s.wv = d_wv;
   p.s.init = d_init;
@@ -614,6 +645,8 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   p.o.cov = out->cov ? o_cov : nullptr;
   p.o.status = out->status ? o_status : nullptr;
   p.o.iters = out->iters ? o_it : nullptr;
+  p.o.resid = o_res;
+  p.s.want_resid = o_res != nullptr;
   if (learned) {
     // the fallback merge compares costs: keep them even if not requested
     p.o.cost = o_cost;
@@ -686,6 +719,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
       q.o.cov = off(p.o.cov, 21);
       q.o.status = off(p.o.status, 1);
       q.o.iters = off(p.o.iters, 2);
+      q.o.resid = off(p.o.resid, c->t.nb);
       q.w.counter = c->d_ctr + 2 * i;
       q.w.s1x = p.w.s1x + a * (c->t.K + 2);
       q.w.s1meta = p.w.s1meta + a;
@@ -704,11 +738,13 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
           {out->var_ET, q.o.var_ET, (size_t)m * 4}, {out->cost, q.o.cost, (size_t)m * 4},
           {out->rms, q.o.rms, (size_t)m * 4}, {out->hfdi, q.o.hfdi, (size_t)m * 4},
           {out->cov, q.o.cov, (size_t)m * 21 * 4}, {out->status, q.o.status, (size_t)m},
-          {out->iters, q.o.iters, (size_t)m * 4}};
+          {out->iters, q.o.iters, (size_t)m * 4},
+          {out->resid_spec, q.o.resid, (size_t)m * c->t.nb * 4}};
       const size_t eo[] = {(size_t)a * NS * 4, (size_t)a * 4, (size_t)a * 4, (size_t)a * 4,
                            (size_t)a * 4, (size_t)a * 4, (size_t)a * 4, (size_t)a * 4,
-                           (size_t)a * 21 * 4, (size_t)a, (size_t)a * 4};
-      for (int k = 0; k < 11; k++)
+                           (size_t)a * 21 * 4, (size_t)a, (size_t)a * 4,
+                           (size_t)a * c->t.nb * 4};
+      for (int k = 0; k < 12; k++)
         if (back[k].h)
           CK(cudaMemcpyAsync((char *)back[k].h + eo[k], back[k].d, back[k].b,
                              cudaMemcpyDeviceToHost, cp));
@@ -731,7 +767,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
       {out->state, o_state, s_state}, {out->ET, o_ET, szf}, {out->sdT, o_sdT, szf},
       {out->alpha, o_alpha, szf}, {out->var_ET, o_var, szf}, {out->cost, o_cost, szf},
       {out->rms, o_rms, szf}, {out->hfdi, o_hfdi, szf}, {out->cov, o_cov, s_cov},
-      {out->status, o_status, s_u8}, {out->iters, o_it, s_it}};
+      {out->status, o_status, s_u8}, {out->iters, o_it, s_it}, {out->resid_spec, o_res, s_res}};
   for (auto &b : back)
     if (b.h) CK(cudaMemcpyAsync(b.h, b.d, b.b, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -784,6 +820,7 @@ fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   s->solves64_1 = v[ST_S64_1];
   s->solves64_2 = v[ST_S64_2];
   s->mma_rounds2 = v[ST_MMA2];
+  s->n_post64 = v[ST_POST64];
   for (int k = 0; k < 8; k++) s->status_counts[k] = v[ST_STATUS0 + k];
   // algorithmic flops (FMA = 2): stage 1 per band and evaluation; stage 2 per
   // band and evaluation (Jacobian, normal equations, cost and its
@@ -823,15 +860,16 @@ fire_status_t fire_normal_equations(fire_ctx_t *c, int32_t stage, const float *r
     fire_default_priors(&pd, c->t.K, c->t.nt, c->t.tglo, c->t.tglo + c->t.tgstep * (c->t.nt - 1));
     pri = &pd;
   }
-  if (!priors_valid(*pri, c->t.K)) return FIRE_ERR_ARG;
   LMLaunch p;
   memset(&p, 0, sizeof(p));
+  if (!priors_valid(*pri, c->t.K) || !noise_sd_valid(*pri, c->t.nb)) return FIRE_ERR_ARG;
   p.t = c->t;
-  fill_kconfig(p.c, c->cfg, *pri, c->t.K);
+  fill_kconfig(p.c, c->cfg, *pri, c->t.K, c->t.nb);
   p.s.n_pix = n;
   p.s.rad = radiance;
   p.s.wv = wv_bin;
   p.w.err = c->d_err;
+  CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), (cudaStream_t)stream));
   return cuda_status(launch_normal_eq(p, stage, states, H, g, cost, (cudaStream_t)stream,
                                       c->tune_variant));
 }

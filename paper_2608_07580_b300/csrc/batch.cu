@@ -45,6 +45,7 @@ fire_status_t build_items(const fire_ctx *c, const fire_batch_item_t *items, int
     s.out.hfdi = it.out.hfdi;
     s.out.status = it.out.status;
     s.out.iters = it.out.iters;
+    s.out.resid = it.out.resid_spec;
     h_prefix[i] = tot;
     tot += it.n_pix;
   }
@@ -54,15 +55,21 @@ fire_status_t build_items(const fire_ctx *c, const fire_batch_item_t *items, int
   return FIRE_OK;
 }
 
+int any_resid(const fire_batch_item_t *items, int n_items) {
+  for (int i = 0; i < n_items; i++)
+    if (items[i].out.resid_spec) return 1;
+  return 0;
+}
+
 fire_status_t ensure_items(fire_ctx *c, int n_items) {
   if (n_items <= c->items_cap) return FIRE_OK;
-  cudaFree(c->d_items);
-  cudaFree(c->d_prefix);
+  dev_free(c->d_items);
+  dev_free(c->d_prefix);
   c->d_items = nullptr;
   c->d_prefix = nullptr;
   c->items_cap = 0;
-  BCK(cudaMalloc((void **)&c->d_items, sizeof(SceneItem) * n_items));
-  BCK(cudaMalloc((void **)&c->d_prefix, sizeof(long long) * (n_items + 1)));
+  BCK(dev_malloc((void **)&c->d_items, sizeof(SceneItem) * n_items));
+  BCK(dev_malloc((void **)&c->d_prefix, sizeof(long long) * (n_items + 1)));
   c->items_cap = n_items;
   return FIRE_OK;
 }
@@ -112,6 +119,7 @@ fire_status_t fire_retrieve_batch(fire_ctx_t *c, const fire_batch_item_t *items,
   if (e == FIRE_OK) e = ensure_items(c, n_items);
   LMLaunch p;
   if (e == FIRE_OK) e = prepare_launch(c, pri, total, gate_mode == FIRE_FIT_HFDI, p);
+  if (e == FIRE_OK) p.s.want_resid = any_resid(items, n_items);
   if (e == FIRE_OK) {
     // synchronous copies: the host tables are released before returning
     if (cudaMemcpyAsync(c->d_items, h_items, sizeof(SceneItem) * n_items, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -150,22 +158,23 @@ fire_status_t fire_graph_capture(fire_ctx_t *c, const fire_batch_item_t *items, 
   long long total = 0;
   if (cudaMallocHost((void **)&g->h_items, sizeof(SceneItem) * n_items) != cudaSuccess ||
       cudaMallocHost((void **)&g->h_prefix, sizeof(long long) * (n_items + 1)) != cudaSuccess ||
-      cudaMalloc((void **)&g->d_items, sizeof(SceneItem) * n_items) != cudaSuccess ||
-      cudaMalloc((void **)&g->d_prefix, sizeof(long long) * (n_items + 1)) != cudaSuccess)
+      dev_malloc((void **)&g->d_items, sizeof(SceneItem) * n_items) != cudaSuccess ||
+      dev_malloc((void **)&g->d_prefix, sizeof(long long) * (n_items + 1)) != cudaSuccess)
     e = FIRE_ERR_NOMEM;
   if (e == FIRE_OK) e = build_items(c, items, n_items, g->h_items, g->h_prefix, &total);
   const size_t nn = (size_t)(total > 0 ? total : 1);
   if (e == FIRE_OK &&
-      (cudaMalloc((void **)&g->d_s1x, nn * (c->t.K + 2) * 4) != cudaSuccess ||
-       cudaMalloc((void **)&g->d_s1meta, nn * 4) != cudaSuccess ||
-       cudaMalloc((void **)&g->d_s2x, nn * 32 * 4) != cudaSuccess ||
-       cudaMalloc((void **)&g->d_s2g, nn * 6 * 4) != cudaSuccess ||
-       cudaMalloc((void **)&g->d_work, (size_t)(2 + ST_COUNT) * 8) != cudaSuccess ||
-       cudaMalloc((void **)&g->d_err, sizeof(int)) != cudaSuccess))
+      (dev_malloc((void **)&g->d_s1x, nn * (c->t.K + 2) * 4) != cudaSuccess ||
+       dev_malloc((void **)&g->d_s1meta, nn * 4) != cudaSuccess ||
+       dev_malloc((void **)&g->d_s2x, nn * 32 * 4) != cudaSuccess ||
+       dev_malloc((void **)&g->d_s2g, nn * 6 * 4) != cudaSuccess ||
+       dev_malloc((void **)&g->d_work, (size_t)(2 + ST_COUNT) * 8) != cudaSuccess ||
+       dev_malloc((void **)&g->d_err, sizeof(int)) != cudaSuccess))
     e = FIRE_ERR_NOMEM;
   LMLaunch p;
   if (e == FIRE_OK) e = prepare_launch(c, pri, total, gate_mode == FIRE_FIT_HFDI, p, false);
   if (e == FIRE_OK) {
+    p.s.want_resid = any_resid(items, n_items);
     p.w.s1x = g->d_s1x;
     p.w.s1meta = g->d_s1meta;
     p.w.s2x = g->d_s2x;
@@ -217,14 +226,14 @@ void fire_graph_destroy(fire_graph_t *g) {
   if (g->graph) cudaGraphDestroy(g->graph);
   cudaFreeHost(g->h_items);
   cudaFreeHost(g->h_prefix);
-  cudaFree(g->d_items);
-  cudaFree(g->d_prefix);
-  cudaFree(g->d_s1x);
-  cudaFree(g->d_s1meta);
-  cudaFree(g->d_s2x);
-  cudaFree(g->d_s2g);
-  cudaFree(g->d_work);
-  cudaFree(g->d_err);
+  dev_free(g->d_items);
+  dev_free(g->d_prefix);
+  dev_free(g->d_s1x);
+  dev_free(g->d_s1meta);
+  dev_free(g->d_s2x);
+  dev_free(g->d_s2g);
+  dev_free(g->d_work);
+  dev_free(g->d_err);
   delete g;
 }
 

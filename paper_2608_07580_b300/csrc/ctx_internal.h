@@ -12,6 +12,8 @@ struct fire_ctx {
   firert::KTables t;
   // device buffers
   float *d_image = nullptr;
+  float *d_planck_full = nullptr;    // [nt][nb] Planck grid over every band (residual spectrum)
+  double *d_planck64 = nullptr;      // [nt][n2] FP64 Planck grid of the stage-2 bands (posterior)
   unsigned char *d_plop = nullptr;   // stage-2 Planck grid as the tensor-core operand
   float4 *d_wvtab = nullptr;
   float *d_sat = nullptr;
@@ -62,6 +64,8 @@ struct fire_ctx {
 namespace firert {
 // bounds, prior and start-rule checks of a priors block
 bool priors_valid(const fire_priors_t &p, int K);
+// per-band noise sd (host array) positive and finite, when given
+bool noise_sd_valid(const fire_priors_t &p, int nb);
 // the next 4 timing events of the context (nullptr when timing is off)
 cudaEvent_t *timing_events(fire_ctx *c);
 fire_status_t run_fit(fire_ctx *c, LMLaunch &p, bool learned, cudaStream_t st);

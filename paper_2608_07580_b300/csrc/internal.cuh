@@ -10,6 +10,7 @@ namespace firert {
 constexpr int kWarp = 32;
 constexpr int kMaxK = 8;
 constexpr int kMaxTgrid = 128;
+constexpr int kMaxBands = 512;
 constexpr int kScratchPerNode = 8;   // floats per grid node in the warp scratch
 
 // per-pixel status codes (mirrors the header)
@@ -46,6 +47,8 @@ struct KTables {
   // (hi, mid, lo), each plrows x 64 nodes, K-major 128-byte-swizzled rows
   const unsigned char *plop;
   int plrows;              // n2 rounded up to a multiple of 8
+  const float *planck_full;  // [nt][nb] B(lambda_b, T_j) over every band (residual spectrum)
+  const double *planck64;    // [nt][n2] B(lambda_b, T_j) in FP64 over the stage-2 bands (posterior)
 };
 
 struct KConfig {
@@ -57,9 +60,12 @@ struct KConfig {
   int max_it1, max_it2;
   float tau0, tol_g, tol_x, tol_f, kappa_max, dfloor;
   float noise_rel, noise_abs;
-  int weighted;
+  int weighted;             // 1: weights 1 / variance (noise model, or per-band sd)
   float hfdi_thresh;
   float ident_sd_et, ident_alpha_snr;
+  long long wait_spins;     // polls of a bounded wait before it gives up
+  int has_nsd;              // 1: the caller's per-band noise sd weight the loss
+  float nsd[kMaxBands];     // noise_sd_b (weights 1 / noise_sd_b^2)
 };
 
 // one scene of a batched call: device pointers, its own outputs
@@ -71,6 +77,7 @@ struct SceneItem {
     float *state, *ET, *sdT, *alpha, *cov, *var_ET, *cost, *rms, *hfdi;
     uint8_t *status;
     uint16_t *iters;
+    float *resid;
   } out;
 };
 
@@ -87,18 +94,20 @@ struct KScene {
   int gate;                // 1: HFDI gate
   int init_best;           // 1: stage 2 starts from the lower-cost of the given
                            //    start and the stage-1-derived one (learned start)
+  int want_resid;          // 1: some output asks for the residual spectrum
 };
 
 struct KOut {
   float *state, *ET, *sdT, *alpha, *cov, *var_ET, *cost, *rms, *hfdi;
   uint8_t *status;
   uint16_t *iters;
+  float *resid;            // [n][nb] or nullptr
 };
 
 // device counters, indices into KWork::stats
 enum : int {
   ST_NPIX = 0, ST_IT1, ST_IT2, ST_FP64, ST_BAND1, ST_BAND2, ST_NODEBAND2, ST_S64_1, ST_S64_2, ST_MMA2,
-  ST_STATUS0,
+  ST_POST64, ST_STATUS0,
   ST_COUNT = ST_STATUS0 + 8
 };
 
@@ -122,6 +131,8 @@ struct LMLaunch {
   KOut o;
   KWork w;
 };
+// passed by value as a kernel parameter: within the 4 KB parameter space
+static_assert(sizeof(LMLaunch) <= 4096, "LMLaunch exceeds the kernel parameter space");
 
 // BF16 tensor-core GEMM C = A B^T (kernels_gemm.cu)
 enum : int { EPI_F32 = 0, EPI_BIAS_RELU = 1, EPI_BIAS_TANH = 2, EPI_RELU_MASK = 3 };
@@ -155,7 +166,16 @@ cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *bloc
                       int variant = 0, cudaEvent_t *ev = nullptr);
 size_t lm_smem_bytes(const KTables &t, int warps_per_cta = 8);
 cudaError_t launch_merge_fallback(const long long *idx, const float *cost_first, long long nfb,
-                                  const KOut &compact, const KOut &out, int K, cudaStream_t st);
+                                  const KOut &compact, const KOut &out, int K, int nb,
+                                  cudaStream_t st);
+// B(lambda_b, T_j) for every band and grid node, [nt][nb] (FP64, stored fp32)
+cudaError_t launch_planck_full(const KTables &t, const float *wl, float *out, cudaStream_t st);
+// B(lambda_b, T_j) over the stage-2 bands, [nt][n2], kept in FP64
+cudaError_t launch_planck64(const KTables &t, const float *wl, double *out, cudaStream_t st);
+// device allocations of the library: through the caller's allocator when
+// one is installed (fire_set_allocator), else cudaMalloc / cudaFree
+cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
 // variant: the launch shape whose stage-2 evaluation is used (as launch_lm)
 cudaError_t launch_normal_eq(const LMLaunch &p, int stage, const float *states, float *H, float *g,
                              float *cost, cudaStream_t st, int variant = 0);

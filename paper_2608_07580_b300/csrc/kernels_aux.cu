@@ -58,6 +58,34 @@ __global__ void build_tables_kernel(KTables t, const float *wl, const float *e0,
   }
 }
 
+// B(lambda_b, T_j) for every band and grid node, [nt][nb] (Eq. thermal, the
+// same FP64 formula as the stage-2 grid above, stored fp32)
+__global__ void planck_full_kernel(KTables t, const float *wl, float *out) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int nthr = gridDim.x * blockDim.x;
+  for (int e = tid; e < t.nt * t.nb; e += nthr) {
+    int j = e / t.nb, b = e % t.nb;
+    double lam = (double)wl[b] * 1e-9;
+    double T = (double)t.tglo + j * (double)t.tgstep;
+    double ex = exp(-kH * kC / (kKB * lam * T));
+    out[e] = (float)(2.0 * kH * kC * kC / (lam * lam * lam * lam * lam) * 1e-9 * ex / (1.0 - ex));
+  }
+}
+
+// B(lambda_b, T_j) over the stage-2 bands, [nt][n2], kept in FP64 (the
+// posterior's normal matrix at the final state)
+__global__ void planck64_kernel(KTables t, const float *wl, double *out) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int nthr = gridDim.x * blockDim.x;
+  for (int e = tid; e < t.nt * t.n2; e += nthr) {
+    int j = e / t.n2, b = t.b2lo + e % t.n2;
+    double lam = (double)wl[b] * 1e-9;
+    double T = (double)t.tglo + j * (double)t.tgstep;
+    double ex = exp(-kH * kC / (kKB * lam * T));
+    out[e] = 2.0 * kH * kC * kC / (lam * lam * lam * lam * lam) * 1e-9 * ex / (1.0 - ex);
+  }
+}
+
 // Forward model, one warp per state (the model itself is warp_forward in
 // model.cuh), with optional counter-based noise.
 __global__ void __launch_bounds__(256) forward_kernel(KTables t, int mode, const float *state,
@@ -114,6 +142,16 @@ cudaError_t launch_build_tables(const KTables &t, const float *wl, const float *
                                   const float win[6], cudaStream_t st) {
   build_tables_kernel<<<64, 256, 0, st>>>(t, wl, e0, cos_sza, td, tu, ra, sa, endm, image, wvtab,
                                           win[0], win[1], win[2], win[3], win[4], win[5]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_planck_full(const KTables &t, const float *wl, float *out, cudaStream_t st) {
+  planck_full_kernel<<<64, 256, 0, st>>>(t, wl, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_planck64(const KTables &t, const float *wl, double *out, cudaStream_t st) {
+  planck64_kernel<<<64, 256, 0, st>>>(t, wl, out);
   return cudaGetLastError();
 }
 

@@ -78,15 +78,10 @@ __device__ __forceinline__ constexpr int up(int a, int b) {
   return a <= b ? a * P - (a * (a - 1)) / 2 + (b - a) : b * P - (b * (b - 1)) / 2 + (a - b);
 }
 
-// Reciprocal square root without division for the FP64 covariance: an FP32
-// seed refined with two Newton-Raphson steps y <- y (3 - x y^2) / 2 (quadratic
-// convergence: 2^-23 -> 2^-46 -> full precision).
-__device__ __forceinline__ double rsq(double x) {
-  double y = (double)rsqrtf((float)x);
-  y = y * (1.5 - 0.5 * x * y * y);
-  y = y * (1.5 - 0.5 * x * y * y);
-  return y;
-}
+// Reciprocal square root for the FP64 covariance (IEEE double square root
+// and division: the pivots of a near-singular matrix leave the FP32 range,
+// so no FP32 seed)
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
 
 // expm1(y) for |y| < 0.5 by its Taylor series to y^9 (truncation below
 // |y|^10 / 10! e^|y| < 5e-10 |y|): nine FMAs, no branches
@@ -116,14 +111,11 @@ __device__ __forceinline__ float2 em1_mid2(float2 y) {
 }
 
 // ------------------------------------------------------------- solve ----
-// reciprocal square root for the step solve: the SFU in FP32; in FP64 an FP32
-// seed and one Newton-Raphson step (2^-22 -> below 2^-43, past the FP32
-// rounding that the normal matrix itself carries)
+// reciprocal square root for the step solve: the SFU in FP32; in FP64 the
+// IEEE double square root and division (the cold path of ill-conditioned
+// steps, whose pivots may leave the FP32 range)
 __device__ __forceinline__ float rsq_step(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq_step(double x) {
-  const double y = (double)rsqrtf((float)x);
-  return y * (1.5 - 0.5 * x * y * y);
-}
+__device__ __forceinline__ double rsq_step(double x) { return 1.0 / sqrt(x); }
 
 // Solve (H + lam D) d = rhs over the free variables on the diagonally scaled
 // matrix; pinned variables are identity rows with their displacement moved
@@ -260,21 +252,18 @@ __device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, c
   while (L.it < max_it) {
     if (L.fresh) {
       bool small = true;
-      float mx = 0.f;
       static_for<P>([&](auto A_) {
         constexpr int a = decltype(A_)::value;
         float xv = St::template rsel<a>(x, m);
         bool lo_hit = xv <= S.template lo_r<a>(c, m);
         bool hi_hit = St::template has_upper<a>() && xv >= S.template hi_r<a>(c, m);
         L.act[a] = (lo_hit && g[a] <= 0.f) || (hi_hit && g[a] >= 0.f);
-        float haa = H[up<P>(a, a)];
-        if (!L.act[a]) {
-          if (fabsf(g[a]) > c.tol_g * sqrtf(haa * cst)) small = false;
-          mx = fmaxf(mx, haa);
-        }
+        if (!L.act[a] && fabsf(g[a]) > c.tol_g * sqrtf(H[up<P>(a, a)] * cst)) small = false;
       });
       if (small) { L.status = PX_CONVERGED; return false; }
-      if (L.lam < 0.f) L.lam = c.tau0 * mx;
+      // the damping matrix is diag H, so lambda is the relative damping of
+      // every diagonal: it starts at tau0 whatever the units of H
+      if (L.lam < 0.f) L.lam = c.tau0;
       L.fresh = false;
     }
     // damping diagonal, projected-Newton solve with re-solve on bound hits
@@ -448,7 +437,7 @@ __host__ __device__ __forceinline__ int pix_stride1(const KTables &t, int G) {
   int f = 4 * band_slots(t.n1, G);
   return f + ((G - f % 32) % 32 + 32) % 32;
 }
-constexpr int kNE2 = 48;   // stage-2 per-pixel slot: trial H[21], g[6], floor[6] at 30, proposal x[6] at 40
+constexpr int kNE2 = 48;   // stage-2 per-pixel slot: trial H[21], g[6], floor[6] at 30
 __host__ __device__ __forceinline__ int pix_stride2(const KTables &t, int G) {
   int f = t.nt * kScratchPerNode + 5 * band_slots(t.n2, G) + kNE2;
   return f + ((G - f % 32) % 32 + 32) % 32;
@@ -1029,7 +1018,8 @@ struct Stage2 {
 // division-free: Jacobi scaling and the Cholesky pivots use Newton-refined
 // reciprocal square roots, and C = L^-T L^-1 from the triangular inverse.
 struct CovIO {
-  float x[6], H[21], g[6], s2;
+  float x[6], g[6], s2;
+  double H[21];
   float cov[21];
   bool cov_ok;
   double vE, va;
@@ -1037,7 +1027,7 @@ struct CovIO {
 
 __device__ __noinline__ void laplace_cov(const KConfig &c, CovIO &io) {
   const float (&x)[6] = io.x;
-  const float (&H)[21] = io.H;
+  const double (&H)[21] = io.H;
   const float (&g)[6] = io.g;
   const float s2 = io.s2;
   float (&cov)[21] = io.cov;
@@ -1048,18 +1038,18 @@ __device__ __noinline__ void laplace_cov(const KConfig &c, CovIO &io) {
 #pragma unroll
   for (int k = 0; k < 6; k++) {
     bool act = (x[k] <= c.lo2[k] && g[k] <= 0.f) || (x[k] >= c.hi2[k] && g[k] >= 0.f);
-    zc[k] = !act && !(H[up<6>(k, k)] > 0.f);
+    zc[k] = !act && !(H[up<6>(k, k)] > 0.0);
     fix[k] = act || zc[k];
   }
   double A[21], rd[6], il[6];
 #pragma unroll
-  for (int i = 0; i < 6; i++) rd[i] = fix[i] ? 1.0 : rsq((double)H[up<6>(i, i)]);
+  for (int i = 0; i < 6; i++) rd[i] = fix[i] ? 1.0 : rsq(H[up<6>(i, i)]);
 #pragma unroll
   for (int i = 0; i < 6; i++)
 #pragma unroll
     for (int j = 0; j <= i; j++)
       A[i * (i + 1) / 2 + j] = (fix[i] || fix[j]) ? (i == j ? 1.0 : 0.0)
-                                                   : (double)H[up<6>(i, j)] * rd[i] * rd[j];
+                                                   : H[up<6>(i, j)] * rd[i] * rd[j];
   cov_ok = true;
 #pragma unroll
   for (int j = 0; j < 6; j++) {
@@ -1127,16 +1117,24 @@ __device__ __forceinline__ unsigned smem_u32(const void *p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 
+// true in every thread of the CTA if a kernel of this fit has set the error
+// word (a bounded wait gave up): the later kernels of the fit then leave at
+// once. Called by all threads of the CTA at the same point.
+__device__ __forceinline__ bool cta_err(const int *err) {
+  return __syncthreads_or(threadIdx.x == 0 && *(volatile const int *)err != 0) != 0;
+}
+
 // Stage the first nfloats of the per-CTA table image into shared memory with 1D bulk copies
-// completing on one mbarrier. The wait is bounded: on timeout the error flag
-// is set, the copies still in flight are waited for (bounded again) and the
-// CTA leaves (returns false).
+// completing on one mbarrier. The wait is bounded (spins polls): on timeout
+// the error flag is set, the copies still in flight are waited for (bounded
+// again, by 2^26 polls, so the CTA never leaves with a copy landing in its
+// shared memory) and the CTA leaves (returns false).
 // The table image (its first nfloats floats) goes to the start of the
 // dynamic shared memory; an optional second region (bytes2 bytes from src2 to
 // dst2, both 16-byte aligned, bytes2 a multiple of 16) rides on the same
 // mbarrier.
 __device__ __forceinline__ bool stage_tables(const KTables &t, float *smem, int nfloats,
-                                             unsigned long long *bar, int *err,
+                                             unsigned long long *bar, int *err, long long spins,
                                              void *dst2 = nullptr, const void *src2 = nullptr,
                                              unsigned bytes2 = 0) {
   const unsigned bytes = (unsigned)nfloats * 4u;
@@ -1165,10 +1163,12 @@ __device__ __forceinline__ bool stage_tables(const KTables &t, float *smem, int 
     }
   }
   __syncthreads();
+  // the bounded wait polls with the non-blocking test (each poll returns at
+  // once, so `spins` counts polls, not the hardware's suspend intervals)
   unsigned done = 0;
-  for (long long spin = 0; spin < (1ll << 26) && !done; spin++)
+  for (long long spin = 0; spin < spins && !done; spin++)
     asm volatile(
-        "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
+        "{ .reg .pred P; mbarrier.test_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
         : "=r"(done) : "r"(smem_u32(bar)) : "memory");
   if (__syncthreads_and(done)) return true;
   if (threadIdx.x == 0) atomicExch(err, 1);
@@ -1205,7 +1205,7 @@ __device__ __forceinline__ int setup1(Stage1<K, G> &s1, const PixCtx &pc, const 
       bool ok = pc.img[t.lay.off_win1 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
       float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
       Lv = L;
-      wv = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
+      wv = ok ? (c.weighted ? 1.f / (c.has_nsd ? c.nsd[b] * c.nsd[b] : var) : 1.f) : 0.f;
       if (ok) { nv += var; nu++; }
     }
     s1.Lo(i) = Lv;
@@ -1258,7 +1258,7 @@ __device__ __forceinline__ int setup2(Stage2<G> &s2, const PixCtx &pc, const Grp
       for (int k = 0; k < K; k++) rho = fmaf(xs[k], pc.img[t.lay.off_endm + k * t.nb + b], rho);
       yv = L - (q.y + q.x * rho / (1.f - q.z * rho));
       tv = q.w;
-      wv = ok ? (c.weighted ? 1.f / var : 1.f) : 0.f;
+      wv = ok ? (c.weighted ? 1.f / (c.has_nsd ? c.nsd[b] * c.nsd[b] : var) : 1.f) : 0.f;
       if (ok) { nv += var; nu++; }
     }
     s2.Y(i) = yv;
@@ -1319,6 +1319,7 @@ __device__ __forceinline__ PixRef resolve(const LMLaunch &p, long long pix, int 
   r.o.hfdi = it.out.hfdi;
   r.o.status = it.out.status;
   r.o.iters = it.out.iters;
+  r.o.resid = it.out.resid;
   r.opix = loc;
   return r;
 }
@@ -1359,7 +1360,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
   // band buffers
   const int img_f = image_floats(t, 1), wv_f = wvtab_floats(t);
   const float4 *wvs = wv_f ? reinterpret_cast<const float4 *>(smem + img_f) : t.wvtab;
-  if (!stage_tables(t, smem, img_f, &bar, p.w.err, smem + img_f, t.wvtab, (unsigned)wv_f * 4u))
+  if (!stage_tables(t, smem, img_f, &bar, p.w.err, c.wait_spins, smem + img_f, t.wvtab,
+                    (unsigned)wv_f * 4u))
     return;
   const Grp<G> gp(lane);
   PixCtx pc;
@@ -1536,7 +1538,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
   const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
   const int img_f = image_floats(t, 2);
-  if (!stage_tables(t, smem, img_f, &bar, p.w.err)) return;
+  if (cta_err(p.w.err)) return;   // an earlier kernel of this fit gave up
+  if (!stage_tables(t, smem, img_f, &bar, p.w.err, c.wait_spins)) return;
   const Grp<G> gp(lane);
   float *mine = smem + img_f + (threadIdx.x / G) * pix_stride2(t, G);
   PixCtx pc;
@@ -1551,9 +1554,9 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
   const long long n = p.s.n_pix;
   const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
   long long next = 0, end = 0, pix = 0;
-  bool active = false, done = false, first = false, alt = false;
+  bool active = false, done = false, first = false;
   float x[6], xt[6], H[21], g[6], gf[6], cst = 0.f, cd = 0.f;
-  float *ne = S.bb + 5 * S.nbs;   // trial H, g, gradient floor, then the proposal start
+  float *ne = S.bb + 5 * S.nbs;   // trial H, g, gradient floor
   int rc = 0, nfull = 0, status = 0, n2u = 0;
   LMIter<6> L;
   for (;;) {
@@ -1586,21 +1589,12 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       x[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
       const float e = x[0] > x[2] ? (T1 - x[2]) / (x[0] - x[2]) : 0.5f;
       x[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
-      alt = false;
+      // a given start replaces the derived one; the learned start only
+      // seeds stage 1, so that stage 2 starts where plain LM's does
       const float *ini = ref.init;
-      if (ini) {
-        float xg[6];
+      if (ini && !p.s.init_best) {
 #pragma unroll
-        for (int i = 0; i < 6; i++) xg[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
-        if (p.s.init_best) {
-          // learned start: after the derived start, the proposal is tried
-          // as a step and kept if its cost is lower
-          if (gp.sub < 6) ne[40 + gp.sub] = pick(xg, gp.sub);
-          alt = true;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 6; i++) x[i] = xg[i];
-        }
+        for (int i = 0; i < 6; i++) x[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
       }
 #pragma unroll
       for (int i = 0; i < 6; i++) xt[i] = x[i];
@@ -1613,17 +1607,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       active = true;
     }
     if (__all_sync(kFull, done)) break;
-    bool go = active, probe = false;
-    if (active && !first) {
-      if (alt) {
-#pragma unroll
-        for (int i = 0; i < 6; i++) xt[i] = ne[40 + i];
-        alt = false;
-        probe = true;
-      } else {
-        go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
-      }
-    }
+    bool go = active;
+    if (active && !first) go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
     __syncwarp();
     if (go) {
       float ct, cdt, drop;
@@ -1632,14 +1617,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       bool accept = first;
       if (!first) {
         drop += S.prior_drop(c, x, xt);
-        if (probe) {
-          accept = drop > 0.f;
-        } else {
-          const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
-          accept = rho > 0.f;
-          damping_update(L, accept, rho);
-          if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
-        }
+        const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
+        accept = rho > 0.f;
+        damping_update(L, accept, rho);
+        if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
       }
       if (accept) {
 #pragma unroll
@@ -2084,7 +2065,8 @@ __device__ __forceinline__ bool setup(const LMLaunch &p, float *smem, unsigned l
   C.nbs = band_slots(t.n2, G);
   C.ntile = (t.n2 + 127) >> 7;
   C.cols = C.ntile > 1 ? 256 : 128;
-  if (!stage_tables(t, smem, image_floats(t, 1), bar, p.w.err, C.base, t.plop,
+  if (cta_err(p.w.err)) return false;
+  if (!stage_tables(t, smem, image_floats(t, 1), bar, p.w.err, p.c.wait_spins, C.base, t.plop,
                     (unsigned)L.pl_bytes))
     return false;
   uint4 *co = reinterpret_cast<uint4 *>(C.base + L.pl_bytes);
@@ -2112,13 +2094,13 @@ __device__ __forceinline__ bool setup(const LMLaunch &p, float *smem, unsigned l
 // coefficients (flag prm[0] set by every group); mbar is the cohort's;
 // false if the MMA wait timed out
 __device__ __forceinline__ bool round(const KTables &t, Cta &C, int h, unsigned long long *mbar,
-                                      unsigned &phase) {
+                                      unsigned &phase, long long spins) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   co_sync(h);
   if (threadIdx.x == kCoThreads * h)
     mma(C.tmem + (uint32_t)(h * kNc * C.ntile), tc::su32(C.base),
         tc::su32(C.base + 3 * t.plrows * 128 + h * kNc * 128), t.plrows, C.ntile, tc::su32(mbar));
-  const bool w = tc::mbar_wait(tc::su32(mbar), phase, kSpinMMA);
+  const bool w = tc::mbar_wait(tc::su32(mbar), phase, spins);
   phase ^= 1u;
   if (!co_and(h, w)) return false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -2134,7 +2116,7 @@ __device__ __forceinline__ bool round(const KTables &t, Cta &C, int h, unsigned 
 __device__ __forceinline__ void release(const Cta &C, unsigned long long *mbar, unsigned phase,
                                         bool ok, int *err) {
   if (!ok) {
-    if (threadIdx.x == 0) atomicExch(err, 1);
+    if (threadIdx.x % kCoThreads == 0) atomicExch(err, 1);   // the cohort that gave up
     tc::mbar_wait(tc::su32(mbar), phase ^ 1u, kSpinMMA);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -2201,12 +2183,12 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
   Stage2<G> S;
   S.nbs = C.nbs;
   S.bb = mine;
-  float *ne = mine + 5 * S.nbs;   // trial H, g, gradient floor, then the proposal start
+  float *ne = mine + 5 * S.nbs;   // trial H, g, gradient floor
   float *prm = ne + kNE2;
   const long long n = p.s.n_pix;
   const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
   long long next = 0, end = 0, pix = 0;
-  bool active = false, done = false, first = false, alt = false, ok = true;
+  bool active = false, done = false, first = false, ok = true;
   float x[6], xt[6], H[21], g[6], gf[6], cst = 0.f, cd = 0.f;
   int rc = 0, nfull = 0, status = 0, n2u = 0;
   unsigned phase = 0;
@@ -2253,19 +2235,10 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       x[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
       const float e = x[0] > x[2] ? (T1 - x[2]) / (x[0] - x[2]) : 0.5f;
       x[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
-      alt = false;
       const float *ini = ref.init;
-      if (ini) {
-        float xg[6];
+      if (ini && !p.s.init_best) {
 #pragma unroll
-        for (int i = 0; i < 6; i++) xg[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
-        if (p.s.init_best) {
-          if (gp.sub < 6) ne[40 + gp.sub] = pick(xg, gp.sub);
-          alt = true;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 6; i++) x[i] = xg[i];
-        }
+        for (int i = 0; i < 6; i++) x[i] = fminf(fmaxf(ini[K + 2 + i], c.lo2[i]), c.hi2[i]);
       }
 #pragma unroll
       for (int i = 0; i < 6; i++) xt[i] = x[i];
@@ -2302,20 +2275,11 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       }
     }
     if (tcs2::co_and(hc, done)) break;
-    bool go = active, probe = false;
-    if (active && !first) {
-      if (alt) {
-#pragma unroll
-        for (int i = 0; i < 6; i++) xt[i] = ne[40 + i];
-        alt = false;
-        probe = true;
-      } else {
-        go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
-      }
-    }
+    bool go = active;
+    if (active && !first) go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
     if (go) tcs2::coef(t, c, gp, x, xt, co, slot, prm, rc ^ 1);
     if (gp.sub == 0) prm[0] = go ? 1.f : 0.f;
-    if (!tcs2::round(t, C, hc, &mbar[hc], phase)) { ok = false; break; }
+    if (!tcs2::round(t, C, hc, &mbar[hc], phase, c.wait_spins)) { ok = false; break; }
     nround++;
     if (go) {
       float ct, cdt, drop;
@@ -2324,14 +2288,10 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       bool accept = first;
       if (!first) {
         drop += S.prior_drop(c, x, xt);
-        if (probe) {
-          accept = drop > 0.f;
-        } else {
-          const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
-          accept = rho > 0.f;
-          damping_update(L, accept, rho);
-          if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
-        }
+        const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
+        accept = rho > 0.f;
+        damping_update(L, accept, rho);
+        if (accept && drop / cst < c.tol_f) { L.status = PX_CONVERGED; go = false; }
       }
       if (accept) {
 #pragma unroll
@@ -2432,7 +2392,7 @@ __global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_const
       tcs2::coef(t, c, gp, x, x, co, slot, prm, 1);
     }
     if (gp.sub == 0) prm[0] = has ? 1.f : 0.f;
-    if (!tcs2::round(t, C, hc, &mbar[hc], phase)) { ok = false; break; }
+    if (!tcs2::round(t, C, hc, &mbar[hc], phase, c.wait_spins)) { ok = false; break; }
     if (has) {
       float cst, cd, drop;
       tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, x, S.psc, ne, cst, cd, drop);
@@ -2449,103 +2409,295 @@ __global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_const
   tcs2::release(C, &mbar[hc], phase, ok, p.w.err);
 }
 
+// ---- the FP64 normal equations of stage 2 at a pixel's final state, for the
+// Laplace posterior: J^T W J + psc P and J^T W r - psc P (z - pm) in the z
+// coordinates of Eq. (affine) (the gradient decides which variables sit on
+// an outward-pressed bound, so it must not carry FP32 rounding either),
+// with the Jacobian of the thermal term (Eq. thermal, the two-component
+// mixture on the grid) formed in FP64 from the FP64 Planck grid. The
+// covariance inverts this matrix, whose condition number reaches 1e7 and
+// more for the near-degenerate mixture, so an FP32-formed matrix would give
+// variances of no precision. One warp per pixel: the node coefficients go
+// to shared memory (cf [6][kMaxTgrid]), the lanes take the stage-2 bands,
+// and the 21 sums are reduced across the warp (every lane gets them).
+__device__ __noinline__ void normal_matrix64(const LMLaunch &p, const float *row, int wv,
+                                             const float *xs, const double (&x2)[6], double psc,
+                                             double *cf, double (&H)[21], double (&g)[6]) {
+  const KTables &t = p.t;
+  const KConfig &c = p.c;
+  const int lane = threadIdx.x & 31;
+  const double mh = x2[0], sh = x2[1], ms = x2[2], ss = x2[3], eta = x2[4], al = x2[5];
+  double Uh = 0.0, Us = 0.0;
+  for (int j = lane; j < t.nt; j += 32) {
+    const double T = (double)t.tglo + j * (double)t.tgstep;
+    const double dh = (T - mh) / sh, ds = (T - ms) / ss;
+    cf[j] = exp(-0.5 * dh * dh);
+    cf[3 * kMaxTgrid + j] = exp(-0.5 * ds * ds);
+    Uh += cf[j];
+    Us += cf[3 * kMaxTgrid + j];
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    Uh += __shfl_xor_sync(kFull, Uh, o);
+    Us += __shfl_xor_sync(kFull, Us, o);
+  }
+  double dbh = 0.0, m2h = 0.0, dbs = 0.0, m2s = 0.0;
+  for (int j = lane; j < t.nt; j += 32) {
+    const double T = (double)t.tglo + j * (double)t.tgstep;
+    const double wh = cf[j] / Uh, ws = cf[3 * kMaxTgrid + j] / Us;
+    cf[j] = wh;
+    cf[3 * kMaxTgrid + j] = ws;
+    dbh += wh * (T - mh);
+    m2h += wh * (T - mh) * (T - mh);
+    dbs += ws * (T - ms);
+    m2s += ws * (T - ms) * (T - ms);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    dbh += __shfl_xor_sync(kFull, dbh, o);
+    m2h += __shfl_xor_sync(kFull, m2h, o);
+    dbs += __shfl_xor_sync(kFull, dbs, o);
+    m2s += __shfl_xor_sync(kFull, m2s, o);
+  }
+  for (int j = lane; j < t.nt; j += 32) {
+    const double T = (double)t.tglo + j * (double)t.tgstep;
+    const double dh = T - mh, ds = T - ms;
+    const double wh = cf[j], ws = cf[3 * kMaxTgrid + j];
+    cf[kMaxTgrid + j] = wh * (dh - dbh);
+    cf[2 * kMaxTgrid + j] = wh * (dh * dh - m2h);
+    cf[4 * kMaxTgrid + j] = ws * (ds - dbs);
+    cf[5 * kMaxTgrid + j] = ws * (ds * ds - m2s);
+  }
+  __syncwarp();
+  double sc[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) sc[i] = 0.5 * ((double)c.hi2[i] - (double)c.lo2[i]);
+  const double fh2 = al * eta / (sh * sh), fs2 = al * (1.0 - eta) / (ss * ss);
+  double acc[27];   // J^T W J (21), then J^T W r (6)
+#pragma unroll
+  for (int i = 0; i < 27; i++) acc[i] = 0.0;
+  const float4 *wvrow = t.wvtab + (size_t)wv * t.nb;
+  const float *endm = t.image + t.lay.off_endm;
+  for (int i = lane; i < t.n2; i += 32) {
+    const int b = t.b2lo + i;
+    const float L = __ldg(row + b);
+    if (!(t.image[t.lay.off_win2 + b] > 0.f) || (t.sat && L >= __ldg(t.sat + b))) continue;
+    double w = 1.0;
+    if (c.weighted) {
+      const double var = c.has_nsd ? (double)c.nsd[b] * (double)c.nsd[b]
+                                   : (double)c.noise_rel * c.noise_rel * (double)L * L +
+                                         (double)c.noise_abs * c.noise_abs;
+      w = 1.0 / var;
+    }
+    const float4 q = __ldg(&wvrow[b]);
+    const double tu = (double)q.w;
+    double rho = 0.0;
+    for (int k = 0; k < t.K; k++) rho = fma((double)xs[k], (double)__ldg(endm + k * t.nb + b), rho);
+    const double Ls = (double)q.y + (double)q.x * rho / (1.0 - (double)q.z * rho);   // Eq. (solar)
+    double S[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const double *Bp = t.planck64 + i;
+    for (int j = 0; j < t.nt; j++) {
+      const double Bj = __ldg(Bp + (size_t)j * t.n2);
+#pragma unroll
+      for (int k = 0; k < 6; k++) S[k] = fma(cf[k * kMaxTgrid + j], Bj, S[k]);
+    }
+    double J[6];
+    J[0] = tu * fh2 * S[1] * sc[0];
+    J[1] = tu * fh2 * S[2] / sh * sc[1];
+    J[2] = tu * fs2 * S[4] * sc[2];
+    J[3] = tu * fs2 * S[5] / ss * sc[3];
+    J[4] = tu * al * (S[0] - S[3]) * sc[4];
+    J[5] = tu * (eta * S[0] + (1.0 - eta) * S[3]) * sc[5];
+    const double r = (double)L - (Ls + al * tu * (eta * S[0] + (1.0 - eta) * S[3]));
+#pragma unroll
+    for (int a2 = 0; a2 < 6; a2++) {
+      acc[21 + a2] = fma(w * J[a2], r, acc[21 + a2]);
+#pragma unroll
+      for (int b2 = a2; b2 < 6; b2++) acc[up<6>(a2, b2)] = fma(w * J[a2], J[b2], acc[up<6>(a2, b2)]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < 27; i++) acc[i] += __shfl_xor_sync(kFull, acc[i], o);
+#pragma unroll
+  for (int i = 0; i < 21; i++) H[i] = acc[i];
+  // the prior of Eq. (affine)'s z: curvature psc pp, gradient -psc pp (z - pm)
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    const double zk = (double)c.zk2[i] > 0.0 ? (x2[i] - (double)c.lo2[i]) / sc[i] - 1.0 : 0.0;
+    H[up<6>(i, i)] += psc * (double)c.pp2[i];
+    g[i] = acc[21 + i] - psc * (double)c.pp2[i] * (zk - (double)c.pm2[i]);
+  }
+  __syncwarp();
+}
+
 // ---- finalize: moment matching (Sec. 2.3), FP64 Laplace covariance,
 // identifiability and the outputs of every fitted pixel; one thread per
-// pixel, so the FP64 work is not repeated across the lanes of a warp
-__global__ void __launch_bounds__(128) finalize_kernel(const __grid_constant__ LMLaunch p, int K) {
+// pixel, so the FP64 work is not repeated across the lanes of a warp. The
+// covariance first inverts the fit's last FP32 normal matrix; a pixel that
+// may be identifiable (alpha free, and alpha above 0.9 of its threshold
+// times a lower bound of sd(alpha)) is then given the FP64 normal equations
+// of its final state (normal_matrix64, the warp working on one such pixel at
+// a time) and its covariance, var(E[T]) and identifiability come from those.
+// The warps loop over 32 consecutive pixels at a time, so every lane of a
+// warp runs the same iterations.
+constexpr int kFinWarps = 4;
+__global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const __grid_constant__ LMLaunch p,
+                                                                  int K) {
   __shared__ unsigned long long cstat[ST_COUNT];
+  __shared__ double cfs[kFinWarps][6 * kMaxTgrid];
   for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) cstat[i] = 0ull;
-  __syncthreads();
+  if (cta_err(p.w.err)) return;
   const KConfig &c = p.c;
-  const int NSx = K + 8;
-  unsigned long long st_fp64 = 0, st_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < p.s.n_pix;
-       pix += (long long)gridDim.x * blockDim.x) {
-    if (!(p.w.s1meta[pix] & kFitted)) continue;
-    const float *hand = p.w.s2x + pix * kS2Hand;
+  const int NSx = K + 8, lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  unsigned long long st_fp64 = 0, st_post = 0, st_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const long long n = p.s.n_pix, step = (long long)gridDim.x * kFinWarps * 32;
+  for (long long base = ((long long)blockIdx.x * kFinWarps + wib) * 32; base < n; base += step) {
+    const long long pix = base + lane;
+    const bool fitted = pix < n && (p.w.s1meta[pix] & kFitted);
     CovIO io;
+    float cost = 0.f, cdata = 0.f, psc = 0.f;
+    int n2u = 1, status = 0, it2 = 0, nf = 0;
+    bool act_a = false;
+    if (fitted) {
+      const float *hand = p.w.s2x + pix * kS2Hand;
 #pragma unroll
-    for (int k = 0; k < 6; k++) { io.x[k] = hand[k]; io.g[k] = p.w.s2g[pix * 6 + k]; }
+      for (int k = 0; k < 6; k++) { io.x[k] = hand[k]; io.g[k] = p.w.s2g[pix * 6 + k]; }
 #pragma unroll
-    for (int k = 0; k < 21; k++) io.H[k] = hand[6 + k];
-    const float cost = hand[27], cdata = hand[28];
-    const int n2u = __float_as_int(hand[29]), sw = __float_as_int(hand[30]);
-    int status = sw & 0xff;
-    const int it2 = sw >> 8;
-    const float *x2 = io.x;
-    const float ET = x2[4] * x2[0] + (1.f - x2[4]) * x2[2];
-    const float dmu = x2[0] - x2[2];
-    const float sdT = sqrtf(x2[4] * x2[1] * x2[1] + (1.f - x2[4]) * x2[3] * x2[3] +
-                            x2[4] * (1.f - x2[4]) * dmu * dmu);
-    const float rms = sqrtf(cdata / (float)n2u);
-    int nf = 0;
+      for (int k = 0; k < 21; k++) io.H[k] = hand[6 + k];
+      cost = hand[27];
+      cdata = hand[28];
+      n2u = __float_as_int(hand[29]);
+      const int sw = __float_as_int(hand[30]);
+      status = sw & 0xff;
+      it2 = sw >> 8;
+      psc = hand[31];
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
-      bool act = (x2[k] <= c.lo2[k] && io.g[k] <= 0.f) || (x2[k] >= c.hi2[k] && io.g[k] >= 0.f);
-      nf += (!act && io.H[up<6>(k, k)] > 0.f);
-    }
-    io.s2 = c.weighted ? 1.f : cost / (float)(n2u - nf);
-    const bool act_a = (x2[5] <= c.lo2[5] && io.g[5] <= 0.f) || (x2[5] >= c.hi2[5] && io.g[5] >= 0.f);
-    if (act_a && x2[5] <= c.lo2[5]) {
-      // no thermal signal: E[T] is undefined, so is its posterior
-      io.cov_ok = false;
-      io.vE = __longlong_as_double(0x7ff0000000000000ll);
-      io.va = 0.0;
+      for (int k = 0; k < 6; k++) {
+        const bool act = (io.x[k] <= c.lo2[k] && io.g[k] <= 0.f) || (io.x[k] >= c.hi2[k] && io.g[k] >= 0.f);
+        nf += (!act && io.H[up<6>(k, k)] > 0.0);
+      }
+      io.s2 = c.weighted ? 1.f : cost / (float)(n2u - nf);
+      act_a = (io.x[5] <= c.lo2[5] && io.g[5] <= 0.f) || (io.x[5] >= c.hi2[5] && io.g[5] >= 0.f);
+      if (act_a && io.x[5] <= c.lo2[5]) {
+        // no thermal signal: E[T] is undefined, so is its posterior
+        io.cov_ok = false;
+        io.vE = __longlong_as_double(0x7ff0000000000000ll);
+        io.va = 0.0;
 #pragma unroll
-      for (int i = 0; i < 21; i++) io.cov[i] = __int_as_float(0x7fc00000);
-    } else if (nf > 0) {
-      laplace_cov(c, io);
-    } else {
-      io.cov_ok = true;
-      io.vE = io.va = 0.0;
+        for (int i = 0; i < 21; i++) io.cov[i] = __int_as_float(0x7fc00000);
+      } else if (nf > 0) {
+        laplace_cov(c, io);
+      } else {
+        io.cov_ok = true;
+        io.vE = io.va = 0.0;
 #pragma unroll
-      for (int i = 0; i < 21; i++) io.cov[i] = 0.f;
-    }
-    const double sdE = sqrt(io.vE), sda = sqrt(io.va);
-    const bool ident = io.cov_ok && isfinite(sdE) && sdE <= (double)c.ident_sd_et &&
-                       (double)x2[5] >= (double)c.ident_alpha_snr * sda && !act_a && x2[5] > 0.f;
-    if (!ident) status |= PX_F_NOT_IDENT;
-    if (p.w.fb_idx) {
-      // fallback rule of the learned start: the fit did not converge, or its
-      // cost exceeds three times the expected chi-square (n_used - 6) psc
-      const float psc = hand[31];
-      const float expect = (float)(n2u - 6) * (c.weighted ? 1.f : psc);
-      if ((status & 7) != PX_CONVERGED || cost > 3.f * expect) {
-        unsigned long long j = atomicAdd(p.w.fb_count, 1ull);
-        p.w.fb_idx[j] = pix;
-        p.w.fb_cost[j] = cost;
+        for (int i = 0; i < 21; i++) io.cov[i] = 0.f;
       }
     }
-    const PixRef ref = resolve(p, pix, K);
-    const KOut &o = ref.o;
-    const long long op = ref.opix;
-    if (o.state) {
-      for (int k = 0; k < K + 2; k++) o.state[op * NSx + k] = p.w.s1x[pix * (K + 2) + k];
-      for (int k = 0; k < 6; k++) o.state[op * NSx + K + 2 + k] = x2[k];
-    }
-    if (o.cov)
-      for (int k = 0; k < 21; k++) o.cov[op * 21 + k] = io.cov[k];
-    if (o.ET) o.ET[op] = ET;
-    if (o.sdT) o.sdT[op] = sdT;
-    if (o.alpha) o.alpha[op] = x2[5];
-    if (o.var_ET) o.var_ET[op] = (float)io.vE;
-    if (o.cost) o.cost[op] = cost;
-    if (o.rms) o.rms[op] = rms;
-    if (o.status) o.status[op] = (uint8_t)status;
-    if (o.iters) o.iters[2 * op + 1] = (uint16_t)it2;
-    st_fp64 += (status & PX_F_FP64) ? 1ull : 0ull;
+    // the FP64 posterior for pixels that may be identifiable: alpha free and
+    // alpha / sd(alpha) possibly above its threshold. sd(alpha) is at least
+    // sc5 sqrt(s2 / H_55) (the marginal variance of a variable is at least
+    // the inverse of its own curvature), a bound the FP32 matrix gives
+    // without an inversion; 0.9 of the threshold leaves room for rounding
+    const double sd_min = 0.5 * ((double)c.hi2[5] - (double)c.lo2[5]) *
+                          sqrt((double)io.s2 / fmax(io.H[up<6>(5, 5)], 1e-300));
+    const bool cand = fitted && !act_a && nf > 0 &&
+                      (double)io.x[5] >= 0.9 * (double)c.ident_alpha_snr * sd_min;
+    unsigned m = __ballot_sync(kFull, cand);
+    bool mine = false;
+    double H64[21], g64[6];
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const long long sp = __shfl_sync(kFull, pix, src);
+      double xs[6];
 #pragma unroll
-    for (int k = 0; k < 8; k++) st_s[k] += ((status & 7) == k) ? 1ull : 0ull;
+      for (int k = 0; k < 6; k++) xs[k] = (double)__shfl_sync(kFull, io.x[k], src);
+      const double ps = (double)__shfl_sync(kFull, psc, src);
+      const PixRef ref = resolve(p, sp, K);
+      double Hs[21], gs[6];
+      normal_matrix64(p, ref.row, ref.wv, p.w.s1x + sp * (K + 2), xs, ps, cfs[wib], Hs, gs);
+      if (lane == src) {
+        mine = true;
+#pragma unroll
+        for (int i = 0; i < 21; i++) H64[i] = Hs[i];
+#pragma unroll
+        for (int i = 0; i < 6; i++) g64[i] = gs[i];
+      }
+    }
+    if (mine) {
+      // the active set and the free count from the FP64 gradient, then the
+      // covariance from the FP64 matrix
+#pragma unroll
+      for (int i = 0; i < 21; i++) io.H[i] = H64[i];
+      nf = 0;
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        io.g[k] = g64[k] > 0.0 ? 1.f : (g64[k] < 0.0 ? -1.f : 0.f);
+        const bool act = (io.x[k] <= c.lo2[k] && io.g[k] <= 0.f) || (io.x[k] >= c.hi2[k] && io.g[k] >= 0.f);
+        nf += (!act && io.H[up<6>(k, k)] > 0.0);
+      }
+      io.s2 = c.weighted ? 1.f : cost / (float)(n2u - nf);
+      act_a = (io.x[5] <= c.lo2[5] && io.g[5] <= 0.f) || (io.x[5] >= c.hi2[5] && io.g[5] >= 0.f);
+      laplace_cov(c, io);
+      st_post++;
+    }
+    if (fitted) {
+      const float *x2 = io.x;
+      const float ET = x2[4] * x2[0] + (1.f - x2[4]) * x2[2];
+      const float dmu = x2[0] - x2[2];
+      const float sdT = sqrtf(x2[4] * x2[1] * x2[1] + (1.f - x2[4]) * x2[3] * x2[3] +
+                              x2[4] * (1.f - x2[4]) * dmu * dmu);
+      const float rms = sqrtf(cdata / (float)n2u);
+      const double sdE = sqrt(io.vE), sda = sqrt(io.va);
+      const bool ident = io.cov_ok && isfinite(sdE) && sdE <= (double)c.ident_sd_et &&
+                         (double)x2[5] >= (double)c.ident_alpha_snr * sda && !act_a && x2[5] > 0.f;
+      if (!ident) status |= PX_F_NOT_IDENT;
+      if (p.w.fb_idx) {
+        // fallback rule of the learned start: the fit did not converge, or its
+        // cost exceeds three times the expected chi-square (n_used - 6) psc
+        const float expect = (float)(n2u - 6) * (c.weighted ? 1.f : psc);
+        if ((status & 7) != PX_CONVERGED || cost > 3.f * expect) {
+          unsigned long long j = atomicAdd(p.w.fb_count, 1ull);
+          p.w.fb_idx[j] = pix;
+          p.w.fb_cost[j] = cost;
+        }
+      }
+      const PixRef ref = resolve(p, pix, K);
+      const KOut &o = ref.o;
+      const long long op = ref.opix;
+      if (o.state) {
+        for (int k = 0; k < K + 2; k++) o.state[op * NSx + k] = p.w.s1x[pix * (K + 2) + k];
+        for (int k = 0; k < 6; k++) o.state[op * NSx + K + 2 + k] = x2[k];
+      }
+      if (o.cov)
+        for (int k = 0; k < 21; k++) o.cov[op * 21 + k] = io.cov[k];
+      if (o.ET) o.ET[op] = ET;
+      if (o.sdT) o.sdT[op] = sdT;
+      if (o.alpha) o.alpha[op] = x2[5];
+      if (o.var_ET) o.var_ET[op] = (float)io.vE;
+      if (o.cost) o.cost[op] = cost;
+      if (o.rms) o.rms[op] = rms;
+      if (o.status) o.status[op] = (uint8_t)status;
+      if (o.iters) o.iters[2 * op + 1] = (uint16_t)it2;
+      st_fp64 += (status & PX_F_FP64) ? 1ull : 0ull;
+#pragma unroll
+      for (int k = 0; k < 8; k++) st_s[k] += ((status & 7) == k) ? 1ull : 0ull;
+    }
   }
   // warp-aggregate, then one shared atomic per warp and counter
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     st_fp64 += __shfl_xor_sync(kFull, st_fp64, o);
+    st_post += __shfl_xor_sync(kFull, st_post, o);
 #pragma unroll
     for (int k = 0; k < 8; k++) st_s[k] += __shfl_xor_sync(kFull, st_s[k], o);
   }
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     if (st_fp64) atomicAdd(&cstat[ST_FP64], st_fp64);
+    if (st_post) atomicAdd(&cstat[ST_POST64], st_post);
     for (int k = 0; k < 8; k++)
       if (st_s[k]) atomicAdd(&cstat[ST_STATUS0 + k], st_s[k]);
   }
@@ -2554,10 +2706,74 @@ __global__ void __launch_bounds__(128) finalize_kernel(const __grid_constant__ L
     if (cstat[i]) atomicAdd(p.w.stats + i, cstat[i]);
 }
 
+// ---- residual spectrum (Sec. 3.2's spectral residuals): r_b = L_b - M_b(x)
+// of the full forward model Eq. (fm) at each fitted pixel's final state, for
+// every band, one warp per pixel: the normalised grid weights of the two
+// mixture components (Eq. thermal) in shared memory, then per band the
+// solar term (Eq. solar) at the stage-1 surface and the thermal grid sum
+// against the context's Planck table [nt][nb]. Pixels not fitted get NaN.
+__global__ void __launch_bounds__(256) resid_kernel(const __grid_constant__ LMLaunch p) {
+  __shared__ float wsh[8][kMaxTgrid];
+  if (cta_err(p.w.err)) return;
+  const KTables &t = p.t;
+  const int K = t.K, nb = t.nb, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float *wj = wsh[warp];
+  const long long nw = (long long)gridDim.x * 8;
+  for (long long pix = (long long)blockIdx.x * 8 + warp; pix < p.s.n_pix; pix += nw) {
+    const PixRef ref = resolve(p, pix, K);
+    if (!ref.o.resid) continue;
+    float *r = ref.o.resid + ref.opix * nb;
+    if (!(p.w.s1meta[pix] & kFitted)) {
+      for (int b = lane; b < nb; b += 32) r[b] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    const float *x1 = p.w.s1x + pix * (K + 2);
+    const float *x2 = p.w.s2x + pix * kS2Hand;
+    const float mh = x2[0], sh = x2[1], ms = x2[2], ss = x2[3], eta = x2[4], al = x2[5];
+    float uh[kMaxTgrid / 32], us[kMaxTgrid / 32], Uh = 0.f, Us = 0.f;
+#pragma unroll
+    for (int q = 0; q < kMaxTgrid / 32; q++) {
+      const int j = lane + 32 * q;
+      uh[q] = us[q] = 0.f;
+      if (j < t.nt) {
+        const float T = t.tglo + (float)j * t.tgstep;
+        const float dh = (T - mh) / sh, ds = (T - ms) / ss;
+        uh[q] = expf(-0.5f * dh * dh);
+        us[q] = expf(-0.5f * ds * ds);
+      }
+      Uh += uh[q];
+      Us += us[q];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      Uh += __shfl_xor_sync(kFull, Uh, o);
+      Us += __shfl_xor_sync(kFull, Us, o);
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxTgrid / 32; q++) {
+      const int j = lane + 32 * q;
+      if (j < t.nt) wj[j] = eta * uh[q] / Uh + (1.f - eta) * us[q] / Us;
+    }
+    __syncwarp();
+    const float4 *row = t.wvtab + (size_t)ref.wv * nb;
+    const float *endm = t.image + t.lay.off_endm;
+    for (int b = lane; b < nb; b += 32) {
+      const float4 q = __ldg(row + b);
+      float rho = 0.f;
+      for (int k = 0; k < K; k++) rho = fmaf(x1[k], __ldg(endm + k * nb + b), rho);
+      float acc = 0.f;
+      for (int j = 0; j < t.nt; j++) acc = fmaf(wj[j], __ldg(t.planck_full + (size_t)j * nb + b), acc);
+      const float M = q.y + q.x * rho / (1.f - q.z * rho) + al * q.w * acc;
+      r[b] = __ldg(ref.row + b) - M;
+    }
+    __syncwarp();
+  }
+}
+
 // ---- keep the lower-cost of the learned-start fit and the default-start
 // re-fit of each flagged pixel; both get the MLP_FALLBACK flag
 __global__ void merge_fallback_kernel(const long long *idx, const float *cost_first, long long nfb,
-                                      KOut compact, KOut out, int K) {
+                                      KOut compact, KOut out, int K, int nb) {
   const int NSx = K + 8;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nfb;
        j += (long long)gridDim.x * blockDim.x) {
@@ -2577,6 +2793,8 @@ __global__ void merge_fallback_kernel(const long long *idx, const float *cost_fi
         out.iters[2 * pix] = compact.iters[2 * j];
         out.iters[2 * pix + 1] = compact.iters[2 * j + 1];
       }
+      if (out.resid && compact.resid)
+        for (int b = 0; b < nb; b++) out.resid[pix * nb + b] = compact.resid[j * nb + b];
     }
     if (out.status)
       out.status[pix] = (uint8_t)((take ? compact.status[j] : out.status[pix]) | PX_F_MLP_FALLBACK);
@@ -2596,7 +2814,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) normal_eq_kernel(const __grid_co
   const KConfig &c = p.c;
   const int lane = threadIdx.x & 31;
   const int img_f = image_floats(t, stage);
-  if (!stage_tables(t, smem, img_f, &bar, p.w.err)) return;
+  if (!stage_tables(t, smem, img_f, &bar, p.w.err, c.wait_spins)) return;
   const Grp<G> gp(lane);
   const int gid = threadIdx.x / G, groups = blockDim.x / G;
   PixCtx pc;
@@ -2744,12 +2962,19 @@ cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *block
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   if ((e = launch_stage2<K>(p, num_sms, st, blocks_used, v2)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-  long long blocks = (p.s.n_pix + 127) / 128;
+  long long blocks = (p.s.n_pix + kFinWarps * 32 - 1) / (kFinWarps * 32);
   if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
-  finalize_kernel<<<(int)blocks, 128, 0, st>>>(p, K);
+  finalize_kernel<<<(int)blocks, kFinWarps * 32, 0, st>>>(p, K);
   if (blocks_used) *blocks_used += (int)blocks;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ev) return cudaEventRecord(ev[3], st);
+  if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
+  if (p.s.want_resid) {
+    long long rb = (p.s.n_pix + 7) / 8;
+    if (rb > (long long)num_sms * 16) rb = (long long)num_sms * 16;
+    resid_kernel<<<(int)rb, 256, 0, st>>>(p);
+    if (blocks_used) *blocks_used += (int)rb;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
@@ -2813,11 +3038,12 @@ cudaError_t launch_lm(const LMLaunch &p, int num_sms, cudaStream_t st, int *bloc
 }
 
 cudaError_t launch_merge_fallback(const long long *idx, const float *cost_first, long long nfb,
-                                  const KOut &compact, const KOut &out, int K, cudaStream_t st) {
+                                  const KOut &compact, const KOut &out, int K, int nb,
+                                  cudaStream_t st) {
   if (nfb <= 0) return cudaSuccess;
   long long blocks = (nfb + 127) / 128;
   if (blocks > 4096) blocks = 4096;
-  merge_fallback_kernel<<<(int)blocks, 128, 0, st>>>(idx, cost_first, nfb, compact, out, K);
+  merge_fallback_kernel<<<(int)blocks, 128, 0, st>>>(idx, cost_first, nfb, compact, out, K, nb);
   return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ namespace {
 
 template <class T>
 cudaError_t dalloc(T **p, size_t n) {
-  return cudaMalloc((void **)p, n * sizeof(T));
+  return dev_malloc((void **)p, n * sizeof(T));
 }
 
 GemmArgs gemm(const __nv_bfloat16 *A, long long lda, const __nv_bfloat16 *B, long long ldb, int M,
@@ -86,14 +86,14 @@ void fire_mlp_free_buffers(fire_mlp *m) {
                   m->h2, m->h2T, m->z, m->tgt, m->msk, m->dy, m->dyT, m->dh2, m->dh2T, m->dh1,
                   m->dh1T, m->gW1, m->gW2, m->gW3T, m->gb1, m->gb2, m->gb3, m->loss, m->err,
                   m->rad};
-  for (void *p : ptrs) cudaFree(p);
+  for (void *p : ptrs) dev_free(p);
 }
 
 fire_status_t fire_mlp_reserve(fire_mlp *m, long long B) {
   if (B <= m->cap) return FIRE_OK;
   void *old[] = {m->x, m->xT, m->h1, m->h1T, m->h2, m->h2T, m->z, m->tgt, m->msk, m->dy, m->dyT,
                  m->dh2, m->dh2T, m->dh1, m->dh1T, m->rad};
-  for (void *p : old) cudaFree(p);
+  for (void *p : old) dev_free(p);
   const int Din = m->Din, H = m->H;
   m->cap = 0;
   MCK(dalloc(&m->x, (size_t)B * Din));
@@ -358,8 +358,8 @@ fire_status_t fire_mlp_gradients(fire_mlp_t *m, const float *x, const float *tgt
     if (loss) cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDeviceToDevice, st);
   }
   cudaStreamSynchronize(st);
-  cudaFree(ones);
-  cudaFree(zeros);
+  dev_free(ones);
+  dev_free(zeros);
   return e;
 }
 

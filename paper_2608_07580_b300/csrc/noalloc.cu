@@ -1,7 +1,9 @@
 // noalloc.cu — fire_retrieve_static: the plain-LM fit of a device scene
-// whose stage hand-over scratch, work counters, statistics and error word
-// live in one file-scope device array, so that the call allocates nothing.
+// whose stage hand-over scratch, work counters and statistics live in one
+// file-scope device array, so that the call allocates nothing.
 #include <string.h>
+
+#include <mutex>
 
 #include "ctx_internal.h"
 
@@ -20,14 +22,17 @@ constexpr size_t kS1m = al256((size_t)kStaticMaxPix * 4);
 constexpr size_t kS2x = al256((size_t)kStaticMaxPix * 32 * 4);
 constexpr size_t kS2g = al256((size_t)kStaticMaxPix * 6 * 4);
 constexpr size_t kWork = al256((size_t)(2 + ST_COUNT) * 8);
-constexpr size_t kErr = al256(sizeof(int));
-constexpr size_t kStaticBytes = kS1x + kS1m + kS2x + kS2g + kWork + kErr;
+constexpr size_t kStaticBytes = kS1x + kS1m + kS2x + kS2g + kWork;
+static_assert(kStaticBytes <= FIRE_STATIC_SCRATCH_BYTES,
+              "the static scratch outgrew the size the header documents");
 
 static __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
 
 // device address of g_scratch on each device, looked up on the first call
+// (under a lock, so that two threads' first calls do not race on it)
 constexpr int kMaxDevices = 64;
 unsigned char *g_base[kMaxDevices] = {};
+std::mutex g_base_mu;
 
 }  // namespace
 
@@ -43,24 +48,29 @@ extern "C" fire_status_t fire_retrieve_static(fire_ctx_t *c, const fire_scene_t 
     fire_default_priors(&pd, c->t.K, c->t.nt, c->t.tglo, c->t.tglo + c->t.tgstep * (c->t.nt - 1));
     pri = &pd;
   }
-  if (!priors_valid(*pri, c->t.K)) return FIRE_ERR_ARG;
+  if (!priors_valid(*pri, c->t.K) || !noise_sd_valid(*pri, c->t.nb)) return FIRE_ERR_ARG;
   if (pri->init_mode == FIRE_INIT_MLP) return FIRE_ERR_ARG;   // the learned start allocates
   if (pri->init_mode == FIRE_INIT_GIVEN && !pri->init_state) return FIRE_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FIRE_ERR_CUDA;
-  if (!g_base[dev]) {
+  unsigned char *b = nullptr;
+  {
     // set-up, once per device (do this first call outside any stream capture)
-    void *a = nullptr;
-    if (cudaGetSymbolAddress(&a, g_scratch) != cudaSuccess) return FIRE_ERR_CUDA;
-    g_base[dev] = (unsigned char *)a;
+    std::lock_guard<std::mutex> lk(g_base_mu);
+    if (!g_base[dev]) {
+      void *a = nullptr;
+      if (cudaGetSymbolAddress(&a, g_scratch) != cudaSuccess) return FIRE_ERR_CUDA;
+      g_base[dev] = (unsigned char *)a;
+    }
+    b = g_base[dev];
   }
-  unsigned char *b = g_base[dev];
   cudaStream_t st = (cudaStream_t)stream;
   unsigned long long *work = (unsigned long long *)(b + kS1x + kS1m + kS2x + kS2g);
-  int *err = (int *)(b + kS1x + kS1m + kS2x + kS2g + kWork);
-  // the claim counters, the statistics and the error word start at zero
+  // the claim counters, the statistics and the context's error word start
+  // at zero; a bounded wait that gives up sets that word, which the next
+  // fire_get_stats on the context reports as FIRE_ERR_TIMEOUT
   if (cudaMemsetAsync(work, 0, (size_t)(2 + ST_COUNT) * 8, st) != cudaSuccess ||
-      cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
+      cudaMemsetAsync(c->d_err, 0, sizeof(int), st) != cudaSuccess)
     return FIRE_ERR_CUDA;
   c->last_launches = 0;
   if (sc->n_pix == 0) return FIRE_OK;
@@ -74,7 +84,7 @@ extern "C" fire_status_t fire_retrieve_static(fire_ctx_t *c, const fire_scene_t 
   p.w.s2g = (float *)(b + kS1x + kS1m + kS2x);
   p.w.counter = work;
   p.w.stats = work + 2;
-  p.w.err = err;
+  p.w.err = c->d_err;
   p.s.rad = sc->radiance;
   p.s.wv = sc->wv_bin;
   p.s.init = pri->init_mode == FIRE_INIT_GIVEN ? pri->init_state : nullptr;
@@ -89,6 +99,8 @@ extern "C" fire_status_t fire_retrieve_static(fire_ctx_t *c, const fire_scene_t 
   p.o.hfdi = out->hfdi;
   p.o.status = out->status;
   p.o.iters = out->iters;
+  p.o.resid = out->resid_spec;
+  p.s.want_resid = out->resid_spec != nullptr;
   int blocks = 0;
   if (launch_lm(p, c->num_sms, st, &blocks, c->tune_variant) != cudaSuccess) return FIRE_ERR_CUDA;
   c->last_launches = 3;

@@ -31,7 +31,11 @@ SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fir
            "fire_mlp_load", "fire_mlp_next_sample", "fire_ctx_set_mlp", "fire_retrieve_batch",
            "fire_graph_capture", "fire_graph_launch", "fire_graph_destroy", "fire_autotune",
            "fire_set_tuning", "fire_set_kernel_timing", "fire_get_kernel_times",
-           "fire_retrieve_static")
+           "fire_retrieve_static", "fire_set_allocator")
+
+# device allocator hook (fire_set_allocator): alloc(bytes, user) -> ptr, free(ptr, user)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 
 class FireError(RuntimeError):
@@ -54,7 +58,8 @@ class Config_t(C.Structure):
                 ("kappa_max", C.c_float), ("dfloor", C.c_float), ("noise_rel", C.c_float),
                 ("noise_abs", C.c_float), ("weighted", C.c_int32), ("hfdi_thresh", C.c_float),
                 ("hfdi_lambda_hi", C.c_float), ("hfdi_lambda_lo", C.c_float),
-                ("ident_sd_et", C.c_float), ("ident_alpha_snr", C.c_float)]
+                ("ident_sd_et", C.c_float), ("ident_alpha_snr", C.c_float),
+                ("wait_spins", C.c_int64)]
 
 
 class Priors_t(C.Structure):
@@ -64,7 +69,8 @@ class Priors_t(C.Structure):
                 ("pp2", C.c_float * 6), ("init_alpha1", C.c_float), ("init_T1", C.c_float),
                 ("init_sigma", C.c_float), ("init_mu_h_floor", C.c_float),
                 ("init_mu_s_ceil", C.c_float), ("init_eta_lo", C.c_float),
-                ("init_eta_hi", C.c_float), ("init_mode", C.c_int32), ("init_state", C.c_void_p)]
+                ("init_eta_hi", C.c_float), ("init_mode", C.c_int32), ("init_state", C.c_void_p),
+                ("noise_sd", C.c_void_p)]
 
 
 class Scene_t(C.Structure):
@@ -72,9 +78,12 @@ class Scene_t(C.Structure):
                 ("mem", C.c_int32), ("gate_mode", C.c_int32)]
 
 
+OUTPUT_FIELDS = ("state", "ET", "sdT", "alpha", "cov", "var_ET", "cost", "rms", "hfdi", "status",
+                 "iters", "resid_spec")
+
+
 class Outputs_t(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("state", "ET", "sdT", "alpha", "cov", "var_ET", "cost",
-                                          "rms", "hfdi", "status", "iters")]
+    _fields_ = [(n, C.c_void_p) for n in OUTPUT_FIELDS]
 
 
 class Gemm_t(C.Structure):
@@ -108,7 +117,7 @@ class Stats_t(C.Structure):
                 ("solves64_1", C.c_uint64), ("solves64_2", C.c_uint64), ("mma_rounds2", C.c_uint64),
                 ("status_counts", C.c_uint64 * 8), ("flops", C.c_double),
                 ("flops1", C.c_double), ("flops2", C.c_double),
-                ("kernel_launches", C.c_int32)]
+                ("kernel_launches", C.c_int32), ("n_post64", C.c_uint64)]
 
 
 def _load():
@@ -179,6 +188,8 @@ def _load():
     lib.fire_set_tuning.restype = C.c_int
     lib.fire_status_str.argtypes = [C.c_int]
     lib.fire_status_str.restype = C.c_char_p
+    lib.fire_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+    lib.fire_set_allocator.restype = None
     return lib
 
 
@@ -273,13 +284,16 @@ class Context:
         _check(lib.fire_window_bands(self._h, *[C.byref(x) for x in v]), "fire_window_bands")
         return tuple(x.value for x in v)
 
-    def alloc_outputs(self, n, device=True):
-        """Output buffers for n pixels: torch CUDA tensors (device) or numpy (host)."""
+    def alloc_outputs(self, n, device=True, resid=False):
+        """Output buffers for n pixels: torch CUDA tensors (device) or numpy
+        (host); resid adds the residual spectrum [n, n_bands]."""
         ns = self.n_endm + 8
         shapes = {"state": ((n, ns), "f4"), "ET": ((n,), "f4"), "sdT": ((n,), "f4"),
                   "alpha": ((n,), "f4"), "cov": ((n, 21), "f4"), "var_ET": ((n,), "f4"),
                   "cost": ((n,), "f4"), "rms": ((n,), "f4"), "hfdi": ((n,), "f4"),
                   "status": ((n,), "u1"), "iters": ((n, 2), "u2")}
+        if resid:
+            shapes["resid_spec"] = ((n, self.n_bands), "f4")
         if device:
             import torch
             tm = {"f4": torch.float32, "u1": torch.uint8, "u2": torch.int16}
@@ -292,20 +306,30 @@ class Context:
         _check(lib.fire_ctx_set_mlp(self._h, None if mlp is None else mlp._h), "fire_ctx_set_mlp")
         self._mlp = mlp
 
+    def _priors(self, priors, noise_sd):
+        pri = Priors_t()
+        C.memmove(C.byref(pri), C.byref(priors if priors is not None else self.default_priors()),
+                  C.sizeof(Priors_t))
+        if noise_sd is not None:
+            self._nsd = np.ascontiguousarray(noise_sd, dtype=np.float32)
+            if self._nsd.shape != (self.n_bands,):
+                raise FireError("noise_sd must have one value per band")
+            pri.noise_sd = self._nsd.ctypes.data
+        return pri
+
     def retrieve(self, radiance, wv_bin, priors=None, init_state=None, gate_hfdi=False,
-                 outputs=None, stream=None, learned_start=False):
+                 outputs=None, stream=None, learned_start=False, noise_sd=None, resid=False):
         """Fit every pixel. radiance [n, n_bands] float32 and wv_bin [n] (uint16
         numpy or int16/uint16-bit torch): torch CUDA tensors for device
-        scenes, numpy arrays for host scenes (staged inside the call)."""
+        scenes, numpy arrays for host scenes (staged inside the call).
+        noise_sd: per-band noise sd (numpy, host) weighting the loss; resid:
+        also return the residual spectrum."""
         import torch
         host = isinstance(radiance, np.ndarray)
         n = int(radiance.shape[0])
-        if priors is None:
-            priors = self.default_priors()
         if outputs is None:
-            outputs = self.alloc_outputs(n, device=not host)
-        pri = Priors_t()
-        C.memmove(C.byref(pri), C.byref(priors), C.sizeof(Priors_t))
+            outputs = self.alloc_outputs(n, device=not host, resid=resid)
+        pri = self._priors(priors, noise_sd)
         if learned_start:
             pri.init_mode = FIRE_INIT_MLP
         if host:
@@ -328,34 +352,28 @@ class Context:
                 pri.init_mode, pri.init_state = FIRE_INIT_GIVEN, _dptr(init_state, torch.float32)
             ptr = lambda k: _dptr(outputs.get(k))  # noqa: E731
             stream_p = _stream_ptr(stream)
-        o = Outputs_t(*[ptr(k) for k in ("state", "ET", "sdT", "alpha", "cov", "var_ET", "cost",
-                                         "rms", "hfdi", "status", "iters")])
+        o = Outputs_t(*[ptr(k) for k in OUTPUT_FIELDS])
         _check(lib.fire_retrieve(self._h, C.byref(sc), C.byref(pri), C.byref(o), stream_p),
                "fire_retrieve")
         return outputs
 
     def retrieve_static(self, radiance, wv_bin, priors=None, init_state=None, gate_hfdi=False,
-                        outputs=None, stream=None):
+                        outputs=None, stream=None, noise_sd=None):
         """fire_retrieve_static: the plain-LM fit of a device scene (at most
         STATIC_MAX_PIX pixels) through the library's static scratch, without
         any allocation inside the call."""
         import torch
         n = int(radiance.shape[0])
-        if priors is None:
-            priors = self.default_priors()
         if outputs is None:
             outputs = self.alloc_outputs(n)
-        pri = Priors_t()
-        C.memmove(C.byref(pri), C.byref(priors), C.sizeof(Priors_t))
+        pri = self._priors(priors, noise_sd)
         if wv_bin.element_size() != 2:
             raise FireError("wv_bin must be a 16-bit tensor")
         if init_state is not None:
             pri.init_mode, pri.init_state = FIRE_INIT_GIVEN, _dptr(init_state, torch.float32)
         sc = Scene_t(n, _dptr(radiance, torch.float32), _dptr(wv_bin), FIRE_MEM_DEVICE,
                      int(bool(gate_hfdi)))
-        o = Outputs_t(*[_dptr(outputs.get(k)) for k in ("state", "ET", "sdT", "alpha", "cov",
-                                                       "var_ET", "cost", "rms", "hfdi",
-                                                       "status", "iters")])
+        o = Outputs_t(*[_dptr(outputs.get(k)) for k in OUTPUT_FIELDS])
         _check(lib.fire_retrieve_static(self._h, C.byref(sc), C.byref(pri), C.byref(o),
                                         _stream_ptr(stream)), "fire_retrieve_static")
         return outputs
@@ -378,9 +396,7 @@ class Context:
         for i, ((rad, wv), out) in enumerate(zip(scenes, outputs)):
             ptr = lambda k: _dptr(out.get(k))  # noqa: E731
             arr[i] = BatchItem_t(int(rad.shape[0]), _dptr(rad, torch.float32), _dptr(wv),
-                                 Outputs_t(*[ptr(k) for k in ("state", "ET", "sdT", "alpha", "cov",
-                                                              "var_ET", "cost", "rms", "hfdi",
-                                                              "status", "iters")]))
+                                 Outputs_t(*[ptr(k) for k in OUTPUT_FIELDS]))
         return arr
 
     def retrieve_batch(self, scenes, outputs=None, priors=None, gate_hfdi=False, stream=None):
@@ -423,7 +439,8 @@ class Context:
     def set_tuning(self, variant, claim):
         _check(lib.fire_set_tuning(self._h, variant, claim), "fire_set_tuning")
 
-    def normal_equations(self, stage, radiance, wv_bin, states, priors=None, stream=None):
+    def normal_equations(self, stage, radiance, wv_bin, states, priors=None, stream=None,
+                         noise_sd=None):
         """(H, g, cost) of one stage at the given states (device tensors)."""
         import torch
         n = int(states.shape[0])
@@ -431,7 +448,7 @@ class Context:
         H = torch.empty((n, P, P), dtype=torch.float32, device="cuda")
         g = torch.empty((n, P), dtype=torch.float32, device="cuda")
         cost = torch.empty((n,), dtype=torch.float32, device="cuda")
-        pr = None if priors is None else C.byref(priors)
+        pr = C.byref(self._priors(priors, noise_sd))
         _check(lib.fire_normal_equations(self._h, stage, _dptr(radiance, torch.float32),
                                          _dptr(wv_bin), _dptr(states, torch.float32), n, pr,
                                          _dptr(H), _dptr(g), _dptr(cost), _stream_ptr(stream)),

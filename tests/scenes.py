@@ -9,9 +9,9 @@ import synth
 NOISE_REL, NOISE_ABS = 0.005, 1e-4
 
 
-def config1(seed=0, width=64, height=64, **kw):
+def config1(seed=0, width=64, height=64, fire_frac=0.05, **kw):
     t = synth.make_tables(**kw)
-    tr = synth.make_config1_truth(seed=seed, width=width, height=height)
+    tr = synth.make_config1_truth(seed=seed, width=width, height=height, fire_frac=fire_frac)
     z = synth.noise_normals(seed, np.arange(tr.n_pix), t.n_bands)
     L = oracle.synth_radiance(t, 1, tr.state1(), tr.wv_bin, z, NOISE_REL, NOISE_ABS)
     return t, tr, L
@@ -25,26 +25,86 @@ def config2_subset(idx, truth, tables, seed=1):
     return sub, L
 
 
-def parity_stats(o, g, bar_T=0.5, bar_a=1e-3):
-    """Compare GPU outputs g with oracle outputs o over pixels the oracle calls
-    converged and identifiable and the GPU calls converged."""
+def _near(v, thr, rel=0.02):
+    return np.abs(v - thr) <= rel * thr
+
+
+def ident_borderline(o, cfg=None, rel=0.02):
+    """Pixels whose identifiability decision lies within rel of one of its
+    thresholds in the oracle (Laplace sd(E[T]) against ident_sd_et, alpha /
+    sd(alpha) against ident_alpha_snr): there two correct solvers may decide
+    either way."""
+    cfg = cfg or oracle.Config()
+    with np.errstate(invalid="ignore", divide="ignore"):
+        sdE = np.sqrt(o["var_ET"])
+        snr = o["alpha"] / np.sqrt(o["cov"][:, 20])
+    return _near(sdE, cfg.ident_sd_et, rel) | _near(snr, cfg.ident_alpha_snr, rel)
+
+
+# Width of the band around the identifiability thresholds inside which the
+# end-to-end flag mismatches are not counted (reported only).
+IDENT_BAND = 0.1
+
+
+def parity_stats(o, g, bar_T=0.5, bar_a=1e-3, cfg=None, ident_band=IDENT_BAND):
+    """Parity of GPU outputs g with oracle outputs o (the benchmark spec's bar).
+
+    The pool is every pixel the oracle calls converged and identifiable. A
+    pool pixel passes when the GPU also converged and |dE[T]| <= 0.5 K and
+    |d alpha| <= 1e-3 max(alpha_oracle, 1e-4); a pixel the GPU did not
+    converge is a miss. rate = passes / pool.
+
+    Secondary outputs, over the pool pixels that pass: sigma[T] within 0.5 K;
+    the stage-2 cost and the residual rms within 1e-4 relative. sec_rate =
+    pixels passing all of them / those pixels.
+
+    The identifiability flag is reported, not held to a rate: it is a
+    threshold on the Laplace sd(E[T]) and alpha / sd(alpha), which jump
+    where a variable of the near-degenerate mixture sits on its bound in one
+    final state and just off it in the other (both pass the convergence
+    test); the flag is checked against the oracle's decision at the GPU's own
+    final state instead (test_posterior_at_the_gpu_state_matches_oracle).
+    ident_mismatch counts the pixels, converged in both, where the two flags
+    differ outside the band ident_band around the thresholds."""
     ost = o["status"].astype(np.int64)
     gst = np.asarray(g["status"]).astype(np.int64)
     conv_o = (ost & 7) == 0
     ident_o = (ost & oracle.F_NOT_IDENT) == 0
     conv_g = (gst & 7) == 0
-    pool = conv_o & ident_o & conv_g
-    dT = np.abs(np.asarray(g["ET"], np.float64) - o["ET"])
-    da = np.abs(np.asarray(g["alpha"], np.float64) - o["alpha"])
-    okT = dT <= bar_T
-    oka = da <= bar_a * np.maximum(o["alpha"], 1e-4)
-    ok = okT & oka
+    pool = conv_o & ident_o
+    with np.errstate(invalid="ignore"):
+        dT = np.abs(np.asarray(g["ET"], np.float64) - o["ET"])
+        da = np.abs(np.asarray(g["alpha"], np.float64) - o["alpha"])
+        ok_vals = (dT <= bar_T) & (da <= bar_a * np.maximum(o["alpha"], 1e-4))
+    ok = pool & conv_g & ok_vals
     n = int(pool.sum())
+    sec = ok
+    with np.errstate(invalid="ignore", divide="ignore"):
+        dsd = np.abs(np.asarray(g["sdT"], np.float64) - o["sdT"])
+        dcost = np.abs(np.asarray(g["cost"], np.float64) / o["cost"] - 1.0)
+        drms = np.abs(np.asarray(g["rms"], np.float64) / o["rms"] - 1.0)
+    border = ident_borderline(o, cfg, ident_band)
+    ident_g = (gst & oracle.F_NOT_IDENT) == 0
+    f_sd = sec & ~(dsd <= 0.5)
+    f_cost = sec & ~(dcost <= 1e-4)
+    f_rms = sec & ~(drms <= 1e-4)
+    sec_fail = f_sd | f_cost | f_rms
+    both = conv_o & conv_g
+    ident_mis = both & (ident_g != ident_o) & ~border
     return {
-        "n": int(ost.size), "pool": n, "oracle_conv_ident": int((conv_o & ident_o).sum()),
-        "excluded_gpu_not_conv": int((conv_o & ident_o & ~conv_g).sum()),
-        "pass": int((ok & pool).sum()), "rate": float((ok & pool).sum() / max(n, 1)),
-        "max_dT": float(dT[pool].max()) if n else 0.0,
-        "max_rel_da": float((da / np.maximum(o["alpha"], 1e-4))[pool].max()) if n else 0.0,
-        "fail_idx": np.flatnonzero(pool & ~ok),
+        "n": int(ost.size), "pool": n, "pass": int(ok.sum()), "rate": float(ok.sum() / max(n, 1)),
+        "gpu_not_conv": int((pool & ~conv_g).sum()),
+        "value_fail": int((pool & conv_g & ~ok_vals).sum()),
+        "max_dT": float(dT[sec].max()) if sec.any() else 0.0,
+        "max_rel_da": float((da / np.maximum(o["alpha"], 1e-4))[sec].max()) if sec.any() else 0.0,
+        "sec_n": int(sec.sum()), "sec_rate": float((sec & ~sec_fail).sum() / max(int(sec.sum()), 1)),
+        "sdT_fail": int(f_sd.sum()), "cost_fail": int(f_cost.sum()), "rms_fail": int(f_rms.sum()),
+        "max_dsdT": float(dsd[sec].max()) if sec.any() else 0.0,
+        "max_rel_dcost": float(dcost[sec].max()) if sec.any() else 0.0,
+        "both_conv": int(both.sum()), "ident_mismatch": int(ident_mis.sum()),
+        "fail_idx": np.flatnonzero(pool & ~ok), "sec_fail_idx": np.flatnonzero(sec_fail),
     }
+
+
+def summary(s):
+    return {k: v for k, v in s.items() if not k.endswith("_idx")}

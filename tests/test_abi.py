@@ -65,3 +65,34 @@ def test_null_arguments_are_rejected_without_gpu():
     assert lib.fire_ctx_create(C.byref(h), None, None) == 1
     assert lib.fire_retrieve(None, None, None, None, None) == 1
     assert lib.fire_status_str(4) == b"unsupported shape"
+
+
+def test_allocator_hook_failure_gives_nomem_without_gpu():
+    """A failing allocator installed through fire_set_allocator makes
+    fire_ctx_create return FIRE_ERR_NOMEM at its first device allocation
+    (no GPU needed: the hook answers before the runtime is asked)."""
+    import synth
+    from paper_2608_07580_b300 import firert
+    calls = []
+
+    def alloc(n, user):
+        calls.append(n)
+        return None
+
+    a, f = firert.ALLOC_FN(alloc), firert.FREE_FN(lambda p, u: None)
+    firert.lib.fire_set_allocator(a, f, None)
+    try:
+        with pytest.raises(firert.FireError, match="out of memory"):
+            firert.Context(synth.make_tables())
+    finally:
+        firert.lib.fire_set_allocator(firert.ALLOC_FN(), firert.FREE_FN(), None)
+    assert len(calls) == 1 and calls[0] > 0
+
+
+def test_config_and_priors_layout_carry_the_new_fields():
+    from paper_2608_07580_b300 import firert
+    c = firert.default_config()
+    assert c.wait_spins == 0                  # 0 = the default limit
+    p = firert.default_priors(3)
+    assert p.noise_sd is None                 # unweighted Eq. (loss) by default
+    assert "resid_spec" in firert.OUTPUT_FIELDS

@@ -36,24 +36,34 @@ def test_gradients_match_oracle(env):
          "W3": rng.normal(0, 0.15, (16, H)), "b3": rng.normal(0, 0.1, 16),
          "mean": np.zeros(D), "istd": np.ones(D)}
     mlp.params(p)
-    B = 256
-    x = rng.normal(size=(B, D)).astype(np.float32)
-    x[:, 284:] = 0
+    ref = {k: _bf16(p[k]) if k.startswith("W") else p[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    # The kernels store h1 and h2 (the next layer's tensor-core operand) in
+    # bf16, which moves a pre-activation by up to ~2^-8 of the norm of its
+    # terms; a unit that close to 0 may take the other side of its ReLU gate
+    # than in FP64, a discrete change no rounding bound covers. The batch is
+    # therefore drawn from candidates whose pre-activations (FP64, through
+    # the bf16 weights and inputs) all lie farther than 2^-7 of that norm
+    # from zero, and the oracle is the unmodified FP64 backward.
+    cand = rng.normal(size=(1024, D))
+    cand[:, 284:] = 0
+    xc = _bf16(cand)
+    a1, a2, _ = oracle.mlp_forward(ref, xc)
+    n1 = np.sqrt((xc ** 2) @ (ref["W1"] ** 2).T)
+    h1 = np.maximum(a1, 0.0)
+    n2 = np.sqrt((h1 ** 2) @ (ref["W2"] ** 2).T)
+    clear = np.all(np.abs(a1) > 2 ** -7 * n1, axis=1) & np.all(np.abs(a2) > 2 ** -7 * n2, axis=1)
+    keep = np.flatnonzero(clear)
+    B = (min(keep.size, 256) // 8) * 8
+    assert B >= 64, keep.size
+    x = cand[keep[:B]].astype(np.float32)
     tgt = np.tanh(rng.normal(size=(B, 16))).astype(np.float32)
     msk = (rng.uniform(size=(B, 16)) < 0.8).astype(np.float32)
     msk[:, 9:] = 0
     g, loss = mlp.gradients(torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda(),
                             torch.from_numpy(msk).cuda())
-    ref = {k: _bf16(p[k]) if k.startswith("W") else p[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3")}
     lo, go, _ = oracle.mlp_backward(ref, _bf16(x), tgt, msk, n_out=9)
     assert abs(loss / lo - 1) < 2e-2
-    # The kernels store h1, h2 (the next layer's tensor-core operand) and the
-    # back-propagated dy, dh2, dh1 in bf16; the oracle keeps FP64. A bf16
-    # h1 moves layer-2 pre-activations by ~2^-9 relative, which flips the
-    # ReLU gate of the few units near zero; the first layer's gradient sums
-    # over those gates and moves by ~4e-2 on this network (reproduced by a
-    # host emulation of the bf16 stores), the others stay under 2e-2.
-    bound = {"W1": 6e-2, "b1": 6e-2, "W2": 2e-2, "b2": 2e-2, "W3": 2e-2, "b3": 2e-2}
+    bound = {"W1": 2e-2, "b1": 2e-2, "W2": 2e-2, "b2": 2e-2, "W3": 2e-2, "b3": 2e-2}
     pairs = (("W1", g["W1"], go["W1"]), ("b1", g["b1"], go["b1"]), ("W2", g["W2"], go["W2"]),
              ("b2", g["b2"], go["b2"]), ("W3", g["W3T"].T, go["W3"]), ("b3", g["b3"], go["b3"]))
     for name, a, b in pairs:
@@ -107,6 +117,17 @@ def test_learned_start_gains_over_plain_lm(env):
     print("mean iterations plain %.2f learned %.2f, fallback %.3f" % (
         it_p, it_l, np.mean((learned["status"] & 32) > 0)))
     assert it_l < it_p
-    good = ((plain["status"] & 23) == 0) & ((learned["status"] & 7) == 0)
-    agree = np.abs(plain["ET"] - learned["ET"])[good] <= 0.5
-    assert good.sum() > 20 and agree.mean() > 0.8
+    # plain LM judges the learned start: the learned-start retrieval against
+    # the oracle's default-start fit, at the full bar
+    from scenes import parity_stats, summary
+    o = oracle.retrieve(t, L, tr.wv_bin)
+    s = parity_stats(o, learned)
+    print("learned start vs oracle:", summary(s))
+    assert s["pool"] >= 100
+    assert s["rate"] >= 0.999, summary(s)
+    # accuracy against the seeded truth, plain and learned start
+    fire = np.flatnonzero((tr.kind == 1) & ((o["status"] & 23) == 0))
+    T = tr.single[fire, 1]
+    for name, r in (("plain", plain), ("learned", learned)):
+        e = r["ET"][fire] - T
+        print(f"{name}: E[T] vs truth RMSE {np.sqrt(np.mean(e ** 2)):.2f} K, MAE {np.mean(np.abs(e)):.2f} K")

@@ -33,6 +33,31 @@ def test_static_equals_retrieve_twice_in_a_row():
         assert np.all((got["status"] & 7) < 8)
 
 
+def test_static_calls_allocate_no_device_memory():
+    """After a first call (set-up, module loading), further calls with the
+    same preallocated outputs leave the device's free memory unchanged,
+    residual spectrum included; and they still equal fire_retrieve."""
+    import torch
+    from paper_2608_07580_b300 import firert as fr
+    t, tr, L = config1(width=48, height=48)
+    ctx = fr.Context(t)
+    Ld = torch.from_numpy(L).cuda()
+    wd = torch.from_numpy(tr.wv_bin.astype(np.int16)).cuda()
+    out = ctx.alloc_outputs(tr.n_pix, resid=True)
+    ref = _np(ctx.retrieve(Ld, wd, resid=True))
+    ctx.retrieve_static(Ld, wd, outputs=out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        ctx.retrieve_static(Ld, wd, outputs=out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    got = _np(out)
+    for k in KEYS + ("resid_spec",):
+        assert np.array_equal(ref[k], got[k], equal_nan=True), k
+    ctx.stats()   # no timeout recorded
+
+
 def test_static_rejects_oversize_and_learned_start():
     import torch
     from paper_2608_07580_b300 import firert as fr
