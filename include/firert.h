@@ -428,6 +428,15 @@ fire_status_t fire_get_stats(fire_ctx_t *ctx, fire_stats_t *stats);
 fire_status_t fire_window_bands(fire_ctx_t *ctx, int32_t *b1_lo, int32_t *n1,
                                 int32_t *b2_lo, int32_t *n2);
 
+/* Measured issue rate of an arithmetic unit the retrieval's kernels are
+ * bound by, for roofline denominators (synchronous, ~0.1 s): every SM
+ * loaded with independent dependency chains, timed with CUDA events on the
+ * stream. kind 0: FP32 FMA (flop/s, an FMA counted as 2); 1: the packed
+ * two-lane FP32 FMA (flop/s); 2: the SFU's ex2.approx (operations/s); 3:
+ * FP64 FMA (flop/s). seconds (optional) receives the timed duration.
+ * Errors: FIRE_ERR_ARG, FIRE_ERR_NOMEM, FIRE_ERR_CUDA. */
+fire_status_t fire_measure_peak(int32_t kind, double *rate, double *seconds, fire_stream_t stream);
+
 /* Device allocator hook. The library's device allocations (context tables
  * and workspace, host-scene staging, learned-start and batch buffers, the
  * network's weights) go through alloc(bytes, user) while a hook is set, and

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", f) for f in ("api.cu", "kernels_lm.cu", "kernels_aux.cu",
                                                "kernels_gemm.cu", "kernels_mlp.cu", "mlp.cu", "batch.cu",
-                                         "noalloc.cu", "alloc.cu")]
+                                         "noalloc.cu", "alloc.cu", "peaks.cu")]
 DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("internal.cuh", "model.cuh", "mlp_internal.h", "tc.cuh",
                                                        "ctx_internal.h")] + \
     [os.path.join(ROOT, "include", "firert.h")]

@@ -822,15 +822,21 @@ fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   s->mma_rounds2 = v[ST_MMA2];
   s->n_post64 = v[ST_POST64];
   for (int k = 0; k < 8; k++) s->status_counts[k] = v[ST_STATUS0 + k];
-  // algorithmic flops (FMA = 2): stage 1 per band and evaluation; stage 2 per
-  // band and evaluation (Jacobian, normal equations, cost and its
-  // increment-form decrease) plus 7 FMA per band and grid node (the six
-  // weight-moment sums and the weight-increment sum)
+  // algorithmic flops of the method (FMA = 2), per band and evaluation of
+  // each stage's model, Jacobian, normal equations and cost (the build's own
+  // increment-form decrease and FP32 rounding-floor estimate not counted):
+  //  stage 1 (P = K + 1 reduced variables): surface mixture 2K, solar term
+  //    5, Planck factor and its T derivative 9, model and residual 4,
+  //    Jacobian 2K + 6, weighted Jacobian P, J^T W J P (P + 1), J^T W r 2P,
+  //    cost 3: 4K + 27 + P (P + 1) + 3P (71 for K = 3);
+  //  stage 2: mixture model and residual 6, Jacobian 13, weighted Jacobian
+  //    6, J^T W J 42, J^T W r 12, cost 3 = 82, plus the six moment sums
+  //    (two components x three) over the grid: 12 per band and node
   const int K = c->t.K, P1 = K + 1;
-  const double f1 = 4.0 * K + 27.0 + 2.0 * P1 * (P1 + 1) / 2.0 + 3.0 * P1 + 4.0;
-  const double f2 = 30.0 + 2.0 * 21.0 + 3.0 * 6.0 + 4.0 + 6.0;
+  const double f1 = 4.0 * K + 27.0 + P1 * (P1 + 1.0) + 3.0 * P1;
+  const double f2 = 6.0 + 13.0 + 6.0 + 42.0 + 12.0 + 3.0;
   s->flops1 = f1 * (double)s->band_evals1;
-  s->flops2 = f2 * (double)s->band_evals2 + 14.0 * (double)s->node_band_evals2;
+  s->flops2 = f2 * (double)s->band_evals2 + 12.0 * (double)s->node_band_evals2;
   s->flops = s->flops1 + s->flops2;
   s->kernel_launches = c->last_launches;
   return err ? FIRE_ERR_TIMEOUT : FIRE_OK;

@@ -31,7 +31,7 @@ SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fir
            "fire_mlp_load", "fire_mlp_next_sample", "fire_ctx_set_mlp", "fire_retrieve_batch",
            "fire_graph_capture", "fire_graph_launch", "fire_graph_destroy", "fire_autotune",
            "fire_set_tuning", "fire_set_kernel_timing", "fire_get_kernel_times",
-           "fire_retrieve_static", "fire_set_allocator")
+           "fire_retrieve_static", "fire_set_allocator", "fire_measure_peak")
 
 # device allocator hook (fire_set_allocator): alloc(bytes, user) -> ptr, free(ptr, user)
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -190,6 +190,8 @@ def _load():
     lib.fire_status_str.restype = C.c_char_p
     lib.fire_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
     lib.fire_set_allocator.restype = None
+    lib.fire_measure_peak.argtypes = [i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+    lib.fire_measure_peak.restype = C.c_int
     return lib
 
 
@@ -461,6 +463,18 @@ class Context:
         d = {f: getattr(s, f) for f, _ in Stats_t._fields_ if f != "status_counts"}
         d["status_counts"] = list(s.status_counts)
         return d
+
+
+PEAK_KINDS = {"fp32_fma": 0, "fp32_fma2": 1, "sfu_ex2": 2, "fp64_fma": 3}
+
+
+def measure_peak(kind, stream=None):
+    """Measured rate of one arithmetic unit (fire_measure_peak): flop/s for
+    the FMA kinds, operations/s for the SFU's ex2."""
+    r, sec = C.c_double(), C.c_double()
+    _check(lib.fire_measure_peak(PEAK_KINDS[kind], C.byref(r), C.byref(sec), _stream_ptr(stream)),
+           "fire_measure_peak")
+    return r.value, sec.value
 
 
 def block_mean(src, width, height, n_bands, block=12, stream=None):

@@ -435,3 +435,77 @@ def test_oracle_refuses_tables_beyond_its_work_arrays():
     t = synth.make_tables(n_bands=520)
     with pytest.raises(ValueError):
         oracle.synth_radiance(t, 1, np.zeros((1, 5)), np.zeros(1, np.int64))
+
+
+# ------------------------------------------------- the weak prior -------
+def _cost(tables, stage, L, w, x, cfg):
+    return oracle.normal_equations(tables, stage, L, w, x, cfg)[2]
+
+
+def test_gradient_with_prior_matches_finite_differences_of_the_cost():
+    """g = J^T W r - psc P (z - pm) is minus half the z-gradient of the cost
+    (Eq. loss plus the weak prior), prior terms included: checked against
+    central differences of the oracle's own cost, stage 2 in z = 2 (x - lo) /
+    (hi - lo) - 1 and stage 1 along its reduced directions (fraction k
+    against the largest fraction m, then alpha1 and T1), with the default
+    priors (T1 and mixture shape at precision 1, alpha at 1e-6) and with
+    every prior precision raised to 1e3 so that the prior dominates."""
+    t = synth.make_tables()
+    tr = synth.make_config1_truth(seed=31, width=24, height=1, fire_frac=1.0, alpha_range=(1e-2, 0.3))
+    L = oracle.synth_radiance(t, 1, tr.state1(), tr.wv_bin, None).astype(np.float32)
+    rng = np.random.default_rng(33)
+    for cfg in (oracle.Config(), oracle.Config(prior_prec_T1=1e3, prior_prec_mix=1e3, prior_prec_alpha=1e3)):
+        sc2 = 0.5 * (cfg.hi2 - cfg.lo2)
+        sc1 = 0.5 * (cfg.hi1 - cfg.lo1)
+        for j in range(8):
+            w = int(tr.wv_bin[j])
+            xs = rng.dirichlet(np.ones(3))
+            x2 = np.array([rng.uniform(950, 2100), rng.uniform(40, 400), rng.uniform(400, 950),
+                           rng.uniform(40, 400), rng.uniform(0.1, 0.9), 10 ** rng.uniform(-2.5, -0.5)])
+            x = np.concatenate([xs, x2])
+            _, g, _ = oracle.normal_equations(t, 2, L[j], w, x, cfg)
+            h = 1e-5
+            fd = np.empty(6)
+            for i in range(6):
+                xp, xm = x.copy(), x.copy()
+                xp[3 + i] += h * sc2[i]
+                xm[3 + i] -= h * sc2[i]
+                fd[i] = -0.5 * (_cost(t, 2, L[j], w, xp, cfg) - _cost(t, 2, L[j], w, xm, cfg)) / (2 * h)
+            assert np.max(np.abs(g - fd)) <= 1e-5 * np.max(np.abs(g)), (j, g, fd)
+            # stage 1: reduced basis (k != m against m), then alpha1, T1
+            x1 = np.concatenate([xs, [10 ** rng.uniform(-2.5, -0.5), rng.uniform(500, 2000)]])
+            _, g1, _ = oracle.normal_equations(t, 1, L[j], w, x1, cfg)
+            m = int(np.argmax(x1[:3]))
+            dirs = []
+            for k in range(3):
+                if k != m:
+                    d = np.zeros(5)
+                    d[k], d[m] = sc1[k], -sc1[m]
+                    dirs.append(d)
+            for k in (3, 4):
+                d = np.zeros(5)
+                d[k] = sc1[k]
+                dirs.append(d)
+            fd1 = np.array([-0.5 * (_cost(t, 1, L[j], w, x1 + h * d, cfg) -
+                                    _cost(t, 1, L[j], w, x1 - h * d, cfg)) / (2 * h) for d in dirs])
+            assert np.max(np.abs(g1 - fd1)) <= 1e-5 * np.max(np.abs(g1)), (j, g1, fd1)
+
+
+def test_fit_without_data_lands_on_the_prior_means():
+    """With every band weight ~0 (a per-band noise sd of 1e15: weights 1e-30)
+    the cost is the prior alone, so the fit must end on the prior means: T1
+    at the centre of its box, the mixture shape (mu_h, s_h, mu_s, s_s, eta)
+    at the centre of theirs, alpha1 and alpha at 0 (their prior mean z = -1).
+    A dropped prior term, a wrong sign or a wrong scale fails this."""
+    t = synth.make_tables()
+    tr = synth.make_config1_truth(seed=35, width=6, height=1, fire_frac=0.5)
+    L = oracle.synth_radiance(t, 1, tr.state1(), tr.wv_bin, None).astype(np.float32)
+    cfg = oracle.Config(noise_sd=np.full(t.n_bands, 1e15, np.float32))
+    o = oracle.retrieve(t, L, tr.wv_bin, cfg)
+    assert np.all((o["status"] & 7) == oracle.CONVERGED)
+    centre1 = 0.5 * (cfg.lo1[4] + cfg.hi1[4])
+    centre2 = 0.5 * (cfg.lo2 + cfg.hi2)
+    assert np.max(np.abs(o["state"][:, 4] - centre1)) < 1e-3            # T1
+    assert np.max(np.abs(o["state"][:, 3])) < 1e-6                      # alpha1
+    assert np.max(np.abs(o["state"][:, 5:10] - centre2[:5])) < 1e-3     # mixture shape
+    assert np.max(np.abs(o["state"][:, 10])) < 1e-6                     # alpha
