@@ -82,7 +82,10 @@ class Config_t(C.Structure):
                 ("gate_hfdi", C.c_int32), ("hfdi_thresh", C.c_double),
                 ("hfdi_lambda_hi", C.c_double), ("hfdi_lambda_lo", C.c_double),
                 ("ident_sd_et", C.c_double), ("ident_alpha_snr", C.c_double),
-                ("noise_sd", C.c_void_p)]
+                ("noise_sd", C.c_void_p),
+                ("solver", C.c_int32), ("adam_steps1", C.c_int32), ("adam_steps2", C.c_int32),
+                ("adam_lr1", C.c_double), ("adam_lr2", C.c_double), ("adam_clip", C.c_double),
+                ("adam_beta1", C.c_double), ("adam_beta2", C.c_double), ("adam_eps", C.c_double)]
 
 
 class Outputs_t(C.Structure):
@@ -134,6 +137,19 @@ class Config:
     ident_sd_et: float = 100.0
     ident_alpha_snr: float = 3.0
     noise_sd: np.ndarray = None      # per-band noise sd [n_bands]: weights 1 / sd^2
+    # solver: "lm" (damped Gauss-Newton, the default) or "adam", the paper's
+    # optimiser (Sec. 2.6, Eq. adam): 30 steps at lr 0.03 (stage 1), 100 at
+    # 0.015 (stage 2), beta (0.9, 0.999), eps 1e-8, global-norm clip (its
+    # value is garbled in the paper: 1.0 here), no prior
+    solver: str = "lm"
+    adam_steps1: int = 30
+    adam_steps2: int = 100
+    adam_lr1: float = 0.03
+    adam_lr2: float = 0.015
+    adam_clip: float = 1.0
+    adam_beta1: float = 0.9
+    adam_beta2: float = 0.999
+    adam_eps: float = 1e-8
     lo1: np.ndarray = None
     hi1: np.ndarray = None
     lo2: np.ndarray = None
@@ -187,6 +203,12 @@ class Config:
         c.gate_hfdi, c.hfdi_thresh = int(self.gate_hfdi), self.hfdi_thresh
         c.hfdi_lambda_hi, c.hfdi_lambda_lo = self.hfdi_lambdas
         c.ident_sd_et, c.ident_alpha_snr = self.ident_sd_et, self.ident_alpha_snr
+        if self.solver not in ("lm", "adam"):
+            raise ValueError(f"unknown solver {self.solver!r}")
+        c.solver = 1 if self.solver == "adam" else 0
+        c.adam_steps1, c.adam_steps2 = self.adam_steps1, self.adam_steps2
+        c.adam_lr1, c.adam_lr2, c.adam_clip = self.adam_lr1, self.adam_lr2, self.adam_clip
+        c.adam_beta1, c.adam_beta2, c.adam_eps = self.adam_beta1, self.adam_beta2, self.adam_eps
         if self.noise_sd is not None:
             # the C struct points into this array: keep it alive with the struct
             c._noise_sd = np.ascontiguousarray(self.noise_sd, dtype=np.float32)

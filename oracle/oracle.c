@@ -21,10 +21,11 @@
  *                                         sort-based, Duchi et al. 2008)
  *   stage 1 / stage 2 structure           Sec. 2.6
  *   HFDI gate                             Sec. 2.1
- * The optimiser is a damped Gauss-Newton (Levenberg-Marquardt) iteration in
- * place of the paper's Adam; its rules and constants are a stated reading
- * (Nielsen's damping update; active-set handling of bounds; simplex handled
- * in a reduced basis), identical in intent to the GPU path.
+ * Two optimisers: a damped Gauss-Newton (Levenberg-Marquardt) iteration,
+ * whose rules and constants are a stated reading (Nielsen's damping update;
+ * active-set handling of bounds; simplex handled in a reduced basis), and the
+ * paper's own Adam (Sec. 2.6, Eq. adam: fixed step counts and learning rates
+ * per stage, global-norm clip, z clip, simplex projection after each step).
  *
  * Parity unpinned: the per-pixel fit values themselves have no worked
  * example in the paper; the pieces are pinned by closed forms, brute force,
@@ -552,6 +553,66 @@ static int lm_fit(const pix_t *P, const lm_prob_t *q, const orc_config_t *c, dou
   return status;
 }
 
+/* ------------------------------------------------------------ Adam ---- */
+/* The paper's optimiser (Sec. 2.6, Eq. adam): a fixed number of Adam steps
+ * in the z coordinates of Eq. (affine) on Eq. (loss). At each step t =
+ * 1..steps:
+ *   g_t   = grad_z L(x(z_{t-1})) = -2 Jz^T W r  (no prior: Eq. loss as printed),
+ *   g_t  <- g_t min(1, clip / ||g_t||_2)         (global-norm clip),
+ *   m_t   = beta1 m_{t-1} + (1 - beta1) g_t,  v_t = beta2 v_{t-1} + (1 - beta2) g_t^2,
+ *   z_t   = z_{t-1} - lr mhat_t / (sqrt(vhat_t) + eps),
+ *           mhat_t = m_t / (1 - beta1^t), vhat_t = v_t / (1 - beta2^t),
+ * then z_t is clipped to [-1, 1] and the surface fractions (the simplex
+ * group) are projected onto the unit simplex. Every variable, the fractions
+ * included, moves on its own z coordinate. The result is the state after the
+ * last step; its cost, normal matrix and active set are formed there for the
+ * posterior, as after an LM fit. */
+static int adam_fit(const pix_t *P, const lm_prob_t *q, const orc_config_t *c, double *x,
+                    int steps, double lr, lm_res_t *res) {
+  int p = q->p, nb = P->nb;
+  double L[ORC_MAXB];
+  double *J = (double *)malloc(sizeof(double) * nb * p);
+  double H[ORC_NS1 * ORC_NS1], g[ORC_NS1], m[ORC_NS1], v[ORC_NS1], gz[ORC_NS1];
+  res->used64 = 0;
+  res->kappa = 0.0;
+  res->n_used = 0;
+  for (int b = 0; b < nb; b++) res->n_used += q->wst[b] > 0;
+  for (int i = 0; i < p; i++) m[i] = v[i] = 0.0;
+  evaluate(P, q, x, L, J);
+  for (int t = 1; t <= steps; t++) {
+    normal_eq(P, q, x, L, J, H, g);      /* g = Jz^T W r (the prior is off) */
+    double nrm = 0.0;
+    for (int i = 0; i < p; i++) {
+      gz[i] = -2.0 * g[i];
+      nrm += gz[i] * gz[i];
+    }
+    nrm = sqrt(nrm);
+    double f = nrm > c->adam_clip ? c->adam_clip / nrm : 1.0;
+    double bc1 = 1.0 - pow(c->adam_beta1, t), bc2 = 1.0 - pow(c->adam_beta2, t);
+    for (int i = 0; i < p; i++) {
+      if (!(q->hi[i] > q->lo[i])) continue;      /* a fixed variable does not move */
+      double gi = gz[i] * f;
+      m[i] = c->adam_beta1 * m[i] + (1.0 - c->adam_beta1) * gi;
+      v[i] = c->adam_beta2 * v[i] + (1.0 - c->adam_beta2) * gi * gi;
+      double z = zcoord(q, x, i) - lr * (m[i] / bc1) / (sqrt(v[i] / bc2) + c->adam_eps);
+      if (z < -1.0) z = -1.0;
+      if (z > 1.0) z = 1.0;
+      x[i] = q->lo[i] + 0.5 * (q->hi[i] - q->lo[i]) * (z + 1.0);
+    }
+    if (q->nsimp > 0) orc_simplex_project(x, q->nsimp);
+    evaluate(P, q, x, L, J);
+  }
+  normal_eq(P, q, x, L, J, H, g);
+  for (int i = 0; i < p; i++)
+    res->active[i] = (x[i] <= q->lo[i] && g[i] <= 0) || (x[i] >= q->hi[i] && g[i] >= 0);
+  memcpy(res->H, H, sizeof(double) * p * p);
+  res->iters = steps;
+  res->status = ORC_CONVERGED;
+  res->cost = cost_of(P, q, x, L);
+  free(J);
+  return ORC_CONVERGED;
+}
+
 /* ---------------------------------------------------------- HFDI ------ */
 static int nearest_band(const orc_tables_t *t, double lam) {
   int best = 0;
@@ -784,9 +845,13 @@ static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const d
     x1[K] = c->init_alpha1;
     x1[K + 1] = c->init_T1;
   }
-  lm_prob_t q1 = {1, K + 2, K, c->lo1, c->hi1, c->pm1, c->pp1, w1, c->max_it1, psc1};
+  /* the Adam solver minimises Eq. (loss) as printed: no prior term */
+  static const double no_prior[ORC_NS1] = {0};
+  const int adam = c->solver == ORC_SOLVER_ADAM;
+  lm_prob_t q1 = {1, K + 2, K, c->lo1, c->hi1, c->pm1, adam ? no_prior : c->pp1, w1, c->max_it1, psc1};
   lm_res_t r1;
-  lm_fit(P, &q1, c, x1, &r1);
+  if (adam) adam_fit(P, &q1, c, x1, c->adam_steps1, c->adam_lr1, &r1);
+  else lm_fit(P, &q1, c, x1, &r1);
   if (r1.status == ORC_MAXITER) status |= ORC_F_S1_MAXITER;
   if (r1.used64) status |= ORC_F_FP64;
   o->it1[i] = r1.iters;
@@ -818,9 +883,10 @@ static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const d
     if (x2[4] < lo2[4]) x2[4] = lo2[4];
     if (x2[4] > hi2[4]) x2[4] = hi2[4];
   }
-  lm_prob_t q2 = {2, 6, 0, lo2, hi2, c->pm2, c->pp2, w2, c->max_it2, psc2};
+  lm_prob_t q2 = {2, 6, 0, lo2, hi2, c->pm2, adam ? no_prior : c->pp2, w2, c->max_it2, psc2};
   lm_res_t r2;
-  lm_fit(P, &q2, c, x2, &r2);
+  if (adam) adam_fit(P, &q2, c, x2, c->adam_steps2, c->adam_lr2, &r2);
+  else lm_fit(P, &q2, c, x2, &r2);
   if (r2.used64) status |= ORC_F_FP64;
   status |= r2.status;
   o->it2[i] = r2.iters;
@@ -860,7 +926,9 @@ void orc_posterior_at(const orc_tables_t *t, const orc_config_t *c, const float 
   pixel_setup(P, t, c, Lrow, w1, w2, &n1, &n2, &psc1, &psc2);
   for (int b = 0; b < nb; b++) P->Ls[b] = solar_term(P, b, state, NULL);
   const double *x2 = state + K + 2;
-  lm_prob_t q2 = {2, 6, 0, c->lo2, c->hi2, c->pm2, c->pp2, w2, 0, psc2};
+  static const double no_prior[6] = {0};
+  const double *pp2 = c->solver == ORC_SOLVER_ADAM ? no_prior : c->pp2;   /* Adam: Eq. (loss) only */
+  lm_prob_t q2 = {2, 6, 0, c->lo2, c->hi2, c->pm2, pp2, w2, 0, psc2};
   double L[ORC_MAXB], H[36], g[6];
   double *J = (double *)malloc(sizeof(double) * nb * 6);
   evaluate(P, &q2, x2, L, J);
@@ -1022,8 +1090,10 @@ void orc_normal_equations(const orc_tables_t *t, const orc_config_t *c, int stag
     if (ws[b] > 0) { n++; sv += var; }
   }
   double psc = loss_weighted(c) ? 1.0 : sv / n;
-  lm_prob_t q1 = {1, K + 2, K, c->lo1, c->hi1, c->pm1, c->pp1, ws, 0, psc};
-  lm_prob_t q2 = {2, 6, 0, c->lo2, c->hi2, c->pm2, c->pp2, ws, 0, psc};
+  static const double no_prior[ORC_NS1] = {0};
+  const int adam = c->solver == ORC_SOLVER_ADAM;   /* Adam: Eq. (loss) only */
+  lm_prob_t q1 = {1, K + 2, K, c->lo1, c->hi1, c->pm1, adam ? no_prior : c->pp1, ws, 0, psc};
+  lm_prob_t q2 = {2, 6, 0, c->lo2, c->hi2, c->pm2, adam ? no_prior : c->pp2, ws, 0, psc};
   const lm_prob_t *q = stage == 1 ? &q1 : &q2;
   const double *xx = stage == 1 ? x : x + K;
   if (stage == 2)

@@ -55,7 +55,14 @@ typedef struct {
   double ident_sd_et, ident_alpha_snr;
   const float *noise_sd;              /* [n_bands] per-band noise sd, or NULL; when given
                                          the loss is weighted by 1 / sd_b^2 */
+  int32_t solver;                     /* ORC_SOLVER_LM or ORC_SOLVER_ADAM */
+  int32_t adam_steps1, adam_steps2;   /* Adam steps per stage (Sec. 2.6: 30, 100) */
+  double adam_lr1, adam_lr2;          /* learning rates (Sec. 2.6: 0.03, 0.015) */
+  double adam_clip;                   /* global-norm gradient clip */
+  double adam_beta1, adam_beta2, adam_eps;   /* Eq. (adam): 0.9, 0.999, 1e-8 */
 } orc_config_t;
+
+enum { ORC_SOLVER_LM = 0, ORC_SOLVER_ADAM = 1 };
 
 typedef struct {
   double *state;     /* [n][K+8] = [x_surf, a1, T1, mu_h, s_h, mu_s, s_s, eta, a] */
