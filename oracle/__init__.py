@@ -85,7 +85,8 @@ class Config_t(C.Structure):
                 ("noise_sd", C.c_void_p),
                 ("solver", C.c_int32), ("adam_steps1", C.c_int32), ("adam_steps2", C.c_int32),
                 ("adam_lr1", C.c_double), ("adam_lr2", C.c_double), ("adam_clip", C.c_double),
-                ("adam_beta1", C.c_double), ("adam_beta2", C.c_double), ("adam_eps", C.c_double)]
+                ("adam_beta1", C.c_double), ("adam_beta2", C.c_double), ("adam_eps", C.c_double),
+                ("adam_gnoise", C.c_double), ("adam_gseed", C.c_uint64)]
 
 
 class Outputs_t(C.Structure):
@@ -150,6 +151,11 @@ class Config:
     adam_beta1: float = 0.9
     adam_beta2: float = 0.999
     adam_eps: float = 1e-8
+    # sensitivity probe for tests (not part of the method): each Adam
+    # gradient formed as if every band's model value were off by a relative
+    # adam_gnoise times a seeded standard normal (0 = off)
+    adam_gnoise: float = 0.0
+    adam_gseed: int = 0
     lo1: np.ndarray = None
     hi1: np.ndarray = None
     lo2: np.ndarray = None
@@ -209,6 +215,7 @@ class Config:
         c.adam_steps1, c.adam_steps2 = self.adam_steps1, self.adam_steps2
         c.adam_lr1, c.adam_lr2, c.adam_clip = self.adam_lr1, self.adam_lr2, self.adam_clip
         c.adam_beta1, c.adam_beta2, c.adam_eps = self.adam_beta1, self.adam_beta2, self.adam_eps
+        c.adam_gnoise, c.adam_gseed = self.adam_gnoise, self.adam_gseed
         if self.noise_sd is not None:
             # the C struct points into this array: keep it alive with the struct
             c._noise_sd = np.ascontiguousarray(self.noise_sd, dtype=np.float32)

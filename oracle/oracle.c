@@ -272,6 +272,7 @@ typedef struct {
   int max_it;
   double psc;                /* prior scale: mean noise variance of the used bands
                                 (unweighted loss) or 1 (noise-weighted loss) */
+  int64_t pix;               /* pixel index (keys the Adam sensitivity probe) */
 } lm_prob_t;
 
 typedef struct {
@@ -567,6 +568,35 @@ static int lm_fit(const pix_t *P, const lm_prob_t *q, const orc_config_t *c, dou
  * included, moves on its own z coordinate. The result is the state after the
  * last step; its cost, normal matrix and active set are formed there for the
  * posterior, as after an LM fit. */
+/* SplitMix64 (Steele, Lea and Flood 2014) and a Box-Muller normal from two
+ * of its outputs: the counter-based draws of the Adam sensitivity probe. */
+static uint64_t splitmix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+static double probe_normal(uint64_t seed, int64_t pix, int stage, int step, int i) {
+  uint64_t k = splitmix64(seed ^ splitmix64((uint64_t)pix * 4096u + (uint64_t)stage * 1024u + (uint64_t)i));
+  uint64_t a = splitmix64(k + 2u * (uint64_t)step), b = splitmix64(k + 2u * (uint64_t)step + 1u);
+  double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740993.0), u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+  return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+/* The probe's perturbation of the Adam gradient: each band's model value
+ * M_b moved by a relative adam_gnoise times a standard normal (fresh per
+ * pixel, stage, step and band), i.e. g_i -= adam_gnoise sum_b w_b Jz_bi M_b n_b,
+ * the size of the rounding of an FP32 evaluation of the model. */
+static void probe_gradient(const pix_t *P, const lm_prob_t *q, const orc_config_t *c,
+                           const double *L, const double *J, int step, double *g) {
+  int p = q->p;
+  for (int b = 0; b < P->nb; b++) {
+    if (!(q->wst[b] > 0)) continue;
+    double d = c->adam_gnoise * L[b] * probe_normal(c->adam_gseed, q->pix, q->stage, step, b);
+    for (int i = 0; i < p; i++) g[i] -= q->wst[b] * J[b * p + i] * 0.5 * (q->hi[i] - q->lo[i]) * d;
+  }
+}
+
 static int adam_fit(const pix_t *P, const lm_prob_t *q, const orc_config_t *c, double *x,
                     int steps, double lr, lm_res_t *res) {
   int p = q->p, nb = P->nb;
@@ -581,6 +611,7 @@ static int adam_fit(const pix_t *P, const lm_prob_t *q, const orc_config_t *c, d
   evaluate(P, q, x, L, J);
   for (int t = 1; t <= steps; t++) {
     normal_eq(P, q, x, L, J, H, g);      /* g = Jz^T W r (the prior is off) */
+    if (c->adam_gnoise > 0.0) probe_gradient(P, q, c, L, J, t, g);   /* tests only; off by default */
     double nrm = 0.0;
     for (int i = 0; i < p; i++) {
       gz[i] = -2.0 * g[i];
@@ -848,7 +879,7 @@ static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const d
   /* the Adam solver minimises Eq. (loss) as printed: no prior term */
   static const double no_prior[ORC_NS1] = {0};
   const int adam = c->solver == ORC_SOLVER_ADAM;
-  lm_prob_t q1 = {1, K + 2, K, c->lo1, c->hi1, c->pm1, adam ? no_prior : c->pp1, w1, c->max_it1, psc1};
+  lm_prob_t q1 = {1, K + 2, K, c->lo1, c->hi1, c->pm1, adam ? no_prior : c->pp1, w1, c->max_it1, psc1, i};
   lm_res_t r1;
   if (adam) adam_fit(P, &q1, c, x1, c->adam_steps1, c->adam_lr1, &r1);
   else lm_fit(P, &q1, c, x1, &r1);
@@ -883,7 +914,7 @@ static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const d
     if (x2[4] < lo2[4]) x2[4] = lo2[4];
     if (x2[4] > hi2[4]) x2[4] = hi2[4];
   }
-  lm_prob_t q2 = {2, 6, 0, lo2, hi2, c->pm2, adam ? no_prior : c->pp2, w2, c->max_it2, psc2};
+  lm_prob_t q2 = {2, 6, 0, lo2, hi2, c->pm2, adam ? no_prior : c->pp2, w2, c->max_it2, psc2, i};
   lm_res_t r2;
   if (adam) adam_fit(P, &q2, c, x2, c->adam_steps2, c->adam_lr2, &r2);
   else lm_fit(P, &q2, c, x2, &r2);

@@ -60,6 +60,13 @@ typedef struct {
   double adam_lr1, adam_lr2;          /* learning rates (Sec. 2.6: 0.03, 0.015) */
   double adam_clip;                   /* global-norm gradient clip */
   double adam_beta1, adam_beta2, adam_eps;   /* Eq. (adam): 0.9, 0.999, 1e-8 */
+  /* Sensitivity probe for tests, not part of the method (0 = off): at each
+   * Adam step the gradient is formed as if every band's model value were
+   * off by a relative adam_gnoise times a standard normal drawn from
+   * SplitMix64 keyed by (adam_gseed, pixel, stage, step, band): the size of
+   * the rounding of a single-precision evaluation of the model. */
+  double adam_gnoise;
+  uint64_t adam_gseed;
 } orc_config_t;
 
 enum { ORC_SOLVER_LM = 0, ORC_SOLVER_ADAM = 1 };

@@ -205,3 +205,25 @@ def test_adam_ignores_the_prior(scene):
                                           prior_prec_mix=50.0, prior_prec_alpha=50.0))
     for k in ("state", "ET", "cost", "var_ET"):
         assert np.array_equal(a[k], b[k], equal_nan=True), k
+
+
+def test_rounding_probe_is_seeded_and_off_by_default(scene):
+    """The sensitivity probe used by the GPU tests: off at 0, deterministic
+    for a seed, different for another seed, and small (a relative 1e-5 of
+    the model values moves the first stage-1 step of alpha1 and T1 by less
+    than lr / 100 in z)."""
+    t, tr, L = scene
+    base = oracle.retrieve(t, L[:6], tr.wv_bin[:6], cfg=oracle.Config(n_endm=K, solver="adam"))
+    off = oracle.retrieve(t, L[:6], tr.wv_bin[:6], cfg=oracle.Config(n_endm=K, solver="adam", adam_gnoise=0.0,
+                                                                     adam_gseed=7))
+    assert np.array_equal(base["state"], off["state"])
+    p1 = [oracle.retrieve(t, L[:6], tr.wv_bin[:6], cfg=oracle.Config(
+        n_endm=K, solver="adam", adam_gnoise=1e-5, adam_gseed=s)) for s in (1, 1, 2)]
+    assert np.array_equal(p1[0]["state"], p1[1]["state"])
+    assert not np.array_equal(p1[0]["state"], p1[2]["state"])
+    one = dict(n_endm=K, solver="adam", adam_steps1=1, adam_steps2=0)
+    a = oracle.retrieve(t, L[:6], tr.wv_bin[:6], cfg=oracle.Config(**one))
+    b = oracle.retrieve(t, L[:6], tr.wv_bin[:6], cfg=oracle.Config(**one, adam_gnoise=1e-5, adam_gseed=3))
+    lo, hi = _bounds(oracle.Config(n_endm=K), 1)
+    dz = 2 * np.abs(a["state"][:, :K + 2] - b["state"][:, :K + 2]) / (hi - lo)
+    assert np.all(dz[:, K:] < oracle.Config().adam_lr1 / 100)
