@@ -113,7 +113,28 @@ typedef struct {
                                        staging, tensor-core product) before it gives
                                        up and the call reports FIRE_ERR_TIMEOUT;
                                        0 = the default 2^26 */
+  int32_t solver;                   /* FIRE_SOLVER_LM (default) or FIRE_SOLVER_ADAM */
+  int32_t adam_steps1, adam_steps2; /* Adam steps per stage (Sec. 2.6: 30, 100) */
+  double adam_lr1, adam_lr2;        /* Adam learning rates (Sec. 2.6: 0.03, 0.015) */
+  double adam_clip;                 /* global-norm clip of the z gradient (1.0; the
+                                       paper's value is not legible) */
+  double adam_beta1, adam_beta2, adam_eps;  /* Eq. (adam): 0.9, 0.999, 1e-8 (double, so
+                                       that 1 - beta is exact) */
 } fire_config_t;
+
+/* Solvers. FIRE_SOLVER_LM: damped Gauss-Newton with the convergence tests
+ * and caps above, Eq. (loss) plus the weak prior of fire_priors_t.
+ * FIRE_SOLVER_ADAM: the paper's optimiser (Sec. 2.6, Eq. adam): a fixed
+ * adam_steps1 / adam_steps2 Adam steps per stage on Eq. (loss) as printed
+ * (the prior precisions are ignored), every variable on its own z
+ * coordinate of Eq. (affine), the gradient clipped to a global norm of
+ * adam_clip, z clipped to [-1, 1] and the surface fractions projected onto
+ * the unit simplex after each step; the result is the state after the last
+ * step (status CONVERGED, iterations = the step counts), its posterior formed
+ * there as after an LM fit. The launch shape's stage-1 lane count is 16
+ * under Adam; stage 2 runs on the tensor cores (shapes 6-8) or in FP32. */
+#define FIRE_SOLVER_LM 0
+#define FIRE_SOLVER_ADAM 1
 
 /* Priors: bounds of Eq. (affine), a weak diagonal Gaussian prior in z
  * (precision counted in units of one band's noise variance), the start rule.

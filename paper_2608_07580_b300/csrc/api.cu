@@ -54,6 +54,9 @@ int nearest_band(const float *wl, int nb, float lam) {
   return best;
 }
 
+static_assert(kSolverLM == FIRE_SOLVER_LM && kSolverAdam == FIRE_SOLVER_ADAM,
+              "kernel solver codes follow the public ones");
+
 void fill_kconfig(KConfig &k, const fire_config_t &c, const fire_priors_t &p, int K, int nb) {
   memset(&k, 0, sizeof(k));
   for (int i = 0; i < K + 2; i++) {
@@ -95,6 +98,24 @@ void fill_kconfig(KConfig &k, const fire_config_t &c, const fire_priors_t &p, in
   k.has_nsd = p.noise_sd ? 1 : 0;
   if (p.noise_sd)
     for (int b = 0; b < nb && b < kMaxBands; b++) k.nsd[b] = p.noise_sd[b];
+  k.solver = c.solver;
+  k.adam_steps1 = c.adam_steps1;
+  k.adam_steps2 = c.adam_steps2;
+  k.adam_lr1 = (float)c.adam_lr1;
+  k.adam_lr2 = (float)c.adam_lr2;
+  k.adam_clip = (float)c.adam_clip;
+  k.adam_eps = (float)c.adam_eps;
+  k.adam_b1 = (float)c.adam_beta1;
+  k.adam_b2 = (float)c.adam_beta2;
+  k.adam_omb1 = (float)(1.0 - c.adam_beta1);   // 1 - 0.999f would be off by 1.3e-5
+  k.adam_omb2 = (float)(1.0 - c.adam_beta2);
+  k.adam_b1d = c.adam_beta1;
+  k.adam_b2d = c.adam_beta2;
+  if (c.solver == FIRE_SOLVER_ADAM) {
+    // the paper's Adam minimises Eq. (loss) as printed: no prior term
+    for (int i = 0; i < kMaxK + 2; i++) k.pp1[i] = 0.f;
+    for (int i = 0; i < 6; i++) k.pp2[i] = 0.f;
+  }
 }
 
 
@@ -324,6 +345,15 @@ void fire_default_config(fire_config_t *c) {
   c->hfdi_lambda_lo = 2061.f;
   c->ident_sd_et = 100.f;
   c->ident_alpha_snr = 3.f;
+  c->solver = FIRE_SOLVER_LM;
+  c->adam_steps1 = 30;      // Sec. 2.6: 30 steps at 0.03, then 100 at 0.015
+  c->adam_steps2 = 100;
+  c->adam_lr1 = 0.03;
+  c->adam_lr2 = 0.015;
+  c->adam_clip = 1.0;
+  c->adam_beta1 = 0.9;      // Eq. (adam) defaults
+  c->adam_beta2 = 0.999;
+  c->adam_eps = 1e-8;
 }
 
 void fire_default_priors(fire_priors_t *p, int32_t K, int32_t nt, float tlo, float thi) {
@@ -424,6 +454,13 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
     return FIRE_ERR_ARG;
   for (int b = 1; b < nb; b++)
     if (!(tb->wavelength_nm[b] > tb->wavelength_nm[b - 1])) return FIRE_ERR_ARG;
+  if (cfg && (cfg->solver < FIRE_SOLVER_LM || cfg->solver > FIRE_SOLVER_ADAM ||
+              (cfg->solver == FIRE_SOLVER_ADAM &&
+               (cfg->adam_steps1 < 0 || cfg->adam_steps2 < 0 || cfg->adam_steps1 > 65535 ||
+                cfg->adam_steps2 > 65535 || !(cfg->adam_lr1 >= 0.0) || !(cfg->adam_lr2 >= 0.0) ||
+                !(cfg->adam_clip > 0.0) || !(cfg->adam_beta1 >= 0.0 && cfg->adam_beta1 < 1.0) ||
+                !(cfg->adam_beta2 >= 0.0 && cfg->adam_beta2 < 1.0) || !(cfg->adam_eps > 0.0)))))
+    return FIRE_ERR_ARG;
   fire_ctx *c = new (std::nothrow) fire_ctx();
   if (!c) return FIRE_ERR_NOMEM;
   if (cfg) c->cfg = *cfg;

@@ -51,6 +51,9 @@ struct KTables {
   const double *planck64;    // [nt][n2] B(lambda_b, T_j) in FP64 over the stage-2 bands (posterior)
 };
 
+// KConfig::solver values (the public FIRE_SOLVER_LM / FIRE_SOLVER_ADAM)
+constexpr int kSolverLM = 0, kSolverAdam = 1;
+
 struct KConfig {
   float lo1[kMaxK + 2], hi1[kMaxK + 2], pm1[kMaxK + 2], pp1[kMaxK + 2];
   float lo2[6], hi2[6], pm2[6], pp2[6];
@@ -65,6 +68,11 @@ struct KConfig {
   float ident_sd_et, ident_alpha_snr;
   long long wait_spins;     // polls of a bounded wait before it gives up
   int has_nsd;              // 1: the caller's per-band noise sd weight the loss
+  int solver;               // kSolverLM / kSolverAdam
+  int adam_steps1, adam_steps2;
+  float adam_lr1, adam_lr2, adam_clip, adam_eps;
+  float adam_b1, adam_b2, adam_omb1, adam_omb2;   // beta and 1 - beta, each rounded once
+  double adam_b1d, adam_b2d;                      // beta for the bias corrections 1 - beta^t
   float nsd[kMaxBands];     // noise_sd_b (weights 1 / noise_sd_b^2)
 };
 

@@ -391,6 +391,90 @@ __device__ __forceinline__ void damping_update(LMIter<P> &L, bool accept, float 
   }
 }
 
+// ------------------------------------------------------------ Adam -----
+// The paper's optimiser (Sec. 2.6, Eq. adam), the FIRE_SOLVER_ADAM path of
+// the stage kernels: a fixed number of steps, each on every variable's own z
+// coordinate of Eq. (affine). Its moments live in registers of the Adam
+// instantiations only.
+template <int NX>
+struct AdamState {
+  float m[NX], v[NX];
+  __device__ __forceinline__ void reset() {
+#pragma unroll
+    for (int i = 0; i < NX; i++) m[i] = v[i] = 0.f;
+  }
+};
+
+// One Adam step t (1-based) from x, given G = Jz^T W r of every coordinate
+// (the z gradient of Eq. loss is -2 G): the gradient clipped to a global norm
+// of adam_clip, the moment updates, the bias-corrected step
+// lr mhat / (sqrt(vhat) + eps), z clipped to [-1, 1]. A fixed variable
+// (zk = 0) keeps its value.
+template <int NX>
+__device__ __forceinline__ void adam_step(const KConfig &c, int t, float lr, const float *lo,
+                                          const float *hi, const float *zk, const float (&x)[NX],
+                                          const float (&G)[NX], AdamState<NX> &A, float (&xt)[NX]) {
+  float gz[NX], n2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < NX; i++) {
+    gz[i] = zk[i] > 0.f ? -2.f * G[i] : 0.f;
+    n2 = fmaf(gz[i], gz[i], n2);
+  }
+  const float nrm = sqrtf(n2);
+  const float f = nrm > c.adam_clip ? c.adam_clip / nrm : 1.f;
+  // bias corrections 1 - beta^t in FP64 (once per step): in FP32, 1 - 0.999^t
+  // would lose its leading digits to cancellation for small t
+  const float bc1 = (float)(1.0 - pow(c.adam_b1d, (double)t));
+  const float bc2 = (float)(1.0 - pow(c.adam_b2d, (double)t));
+#pragma unroll
+  for (int i = 0; i < NX; i++) {
+    if (!(zk[i] > 0.f)) { xt[i] = x[i]; continue; }
+    const float gi = gz[i] * f;
+    A.m[i] = fmaf(c.adam_b1, A.m[i], c.adam_omb1 * gi);
+    A.v[i] = fmaf(c.adam_b2, A.v[i], c.adam_omb2 * gi * gi);
+    float z = fmaf(x[i] - lo[i], zk[i], -1.f);
+    z -= lr * (A.m[i] / bc1) / (sqrtf(A.v[i] / bc2) + c.adam_eps);
+    z = fminf(fmaxf(z, -1.f), 1.f);
+    xt[i] = fmaf(0.5f * (hi[i] - lo[i]), z + 1.f, lo[i]);
+  }
+}
+
+// The next Adam trial point of stage 1 (false once adam_steps1 steps are
+// taken): the full-coordinate gradient from the reduced one (pivot m) and
+// the pivot's own sum gm, the step, then the simplex projection of the
+// fractions (Sec. 2.6).
+template <int K, class St>
+__device__ __forceinline__ bool adam_next1(const KConfig &c, const float (&x)[K + 2],
+                                           const float (&g)[K + 1], float gm, int m,
+                                           AdamState<K + 2> &A, LMIter<K + 1> &L,
+                                           float (&xt)[K + 2]) {
+  if (L.it >= c.adam_steps1) { L.status = PX_CONVERGED; return false; }
+  float Gf[K + 2];
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    float gr = 0.f;
+#pragma unroll
+    for (int a = 0; a < K - 1; a++)
+      if (a == (k < m ? k : k - 1)) gr = g[a];
+    Gf[k] = k == m ? gm : gr + gm;
+  }
+  Gf[K] = g[K - 1];
+  Gf[K + 1] = g[K];
+  adam_step<K + 2>(c, L.it + 1, c.adam_lr1, c.lo1, c.hi1, c.zk1, x, Gf, A, xt);
+  St::simplex_project(xt);
+  L.it++;
+  return true;
+}
+
+// The next Adam trial point of stage 2 (false once adam_steps2 steps are taken)
+__device__ __forceinline__ bool adam_next2(const KConfig &c, const float (&x)[6], const float (&g)[6],
+                                           AdamState<6> &A, LMIter<6> &L, float (&xt)[6]) {
+  if (L.it >= c.adam_steps2) { L.status = PX_CONVERGED; return false; }
+  adam_step<6>(c, L.it + 1, c.adam_lr2, c.lo2, c.hi2, c.zk2, x, g, A, xt);
+  L.it++;
+  return true;
+}
+
 // ------------------------------------------------------- pixel groups ---
 // G consecutive lanes of a warp fit one pixel, so a warp carries 32 / G
 // pixels. Reductions are xor shuffles restricted to the group's lanes, so a
@@ -527,10 +611,17 @@ struct Stage1 {
   // each increment formed from the exact parameter differences; B_o and
   // 1 / (1 - S_b rho_o) are recomputed at xo with the instructions that
   // formed them when xo was evaluated.
+  //
+  // With GM (the Adam solver, which moves every fraction on its own z
+  // coordinate) it also returns gm = sum_b w_b r_b dL_b/dz_m of the pivot
+  // fraction m, from which the full-coordinate gradient follows:
+  // G_k = g_(k) + gm for k != m, G_m = gm.
+  template <bool GM = false>
   __device__ __forceinline__ void eval(const PixCtx &pc, const Grp<G> &gp, const float (&x)[NX],
                                        int rn, float (&H)[NH], float (&g)[P], float (&gf)[P],
                                        float &cst, float &cd, float &drop, int &m,
-                                       const float (&xo)[NX], bool inc) const {
+                                       const float (&xo)[NX], bool inc, float *gm = nullptr) const {
+    constexpr int NA = NH + P + 5 + (GM ? 1 : 0);
     const KTables &t = *pc.t;
     const KConfig &c = *pc.c;
     m = argmax_frac(x);
@@ -539,9 +630,9 @@ struct Stage1 {
     // round-to-nearest operations per instruction); the pair's two partial
     // sums are added at the end. A masked band of a pair (weight 0) adds
     // exact zeros.
-    float2 sm[NH + P + 5];
+    float2 sm[NA];
 #pragma unroll
-    for (int i = 0; i < NH + P + 5; i++) sm[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < NA; i++) sm[i] = make_float2(0.f, 0.f);
     const float a1 = x[K], invT = 1.f / x[K + 1], invTo = 1.f / xo[K + 1];
     const float dTT = (x[K + 1] - xo[K + 1]) * invT / xo[K + 1];
     const float dal = a1 - xo[K];
@@ -635,6 +726,7 @@ struct Stage1 {
       sm[NH + P + 1] = __ffma2_rn(r, r, sm[NH + P + 1]);
       sm[NH + P + 3] = __ffma2_rn(wM, wM, sm[NH + P + 3]);
       sm[NH + P + 4] = __fadd2_rn(sm[NH + P + 4], wv);
+      if constexpr (GM) sm[NA - 1] = __ffma2_rn(wr, dEm, sm[NA - 1]);
 #pragma unroll
       for (int a = 0; a < P; a++) {
         sm[NH + a] = __ffma2_rn(J[a], wr, sm[NH + a]);
@@ -643,10 +735,11 @@ struct Stage1 {
         for (int bb_ = a; bb_ < P; bb_++) sm[up<P>(a, bb_)] = __ffma2_rn(wj, J[bb_], sm[up<P>(a, bb_)]);
       }
     }
-    float acc[NH + P + 5];
+    float acc[NA];
 #pragma unroll
-    for (int i = 0; i < NH + P + 5; i++) acc[i] = sm[i].x + sm[i].y;
+    for (int i = 0; i < NA; i++) acc[i] = sm[i].x + sm[i].y;
     gp.sum(acc);
+    if constexpr (GM) *gm = acc[NA - 1];
 #pragma unroll
     for (int i = 0; i < NH; i++) H[i] = acc[i];
     // FP32 floor of g_a: kFloorC sqrt(sum_b (w_b J_ba M_b)^2), estimated as
@@ -1346,7 +1439,7 @@ __device__ __forceinline__ float pick(const float (&v)[N], int k) {
 // its groups have run out of pixels.
 
 // ---- stage 1: checks, HFDI gate, stage-1 fit -> scratch
-template <int K, int G, int MAXW>
+template <int K, int G, int MAXW, bool ADAM = false>
 __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_constant__ LMLaunch p) {
   constexpr int P = K + 1, NX = K + 2, NH = P * (P + 1) / 2;
   extern __shared__ __align__(128) float smem[];
@@ -1379,9 +1472,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
   long long next = 0, end = 0, pix = 0, opix = 0;
   uint16_t *iters_out = nullptr;
   bool active = false, done = false, first = false;
-  float x[NX], xt[NX], H[NH], g[P], gf[P], cst = 0.f;
+  float x[NX], xt[NX], H[NH], g[P], gf[P], cst = 0.f, gm = 0.f;
   int m = 0, rc = 0, nfull = 0, status = 0;
   LMIter<P> L;
+  AdamState<NX> A;
   for (;;) {
     // ---- take pixels until one is to be fitted
     while (!active && !done) {
@@ -1437,6 +1531,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
         L = LMIter<P>();
 #pragma unroll
         for (int a = 0; a < P; a++) L.act[a] = false;
+        if constexpr (ADAM) A.reset();
         first = true;
         rc = 0;
         nfull = 0;
@@ -1472,17 +1567,20 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
     // ---- one LM step of this group's pixel: the step, then (with every
     // lane of the warp reconverged) the evaluation
     bool go = false;
-    if (active) go = first || next_trial(S, gp, c, x, H, g, gf, m, cst, c.max_it1, L, xt);
+    if (active) {
+      if constexpr (ADAM) go = first || adam_next1<K, Stage1<K, G>>(c, x, g, gm, m, A, L, xt);
+      else go = first || next_trial(S, gp, c, x, H, g, gf, m, cst, c.max_it1, L, xt);
+    }
     __syncwarp();
     if (go) {
-      float Ht[NH], gt[P], gft[P], ct, cdt, drop;
+      float Ht[NH], gt[P], gft[P], ct, cdt, drop, gmt = 0.f;
       int mt;
       // small steps: decrease in increment form (FP32 resolution)
-      const bool inc = !first && L.pred < kIncBelow * cst;
-      S.eval(pc, gp, xt, rc ^ 1, Ht, gt, gft, ct, cdt, drop, mt, x, inc);
+      const bool inc = !ADAM && !first && L.pred < kIncBelow * cst;
+      S.template eval<ADAM>(pc, gp, xt, rc ^ 1, Ht, gt, gft, ct, cdt, drop, mt, x, inc, &gmt);
       nfull++;
-      bool accept = first;
-      if (!first) {
+      bool accept = first || ADAM;   // an Adam step is always taken
+      if (!first && !ADAM) {
         drop += S.prior_drop(c, x, xt);
         const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
         accept = rho > 0.f;
@@ -1501,6 +1599,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
         }
         cst = ct;
         m = mt;
+        gm = gmt;
         rc ^= 1;
       }
       first = false;
@@ -1528,7 +1627,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
 }
 
 // ---- stage 2: mixture fit from the stage-1 hand-over -> finalize scratch
-template <int K, int G, int MAXW>
+template <int K, int G, int MAXW, bool ADAM = false>
 __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_constant__ LMLaunch p) {
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) unsigned long long bar;
@@ -1559,6 +1658,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
   float *ne = S.bb + 5 * S.nbs;   // trial H, g, gradient floor
   int rc = 0, nfull = 0, status = 0, n2u = 0;
   LMIter<6> L;
+  AdamState<6> A;
   for (;;) {
     while (!active && !done) {
       if (next >= end) {
@@ -1601,6 +1701,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       L = LMIter<6>();
 #pragma unroll
       for (int a = 0; a < 6; a++) L.act[a] = false;
+      if constexpr (ADAM) A.reset();
       first = true;
       rc = 0;
       nfull = 0;
@@ -1608,14 +1709,17 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
     }
     if (__all_sync(kFull, done)) break;
     bool go = active;
-    if (active && !first) go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
+    if (active && !first) {
+      if constexpr (ADAM) go = adam_next2(c, x, g, A, L, xt);
+      else go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
+    }
     __syncwarp();
     if (go) {
       float ct, cdt, drop;
       S.eval(pc, gp, x, xt, rc ^ 1, ne, ct, cdt, drop);
       nfull++;
-      bool accept = first;
-      if (!first) {
+      bool accept = first || ADAM;   // an Adam step is always taken
+      if (!first && !ADAM) {
         drop += S.prior_drop(c, x, xt);
         const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
         accept = rho > 0.f;
@@ -2156,7 +2260,7 @@ __global__ void planck_operand_kernel(const KTables t, const float *image, unsig
 // lm_stage2_kernel (16 lanes per pixel, 8 warps), with the evaluation a
 // round of each 4-warp cohort (tcs2) so that a cohort's 8 pixels share one
 // product
-template <int K>
+template <int K, bool ADAM = false>
 __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_constant__ LMLaunch p) {
   constexpr int G = tcs2::G;
   extern __shared__ __align__(128) float smem[];
@@ -2193,6 +2297,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
   int rc = 0, nfull = 0, status = 0, n2u = 0;
   unsigned phase = 0;
   LMIter<6> L;
+  AdamState<6> A;
   // claim ahead: while a pixel is fitted, the group's first lane takes the
   // group's next claim (its result is first read a round later), and the
   // round after that the claimed pixels' inputs are prefetched into L2, so
@@ -2245,6 +2350,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       L = LMIter<6>();
 #pragma unroll
       for (int a = 0; a < 6; a++) L.act[a] = false;
+      if constexpr (ADAM) A.reset();
       first = true;
       rc = 0;
       nfull = 0;
@@ -2276,7 +2382,10 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
     }
     if (tcs2::co_and(hc, done)) break;
     bool go = active;
-    if (active && !first) go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
+    if (active && !first) {
+      if constexpr (ADAM) go = adam_next2(c, x, g, A, L, xt);
+      else go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
+    }
     if (go) tcs2::coef(t, c, gp, x, xt, co, slot, prm, rc ^ 1);
     if (gp.sub == 0) prm[0] = go ? 1.f : 0.f;
     if (!tcs2::round(t, C, hc, &mbar[hc], phase, c.wait_spins)) { ok = false; break; }
@@ -2285,8 +2394,8 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       float ct, cdt, drop;
       tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, xt, S.psc, ne, ct, cdt, drop);
       nfull++;
-      bool accept = first;
-      if (!first) {
+      bool accept = first || ADAM;   // an Adam step is always taken
+      if (!first && !ADAM) {
         drop += S.prior_drop(c, x, xt);
         const float rho = L.pred > 0.f ? drop / L.pred : -1.f;
         accept = rho > 0.f;
@@ -2915,6 +3024,11 @@ cudaError_t launch_persistent(Kern kern, const LMLaunch &p, int num_sms, cudaStr
 
 template <int K>
 cudaError_t launch_stage1(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu, int v) {
+  if (p.c.solver == kSolverAdam) {
+    // the Adam solver runs on the 16-lane shape
+    const Shape s = kShape1[0];
+    return launch_persistent(lm_stage1_kernel<K, 16, 12, true>, p, num_sms, st, bu, 1, s.G, s.maxw);
+  }
   const Shape s = kShape1[v];
   switch (v) {
     case 1: return launch_persistent(lm_stage1_kernel<K, 8, 12>, p, num_sms, st, bu, 1, s.G, s.maxw);
@@ -2923,10 +3037,10 @@ cudaError_t launch_stage1(const LMLaunch &p, int num_sms, cudaStream_t st, int *
   }
 }
 
-template <int K>
+template <int K, bool ADAM>
 cudaError_t launch_stage2_tc(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu) {
   const size_t smem = (size_t)tcs2::layout(p.t).total;
-  cudaError_t e = cudaFuncSetAttribute(lm_stage2_tc_kernel<K>,
+  cudaError_t e = cudaFuncSetAttribute(lm_stage2_tc_kernel<K, ADAM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int cl = p.s.claim > 0 ? p.s.claim : kClaim;
@@ -2934,16 +3048,24 @@ cudaError_t launch_stage2_tc(const LMLaunch &p, int num_sms, cudaStream_t st, in
   long long blocks = (p.s.n_pix + per_cta - 1) / per_cta;
   if (blocks > num_sms) blocks = num_sms;
   if (blocks < 1) blocks = 1;
-  lm_stage2_tc_kernel<K><<<(int)blocks, tcs2::kWarps * 32, smem, st>>>(p);
+  lm_stage2_tc_kernel<K, ADAM><<<(int)blocks, tcs2::kWarps * 32, smem, st>>>(p);
   if (bu) *bu += (int)blocks;
   return cudaGetLastError();
 }
 
 template <int K>
 cudaError_t launch_stage2(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu, int v) {
+  const bool adam = p.c.solver == kSolverAdam;
   if (v == 2) {
-    if (lm_tc_ok(p.t)) return launch_stage2_tc<K>(p, num_sms, st, bu);
+    if (lm_tc_ok(p.t))
+      return adam ? launch_stage2_tc<K, true>(p, num_sms, st, bu)
+                  : launch_stage2_tc<K, false>(p, num_sms, st, bu);
     v = 1;   // tables outside the tensor-core path: the FP32 shape of 16 lanes
+  }
+  if (adam) {
+    // the Adam solver's FP32 stage 2 runs on the 16-lane shape
+    const Shape s = kShape2[1];
+    return launch_persistent(lm_stage2_kernel<K, 16, 8, true>, p, num_sms, st, bu, 2, s.G, s.maxw);
   }
   const Shape s = kShape2[v];
   if (v == 1) return launch_persistent(lm_stage2_kernel<K, 16, 8>, p, num_sms, st, bu, 2, s.G, s.maxw);

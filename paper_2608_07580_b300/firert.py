@@ -19,6 +19,7 @@ MAX_ENDM = 8
 FIRE_MEM_DEVICE, FIRE_MEM_HOST = 0, 1
 FIRE_INIT_DEFAULT, FIRE_INIT_GIVEN, FIRE_INIT_MLP = 0, 1, 2
 FIRE_FIT_ALL, FIRE_FIT_HFDI = 0, 1
+FIRE_SOLVER_LM, FIRE_SOLVER_ADAM = 0, 1
 PX_CONVERGED, PX_MAXITER, PX_NONFINITE, PX_ALL_MASKED, PX_CHOL_FAIL, PX_NOT_CANDIDATE = range(6)
 PX_F_FP64, PX_F_NOT_IDENT, PX_F_MLP_FALLBACK, PX_F_S1_MAXITER = 8, 16, 32, 64
 STATIC_MAX_PIX = 16384           # scene limit of Context.retrieve_static
@@ -59,7 +60,10 @@ class Config_t(C.Structure):
                 ("noise_abs", C.c_float), ("weighted", C.c_int32), ("hfdi_thresh", C.c_float),
                 ("hfdi_lambda_hi", C.c_float), ("hfdi_lambda_lo", C.c_float),
                 ("ident_sd_et", C.c_float), ("ident_alpha_snr", C.c_float),
-                ("wait_spins", C.c_int64)]
+                ("wait_spins", C.c_int64),
+                ("solver", C.c_int32), ("adam_steps1", C.c_int32), ("adam_steps2", C.c_int32),
+                ("adam_lr1", C.c_double), ("adam_lr2", C.c_double), ("adam_clip", C.c_double),
+                ("adam_beta1", C.c_double), ("adam_beta2", C.c_double), ("adam_eps", C.c_double)]
 
 
 class Priors_t(C.Structure):
@@ -210,6 +214,8 @@ def default_config(**overrides):
         if k in ("win1", "win2h", "win2s"):
             setattr(c, k + "_lo", v[0])
             setattr(c, k + "_hi", v[1])
+        elif k == "solver" and isinstance(v, str):
+            c.solver = {"lm": FIRE_SOLVER_LM, "adam": FIRE_SOLVER_ADAM}[v]
         else:
             setattr(c, k, v)
     return c
