@@ -340,6 +340,37 @@ def hfdi(tables, radiance_row, cfg=None):
     return lib().orc_hfdi(C.byref(th.c), C.byref(c), L.ctypes.data_as(C.POINTER(C.c_float)))
 
 
+WV_LAMBDAS = (870.0, 940.0, 1010.0)     # shoulder, centre, shoulder of the 940 nm feature (nm)
+
+
+def wv_depth_table(tables, lams=WV_LAMBDAS):
+    """Depth of the 940 nm feature of each water-vapour bin of the tables
+    (flat surface, two-way direct path), single precision [n_wv]."""
+    th = _TablesHolder(tables)
+    D = np.empty(tables.n_wv, dtype=np.float32)
+    lib().orc_wv_depth_table(C.byref(th.c), C.c_double(lams[0]), C.c_double(lams[1]),
+                             C.c_double(lams[2]), C.c_void_p(D.ctypes.data))
+    return D
+
+
+def wv_presolve(tables, radiance, width, height, block=12, lams=WV_LAMBDAS):
+    """Water-vapour presolve (Sec. 2.5): per-pixel 940 nm band depth, the
+    lower median of each block x block super-pixel, quantised to a bin of
+    the tables. radiance [height * width, n_bands] row-major image order.
+    Returns (bins [n] uint16, 0xFFFF for a block without any depth;
+    depth [n] float32)."""
+    th = _TablesHolder(tables)
+    L = np.ascontiguousarray(radiance, dtype=np.float32)
+    n = int(width) * int(height)
+    assert L.shape == (n, tables.n_bands)
+    bins = np.empty(n, dtype=np.uint16)
+    depth = np.empty(n, dtype=np.float32)
+    lib().orc_wv_presolve(C.byref(th.c), C.c_void_p(L.ctypes.data), C.c_int64(width), C.c_int64(height),
+                          C.c_int(block), C.c_double(lams[0]), C.c_double(lams[1]), C.c_double(lams[2]),
+                          C.c_void_p(bins.ctypes.data), C.c_void_p(depth.ctypes.data))
+    return bins, depth
+
+
 def retrieve(tables, radiance, wv_bin, cfg=None, init_state=None, n_threads=0):
     """Per-pixel two-stage fit of every row of radiance [n, n_bands] (fp32).
     Returns a dict of FP64 outputs (state [n, K+8], ET, sdT, alpha, cov [n, 21],

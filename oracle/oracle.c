@@ -658,6 +658,98 @@ double orc_hfdi(const orc_tables_t *t, const orc_config_t *c, const float *L) {
   return (a - b) / (a + b);
 }
 
+/* ---------------------------------------------- water-vapour presolve -- */
+/* Sec. 2.5 (pre-solved water vapour): the depth of the 940 nm water
+ * feature against a continuum interpolated linearly across its shoulders,
+ *   D = 1 - L(lc) / (L(lo) + (L(hi) - L(lo)) (lc - lo) / (hi - lo)),
+ * for every pixel; each pixel is then given the median of its 12 x 12
+ * super-pixel (the block of the image it falls in; edge blocks are smaller;
+ * the lower median, the element of rank (n - 1) / 2 of the n finite
+ * depths), and that median is quantised to a bin of the scene's water-vapour
+ * table. The table side: each bin's depth D_j from the same formula applied
+ * to the two-way direct path A tau_down tau_up of a flat surface
+ * (A = E0 cos(theta_s) / pi), in double and then rounded once to single
+ * precision; the median's fractional bin index is found by linear
+ * interpolation between the bins whose depths bracket it and rounded to the
+ * nearest bin (below the first depth: bin 0; above the last: the last).
+ * The depth, the interpolation and the rounding decide an integer, so they
+ * are taken in single precision (the library's precision), with fmaf for
+ * the continuum; a pixel with a non-finite or saturated shoulder or centre
+ * band, or a non-positive continuum, is left out of its block's median; a
+ * block without any depth gets the invalid bin 0xFFFF. */
+static int cmp_float(const void *a, const void *b) {
+  float x = *(const float *)a, y = *(const float *)b;
+  return (x > y) - (x < y);
+}
+
+void orc_wv_depth_table(const orc_tables_t *t, double lam_lo, double lam_c, double lam_hi,
+                        float *D) {
+  int blo = nearest_band(t, lam_lo), bc = nearest_band(t, lam_c), bhi = nearest_band(t, lam_hi);
+  double f = ((double)t->wavelength_nm[bc] - t->wavelength_nm[blo]) /
+             ((double)t->wavelength_nm[bhi] - t->wavelength_nm[blo]);
+  for (int j = 0; j < t->n_wv; j++) {
+    double a[3];
+    int bb[3] = {blo, bc, bhi};
+    for (int q = 0; q < 3; q++) {
+      int b = bb[q];
+      a[q] = (double)t->solar_irr[b] * t->cos_sza / M_PI * (double)t->tau_down[j * t->n_bands + b] *
+             (double)t->tau_up[j * t->n_bands + b];
+    }
+    D[j] = (float)(1.0 - a[1] / (a[0] + (a[2] - a[0]) * f));
+  }
+}
+
+void orc_wv_presolve(const orc_tables_t *t, const float *radiance, int64_t width, int64_t height,
+                     int block, double lam_lo, double lam_c, double lam_hi, uint16_t *bin_out,
+                     float *depth_out) {
+  int nb = t->n_bands;
+  int blo = nearest_band(t, lam_lo), bc = nearest_band(t, lam_c), bhi = nearest_band(t, lam_hi);
+  float cf = (float)(((double)t->wavelength_nm[bc] - t->wavelength_nm[blo]) /
+                     ((double)t->wavelength_nm[bhi] - t->wavelength_nm[blo]));
+  float Dj[ORC_MAXWV];
+  orc_wv_depth_table(t, lam_lo, lam_c, lam_hi, Dj);
+  int64_t n = width * height;
+  float *D = (float *)malloc(sizeof(float) * (n > 0 ? n : 1));
+  for (int64_t p = 0; p < n; p++) {
+    const float *L = radiance + p * nb;
+    float lo = L[blo], c = L[bc], hi = L[bhi];
+    int ok = isfinite(lo) && isfinite(c) && isfinite(hi);
+    if (t->sat_level)
+      ok = ok && lo < t->sat_level[blo] && c < t->sat_level[bc] && hi < t->sat_level[bhi];
+    float cont = fmaf(hi - lo, cf, lo);
+    D[p] = ok && cont > 0.0f ? 1.0f - c / cont : NAN;
+    if (depth_out) depth_out[p] = D[p];
+  }
+  float *v = (float *)malloc(sizeof(float) * block * block);
+  for (int64_t by = 0; by * block < height; by++)
+    for (int64_t bx = 0; bx * block < width; bx++) {
+      int m = 0;
+      for (int64_t y = by * block; y < height && y < (by + 1) * block; y++)
+        for (int64_t x = bx * block; x < width && x < (bx + 1) * block; x++)
+          if (isfinite(D[y * width + x])) v[m++] = D[y * width + x];
+      uint16_t bin = 0xFFFF;
+      if (m > 0) {
+        qsort(v, m, sizeof(float), cmp_float);
+        float med = v[(m - 1) / 2];
+        float fi;
+        int J = t->n_wv;
+        if (!(med > Dj[0])) fi = 0.0f;
+        else if (!(med < Dj[J - 1])) fi = (float)(J - 1);
+        else {
+          int j = 0;
+          while (!(med < Dj[j + 1])) j++;   /* Dj[j] <= med < Dj[j + 1] */
+          fi = (float)j + (med - Dj[j]) / (Dj[j + 1] - Dj[j]);
+        }
+        int b = (int)floorf(fi + 0.5f);
+        bin = (uint16_t)(b < 0 ? 0 : (b > J - 1 ? J - 1 : b));
+      }
+      for (int64_t y = by * block; y < height && y < (by + 1) * block; y++)
+        for (int64_t x = bx * block; x < width && x < (bx + 1) * block; x++) bin_out[y * width + x] = bin;
+    }
+  free(v);
+  free(D);
+}
+
 /* ------------------------------------------------------- forward ------ */
 /* mode 1: state [x_surf(K), a1, T1]; mode 2: [x_surf(K), mu_h, s_h, mu_s, s_s, eta, a] */
 void orc_forward(const orc_tables_t *t, int mode, const double *state, const uint16_t *wv_bin,

@@ -17,6 +17,7 @@
 #define ORC_NS1 (ORC_MAXK + 2)
 #define ORC_NS2 6
 #define ORC_NSTATE (ORC_MAXK + 8)
+#define ORC_MAXWV 256     /* water-vapour bins */
 
 /* per-pixel status: low 3 bits = outcome, upper bits = flags */
 enum {
@@ -109,6 +110,11 @@ void orc_adam(int64_t n, double *w, const double *g, double *m, double *v, int t
 void orc_posterior_at(const orc_tables_t *t, const orc_config_t *c, const float *Lrow, int w,
                       const double *state, double *ET, double *sdT, double *cost, double *rms,
                       double *cov21, double *var_ET, int *ident);
+void orc_wv_depth_table(const orc_tables_t *t, double lam_lo, double lam_c, double lam_hi,
+                        float *D);
+void orc_wv_presolve(const orc_tables_t *t, const float *radiance, int64_t width, int64_t height,
+                     int block, double lam_lo, double lam_c, double lam_hi, uint16_t *bin_out,
+                     float *depth_out);
 void orc_normal_equations(const orc_tables_t *t, const orc_config_t *c, int stage,
                           const float *Lrow, int w, const double *x, double *Hout, double *gout,
                           double *cost_out);
