@@ -434,6 +434,37 @@ fire_status_t fire_retrieve_static(fire_ctx_t *ctx, const fire_scene_t *scene,
                                    const fire_priors_t *priors, const fire_outputs_t *out,
                                    fire_stream_t stream);
 
+/* Water-vapour presolve (Sec. 2.5, "pre-solved water vapor"): the bins that
+ * fire_retrieve's scene takes, from the radiance itself.
+ * - radiance: DEVICE [height * width][n_bands] fp32, pixels in row-major
+ *   image order (x fastest); wv_bin_out: DEVICE [height * width];
+ *   depth_out: DEVICE [height * width] or NULL (the per-pixel depth).
+ * - For every pixel the depth of the 940 nm water feature against a
+ *   continuum interpolated linearly across its shoulders,
+ *   D = 1 - L(lc) / (L(lo) + (L(hi) - L(lo)) (lc - lo) / (hi - lo)), at the
+ *   bands nearest to lams = {lo, lc, hi} nm (NULL: {870, 940, 1010}); a pixel
+ *   with a non-finite or saturated one of the three bands, or a
+ *   non-positive continuum, has no depth (NaN). Each pixel then gets the
+ *   lower median (rank (n - 1) / 2) of the n depths of its block x block
+ *   super-pixel (blocks from the image origin; edge blocks are smaller),
+ *   quantised to the table: the fractional bin index by linear
+ *   interpolation between the bracketing depths of fire_wv_depth_table,
+ *   rounded to the nearest bin, clamped to [0, n_wv - 1]. A block without
+ *   any depth gets 0xFFFF (an invalid bin: fire_retrieve reports its pixels
+ *   NONFINITE). Depths, interpolation and rounding are single precision.
+ * - Errors: FIRE_ERR_ARG (block outside 1..16, null pointers with pixels,
+ *   shoulder / centre bands not in order, table depths not increasing with
+ *   the bin); FIRE_ERR_CUDA. Asynchronous on the stream. */
+fire_status_t fire_wv_presolve(fire_ctx_t *ctx, const float *radiance, int64_t width, int64_t height,
+                               int32_t block, const float *lams, uint16_t *wv_bin_out,
+                               float *depth_out, fire_stream_t stream);
+/* The flat-surface depth of the 940 nm feature of every water-vapour bin of
+ * the context's tables, D_j from the same formula applied to the two-way
+ * direct path E0 cos(theta_s) / pi tau_down tau_up (in double, rounded once
+ * to float): HOST depth_out [n_wv]. lams as for fire_wv_presolve.
+ * Synchronous; errors FIRE_ERR_ARG. */
+fire_status_t fire_wv_depth_table(fire_ctx_t *ctx, const float *lams, float *depth_out);
+
 /* Per-kernel timing. With timing on, every fit launch records CUDA events
  * on its stream around the stage-1, stage-2 and finalize kernels (no
  * synchronisation). fire_get_kernel_times waits for the last one and

@@ -465,6 +465,12 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
   if (!c) return FIRE_ERR_NOMEM;
   if (cfg) c->cfg = *cfg;
   else fire_default_config(&c->cfg);
+  // host copies for the water-vapour presolve's depth table
+  c->h_wl.assign(tb->wavelength_nm, tb->wavelength_nm + nb);
+  c->h_e0.assign(tb->solar_irr, tb->solar_irr + nb);
+  c->h_td.assign(tb->tau_down, tb->tau_down + (size_t)nwv * nb);
+  c->h_tu.assign(tb->tau_up, tb->tau_up + (size_t)nwv * nb);
+  c->h_cos = tb->cos_sza;
   cudaGetDevice(&c->device);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
 
@@ -943,6 +949,53 @@ fire_status_t fire_gemm_bf16(const fire_gemm_t *q, fire_stream_t stream) {
   g.accumulate = q->accumulate;
   g.err = q->err;
   return cuda_status(launch_gemm(g, (cudaStream_t)stream));
+}
+
+// the band whose centre is nearest to lam (the first of equals)
+static int nearest_band(const std::vector<float> &wl, double lam) {
+  int best = 0;
+  for (int b = 1; b < (int)wl.size(); b++)
+    if (fabs((double)wl[b] - lam) < fabs((double)wl[best] - lam)) best = b;
+  return best;
+}
+
+fire_status_t fire_wv_depth_table(fire_ctx_t *c, const float *lams, float *depth_out) {
+  if (!c || !depth_out) return FIRE_ERR_ARG;
+  const double lo = lams ? lams[0] : 870.0, lc = lams ? lams[1] : 940.0, hi = lams ? lams[2] : 1010.0;
+  const int nb = c->t.nb, nwv = c->t.nwv;
+  const int blo = nearest_band(c->h_wl, lo), bc = nearest_band(c->h_wl, lc), bhi = nearest_band(c->h_wl, hi);
+  if (!(blo < bc && bc < bhi)) return FIRE_ERR_ARG;
+  const double f = ((double)c->h_wl[bc] - c->h_wl[blo]) / ((double)c->h_wl[bhi] - c->h_wl[blo]);
+  for (int j = 0; j < nwv; j++) {
+    double a[3];
+    const int bb[3] = {blo, bc, bhi};
+    for (int q = 0; q < 3; q++) {
+      const int b = bb[q];
+      a[q] = (double)c->h_e0[b] * (double)c->h_cos / M_PI * (double)c->h_td[(size_t)j * nb + b] *
+             (double)c->h_tu[(size_t)j * nb + b];
+    }
+    depth_out[j] = (float)(1.0 - a[1] / (a[0] + (a[2] - a[0]) * f));
+  }
+  return FIRE_OK;
+}
+
+fire_status_t fire_wv_presolve(fire_ctx_t *c, const float *radiance, int64_t width, int64_t height,
+                               int32_t block, const float *lams, uint16_t *wv_bin_out, float *depth_out,
+                               fire_stream_t stream) {
+  if (!c || width < 0 || height < 0 || block < 1 || block > 16) return FIRE_ERR_ARG;
+  if (width * height > 0 && (!radiance || !wv_bin_out)) return FIRE_ERR_ARG;
+  const double lo = lams ? lams[0] : 870.0, lc = lams ? lams[1] : 940.0, hi = lams ? lams[2] : 1010.0;
+  const int blo = nearest_band(c->h_wl, lo), bc = nearest_band(c->h_wl, lc), bhi = nearest_band(c->h_wl, hi);
+  WvLut lut;
+  lut.n = c->t.nwv;
+  fire_status_t s = fire_wv_depth_table(c, lams, lut.D);
+  if (s != FIRE_OK) return s;
+  for (int j = 1; j < lut.n; j++)
+    if (!(lut.D[j] > lut.D[j - 1])) return FIRE_ERR_ARG;   // the depths must increase with water
+  const float cf = (float)(((double)c->h_wl[bc] - c->h_wl[blo]) / ((double)c->h_wl[bhi] - c->h_wl[blo]));
+  return cuda_status(launch_wv_presolve(radiance, c->t.nb, (long long)width, (long long)height, block, blo, bc,
+                                        bhi, cf, c->d_sat, lut, wv_bin_out, depth_out,
+                                        (cudaStream_t)stream));
 }
 
 fire_status_t fire_block_mean(const float *src, int32_t w, int32_t h, int32_t nb, int32_t blk,

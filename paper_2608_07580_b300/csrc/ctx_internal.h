@@ -59,6 +59,9 @@ struct fire_ctx {
   cudaStream_t fit_st2 = nullptr;
   unsigned long long *d_ctr = nullptr;
   size_t tev_used = 0;
+  // host copies of the tables the water-vapour presolve's depth table needs
+  std::vector<float> h_wl, h_e0, h_td, h_tu;
+  float h_cos = 0.f;
 };
 
 namespace firert {

@@ -196,6 +196,14 @@ bool lm_tc_ok(const KTables &t);
 cudaError_t launch_forward(const KTables &t, int mode, const float *state, const uint16_t *wv,
                            int64_t n, float noise_rel, float noise_abs, uint64_t seed,
                            uint64_t stream_id, int64_t pix0, float *out, cudaStream_t st);
+// water-vapour presolve: the 940 nm depths of the table's bins (increasing)
+struct WvLut {
+  float D[256];
+  int n;
+};
+cudaError_t launch_wv_presolve(const float *rad, int nb, long long W, long long H, int B, int blo,
+                               int bc, int bhi, float cf, const float *sat, const WvLut &lut,
+                               uint16_t *bins, float *depth, cudaStream_t st);
 cudaError_t launch_block_mean(const float *src, int w, int h, int nb, int blk, float *dst,
                               cudaStream_t st);
 

@@ -134,6 +134,99 @@ __global__ void block_mean_kernel(const float *src, int w, int h, int nb, int bl
   }
 }
 
+// ---- water-vapour presolve (Sec. 2.5): one warp per super-pixel. Each lane
+// forms the 940 nm band depth of up to kWvPerLane of the block's pixels,
+// D = 1 - L_c / fma(L_hi - L_lo, cf, L_lo), in single precision; the warp
+// then selects the lower median (rank (n - 1) / 2 of the n finite depths)
+// by a most-significant-bit-first radix select on order-preserving integer
+// keys (32 ballot-count rounds), interpolates its fractional bin index
+// between the bracketing depths of the table and rounds it to the nearest
+// bin, and writes that bin for every pixel of the block. Three floats of
+// each 1136-byte radiance row are read: DRAM moves one 32-byte sector per
+// band per pixel.
+constexpr int kWvPerLane = 8;     // 32 x 8 = 256 pixels: blocks up to 16 x 16
+
+__device__ __forceinline__ unsigned order_key(float v) {
+  const unsigned u = __float_as_uint(v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_value(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void __launch_bounds__(256) wv_presolve_kernel(const float *rad, int nb, long long W,
+                                                          long long H, int B, int blo, int bc, int bhi,
+                                                          float cf, const float *sat, WvLut lut,
+                                                          uint16_t *bins, float *depth) {
+  const int lane = threadIdx.x & 31;
+  const long long nbx = (W + B - 1) / B, nby = (H + B - 1) / B;
+  const long long blk = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (blk >= nbx * nby) return;                 // warp-uniform
+  const long long by = blk / nbx, bx = blk % nbx;
+  const long long x0 = bx * B, y0 = by * B;
+  const int bw = (int)min((long long)B, W - x0), bh = (int)min((long long)B, H - y0);
+  const int np = bw * bh;
+  unsigned key[kWvPerLane];
+  bool ok[kWvPerLane];
+  int nv = 0;
+#pragma unroll
+  for (int q = 0; q < kWvPerLane; q++) {
+    const int i = lane + 32 * q;
+    ok[q] = false;
+    key[q] = 0u;
+    if (i < np) {
+      const long long p = (y0 + i / bw) * W + x0 + i % bw;
+      const float *row = rad + p * nb;
+      const float lo = __ldg(row + blo), c = __ldg(row + bc), hi = __ldg(row + bhi);
+      bool v = isfinite(lo) && isfinite(c) && isfinite(hi);
+      if (sat) v = v && lo < __ldg(sat + blo) && c < __ldg(sat + bc) && hi < __ldg(sat + bhi);
+      const float cont = fmaf(hi - lo, cf, lo);
+      v = v && cont > 0.f;
+      const float D = v ? 1.f - c / cont : __int_as_float(0x7fc00000);
+      if (depth) depth[p] = D;
+      ok[q] = v;
+      key[q] = order_key(D);
+      nv += v;
+    }
+  }
+  const int n = __reduce_add_sync(0xffffffffu, nv);
+  uint16_t bin = 0xFFFF;
+  if (n > 0) {
+    // the k-th smallest key, k = (n - 1) / 2, bit by bit from the top
+    unsigned want = 0u;
+    int k = (n - 1) / 2;
+    for (int bit = 31; bit >= 0; bit--) {
+      const unsigned hi_mask = bit == 31 ? 0u : (0xffffffffu << (bit + 1));
+      int cnt = 0;
+#pragma unroll
+      for (int q = 0; q < kWvPerLane; q++)
+        cnt += ok[q] && (key[q] & hi_mask) == want && !((key[q] >> bit) & 1u);
+      cnt = __reduce_add_sync(0xffffffffu, cnt);
+      if (k >= cnt) {
+        want |= 1u << bit;
+        k -= cnt;
+      }
+    }
+    const float med = key_value(want);
+    const int J = lut.n;
+    float fi;
+    if (!(med > lut.D[0])) fi = 0.f;
+    else if (!(med < lut.D[J - 1])) fi = (float)(J - 1);
+    else {
+      int j = 0;
+      while (!(med < lut.D[j + 1])) j++;        // D[j] <= med < D[j + 1]
+      fi = (float)j + (med - lut.D[j]) / (lut.D[j + 1] - lut.D[j]);
+    }
+    const int b = (int)floorf(fi + 0.5f);
+    bin = (uint16_t)(b < 0 ? 0 : (b > J - 1 ? J - 1 : b));
+  }
+#pragma unroll
+  for (int q = 0; q < kWvPerLane; q++) {
+    const int i = lane + 32 * q;
+    if (i < np) bins[(y0 + i / bw) * W + x0 + i % bw] = bin;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_build_tables(const KTables &t, const float *wl, const float *e0, float cos_sza,
@@ -174,6 +267,17 @@ cudaError_t launch_block_mean(const float *src, int w, int h, int nb, int blk, f
   long long blocks = (total + 255) / 256;
   if (blocks > 148 * 32) blocks = 148 * 32;
   block_mean_kernel<<<(int)blocks, 256, 0, st>>>(src, w, h, nb, blk, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wv_presolve(const float *rad, int nb, long long W, long long H, int B, int blo,
+                               int bc, int bhi, float cf, const float *sat, const WvLut &lut,
+                               uint16_t *bins, float *depth, cudaStream_t st) {
+  const long long nblk = ((W + B - 1) / B) * ((H + B - 1) / B);
+  if (nblk <= 0) return cudaSuccess;
+  const long long grid = (nblk + 7) / 8;         // 8 warps (super-pixels) per CTA
+  wv_presolve_kernel<<<(unsigned)grid, 256, 0, st>>>(rad, nb, W, H, B, blo, bc, bhi, cf, sat, lut, bins,
+                                                     depth);
   return cudaGetLastError();
 }
 

@@ -32,7 +32,8 @@ SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fir
            "fire_mlp_load", "fire_mlp_next_sample", "fire_ctx_set_mlp", "fire_retrieve_batch",
            "fire_graph_capture", "fire_graph_launch", "fire_graph_destroy", "fire_autotune",
            "fire_set_tuning", "fire_set_kernel_timing", "fire_get_kernel_times",
-           "fire_retrieve_static", "fire_set_allocator", "fire_measure_peak")
+           "fire_retrieve_static", "fire_set_allocator", "fire_measure_peak", "fire_wv_presolve",
+           "fire_wv_depth_table")
 
 # device allocator hook (fire_set_allocator): alloc(bytes, user) -> ptr, free(ptr, user)
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -140,6 +141,10 @@ def _load():
     lib.fire_forward.argtypes = [vp, i32, vp, vp, i64, f32, f32, u64, u64, i64, vp, vp]
     lib.fire_forward.restype = C.c_int
     lib.fire_block_mean.argtypes = [vp, i32, i32, i32, i32, vp, vp]
+    lib.fire_wv_presolve.argtypes = [vp, vp, i64, i64, i32, vp, vp, vp, vp]
+    lib.fire_wv_presolve.restype = C.c_int
+    lib.fire_wv_depth_table.argtypes = [vp, vp, vp]
+    lib.fire_wv_depth_table.restype = C.c_int
     lib.fire_block_mean.restype = C.c_int
     lib.fire_get_stats.argtypes = [vp, C.POINTER(Stats_t)]
     lib.fire_get_stats.restype = C.c_int
@@ -263,6 +268,7 @@ class Context:
         self.n_bands = int(k[0].size)
         self.n_endm = int(k[6].shape[0])
         self.n_tgrid = int(getattr(tables, "n_tgrid", 64))
+        self.n_wv = int(k[3].shape[0])
         self.tgrid = tgrid
         tb = Tables_t(self.n_bands, int(k[3].shape[0]), self.n_endm, self.n_tgrid, p(k[0]),
                       p(k[1]), float(tables.cos_sza), p(k[2]), p(k[3]), p(k[4]), p(k[5]),
@@ -462,6 +468,30 @@ class Context:
                                          _dptr(H), _dptr(g), _dptr(cost), _stream_ptr(stream)),
                "fire_normal_equations")
         return H, g, cost
+
+    def wv_depth_table(self, lams=None):
+        """fire_wv_depth_table: the 940 nm depth of every water-vapour bin."""
+        D = np.empty(self.n_wv, dtype=np.float32)
+        lp = None if lams is None else np.ascontiguousarray(lams, dtype=np.float32)
+        _check(lib.fire_wv_depth_table(self._h, None if lp is None else lp.ctypes.data, D.ctypes.data),
+               "fire_wv_depth_table")
+        return D
+
+    def wv_presolve(self, radiance, width, height, block=12, lams=None, depth=False, out=None,
+                    stream=None):
+        """fire_wv_presolve: per-pixel water-vapour bins (int16 CUDA tensor
+        holding the uint16 bits) from device radiance in row-major image
+        order; with depth, also the per-pixel 940 nm depths."""
+        import torch
+        n = int(width) * int(height)
+        if out is None:
+            out = torch.empty((n,), dtype=torch.int16, device="cuda")
+        d = torch.empty((n,), dtype=torch.float32, device="cuda") if depth else None
+        lp = None if lams is None else np.ascontiguousarray(lams, dtype=np.float32)
+        _check(lib.fire_wv_presolve(self._h, _dptr(radiance, torch.float32), int(width), int(height), int(block),
+                                    None if lp is None else lp.ctypes.data, _dptr(out), _dptr(d),
+                                    _stream_ptr(stream)), "fire_wv_presolve")
+        return (out, d) if depth else out
 
     def stats(self):
         s = Stats_t()
