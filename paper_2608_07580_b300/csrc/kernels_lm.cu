@@ -1205,6 +1205,62 @@ __device__ __noinline__ void laplace_cov(const KConfig &c, CovIO &io) {
   va = Cx[up<6>(5, 5)];
 }
 
+// A lower bound of the Laplace variance of alpha over every active set the
+// final state admits, from the FP32 normal matrix: every variable on a bound
+// held (holding more variables can only lower alpha's marginal variance),
+// in z units of the Jacobi-scaled matrix A = D^-1/2 H D^-1/2. Returns false
+// when the bound cannot be trusted: the scaled matrix not positive definite,
+// or trace(A^-1) so large that the FP32 matrix's error (a relative 5e-5 of
+// the diagonal scale, six times the measured 8.5e-6) could move A^-1 by more
+// than a quarter (6 x 5e-5 x trace(A^-1) >= 0.25).
+__device__ __noinline__ bool alpha_var_floor(const KConfig &c, const CovIO &io, double &va_min) {
+  bool fix[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++)
+    fix[k] = io.x[k] <= c.lo2[k] || io.x[k] >= c.hi2[k] || !(io.H[up<6>(k, k)] > 0.0);
+  if (fix[5]) return false;
+  double A[21], rd[6];
+#pragma unroll
+  for (int i = 0; i < 6; i++) rd[i] = fix[i] ? 1.0 : rsq(io.H[up<6>(i, i)]);
+#pragma unroll
+  for (int i = 0; i < 6; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++)
+      A[i * (i + 1) / 2 + j] = (fix[i] || fix[j]) ? (i == j ? 1.0 : 0.0) : io.H[up<6>(i, j)] * rd[i] * rd[j];
+  double il[6];
+#pragma unroll
+  for (int j = 0; j < 6; j++) {
+    double s = A[j * (j + 1) / 2 + j];
+#pragma unroll
+    for (int k = 0; k < j; k++) s -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+    if (!(s > 0.0)) return false;
+    const double r = rsq(s);
+    il[j] = r;
+#pragma unroll
+    for (int i = j + 1; i < 6; i++) {
+      double t = A[i * (i + 1) / 2 + j];
+#pragma unroll
+      for (int k = 0; k < j; k++) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+      A[i * (i + 1) / 2 + j] = t * r;
+    }
+  }
+  // W = L^-1: trace(A^-1) = sum of W's squares, (A^-1)_55 = sum_k W_k5^2 = W_55^2
+  double W[21], tr = 0.0;
+#pragma unroll
+  for (int v = 0; v < 6; v++)
+#pragma unroll
+    for (int i = v; i < 6; i++) {
+      double t = (i == v) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = v; k < i; k++) t -= A[i * (i + 1) / 2 + k] * W[k * (k + 1) / 2 + v];
+      W[i * (i + 1) / 2 + v] = t * il[i];
+      if (!fix[i] && !fix[v]) tr += W[i * (i + 1) / 2 + v] * W[i * (i + 1) / 2 + v];
+    }
+  if (!(6.0 * 5e-5 * tr < 0.25)) return false;
+  va_min = W[20] * W[20] * rd[5] * rd[5];   // z units squared
+  return true;
+}
+
 // ------------------------------------------------------------ kernels ---
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -2712,8 +2768,18 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const __grid_c
     // without an inversion; 0.9 of the threshold leaves room for rounding
     const double sd_min = 0.5 * ((double)c.hi2[5] - (double)c.lo2[5]) *
                           sqrt((double)io.s2 / fmax(io.H[up<6>(5, 5)], 1e-300));
-    const bool cand = fitted && !act_a && nf > 0 &&
-                      (double)io.x[5] >= 0.9 * (double)c.ident_alpha_snr * sd_min;
+    bool cand = fitted && !act_a && nf > 0 &&
+                (double)io.x[5] >= 0.9 * (double)c.ident_alpha_snr * sd_min;
+    // ... and not surely unidentifiable: alpha below half its threshold
+    // against the floor of sd(alpha) over every admissible active set (with
+    // the matrix error allowed for, sd(alpha) stays above 0.86 of that
+    // floor, so alpha / sd(alpha) < 0.58 of the threshold whatever the FP64
+    // matrix gives); s2 moves by under 3 % with the free count
+    double va_min;
+    if (cand && alpha_var_floor(c, io, va_min)) {
+      const double sda_min = 0.5 * ((double)c.hi2[5] - (double)c.lo2[5]) * sqrt((double)io.s2 * 0.97 * va_min);
+      if ((double)io.x[5] < 0.5 * (double)c.ident_alpha_snr * sda_min) cand = false;
+    }
     unsigned m = __ballot_sync(kFull, cand);
     bool mine = false;
     double H64[21], g64[6];
