@@ -434,6 +434,26 @@ fire_status_t fire_retrieve_static(fire_ctx_t *ctx, const fire_scene_t *scene,
                                    const fire_priors_t *priors, const fire_outputs_t *out,
                                    fire_stream_t stream);
 
+/* HFDI (Sec. 2.1): (L_hi - L_lo) / (L_hi + L_lo) of every pixel at the bands
+ * nearest to the config's hfdi_lambda_hi / hfdi_lambda_lo (2430 / 2061 nm),
+ * the index the fit's gate tests; NaN where either band is not finite.
+ * DEVICE radiance [n_pix][n_bands], hfdi_out [n_pix]. For the threshold
+ * studies of the paper's appendix. Errors: FIRE_ERR_ARG, FIRE_ERR_CUDA.
+ * Asynchronous on the stream. */
+fire_status_t fire_hfdi(fire_ctx_t *ctx, const float *radiance, int64_t n_pix, float *hfdi_out,
+                        fire_stream_t stream);
+
+/* Thermal injection, Eq. (inject) (Sec. 2.8): radiance_out = radiance_bg +
+ * alpha tau_up(lambda) B(lambda, T) for every band of every pixel, tau_up of
+ * the pixel's water-vapour bin (an out-of-range bin gives a NaN row), the
+ * Planck term in FP64. All pointers DEVICE: radiance_bg, radiance_out
+ * [n_pix][n_bands] (may alias), wv_bin, alpha, T [n_pix]. The injection
+ * experiment's input generator. Errors: FIRE_ERR_ARG, FIRE_ERR_CUDA.
+ * Asynchronous on the stream. */
+fire_status_t fire_inject(fire_ctx_t *ctx, const float *radiance_bg, const uint16_t *wv_bin,
+                          const float *alpha, const float *T, int64_t n_pix, float *radiance_out,
+                          fire_stream_t stream);
+
 /* Water-vapour presolve (Sec. 2.5, "pre-solved water vapor"): the bins that
  * fire_retrieve's scene takes, from the radiance itself.
  * - radiance: DEVICE [height * width][n_bands] fp32, pixels in row-major

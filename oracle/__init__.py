@@ -340,6 +340,20 @@ def hfdi(tables, radiance_row, cfg=None):
     return lib().orc_hfdi(C.byref(th.c), C.byref(c), L.ctypes.data_as(C.POINTER(C.c_float)))
 
 
+def inject(tables, L_bg, wv_bin, alpha, T):
+    """Eq. (inject): L_bg + alpha tau_up B(lambda, T) per pixel (fp32)."""
+    th = _TablesHolder(tables)
+    Lb = np.ascontiguousarray(L_bg, dtype=np.float32)
+    wv = np.ascontiguousarray(wv_bin, dtype=np.uint16)
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    TT = np.ascontiguousarray(T, dtype=np.float64)
+    out = np.empty_like(Lb)
+    lib().orc_inject(C.byref(th.c), C.c_void_p(Lb.ctypes.data), C.c_void_p(wv.ctypes.data),
+                     C.c_void_p(a.ctypes.data), C.c_void_p(TT.ctypes.data), C.c_int64(wv.size),
+                     C.c_void_p(out.ctypes.data))
+    return out
+
+
 WV_LAMBDAS = (870.0, 940.0, 1010.0)     # shoulder, centre, shoulder of the 940 nm feature (nm)
 
 

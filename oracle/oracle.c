@@ -658,6 +658,21 @@ double orc_hfdi(const orc_tables_t *t, const orc_config_t *c, const float *L) {
   return (a - b) / (a + b);
 }
 
+/* ------------------------------------------------ thermal injection ---- */
+/* Eq. (inject), Sec. 2.8: a single-temperature thermal term added to a
+ * background spectrum, L_inj = L_bg + alpha tau_up(lambda) B(lambda, T), with
+ * the background pixel's water-vapour bin for tau_up; in double, rounded
+ * once to single precision. */
+void orc_inject(const orc_tables_t *t, const float *L_bg, const uint16_t *wv_bin, const double *alpha,
+                const double *T, int64_t n, float *L_out) {
+  int nb = t->n_bands;
+  for (int64_t i = 0; i < n; i++)
+    for (int b = 0; b < nb; b++) {
+      double tu = t->tau_up[(int64_t)wv_bin[i] * nb + b];
+      L_out[i * nb + b] = (float)((double)L_bg[i * nb + b] + alpha[i] * tu * orc_planck(t->wavelength_nm[b], T[i]));
+    }
+}
+
 /* ---------------------------------------------- water-vapour presolve -- */
 /* Sec. 2.5 (pre-solved water vapour): the depth of the 940 nm water
  * feature against a continuum interpolated linearly across its shoulders,

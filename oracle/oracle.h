@@ -110,6 +110,8 @@ void orc_adam(int64_t n, double *w, const double *g, double *m, double *v, int t
 void orc_posterior_at(const orc_tables_t *t, const orc_config_t *c, const float *Lrow, int w,
                       const double *state, double *ET, double *sdT, double *cost, double *rms,
                       double *cov21, double *var_ET, int *ident);
+void orc_inject(const orc_tables_t *t, const float *L_bg, const uint16_t *wv_bin, const double *alpha,
+                const double *T, int64_t n, float *L_out);
 void orc_wv_depth_table(const orc_tables_t *t, double lam_lo, double lam_c, double lam_hi,
                         float *D);
 void orc_wv_presolve(const orc_tables_t *t, const float *radiance, int64_t width, int64_t height,

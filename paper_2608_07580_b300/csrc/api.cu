@@ -420,6 +420,7 @@ void fire_ctx_destroy(fire_ctx_t *ctx) {
   dev_free(ctx->d_planck64);
   dev_free(ctx->d_plop);
   dev_free(ctx->d_wvtab);
+  dev_free(ctx->d_wl);
   dev_free(ctx->d_sat);
   dev_free(ctx->d_work);
   dev_free(ctx->d_err);
@@ -523,6 +524,9 @@ fire_status_t fire_ctx_create(fire_ctx_t **out, const fire_tables_t *tb, const f
     if ((st = dev_alloc(&c->d_err, sizeof(int))) != FIRE_OK) break;
     if ((st = cuda_status(cudaMemset(c->d_err, 0, sizeof(int)))) != FIRE_OK) break;
     if ((st = dev_alloc(&raw, nraw * 4)) != FIRE_OK) break;
+    if ((st = dev_alloc(&c->d_wl, (size_t)nb * 4)) != FIRE_OK) break;
+    if ((st = cuda_status(cudaMemcpy(c->d_wl, tb->wavelength_nm, nb * 4, cudaMemcpyHostToDevice))) != FIRE_OK)
+      break;
     if (tb->sat_level) {
       if ((st = dev_alloc(&c->d_sat, (size_t)nb * 4)) != FIRE_OK) break;
       if ((st = cuda_status(cudaMemcpy(c->d_sat, tb->sat_level, nb * 4, cudaMemcpyHostToDevice))) != FIRE_OK) break;
@@ -996,6 +1000,24 @@ fire_status_t fire_wv_presolve(fire_ctx_t *c, const float *radiance, int64_t wid
   return cuda_status(launch_wv_presolve(radiance, c->t.nb, (long long)width, (long long)height, block, blo, bc,
                                         bhi, cf, c->d_sat, lut, wv_bin_out, depth_out,
                                         (cudaStream_t)stream));
+}
+
+fire_status_t fire_hfdi(fire_ctx_t *c, const float *radiance, int64_t n_pix, float *hfdi_out,
+                        fire_stream_t stream) {
+  if (!c || n_pix < 0) return FIRE_ERR_ARG;
+  if (n_pix == 0) return FIRE_OK;
+  if (!radiance || !hfdi_out) return FIRE_ERR_ARG;
+  return cuda_status(launch_hfdi(radiance, c->t.nb, (long long)n_pix, c->t.bh, c->t.bl, hfdi_out,
+                                 (cudaStream_t)stream));
+}
+
+fire_status_t fire_inject(fire_ctx_t *c, const float *radiance_bg, const uint16_t *wv_bin, const float *alpha,
+                          const float *T, int64_t n_pix, float *radiance_out, fire_stream_t stream) {
+  if (!c || n_pix < 0) return FIRE_ERR_ARG;
+  if (n_pix == 0) return FIRE_OK;
+  if (!radiance_bg || !wv_bin || !alpha || !T || !radiance_out) return FIRE_ERR_ARG;
+  return cuda_status(launch_inject(c->t, c->d_wl, radiance_bg, wv_bin, alpha, T, (long long)n_pix,
+                                   radiance_out, (cudaStream_t)stream));
 }
 
 fire_status_t fire_block_mean(const float *src, int32_t w, int32_t h, int32_t nb, int32_t blk,

@@ -12,6 +12,7 @@ struct fire_ctx {
   firert::KTables t;
   // device buffers
   float *d_image = nullptr;
+  float *d_wl = nullptr;             // [nb] band centres (nm), for Eq. (inject)
   float *d_planck_full = nullptr;    // [nt][nb] Planck grid over every band (residual spectrum)
   double *d_planck64 = nullptr;      // [nt][n2] FP64 Planck grid of the stage-2 bands (posterior)
   unsigned char *d_plop = nullptr;   // stage-2 Planck grid as the tensor-core operand

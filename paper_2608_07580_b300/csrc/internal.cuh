@@ -204,6 +204,10 @@ struct WvLut {
 cudaError_t launch_wv_presolve(const float *rad, int nb, long long W, long long H, int B, int blo,
                                int bc, int bhi, float cf, const float *sat, const WvLut &lut,
                                uint16_t *bins, float *depth, cudaStream_t st);
+cudaError_t launch_inject(const KTables &t, const float *wl, const float *bg, const uint16_t *wv,
+                          const float *alpha, const float *T, long long n, float *out, cudaStream_t st);
+cudaError_t launch_hfdi(const float *rad, int nb, long long n, int bhi, int blo, float *out,
+                        cudaStream_t st);
 cudaError_t launch_block_mean(const float *src, int w, int h, int nb, int blk, float *dst,
                               cudaStream_t st);
 

@@ -86,6 +86,38 @@ __global__ void planck64_kernel(KTables t, const float *wl, double *out) {
   }
 }
 
+// Eq. (inject): out = L_bg + alpha tau_up B(lambda, T) for each band of each
+// pixel, the Planck term in FP64 (an input generator: exact to the fp32
+// store), tau_up of the pixel's water-vapour bin; an invalid bin gives NaN
+__global__ void inject_kernel(KTables t, const float *wl, const float *bg, const uint16_t *wv,
+                              const float *alpha, const float *T, long long n, float *out) {
+  const long long total = n * t.nb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / t.nb;
+    const int b = (int)(e % t.nb);
+    const int w = wv[i];
+    if (w >= t.nwv) {
+      out[e] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    const double lam = (double)wl[b] * 1e-9;
+    const double x = kH * kC / (kKB * lam * (double)T[i]);
+    const double B = 2.0 * kH * kC * kC / (lam * lam * lam * lam * lam) * 1e-9 / expm1(x);
+    out[e] = (float)((double)bg[e] + (double)alpha[i] * (double)t.wvtab[(size_t)w * t.nb + b].w * B);
+  }
+}
+
+// HFDI (Sec. 2.1): (L_hi - L_lo) / (L_hi + L_lo) at the two gate bands, one
+// thread per pixel; NaN where either band is not finite
+__global__ void hfdi_kernel(const float *rad, int nb, long long n, int bhi, int blo, float *out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float h = __ldg(rad + i * nb + bhi), l = __ldg(rad + i * nb + blo);
+    out[i] = (isfinite(h) && isfinite(l)) ? (h - l) / (h + l) : __int_as_float(0x7fc00000);
+  }
+}
+
 // Forward model, one warp per state (the model itself is warp_forward in
 // model.cuh), with optional counter-based noise.
 __global__ void __launch_bounds__(256) forward_kernel(KTables t, int mode, const float *state,
@@ -278,6 +310,25 @@ cudaError_t launch_wv_presolve(const float *rad, int nb, long long W, long long 
   const long long grid = (nblk + 7) / 8;         // 8 warps (super-pixels) per CTA
   wv_presolve_kernel<<<(unsigned)grid, 256, 0, st>>>(rad, nb, W, H, B, blo, bc, bhi, cf, sat, lut, bins,
                                                      depth);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inject(const KTables &t, const float *wl, const float *bg, const uint16_t *wv,
+                          const float *alpha, const float *T, long long n, float *out, cudaStream_t st) {
+  const long long total = n * t.nb;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  inject_kernel<<<(int)blocks, 256, 0, st>>>(t, wl, bg, wv, alpha, T, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hfdi(const float *rad, int nb, long long n, int bhi, int blo, float *out,
+                        cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  hfdi_kernel<<<(int)blocks, 256, 0, st>>>(rad, nb, n, bhi, blo, out);
   return cudaGetLastError();
 }
 

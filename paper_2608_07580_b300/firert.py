@@ -33,7 +33,7 @@ SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fir
            "fire_graph_capture", "fire_graph_launch", "fire_graph_destroy", "fire_autotune",
            "fire_set_tuning", "fire_set_kernel_timing", "fire_get_kernel_times",
            "fire_retrieve_static", "fire_set_allocator", "fire_measure_peak", "fire_wv_presolve",
-           "fire_wv_depth_table")
+           "fire_wv_depth_table", "fire_inject", "fire_hfdi")
 
 # device allocator hook (fire_set_allocator): alloc(bytes, user) -> ptr, free(ptr, user)
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -145,6 +145,10 @@ def _load():
     lib.fire_wv_presolve.restype = C.c_int
     lib.fire_wv_depth_table.argtypes = [vp, vp, vp]
     lib.fire_wv_depth_table.restype = C.c_int
+    lib.fire_inject.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp]
+    lib.fire_inject.restype = C.c_int
+    lib.fire_hfdi.argtypes = [vp, vp, i64, vp, vp]
+    lib.fire_hfdi.restype = C.c_int
     lib.fire_block_mean.restype = C.c_int
     lib.fire_get_stats.argtypes = [vp, C.POINTER(Stats_t)]
     lib.fire_get_stats.restype = C.c_int
@@ -469,12 +473,34 @@ class Context:
                "fire_normal_equations")
         return H, g, cost
 
+    def hfdi(self, radiance, out=None, stream=None):
+        """fire_hfdi: the gate index of every pixel (torch CUDA tensors)."""
+        import torch
+        n = int(radiance.shape[0])
+        if out is None:
+            out = torch.empty((n,), dtype=torch.float32, device="cuda")
+        _check(lib.fire_hfdi(self._h, _dptr(radiance, torch.float32), n, _dptr(out, torch.float32),
+                             _stream_ptr(stream)), "fire_hfdi")
+        return out
+
+    def inject(self, radiance_bg, wv_bin, alpha, T, out=None, stream=None):
+        """fire_inject (Eq. inject): radiance_bg + alpha tau_up B(lambda, T),
+        all torch CUDA tensors."""
+        import torch
+        n = int(radiance_bg.shape[0])
+        if out is None:
+            out = torch.empty_like(radiance_bg)
+        _check(lib.fire_inject(self._h, _dptr(radiance_bg, torch.float32), _dptr(wv_bin),
+                               _dptr(alpha, torch.float32), _dptr(T, torch.float32), n,
+                               _dptr(out, torch.float32), _stream_ptr(stream)), "fire_inject")
+        return out
+
     def wv_depth_table(self, lams=None):
         """fire_wv_depth_table: the 940 nm depth of every water-vapour bin."""
         D = np.empty(self.n_wv, dtype=np.float32)
         lp = None if lams is None else np.ascontiguousarray(lams, dtype=np.float32)
         _check(lib.fire_wv_depth_table(self._h, None if lp is None else lp.ctypes.data, D.ctypes.data),
-               "fire_wv_depth_table")
+               "fire_wv_depth_table", "fire_inject", "fire_hfdi")
         return D
 
     def wv_presolve(self, radiance, width, height, block=12, lams=None, depth=False, out=None,

@@ -12,7 +12,7 @@ oracle's forward model (tests) or the library's own forward kernel (bench).
 from .scenes import (  # noqa: F401
     N_BANDS_DEFAULT, TGRID_LO, TGRID_HI, band_centres, make_tables, Tables,
     make_config1_truth, make_config2_truth, make_config3_scenes,
-    make_config5_fine_truth, make_injection_truth, Truth, noise_normals,
+    make_config5_fine_truth, make_injection_experiment, Truth, noise_normals,
     splitmix64, counter_u64, counter_uniform, STREAM_NOISE, STREAM_MLP,
     wv_quantise, state_bounds, block_mean_shape,
 )

@@ -189,12 +189,15 @@ class Tables:
 
 
 def make_tables(n_bands=N_BANDS_DEFAULT, n_wv=16, n_tgrid=64, cos_sza=COS_SZA_DEFAULT,
-                path_reflectance=False, sat_level=None):
-    """Band tables for one scene; every array fp32, C-contiguous."""
+                path_reflectance=False, sat_level=None, wv_values=None, flat_reflectance=None):
+    """Band tables for one scene; every array fp32, C-contiguous. wv_values
+    (cm) replaces the n_wv bin centres; flat_reflectance makes every
+    endmember that constant (a flat surface whatever the fractions)."""
     centres = band_centres(n_bands)
     fine = _fine_grid(centres)
     e0 = _srf_resample(fine, solar_irradiance_fine(fine), centres)
-    wv = wv_bin_centres(n_wv)
+    wv = wv_bin_centres(n_wv) if wv_values is None else np.asarray(wv_values, np.float64)
+    n_wv = wv.size
     tau_f = np.stack([transmittance_fine(fine, w) for w in wv])
     tau_up = _srf_resample(fine, tau_f, centres)
     tau_down = _srf_resample(fine, tau_f ** (1.0 / cos_sza), centres)
@@ -205,6 +208,8 @@ def make_tables(n_bands=N_BANDS_DEFAULT, n_wv=16, n_tgrid=64, cos_sza=COS_SZA_DE
         rho_atm = np.zeros((n_wv, n_bands))
         sph = np.zeros((n_wv, n_bands))
     endm = _srf_resample(fine, endmembers_fine(fine), centres)
+    if flat_reflectance is not None:
+        endm = np.full_like(endm, float(flat_reflectance))
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)  # noqa: E731
     sat = None if sat_level is None else f32(np.full(n_bands, float(sat_level)))
     return Tables(f32(centres), f32(e0), float(cos_sza), f32(tau_down), f32(tau_up),
@@ -289,13 +294,20 @@ def make_config1_truth(seed=0, width=64, height=64, n_endm=3, n_wv=16, fire_frac
     return tr
 
 
-def make_injection_truth(seed=7, n=2048, n_endm=3, n_wv=16, t_range=(500.0, 1700.0),
-                         alpha_range=(1e-3, 0.5)):
-    """Eq. (inject) analog: every pixel carries one injected temperature
-    U[500, 1700] K over a synthetic background (Sec. 2.8)."""
-    tr = make_config1_truth(seed, n, 1, n_endm, n_wv, fire_frac=1.0, t_range=t_range,
-                            alpha_range=alpha_range)
-    return tr
+def make_injection_experiment(seed=7, n=8192, n_endm=3, n_wv=16, t_range=(500.0, 1700.0),
+                              alpha_range=(0.01, 1.0)):
+    """The injection experiment of Sec. 2.8 / 3.1 (Eq. inject): n non-fire
+    background pixels (water vapour U[0.5, 3] cm, Dirichlet surface, no
+    fire) and, for each, an injected temperature T ~ U[t_range] and a
+    gray-body scaling alpha ~ U[alpha_range] (the paper draws both uniformly
+    and gives no alpha range). Returns (truth of the backgrounds, alpha, T);
+    the caller forms the background radiance (forward model plus noise) and
+    adds alpha tau_up B(lambda, T) to it."""
+    tr = make_config1_truth(seed, n, 1, n_endm, n_wv, fire_frac=0.0)
+    rng = np.random.default_rng(seed + 1000)
+    T = rng.uniform(*t_range, n)
+    alpha = rng.uniform(*alpha_range, n)
+    return tr, alpha, T
 
 
 def _smooth_field(rng, width, height, lo, hi, n_modes=6):

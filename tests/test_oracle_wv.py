@@ -1,8 +1,9 @@
-"""Pins of the oracle's water-vapour presolve (Sec. 2.5): the depth table
-against flat-surface radiance formed here in closed form, the block median
-and the quantisation against an independent numpy restatement (single
-precision where the decision is an integer), recovery of known per-block
-bins from the forward model, ragged edge blocks and empty blocks."""
+"""Pins of the oracle's input-side steps. The water-vapour presolve (Sec.
+2.5): the depth table against flat-surface radiance formed here in closed
+form, the block median and the quantisation against an independent numpy
+restatement (single precision where the decision is an integer), recovery
+of known per-block bins from the forward model, ragged edge blocks and empty
+blocks. The thermal injection (Eq. inject) against the forward model."""
 import numpy as np
 import pytest
 
@@ -158,3 +159,19 @@ def test_even_block_takes_the_lower_median():
     bins[0] = 9
     got, _ = oracle.wv_presolve(t, _flat_radiance(t, bins), 12, 12)
     assert np.all(got == 9)
+
+
+def test_injection_is_the_forward_models_thermal_term():
+    """Eq. (inject) onto a noise-free background equals the forward model of
+    the same surface with that single-temperature fire (alpha, T): the
+    thermal term alpha tau_up B(lambda, T) is the only difference; alpha = 0
+    returns the background."""
+    t = synth.make_tables()
+    tr, alpha, T = synth.make_injection_experiment(seed=3, n=64)
+    bg = oracle.forward(t, 1, tr.state1(), tr.wv_bin).astype(np.float32)
+    inj = oracle.inject(t, bg, tr.wv_bin, alpha, T)
+    st = tr.state1()
+    st[:, 3], st[:, 4] = alpha, T
+    fire = oracle.forward(t, 1, st, tr.wv_bin)
+    assert np.allclose(inj, fire, rtol=2e-7, atol=1e-12)
+    assert np.array_equal(oracle.inject(t, bg, tr.wv_bin, np.zeros(64), T), bg)
