@@ -500,7 +500,7 @@ class Context:
         D = np.empty(self.n_wv, dtype=np.float32)
         lp = None if lams is None else np.ascontiguousarray(lams, dtype=np.float32)
         _check(lib.fire_wv_depth_table(self._h, None if lp is None else lp.ctypes.data, D.ctypes.data),
-               "fire_wv_depth_table", "fire_inject", "fire_hfdi")
+               "fire_wv_depth_table")
         return D
 
     def wv_presolve(self, radiance, width, height, block=12, lams=None, depth=False, out=None,
