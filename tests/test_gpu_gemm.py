@@ -57,3 +57,16 @@ def test_gemm_accumulate(env):
     torch.cuda.synchronize()
     ref = 1.0 + A.float() @ B.float().T
     assert torch.allclose(Cf, ref, atol=1e-3, rtol=1e-5)
+
+
+def test_gemm_rejects_unaligned_operands(env):
+    """Operand bases must be 16-byte aligned (TMA and the 16-byte copies):
+    a base 8 bytes off is refused before any launch."""
+    torch, fr = env
+    flat = torch.zeros(64 * 64 + 4, device="cuda", dtype=torch.bfloat16)
+    A = flat[4:].view(64, 64)             # contiguous, 8 bytes past a 16-byte boundary
+    assert A.is_contiguous() and A.data_ptr() % 16 == 8
+    B = torch.zeros(16, 64, device="cuda", dtype=torch.bfloat16)
+    Cf = torch.zeros(64, 16, device="cuda")
+    with pytest.raises(fr.FireError):
+        fr.gemm_bf16(A, B, Cf=Cf)
