@@ -362,7 +362,7 @@ def adam_figure(torch, firert, t, tr, rad, wv_d, args, stream, tune, lm_fire, sa
     ctx = firert.Context(t, firert.default_config(solver="adam"))
     ctx.set_tuning(tune["variant"], tune["claim"])
     out = ctx.alloc_outputs(n)
-    ms = time_fits(torch, lambda: ctx.retrieve(rad, wv_d, outputs=out), max(2, args.steps // 2), stream)
+    ms = time_fits(torch, lambda: ctx.retrieve(rad, wv_d, outputs=out), args.extra_steps, stream)
     stats = ctx.stats()
     fire = np.flatnonzero(tr.kind != 0)
     truth = tr.mix[fire, 0] if tr.kind.max() == 2 else tr.single[fire, 1]
@@ -598,9 +598,9 @@ def batched_figure(torch, ctx, t, args, stream, tune):
     n = sum(int(r.shape[0]) for r, _ in scenes)
     ctx.retrieve_batch(scenes, outputs=outs)          # warm-up
     torch.cuda.synchronize()
-    direct_ms = time_fits(torch, lambda: ctx.retrieve_batch(scenes, outputs=outs), 2, stream)
+    direct_ms = time_fits(torch, lambda: ctx.retrieve_batch(scenes, outputs=outs), 1, stream)
     g = ctx.capture_batch(scenes, outs)
-    graph_ms = time_fits(torch, lambda: g.launch(stream), max(2, args.steps // 2), stream)
+    graph_ms = time_fits(torch, lambda: g.launch(stream), args.extra_steps, stream)
     stats = ctx.stats()
     allo, allg, allk = [], [], []
     t0 = time.perf_counter()
@@ -663,7 +663,7 @@ def coarse_figure(torch, ctx, t, args, stream, mlp=None):
     Ld = torch.from_numpy(Lc).cuda()
     wd = torch.from_numpy(wvc.astype(np.int16)).cuda()
     out = ctx.alloc_outputs(nc)
-    ms = time_fits(torch, lambda: ctx.retrieve(Ld, wd, outputs=out), max(2, args.steps // 2), stream)
+    ms = time_fits(torch, lambda: ctx.retrieve(Ld, wd, outputs=out), max(3, args.extra_steps), stream)
     g = {k: v.cpu().numpy() for k, v in out.items()}
     kind_f = tr.kind.reshape(H, W)[: ch * B, : Wc].reshape(ch, B, cw, B)
     kind_c = (kind_f.max(axis=(1, 3)) > 0).astype(np.uint8).reshape(-1)
@@ -685,7 +685,7 @@ def coarse_figure(torch, ctx, t, args, stream, mlp=None):
     if mlp is not None:
         ctx.set_mlp(mlp)
         ms_l = time_fits(torch, lambda: ctx.retrieve(Ld, wd, outputs=out, learned_start=True),
-                         max(2, args.steps // 2), stream)
+                         max(3, args.extra_steps), stream)
         gl = {k: v.cpu().numpy() for k, v in out.items()}
         learned = {"value": nc / (ms_l / 1e3), "ms_per_fit": ms_l,
                    "fallback_frac": float(np.mean((gl["status"] & 32) > 0)),
@@ -753,6 +753,8 @@ def main():
     ap.add_argument("--batch-max-px", type=int, default=None, help="cap of the batched stream's pixels")
     ap.add_argument("--batch-sample", type=int, default=300,
                     help="oracle pixels per batched scene (half fire pixels)")
+    ap.add_argument("--extra-steps", type=int, default=2,
+                    help="timed repetitions of each secondary figure (after one untimed)")
     ap.add_argument("--inject-px", type=int, default=262144, help="pixels of the injection experiment")
     ap.add_argument("--inject-sample", type=int, default=1500, help="oracle pixels of the injection experiment")
     ap.add_argument("--adam-sample", type=int, default=2000,
