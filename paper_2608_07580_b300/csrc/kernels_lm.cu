@@ -213,20 +213,6 @@ struct LMResult {
   float cost, cdata;
 };
 
-// FP64 re-solve of an ill-conditioned step, kept out of line (cold path) so
-// the hot loop stays small in the instruction cache.
-template <int P>
-struct Solve64 {
-  float H[P * (P + 1) / 2], g[P], D[P], dr[P];
-  bool pin[P];
-  float lam, kap;
-};
-
-template <int P>
-__device__ __noinline__ bool solve_fp64(Solve64<P> &q) {
-  return damped_solve<P, double>(q.H, q.g, q.lam, q.D, q.pin, q.dr, q.kap);
-}
-
 // State of the damped iteration shared by the two stage drivers.
 template <int P>
 struct LMIter {
@@ -241,12 +227,18 @@ struct LMIter {
 // kFloorC), then the damped projected-Newton step and the
 // trial point xt with its predicted decrease. Returns false when the fit
 // stops (converged, step below tol_x, damping overflow, iteration cap).
-template <class St>
-__device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, const KConfig &c,
-                                           const float (&x)[St::NX], const float (&H)[St::NH],
-                                           const float (&g)[St::P], const float (&gf)[St::P], int m,
-                                           float cst, int max_it, LMIter<St::P> &L,
-                                           float (&xt)[St::NX]) {
+// T is the precision of the step solve. In FP32 an ill-conditioned or
+// indefinite damped matrix sets want64 and returns at once, leaving the
+// iteration's state as it is, so that the FP64 instantiation (out of line:
+// next_trial64) takes the whole step from there; keeping the rare FP64 path
+// out of this function keeps the hot loop's registers free (with the FP64
+// call inline the solve took 5,400 instead of 3,400 cycles per trial).
+template <class St, typename T>
+__device__ __forceinline__ bool next_trial_t(const St &S, const Grp<St::GL> &gp, const KConfig &c,
+                                             const float (&x)[St::NX], const float (&H)[St::NH],
+                                             const float (&g)[St::P], const float (&gf)[St::P], int m,
+                                             float cst, int max_it, LMIter<St::P> &L,
+                                             float (&xt)[St::NX], bool &want64) {
   constexpr int P = St::P, NX = St::NX;
 #pragma unroll 1
   while (L.it < max_it) {
@@ -289,31 +281,13 @@ __device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, c
       for (int a = 0; a < P; a++) nf += !pin[a];
       if (nf == 0) break;
       float kap = 0.f;
-      ok = damped_solve<P, float>(H, g, L.lam, D, pin, dr, kap);
-      if (!ok || !(kap <= c.kappa_max)) {
-        // FP64 re-solve by the group's first lane only (the FP64 pipe is a
-        // sixty-fourth of the FP32 one), the step broadcast to the group
-        bool ok64 = false;
-        if (gp.sub == 0) {
-          Solve64<P> q;
-#pragma unroll
-          for (int i = 0; i < St::NH; i++) q.H[i] = H[i];
-#pragma unroll
-          for (int a = 0; a < P; a++) {
-            q.g[a] = g[a];
-            q.D[a] = D[a];
-            q.pin[a] = pin[a];
-            q.dr[a] = dr[a];
-          }
-          q.lam = L.lam;
-          ok64 = solve_fp64<P>(q);
-#pragma unroll
-          for (int a = 0; a < P; a++) dr[a] = q.dr[a];
+      ok = damped_solve<P, T>(H, g, L.lam, D, pin, dr, kap);
+      if constexpr (sizeof(T) == sizeof(float)) {
+        if (!ok || !(kap <= c.kappa_max)) {
+          want64 = true;
+          return false;
         }
-        const int lead = gp.lane & ~(St::GL - 1);
-        ok = __shfl_sync(gp.mask, ok64 ? 1 : 0, lead) != 0;
-#pragma unroll
-        for (int a = 0; a < P; a++) dr[a] = __shfl_sync(gp.mask, dr[a], lead);
+      } else {
         L.used64 = true;
         L.n64++;
       }
@@ -377,6 +351,49 @@ __device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, c
   });
   if (small) L.status = PX_CONVERGED;
   return false;
+}
+
+// The LM step with its solves in FP64, out of line: inputs and outputs in
+// one struct, so that the caller's arrays are not address-taken
+template <class St>
+struct Step64 {
+  float x[St::NX], H[St::NH], g[St::P], gf[St::P], xt[St::NX];
+  int m, max_it;
+  float cst;
+  LMIter<St::P> L;
+};
+template <class St>
+__device__ __noinline__ bool next_trial64(const St &S, const Grp<St::GL> &gp, const KConfig &c,
+                                          Step64<St> &q) {
+  bool unused = false;
+  return next_trial_t<St, double>(S, gp, c, q.x, q.H, q.g, q.gf, q.m, q.cst, q.max_it, q.L, q.xt, unused);
+}
+
+template <class St>
+__device__ __forceinline__ bool next_trial(const St &S, const Grp<St::GL> &gp, const KConfig &c,
+                                           const float (&x)[St::NX], const float (&H)[St::NH],
+                                           const float (&g)[St::P], const float (&gf)[St::P], int m,
+                                           float cst, int max_it, LMIter<St::P> &L,
+                                           float (&xt)[St::NX]) {
+  bool want64 = false;
+  const bool go = next_trial_t<St, float>(S, gp, c, x, H, g, gf, m, cst, max_it, L, xt, want64);
+  if (!want64) return go;
+  Step64<St> q;
+#pragma unroll
+  for (int i = 0; i < St::NX; i++) { q.x[i] = x[i]; q.xt[i] = xt[i]; }
+#pragma unroll
+  for (int i = 0; i < St::NH; i++) q.H[i] = H[i];
+#pragma unroll
+  for (int a = 0; a < St::P; a++) { q.g[a] = g[a]; q.gf[a] = gf[a]; }
+  q.m = m;
+  q.max_it = max_it;
+  q.cst = cst;
+  q.L = L;
+  const bool go64 = next_trial64<St>(S, gp, c, q);
+  L = q.L;
+#pragma unroll
+  for (int i = 0; i < St::NX; i++) xt[i] = q.xt[i];
+  return go64;
 }
 
 // Nielsen damping update after a step with gain ratio rho
