@@ -112,7 +112,7 @@ class Config:
     win1: tuple = (350.0, 2500.0)
     win2h: tuple = (900.0, 1800.0)
     win2s: tuple = (1500.0, 2500.0)
-    init_alpha1: float = 0.01
+    init_alpha1: float = 0.0
     init_T1: float = 800.0
     init_sigma: float = 100.0
     init_mu_h_floor: float = 1000.0

@@ -384,7 +384,7 @@ void fire_default_priors(fire_priors_t *p, int32_t K, int32_t nt, float tlo, flo
     p->pm2[i] = i == 5 ? -1.f : 0.f;
     p->pp2[i] = i == 5 ? 1e-6f : 1.f;
   }
-  p->init_alpha1 = 0.01f;
+  p->init_alpha1 = 0.f;   // no fire until the data say so (the prior's mean for alpha)
   p->init_T1 = 800.f;
   p->init_sigma = 100.f;
   p->init_mu_h_floor = 1000.f;
