@@ -1017,6 +1017,11 @@ static void retrieve_pixel(const orc_tables_t *t, const orc_config_t *c, const d
     double T1 = x1[K + 1];
     double e = (x2[0] > x2[2]) ? (T1 - x2[2]) / (x2[0] - x2[2]) : 0.5;
     x2[4] = e < c->init_eta_lo ? c->init_eta_lo : (e > c->init_eta_hi ? c->init_eta_hi : e);
+    /* stage 1 found no thermal signal (alpha1 on its lower bound, so T1
+     * says nothing): the mixture shape starts at the prior's means, where
+     * its fit ends while the data give alpha no signal either */
+    if (x1[K] <= c->lo1[K])
+      for (int k = 0; k < 5; k++) x2[k] = lo2[k] + 0.5 * (hi2[k] - lo2[k]) * (c->pm2[k] + 1.0);
   } else {
     if (x2[4] < lo2[4]) x2[4] = lo2[4];
     if (x2[4] > hi2[4]) x2[4] = hi2[4];

@@ -1767,6 +1767,13 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       x[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
       const float e = x[0] > x[2] ? (T1 - x[2]) / (x[0] - x[2]) : 0.5f;
       x[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
+      // stage 1 found no thermal signal (alpha1 on its bound, T1 says
+      // nothing): the mixture shape starts at the prior's means, where its
+      // fit ends while the data give alpha no signal either
+      if (x1[K] <= c.lo1[K]) {
+#pragma unroll
+        for (int k = 0; k < 5; k++) x[k] = fmaf(0.5f * (c.hi2[k] - c.lo2[k]), c.pm2[k] + 1.f, c.lo2[k]);
+      }
       // a given start replaces the derived one; the learned start only
       // seeds stage 1, so that stage 2 starts where plain LM's does
       const float *ini = ref.init;
@@ -2418,6 +2425,13 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       x[5] = fminf(fmaxf(x1[K], c.lo2[5]), c.hi2[5]);
       const float e = x[0] > x[2] ? (T1 - x[2]) / (x[0] - x[2]) : 0.5f;
       x[4] = fminf(fmaxf(e, c.init_eta_lo), c.init_eta_hi);
+      // stage 1 found no thermal signal (alpha1 on its bound, T1 says
+      // nothing): the mixture shape starts at the prior's means, where its
+      // fit ends while the data give alpha no signal either
+      if (x1[K] <= c.lo1[K]) {
+#pragma unroll
+        for (int k = 0; k < 5; k++) x[k] = fmaf(0.5f * (c.hi2[k] - c.lo2[k]), c.pm2[k] + 1.f, c.lo2[k]);
+      }
       const float *ini = ref.init;
       if (ini && !p.s.init_best) {
 #pragma unroll
