@@ -1394,6 +1394,52 @@ __device__ __forceinline__ int setup1(Stage1<K, G> &s1, const PixCtx &pc, const 
   return nu;
 }
 
+// The ungated intake in one pass over the pixel's radiance row: the
+// finiteness of every band (this lane's part, fin), the stage-1 buffers as
+// setup1 builds them, and the stage-2 band count as count2 forms it (the
+// stage-2 bands lie inside the stage-1 range). Returns nothing but through
+// the references; n1u, n2u and the prior scale are group totals.
+template <int K, int G>
+__device__ __forceinline__ void setup1_fused(Stage1<K, G> &s1, const PixCtx &pc, const Grp<G> &gp,
+                                             const float *row, bool &fin, int &n1u, int &n2u) {
+  const KTables &t = *pc.t;
+  const KConfig &c = *pc.c;
+  float nv = 0.f;
+  int nu = 0, nu2 = 0;
+  bool f = true;
+  for (int i = gp.sub; i < s1.nbs; i += G) {
+    float Lv = 0.f, wv = 0.f;
+    if (i < t.n1) {
+      const int b = t.b1lo + i;
+      const float L = __ldg(row + b);
+      f = f && isfinite(L);
+      const bool unsat = !(t.sat && L >= __ldg(t.sat + b));
+      const bool ok = pc.img[t.lay.off_win1 + b] > 0.f && unsat;
+      const float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
+      Lv = L;
+      wv = ok ? (c.weighted ? 1.f / (c.has_nsd ? c.nsd[b] * c.nsd[b] : var) : 1.f) : 0.f;
+      if (ok) { nv += var; nu++; }
+      if (b >= t.b2lo && b < t.b2lo + t.n2) nu2 += (pc.img[t.lay.off_win2 + b] > 0.f && unsat) ? 1 : 0;
+    }
+    s1.Lo(i) = Lv;
+    s1.W(i) = wv;
+#pragma unroll
+    for (int k = 2; k < 4; k++) s1.bb[k * s1.nbs + i] = 0.f;
+  }
+  // the bands outside the stage-1 range: finiteness only
+  for (int b = gp.sub; b < t.b1lo; b += G) f = f && isfinite(__ldg(row + b));
+  for (int b = t.b1lo + t.n1 + gp.sub; b < t.nb; b += G) f = f && isfinite(__ldg(row + b));
+  fin = f;
+  nv = gp.sum1(nv);
+  n1u = gp.isum(nu);
+  n2u = gp.isum(nu2);
+  s1.psc = c.weighted ? 1.f : nv / (float)max(n1u, 1);
+  s1.sf = 0.5f * (c.hi1[0] - c.lo1[0]);
+  s1.sa = 0.5f * (c.hi1[K] - c.lo1[K]);
+  s1.sT = 0.5f * (c.hi1[K + 1] - c.lo1[K + 1]);
+  gp.sync();
+}
+
 // stage-2 band count (mask x window) without building the stage state
 template <int G>
 __device__ __forceinline__ int count2(const PixCtx &pc, const Grp<G> &gp, const float *row) {
@@ -1570,7 +1616,15 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
       const bool wv_ok = wvb < t.nwv;   // an out-of-range bin is an invalid input
       pc.wvrow = wvs + (size_t)(wv_ok ? wvb : 0) * t.nb;
       bool fin = true;
-      for (int b = gp.sub; b < t.nb; b += G) fin = fin && isfinite(__ldg(row + b));
+      int n1u = 0, n2u = 0;
+      // every pixel is fitted (no gate) and the stage-2 bands lie inside the
+      // stage-1 range: one pass builds the stage-1 buffers with the
+      // finiteness test; gated, most pixels stop at the gate, so the
+      // finiteness pass comes first
+      const bool fuse = !p.s.gate && t.b2lo >= t.b1lo && t.b2lo + t.n2 <= t.b1lo + t.n1;
+      if (fuse) setup1_fused(S, pc, gp, row, fin, n1u, n2u);
+      else
+        for (int b = gp.sub; b < t.nb; b += G) fin = fin && isfinite(__ldg(row + b));
       fin = gp.all(fin) && wv_ok;
       const float Lh = __ldg(row + t.bh), Ll = __ldg(row + t.bl);
       float hf = (Lh - Ll) / (Lh + Ll);
@@ -1582,8 +1636,10 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
       } else if (p.s.gate && !(hf >= c.hfdi_thresh)) {
         status = PX_NOT_CANDIDATE;
       } else {
-        const int n1u = setup1(S, pc, gp, row);
-        const int n2u = count2(pc, gp, row);
+        if (!fuse) {
+          n1u = setup1(S, pc, gp, row);
+          n2u = count2(pc, gp, row);
+        }
         if (n1u <= K + 2 || n2u <= 6) status = PX_ALL_MASKED;
         else fit = true;
       }
