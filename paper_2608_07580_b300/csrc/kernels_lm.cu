@@ -1925,8 +1925,8 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
 // increment), are one dense product per CTA and round once the pixels of
 // the CTA evaluate together:
 //   D[band b][8 s + k'] = sum_j Bgrid[b][j] C[8 s + k'][j], k' = k (even s) or k ^ 4 (odd s),
-// M = 128 bands per tile (two tiles cover up to 256 bands), N = 16 pixel
-// slots x 8 coefficients, K = 64 nodes. Both operands are split into three
+// M = 128 bands per tile (two tiles cover up to 256 bands), N = 8 pixel
+// slots of a cohort x 8 coefficients, K = 64 nodes. Both operands are split into three
 // bf16 parts (x = x0 + x1 + x2, each part the bf16 rounding of what the
 // previous ones leave, 27 significant bits together) and the six products
 // of parts whose orders add up to at most 2 are accumulated in FP32 in
@@ -1940,18 +1940,25 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
 // 8 rows of the coefficient operand; (2) one thread issues the MMAs and
 // commits them to an mbarrier; (3) with the sums in tensor memory, warp w
 // reads lane quarter w & 3 (32 bands of each tile) and forms, for the 8
-// pixel slots of its half, each band's residual, Jacobian row and
-// contributions to J^T W J, J^T W r, the cost and the increment-form
-// decrease; a reduce-scatter across the warp leaves one of the 32 sums per
-// lane, written as the quarter's partial; (4) each group adds its four
-// quarters' partials.
+// pixel slots of its cohort, each band's residual, Jacobian row and
+// contributions to J^T J, J^T r, the cost and the increment-form decrease;
+// a reduce-scatter across the warp leaves one of the 32 sums per lane,
+// written as the quarter's partial; (4) each group adds its four quarters'
+// partials.
+//
+// This path fits the unweighted loss (every used band weight 1): a pixel's
+// slot holds only y (radiance minus the fixed solar term) and tau_up, both
+// 0 on a band the window or saturation masks, so a masked band adds exact
+// zeros and no weight buffer is needed; the weighted loss runs the FP32
+// stage 2. With the two band buffers and no table image in shared memory,
+// three cohorts fit one SM.
 namespace tcs2 {
-constexpr int G = 16, kWarps = 8, kSlots = kWarps * 32 / G;   // 16 pixels per CTA
-// two cohorts of 4 warps (one per TMEM lane quarter) and 8 pixel slots each,
-// with their own product, mbarrier and named barrier: a cohort waits only
-// for its own 8 pixels, and one cohort's CUDA-core work overlaps the other's
-// product
-constexpr int kCohorts = 2, kCoSlots = kSlots / kCohorts, kCoThreads = kWarps * 32 / kCohorts;
+constexpr int G = 16, kWarps = 12, kSlots = kWarps * 32 / G;   // 24 pixels per CTA
+// three cohorts of 4 warps (one per TMEM lane quarter) and 8 pixel slots
+// each, with their own product, mbarrier and named barrier: a cohort waits
+// only for its own 8 pixels, and the cohorts' CUDA-core work overlaps the
+// others' products and step logic
+constexpr int kCohorts = 3, kCoSlots = kSlots / kCohorts, kCoThreads = kWarps * 32 / kCohorts;
 constexpr int kN = kSlots * 8;            // coefficient rows
 constexpr int kNc = kCoSlots * 8;         // D columns of one cohort and band tile
 constexpr int kCoPart = kN * 128;         // bytes of one part of the coefficient operand
@@ -1959,27 +1966,64 @@ constexpr int kPrm = 16;                  // per-slot parameters of the band pha
 constexpr int kPartStride = 4 * 32 + 16;  // per-slot partial sums [4 quarters][32], padded
 constexpr long long kSpinMMA = 1ll << 24;
 
-// per-slot block: band buffers [5][nbs] (y, tau_up, weight, residuals),
-// the ne slot, the parameters; stride congruent to 16 modulo 32 floats so
-// the two groups of a warp hit different banks
+// per-slot block: band buffers [2][nbs] (y, tau_up), two ne slots (the
+// normal equations of the accepted state and of the trial, swapped on
+// acceptance, so that they need no registers), the parameters; stride
+// congruent to 16 modulo 32 floats so the two groups of a warp hit
+// different banks
 __host__ __device__ __forceinline__ int slot_floats(const KTables &t) {
-  const int f = 5 * band_slots(t.n2, G) + kNE2 + kPrm;
+  const int f = 2 * band_slots(t.n2, G) + 2 * kNE2 + kPrm;
   return f + ((16 - f % 32) % 32 + 32) % 32;
 }
 struct Lay {
-  int head_bytes;          // table image up to the Planck grid
   int pl_bytes, co_bytes;  // operands (offsets from the 1024-aligned base)
   int slots_off, parts_off, total;   // bytes from the aligned base; total dynamic bytes
 };
 __host__ __device__ __forceinline__ Lay layout(const KTables &t) {
   Lay L;
-  L.head_bytes = image_floats(t, 1) * 4;
   L.pl_bytes = 3 * t.plrows * 128;
   L.co_bytes = 3 * kCoPart;
   L.slots_off = L.pl_bytes + L.co_bytes;
   L.parts_off = L.slots_off + kSlots * slot_floats(t) * 4;
-  L.total = L.head_bytes + 1024 + L.parts_off + kSlots * kPartStride * 4;
+  L.total = 1024 + L.parts_off + kSlots * kPartStride * 4;
   return L;
+}
+
+// slot set-up of a pixel: y = L - Ls(x_surf) (solar term fixed, Eq. solar)
+// and tau_up on the used bands, 0 and 0 on the masked ones; the prior scale
+// (mean noise variance of the used bands). The table image is read from
+// global memory (once per pixel). Returns the used-band count.
+template <int K>
+__device__ __forceinline__ int setup_slot(const KTables &t, const KConfig &c, const Grp<G> &gp,
+                                          const float4 *wvrow, const float *row, const float (&xs)[K],
+                                          float *sb, int nbs, float &psc) {
+  float nv = 0.f;
+  int nu = 0;
+  for (int i = gp.sub; i < nbs; i += G) {
+    float yv = 0.f, tv = 0.f;
+    if (i < t.n2) {
+      const int b = t.b2lo + i;
+      const float L = __ldg(row + b);
+      const bool ok = __ldg(t.image + t.lay.off_win2 + b) > 0.f && !(t.sat && L >= __ldg(t.sat + b));
+      if (ok) {
+        const float4 q = __ldg(wvrow + b);
+        float rho = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++) rho = fmaf(xs[k], __ldg(t.image + t.lay.off_endm + k * t.nb + b), rho);
+        yv = L - (q.y + q.x * rho / (1.f - q.z * rho));
+        tv = q.w;
+        nv += c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
+        nu++;
+      }
+    }
+    sb[i] = yv;
+    sb[nbs + i] = tv;
+  }
+  nv = gp.sum1(nv);
+  nu = gp.isum(nu);
+  psc = nv / (float)max(nu, 1);
+  gp.sync();
+  return nu;
 }
 
 __device__ __forceinline__ void split3(float v, __nv_bfloat16 &p0, __nv_bfloat16 &p1,
@@ -2001,7 +2045,7 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
 // band-phase parameters of the slot
 __device__ __forceinline__ void coef(const KTables &t, const KConfig &c, const Grp<G> &gp,
                                      const float (&x)[6], const float (&xt)[6], unsigned char *co,
-                                     int slot, float *prm, int rn) {
+                                     int slot, float *prm) {
   const float mh = xt[0], sh = xt[1], ms = xt[2], ss = xt[3], eta = xt[4], al = xt[5];
   const float eo = x[4];
   const float ih = 1.f / x[1], iht = 1.f / sh, is = 1.f / x[3], ist = 1.f / ss;
@@ -2081,7 +2125,7 @@ __device__ __forceinline__ void coef(const KTables &t, const KConfig &c, const G
   }
   // band-phase parameters: [1] eta, [2] alpha, [3] alpha - alpha_o, [4..7]
   // the Jacobian factors of mu_h, s_h, mu_s, s_s, [8] [9] z scales of eta and
-  // alpha, [10] the residual buffer written; [0] (the flag) is set by the caller
+  // alpha; [0] (the flag) is set by the caller
   const float sc0 = 0.5f * (c.hi2[0] - c.lo2[0]), sc1 = 0.5f * (c.hi2[1] - c.lo2[1]);
   const float sc2 = 0.5f * (c.hi2[2] - c.lo2[2]), sc3 = 0.5f * (c.hi2[3] - c.lo2[3]);
   const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
@@ -2096,10 +2140,9 @@ __device__ __forceinline__ void coef(const KTables &t, const KConfig &c, const G
     case 7: v = (1.f - eta) * (iss2 / ss) * sc3; break;
     case 8: v = 0.5f * (c.hi2[4] - c.lo2[4]); break;
     case 9: v = 0.5f * (c.hi2[5] - c.lo2[5]); break;
-    case 10: v = (float)rn; break;
     default: break;
   }
-  if (gp.sub >= 1 && gp.sub <= 10) prm[gp.sub] = v;
+  if (gp.sub >= 1 && gp.sub <= 9) prm[gp.sub] = v;
 }
 
 // (2) the six part products of one cohort (its 64 coefficient rows),
@@ -2163,7 +2206,7 @@ __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slo
 #pragma unroll 1
   for (int s = 8 * h; s < 8 * h + 8; s++) {
     float *sb = slots + s * sstride;
-    const float *prm = sb + 5 * nbs + kNE2;
+    const float *prm = sb + 2 * nbs + 2 * kNE2;
     if (prm[0] == 0.f) continue;
     float v[2][8];
     // the cohort's columns start at h * 64 * ntile; tile m at + 64 m
@@ -2183,10 +2226,9 @@ __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slo
     }
     const float eta = prm[1], al = prm[2], da = prm[3];
     const float f0 = prm[4], f1 = prm[5], f2 = prm[6], f3 = prm[7], sc4 = prm[8], sc5 = prm[9];
-    const int rn = prm[10] != 0.f ? 1 : 0;
-    const float *Y = sb, *TU = sb + nbs, *W = sb + 2 * nbs;
-    const float *ro = sb + (4 - rn) * nbs;
-    float *rw = sb + (3 + rn) * nbs;
+    const float *Y = sb, *TU = sb + nbs;
+    // [0, 21) J^T J, [21, 27) J^T r, 27 cost, 28 decrease, 29 sum of squared
+    // thermal model values; 30, 31 unused
     float acc[32];
 #pragma unroll
     for (int i = 0; i < 32; i++) acc[i] = 0.f;
@@ -2194,17 +2236,18 @@ __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slo
     for (int m = 0; m < 2; m++) {
       const int b = 128 * m + 32 * q + l;
       if (m < ntile && b < t.n2) {
-        const float wv = W[b];
-        if (wv > 0.f) {
+        const float tuv = TU[b];
+        if (tuv > 0.f) {
           const float *S = v[m];
           const float Bh = S[0], Bs = S[3];
           const float Bm = eta * Bh + (1.f - eta) * Bs;
-          const float tuv = TU[b];
           const float atu = al * tuv;
-          const float r = Y[b] - atu * Bm;
-          rw[b] = r;
+          const float M = atu * Bm;
+          const float r = Y[b] - M;
+          // decrease from the current state in increment form:
+          // dM (2 r + dM) = r_o^2 - r^2 with r_o = r + dM
           const float dM = tuv * fmaf(al, S[6], da * (Bm - S[6]));
-          acc[NH + P + 2] = fmaf(wv * dM, 2.f * ro[b] - dM, acc[NH + P + 2]);
+          acc[NH + P + 1] = fmaf(dM, fmaf(2.f, r, dM), acc[NH + P + 1]);
           float J[6];
           J[0] = atu * S[1] * f0;
           J[1] = atu * S[2] * f1;
@@ -2212,18 +2255,13 @@ __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slo
           J[3] = atu * S[5] * f3;
           J[4] = atu * (Bh - Bs) * sc4;
           J[5] = tuv * Bm * sc5;
-          const float wr = wv * r;
-          const float wM = wv * atu * Bm;
-          acc[NH + P] = fmaf(wr, r, acc[NH + P]);
-          acc[NH + P + 1] = fmaf(r, r, acc[NH + P + 1]);
-          acc[NH + P + 3] = fmaf(wM, wM, acc[NH + P + 3]);
-          acc[NH + P + 4] += wv;
+          acc[NH + P] = fmaf(r, r, acc[NH + P]);
+          acc[NH + P + 2] = fmaf(M, M, acc[NH + P + 2]);
 #pragma unroll
           for (int a = 0; a < P; a++) {
-            acc[NH + a] = fmaf(J[a], wr, acc[NH + a]);
-            const float wj = wv * J[a];
+            acc[NH + a] = fmaf(J[a], r, acc[NH + a]);
 #pragma unroll
-            for (int b2 = a; b2 < P; b2++) acc[up<P>(a, b2)] = fmaf(wj, J[b2], acc[up<P>(a, b2)]);
+            for (int b2 = a; b2 < P; b2++) acc[up<P>(a, b2)] = fmaf(J[a], J[b2], acc[up<P>(a, b2)]);
           }
         }
       }
@@ -2233,9 +2271,10 @@ __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slo
 }
 
 // (4) the slot's totals: H, g and the floor to ne (as the FP32 evaluation),
-// cost, data cost and decrease to the caller
+// cost, data cost and decrease to the caller; nu is the used-band count
+// (the sum of the unit weights)
 __device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, float *ps,
-                                     const float (&xt)[6], float psc, float *ne, float &cst,
+                                     const float (&xt)[6], float psc, int nu, float *ne, float &cst,
                                      float &cd, float &drop) {
   constexpr int NH = 21, P = 6;
   float a = 0.f, b = 0.f;
@@ -2252,10 +2291,10 @@ __device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, float *
 #pragma unroll
   for (int i = 0; i < 32; i++) acc[i] = ps[i];
   cst = acc[NH + P];
-  cd = acc[NH + P + 1];
-  drop = acc[NH + P + 2];
+  cd = acc[NH + P];
+  drop = acc[NH + P + 1];
   float gfl[P];
-  const float m2 = acc[NH + P + 3] / fmaxf(acc[NH + P + 4], 1e-30f);
+  const float m2 = acc[NH + P + 2] / fmaxf((float)nu, 1.f);
 #pragma unroll
   for (int i = 0; i < P; i++) gfl[i] = kFloorC * sqrtf(acc[up<P>(i, i)] * m2);
 #pragma unroll
@@ -2275,8 +2314,8 @@ __device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, float *
   gp.sync();
 }
 
-// CTA set-up: tables and Planck operand staged, coefficient operand zeroed,
-// the MMA mbarrier initialised, tensor memory allocated (128 columns per
+// CTA set-up: Planck operand staged, coefficient operand zeroed, the MMA
+// mbarriers initialised, tensor memory allocated (64 columns per cohort and
 // band tile). Returns false (nothing allocated) if the staging timed out.
 struct Cta {
   unsigned char *base;      // 1024-aligned: Planck operand, coefficient operand, slots, parts
@@ -2302,22 +2341,25 @@ __device__ __forceinline__ bool setup(const LMLaunch &p, float *smem, unsigned l
   // mbar: one per cohort
   const KTables &t = p.t;
   const Lay L = layout(t);
-  const unsigned a = tc::su32(smem) + (unsigned)L.head_bytes;
-  C.base = reinterpret_cast<unsigned char *>(smem) + L.head_bytes + ((1024u - (a & 1023u)) & 1023u);
+  const unsigned a = tc::su32(smem);
+  C.base = reinterpret_cast<unsigned char *>(smem) + ((1024u - (a & 1023u)) & 1023u);
   C.slots = reinterpret_cast<float *>(C.base + L.slots_off);
   C.parts = reinterpret_cast<float *>(C.base + L.parts_off);
   C.sstride = slot_floats(t);
   C.nbs = band_slots(t.n2, G);
   C.ntile = (t.n2 + 127) >> 7;
-  C.cols = C.ntile > 1 ? 256 : 128;
+  // tensor memory: 64 columns per cohort and band tile, allocated as a power of 2
+  C.cols = 32;
+  while (C.cols < kCohorts * kNc * C.ntile) C.cols <<= 1;
   if (cta_err(p.w.err)) return false;
-  if (!stage_tables(t, smem, image_floats(t, 1), bar, p.w.err, p.c.wait_spins, C.base, t.plop,
-                    (unsigned)L.pl_bytes))
+  // only the Planck operand is staged: the slot set-up reads the table image
+  // from global memory
+  if (!stage_tables(t, smem, 0, bar, p.w.err, p.c.wait_spins, C.base, t.plop, (unsigned)L.pl_bytes))
     return false;
   uint4 *co = reinterpret_cast<uint4 *>(C.base + L.pl_bytes);
   for (int i = threadIdx.x; i < L.co_bytes / 16; i += blockDim.x) co[i] = make_uint4(0, 0, 0, 0);
   for (int i = threadIdx.x; i < kSlots; i += blockDim.x)
-    C.slots[i * C.sstride + 5 * C.nbs + kNE2] = 0.f;
+    C.slots[i * C.sstride + 2 * C.nbs + 2 * kNE2] = 0.f;
   if (threadIdx.x == 0) {
     for (int h = 0; h < kCohorts; h++)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(mbar + h)));
@@ -2398,11 +2440,11 @@ __global__ void planck_operand_kernel(const KTables t, const float *image, unsig
 }  // namespace tcs2
 
 // ---- stage 2 with the grid-node sums on the tensor cores: the fit of
-// lm_stage2_kernel (16 lanes per pixel, 8 warps), with the evaluation a
+// lm_stage2_kernel (16 lanes per pixel, 12 warps), with the evaluation a
 // round of each 4-warp cohort (tcs2) so that a cohort's 8 pixels share one
-// product
+// product; unweighted loss only
 template <int K, bool ADAM = false>
-__global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_constant__ LMLaunch p) {
+__global__ void __launch_bounds__(tcs2::kWarps * 32, 1) lm_stage2_tc_kernel(const __grid_constant__ LMLaunch p) {
   constexpr int G = tcs2::G;
   extern __shared__ __align__(128) float smem[];
   __shared__ __align__(8) unsigned long long bar, mbar[tcs2::kCohorts];
@@ -2419,23 +2461,19 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
   const int slot = threadIdx.x / G;
   float *mine = C.slots + slot * C.sstride;
   unsigned char *co = C.base + 3 * t.plrows * 128;
-  PixCtx pc;
-  pc.t = &t;
-  pc.c = &c;
-  pc.img = smem;
-  pc.node = nullptr;
-  pc.wvrow = t.wvtab;
   Stage2<G> S;
   S.nbs = C.nbs;
   S.bb = mine;
-  float *ne = mine + 5 * S.nbs;   // trial H, g, gradient floor
-  float *prm = ne + kNE2;
+  // two ne slots: cb holds H, g and the gradient floor of the accepted
+  // state, cb ^ 1 receives the trial's
+  float *ne2 = mine + 2 * S.nbs;
+  float *prm = ne2 + 2 * kNE2;
   const long long n = p.s.n_pix;
   const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
   long long next = 0, end = 0, pix = 0;
   bool active = false, done = false, first = false, ok = true;
-  float x[6], xt[6], H[21], g[6], gf[6], cst = 0.f, cd = 0.f;
-  int rc = 0, nfull = 0, status = 0, n2u = 0;
+  float x[6], xt[6], cst = 0.f, cd = 0.f;
+  int nfull = 0, status = 0, n2u = 0, cb = 0;
   unsigned phase = 0;
   LMIter<6> L;
   AdamState<6> A;
@@ -2465,14 +2503,14 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       if (!(meta & kFitted)) continue;
       status = meta & 0xff;
       const PixRef ref = resolve(p, pix, K);
-      pc.wvrow = t.wvtab + (size_t)ref.wv * t.nb;
       float x1[K + 2];
 #pragma unroll
       for (int i = 0; i < K + 2; i++) x1[i] = p.w.s1x[pix * (K + 2) + i];
       float xs[K];
 #pragma unroll
       for (int k = 0; k < K; k++) xs[k] = x1[k];
-      n2u = setup2<K>(S, pc, gp, ref.row, xs);
+      n2u = tcs2::setup_slot<K>(t, c, gp, t.wvtab + (size_t)ref.wv * t.nb, ref.row, xs, mine, S.nbs,
+                                S.psc);
       const float T1 = x1[K + 1];
       x[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
       x[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
@@ -2500,7 +2538,6 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       for (int a = 0; a < 6; a++) L.act[a] = false;
       if constexpr (ADAM) A.reset();
       first = true;
-      rc = 0;
       nfull = 0;
       active = true;
     }
@@ -2530,17 +2567,22 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
     }
     if (tcs2::co_and(hc, done)) break;
     bool go = active;
+    const float *cur = ne2 + cb * kNE2;
+    const float(&H)[21] = *reinterpret_cast<const float(*)[21]>(cur);
+    const float(&g)[6] = *reinterpret_cast<const float(*)[6]>(cur + 21);
+    const float(&gf)[6] = *reinterpret_cast<const float(*)[6]>(cur + 30);
     if (active && !first) {
       if constexpr (ADAM) go = adam_next2(c, x, g, A, L, xt);
       else go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
     }
-    if (go) tcs2::coef(t, c, gp, x, xt, co, slot, prm, rc ^ 1);
+    if (go) tcs2::coef(t, c, gp, x, xt, co, slot, prm);
     if (gp.sub == 0) prm[0] = go ? 1.f : 0.f;
     if (!tcs2::round(t, C, hc, &mbar[hc], phase, c.wait_spins)) { ok = false; break; }
     nround++;
     if (go) {
       float ct, cdt, drop;
-      tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, xt, S.psc, ne, ct, cdt, drop);
+      tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, xt, S.psc, n2u, ne2 + (cb ^ 1) * kNE2,
+                 ct, cdt, drop);
       nfull++;
       bool accept = first || ADAM;   // an Adam step is always taken
       if (!first && !ADAM) {
@@ -2553,20 +2595,14 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
       if (accept) {
 #pragma unroll
         for (int i = 0; i < 6; i++) x[i] = xt[i];
-#pragma unroll
-        for (int i = 0; i < 21; i++) H[i] = ne[i];
-#pragma unroll
-        for (int a = 0; a < 6; a++) {
-          g[a] = ne[21 + a];
-          gf[a] = ne[30 + a];
-        }
+        cb ^= 1;
         cst = ct;
         cd = cdt;
-        rc ^= 1;
       }
       first = false;
     }
     if (active && !go) {
+      const float *fin = ne2 + cb * kNE2;   // the accepted state's H and g
       // ---- hand the final state and normal equations to the finalize kernel
       if (L.used64) status |= PX_F_FP64;
       status |= L.status;
@@ -2576,7 +2612,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
         if ((k & (G - 1)) != gp.sub) continue;
         float v;
         if (k < 6) v = x[k];
-        else if (k < 27) v = H[k - 6];
+        else if (k < 27) v = fin[k - 6];
         else if (k == 27) v = cst;
         else if (k == 28) v = cd;
         else if (k == 29) v = __int_as_float(n2u);
@@ -2584,7 +2620,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
         else v = S.psc;
         hand[k] = v;
       }
-      if (gp.sub < 6) p.w.s2g[pix * 6 + gp.sub] = pick(g, gp.sub);
+      if (gp.sub < 6) p.w.s2g[pix * 6 + gp.sub] = fin[21 + gp.sub];
       if (gp.sub == 0) {
         atomicAdd(&cstat[ST_IT2], (unsigned long long)L.it);
         atomicAdd(&cstat[ST_S64_2], (unsigned long long)L.n64);
@@ -2605,7 +2641,7 @@ __global__ void __launch_bounds__(256, 1) lm_stage2_tc_kernel(const __grid_const
 // ---- one stage-2 evaluation per state through the tensor-core round (test
 // hook of the normal equations): 16 states per CTA and round
 template <int K>
-__global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_constant__ LMLaunch p,
+__global__ void __launch_bounds__(tcs2::kWarps * 32, 1) normal_eq_tc_kernel(const __grid_constant__ LMLaunch p,
                                                               const float *states, float *Hout,
                                                               float *gout, float *cost_out) {
   constexpr int G = tcs2::G;
@@ -2621,16 +2657,11 @@ __global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_const
   const int slot = threadIdx.x / G;
   float *mine = C.slots + slot * C.sstride;
   unsigned char *co = C.base + 3 * t.plrows * 128;
-  PixCtx pc;
-  pc.t = &t;
-  pc.c = &c;
-  pc.img = smem;
-  pc.node = nullptr;
   Stage2<G> S;
   S.nbs = C.nbs;
   S.bb = mine;
-  float *ne = mine + 5 * S.nbs;
-  float *prm = ne + kNE2;
+  float *ne = mine + 2 * S.nbs;
+  float *prm = ne + 2 * kNE2;
   unsigned phase = 0;
   bool ok = true;
   for (long long b0 = (long long)blockIdx.x * tcs2::kSlots; b0 < p.s.n_pix;
@@ -2638,21 +2669,22 @@ __global__ void __launch_bounds__(256, 1) normal_eq_tc_kernel(const __grid_const
     const long long pix = b0 + slot;
     const bool has = pix < p.s.n_pix;
     float x[6];
+    int nu = 0;
     if (has) {
-      pc.wvrow = t.wvtab + (size_t)min((int)p.s.wv[pix], t.nwv - 1) * t.nb;
       float xs[K];
 #pragma unroll
       for (int k = 0; k < K; k++) xs[k] = states[pix * (K + 6) + k];
 #pragma unroll
       for (int i = 0; i < 6; i++) x[i] = states[pix * (K + 6) + K + i];
-      setup2<K>(S, pc, gp, p.s.rad + pix * t.nb, xs);
-      tcs2::coef(t, c, gp, x, x, co, slot, prm, 1);
+      nu = tcs2::setup_slot<K>(t, c, gp, t.wvtab + (size_t)min((int)p.s.wv[pix], t.nwv - 1) * t.nb,
+                               p.s.rad + pix * t.nb, xs, mine, S.nbs, S.psc);
+      tcs2::coef(t, c, gp, x, x, co, slot, prm);
     }
     if (gp.sub == 0) prm[0] = has ? 1.f : 0.f;
     if (!tcs2::round(t, C, hc, &mbar[hc], phase, c.wait_spins)) { ok = false; break; }
     if (has) {
       float cst, cd, drop;
-      tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, x, S.psc, ne, cst, cd, drop);
+      tcs2::post(c, gp, C.parts + slot * tcs2::kPartStride, x, S.psc, nu, ne, cst, cd, drop);
       if (gp.sub == 0) {
         for (int a = 0; a < 6; a++) {
           gout[pix * 6 + a] = ne[21 + a];
@@ -3215,10 +3247,10 @@ template <int K>
 cudaError_t launch_stage2(const LMLaunch &p, int num_sms, cudaStream_t st, int *bu, int v) {
   const bool adam = p.c.solver == kSolverAdam;
   if (v == 2) {
-    if (lm_tc_ok(p.t))
+    if (lm_tc_ok(p.t) && !p.c.weighted)
       return adam ? launch_stage2_tc<K, true>(p, num_sms, st, bu)
                   : launch_stage2_tc<K, false>(p, num_sms, st, bu);
-    v = 1;   // tables outside the tensor-core path: the FP32 shape of 16 lanes
+    v = 1;   // tables outside the tensor-core path, or a weighted loss: the FP32 shape of 16 lanes
   }
   if (adam) {
     // the Adam solver's FP32 stage 2 runs on the 16-lane shape
@@ -3261,7 +3293,7 @@ cudaError_t launch_k(const LMLaunch &p, int num_sms, cudaStream_t st, int *block
 template <int K>
 cudaError_t launch_ne_k(const LMLaunch &p, int stage, const float *states, float *H, float *g,
                         float *cost, cudaStream_t st, int variant) {
-  if (stage == 2 && (variant / 3) % 3 == 2 && lm_tc_ok(p.t)) {
+  if (stage == 2 && (variant / 3) % 3 == 2 && lm_tc_ok(p.t) && !p.c.weighted) {
     const size_t smem = (size_t)tcs2::layout(p.t).total;
     cudaError_t e = cudaFuncSetAttribute(normal_eq_tc_kernel<K>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
