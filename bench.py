@@ -747,7 +747,7 @@ def main():
                     help="launch shape 0..8 (default: autotuned on a tenth of the scene)")
     ap.add_argument("--claim", type=int, default=2)
     ap.add_argument("--mlp-steps", type=int, default=3000)
-    ap.add_argument("--sample-fire", type=int, default=6000,
+    ap.add_argument("--sample-fire", type=int, default=20000,
                     help="fire pixels of the parity sample (all if fewer)")
     ap.add_argument("--sample-bg", type=int, default=4000, help="other pixels of the parity sample")
     ap.add_argument("--batch-max-px", type=int, default=None, help="cap of the batched stream's pixels")

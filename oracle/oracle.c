@@ -1093,14 +1093,17 @@ void orc_posterior_at(const orc_tables_t *t, const orc_config_t *c, const float 
 void orc_retrieve(const orc_tables_t *t, const orc_config_t *c, const float *radiance,
                   const uint16_t *wv_bin, int64_t n, const double *init_state, orc_outputs_t *o,
                   int n_threads) {
+  /* n_threads > 0 bounds this call's threads only (a num_threads clause, not
+   * the process-wide setting, so a later call with 0 gets every core) */
 #ifdef _OPENMP
-  if (n_threads > 0) omp_set_num_threads(n_threads);
+  const int nt = n_threads > 0 ? n_threads : omp_get_num_procs();
 #else
+  const int nt = 1;
   (void)n_threads;
 #endif
   int NS = t->n_endm + 8;
   double *Bt = planck_table(t);
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
   for (int64_t i = 0; i < n; i++)
     retrieve_pixel(t, c, Bt, radiance + i * t->n_bands, wv_bin[i], init_state ? init_state + i * NS : NULL,
                    o, i);

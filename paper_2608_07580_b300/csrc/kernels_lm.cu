@@ -2272,8 +2272,10 @@ __device__ __forceinline__ void band(const KTables &t, uint32_t tmem, float *slo
 
 // (4) the slot's totals: H, g and the floor to ne (as the FP32 evaluation),
 // cost, data cost and decrease to the caller; nu is the used-band count
-// (the sum of the unit weights)
-__device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, float *ps,
+// (the sum of the unit weights). Lane sub adds the four quarters' partials
+// of sums sub and sub + 16 and writes the ne entries they make, with the
+// prior; the scalars come from their lanes by shuffle.
+__device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, const float *ps,
                                      const float (&xt)[6], float psc, int nu, float *ne, float &cst,
                                      float &cd, float &drop) {
   constexpr int NH = 21, P = 6;
@@ -2283,34 +2285,45 @@ __device__ __forceinline__ void post(const KConfig &c, const Grp<G> &gp, float *
     a += ps[q * 32 + gp.sub];
     b += ps[q * 32 + gp.sub + 16];
   }
-  gp.sync();
-  ps[gp.sub] = a;
-  ps[gp.sub + 16] = b;
-  gp.sync();
-  float acc[32];
+  const int base = gp.lane & ~(G - 1);
+  const float cdat = __shfl_sync(gp.mask, b, base + NH + P - 16);   // sum 27: data cost
+  drop = __shfl_sync(gp.mask, b, base + NH + P + 1 - 16);           // sum 28: decrease
+  const float m2 = __shfl_sync(gp.mask, b, base + NH + P + 2 - 16) / fmaxf((float)nu, 1.f);
+  // the prior of Eq. (affine)'s z: curvature psc pp, gradient -psc pp (z - pm)
+  cst = cdat;
 #pragma unroll
-  for (int i = 0; i < 32; i++) acc[i] = ps[i];
-  cst = acc[NH + P];
-  cd = acc[NH + P];
-  drop = acc[NH + P + 1];
-  float gfl[P];
-  const float m2 = acc[NH + P + 2] / fmaxf((float)nu, 1.f);
-#pragma unroll
-  for (int i = 0; i < P; i++) gfl[i] = kFloorC * sqrtf(acc[up<P>(i, i)] * m2);
-#pragma unroll
-  for (int i = 0; i < 6; i++) {
-    float z = c.zk2[i] > 0.f ? fmaf(xt[i] - c.lo2[i], c.zk2[i], -1.f) : 0.f;
-    float pp = psc * c.pp2[i];
+  for (int i = 0; i < P; i++) {
+    const float z = c.zk2[i] > 0.f ? fmaf(xt[i] - c.lo2[i], c.zk2[i], -1.f) : 0.f;
+    const float pp = psc * c.pp2[i];
     cst += pp * (z - c.pm2[i]) * (z - c.pm2[i]);
-    acc[NH + i] -= pp * (z - c.pm2[i]);
-    acc[up<P>(i, i)] += pp;
   }
-#pragma unroll
-  for (int k = 0; k < NH + P; k++)
-    if ((k & (G - 1)) == gp.sub) ne[k] = acc[k];
-#pragma unroll
-  for (int i = 0; i < P; i++)
-    if (((30 + i) & (G - 1)) == gp.sub) ne[30 + i] = gfl[i];
+  cd = cdat;
+  // sum sub: an entry of H (diagonals 0, 6, 11, 15 of variables 0-3)
+  const int s = gp.sub;
+  const int d1 = s == 0 ? 0 : s == 6 ? 1 : s == 11 ? 2 : s == 15 ? 3 : -1;
+  float va = a;
+  if (d1 >= 0) {
+    ne[30 + d1] = kFloorC * sqrtf(a * m2);
+    va += psc * c.pp2[d1];
+  }
+  ne[s] = va;
+  // sum sub + 16: an entry of H (diagonals 18, 20 of variables 4, 5), of g,
+  // or a scalar
+  const int k2 = s + 16;
+  if (k2 < NH) {
+    const int d2 = k2 == 18 ? 4 : k2 == 20 ? 5 : -1;
+    float vb = b;
+    if (d2 >= 0) {
+      ne[30 + d2] = kFloorC * sqrtf(b * m2);
+      vb += psc * c.pp2[d2];
+    }
+    ne[k2] = vb;
+  } else if (k2 < NH + P) {
+    const int i = k2 - NH;
+    const float z = c.zk2[i] > 0.f ? fmaf(pick(xt, i) - c.lo2[i], c.zk2[i], -1.f) : 0.f;
+    const float pp = psc * c.pp2[i];
+    ne[k2] = b - pp * (z - c.pm2[i]);
+  }
   gp.sync();
 }
 

@@ -155,6 +155,7 @@ def test_config1_parity(fr, torch, c1, c1_oracle):
     st = ctx.stats()
     print("stats:", st)
     assert st["n_pixels"] == tr.n_pix
+    assert st["mma_rounds2"] > 0   # the default (unweighted) fit runs the tensor-core stage 2
     assert_parity(s, 100, "config1")
     # the per-pixel outcome codes agree
     go, oo = g["status"] & 7, c1_oracle["status"] & 7
@@ -170,13 +171,18 @@ def c30():
 
 @pytest.fixture(scope="module")
 def flight_fire():
-    """6,000 fire pixels and 2,000 others of the flight-line chunk (1240 x
+    """20,000 fire pixels and 2,000 others of the flight-line chunk (1240 x
     2048, seed 1: the paper's Gaussian p(T) on the grid, 2 % fire fronts),
-    radiance from the oracle's forward model plus the counter-based noise."""
+    radiance from the oracle's forward model plus the counter-based noise.
+    The pool of converged identifiable pixels (~4,800) lets the 99.9 % bar
+    resolve a few misses: the near-degenerate mixture leaves a few pixels in
+    10,000 whose FP32 and FP64 paths part (a flat valley that one side
+    crosses within the iteration cap and the other not, or a second
+    minimum), so a pool of ~1,500 decided the bar on one pixel."""
     t = synth.make_tables()
     tr = synth.make_config2_truth(seed=1)
     rng = np.random.default_rng(17)
-    idx = np.sort(np.concatenate([rng.choice(np.flatnonzero(tr.kind == 2), 6000, replace=False),
+    idx = np.sort(np.concatenate([rng.choice(np.flatnonzero(tr.kind == 2), 20000, replace=False),
                                   rng.choice(np.flatnonzero(tr.kind == 0), 2000, replace=False)]))
     sub, L = config2_subset(idx, tr, t)
     return t, sub, L
@@ -190,9 +196,9 @@ def flight_fire_oracle(flight_fire):
 
 @pytest.mark.parametrize("variant", [6, 3])
 def test_flight_line_fire_pixels_parity(fr, torch, flight_fire, flight_fire_oracle, variant):
-    """A pool of ~1,500 converged identifiable flight-line fire pixels,
-    through the tensor-core (6) and the FP32 (3) stage-2 evaluation: the
-    99.9 % bar resolves one miss in a thousand here."""
+    """A pool of ~4,800 converged identifiable flight-line fire pixels,
+    through the tensor-core (6) and the FP32 (3) stage-2 evaluation, at the
+    99.9 % bar."""
     t, sub, L = flight_fire
     ctx = fr.Context(t)
     ctx.set_tuning(variant, 2)
@@ -498,6 +504,9 @@ def test_noise_weighted_loss_matches_oracle(fr, torch, c30, variant):
     o = oracle.retrieve(t, L, tr.wv_bin, cfg=cfg)
     out = _np(ctx.retrieve(_dev(torch, L, torch.float32),
                            _dev(torch, tr.wv_bin.astype(np.int16), torch.int16)))
+    # the tensor-core stage 2 fits the unweighted loss only: a weighted fit
+    # runs the FP32 stage 2 whatever the launch shape
+    assert ctx.stats()["mma_rounds2"] == 0
     s = parity_stats(o, out, cfg=cfg)
     assert_stress_parity(s, 1000, f"weighted, variant {variant}")
 
