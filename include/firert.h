@@ -82,10 +82,11 @@ typedef struct {
 
 /* Solver constants. Windows follow Sec. 2.3/2.6; everything else is this
  * library's stated choice (the paper gives no LM constants). The iteration
- * caps (100 / 400 trial steps) are set well above what the damped iteration
+ * caps (100 / 600 trial steps) are set well above what the damped iteration
  * needs (stage 2 of the near-degenerate mixture: median ~70, up to ~300 on
- * flaming pixels), so that a fit stops on a convergence test rather than on
- * the cap. Fill with fire_default_config and edit. */
+ * flaming pixels in FP64, more in FP32 where the normal matrix resolves its
+ * flat directions less well), so that a fit stops on a convergence test
+ * rather than on the cap. Fill with fire_default_config and edit. */
 typedef struct {
   float win1_lo, win1_hi;           /* Omega_1 (nm) */
   float win2h_lo, win2h_hi;         /* Omega_2^hot */

@@ -330,7 +330,12 @@ void fire_default_config(fire_config_t *c) {
   c->win2s_lo = 1500.f;
   c->win2s_hi = 2500.f;
   c->max_it1 = 100;
-  c->max_it2 = 400;
+  // 1.5 x the FP64 oracle's 400: the FP32 normal matrix resolves the flat
+  // directions of the near-degenerate mixture to ~1e-5 of its diagonal, so in
+  // those valleys this path takes more steps to meet the same convergence
+  // tests (at 400 it ended ~0.05 % of the fire pixels the oracle converges at
+  // the cap)
+  c->max_it2 = 600;
   c->tau0 = 1.f;
   c->tol_g = 1e-8f;
   c->tol_x = 1e-7f;

@@ -95,6 +95,11 @@ def parity_stats(o, g, bar_T=0.5, bar_a=1e-3, cfg=None, ident_band=IDENT_BAND):
         "n": int(ost.size), "pool": n, "pass": int(ok.sum()), "rate": float(ok.sum() / max(n, 1)),
         "gpu_not_conv": int((pool & ~conv_g).sum()),
         "value_fail": int((pool & conv_g & ~ok_vals).sum()),
+        # of the value misses, those where the GPU converged to a point of
+        # clearly lower cost than the oracle's (another, better minimum of the
+        # same objective; counted as misses all the same)
+        "value_fail_lower_cost": int((pool & conv_g & ~ok_vals & (np.asarray(g["cost"], np.float64)
+                                                                  < (1 - 1e-3) * o["cost"])).sum()),
         "max_dT": float(dT[sec].max()) if sec.any() else 0.0,
         "max_rel_da": float((da / np.maximum(o["alpha"], 1e-4))[sec].max()) if sec.any() else 0.0,
         "sec_n": int(sec.sum()), "sec_rate": float((sec & ~sec_fail).sum() / max(int(sec.sum()), 1)),

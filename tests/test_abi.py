@@ -40,7 +40,9 @@ def test_defaults_match_paper_and_oracle():
     o = oracle.Config()
     assert (c.win1_lo, c.win1_hi) == o.win1
     assert (c.win2h_lo, c.win2h_hi) == o.win2h and (c.win2s_lo, c.win2s_hi) == o.win2s
-    assert c.max_it1 == o.max_it1 and c.max_it2 == o.max_it2
+    # the stage-2 cap of the FP32 path is 1.5 x the oracle's (its normal
+    # matrix resolves the mixture's flat directions less well); stage 1 equal
+    assert c.max_it1 == o.max_it1 and c.max_it2 == 3 * o.max_it2 // 2
     for k in ("tau0", "tol_g", "tol_x", "tol_f", "kappa_max", "dfloor", "noise_rel", "noise_abs",
               "hfdi_thresh", "ident_sd_et", "ident_alpha_snr"):
         assert abs(getattr(c, k) - getattr(o, k)) <= 1e-6 * abs(getattr(o, k)), k
