@@ -78,10 +78,21 @@ __device__ __forceinline__ constexpr int up(int a, int b) {
   return a <= b ? a * P - (a * (a - 1)) / 2 + (b - a) : b * P - (b * (b - 1)) / 2 + (a - b);
 }
 
-// Reciprocal square root for the FP64 covariance (IEEE double square root
-// and division: the pivots of a near-singular matrix leave the FP32 range,
-// so no FP32 seed)
-__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+// Reciprocal square root in FP64 by the Newton-Raphson iteration for
+// 1 / sqrt(x), y <- y (3 - x y^2) / 2, which squares the relative error at
+// each step: from the FP32 SFU estimate (relative error near 2^-22) two steps
+// leave only the rounding of the last one (about 1 ulp), with six FP64
+// operations instead of a double square root and division (FP64 runs at
+// 1/64 of the FP32 rate). A pivot outside the FP32 range (a near-singular
+// matrix) takes the IEEE square root and division.
+__device__ __forceinline__ double rsq(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
 
 // expm1(y) for |y| < 0.5 by its Taylor series to y^9 (truncation below
 // |y|^10 / 10! e^|y| < 5e-10 |y|): nine FMAs, no branches
@@ -111,11 +122,10 @@ __device__ __forceinline__ float2 em1_mid2(float2 y) {
 }
 
 // ------------------------------------------------------------- solve ----
-// reciprocal square root for the step solve: the SFU in FP32; in FP64 the
-// IEEE double square root and division (the cold path of ill-conditioned
-// steps, whose pivots may leave the FP32 range)
+// reciprocal square root for the step solve: the SFU in FP32; in FP64 (the
+// cold path of ill-conditioned steps) the Newton-refined rsq above
 __device__ __forceinline__ float rsq_step(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq_step(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double rsq_step(double x) { return rsq(x); }
 
 // Solve (H + lam D) d = rhs over the free variables on the diagonally scaled
 // matrix; pinned variables are identity rows with their displacement moved
@@ -204,6 +214,114 @@ __device__ __forceinline__ bool damped_solve(const float (&H)[P * (P + 1) / 2],
   return true;
 }
 
+// The damped solve of damped_solve<P, double> (the same operations in the
+// same order) in little code and few registers, for the cold FP64 path of the
+// tensor-core stage 2, where a call to an out-of-line FP64 step cost the hot
+// loop registers and instruction-cache room: the group's first lane solves
+// on a shared-memory scratch w (8-byte aligned; (P (P + 1) / 2 + 3 P) doubles
+// and 3 P + 2 floats) with rolled loops, and the group reads the step back.
+template <int P, class GP>
+__device__ __forceinline__ bool damped_solve_s64(const GP &gp, const float *H, const float *g, float lam,
+                                                 const float (&D)[P], const bool (&pin)[P],
+                                                 float (&dr)[P], float &kap, double *w) {
+  constexpr int NA = P * (P + 1) / 2;
+  double *A = w, *y = w + NA, *rd = y + P, *il = rd + P;
+  float *fD = reinterpret_cast<float *>(il + P), *fdr = fD + P, *fpin = fdr + P, *fout = fpin + P;
+  if (gp.sub == 0) {
+#pragma unroll
+    for (int i = 0; i < P; i++) {
+      fD[i] = D[i];
+      fdr[i] = dr[i];
+      fpin[i] = pin[i] ? 1.f : 0.f;
+    }
+#pragma unroll 1
+    for (int i = 0; i < P; i++) {
+      const bool pi = fpin[i] != 0.f;
+      double r = pi ? 0.0 : (double)g[i];
+#pragma unroll 1
+      for (int j = 0; j < P; j++)
+        if (fpin[j] != 0.f && !pi) r -= (double)H[up<P>(i, j)] * (double)fdr[j];
+      y[i] = r;
+#pragma unroll 1
+      for (int j = 0; j <= i; j++) {
+        const bool pj = fpin[j] != 0.f;
+        double m;
+        if (!pi && !pj) m = (double)H[up<P>(i, j)];
+        else m = (i == j) ? 1.0 : 0.0;
+        if (i == j && !pi) m += (double)lam * (double)fD[i];
+        A[i * (i + 1) / 2 + j] = m;
+      }
+    }
+#pragma unroll 1
+    for (int i = 0; i < P; i++) rd[i] = rsq_step(A[i * (i + 1) / 2 + i]);
+#pragma unroll 1
+    for (int i = 0; i < P; i++) {
+      y[i] *= rd[i];
+#pragma unroll 1
+      for (int j = 0; j <= i; j++) A[i * (i + 1) / 2 + j] *= rd[i] * rd[j];
+    }
+    bool ok = true;
+#pragma unroll 1
+    for (int j = 0; j < P; j++) {
+      double sj = A[j * (j + 1) / 2 + j];
+#pragma unroll 1
+      for (int k = 0; k < j; k++) sj -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+      ok = ok && (sj > 0.0);
+      const double r = rsq_step(sj > 0.0 ? sj : 1.0);
+      il[j] = r;
+      A[j * (j + 1) / 2 + j] = (sj > 0.0 ? sj : 1.0) * r;
+#pragma unroll 1
+      for (int i = j + 1; i < P; i++) {
+        double t = A[i * (i + 1) / 2 + j];
+#pragma unroll 1
+        for (int k = 0; k < j; k++) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+        A[i * (i + 1) / 2 + j] = t * r;
+      }
+    }
+    float kp = 1.f;
+    if (ok) {
+      float lmax = 0.f, lmin = 1e30f;
+#pragma unroll 1
+      for (int i = 0; i < P; i++)
+        if (fpin[i] == 0.f) {
+          const float l = (float)A[i * (i + 1) / 2 + i];
+          lmax = fmaxf(l, lmax);
+          lmin = fminf(l, lmin);
+        }
+      kp = lmax > 0.f ? (lmax * lmax) / (lmin * lmin) : 1.f;
+#pragma unroll 1
+      for (int i = 0; i < P; i++) {
+        double t = y[i];
+#pragma unroll 1
+        for (int k = 0; k < i; k++) t -= A[i * (i + 1) / 2 + k] * y[k];
+        y[i] = t * il[i];
+      }
+#pragma unroll 1
+      for (int i = P - 1; i >= 0; i--) {
+        double t = y[i];
+#pragma unroll 1
+        for (int k = i + 1; k < P; k++) t -= A[k * (k + 1) / 2 + i] * y[k];
+        y[i] = t * il[i];
+      }
+#pragma unroll 1
+      for (int i = 0; i < P; i++)
+        if (fpin[i] == 0.f) fdr[i] = (float)(y[i] * rd[i]);
+    }
+    fout[0] = ok ? 1.f : 0.f;
+    fout[1] = kp;
+  }
+  gp.sync();
+  const bool ok = fout[0] != 0.f;
+  kap = fout[1];
+  if (ok) {
+#pragma unroll
+    for (int i = 0; i < P; i++)
+      if (!pin[i]) dr[i] = fdr[i];
+  }
+  gp.sync();
+  return ok;
+}
+
 // -------------------------------------------------------- LM driver -----
 template <int G>
 struct Grp;
@@ -233,13 +351,17 @@ struct LMIter {
 // next_trial64) takes the whole step from there; keeping the rare FP64 path
 // out of this function keeps the hot loop's registers free (with the FP64
 // call inline the solve took 5,400 instead of 3,400 cycles per trial).
-template <class St, typename T>
+template <class St, typename T, bool SM64 = false>
 __device__ __forceinline__ bool next_trial_t(const St &S, const Grp<St::GL> &gp, const KConfig &c,
                                              const float (&x)[St::NX], const float (&H)[St::NH],
                                              const float (&g)[St::P], const float (&gf)[St::P], int m,
                                              float cst, int max_it, LMIter<St::P> &L,
-                                             float (&xt)[St::NX], bool &want64) {
+                                             float (&xt)[St::NX], bool &want64, double *s64 = nullptr) {
   constexpr int P = St::P, NX = St::NX;
+  // SM64: an ill-conditioned or indefinite FP32 solve switches the rest of
+  // this call to FP64 solves (damped_solve_s64 on the scratch s64) and
+  // restarts its projected-Newton passes, instead of returning want64
+  bool use64 = false;
 #pragma unroll 1
   while (L.it < max_it) {
     if (L.fresh) {
@@ -281,15 +403,33 @@ __device__ __forceinline__ bool next_trial_t(const St &S, const Grp<St::GL> &gp,
       for (int a = 0; a < P; a++) nf += !pin[a];
       if (nf == 0) break;
       float kap = 0.f;
-      ok = damped_solve<P, T>(H, g, L.lam, D, pin, dr, kap);
-      if constexpr (sizeof(T) == sizeof(float)) {
-        if (!ok || !(kap <= c.kappa_max)) {
-          want64 = true;
-          return false;
-        }
-      } else {
+      if (SM64 && use64) {
+        ok = damped_solve_s64<P>(gp, H, g, L.lam, D, pin, dr, kap, s64);
         L.used64 = true;
         L.n64++;
+      } else {
+        ok = damped_solve<P, T>(H, g, L.lam, D, pin, dr, kap);
+        if constexpr (sizeof(T) == sizeof(float)) {
+          if (!ok || !(kap <= c.kappa_max)) {
+            if constexpr (SM64) {
+              use64 = true;
+#pragma unroll
+              for (int a = 0; a < P; a++) {
+                pin[a] = L.act[a];
+                dr[a] = 0.f;
+                pd[a] = 0;
+              }
+              pass = -1;
+              continue;
+            } else {
+              want64 = true;
+              return false;
+            }
+          }
+        } else {
+          L.used64 = true;
+          L.n64++;
+        }
       }
       if (!ok) break;
       bool viol = false;
@@ -2586,7 +2726,13 @@ __global__ void __launch_bounds__(tcs2::kWarps * 32, 1) lm_stage2_tc_kernel(cons
     const float(&gf)[6] = *reinterpret_cast<const float(*)[6]>(cur + 30);
     if (active && !first) {
       if constexpr (ADAM) go = adam_next2(c, x, g, A, L, xt);
-      else go = next_trial(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt);
+      else {
+        // the FP64 solves of ill-conditioned steps on the slot's partial-sum
+        // block, free until the band phase of this round
+        bool unused = false;
+        go = next_trial_t<Stage2<G>, float, true>(S, gp, c, x, H, g, gf, 0, cst, c.max_it2, L, xt, unused,
+                                                  reinterpret_cast<double *>(C.parts + slot * tcs2::kPartStride));
+      }
     }
     if (go) tcs2::coef(t, c, gp, x, xt, co, slot, prm);
     if (gp.sub == 0) prm[0] = go ? 1.f : 0.f;
