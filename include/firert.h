@@ -391,12 +391,14 @@ void fire_graph_destroy(fire_graph_t *g);
  * per pixel of stage 1 (0 = 16 lanes, two pixels per warp; 1 = 8 lanes,
  * four per warp; 2 = 32 lanes, one per warp), s2 the stage-2 evaluation
  * (0 = FP32 with 32 lanes per pixel; 1 = FP32 with 16; 2 = 16 lanes per
- * pixel, 16 pixels per CTA, with the grid-node sums of the CTA's pixels as
- * one bf16x3 tensor-core product per round; tables with more than 64 grid
- * nodes or 256 stage-2 bands take 1 instead). claim: pixels per work claim
- * (1, 2, 4, 8). Each stage runs one persistent CTA per SM with as many warps
- * as its shared memory allows (at most 12 for stage 1, 8 for stage 2). A
- * new context starts at variant 6 where the tables allow it, else 3.
+ * pixel, 24 pixels per CTA in three 4-warp cohorts, with the grid-node sums
+ * of a cohort's 8 pixels as one bf16x3 tensor-core product per round; tables
+ * with more than 64 grid nodes or more stage-2 bands than its shared memory
+ * holds (about 225), and the weighted loss, take 1 instead). claim: pixels
+ * per work claim (1, 2, 4, 8). Each stage runs one persistent CTA per SM with
+ * as many warps as its shared memory allows (at most 12 for stage 1, 8 for
+ * the FP32 stage 2, 12 for the tensor-core stage 2). A new context starts at
+ * variant 6 where the tables allow it, else 3.
  * fire_set_tuning sets a shape directly (variant 0..8, claim 1..64); the
  * stage-2 evaluation of the set shape is also the one that
  * fire_normal_equations uses. */
