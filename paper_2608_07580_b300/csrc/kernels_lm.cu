@@ -2540,14 +2540,17 @@ __device__ __forceinline__ bool round(const KTables &t, Cta &C, int h, unsigned 
   if (threadIdx.x == kCoThreads * h)
     mma(C.tmem + (uint32_t)(h * kNc * C.ntile), tc::su32(C.base),
         tc::su32(C.base + 3 * t.plrows * 128 + h * kNc * 128), t.plrows, C.ntile, tc::su32(mbar));
-  const bool w = tc::mbar_wait(tc::su32(mbar), phase, spins);
+  // each warp reads the product once its own wait has seen the commit (the
+  // warp's lanes agree first, the band phase shuffles across all of them);
+  // the cohort agrees on a timed-out wait at the one barrier after the band
+  // phase (a warp whose wait gave up skips the phase, and the round is
+  // dropped)
+  const bool w = __all_sync(kFull, tc::mbar_wait(tc::su32(mbar), phase, spins));
   phase ^= 1u;
-  if (!co_and(h, w)) return false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  band(t, C.tmem, C.slots, C.sstride, C.parts, C.nbs);
+  if (w) band(t, C.tmem, C.slots, C.sstride, C.parts, C.nbs);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  co_sync(h);
-  return true;
+  return co_and(h, w);
 }
 
 // release (both cohorts): on a timed-out round, a bounded wait for the
