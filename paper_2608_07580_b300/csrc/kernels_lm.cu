@@ -2292,13 +2292,19 @@ __device__ __forceinline__ void mma(uint32_t tmem, unsigned pl, unsigned co, int
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   constexpr uint32_t idesc = tc::idesc_bf16(128, kNc);
   constexpr int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
+  // the descriptors of the 24 products of a tile are the base descriptors
+  // plus fixed offsets (the start-address field counts 16-byte units and
+  // shared addresses stay below its 256 KB range), so each costs one add
+  const uint64_t b0 = tc::sdesc(co);
+  const uint64_t apart = (uint64_t)(((unsigned)plrows * 128u) >> 4);
   for (int m = 0; m < ntile; m++) {
+    const uint64_t am = tc::sdesc(pl + (unsigned)(m * 16384));
 #pragma unroll
     for (int pr = 0; pr < 6; pr++)
 #pragma unroll
       for (int kk = 0; kk < 4; kk++) {
-        const uint64_t ad = tc::sdesc(pl + (unsigned)(pa[pr] * plrows * 128 + m * 16384 + kk * 32));
-        const uint64_t bd = tc::sdesc(co + (unsigned)(pb[pr] * kCoPart + kk * 32));
+        const uint64_t ad = am + (uint64_t)pa[pr] * apart + (uint64_t)(kk * 2);
+        const uint64_t bd = b0 + (uint64_t)((pb[pr] * kCoPart + kk * 32) >> 4);
         const uint32_t acc = (pr > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
