@@ -2139,6 +2139,7 @@ __device__ __forceinline__ int setup_slot(const KTables &t, const KConfig &c, co
                                           float *sb, int nbs, float &psc) {
   float nv = 0.f;
   int nu = 0;
+#pragma unroll 1
   for (int i = gp.sub; i < nbs; i += G) {
     float yv = 0.f, tv = 0.f;
     if (i < t.n2) {
@@ -2713,6 +2714,7 @@ __global__ void __launch_bounds__(tcs2::kWarps * 32, 1) lm_stage2_tc_kernel(cons
           // 11 lines per pixel: 8 of the stage-2 radiance window, the
           // stage-1 status word, the stage-1 state and the WV bin
           const long long e_end = min((long long)nclaim, n - b) * 11;
+#pragma unroll 1
           for (long long e = gp.sub; e < e_end; e += G) {
             const long long q = b + e / 11;
             const int l = (int)(e % 11);
@@ -2775,19 +2777,17 @@ __global__ void __launch_bounds__(tcs2::kWarps * 32, 1) lm_stage2_tc_kernel(cons
       if (L.used64) status |= PX_F_FP64;
       status |= L.status;
       float *hand = p.w.s2x + pix * kS2Hand;
-#pragma unroll
-      for (int k = 0; k < 32; k++) {
-        if ((k & (G - 1)) != gp.sub) continue;
-        float v;
-        if (k < 6) v = x[k];
-        else if (k < 27) v = fin[k - 6];
-        else if (k == 27) v = cst;
-        else if (k == 28) v = cd;
-        else if (k == 29) v = __int_as_float(n2u);
-        else if (k == 30) v = __int_as_float(status | (L.it << 8));
-        else v = S.psc;
-        hand[k] = v;
-      }
+      // lane sub writes entries sub and sub + 16: the state, H, then the scalars
+      const int hs = gp.sub, hk = gp.sub + 16;
+      hand[hs] = hs < 6 ? pick(x, hs) : fin[max(hs - 6, 0)];
+      float hv;
+      if (hk < 27) hv = fin[hk - 6];
+      else if (hk == 27) hv = cst;
+      else if (hk == 28) hv = cd;
+      else if (hk == 29) hv = __int_as_float(n2u);
+      else if (hk == 30) hv = __int_as_float(status | (L.it << 8));
+      else hv = S.psc;
+      hand[hk] = hv;
       if (gp.sub < 6) p.w.s2g[pix * 6 + gp.sub] = fin[21 + gp.sub];
       if (gp.sub == 0) {
         atomicAdd(&cstat[ST_IT2], (unsigned long long)L.it);
