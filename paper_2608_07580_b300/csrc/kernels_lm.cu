@@ -2267,23 +2267,21 @@ __device__ __forceinline__ void coef(const KTables &t, const KConfig &c, const G
   // band-phase parameters: [1] eta, [2] alpha, [3] alpha - alpha_o, [4..7]
   // the Jacobian factors of mu_h, s_h, mu_s, s_s, [8] [9] z scales of eta and
   // alpha; [0] (the flag) is set by the caller
-  const float sc0 = 0.5f * (c.hi2[0] - c.lo2[0]), sc1 = 0.5f * (c.hi2[1] - c.lo2[1]);
-  const float sc2 = 0.5f * (c.hi2[2] - c.lo2[2]), sc3 = 0.5f * (c.hi2[3] - c.lo2[3]);
-  const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
-  float v = 0.f;
-  switch (gp.sub) {
-    case 1: v = eta; break;
-    case 2: v = al; break;
-    case 3: v = al - x[5]; break;
-    case 4: v = eta * ish2 * sc0; break;
-    case 5: v = eta * (ish2 / sh) * sc1; break;
-    case 6: v = (1.f - eta) * iss2 * sc2; break;
-    case 7: v = (1.f - eta) * (iss2 / ss) * sc3; break;
-    case 8: v = 0.5f * (c.hi2[4] - c.lo2[4]); break;
-    case 9: v = 0.5f * (c.hi2[5] - c.lo2[5]); break;
-    default: break;
+  // (the group's first lane writes them: less code than a per-lane choice)
+  if (gp.sub == 0) {
+    const float sc0 = 0.5f * (c.hi2[0] - c.lo2[0]), sc1 = 0.5f * (c.hi2[1] - c.lo2[1]);
+    const float sc2 = 0.5f * (c.hi2[2] - c.lo2[2]), sc3 = 0.5f * (c.hi2[3] - c.lo2[3]);
+    const float ish2 = 1.f / (sh * sh), iss2 = 1.f / (ss * ss);
+    prm[1] = eta;
+    prm[2] = al;
+    prm[3] = al - x[5];
+    prm[4] = eta * ish2 * sc0;
+    prm[5] = eta * (ish2 / sh) * sc1;
+    prm[6] = (1.f - eta) * iss2 * sc2;
+    prm[7] = (1.f - eta) * (iss2 / ss) * sc3;
+    prm[8] = 0.5f * (c.hi2[4] - c.lo2[4]);
+    prm[9] = 0.5f * (c.hi2[5] - c.lo2[5]);
   }
-  if (gp.sub >= 1 && gp.sub <= 9) prm[gp.sub] = v;
 }
 
 // (2) the six part products of one cohort (its 64 coefficient rows),
