@@ -59,7 +59,8 @@ constexpr float kIncBelow = 1e-5f;
 // M_b)^2), u = 2^-24. Where the noise is low (block-averaged spectra) this
 // floor exceeds the gradient tolerance and an FP32 fit cannot pass the test;
 // such a fit runs to the iteration cap and is reported converged if its
-// gradient is within the tolerance plus the floor there.
+// gradient is within the tolerance plus the floor there (and plus the
+// gradient that the FP32 spacing of the state makes: see next_trial_t).
 constexpr float kFloorC = 8.f * 5.9604645e-8f;
 
 template <int I>
@@ -483,11 +484,25 @@ __device__ __forceinline__ bool next_trial_t(const St &S, const Grp<St::GL> &gp,
     return true;
   }
   // iteration cap: converged if the gradient of the free variables is within
-  // the tolerance plus its FP32 rounding floor
+  // the tolerance plus its FP32 floors: the rounding of its band sums (gf),
+  // and the spacing of the FP32 state, the gradient that moves of the free
+  // variables by two units in the last place make, sum_b |H_ab| u_b. Next to
+  // a minimum sharper than that spacing no FP32 state meets the tolerance,
+  // and the iteration cycles between neighbouring states up to the cap.
+  float Uz[NX], u[P];
+#pragma unroll
+  for (int i = 0; i < NX; i++) Uz[i] = fabsf(x[i]) * 0x1p-22f * S.zk(c, i);
+  static_for<P>([&](auto A_) {
+    constexpr int a = decltype(A_)::value;
+    u[a] = L.act[a] ? 0.f : St::template rsel<a>(Uz, m);
+  });
   bool small = true;
   static_for<P>([&](auto A_) {
     constexpr int a = decltype(A_)::value;
-    if (!L.act[a] && fabsf(g[a]) > fmaf(c.tol_g, sqrtf(H[up<P>(a, a)] * cst), gf[a])) small = false;
+    float q = gf[a];
+#pragma unroll
+    for (int b = 0; b < P; b++) q = fmaf(fabsf(H[up<P>(a, b)]), u[b], q);
+    if (!L.act[a] && fabsf(g[a]) > fmaf(c.tol_g, sqrtf(H[up<P>(a, a)] * cst), q)) small = false;
   });
   if (small) L.status = PX_CONVERGED;
   return false;
@@ -1534,20 +1549,21 @@ __device__ __forceinline__ int setup1(Stage1<K, G> &s1, const PixCtx &pc, const 
   return nu;
 }
 
-// The ungated intake in one pass over the pixel's radiance row: the
-// finiteness of every band (this lane's part, fin), the stage-1 buffers as
-// setup1 builds them, and the stage-2 band count as count2 forms it (the
-// stage-2 bands lie inside the stage-1 range). Returns nothing but through
-// the references; n1u, n2u and the prior scale are group totals.
-template <int K, int G>
-__device__ __forceinline__ void setup1_fused(Stage1<K, G> &s1, const PixCtx &pc, const Grp<G> &gp,
-                                             const float *row, bool &fin, int &n1u, int &n2u) {
+// The ungated intake of one pixel in one pass over its radiance row, by a
+// whole warp (32 lanes over the row: at 8 lanes a pixel a quarter of the
+// dependent loads per lane): the finiteness of every band, the stage-1
+// buffers as setup1 builds them (bb, the pixel's band buffers) and the
+// stage-2 band count as count2 forms it (the stage-2 bands lie inside the
+// stage-1 range). fin, n1u, n2u and the prior scale are warp totals.
+__device__ __forceinline__ void setup1_warp(const PixCtx &pc, int lane, const float *row, float *bb, int nbs,
+                                            bool &fin, int &n1u, int &n2u, float &psc) {
   const KTables &t = *pc.t;
   const KConfig &c = *pc.c;
   float nv = 0.f;
   int nu = 0, nu2 = 0;
   bool f = true;
-  for (int i = gp.sub; i < s1.nbs; i += G) {
+#pragma unroll 1
+  for (int i = lane; i < nbs; i += 32) {
     float Lv = 0.f, wv = 0.f;
     if (i < t.n1) {
       const int b = t.b1lo + i;
@@ -1561,23 +1577,26 @@ __device__ __forceinline__ void setup1_fused(Stage1<K, G> &s1, const PixCtx &pc,
       if (ok) { nv += var; nu++; }
       if (b >= t.b2lo && b < t.b2lo + t.n2) nu2 += (pc.img[t.lay.off_win2 + b] > 0.f && unsat) ? 1 : 0;
     }
-    s1.Lo(i) = Lv;
-    s1.W(i) = wv;
-#pragma unroll
-    for (int k = 2; k < 4; k++) s1.bb[k * s1.nbs + i] = 0.f;
+    bb[i] = Lv;
+    bb[nbs + i] = wv;
+    bb[2 * nbs + i] = 0.f;
+    bb[3 * nbs + i] = 0.f;
   }
-  // the bands outside the stage-1 range: finiteness only
-  for (int b = gp.sub; b < t.b1lo; b += G) f = f && isfinite(__ldg(row + b));
-  for (int b = t.b1lo + t.n1 + gp.sub; b < t.nb; b += G) f = f && isfinite(__ldg(row + b));
-  fin = f;
-  nv = gp.sum1(nv);
-  n1u = gp.isum(nu);
-  n2u = gp.isum(nu2);
-  s1.psc = c.weighted ? 1.f : nv / (float)max(n1u, 1);
-  s1.sf = 0.5f * (c.hi1[0] - c.lo1[0]);
-  s1.sa = 0.5f * (c.hi1[K] - c.lo1[K]);
-  s1.sT = 0.5f * (c.hi1[K + 1] - c.lo1[K + 1]);
-  gp.sync();
+#pragma unroll 1
+  for (int b = lane; b < t.b1lo; b += 32) f = f && isfinite(__ldg(row + b));
+#pragma unroll 1
+  for (int b = t.b1lo + t.n1 + lane; b < t.nb; b += 32) f = f && isfinite(__ldg(row + b));
+  fin = __all_sync(kFull, f);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    nv += __shfl_xor_sync(kFull, nv, o);
+    nu += __shfl_xor_sync(kFull, nu, o);
+    nu2 += __shfl_xor_sync(kFull, nu2, o);
+  }
+  n1u = nu;
+  n2u = nu2;
+  psc = c.weighted ? 1.f : nv / (float)max(nu, 1);
+  __syncwarp();
 }
 
 // stage-2 band count (mask x window) without building the stage state
@@ -1740,30 +1759,64 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
   int m = 0, rc = 0, nfull = 0, status = 0;
   LMIter<P> L;
   AdamState<NX> A;
+  S.sf = 0.5f * (c.hi1[0] - c.lo1[0]);
+  S.sa = 0.5f * (c.hi1[K] - c.lo1[K]);
+  S.sT = 0.5f * (c.hi1[K + 1] - c.lo1[K + 1]);
+  // every pixel is fitted (no gate) and the stage-2 bands lie inside the
+  // stage-1 range: one pass builds the stage-1 buffers with the finiteness
+  // test, by the whole warp; gated, most pixels stop at the gate, so the
+  // group's own finiteness pass comes first
+  const bool fuse = !p.s.gate && t.b2lo >= t.b1lo && t.b2lo + t.n2 <= t.b1lo + t.n1;
   for (;;) {
-    // ---- take pixels until one is to be fitted
-    while (!active && !done) {
-      if (next >= end) {
-        const long long b = claim(p.w.counter, gp, nclaim);
-        if (b >= n) { done = true; break; }
-        next = b;
-        end = min(b + (long long)nclaim, n);
+    // ---- take pixels until one is to be fitted, for every group of the
+    // warp without one
+    while (__any_sync(kFull, !active && !done)) {
+      bool have = false;
+      PixRef ref{};
+      if (!active && !done) {
+        if (next >= end) {
+          const long long b = claim(p.w.counter, gp, nclaim);
+          if (b >= n) {
+            done = true;
+          } else {
+            next = b;
+            end = min(b + (long long)nclaim, n);
+          }
+        }
+        if (!done) {
+          pix = next++;
+          ref = resolve(p, pix, K);
+          have = true;
+        }
       }
-      pix = next++;
-      const PixRef ref = resolve(p, pix, K);
       const float *row = ref.row;
+      bool fin = true;
+      int n1u = 0, n2u = 0;
+      if (fuse) {
+        unsigned need = __ballot_sync(kFull, have && gp.sub == 0);
+        while (need) {
+          const int src = __ffs(need) - 1;
+          need &= need - 1;
+          const float *rs = reinterpret_cast<const float *>(
+              __shfl_sync(kFull, reinterpret_cast<unsigned long long>(row), src));
+          bool fs;
+          int a1, a2;
+          float ps;
+          float *bbs = smem + img_f + wv_f + ((threadIdx.x & ~31) + src) / G * pix_stride1(t, G);
+          setup1_warp(pc, lane, rs, bbs, S.nbs, fs, a1, a2, ps);
+          if ((lane ^ src) < G) {
+            fin = fs;
+            n1u = a1;
+            n2u = a2;
+            S.psc = ps;
+          }
+        }
+      }
+      if (!have) continue;
       const int wvb = ref.wv;
       const bool wv_ok = wvb < t.nwv;   // an out-of-range bin is an invalid input
       pc.wvrow = wvs + (size_t)(wv_ok ? wvb : 0) * t.nb;
-      bool fin = true;
-      int n1u = 0, n2u = 0;
-      // every pixel is fitted (no gate) and the stage-2 bands lie inside the
-      // stage-1 range: one pass builds the stage-1 buffers with the
-      // finiteness test; gated, most pixels stop at the gate, so the
-      // finiteness pass comes first
-      const bool fuse = !p.s.gate && t.b2lo >= t.b1lo && t.b2lo + t.n2 <= t.b1lo + t.n1;
-      if (fuse) setup1_fused(S, pc, gp, row, fin, n1u, n2u);
-      else
+      if (!fuse)
         for (int b = gp.sub; b < t.nb; b += G) fin = fin && isfinite(__ldg(row + b));
       fin = gp.all(fin) && wv_ok;
       const float Lh = __ldg(row + t.bh), Ll = __ldg(row + t.bl);
@@ -2164,6 +2217,45 @@ __device__ __forceinline__ int setup_slot(const KTables &t, const KConfig &c, co
   nu = gp.isum(nu);
   psc = nv / (float)max(nu, 1);
   gp.sync();
+  return nu;
+}
+
+// setup_slot of one pixel by a whole warp: 32 lanes over the bands, so half
+// the dependent loads per lane, and the noise sum reduced over the warp
+template <int K>
+__device__ __forceinline__ int setup_slot_warp(const KTables &t, const KConfig &c, int lane,
+                                               const float4 *wvrow, const float *row, const float (&xs)[K],
+                                               float *sb, int nbs, float &psc) {
+  float nv = 0.f;
+  int nu = 0;
+#pragma unroll 1
+  for (int i = lane; i < nbs; i += 32) {
+    float yv = 0.f, tv = 0.f;
+    if (i < t.n2) {
+      const int b = t.b2lo + i;
+      const float L = __ldg(row + b);
+      const bool ok = __ldg(t.image + t.lay.off_win2 + b) > 0.f && !(t.sat && L >= __ldg(t.sat + b));
+      if (ok) {
+        const float4 q = __ldg(wvrow + b);
+        float rho = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; k++) rho = fmaf(xs[k], __ldg(t.image + t.lay.off_endm + k * t.nb + b), rho);
+        yv = L - (q.y + q.x * rho / (1.f - q.z * rho));
+        tv = q.w;
+        nv += c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
+        nu++;
+      }
+    }
+    sb[i] = yv;
+    sb[nbs + i] = tv;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    nv += __shfl_xor_sync(kFull, nv, o);
+    nu += __shfl_xor_sync(kFull, nu, o);
+  }
+  psc = nv / (float)max(nu, 1);
+  __syncwarp();
   return nu;
 }
 
@@ -2645,6 +2737,12 @@ __global__ void __launch_bounds__(tcs2::kWarps * 32, 1) lm_stage2_tc_kernel(cons
   unsigned long long pfb = 0;   // first lane: base index of the claim held in reserve
   int pfs = 0;                  // 0: none held, 1: claimed, 2: prefetched
   unsigned long long nround = 0;
+  // a pixel taken this round whose slot set-up is pending: radiance row,
+  // WV bin, stage-1 surface weights
+  bool pend = false;
+  const float *prow = nullptr;
+  int pwv = 0;
+  float xsp[K];
   for (;;) {
     while (!active && !done) {
       if (next >= end) {
@@ -2667,11 +2765,11 @@ __global__ void __launch_bounds__(tcs2::kWarps * 32, 1) lm_stage2_tc_kernel(cons
       float x1[K + 2];
 #pragma unroll
       for (int i = 0; i < K + 2; i++) x1[i] = p.w.s1x[pix * (K + 2) + i];
-      float xs[K];
 #pragma unroll
-      for (int k = 0; k < K; k++) xs[k] = x1[k];
-      n2u = tcs2::setup_slot<K>(t, c, gp, t.wvtab + (size_t)ref.wv * t.nb, ref.row, xs, mine, S.nbs,
-                                S.psc);
+      for (int k = 0; k < K; k++) xsp[k] = x1[k];
+      prow = ref.row;
+      pwv = ref.wv;
+      pend = true;
       const float T1 = x1[K + 1];
       x[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
       x[2] = fminf(fmaxf(fminf(T1, c.init_mu_s_ceil), c.lo2[2]), c.hi2[2]);
@@ -2701,6 +2799,30 @@ __global__ void __launch_bounds__(tcs2::kWarps * 32, 1) lm_stage2_tc_kernel(cons
       first = true;
       nfull = 0;
       active = true;
+    }
+    {
+      // the set-ups of the pixels the warp's two groups just took, one after
+      // the other, each by the whole warp
+      unsigned need = __ballot_sync(kFull, pend && gp.sub == 0);
+      while (need) {
+        const int src = __ffs(need) - 1;
+        need &= need - 1;
+        const float *rs = reinterpret_cast<const float *>(
+            __shfl_sync(kFull, reinterpret_cast<unsigned long long>(prow), src));
+        const int ws = __shfl_sync(kFull, pwv, src);
+        float xss[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) xss[k] = __shfl_sync(kFull, xsp[k], src);
+        float pss;
+        const int nu = tcs2::setup_slot_warp<K>(t, c, lane, t.wvtab + (size_t)ws * t.nb, rs, xss,
+                                                C.slots + (((threadIdx.x & ~31) + src) / G) * C.sstride,
+                                                S.nbs, pss);
+        if ((lane ^ src) < G) {
+          n2u = nu;
+          S.psc = pss;
+        }
+      }
+      pend = false;
     }
     if (active && next >= end) {
       if (pfs == 0) {
