@@ -35,7 +35,10 @@ typedef enum {
   FIRE_ERR_SHAPE = 4,      /* sizes outside what the kernels support */
   FIRE_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
   FIRE_ERR_CHECKPOINT = 6, /* bad or corrupt MLP checkpoint */
-  FIRE_ERR_STATE = 7       /* call not valid in the context's state */
+  FIRE_ERR_STATE = 7,      /* call not valid in the context's state */
+  FIRE_ERR_BOUNDS = 8      /* bounds-checked builds only (FIRERT_DEBUG): an index check
+                              in a fit kernel failed and its access was skipped; the
+                              site is in fire_debug_word */
 } fire_status_t;
 
 /* Per-pixel status byte: low 3 bits are the outcome, upper bits are flags. */
@@ -526,6 +529,20 @@ typedef void (*fire_free_fn)(void *ptr, void *user);
 void fire_set_allocator(fire_alloc_fn alloc, fire_free_fn free_fn, void *user);
 
 const char *fire_status_str(fire_status_t s);
+
+/* Build flags of the loaded library: bit 0 set when it was compiled with
+ * FIRERT_DEBUG, the bounds-checked build (libfirert_debug.so), in which the
+ * fit kernels (stage 1, both stage 2s, finalize) check their per-pixel
+ * indices, band indices and shared-memory regions before the access; a
+ * failed check records its site in the fit's device error word (the first
+ * failure wins), skips the access and never traps. The release build
+ * compiles the checks out. */
+int32_t fire_build_flags(void);
+/* The context's device error word after its last fit (synchronises the
+ * device): 0, 1 (a bounded wait gave up: FIRE_ERR_TIMEOUT) or 0x100 | site
+ * (a failed index check of a bounds-checked build: FIRE_ERR_BOUNDS). Errors:
+ * FIRE_ERR_ARG, FIRE_ERR_CUDA. */
+fire_status_t fire_debug_word(fire_ctx_t *ctx, int32_t *word);
 
 #ifdef __cplusplus
 }

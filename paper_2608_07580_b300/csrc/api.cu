@@ -400,6 +400,30 @@ void fire_default_priors(fire_priors_t *p, int32_t K, int32_t nt, float tlo, flo
   p->init_state = nullptr;
 }
 
+// the status a fit reports for its device error word: 1 from a bounded wait
+// that gave up, 0x100 | site from a failed index check (FIRERT_DEBUG)
+static fire_status_t err_status(int err) {
+  if (!err) return FIRE_OK;
+  return (err & kErrBounds) ? FIRE_ERR_BOUNDS : FIRE_ERR_TIMEOUT;
+}
+
+int32_t fire_build_flags(void) {
+#ifdef FIRERT_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+fire_status_t fire_debug_word(fire_ctx_t *c, int32_t *word) {
+  if (!c || !word) return FIRE_ERR_ARG;
+  CK(cudaDeviceSynchronize());
+  int err = 0;
+  CK(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  *word = err;
+  return FIRE_OK;
+}
+
 const char *fire_status_str(fire_status_t s) {
   switch (s) {
     case FIRE_OK: return "ok";
@@ -410,6 +434,7 @@ const char *fire_status_str(fire_status_t s) {
     case FIRE_ERR_TIMEOUT: return "device wait timed out";
     case FIRE_ERR_CHECKPOINT: return "bad checkpoint";
     case FIRE_ERR_STATE: return "invalid state";
+    case FIRE_ERR_BOUNDS: return "index check failed (bounds-checked build)";
   }
   return "unknown status";
 }
@@ -806,7 +831,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
     CK(cudaStreamSynchronize(st));
     int err = 0;
     CK(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    return err ? FIRE_ERR_TIMEOUT : FIRE_OK;
+    return err_status(err);
   }
   CK(cudaMemcpyAsync(d_rad, sc->radiance, s_rad, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_wv, sc->wv_bin, s_wv, cudaMemcpyHostToDevice, st));
@@ -825,7 +850,7 @@ fire_status_t fire_retrieve(fire_ctx_t *c, const fire_scene_t *sc, const fire_pr
   CK(cudaStreamSynchronize(st));
   int err = 0;
   CK(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  return err ? FIRE_ERR_TIMEOUT : FIRE_OK;
+  return err_status(err);
 }
 
 fire_status_t fire_set_kernel_timing(fire_ctx_t *c, int32_t on) {
@@ -891,7 +916,7 @@ fire_status_t fire_get_stats(fire_ctx_t *c, fire_stats_t *s) {
   s->flops2 = f2 * (double)s->band_evals2 + 12.0 * (double)s->node_band_evals2;
   s->flops = s->flops1 + s->flops2;
   s->kernel_launches = c->last_launches;
-  return err ? FIRE_ERR_TIMEOUT : FIRE_OK;
+  return err_status(err);
 }
 
 fire_status_t fire_forward(fire_ctx_t *c, int32_t mode, const float *state, const uint16_t *wv,

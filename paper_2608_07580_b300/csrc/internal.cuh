@@ -13,6 +13,32 @@ constexpr int kMaxTgrid = 128;
 constexpr int kMaxBands = 512;
 constexpr int kScratchPerNode = 8;   // floats per grid node in the warp scratch
 
+// Device error word of a fit: 1 when a bounded wait gave up; kErrBounds |
+// site when an index check of a bounds-checked build failed.
+constexpr int kErrBounds = 0x100;
+
+// Index checks of the bounds-checked build (compiled with FIRERT_DEBUG):
+// fr_ok(ok, err, site) is ok; a false check records kErrBounds | site in the
+// error word (the first failure wins) and the caller skips the access. Never
+// traps. In the release build the check is the constant true and the
+// condition is not evaluated.
+#ifdef FIRERT_DEBUG
+__device__ __forceinline__ bool fr_check(bool ok, int *err, int site) {
+  if (!ok && err) atomicCAS(err, 0, kErrBounds | site);
+  return ok;
+}
+#define fr_ok(ok, err, site) ::firert::fr_check((ok), (err), (site))
+#else
+#define fr_ok(ok, err, site) true
+#endif
+
+// bytes of dynamic shared memory the running kernel was launched with
+__device__ __forceinline__ unsigned dyn_smem_bytes() {
+  unsigned v;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
+
 // per-pixel status codes (mirrors the header)
 enum : int {
   PX_CONVERGED = 0, PX_MAXITER = 1, PX_NONFINITE = 2, PX_ALL_MASKED = 3, PX_CHOL_FAIL = 4,

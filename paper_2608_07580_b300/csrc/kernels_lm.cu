@@ -1556,7 +1556,7 @@ __device__ __forceinline__ int setup1(Stage1<K, G> &s1, const PixCtx &pc, const 
 // stage-2 band count as count2 forms it (the stage-2 bands lie inside the
 // stage-1 range). fin, n1u, n2u and the prior scale are warp totals.
 __device__ __forceinline__ void setup1_warp(const PixCtx &pc, int lane, const float *row, float *bb, int nbs,
-                                            bool &fin, int &n1u, int &n2u, float &psc) {
+                                            bool &fin, int &n1u, int &n2u, float &psc, int *err) {
   const KTables &t = *pc.t;
   const KConfig &c = *pc.c;
   float nv = 0.f;
@@ -1565,7 +1565,7 @@ __device__ __forceinline__ void setup1_warp(const PixCtx &pc, int lane, const fl
 #pragma unroll 1
   for (int i = lane; i < nbs; i += 32) {
     float Lv = 0.f, wv = 0.f;
-    if (i < t.n1) {
+    if (i < t.n1 && fr_ok(t.b1lo + i < t.nb, err, 13)) {   // site 13: band inside the row
       const int b = t.b1lo + i;
       const float L = __ldg(row + b);
       f = f && isfinite(L);
@@ -1749,6 +1749,12 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
   Stage1<K, G> S;
   S.nbs = band_slots(t.n1, G);
   S.bb = smem + img_f + wv_f + (threadIdx.x / G) * pix_stride1(t, G);
+#ifdef FIRERT_DEBUG
+  // site 11: this group's band buffers end inside the launch's shared memory
+  if (!__syncthreads_and(fr_ok(reinterpret_cast<unsigned char *>(S.bb + 4 * S.nbs) <=
+                                   reinterpret_cast<unsigned char *>(smem) + dyn_smem_bytes(), p.w.err, 11)))
+    return;
+#endif
   const int NSx = K + 8;
   const long long n = p.s.n_pix;
   const int nclaim = p.s.claim > 0 ? p.s.claim : kClaim;
@@ -1785,8 +1791,12 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
         }
         if (!done) {
           pix = next++;
-          ref = resolve(p, pix, K);
-          have = true;
+          if (fr_ok(pix < n, p.w.err, 12)) {   // site 12: claimed pixel
+            ref = resolve(p, pix, K);
+            have = true;
+          } else {
+            done = true;
+          }
         }
       }
       const float *row = ref.row;
@@ -1803,7 +1813,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
           int a1, a2;
           float ps;
           float *bbs = smem + img_f + wv_f + ((threadIdx.x & ~31) + src) / G * pix_stride1(t, G);
-          setup1_warp(pc, lane, rs, bbs, S.nbs, fs, a1, a2, ps);
+          setup1_warp(pc, lane, rs, bbs, S.nbs, fs, a1, a2, ps, p.w.err);
           if ((lane ^ src) < G) {
             fin = fs;
             n1u = a1;
@@ -1983,6 +1993,13 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
   bool active = false, done = false, first = false;
   float x[6], xt[6], H[21], g[6], gf[6], cst = 0.f, cd = 0.f;
   float *ne = S.bb + 5 * S.nbs;   // trial H, g, gradient floor
+#ifdef FIRERT_DEBUG
+  // site 31: this group's node scratch, band buffers and normal-equation
+  // block end inside the launch's shared memory
+  if (!__syncthreads_and(fr_ok(reinterpret_cast<unsigned char *>(ne + kNE2) <=
+                                   reinterpret_cast<unsigned char *>(smem) + dyn_smem_bytes(), p.w.err, 31)))
+    return;
+#endif
   int rc = 0, nfull = 0, status = 0, n2u = 0;
   LMIter<6> L;
   AdamState<6> A;
@@ -1995,6 +2012,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
         end = min(b + (long long)nclaim, n);
       }
       pix = next++;
+      if (!fr_ok(pix < n, p.w.err, 32)) { done = true; break; }   // site 32: claimed pixel
       const int meta = p.w.s1meta[pix];
       if (!(meta & kFitted)) continue;
       status = meta & 0xff;
@@ -2225,13 +2243,13 @@ __device__ __forceinline__ int setup_slot(const KTables &t, const KConfig &c, co
 template <int K>
 __device__ __forceinline__ int setup_slot_warp(const KTables &t, const KConfig &c, int lane,
                                                const float4 *wvrow, const float *row, const float (&xs)[K],
-                                               float *sb, int nbs, float &psc) {
+                                               float *sb, int nbs, float &psc, int *err) {
   float nv = 0.f;
   int nu = 0;
 #pragma unroll 1
   for (int i = lane; i < nbs; i += 32) {
     float yv = 0.f, tv = 0.f;
-    if (i < t.n2) {
+    if (i < t.n2 && fr_ok(t.b2lo + i < t.nb, err, 23)) {   // site 23: band inside the row
       const int b = t.b2lo + i;
       const float L = __ldg(row + b);
       const bool ok = __ldg(t.image + t.lay.off_win2 + b) > 0.f && !(t.sat && L >= __ldg(t.sat + b));
@@ -2601,6 +2619,14 @@ __device__ __forceinline__ bool setup(const LMLaunch &p, float *smem, unsigned l
   // tensor memory: 64 columns per cohort and band tile, allocated as a power of 2
   C.cols = 32;
   while (C.cols < kCohorts * kNc * C.ntile) C.cols <<= 1;
+#ifdef FIRERT_DEBUG
+  // site 21: the partial sums end inside the launch's shared memory; 22:
+  // the cohorts' accumulators fit the 512 TMEM columns
+  const bool in = fr_ok(reinterpret_cast<unsigned char *>(C.parts + kSlots * kPartStride) <=
+                            reinterpret_cast<unsigned char *>(smem) + dyn_smem_bytes(), p.w.err, 21) &&
+                  fr_ok(C.cols <= 512, p.w.err, 22);
+  if (!__syncthreads_and(in)) return false;
+#endif
   if (cta_err(p.w.err)) return false;
   // only the Planck operand is staged: the slot set-up reads the table image
   // from global memory
@@ -2758,6 +2784,7 @@ __global__ void __launch_bounds__(tcs2::kWarps * 32, 1) lm_stage2_tc_kernel(cons
         end = min(b + (long long)nclaim, n);
       }
       pix = next++;
+      if (!fr_ok(pix < n, p.w.err, 24)) { done = true; break; }   // site 24: claimed pixel
       const int meta = p.w.s1meta[pix];
       if (!(meta & kFitted)) continue;
       status = meta & 0xff;
@@ -2816,7 +2843,7 @@ __global__ void __launch_bounds__(tcs2::kWarps * 32, 1) lm_stage2_tc_kernel(cons
         float pss;
         const int nu = tcs2::setup_slot_warp<K>(t, c, lane, t.wvtab + (size_t)ws * t.nb, rs, xss,
                                                 C.slots + (((threadIdx.x & ~31) + src) / G) * C.sstride,
-                                                S.nbs, pss);
+                                                S.nbs, pss, p.w.err);
         if ((lane ^ src) < G) {
           n2u = nu;
           S.psc = pss;

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfirert.so")
+# FIRERT_DEBUG=1 in the environment loads the bounds-checked build
+LIB_PATH = os.path.join(_HERE, "libfirert_debug.so" if os.environ.get("FIRERT_DEBUG") == "1"
+                        else "libfirert.so")
 
 MAX_ENDM = 8
 FIRE_MEM_DEVICE, FIRE_MEM_HOST = 0, 1
@@ -33,7 +35,7 @@ SYMBOLS = ("fire_default_config", "fire_default_priors", "fire_ctx_create", "fir
            "fire_graph_capture", "fire_graph_launch", "fire_graph_destroy", "fire_autotune",
            "fire_set_tuning", "fire_set_kernel_timing", "fire_get_kernel_times",
            "fire_retrieve_static", "fire_set_allocator", "fire_measure_peak", "fire_wv_presolve",
-           "fire_wv_depth_table", "fire_inject", "fire_hfdi")
+           "fire_wv_depth_table", "fire_inject", "fire_hfdi", "fire_build_flags", "fire_debug_word")
 
 # device allocator hook (fire_set_allocator): alloc(bytes, user) -> ptr, free(ptr, user)
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -131,6 +133,10 @@ def _load():
     lib = C.CDLL(LIB_PATH)
     vp, i32, i64, f32, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_uint64
     lib.fire_default_config.argtypes = [C.POINTER(Config_t)]
+    lib.fire_build_flags.argtypes = []
+    lib.fire_build_flags.restype = C.c_int32
+    lib.fire_debug_word.argtypes = [vp, C.POINTER(C.c_int32)]
+    lib.fire_debug_word.restype = C.c_int
     lib.fire_default_priors.argtypes = [C.POINTER(Priors_t), i32, i32, f32, f32]
     lib.fire_ctx_create.argtypes = [C.POINTER(vp), C.POINTER(Tables_t), C.POINTER(Config_t)]
     lib.fire_ctx_create.restype = C.c_int
@@ -525,6 +531,18 @@ class Context:
         d = {f: getattr(s, f) for f, _ in Stats_t._fields_ if f != "status_counts"}
         d["status_counts"] = list(s.status_counts)
         return d
+
+    def debug_word(self):
+        """The device error word after the last fit (fire_debug_word): 0, 1 (a
+        bounded wait gave up) or 0x100 | site (a failed index check)."""
+        w = C.c_int32(0)
+        _check(lib.fire_debug_word(self._h, C.byref(w)), "fire_debug_word")
+        return w.value
+
+
+def build_flags():
+    """fire_build_flags: bit 0 set in the bounds-checked build."""
+    return int(lib.fire_build_flags())
 
 
 PEAK_KINDS = {"fp32_fma": 0, "fp32_fma2": 1, "sfu_ex2": 2, "fp64_fma": 3}

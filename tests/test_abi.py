@@ -98,3 +98,18 @@ def test_config_and_priors_layout_carry_the_new_fields():
     p = firert.default_priors(3)
     assert p.noise_sd is None                 # unweighted Eq. (loss) by default
     assert "resid_spec" in firert.OUTPUT_FIELDS
+
+
+def test_bounds_checked_build_exports_every_symbol_and_says_so():
+    """The FIRERT_DEBUG build (libfirert_debug.so): same ABI, build flag set;
+    the release build's flag is clear."""
+    from paper_2608_07580_b300 import build
+    dbg = C.CDLL(build.build(debug=True))
+    rel = C.CDLL(build.build())
+    for name in sorted(_declared()):
+        assert hasattr(dbg, name), name
+    dbg.fire_build_flags.restype = rel.fire_build_flags.restype = C.c_int32
+    assert dbg.fire_build_flags() & 1 == 1
+    assert rel.fire_build_flags() & 1 == 0
+    dbg.fire_status_str.restype = C.c_char_p
+    assert b"index check" in dbg.fire_status_str(8)
