@@ -1650,6 +1650,49 @@ __device__ __forceinline__ int setup2(Stage2<G> &s2, const PixCtx &pc, const Grp
   return nu;
 }
 
+// setup2 of one pixel by a whole warp (32 lanes over its bands; bb is the
+// pixel's band buffers, [5][nbs] as Stage2 lays them out); returns the
+// used-band count, psc the prior scale (warp totals)
+template <int K>
+__device__ __forceinline__ int setup2_warp(const PixCtx &pc, int lane, const float4 *wvrow, const float *row,
+                                           const float (&xs)[K], float *bb, int nbs, float &psc, int *err) {
+  const KTables &t = *pc.t;
+  const KConfig &c = *pc.c;
+  float nv = 0.f;
+  int nu = 0;
+#pragma unroll 1
+  for (int i = lane; i < nbs; i += 32) {
+    float yv = 0.f, tv = 0.f, wv = 0.f;
+    if (i < t.n2 && fr_ok(t.b2lo + i < t.nb, err, 33)) {   // site 33: band inside the row
+      const int b = t.b2lo + i;
+      const float L = __ldg(row + b);
+      const bool ok = pc.img[t.lay.off_win2 + b] > 0.f && !(t.sat && L >= __ldg(t.sat + b));
+      const float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
+      const float4 q = __ldg(wvrow + b);
+      float rho = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; k++) rho = fmaf(xs[k], pc.img[t.lay.off_endm + k * t.nb + b], rho);
+      yv = L - (q.y + q.x * rho / (1.f - q.z * rho));
+      tv = q.w;
+      wv = ok ? (c.weighted ? 1.f / (c.has_nsd ? c.nsd[b] * c.nsd[b] : var) : 1.f) : 0.f;
+      if (ok) { nv += var; nu++; }
+    }
+    bb[i] = yv;
+    bb[nbs + i] = tv;
+    bb[2 * nbs + i] = wv;
+    bb[3 * nbs + i] = yv;
+    bb[4 * nbs + i] = yv;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    nv += __shfl_xor_sync(kFull, nv, o);
+    nu += __shfl_xor_sync(kFull, nu, o);
+  }
+  psc = c.weighted ? 1.f : nv / (float)max(nu, 1);
+  __syncwarp();
+  return nu;
+}
+
 // Where pixel pix reads its inputs and writes its outputs: the single scene
 // (optionally through a subset index), or the scene of a batch that holds
 // global pixel pix (binary search over the scenes' first pixels).
@@ -2003,6 +2046,11 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
   int rc = 0, nfull = 0, status = 0, n2u = 0;
   LMIter<6> L;
   AdamState<6> A;
+  // a pixel taken this round whose set-up is pending (16-lane groups: the
+  // warp sets it up): radiance row, stage-1 surface weights
+  bool pend = false;
+  const float *prow = nullptr;
+  float xsp[K];
   for (;;) {
     while (!active && !done) {
       if (next >= end) {
@@ -2024,7 +2072,14 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       float xs[K];
 #pragma unroll
       for (int k = 0; k < K; k++) xs[k] = x1[k];
-      n2u = setup2<K>(S, pc, gp, ref.row, xs);
+      if constexpr (G == 32) {
+        n2u = setup2<K>(S, pc, gp, ref.row, xs);
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; k++) xsp[k] = xs[k];
+        prow = ref.row;
+        pend = true;
+      }
       // the start derived from the stage-1 result
       const float T1 = x1[K + 1];
       x[0] = fminf(fmaxf(fmaxf(T1, c.init_mu_h_floor), c.lo2[0]), c.hi2[0]);
@@ -2058,6 +2113,31 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
       rc = 0;
       nfull = 0;
       active = true;
+    }
+    if constexpr (G < 32) {
+      // the set-ups of the pixels the warp's groups just took, one after the
+      // other, each by the whole warp (32 lanes over the bands instead of 16)
+      unsigned need = __ballot_sync(kFull, pend && gp.sub == 0);
+      while (need) {
+        const int src = __ffs(need) - 1;
+        need &= need - 1;
+        const float *rs = reinterpret_cast<const float *>(
+            __shfl_sync(kFull, reinterpret_cast<unsigned long long>(prow), src));
+        const float4 *ws = reinterpret_cast<const float4 *>(
+            __shfl_sync(kFull, reinterpret_cast<unsigned long long>(pc.wvrow), src));
+        float xss[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) xss[k] = __shfl_sync(kFull, xsp[k], src);
+        float *bbs = smem + img_f + ((threadIdx.x & ~31) + src) / G * pix_stride2(t, G) +
+                     t.nt * kScratchPerNode;
+        float pss;
+        const int nu = setup2_warp<K>(pc, lane, ws, rs, xss, bbs, S.nbs, pss, p.w.err);
+        if ((lane ^ src) < G) {
+          n2u = nu;
+          S.psc = pss;
+        }
+      }
+      pend = false;
     }
     if (__all_sync(kFull, done)) break;
     bool go = active;
