@@ -1549,12 +1549,33 @@ __device__ __forceinline__ int setup1(Stage1<K, G> &s1, const PixCtx &pc, const 
   return nu;
 }
 
+// A warp-wide loop over a pixel's bands (lane l takes band i0 + l of each
+// block of 32) that sums like the pixel's G-lane group would: class_add adds,
+// in band order, the values of this lane's class (lane mod G) in the block,
+// so that every lane holds its group lane's running sum; class_total then
+// reduces the G classes with Grp<G>::sum1's butterfly. The results are the
+// group loop's to the bit.
+template <int G>
+__device__ __forceinline__ float class_add(float acc, float v, int lane) {
+#pragma unroll
+  for (int q = 0; q < 32 / G; q++) acc += __shfl_sync(kFull, v, (lane & (G - 1)) + q * G);
+  return acc;
+}
+template <int G>
+__device__ __forceinline__ float class_total(float acc) {
+#pragma unroll
+  for (int o = G / 2; o; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  return acc;
+}
+
 // The ungated intake of one pixel in one pass over its radiance row, by a
 // whole warp (32 lanes over the row: at 8 lanes a pixel a quarter of the
 // dependent loads per lane): the finiteness of every band, the stage-1
 // buffers as setup1 builds them (bb, the pixel's band buffers) and the
 // stage-2 band count as count2 forms it (the stage-2 bands lie inside the
-// stage-1 range). fin, n1u, n2u and the prior scale are warp totals.
+// stage-1 range). fin, n1u, n2u and the prior scale are warp totals, the
+// prior scale summed in the order of the pixel's G-lane group.
+template <int G>
 __device__ __forceinline__ void setup1_warp(const PixCtx &pc, int lane, const float *row, float *bb, int nbs,
                                             bool &fin, int &n1u, int &n2u, float &psc, int *err) {
   const KTables &t = *pc.t;
@@ -1563,8 +1584,9 @@ __device__ __forceinline__ void setup1_warp(const PixCtx &pc, int lane, const fl
   int nu = 0, nu2 = 0;
   bool f = true;
 #pragma unroll 1
-  for (int i = lane; i < nbs; i += 32) {
-    float Lv = 0.f, wv = 0.f;
+  for (int i0 = 0; i0 < nbs; i0 += 32) {
+    const int i = i0 + lane;
+    float Lv = 0.f, wv = 0.f, vv = 0.f;
     if (i < t.n1 && fr_ok(t.b1lo + i < t.nb, err, 13)) {   // site 13: band inside the row
       const int b = t.b1lo + i;
       const float L = __ldg(row + b);
@@ -1574,22 +1596,25 @@ __device__ __forceinline__ void setup1_warp(const PixCtx &pc, int lane, const fl
       const float var = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
       Lv = L;
       wv = ok ? (c.weighted ? 1.f / (c.has_nsd ? c.nsd[b] * c.nsd[b] : var) : 1.f) : 0.f;
-      if (ok) { nv += var; nu++; }
+      if (ok) { vv = var; nu++; }
       if (b >= t.b2lo && b < t.b2lo + t.n2) nu2 += (pc.img[t.lay.off_win2 + b] > 0.f && unsat) ? 1 : 0;
     }
-    bb[i] = Lv;
-    bb[nbs + i] = wv;
-    bb[2 * nbs + i] = 0.f;
-    bb[3 * nbs + i] = 0.f;
+    nv = class_add<G>(nv, vv, lane);
+    if (i < nbs) {
+      bb[i] = Lv;
+      bb[nbs + i] = wv;
+      bb[2 * nbs + i] = 0.f;
+      bb[3 * nbs + i] = 0.f;
+    }
   }
 #pragma unroll 1
   for (int b = lane; b < t.b1lo; b += 32) f = f && isfinite(__ldg(row + b));
 #pragma unroll 1
   for (int b = t.b1lo + t.n1 + lane; b < t.nb; b += 32) f = f && isfinite(__ldg(row + b));
   fin = __all_sync(kFull, f);
+  nv = class_total<G>(nv);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    nv += __shfl_xor_sync(kFull, nv, o);
     nu += __shfl_xor_sync(kFull, nu, o);
     nu2 += __shfl_xor_sync(kFull, nu2, o);
   }
@@ -1653,7 +1678,7 @@ __device__ __forceinline__ int setup2(Stage2<G> &s2, const PixCtx &pc, const Grp
 // setup2 of one pixel by a whole warp (32 lanes over its bands; bb is the
 // pixel's band buffers, [5][nbs] as Stage2 lays them out); returns the
 // used-band count, psc the prior scale (warp totals)
-template <int K>
+template <int K, int G>
 __device__ __forceinline__ int setup2_warp(const PixCtx &pc, int lane, const float4 *wvrow, const float *row,
                                            const float (&xs)[K], float *bb, int nbs, float &psc, int *err) {
   const KTables &t = *pc.t;
@@ -1661,8 +1686,9 @@ __device__ __forceinline__ int setup2_warp(const PixCtx &pc, int lane, const flo
   float nv = 0.f;
   int nu = 0;
 #pragma unroll 1
-  for (int i = lane; i < nbs; i += 32) {
-    float yv = 0.f, tv = 0.f, wv = 0.f;
+  for (int i0 = 0; i0 < nbs; i0 += 32) {
+    const int i = i0 + lane;
+    float yv = 0.f, tv = 0.f, wv = 0.f, vv = 0.f;
     if (i < t.n2 && fr_ok(t.b2lo + i < t.nb, err, 33)) {   // site 33: band inside the row
       const int b = t.b2lo + i;
       const float L = __ldg(row + b);
@@ -1675,19 +1701,20 @@ __device__ __forceinline__ int setup2_warp(const PixCtx &pc, int lane, const flo
       yv = L - (q.y + q.x * rho / (1.f - q.z * rho));
       tv = q.w;
       wv = ok ? (c.weighted ? 1.f / (c.has_nsd ? c.nsd[b] * c.nsd[b] : var) : 1.f) : 0.f;
-      if (ok) { nv += var; nu++; }
+      if (ok) { vv = var; nu++; }
     }
-    bb[i] = yv;
-    bb[nbs + i] = tv;
-    bb[2 * nbs + i] = wv;
-    bb[3 * nbs + i] = yv;
-    bb[4 * nbs + i] = yv;
+    nv = class_add<G>(nv, vv, lane);
+    if (i < nbs) {
+      bb[i] = yv;
+      bb[nbs + i] = tv;
+      bb[2 * nbs + i] = wv;
+      bb[3 * nbs + i] = yv;
+      bb[4 * nbs + i] = yv;
+    }
   }
+  nv = class_total<G>(nv);
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    nv += __shfl_xor_sync(kFull, nv, o);
-    nu += __shfl_xor_sync(kFull, nu, o);
-  }
+  for (int o = 16; o; o >>= 1) nu += __shfl_xor_sync(kFull, nu, o);
   psc = c.weighted ? 1.f : nv / (float)max(nu, 1);
   __syncwarp();
   return nu;
@@ -1856,7 +1883,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage1_kernel(const __grid_co
           int a1, a2;
           float ps;
           float *bbs = smem + img_f + wv_f + ((threadIdx.x & ~31) + src) / G * pix_stride1(t, G);
-          setup1_warp(pc, lane, rs, bbs, S.nbs, fs, a1, a2, ps, p.w.err);
+          setup1_warp<G>(pc, lane, rs, bbs, S.nbs, fs, a1, a2, ps, p.w.err);
           if ((lane ^ src) < G) {
             fin = fs;
             n1u = a1;
@@ -2131,7 +2158,7 @@ __global__ void __launch_bounds__(MAXW * 32, 1) lm_stage2_kernel(const __grid_co
         float *bbs = smem + img_f + ((threadIdx.x & ~31) + src) / G * pix_stride2(t, G) +
                      t.nt * kScratchPerNode;
         float pss;
-        const int nu = setup2_warp<K>(pc, lane, ws, rs, xss, bbs, S.nbs, pss, p.w.err);
+        const int nu = setup2_warp<K, G>(pc, lane, ws, rs, xss, bbs, S.nbs, pss, p.w.err);
         if ((lane ^ src) < G) {
           n2u = nu;
           S.psc = pss;
@@ -2327,8 +2354,9 @@ __device__ __forceinline__ int setup_slot_warp(const KTables &t, const KConfig &
   float nv = 0.f;
   int nu = 0;
 #pragma unroll 1
-  for (int i = lane; i < nbs; i += 32) {
-    float yv = 0.f, tv = 0.f;
+  for (int i0 = 0; i0 < nbs; i0 += 32) {
+    const int i = i0 + lane;
+    float yv = 0.f, tv = 0.f, vv = 0.f;
     if (i < t.n2 && fr_ok(t.b2lo + i < t.nb, err, 23)) {   // site 23: band inside the row
       const int b = t.b2lo + i;
       const float L = __ldg(row + b);
@@ -2340,18 +2368,19 @@ __device__ __forceinline__ int setup_slot_warp(const KTables &t, const KConfig &
         for (int k = 0; k < K; k++) rho = fmaf(xs[k], __ldg(t.image + t.lay.off_endm + k * t.nb + b), rho);
         yv = L - (q.y + q.x * rho / (1.f - q.z * rho));
         tv = q.w;
-        nv += c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
+        vv = c.noise_rel * c.noise_rel * L * L + c.noise_abs * c.noise_abs;
         nu++;
       }
     }
-    sb[i] = yv;
-    sb[nbs + i] = tv;
+    nv = class_add<G>(nv, vv, lane);
+    if (i < nbs) {
+      sb[i] = yv;
+      sb[nbs + i] = tv;
+    }
   }
+  nv = class_total<G>(nv);
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    nv += __shfl_xor_sync(kFull, nv, o);
-    nu += __shfl_xor_sync(kFull, nu, o);
-  }
+  for (int o = 16; o; o >>= 1) nu += __shfl_xor_sync(kFull, nu, o);
   psc = nv / (float)max(nu, 1);
   __syncwarp();
   return nu;
