@@ -278,8 +278,8 @@ def tensor_figure(stats, n2, ms_per_fit, peaks):
 # of the 256 x 1024 flight-line sub-chunk (262,144 px) of the current
 # kernels; a launch reads each pixel's inputs once, so its traffic scales
 # with the pixels it fits. Empty while the kernels are newer than the capture.
-PROFILED_TRAFFIC_PER_PX = {"lm_stage2_tc_kernel": (264.735e6 + 32.241e6) / 262144,
-                           "lm_stage1_kernel": (300.746e6 + 13.560e6) / 262144}
+PROFILED_TRAFFIC_PER_PX = {"lm_stage2_tc_kernel": (264.605e6 + 32.627e6) / 262144,
+                           "lm_stage1_kernel": (302.378e6 + 13.215e6) / 262144}
 
 TC_N = 64     # D columns per tensor-core round: one cohort's 8 pixel slots x 8 node coefficients
 
