@@ -196,7 +196,7 @@ def run_reference(args):
 # ------------------------------------------------------------ parity ----
 def parity_block(o, g, kind):
     """The retrieval's outputs against the oracle's on the same inputs:
-    the benchmark spec's bar over the oracle's converged identifiable pixels (GPU
+    the parity bar over the oracle's converged identifiable pixels (GPU
     non-convergence a miss), the secondary outputs, the non-fire pixels'
     surface fractions, alpha and cost, and the error per output."""
     from scenes import parity_stats, summary

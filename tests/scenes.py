@@ -47,7 +47,7 @@ IDENT_BAND = 0.1
 
 
 def parity_stats(o, g, bar_T=0.5, bar_a=1e-3, cfg=None, ident_band=IDENT_BAND):
-    """Parity of GPU outputs g with oracle outputs o (the benchmark spec's bar).
+    """Parity of GPU outputs g with oracle outputs o (the parity bar).
 
     The pool is every pixel the oracle calls converged and identifiable. A
     pool pixel passes when the GPU also converged and |dE[T]| <= 0.5 K and

@@ -118,7 +118,7 @@ _ALL = []
 
 
 def assert_parity(s, min_pool, what=""):
-    """The benchmark spec's bar (>= 99.9 % of the oracle's converged identifiable
+    """The parity bar (>= 99.9 % of the oracle's converged identifiable
     pixels, GPU non-convergence counted as a miss) on a pool of at least
     min_pool pixels; the secondary outputs (sigma[T], cost, rms) of the
     pixels that pass agree on >= 99 % of them (cost and rms follow the
